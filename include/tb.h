@@ -1,0 +1,218 @@
+/*
+ * tb.h - C ABI of the GB300 linear-scaling tight-binding force library.
+ *
+ * The library evaluates, for every target atom of a periodic cubic cell, the
+ * local electronic structure of the paper's linear-scaling method:
+ *   cluster of atoms within the cutoff radius (Sec. 2, locality),
+ *   block Krylov space seeded with the target's four sp3 orbitals
+ *   (Sec. 3, Eq. (Krylov), block form of Eqs. (lanczos)/(lanczos_blas3)),
+ *   eigenpairs of the projected matrix T = V^T H V (Sec. 3),
+ *   density-matrix columns rho|i,a> with the occupation f(e) (Sec. 2),
+ *   a global chemical potential, and forces <F_i> = Tr[rho F_i] (Sec. 2),
+ * on the Hamiltonian of Eq. (1) (orthogonal sp3 Slater-Koster model with GSP
+ * distance scaling; Sec. 5 names Xu's parameterisation and its 2.6 A cutoff).
+ *
+ * General rules
+ *  - Every array argument is a DEVICE pointer owned by the caller, unless the
+ *    argument's comment says "host".  The library owns only the opaque context
+ *    (parameters, device workspace, a device status word).
+ *  - Every call is ordered on `stream` (a cudaStream_t passed as void*; NULL is
+ *    the legacy default stream) and returns without synchronising the host.
+ *    After tb_ctx_reserve no call allocates memory, so the call sequence can be
+ *    captured into a CUDA graph.  tb_ctx_create / tb_ctx_reserve /
+ *    tb_ctx_destroy / tb_get_status are not capturable.
+ *  - Host-side argument errors return a status at once.  Problems detected on
+ *    the device (capacity overflow, non-finite values, eigen-iteration or mu
+ *    non-convergence, a wait that timed out, positions outside [0, L)) are
+ *    written to the context's device status word (first error wins) and are
+ *    read back with tb_get_status.  No call traps or aborts.
+ *  - Units: A, eV, fs, amu.  Forces in eV/A.  Positions must lie in [0, L).
+ *  - Orbital order on every atom: s, px, py, pz.
+ *  - Index type int32; sizes are int.
+ */
+#ifndef TB_H
+#define TB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tb_status {
+  TB_OK = 0,
+  TB_ERR_INVALID_ARG = 1,     /* bad pointer/size/parameter, or position outside [0,L) */
+  TB_ERR_CUDA = 2,            /* a CUDA runtime call failed                            */
+  TB_ERR_NOMEM = 3,           /* workspace allocation failed (tb_ctx_reserve only)     */
+  TB_ERR_CAPACITY = 4,        /* a list or cluster exceeded max_hnbr / max_cluster     */
+  TB_ERR_NONFINITE = 5,       /* NaN/Inf met in an input or intermediate              */
+  TB_ERR_BREAKDOWN = 6,       /* Krylov seed block lost rank (cannot happen for E_i)   */
+  TB_ERR_NO_CONVERGENCE = 7,  /* projected eigensolve or mu search did not converge    */
+  TB_ERR_TIMEOUT = 8,         /* a bounded device-side wait gave up                    */
+  TB_ERR_NOT_RESERVED = 9     /* workspace missing or too small for n                  */
+} tb_status;
+
+typedef enum tb_precision {
+  /* Everything in FP64. */
+  TB_PREC_FP64 = 0,
+  /* H.V sweeps, Krylov basis and its inner products in FP32; the block
+   * tridiagonal T, eigenvalues (FP64 Rayleigh quotients), mu, density-matrix
+   * blocks, energies and forces in FP64. */
+  TB_PREC_MIXED = 1
+} tb_precision;
+
+/* Model and numerical parameters (all lengths A, energies eV). */
+typedef struct tb_params {
+  /* Eq. (1): on-site energies and Slater-Koster two-centre integrals at r0 */
+  double Es, Ep, Vss, Vsp, Vpps, Vppp;
+  /* hopping scaling s(r) = (r0/r)^n exp{n[-(r/rc)^nc + (r0/rc)^nc]} */
+  double r0, n, nc, rc;
+  /* pair repulsion phi(r) = phi0 (d0/r)^m exp{m[-(r/dc)^mc + (d0/dc)^mc]} */
+  double phi0, d0, m, mc, dc;
+  /* C1 cubic tail on [r1, rm]; s and phi vanish for r >= rm (the hopping
+   * cutoff; the Hamiltonian neighbour list uses r <= rm) */
+  double r1, rm;
+  double kT;          /* Fermi smearing (eV), > 0                                */
+  double Rc;          /* cluster cutoff radius (A), Rc >= rm, Rc < L/2 advisable */
+  double defl_tol;    /* absolute deflation threshold on a new Krylov column (eV)*/
+  double mu_tol;      /* mu search stops when |N(mu) - N_e| <= mu_tol * N_e      */
+  int r;              /* Krylov block order: basis of r blocks, 4r columns, 1..16 */
+  int prec;           /* tb_precision                                            */
+  int max_hnbr;       /* capacity of one Hamiltonian neighbour list, <= 32       */
+  int max_cluster;    /* capacity of one cluster (target included), <= 1024      */
+  int reorth_passes;  /* classical Gram-Schmidt passes against all blocks: 1 or 2*/
+  int mu_max_iter;    /* cap on mu search passes (e.g. 100)                      */
+  long long timeout_cycles; /* budget of any device spin-wait, in SM clocks      */
+} tb_params;
+
+typedef struct tb_ctx tb_ctx;
+
+/* Fill *p with the library defaults for numerical fields (model constants are
+ * zeroed: the caller sets them).  Host pointer.  Never fails for p != NULL. */
+tb_status tb_params_default(tb_params* p);
+
+/* Create a context on the current CUDA device.  *out (host) receives the
+ * handle.  Validates *p (host).  Allocates a small device status word.  */
+tb_status tb_ctx_create(tb_ctx** out, const tb_params* p);
+
+/* Free the context and its workspace.  Synchronises the device. */
+tb_status tb_ctx_destroy(tb_ctx* ctx);
+
+/* Allocate (or grow) the device workspace for systems of up to n_atoms atoms.
+ * The only call after tb_ctx_create that allocates.  Synchronises. */
+tb_status tb_ctx_reserve(tb_ctx* ctx, int n_atoms);
+
+/* Bytes of device workspace currently held (host out). */
+tb_status tb_ctx_workspace_bytes(const tb_ctx* ctx, size_t* bytes);
+
+/* Read and clear the device status word: *code (host) gets a tb_status, *info
+ * (host) an index or size qualifying it (e.g. the offending atom or the
+ * capacity that would have been needed).  Synchronises `stream`. */
+tb_status tb_get_status(tb_ctx* ctx, int* code, int* info, void* stream);
+
+/*
+ * a1. Neighbour and cluster lists (Sec. 2: atoms within the cutoff radius of
+ * the target).  Brute force over all pairs with an FP32 prefilter; the
+ * membership decision is the FP64 test below, so the lists are bit-exact:
+ *   d = x_j - x_i;  d -= L * rint(d / L)  (per component, ties to even)
+ *   r2 = (dx*dx + dy*dy) + dz*dz   (each operation rounded, no FMA)
+ *   Hamiltonian list of i: all j != i with r2 <= rm*rm, ascending j;
+ *   cluster of i: i itself first, then all j != i with r2 <= Rc*Rc, ascending.
+ * pos   [n*3]  FP64, row-major (x,y,z per atom), each in [0, L)
+ * h_off [n+1]  out, CSR offsets of the Hamiltonian lists
+ * h_idx [n*max_hnbr] out (capacity), CSR column indices
+ * c_off [n+1]  out, CSR offsets of the clusters
+ * c_idx [n*max_cluster] out (capacity)
+ * A list longer than its capacity sets TB_ERR_CAPACITY (info = the length
+ * needed) and is truncated to the capacity.
+ */
+tb_status tb_build_neighbors(tb_ctx* ctx, int n, const double* pos, double L,
+                             int* h_off, int* h_idx, int* c_off, int* c_idx,
+                             void* stream);
+
+/*
+ * a2. Hamiltonian blocks of Eq. (1) for every directed bond p = (i -> j),
+ * j = h_idx[p], d = R_j - R_i (minimum image), l = d/|d|:
+ *   Hblk[p*16 + a*4 + b]      = H_{i a, j b} = s(|d|) * SK_ab(l)
+ *   dHblk[p*48 + k*16 + a*4 + b] = d H_{i a, j b} / d d_k
+ *   (so dH/dR_i = -dHblk and dH/dR_j = +dHblk).
+ * The on-site block diag(Es, Ep, Ep, Ep) is implicit (not stored).
+ * Hmirror (optional, may be NULL): FP32 copy of Hblk, [p*16 + a*4 + b], used
+ * by TB_PREC_MIXED.  Arrays sized by h_off[n] entries.
+ */
+tb_status tb_assemble_H(tb_ctx* ctx, int n, const double* pos, double L,
+                        const int* h_off, const int* h_idx,
+                        double* Hblk, double* dHblk, float* Hmirror,
+                        void* stream);
+
+/*
+ * a3-a7. Per target atom i: cluster map, block Krylov space of order r from
+ * V_1 = E_i (the four orbitals of i), block Lanczos with full
+ * reorthogonalisation and deflation, T = block tridiagonal (A_k, B_k), its
+ * eigenpairs (lam_m, U), and the spectral record.  With NT = 4r and kdim[i]
+ * the number of Krylov columns kept (<= NT):
+ *   lambda[i*NT + m]            Ritz values, ascending, m < kdim[i]; 0 beyond
+ *   S[(i*4 + a)*NT + m]          = U[a][m], the seed-block components
+ *   P[((i + h_off[i] + q)*4 + b)*NT + m] = sum_l V[row(q,b)][l] U[l][m]
+ *       q = 0 is the target itself, q = 1..deg(i) its Hamiltonian neighbours
+ *       in h_idx order; P needs (n + h_off[n]) * 4 * NT doubles
+ *   kdim[i]                      int
+ * Then rho_{(q) b, i a} = sum_m P[q,b,m] f((lam_m - mu)/kT) S[a,m].
+ * Hmirror must be non-NULL when prec == TB_PREC_MIXED.
+ */
+tb_status tb_krylov_density(tb_ctx* ctx, int n, const int* c_off, const int* c_idx,
+                            const int* h_off, const int* h_idx,
+                            const double* Hblk, const float* Hmirror,
+                            double* lambda, double* S, double* P, int* kdim,
+                            void* stream);
+
+/*
+ * a8. Chemical potential: solves 2 sum_i sum_m w_im f((lam_im - mu)/kT) = N_e
+ * with w_im = sum_a S[i,a,m]^2 and f(x) = 1/(1+e^x), by bracketed Newton
+ * steps with bisection fallback, in FP64, in one cooperative launch.
+ * mu_guess (device, may be NULL): starting point if inside the bracket.
+ * mu (device, out): one double.  n_count (device, out, may be NULL): N(mu).
+ * Stops when |N(mu) - N_e| <= mu_tol * N_e or the bracket is below 1e-13 eV;
+ * after mu_max_iter passes sets TB_ERR_NO_CONVERGENCE (mu = best estimate).
+ */
+tb_status tb_find_mu(tb_ctx* ctx, int n, const double* lambda, const double* S,
+                     const int* kdim, double n_electrons, const double* mu_guess,
+                     double* mu, double* n_count, void* stream);
+
+/*
+ * a9-a10. Density-matrix blocks, energies and forces (Sec. 2: <F> = Tr[rho F]).
+ *   rho^(i)_{q b, i a} = sum_m P[q,b,m] f_m S[a,m]
+ *   F_k = 2 sum_{j in H(k)} sum_{a,b} [rho^(k)_{j b,k a} + rho^(j)_{k a,j b}]
+ *         dHblk(k->j)_{a b}  -  dE_rep/dR_k
+ *   (each density-matrix column from its own atom's Krylov run; pairwise, so
+ *   the forces sum to zero up to rounding).
+ * F [n*3] out, FP64.
+ * energies [8] out, FP64: {E_band, -TS, A = E_band - TS, E_rep,
+ *   E_total = A + E_rep, N(mu), mu, 0}.
+ *   E_band = 2 sum w f lam; -TS = 2 kT sum w [f ln f + (1-f) ln(1-f)];
+ *   E_rep = sum over bonds i<j of phi(r_ij).
+ */
+tb_status tb_forces(tb_ctx* ctx, int n, const double* pos, double L,
+                    const int* h_off, const int* h_idx, const double* dHblk,
+                    const double* lambda, const double* S, const double* P,
+                    const int* kdim, const double* mu, double* F,
+                    double* energies, void* stream);
+
+/*
+ * a12. One NVE velocity-Verlet step (fs, amu; 1 eV/(A amu) = 9.648533e-3 A/fs^2):
+ *   v += dt/2 F/m;  x = wrap(x + dt v);  F = F(x) [a1..a10];  v += dt/2 F/m.
+ * pos, vel, F [n*3] in/out.  F on entry must be the force at pos.
+ * energies [8] out as in tb_forces, with energies[7] = kinetic energy (eV).
+ * n_electrons = 4 n.  Uses the context's own list/H/spectral buffers.
+ */
+tb_status tb_md_step(tb_ctx* ctx, int n, double* pos, double* vel, double* F,
+                     double L, double dt_fs, double mass_amu, double* energies,
+                     void* stream);
+
+/* Library version string (static, host). */
+const char* tb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TB_H */

@@ -1,0 +1,19 @@
+"""GB300 (sm_103a) linear-scaling tight-binding forces: local block-Krylov
+density-matrix columns per target atom, global chemical potential, pair
+Hellmann-Feynman forces and velocity-Verlet MD, behind the C ABI of
+include/tb.h.  The Python layer only marshals arguments; importing the package
+loads libtb.so and raises if it has not been built.
+"""
+from . import binding
+from .binding import (TBParams, TBError, make_params, tb_ctx_create, tb_ctx_destroy,
+                      tb_ctx_reserve, tb_ctx_workspace_bytes, tb_get_status,
+                      tb_build_neighbors, tb_assemble_H, tb_krylov_density, tb_find_mu,
+                      tb_forces, tb_md_step, tb_version)
+from .system import TBSystem
+
+binding.lib()   # fail loudly now if the CUDA library is missing
+
+__all__ = ["TBParams", "TBError", "make_params", "tb_ctx_create", "tb_ctx_destroy",
+           "tb_ctx_reserve", "tb_ctx_workspace_bytes", "tb_get_status",
+           "tb_build_neighbors", "tb_assemble_H", "tb_krylov_density", "tb_find_mu",
+           "tb_forces", "tb_md_step", "tb_version", "TBSystem"]

@@ -1,0 +1,212 @@
+"""ctypes binding of the C ABI in include/tb.h.
+
+Argument marshalling only: every function below checks tensor dtype, device
+and contiguity, then forwards raw device pointers, sizes and the current CUDA
+stream to the function of the same name in libtb.so.  There is no CPU path: if
+the library is missing, importing this module raises.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtb.so")
+
+TB_OK = 0
+STATUS_NAMES = {0: "TB_OK", 1: "TB_ERR_INVALID_ARG", 2: "TB_ERR_CUDA", 3: "TB_ERR_NOMEM",
+                4: "TB_ERR_CAPACITY", 5: "TB_ERR_NONFINITE", 6: "TB_ERR_BREAKDOWN",
+                7: "TB_ERR_NO_CONVERGENCE", 8: "TB_ERR_TIMEOUT", 9: "TB_ERR_NOT_RESERVED"}
+TB_PREC_FP64 = 0
+TB_PREC_MIXED = 1
+
+EXPORTS = ["tb_params_default", "tb_ctx_create", "tb_ctx_destroy", "tb_ctx_reserve",
+           "tb_ctx_workspace_bytes", "tb_get_status", "tb_build_neighbors",
+           "tb_assemble_H", "tb_krylov_density", "tb_find_mu", "tb_forces", "tb_md_step",
+           "tb_version"]
+
+
+class TBParams(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("Es", "Ep", "Vss", "Vsp", "Vpps", "Vppp", "r0", "n", "nc", "rc",
+                 "phi0", "d0", "m", "mc", "dc", "r1", "rm", "kT", "Rc", "defl_tol",
+                 "mu_tol")] + \
+              [(k, ctypes.c_int) for k in
+               ("r", "prec", "max_hnbr", "max_cluster", "reorth_passes", "mu_max_iter")] + \
+              [("timeout_cycles", ctypes.c_longlong)]
+
+
+class TBError(RuntimeError):
+    def __init__(self, fn, code, info=None):
+        self.code = code
+        self.info = info
+        msg = f"{fn} -> {STATUS_NAMES.get(code, code)}"
+        if info is not None:
+            msg += f" (info {info})"
+        super().__init__(msg)
+
+
+def load_library(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"libtb.so not built at {path}: run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I, D, VP = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    sig = {
+        "tb_params_default": [ctypes.POINTER(TBParams)],
+        "tb_ctx_create": [ctypes.POINTER(P), ctypes.POINTER(TBParams)],
+        "tb_ctx_destroy": [P],
+        "tb_ctx_reserve": [P, I],
+        "tb_ctx_workspace_bytes": [P, ctypes.POINTER(ctypes.c_size_t)],
+        "tb_get_status": [P, ctypes.POINTER(I), ctypes.POINTER(I), VP],
+        "tb_build_neighbors": [P, I, VP, D, VP, VP, VP, VP, VP],
+        "tb_assemble_H": [P, I, VP, D, VP, VP, VP, VP, VP, VP],
+        "tb_krylov_density": [P, I, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP],
+        "tb_find_mu": [P, I, VP, VP, VP, D, VP, VP, VP, VP],
+        "tb_forces": [P, I, VP, D, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP],
+        "tb_md_step": [P, I, VP, VP, VP, D, D, D, VP, VP],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.tb_version.argtypes = []
+    lib.tb_version.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _check(fn, code):
+    if code != TB_OK:
+        raise TBError(fn, code)
+
+
+def _ptr(t, dtype, name):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_params(p, prec):
+    """tb_params from a dict of model constants plus kT, Rc, r, caps."""
+    tp = TBParams()
+    _check("tb_params_default", lib().tb_params_default(ctypes.byref(tp)))
+    for k in ("Es", "Ep", "Vss", "Vsp", "Vpps", "Vppp", "r0", "n", "nc", "rc", "phi0",
+              "d0", "m", "mc", "dc", "r1", "rm", "kT", "Rc"):
+        setattr(tp, k, float(p[k]))
+    tp.r = int(p["r"])
+    tp.max_hnbr = int(p.get("max_hnbr", 32))
+    tp.max_cluster = int(p.get("max_cluster", 128))
+    tp.prec = TB_PREC_FP64 if prec in ("fp64", TB_PREC_FP64) else TB_PREC_MIXED
+    tp.defl_tol = float(p.get("defl_tol", 1e-9 if tp.prec == TB_PREC_FP64 else 1e-4))
+    tp.reorth_passes = int(p.get("reorth_passes", 2))
+    tp.mu_tol = float(p.get("mu_tol", 1e-12))
+    tp.mu_max_iter = int(p.get("mu_max_iter", 100))
+    if "timeout_cycles" in p:
+        tp.timeout_cycles = int(p["timeout_cycles"])
+    return tp
+
+
+# ---------------------------------------------------------------- same-name calls
+
+def tb_ctx_create(params):
+    h = ctypes.c_void_p()
+    _check("tb_ctx_create", lib().tb_ctx_create(ctypes.byref(h), ctypes.byref(params)))
+    return h
+
+
+def tb_ctx_destroy(ctx):
+    _check("tb_ctx_destroy", lib().tb_ctx_destroy(ctx))
+
+
+def tb_ctx_reserve(ctx, n_atoms):
+    _check("tb_ctx_reserve", lib().tb_ctx_reserve(ctx, int(n_atoms)))
+
+
+def tb_ctx_workspace_bytes(ctx):
+    b = ctypes.c_size_t()
+    _check("tb_ctx_workspace_bytes", lib().tb_ctx_workspace_bytes(ctx, ctypes.byref(b)))
+    return b.value
+
+
+def tb_get_status(ctx, stream=None):
+    code, info = ctypes.c_int(), ctypes.c_int()
+    _check("tb_get_status", lib().tb_get_status(ctx, ctypes.byref(code), ctypes.byref(info),
+                                                 _stream(stream)))
+    return code.value, info.value
+
+
+def tb_build_neighbors(ctx, n, pos, L, h_off, h_idx, c_off, c_idx, stream=None):
+    i32, f64 = torch.int32, torch.float64
+    _check("tb_build_neighbors", lib().tb_build_neighbors(
+        ctx, n, _ptr(pos, f64, "pos"), float(L), _ptr(h_off, i32, "h_off"),
+        _ptr(h_idx, i32, "h_idx"), _ptr(c_off, i32, "c_off"), _ptr(c_idx, i32, "c_idx"),
+        _stream(stream)))
+
+
+def tb_assemble_H(ctx, n, pos, L, h_off, h_idx, Hblk, dHblk, Hmirror=None, stream=None):
+    i32, f64 = torch.int32, torch.float64
+    _check("tb_assemble_H", lib().tb_assemble_H(
+        ctx, n, _ptr(pos, f64, "pos"), float(L), _ptr(h_off, i32, "h_off"),
+        _ptr(h_idx, i32, "h_idx"), _ptr(Hblk, f64, "Hblk"), _ptr(dHblk, f64, "dHblk"),
+        _ptr(Hmirror, torch.float32, "Hmirror"), _stream(stream)))
+
+
+def tb_krylov_density(ctx, n, c_off, c_idx, h_off, h_idx, Hblk, Hmirror, lam, S, P, kdim,
+                      stream=None):
+    i32, f64 = torch.int32, torch.float64
+    _check("tb_krylov_density", lib().tb_krylov_density(
+        ctx, n, _ptr(c_off, i32, "c_off"), _ptr(c_idx, i32, "c_idx"),
+        _ptr(h_off, i32, "h_off"), _ptr(h_idx, i32, "h_idx"), _ptr(Hblk, f64, "Hblk"),
+        _ptr(Hmirror, torch.float32, "Hmirror"), _ptr(lam, f64, "lambda"),
+        _ptr(S, f64, "S"), _ptr(P, f64, "P"), _ptr(kdim, i32, "kdim"), _stream(stream)))
+
+
+def tb_find_mu(ctx, n, lam, S, kdim, n_electrons, mu_guess, mu, n_count=None, stream=None):
+    i32, f64 = torch.int32, torch.float64
+    _check("tb_find_mu", lib().tb_find_mu(
+        ctx, n, _ptr(lam, f64, "lambda"), _ptr(S, f64, "S"), _ptr(kdim, i32, "kdim"),
+        float(n_electrons), _ptr(mu_guess, f64, "mu_guess"), _ptr(mu, f64, "mu"),
+        _ptr(n_count, f64, "n_count"), _stream(stream)))
+
+
+def tb_forces(ctx, n, pos, L, h_off, h_idx, dHblk, lam, S, P, kdim, mu, F, energies,
+              stream=None):
+    i32, f64 = torch.int32, torch.float64
+    _check("tb_forces", lib().tb_forces(
+        ctx, n, _ptr(pos, f64, "pos"), float(L), _ptr(h_off, i32, "h_off"),
+        _ptr(h_idx, i32, "h_idx"), _ptr(dHblk, f64, "dHblk"), _ptr(lam, f64, "lambda"),
+        _ptr(S, f64, "S"), _ptr(P, f64, "P"), _ptr(kdim, i32, "kdim"), _ptr(mu, f64, "mu"),
+        _ptr(F, f64, "F"), _ptr(energies, f64, "energies"), _stream(stream)))
+
+
+def tb_md_step(ctx, n, pos, vel, F, L, dt_fs, mass_amu, energies, stream=None):
+    f64 = torch.float64
+    _check("tb_md_step", lib().tb_md_step(
+        ctx, n, _ptr(pos, f64, "pos"), _ptr(vel, f64, "vel"), _ptr(F, f64, "F"), float(L),
+        float(dt_fs), float(mass_amu), _ptr(energies, f64, "energies"), _stream(stream)))
+
+
+def tb_version():
+    return lib().tb_version().decode()

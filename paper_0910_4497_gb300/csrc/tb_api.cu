@@ -1,0 +1,287 @@
+// C ABI entry points: argument checks, context and workspace management, and
+// the stream-ordered launch sequence of each call.  Kernels live in the other
+// translation units.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include "tb_internal.cuh"
+
+size_t krylov_basis_bytes_global(const tb_ctx* c);
+
+namespace {
+
+bool finite_pos(double x) { return x == x && x < 1e300 && x > -1e300; }
+
+tb_status check_params(const tb_params& p) {
+  if (!(p.kT > 0.0) || !(p.Rc >= p.rm) || !(p.rm > p.r1) || !(p.r1 > 0.0)) return TB_ERR_INVALID_ARG;
+  if (!(p.r0 > 0.0) || !(p.rc > 0.0) || !(p.dc > 0.0) || !(p.d0 > 0.0)) return TB_ERR_INVALID_ARG;
+  if (p.r < 1 || p.r > tbk::MAX_R) return TB_ERR_INVALID_ARG;
+  if (p.prec != TB_PREC_FP64 && p.prec != TB_PREC_MIXED) return TB_ERR_INVALID_ARG;
+  if (p.max_hnbr < 1 || p.max_hnbr > tbk::MAX_HNBR) return TB_ERR_INVALID_ARG;
+  if (p.max_cluster < 1 || p.max_cluster > tbk::MAX_CLUSTER) return TB_ERR_INVALID_ARG;
+  if (p.reorth_passes < 0 || p.reorth_passes > 2) return TB_ERR_INVALID_ARG;
+  if (p.mu_max_iter < 1 || !(p.mu_tol > 0.0) || !(p.defl_tol >= 0.0)) return TB_ERR_INVALID_ARG;
+  if (p.timeout_cycles <= 0) return TB_ERR_INVALID_ARG;
+  if (!finite_pos(p.Es) || !finite_pos(p.Ep)) return TB_ERR_INVALID_ARG;
+  return TB_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Carver {
+  unsigned char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += align256(sizeof(T) * count);
+    return p;
+  }
+};
+
+// Lays out every workspace sub-buffer; with base == nullptr only sizes them.
+size_t carve(tb_ctx* c, int n, unsigned char* base) {
+  const tb_params& p = c->p;
+  const size_t NT = 4 * (size_t)p.r;
+  const size_t hcap = (size_t)n * p.max_hnbr;
+  const size_t rows = (size_t)n + hcap;   // row blocks of Y, P, rho
+  const size_t tv = p.prec == TB_PREC_FP64 ? sizeof(double) : sizeof(float);
+  Carver k{base};
+  c->scan_h = k.take<int>(n + 1);
+  c->scan_c = k.take<int>(n + 1);
+  c->T = k.take<double>((size_t)n * NT * NT);
+  c->Y = k.take<unsigned char>(rows * 4 * NT * tv);
+  c->colmask = k.take<unsigned long long>(n);
+  c->Zf = k.take<float>((size_t)n * NT * NT);
+  c->lamf = k.take<float>((size_t)n * NT);
+  c->Vg = k.take<unsigned char>(krylov_basis_bytes_global(c));
+  c->lcol = k.take<int>((size_t)c->kry_grid * p.max_cluster * p.max_hnbr);
+  c->lblk = k.take<int>((size_t)c->kry_grid * p.max_cluster * p.max_hnbr);
+  c->mu_part = k.take<double>(4 * (size_t)(c->mu_grid > 0 ? c->mu_grid : 1));
+  c->bar = k.take<unsigned>(4);
+  c->mu_state = k.take<double>(4);
+  c->rho = k.take<double>(rows * 16 > (size_t)n * 2 ? rows * 16 : (size_t)n * 2);
+  c->per_target = k.take<double>((size_t)n * 5);
+  c->h_off = k.take<int>(n + 1);
+  c->h_idx = k.take<int>(hcap);
+  c->c_off = k.take<int>(n + 1);
+  c->c_idx = k.take<int>((size_t)n * p.max_cluster);
+  c->Hblk = k.take<double>(hcap * 16);
+  c->dHblk = k.take<double>(hcap * 48);
+  c->Hmir = k.take<float>(hcap * 16);
+  c->lambda = k.take<double>((size_t)n * NT);
+  c->S = k.take<double>((size_t)n * 4 * NT);
+  c->P = k.take<double>(rows * 4 * NT);
+  c->kdim = k.take<int>(n);
+  c->mu = k.take<double>(1);
+  c->ncount = k.take<double>(1);
+  return k.off;
+}
+
+tb_status ready(tb_ctx* c, int n) {
+  if (!c) return TB_ERR_INVALID_ARG;
+  if (n < 0) return TB_ERR_INVALID_ARG;
+  if (n > c->reserved_n || !c->ws) return TB_ERR_NOT_RESERVED;
+  return TB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tb_status tb_params_default(tb_params* p) {
+  if (!p) return TB_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->kT = 0.1;
+  p->Rc = 5.0;
+  p->r1 = 2.45;
+  p->rm = 2.6;
+  p->defl_tol = 1e-9;
+  p->mu_tol = 1e-12;
+  p->r = 8;
+  p->prec = TB_PREC_FP64;
+  p->max_hnbr = 32;
+  p->max_cluster = 128;
+  p->reorth_passes = 2;
+  p->mu_max_iter = 100;
+  p->timeout_cycles = 4000000000LL;
+  return TB_OK;
+}
+
+tb_status tb_ctx_create(tb_ctx** out, const tb_params* p) {
+  if (!out || !p) return TB_ERR_INVALID_ARG;
+  *out = nullptr;
+  tb_status st = check_params(*p);
+  if (st != TB_OK) return st;
+  tb_ctx* c = new (std::nothrow) tb_ctx();
+  if (!c) return TB_ERR_NOMEM;
+  c->p = *p;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return TB_ERR_CUDA;
+  }
+  if ((st = krylov_configure(c)) != TB_OK || (st = eig_configure(c)) != TB_OK ||
+      (st = mu_configure(c)) != TB_OK) {
+    delete c;
+    return st;
+  }
+  if (cudaMalloc(&c->d_status, 2 * sizeof(int)) != cudaSuccess) {
+    delete c;
+    return TB_ERR_NOMEM;
+  }
+  if (cudaMemset(c->d_status, 0, 2 * sizeof(int)) != cudaSuccess) {
+    cudaFree(c->d_status);
+    delete c;
+    return TB_ERR_CUDA;
+  }
+  *out = c;
+  return TB_OK;
+}
+
+tb_status tb_ctx_destroy(tb_ctx* c) {
+  if (!c) return TB_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  if (c->ws) cudaFree(c->ws);
+  if (c->d_status) cudaFree(c->d_status);
+  delete c;
+  return TB_OK;
+}
+
+tb_status tb_ctx_reserve(tb_ctx* c, int n_atoms) {
+  if (!c || n_atoms < 0) return TB_ERR_INVALID_ARG;
+  if (n_atoms <= c->reserved_n && c->ws) return TB_OK;
+  const size_t bytes = carve(c, n_atoms, nullptr);
+  if (c->ws) {
+    cudaDeviceSynchronize();
+    cudaFree(c->ws);
+    c->ws = nullptr;
+    c->reserved_n = 0;
+    c->ws_bytes = 0;
+  }
+  unsigned char* ws = nullptr;
+  if (cudaMalloc(&ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return TB_ERR_NOMEM;
+  }
+  carve(c, n_atoms, ws);
+  c->ws = ws;
+  c->ws_bytes = bytes;
+  c->reserved_n = n_atoms;
+  TB_CUDA_TRY(cudaMemset(ws, 0, bytes));
+  TB_CUDA_TRY(cudaMemset(c->mu, 0xff, sizeof(double)));   // NaN: no previous mu
+  TB_CUDA_TRY(cudaDeviceSynchronize());
+  return TB_OK;
+}
+
+tb_status tb_ctx_workspace_bytes(const tb_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return TB_ERR_INVALID_ARG;
+  *bytes = c->ws_bytes;
+  return TB_OK;
+}
+
+tb_status tb_get_status(tb_ctx* c, int* code, int* info, void* stream) {
+  if (!c || !code) return TB_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int h[2] = {0, 0};
+  TB_CUDA_TRY(cudaMemcpyAsync(h, c->d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
+  TB_CUDA_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(h), s));
+  TB_CUDA_TRY(cudaStreamSynchronize(s));
+  *code = h[0];
+  if (info) *info = h[1];
+  return TB_OK;
+}
+
+tb_status tb_build_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h_off,
+                             int* h_idx, int* c_off, int* c_idx, void* stream) {
+  tb_status st = ready(c, n);
+  if (st != TB_OK) return st;
+  if (n == 0) return TB_OK;
+  if (!pos || !h_off || !h_idx || !c_off || !c_idx || !(L > 0.0) || !finite_pos(L))
+    return TB_ERR_INVALID_ARG;
+  return launch_neighbors(c, n, pos, L, h_off, h_idx, c_off, c_idx,
+                          static_cast<cudaStream_t>(stream));
+}
+
+tb_status tb_assemble_H(tb_ctx* c, int n, const double* pos, double L, const int* h_off,
+                        const int* h_idx, double* Hblk, double* dHblk, float* Hmirror,
+                        void* stream) {
+  tb_status st = ready(c, n);
+  if (st != TB_OK) return st;
+  if (n == 0) return TB_OK;
+  if (!pos || !h_off || !h_idx || !Hblk || !dHblk || !(L > 0.0)) return TB_ERR_INVALID_ARG;
+  if (c->p.prec == TB_PREC_MIXED && !Hmirror) return TB_ERR_INVALID_ARG;
+  return launch_assemble(c, n, pos, L, h_off, h_idx, Hblk, dHblk, Hmirror,
+                         static_cast<cudaStream_t>(stream));
+}
+
+tb_status tb_krylov_density(tb_ctx* c, int n, const int* c_off, const int* c_idx,
+                            const int* h_off, const int* h_idx, const double* Hblk,
+                            const float* Hmirror, double* lambda, double* S, double* P,
+                            int* kdim, void* stream) {
+  tb_status st = ready(c, n);
+  if (st != TB_OK) return st;
+  if (n == 0) return TB_OK;
+  if (!c_off || !c_idx || !h_off || !h_idx || !lambda || !S || !P || !kdim)
+    return TB_ERR_INVALID_ARG;
+  if (c->p.prec == TB_PREC_FP64 && !Hblk) return TB_ERR_INVALID_ARG;
+  if (c->p.prec == TB_PREC_MIXED && !Hmirror) return TB_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = launch_krylov(c, n, c_off, c_idx, h_off, h_idx, Hblk, Hmirror, s)) != TB_OK) return st;
+  return launch_eig(c, n, h_off, lambda, S, P, kdim, s);
+}
+
+tb_status tb_find_mu(tb_ctx* c, int n, const double* lambda, const double* S, const int* kdim,
+                     double n_electrons, const double* mu_guess, double* mu, double* n_count,
+                     void* stream) {
+  tb_status st = ready(c, n);
+  if (st != TB_OK) return st;
+  if (!lambda || !S || !kdim || !mu || n <= 0 || !(n_electrons > 0.0)) return TB_ERR_INVALID_ARG;
+  return launch_mu(c, n, lambda, S, n_electrons, mu_guess, mu, n_count,
+                   static_cast<cudaStream_t>(stream));
+}
+
+tb_status tb_forces(tb_ctx* c, int n, const double* pos, double L, const int* h_off,
+                    const int* h_idx, const double* dHblk, const double* lambda,
+                    const double* S, const double* P, const int* kdim, const double* mu,
+                    double* F, double* energies, void* stream) {
+  tb_status st = ready(c, n);
+  if (st != TB_OK) return st;
+  if (n == 0) return TB_OK;
+  if (!pos || !h_off || !h_idx || !dHblk || !lambda || !S || !P || !kdim || !mu || !F ||
+      !energies || !(L > 0.0))
+    return TB_ERR_INVALID_ARG;
+  return launch_forces(c, n, pos, L, h_off, h_idx, dHblk, lambda, S, P, kdim, mu, F,
+                       energies, static_cast<cudaStream_t>(stream));
+}
+
+tb_status tb_md_step(tb_ctx* c, int n, double* pos, double* vel, double* F, double L,
+                     double dt_fs, double mass_amu, double* energies, void* stream) {
+  tb_status st = ready(c, n);
+  if (st != TB_OK) return st;
+  if (n == 0) return TB_OK;
+  if (!pos || !vel || !F || !energies || !(L > 0.0) || !(mass_amu > 0.0) || !(dt_fs > 0.0))
+    return TB_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = launch_md_kick_drift(c, n, pos, vel, F, L, dt_fs, mass_amu, s)) != TB_OK) return st;
+  if ((st = launch_neighbors(c, n, pos, L, c->h_off, c->h_idx, c->c_off, c->c_idx, s)) != TB_OK)
+    return st;
+  if ((st = launch_assemble(c, n, pos, L, c->h_off, c->h_idx, c->Hblk, c->dHblk,
+                            c->p.prec == TB_PREC_MIXED ? c->Hmir : nullptr, s)) != TB_OK)
+    return st;
+  if ((st = launch_krylov(c, n, c->c_off, c->c_idx, c->h_off, c->h_idx, c->Hblk, c->Hmir, s)) !=
+      TB_OK)
+    return st;
+  if ((st = launch_eig(c, n, c->h_off, c->lambda, c->S, c->P, c->kdim, s)) != TB_OK) return st;
+  if ((st = launch_mu(c, n, c->lambda, c->S, 4.0 * n, c->mu, c->mu, c->ncount, s)) != TB_OK)
+    return st;
+  if ((st = launch_forces(c, n, pos, L, c->h_off, c->h_idx, c->dHblk, c->lambda, c->S, c->P,
+                          c->kdim, c->mu, F, energies, s)) != TB_OK)
+    return st;
+  return launch_md_kick(c, n, vel, F, dt_fs, mass_amu, energies, s);
+}
+
+const char* tb_version(void) { return "tb-gb300 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,458 @@
+// a8-a10, a12: chemical potential, density-matrix blocks, energies, forces
+// (Sec. 2: rho = sum_m |m> f(e_m) <m|, <F_i> = Tr[rho F_i]) and the
+// velocity-Verlet kernels.
+//
+// Occupation f(x) = 1/(1+e^x) per spin orbital, spin factor 2, x = (lam-mu)/kT.
+// The electron count uses the Ritz pairs of every target weighted by their
+// seed-block weight w = sum_a S_a^2 (Gauss quadrature of the local density of
+// states).  All sums are taken in a fixed order (per-thread, then fixed
+// shuffle trees, then a fixed sequence over blocks), so results are
+// deterministic from run to run.
+#include "tb_internal.cuh"
+#include "tb_model.cuh"
+
+namespace {
+
+constexpr int MT = 256;    // mu kernel threads
+constexpr int RT = 128;    // rho kernel threads
+
+__device__ __forceinline__ double fermi(double x) {
+  if (x > 50.0) return 0.0;
+  if (x < -50.0) return 1.0;
+  if (x > 0.0) {
+    const double e = exp(-x);
+    return e / (1.0 + e);
+  }
+  return 1.0 / (1.0 + exp(x));
+}
+
+__device__ __forceinline__ double entropy_term(double f) {
+  double t = 0.0;
+  if (f > 0.0) t += f * log(f);
+  if (f < 1.0) t += (1.0 - f) * log(1.0 - f);
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier on a monotone arrival counter.  Gives up after `timeout`
+// SM clocks, sets TB_ERR_TIMEOUT and returns false (the caller then leaves).
+__device__ bool grid_barrier(unsigned* bar, unsigned target, long long timeout, int* st,
+                             int* sflag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    const long long t0 = clock64();
+    int ok = 1;
+    while (ld_acquire(bar) < target) {
+      if (clock64() - t0 > timeout) {
+        ok = 0;
+        tbk::set_status(st, TB_ERR_TIMEOUT, (int)blockIdx.x);
+        break;
+      }
+      __nanosleep(100);
+    }
+    __threadfence();
+    *sflag = ok;
+  }
+  __syncthreads();
+  return *sflag != 0;
+}
+
+struct MuArgs {
+  long long npairs;
+  int NT;
+  const double* lambda;
+  const double* S;
+  double kT, ne, tolN;
+  const double* guess;
+  double* mu_out;
+  double* ncount_out;
+  double* part;        // 2 generations x gridDim x 2
+  unsigned* bar;
+  int max_iter;
+  long long timeout;
+  int* st;
+};
+
+__device__ __forceinline__ double pair_weight(const double* S, int NT, long long q) {
+  const long long i = q / NT;
+  const int k = (int)(q - i * NT);
+  const double* s = S + (size_t)i * 4 * NT + k;
+  return s[0] * s[0] + s[NT] * s[NT] + s[2 * NT] * s[2 * NT] + s[3 * NT] * s[3 * NT];
+}
+
+// Sum two per-block partials over all blocks in a fixed order (warp 0).
+__device__ void sum_partials(const double* part, int G, double* out2) {
+  if (threadIdx.x < 32) {
+    double a = 0.0, b = 0.0;
+    for (int g = threadIdx.x; g < G; g += 32) {
+      a += part[2 * g];
+      b += part[2 * g + 1];
+    }
+    a = tbk::warp_sum(a);
+    b = tbk::warp_sum(b);
+    if (threadIdx.x == 0) { out2[0] = a; out2[1] = b; }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
+  __shared__ double red[MT / 32 * 2];
+  __shared__ double tot[2];
+  __shared__ int sflag;
+  const int G = gridDim.x;
+  const long long gtid = (long long)blockIdx.x * MT + threadIdx.x;
+  const long long gstride = (long long)G * MT;
+  unsigned gen = 0;
+  // ---- bracket: [min lam - 40 kT, max lam + 40 kT] over pairs with weight
+  double lmin = 1e300, lmax = -1e300;
+  for (long long q = gtid; q < a.npairs; q += gstride) {
+    if (pair_weight(a.S, a.NT, q) > 0.0) {
+      const double l = a.lambda[q];
+      lmin = fmin(lmin, l);
+      lmax = fmax(lmax, l);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lmin = fmin(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+    lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) { red[2 * (threadIdx.x >> 5)] = lmin; red[2 * (threadIdx.x >> 5) + 1] = lmax; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m0 = 1e300, m1 = -1e300;
+    for (int w = 0; w < MT / 32; ++w) { m0 = fmin(m0, red[2 * w]); m1 = fmax(m1, red[2 * w + 1]); }
+    a.part[2 * blockIdx.x] = m0;
+    a.part[2 * blockIdx.x + 1] = -m1;
+  }
+  if (!grid_barrier(a.bar, (++gen) * G, a.timeout, a.st, &sflag)) return;
+  if (threadIdx.x < 32) {
+    double m0 = 1e300, m1 = 1e300;
+    for (int g = threadIdx.x; g < G; g += 32) { m0 = fmin(m0, a.part[2 * g]); m1 = fmin(m1, a.part[2 * g + 1]); }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      m0 = fmin(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+      m1 = fmin(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+    }
+    if (threadIdx.x == 0) { tot[0] = m0; tot[1] = -m1; }
+  }
+  __syncthreads();
+  double lo = tot[0] - 40.0 * a.kT, hi = tot[1] + 40.0 * a.kT;
+  double mu = 0.5 * (lo + hi);
+  if (a.guess) {
+    const double g = *a.guess;
+    if (isfinite(g) && g > lo && g < hi) mu = g;
+  }
+  double width_prev2 = hi - lo, width_prev1 = hi - lo;
+  double Nmu = 0.0;
+  bool conv = false;
+  for (int it = 0; it < a.max_iter; ++it) {
+    double n = 0.0, dn = 0.0;
+    for (long long q = gtid; q < a.npairs; q += gstride) {
+      const double w = pair_weight(a.S, a.NT, q);
+      if (w == 0.0) continue;
+      const double f = fermi((a.lambda[q] - mu) / a.kT);
+      n += w * f;
+      dn += w * f * (1.0 - f);
+    }
+    double v[2] = {n, dn};
+    tbk::block_sum<double, 2>(v, red, tot);
+    // generation 0 held the bracket partials; iterations alternate 1, 0, 1, ...
+    double* pg = a.part + (size_t)((it + 1) & 1) * 2 * G;
+    if (threadIdx.x == 0) { pg[2 * blockIdx.x] = tot[0]; pg[2 * blockIdx.x + 1] = tot[1]; }
+    if (!grid_barrier(a.bar, (++gen) * G, a.timeout, a.st, &sflag)) return;
+    sum_partials(pg, G, tot);
+    Nmu = 2.0 * tot[0];
+    const double dN = 2.0 * tot[1] / a.kT;
+    if (fabs(Nmu - a.ne) <= a.tolN || hi - lo < 1e-13) { conv = true; break; }
+    if (Nmu < a.ne) lo = mu; else hi = mu;
+    const double newton = mu - (Nmu - a.ne) / dN;
+    const bool slow = (hi - lo) > 0.5 * width_prev2;
+    width_prev2 = width_prev1;
+    width_prev1 = hi - lo;
+    mu = (dN > 0.0 && newton > lo && newton < hi && !slow) ? newton : 0.5 * (lo + hi);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *a.mu_out = mu;
+    if (a.ncount_out) *a.ncount_out = Nmu;
+    if (!conv) tbk::set_status(a.st, TB_ERR_NO_CONVERGENCE, -1);
+  }
+}
+
+// ---------------------------------------------------------------- rho blocks
+
+struct RhoArgs {
+  int NT;
+  const int* h_off;
+  const int* kdim;
+  const double* lambda;
+  const double* S;
+  const double* P;
+  const double* mu;
+  double kT;
+  double* rho;
+  double* per_target;   // n x 5
+  int* st;
+};
+
+__global__ void __launch_bounds__(RT) rho_kernel(const RhoArgs a) {
+  __shared__ double fk[tbk::MAX_NT];
+  __shared__ double sk[4 * tbk::MAX_NT];
+  __shared__ double red[RT / 32 * 3];
+  __shared__ double tot[3];
+  const int i = blockIdx.x, NT = a.NT;
+  const int m = a.kdim[i];
+  const double mu = *a.mu;
+  const double* lam = a.lambda + (size_t)i * NT;
+  const double* Si = a.S + (size_t)i * 4 * NT;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int k = threadIdx.x; k < NT; k += RT) {
+    double f = 0.0;
+    if (k < m) {
+      f = fermi((lam[k] - mu) / a.kT);
+      const double w = Si[k] * Si[k] + Si[NT + k] * Si[NT + k] + Si[2 * NT + k] * Si[2 * NT + k] +
+                       Si[3 * NT + k] * Si[3 * NT + k];
+      v[0] += w * f * lam[k];
+      v[1] += w * entropy_term(f);
+      v[2] += w * f;
+    }
+    fk[k] = f;
+    for (int al = 0; al < 4; ++al) sk[al * NT + k] = Si[al * NT + k];
+  }
+  tbk::block_sum<double, 3>(v, red, tot);
+  if (threadIdx.x == 0) {
+    a.per_target[5 * i + 0] = 2.0 * tot[0];
+    a.per_target[5 * i + 1] = 2.0 * a.kT * tot[1];
+    a.per_target[5 * i + 2] = 2.0 * tot[2];
+  }
+  const int deg = a.h_off[i + 1] - a.h_off[i];
+  const size_t base = (size_t)(i + a.h_off[i]);
+  const int nout = (deg + 1) * 16;
+  for (int q = threadIdx.x; q < nout; q += RT) {
+    const int blk = q >> 4, be = (q >> 2) & 3, al = q & 3;
+    const double* pr = a.P + ((base + blk) * 4 + be) * NT;
+    double t = 0.0;
+    for (int k = 0; k < m; ++k) t += pr[k] * fk[k] * sk[al * NT + k];
+    a.rho[(base + blk) * 16 + be * 4 + al] = t;
+  }
+}
+
+// ---------------------------------------------------------------- forces
+
+struct ForceArgs {
+  int n;
+  const double* pos;
+  double L;
+  const int* h_off;
+  const int* h_idx;
+  const double* dH;
+  const double* rho;
+  tb_gsp rep;
+  double* F;
+  double* per_target;
+  int* st;
+};
+
+__global__ void __launch_bounds__(256) force_kernel(const ForceArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (k >= a.n) return;
+  const int p0 = a.h_off[k], deg = a.h_off[k + 1] - p0;
+  double fx = 0.0, fy = 0.0, fz = 0.0, erep = 0.0;
+  if (lane < deg) {
+    const int p = p0 + lane;
+    const int j = a.h_idx[p];
+    // position of k in j's (ascending) list
+    int lo = a.h_off[j], hi = a.h_off[j + 1];
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (a.h_idx[mid] < k) lo = mid + 1; else hi = mid;
+    }
+    if (lo >= a.h_off[j + 1] || a.h_idx[lo] != k) {
+      tbk::set_status(a.st, TB_ERR_INVALID_ARG, k);
+    } else {
+      const int rq = lo - a.h_off[j];
+      const double* rk = a.rho + ((size_t)(k + p0) + 1 + lane) * 16;   // rho^(k)_{j b, k a} [b][a]
+      const double* rj = a.rho + ((size_t)(j + a.h_off[j]) + 1 + rq) * 16;  // rho^(j)_{k a, j b} [a][b]
+      const double* G = a.dH + (size_t)p * 48;
+      double acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int al = 0; al < 4; ++al)
+#pragma unroll
+        for (int be = 0; be < 4; ++be) {
+          const double rs = rk[be * 4 + al] + rj[al * 4 + be];
+#pragma unroll
+          for (int kk = 0; kk < 3; ++kk) acc[kk] += rs * G[kk * 16 + al * 4 + be];
+        }
+      double d[3];
+#pragma unroll
+      for (int kk = 0; kk < 3; ++kk) {
+        const double x = a.pos[3 * j + kk] - a.pos[3 * k + kk];
+        d[kk] = x - a.L * rint(x / a.L);
+      }
+      const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      double phi, dphi;
+      tb_gsp_eval(a.rep, r, phi, dphi);
+      fx = 2.0 * acc[0] + dphi * d[0] / r;
+      fy = 2.0 * acc[1] + dphi * d[1] / r;
+      fz = 2.0 * acc[2] + dphi * d[2] / r;
+      erep = 0.5 * phi;
+    }
+  }
+  fx = tbk::warp_sum(fx);
+  fy = tbk::warp_sum(fy);
+  fz = tbk::warp_sum(fz);
+  erep = tbk::warp_sum(erep);
+  if (lane == 0) {
+    a.F[3 * k] = fx;
+    a.F[3 * k + 1] = fy;
+    a.F[3 * k + 2] = fz;
+    a.per_target[5 * k + 3] = erep;
+    if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) tbk::set_status(a.st, TB_ERR_NONFINITE, k);
+  }
+}
+
+// energies[8] = {E_band, -TS, A, E_rep, E_tot, N(mu), mu, KE}; columns of
+// per_target: E_band, -TS, N_e, E_rep, KE.  `cols` selects what to refresh.
+__global__ void __launch_bounds__(1024)
+energy_reduce_kernel(int n, const double* per_target, const double* mu, double* energies,
+                     int with_ke) {
+  __shared__ double red[32 * 5];
+  __shared__ double tot[5];
+  double v[5] = {0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < n; i += 1024)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) v[c] += per_target[5 * i + c];
+  tbk::block_sum<double, 5>(v, red, tot);
+  if (threadIdx.x == 0) {
+    if (with_ke) {
+      energies[7] = tot[4];
+    } else {
+      energies[0] = tot[0];
+      energies[1] = tot[1];
+      energies[2] = tot[0] + tot[1];
+      energies[3] = tot[3];
+      energies[4] = tot[0] + tot[1] + tot[3];
+      energies[5] = tot[2];
+      energies[6] = *mu;
+      energies[7] = 0.0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Verlet
+
+constexpr double ACC_CONV = 9.648533e-3;   // (eV/A/amu) -> A/fs^2
+
+__global__ void kick_drift_kernel(int n, double* pos, double* vel, const double* F, double L,
+                                  double dt, double mass) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * n) return;
+  const double v = vel[t] + 0.5 * dt * ACC_CONV / mass * F[t];
+  vel[t] = v;
+  double x = fmod(pos[t] + dt * v, L);
+  if (x < 0.0) x += L;
+  if (x >= L) x = 0.0;
+  pos[t] = x;
+}
+
+__global__ void kick_kernel(int n, double* vel, const double* F, double dt, double mass,
+                            double* per_target) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double ke = 0.0;
+  for (int kk = 0; kk < 3; ++kk) {
+    const double v = vel[3 * i + kk] + 0.5 * dt * ACC_CONV / mass * F[3 * i + kk];
+    vel[3 * i + kk] = v;
+    ke += v * v;
+  }
+  per_target[5 * i + 4] = 0.5 * mass * ke / ACC_CONV;
+}
+
+}  // namespace
+
+tb_status mu_configure(tb_ctx* c) {
+  int occ = 0;
+  TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mu_kernel, MT, 0));
+  if (occ < 1) return TB_ERR_CUDA;
+  c->mu_grid = c->num_sms;   // one block per SM: co-resident, short final sums
+  return TB_OK;
+}
+
+tb_status launch_mu(tb_ctx* c, int n, const double* lambda, const double* S,
+                    double n_electrons, const double* mu_guess, double* mu,
+                    double* n_count, cudaStream_t s) {
+  const int NT = 4 * c->p.r;
+  MuArgs a;
+  a.npairs = (long long)n * NT;
+  a.NT = NT;
+  a.lambda = lambda;
+  a.S = S;
+  a.kT = c->p.kT;
+  a.ne = n_electrons;
+  a.tolN = c->p.mu_tol * n_electrons;
+  a.guess = mu_guess;
+  a.mu_out = mu;
+  a.ncount_out = n_count;
+  a.part = c->mu_part;
+  a.bar = c->bar;
+  a.max_iter = c->p.mu_max_iter;
+  a.timeout = c->p.timeout_cycles;
+  a.st = c->d_status;
+  long long want = (a.npairs + MT * 4 - 1) / (MT * 4);
+  int grid = (int)(want < c->mu_grid ? want : c->mu_grid);
+  if (grid < 1) grid = 1;
+  TB_CUDA_TRY(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), s));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(MT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  TB_CUDA_TRY(cudaLaunchKernelEx(&cfg, mu_kernel, a));
+  return TB_OK;
+}
+
+tb_status launch_forces(tb_ctx* c, int n, const double* pos, double L, const int* h_off,
+                        const int* h_idx, const double* dHblk, const double* lambda,
+                        const double* S, const double* P, const int* kdim, const double* mu,
+                        double* F, double* energies, cudaStream_t s) {
+  const int NT = 4 * c->p.r;
+  RhoArgs ra{NT, h_off, kdim, lambda, S, P, mu, c->p.kT, c->rho, c->per_target, c->d_status};
+  rho_kernel<<<n, RT, 0, s>>>(ra);
+  TB_CUDA_TRY(cudaGetLastError());
+  ForceArgs fa{n, pos, L, h_off, h_idx, dHblk, c->rho, tb_repulsion_gsp(c->p), F,
+               c->per_target, c->d_status};
+  force_kernel<<<(int)(((long long)n * 32 + 255) / 256), 256, 0, s>>>(fa);
+  TB_CUDA_TRY(cudaGetLastError());
+  energy_reduce_kernel<<<1, 1024, 0, s>>>(n, c->per_target, mu, energies, 0);
+  TB_CUDA_TRY(cudaGetLastError());
+  return TB_OK;
+}
+
+tb_status launch_md_kick_drift(tb_ctx* c, int n, double* pos, double* vel, const double* F,
+                               double L, double dt, double mass, cudaStream_t s) {
+  kick_drift_kernel<<<(3 * n + 255) / 256, 256, 0, s>>>(n, pos, vel, F, L, dt, mass);
+  TB_CUDA_TRY(cudaGetLastError());
+  return TB_OK;
+}
+
+tb_status launch_md_kick(tb_ctx* c, int n, double* vel, const double* F, double dt,
+                         double mass, double* energies, cudaStream_t s) {
+  kick_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, vel, F, dt, mass, c->per_target);
+  TB_CUDA_TRY(cudaGetLastError());
+  energy_reduce_kernel<<<1, 1024, 0, s>>>(n, c->per_target, c->mu, energies, 1);
+  TB_CUDA_TRY(cudaGetLastError());
+  return TB_OK;
+}

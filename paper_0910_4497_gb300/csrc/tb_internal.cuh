@@ -1,0 +1,125 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "tb.h"
+
+#define TB_CUDA_TRY(call)                                  \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return TB_ERR_CUDA;             \
+  } while (0)
+
+namespace tbk {
+
+constexpr int MAX_R = 16;           // Krylov block order cap -> NT <= 64
+constexpr int MAX_NT = 4 * MAX_R;
+constexpr int MAX_HNBR = 32;        // one warp lane per Hamiltonian neighbour
+constexpr int MAX_CLUSTER = 1024;
+
+// Device status word: [0] = first tb_status code, [1] = qualifying info.
+__device__ __forceinline__ void set_status(int* st, int code, int info) {
+  if (atomicCAS(st, 0, code) == 0) atomicExch(st + 1, info);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Fixed-order block reduction of M values per thread (M <= 16).  Every thread
+// passes its partials; on return out[0..M) (shared) holds the totals.  Uses
+// red[nwarps*M] shared scratch.  Contains two __syncthreads().
+template <typename T, int M>
+__device__ __forceinline__ void block_sum(T (&v)[M], T* red, T* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < M; ++q) v[q] = warp_sum(v[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < M; ++q) red[warp * M + q] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < M) {
+    T s = 0;
+    for (int w = 0; w < nw; ++w) s += red[w * M + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+}  // namespace tbk
+
+struct tb_ctx {
+  tb_params p;
+  int device = 0;
+  int num_sms = 0;
+  int* d_status = nullptr;           // 2 ints
+  // workspace
+  int reserved_n = 0;
+  size_t ws_bytes = 0;
+  unsigned char* ws = nullptr;
+  // sub-buffers inside ws
+  int* scan_h = nullptr;             // n+1 counts (H lists)
+  int* scan_c = nullptr;             // n+1 counts (clusters)
+  double* T = nullptr;               // n * NT * NT
+  void* Y = nullptr;                 // n*(1+max_hnbr)*4*NT  (TV precision)
+  unsigned long long* colmask = nullptr;  // n
+  float* Zf = nullptr;               // n * NT * NT
+  float* lamf = nullptr;             // n * NT
+  void* Vg = nullptr;                // kry_grid * Dmax * NT (TV) when the basis is global
+  int* lcol = nullptr;               // kry_grid * max_cluster * max_hnbr
+  int* lblk = nullptr;
+  double* mu_part = nullptr;         // mu_grid * 4
+  unsigned int* bar = nullptr;       // barrier counter
+  double* mu_state = nullptr;        // 4 doubles
+  double* rho = nullptr;             // n*(1+max_hnbr)*16
+  double* per_target = nullptr;      // n * 4
+  double* dscratch = nullptr;        // eig refinement scratch
+  // MD-owned buffers
+  int *h_off = nullptr, *h_idx = nullptr, *c_off = nullptr, *c_idx = nullptr;
+  double *Hblk = nullptr, *dHblk = nullptr;
+  float* Hmir = nullptr;
+  double *lambda = nullptr, *S = nullptr, *P = nullptr;
+  int* kdim = nullptr;
+  double *mu = nullptr, *ncount = nullptr;
+  // launch configuration
+  int kry_grid = 0;
+  size_t kry_smem = 0;
+  bool kry_vsmem = false;
+  int eig_grid = 0;
+  size_t eig_smem = 0;
+  size_t fin_smem = 0;
+  int mu_grid = 0;
+};
+
+// Launchers (defined in the kernel translation units).
+tb_status launch_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h_off,
+                           int* h_idx, int* c_off, int* c_idx, cudaStream_t s);
+tb_status launch_assemble(tb_ctx* c, int n, const double* pos, double L,
+                          const int* h_off, const int* h_idx, double* Hblk,
+                          double* dHblk, float* Hmir, cudaStream_t s);
+tb_status krylov_configure(tb_ctx* c);
+tb_status launch_krylov(tb_ctx* c, int n, const int* c_off, const int* c_idx,
+                        const int* h_off, const int* h_idx, const double* Hblk,
+                        const float* Hmir, cudaStream_t s);
+tb_status eig_configure(tb_ctx* c);
+tb_status launch_eig(tb_ctx* c, int n, const int* h_off, double* lambda, double* S,
+                     double* P, int* kdim, cudaStream_t s);
+tb_status mu_configure(tb_ctx* c);
+tb_status launch_mu(tb_ctx* c, int n, const double* lambda, const double* S,
+                    double n_electrons, const double* mu_guess, double* mu,
+                    double* n_count, cudaStream_t s);
+tb_status launch_forces(tb_ctx* c, int n, const double* pos, double L,
+                        const int* h_off, const int* h_idx, const double* dHblk,
+                        const double* lambda, const double* S, const double* P,
+                        const int* kdim, const double* mu, double* F,
+                        double* energies, cudaStream_t s);
+tb_status launch_md_kick_drift(tb_ctx* c, int n, double* pos, double* vel,
+                               const double* F, double L, double dt, double mass,
+                               cudaStream_t s);
+tb_status launch_md_kick(tb_ctx* c, int n, double* vel, const double* F,
+                         double dt, double mass, double* energies, cudaStream_t s);

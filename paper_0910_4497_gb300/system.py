@@ -1,0 +1,136 @@
+"""Device buffers for one periodic cell and the call sequence of one force
+evaluation through the C ABI (a1..a10), optionally captured as a CUDA graph.
+
+PyTorch is used only to own device memory and streams; every step of the
+evaluation runs in libtb.so.
+"""
+import torch
+
+from . import binding as B
+
+
+class TBSystem:
+    """One cell of n atoms in a cubic box of side L.
+
+    params: dict with the model constants (Es, Ep, Vss, Vsp, Vpps, Vppp, r0, n, nc,
+    rc, phi0, d0, m, mc, dc, r1, rm), kT, Rc, r, and optionally max_hnbr,
+    max_cluster, defl_tol, reorth_passes, mu_tol, mu_max_iter.
+    prec: "fp64" or "mixed".
+    """
+
+    def __init__(self, n, L, params, prec="fp64", device="cuda"):
+        self.n, self.L = int(n), float(L)
+        self.prec = prec
+        self.params = dict(params)
+        self.tp = B.make_params(self.params, prec)
+        self.NT = 4 * self.tp.r
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.ctx = B.tb_ctx_create(self.tp)
+            B.tb_ctx_reserve(self.ctx, self.n)
+        n, NT, mh, mc = self.n, self.NT, self.tp.max_hnbr, self.tp.max_cluster
+        kw = dict(device=self.device)
+        i32, f64, f32 = torch.int32, torch.float64, torch.float32
+        self.pos = torch.zeros((n, 3), dtype=f64, **kw)
+        self.h_off = torch.zeros(n + 1, dtype=i32, **kw)
+        self.h_idx = torch.zeros(n * mh, dtype=i32, **kw)
+        self.c_off = torch.zeros(n + 1, dtype=i32, **kw)
+        self.c_idx = torch.zeros(n * mc, dtype=i32, **kw)
+        self.Hblk = torch.zeros(n * mh * 16, dtype=f64, **kw)
+        self.dHblk = torch.zeros(n * mh * 48, dtype=f64, **kw)
+        self.Hmir = torch.zeros(n * mh * 16, dtype=f32, **kw) if self.tp.prec == B.TB_PREC_MIXED else None
+        self.lam = torch.zeros(n * NT, dtype=f64, **kw)
+        self.S = torch.zeros(n * 4 * NT, dtype=f64, **kw)
+        self.P = torch.zeros((n + n * mh) * 4 * NT, dtype=f64, **kw)
+        self.kdim = torch.zeros(n, dtype=i32, **kw)
+        self.mu = torch.full((1,), float("nan"), dtype=f64, **kw)
+        self.ncount = torch.zeros(1, dtype=f64, **kw)
+        self.F = torch.zeros((n, 3), dtype=f64, **kw)
+        self.vel = torch.zeros((n, 3), dtype=f64, **kw)
+        self.energies = torch.zeros(8, dtype=f64, **kw)
+        self.graph = None
+
+    # -- the five stages of one force evaluation
+    def neighbors(self, stream=None):
+        B.tb_build_neighbors(self.ctx, self.n, self.pos, self.L, self.h_off, self.h_idx,
+                             self.c_off, self.c_idx, stream)
+
+    def assemble(self, stream=None):
+        B.tb_assemble_H(self.ctx, self.n, self.pos, self.L, self.h_off, self.h_idx,
+                        self.Hblk, self.dHblk, self.Hmir, stream)
+
+    def krylov(self, stream=None):
+        B.tb_krylov_density(self.ctx, self.n, self.c_off, self.c_idx, self.h_off,
+                            self.h_idx, self.Hblk, self.Hmir, self.lam, self.S, self.P,
+                            self.kdim, stream)
+
+    def find_mu(self, stream=None, warm_start=True):
+        B.tb_find_mu(self.ctx, self.n, self.lam, self.S, self.kdim, 4.0 * self.n,
+                     self.mu if warm_start else None, self.mu, self.ncount, stream)
+
+    def forces(self, stream=None):
+        B.tb_forces(self.ctx, self.n, self.pos, self.L, self.h_off, self.h_idx, self.dHblk,
+                    self.lam, self.S, self.P, self.kdim, self.mu, self.F, self.energies,
+                    stream)
+
+    def evaluate(self, stream=None, warm_start=False):
+        """One full force evaluation (a1..a10) of the positions in self.pos."""
+        self.neighbors(stream)
+        self.assemble(stream)
+        self.krylov(stream)
+        self.find_mu(stream, warm_start=warm_start)
+        self.forces(stream)
+
+    def md_step(self, dt_fs, mass_amu, stream=None):
+        B.tb_md_step(self.ctx, self.n, self.pos, self.vel, self.F, self.L, dt_fs, mass_amu,
+                     self.energies, stream)
+
+    # -- CUDA graph of one evaluation
+    def capture(self):
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(s):
+            for _ in range(2):
+                self.evaluate(s)
+        torch.cuda.current_stream(self.device).wait_stream(s)
+        torch.cuda.synchronize(self.device)
+        self.check()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.evaluate()
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def set_positions(self, pos):
+        self.pos.copy_(torch.as_tensor(pos, dtype=torch.float64), non_blocking=True)
+
+    def check(self, stream=None):
+        code, info = B.tb_get_status(self.ctx, stream)
+        if code != B.TB_OK:
+            raise B.TBError("device status", code, info)
+
+    def status(self, stream=None):
+        return B.tb_get_status(self.ctx, stream)
+
+    # -- views for comparisons
+    def lists(self):
+        ho = self.h_off.cpu().numpy()
+        hi = self.h_idx.cpu().numpy()
+        co = self.c_off.cpu().numpy()
+        ci = self.c_idx.cpu().numpy()
+        return ([hi[ho[i]:ho[i + 1]] for i in range(self.n)],
+                [ci[co[i]:co[i + 1]] for i in range(self.n)])
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            B.tb_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -5,6 +5,7 @@ library next to this file.  No CMake, no torch extension machinery: the
 library exposes a plain C ABI (include/tb.h).
 """
 import os
+import platform
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -13,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(HERE, "_build")
+BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "libtb.so")
 SOURCES = ["tb_api.cu", "tb_neighbors.cu", "tb_hamiltonian.cu", "tb_krylov.cu",
            "tb_eig.cu", "tb_density.cu"]

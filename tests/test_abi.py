@@ -45,7 +45,7 @@ def test_library_exports_every_declared_symbol(built):
     assert set(declared_functions()) <= exported
 
 
-def test_build_flags_target_sm103a():
+def test_build_flags_target_sm103a(built):
     from paper_0910_4497_gb300 import build as b
     assert b.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark: atom force evaluations per second on the 1920-atom compressed
+fcc C60 cell (2x2x2 supercell at a = 13.0 A, cluster cutoff 6.0 A, Krylov block
+order r = 12), one full force evaluation (lists, Hamiltonian blocks, block
+Lanczos, projected eigensolve, mu, density blocks, forces) per step, replayed
+as one CUDA graph.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
+                  [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With --gpus N > 1 (torchrun, one rank per GPU)
+every rank evaluates its own replica of the cell; value = total atoms / max time.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("atom force evals/s (batched mixed vs plain FP64, 1 GB300) at "
+          "≤1e-3 eV/Å error")
+UNIT = "atom force evals/s"
+WORKLOAD = "c60_fcc_2x2x2_compressed_1920"
+CONFIG_INDEX = 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reorth-passes", type=int, default=2)
+    return ap.parse_args()
+
+
+def workload():
+    from synth import CONFIGS, fcc_c60_crystal, workload_params
+    cfg = CONFIGS[CONFIG_INDEX]
+    pos, L, _ = fcc_c60_crystal(cfg["ncell"], cfg["a"], cfg["jitter"], cfg["seed"],
+                                cfg["bridges"])
+    p = workload_params(cfg, defl_tol=1e-9)
+    return cfg, pos, L, p
+
+
+def config_dict(cfg, n, extra):
+    d = {"workload": WORKLOAD, "n_atoms": n, "a": cfg["a"], "ncell": cfg["ncell"],
+         "Rc": cfg["Rc"], "krylov_r": cfg["r"], "kT": cfg["kT"]}
+    d.update(extra)
+    return d
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def time_oracle_full(pos, L, p):
+    """One full oracle force evaluation, single process."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import oracle
+    t0 = time.perf_counter()
+    oracle.force_evaluation(pos, L, p)
+    return time.perf_counter() - t0
+
+
+def oracle_sample_step(ctxd, stride=10):
+    """Per-target oracle work (cluster H, block Lanczos, eigenpairs, density
+    blocks at a fixed mu) for every `stride`-th target."""
+    from oracle.pipeline import target_record
+    from oracle.density import rho_blocks
+    p = ctxd["p"]
+    t0 = time.perf_counter()
+    nt = 0
+    for i in range(0, len(ctxd["pos"]), stride):
+        lam, S, P = target_record(ctxd["bonds"], ctxd["cl"][i], ctxd["hl"][i], p["r"],
+                                  p["defl_tol"])
+        rho_blocks(S, P, lam, 4.5, p["kT"])
+        nt += 1
+    return nt, time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    cfg, pos, L, p = workload()
+    from oracle.neighbors import neighbor_lists, cluster_lists
+    from oracle.hamiltonian import BondTable
+    hl = neighbor_lists(pos, L, p["rm"])
+    cl = cluster_lists(pos, L, p["Rc"])
+    ctxd = dict(pos=pos, p=p, hl=hl, cl=cl, bonds=BondTable(pos, L, hl, p))
+    for _ in range(args.warmup):
+        oracle_sample_step(ctxd)
+    tot_t, tot_n = 0.0, 0
+    for _ in range(args.steps):
+        nt, dt = oracle_sample_step(ctxd)
+        tot_t += dt
+        tot_n += nt
+    value = tot_n / tot_t
+    sample = (f"per step: cluster H, block Lanczos, eigenpairs and density blocks of "
+              f"{tot_n // args.steps} of the {len(pos)} targets (every 10th); lists and "
+              f"bond table built once outside the timed region")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": config_dict(cfg, len(pos), {"l2": "n/a (CPU)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(index), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.3)
+        self.p.terminate()
+        self.p.wait(timeout=10)
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- our path
+
+def algorithmic_sweep_bytes(system, prec):
+    """Bytes per Krylov launch of the H.V sweeps: per target and sweep
+    nnzb*(16 b_H + 4) + 2*(4 n_c * 4 b_V), times r sweeps, summed over targets."""
+    import numpy as np
+    hl, cl = system.lists()
+    n = system.n
+    bH = 8 if prec == "fp64" else 4
+    r = system.tp.r
+    total = 0
+    hsets = [set(x.tolist()) for x in hl]
+    for i in range(n):
+        c = cl[i]
+        cs = set(c.tolist())
+        nnzb = len(c) + sum(len(hsets[a] & cs) for a in c)
+        total += r * (nnzb * (16 * bH + 4) + 2 * (4 * len(c) * 4 * bH))
+    return total
+
+
+def kernel_traffic(prec):
+    """DRAM bytes per Krylov launch from the committed ncu summary, or None if
+    the kernel source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "krylov_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    src = open(os.path.join(ROOT, "paper_0910_4497_gb300", "csrc", "tb_krylov.cu"), "rb").read()
+    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return rec.get("dram_bytes_per_launch", {}).get(prec)
+
+
+def run_ours(args):
+    import torch
+    import __graft_entry__
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        dist.barrier()
+        if rank != 0:
+            __graft_entry__.build()
+    else:
+        __graft_entry__.build()
+        torch.cuda.set_device(local)
+    import paper_0910_4497_gb300 as tb
+    from paper_0910_4497_gb300 import binding as B
+
+    cfg, pos, L, p = workload()
+    p["reorth_passes"] = args.reorth_passes
+    n = len(pos)
+    cpu_base = None
+    if rank == 0 and not args.no_cpu_baseline:
+        t_or = time_oracle_full(pos, L, p)       # before any GPU work of this process
+        cpu_base = {"value": n / t_or, "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": f"one full FP64 oracle force evaluation of the {n}-atom cell "
+                              f"({t_or:.1f} s, single process)"}
+    dev = torch.device("cuda", local)
+    system = tb.TBSystem(n, L, p, prec=args.prec, device=dev)
+    B.tb_profile_enable(system.ctx, True)
+    system.set_positions(pos)
+    system.capture()
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        system.replay()
+    torch.cuda.synchronize(dev)
+    system.check()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- device-resident timed region
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    stage_ms = {k: [] for k in B.STAGES}
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(float(k))                       # evict L2 between steps
+        ev[k][0].record(stream)
+        system.replay()
+        ev[k][1].record(stream)
+        ev[k][1].synchronize()
+        for name, v in B.tb_profile_read(system.ctx).items():
+            stage_ms[name].append(v)
+    barrier()
+    clk = clocks.stop() if clocks else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = t.item()
+    system.check()
+    value = world * n * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    pin_pos = torch.as_tensor(pos, dtype=torch.float64).pin_memory()
+    pin_F = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    pin_E = torch.empty(8, dtype=torch.float64).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e2e_ms = 0.0
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0.record(stream)
+        system.pos.copy_(pin_pos, non_blocking=True)
+        system.replay()
+        pin_F.copy_(system.F, non_blocking=True)
+        pin_E.copy_(system.energies, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = t.item()
+    e2e_value = world * n * args.steps / (e2e_ms / 1e3)
+
+    if rank == 0:
+        kry = [v for v in stage_ms["krylov"] if v > 0]
+        kry_ms = statistics.mean(kry) if kry else None
+        alg = algorithmic_sweep_bytes(system, args.prec)
+        peaks = {}
+        pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(pk):
+            peaks = json.load(open(pk))
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        achieved = alg / (kry_ms * 1e-3) / 1e9 if kry_ms else None
+        roof = {"bound": "hbm", "kernel": "krylov_kernel (block Lanczos H.V sweeps + "
+                "reorthogonalisation, one CTA per target)",
+                "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "frac": achieved / hbm if achieved else None,
+                "traffic": kernel_traffic(args.prec),
+                "algorithmic_bytes_per_launch": alg, "kernel_ms": kry_ms}
+        stages = {k: (statistics.mean([x for x in v if x >= 0]) if any(x >= 0 for x in v)
+                      else None) for k, v in stage_ms.items()}
+        launches_per_step = 12   # 4 list + 1 assembly + 3 Krylov/eig + 1 mu + 3 forces
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.prec == "mixed" else "f64", "data": "synthetic",
+            "config": config_dict(cfg, n, {
+                "precision": args.prec, "l2": "flushed between steps (256 MB write)",
+                "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                "graph": "one CUDA graph per force evaluation",
+                "reorth_passes": args.reorth_passes}),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 3 * 8,
+                    "d2h_bytes_per_step": n * 3 * 8 + 8 * 8},
+            "roofline": roof,
+            "cpu_baseline": cpu_base,
+            "clocks": clk,
+            "gpu_launches": launches_per_step * args.steps,
+            "stage_ms": stages,
+        }
+        print(json.dumps(line), flush=True)
+    system.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

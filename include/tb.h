@@ -209,6 +209,19 @@ tb_status tb_md_step(tb_ctx* ctx, int n, double* pos, double* vel, double* F,
                      double L, double dt_fs, double mass_amu, double* energies,
                      void* stream);
 
+/*
+ * Stage timing (tracing aid).  When enabled, every later call records a pair of
+ * CUDA events around each of its stages on its stream (as external event nodes
+ * when the stream is being captured into a graph, so graph replays record them
+ * too).  Stages: 0 lists, 1 assembly, 2 block Lanczos, 3 projected
+ * eigensolve + spectral record, 4 mu, 5 density blocks + forces + energies.
+ * tb_profile_enable creates the events (not capturable).
+ * tb_profile_read (host out ms[6]) returns the elapsed time of each stage's most
+ * recent execution, or -1 for a stage not yet run; the caller synchronises first.
+ */
+tb_status tb_profile_enable(tb_ctx* ctx, int enable);
+tb_status tb_profile_read(tb_ctx* ctx, float* ms);
+
 /* Library version string (static, host). */
 const char* tb_version(void);
 

@@ -23,7 +23,7 @@ TB_PREC_MIXED = 1
 EXPORTS = ["tb_params_default", "tb_ctx_create", "tb_ctx_destroy", "tb_ctx_reserve",
            "tb_ctx_workspace_bytes", "tb_get_status", "tb_build_neighbors",
            "tb_assemble_H", "tb_krylov_density", "tb_find_mu", "tb_forces", "tb_md_step",
-           "tb_version"]
+           "tb_profile_enable", "tb_profile_read", "tb_version"]
 
 
 class TBParams(ctypes.Structure):
@@ -64,6 +64,8 @@ def load_library(path=LIB_PATH):
         "tb_find_mu": [P, I, VP, VP, VP, D, VP, VP, VP, VP],
         "tb_forces": [P, I, VP, D, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP],
         "tb_md_step": [P, I, VP, VP, VP, D, D, D, VP, VP],
+        "tb_profile_enable": [P, I],
+        "tb_profile_read": [P, ctypes.POINTER(ctypes.c_float)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -206,6 +208,19 @@ def tb_md_step(ctx, n, pos, vel, F, L, dt_fs, mass_amu, energies, stream=None):
     _check("tb_md_step", lib().tb_md_step(
         ctx, n, _ptr(pos, f64, "pos"), _ptr(vel, f64, "vel"), _ptr(F, f64, "F"), float(L),
         float(dt_fs), float(mass_amu), _ptr(energies, f64, "energies"), _stream(stream)))
+
+
+STAGES = ("lists", "assemble", "krylov", "eig", "mu", "forces")
+
+
+def tb_profile_enable(ctx, enable=True):
+    _check("tb_profile_enable", lib().tb_profile_enable(ctx, 1 if enable else 0))
+
+
+def tb_profile_read(ctx):
+    ms = (ctypes.c_float * 6)()
+    _check("tb_profile_read", lib().tb_profile_read(ctx, ms))
+    return dict(zip(STAGES, list(ms)))
 
 
 def tb_version():

@@ -88,6 +88,30 @@ tb_status ready(tb_ctx* c, int n) {
 
 }  // namespace
 
+tb_status prof_mark(tb_ctx* c, int stage, bool end, cudaStream_t s) {
+  if (!c->profiling) return TB_OK;
+  cudaEvent_t ev = c->prof_ev[2 * stage + (end ? 1 : 0)];
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  TB_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+  if (cs == cudaStreamCaptureStatusActive) {
+    TB_CUDA_TRY(cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal));
+  } else {
+    TB_CUDA_TRY(cudaEventRecord(ev, s));
+  }
+  if (end) c->prof_ran[stage] = true;
+  return TB_OK;
+}
+
+#define TB_STAGE(c, stage, s, call)                                  \
+  do {                                                               \
+    tb_status st_ = prof_mark((c), (stage), false, (s));             \
+    if (st_ != TB_OK) return st_;                                    \
+    st_ = (call);                                                    \
+    if (st_ != TB_OK) return st_;                                    \
+    st_ = prof_mark((c), (stage), true, (s));                        \
+    if (st_ != TB_OK) return st_;                                    \
+  } while (0)
+
 extern "C" {
 
 tb_status tb_params_default(tb_params* p) {
@@ -145,6 +169,8 @@ tb_status tb_ctx_destroy(tb_ctx* c) {
   cudaDeviceSynchronize();
   if (c->ws) cudaFree(c->ws);
   if (c->d_status) cudaFree(c->d_status);
+  for (int q = 0; q < 12; ++q)
+    if (c->prof_ev[q]) cudaEventDestroy(c->prof_ev[q]);
   delete c;
   return TB_OK;
 }
@@ -200,8 +226,9 @@ tb_status tb_build_neighbors(tb_ctx* c, int n, const double* pos, double L, int*
   if (n == 0) return TB_OK;
   if (!pos || !h_off || !h_idx || !c_off || !c_idx || !(L > 0.0) || !finite_pos(L))
     return TB_ERR_INVALID_ARG;
-  return launch_neighbors(c, n, pos, L, h_off, h_idx, c_off, c_idx,
-                          static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TB_STAGE(c, 0, s, launch_neighbors(c, n, pos, L, h_off, h_idx, c_off, c_idx, s));
+  return TB_OK;
 }
 
 tb_status tb_assemble_H(tb_ctx* c, int n, const double* pos, double L, const int* h_off,
@@ -212,8 +239,9 @@ tb_status tb_assemble_H(tb_ctx* c, int n, const double* pos, double L, const int
   if (n == 0) return TB_OK;
   if (!pos || !h_off || !h_idx || !Hblk || !dHblk || !(L > 0.0)) return TB_ERR_INVALID_ARG;
   if (c->p.prec == TB_PREC_MIXED && !Hmirror) return TB_ERR_INVALID_ARG;
-  return launch_assemble(c, n, pos, L, h_off, h_idx, Hblk, dHblk, Hmirror,
-                         static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TB_STAGE(c, 1, s, launch_assemble(c, n, pos, L, h_off, h_idx, Hblk, dHblk, Hmirror, s));
+  return TB_OK;
 }
 
 tb_status tb_krylov_density(tb_ctx* c, int n, const int* c_off, const int* c_idx,
@@ -228,8 +256,9 @@ tb_status tb_krylov_density(tb_ctx* c, int n, const int* c_off, const int* c_idx
   if (c->p.prec == TB_PREC_FP64 && !Hblk) return TB_ERR_INVALID_ARG;
   if (c->p.prec == TB_PREC_MIXED && !Hmirror) return TB_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if ((st = launch_krylov(c, n, c_off, c_idx, h_off, h_idx, Hblk, Hmirror, s)) != TB_OK) return st;
-  return launch_eig(c, n, h_off, lambda, S, P, kdim, s);
+  TB_STAGE(c, 2, s, launch_krylov(c, n, c_off, c_idx, h_off, h_idx, Hblk, Hmirror, s));
+  TB_STAGE(c, 3, s, launch_eig(c, n, h_off, lambda, S, P, kdim, s));
+  return TB_OK;
 }
 
 tb_status tb_find_mu(tb_ctx* c, int n, const double* lambda, const double* S, const int* kdim,
@@ -238,8 +267,9 @@ tb_status tb_find_mu(tb_ctx* c, int n, const double* lambda, const double* S, co
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;
   if (!lambda || !S || !kdim || !mu || n <= 0 || !(n_electrons > 0.0)) return TB_ERR_INVALID_ARG;
-  return launch_mu(c, n, lambda, S, n_electrons, mu_guess, mu, n_count,
-                   static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TB_STAGE(c, 4, s, launch_mu(c, n, lambda, S, n_electrons, mu_guess, mu, n_count, s));
+  return TB_OK;
 }
 
 tb_status tb_forces(tb_ctx* c, int n, const double* pos, double L, const int* h_off,
@@ -252,8 +282,10 @@ tb_status tb_forces(tb_ctx* c, int n, const double* pos, double L, const int* h_
   if (!pos || !h_off || !h_idx || !dHblk || !lambda || !S || !P || !kdim || !mu || !F ||
       !energies || !(L > 0.0))
     return TB_ERR_INVALID_ARG;
-  return launch_forces(c, n, pos, L, h_off, h_idx, dHblk, lambda, S, P, kdim, mu, F,
-                       energies, static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TB_STAGE(c, 5, s, launch_forces(c, n, pos, L, h_off, h_idx, dHblk, lambda, S, P, kdim, mu,
+                                  F, energies, s));
+  return TB_OK;
 }
 
 tb_status tb_md_step(tb_ctx* c, int n, double* pos, double* vel, double* F, double L,
@@ -280,6 +312,31 @@ tb_status tb_md_step(tb_ctx* c, int n, double* pos, double* vel, double* F, doub
                           c->kdim, c->mu, F, energies, s)) != TB_OK)
     return st;
   return launch_md_kick(c, n, vel, F, dt_fs, mass_amu, energies, s);
+}
+
+tb_status tb_profile_enable(tb_ctx* c, int enable) {
+  if (!c) return TB_ERR_INVALID_ARG;
+  if (enable) {
+    for (int q = 0; q < 12; ++q)
+      if (!c->prof_ev[q]) TB_CUDA_TRY(cudaEventCreate(&c->prof_ev[q]));
+  }
+  c->profiling = enable != 0;
+  return TB_OK;
+}
+
+tb_status tb_profile_read(tb_ctx* c, float* ms) {
+  if (!c || !ms) return TB_ERR_INVALID_ARG;
+  for (int q = 0; q < 6; ++q) {
+    ms[q] = -1.f;
+    if (c->prof_ev[2 * q] && c->prof_ran[q]) {
+      float t = -1.f;
+      if (cudaEventElapsedTime(&t, c->prof_ev[2 * q], c->prof_ev[2 * q + 1]) == cudaSuccess)
+        ms[q] = t;
+      else
+        cudaGetLastError();
+    }
+  }
+  return TB_OK;
 }
 
 const char* tb_version(void) { return "tb-gb300 0.1.0 (sm_103a)"; }

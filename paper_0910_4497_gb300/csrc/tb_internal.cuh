@@ -94,7 +94,14 @@ struct tb_ctx {
   size_t eig_smem = 0;
   size_t fin_smem = 0;
   int mu_grid = 0;
+  // stage timing events (tb_profile_enable)
+  bool profiling = false;
+  bool prof_ran[6] = {false, false, false, false, false, false};
+  cudaEvent_t prof_ev[12] = {};
 };
+
+// Stage timing helpers: record an event pair around a stage when enabled.
+tb_status prof_mark(tb_ctx* c, int stage, bool end, cudaStream_t s);
 
 // Launchers (defined in the kernel translation units).
 tb_status launch_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h_off,

@@ -68,8 +68,8 @@ def time_oracle_full(pos, L, p):
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     import oracle
     t0 = time.perf_counter()
-    oracle.force_evaluation(pos, L, p)
-    return time.perf_counter() - t0
+    res = oracle.force_evaluation(pos, L, p)
+    return time.perf_counter() - t0, res
 
 
 def oracle_sample_step(ctxd, stride=10):
@@ -226,8 +226,9 @@ def run_ours(args):
     p["reorth_passes"] = args.reorth_passes
     n = len(pos)
     cpu_base = None
+    ref = None
     if rank == 0 and not args.no_cpu_baseline:
-        t_or = time_oracle_full(pos, L, p)       # before any GPU work of this process
+        t_or, ref = time_oracle_full(pos, L, p)  # before any GPU work of this process
         cpu_base = {"value": n / t_or, "unit": UNIT, "cores": 1, "kind": "oracle",
                     "sample": f"one full FP64 oracle force evaluation of the {n}-atom cell "
                               f"({t_or:.1f} s, single process)"}
@@ -272,6 +273,16 @@ def run_ours(args):
         total_ms = t.item()
     system.check()
     value = world * n * args.steps / (total_ms / 1e3)
+    accuracy = None
+    if ref is not None:
+        import numpy as np
+        F = system.F.cpu().numpy()
+        e = system.energies.cpu().numpy()
+        dF = np.abs(F - ref.F)
+        accuracy = {"vs": "FP64 CPU oracle, same input",
+                    "force_err_max_eV_per_A": float(dF.max()),
+                    "force_err_rms_eV_per_A": float(np.sqrt(np.mean(dF ** 2))),
+                    "band_energy_rel_err": float(abs(e[0] - ref.E_band) / abs(ref.E_band))}
 
     # ---- end to end through the public API with host buffers
     pin_pos = torch.as_tensor(pos, dtype=torch.float64).pin_memory()
@@ -333,6 +344,7 @@ def run_ours(args):
             "clocks": clk,
             "gpu_launches": launches_per_step * args.steps,
             "stage_ms": stages,
+            "accuracy": accuracy,
         }
         print(json.dumps(line), flush=True)
     system.close()

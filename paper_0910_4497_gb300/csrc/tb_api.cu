@@ -20,7 +20,7 @@ tb_status check_params(const tb_params& p) {
   if (p.prec != TB_PREC_FP64 && p.prec != TB_PREC_MIXED) return TB_ERR_INVALID_ARG;
   if (p.max_hnbr < 1 || p.max_hnbr > tbk::MAX_HNBR) return TB_ERR_INVALID_ARG;
   if (p.max_cluster < 1 || p.max_cluster > tbk::MAX_CLUSTER) return TB_ERR_INVALID_ARG;
-  if (p.reorth_passes < 0 || p.reorth_passes > 2) return TB_ERR_INVALID_ARG;
+  if (p.reorth_passes < 1 || p.reorth_passes > 2) return TB_ERR_INVALID_ARG;
   if (p.mu_max_iter < 1 || !(p.mu_tol > 0.0) || !(p.defl_tol >= 0.0)) return TB_ERR_INVALID_ARG;
   if (p.timeout_cycles <= 0) return TB_ERR_INVALID_ARG;
   if (!finite_pos(p.Es) || !finite_pos(p.Ep)) return TB_ERR_INVALID_ARG;
@@ -56,8 +56,7 @@ size_t carve(tb_ctx* c, int n, unsigned char* base) {
   c->Zf = k.take<float>((size_t)n * NT * NT);
   c->lamf = k.take<float>((size_t)n * NT);
   c->Vg = k.take<unsigned char>(krylov_basis_bytes_global(c));
-  c->lcol = k.take<int>((size_t)c->kry_grid * p.max_cluster * p.max_hnbr);
-  c->lblk = k.take<int>((size_t)c->kry_grid * p.max_cluster * p.max_hnbr);
+  c->lent = k.take<int2>((size_t)c->kry_grid * p.max_cluster * p.max_hnbr);
   c->mu_part = k.take<double>(4 * (size_t)(c->mu_grid > 0 ? c->mu_grid : 1));
   c->bar = k.take<unsigned>(4);
   c->mu_state = k.take<double>(4);

@@ -73,6 +73,7 @@ struct MuArgs {
   const double* guess;
   double* mu_out;
   double* ncount_out;
+  int* iters_out;
   double* part;        // 2 generations x gridDim x 2
   unsigned* bar;
   int max_iter;
@@ -150,9 +151,10 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
     const double g = *a.guess;
     if (isfinite(g) && g > lo && g < hi) mu = g;
   }
-  double width_prev2 = hi - lo, width_prev1 = hi - lo;
+  double dxold = hi - lo, dx = dxold;
   double Nmu = 0.0;
   bool conv = false;
+  int iters = 0;
   for (int it = 0; it < a.max_iter; ++it) {
     double n = 0.0, dn = 0.0;
     for (long long q = gtid; q < a.npairs; q += gstride) {
@@ -173,15 +175,25 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
     const double dN = 2.0 * tot[1] / a.kT;
     if (fabs(Nmu - a.ne) <= a.tolN || hi - lo < 1e-13) { conv = true; break; }
     if (Nmu < a.ne) lo = mu; else hi = mu;
-    const double newton = mu - (Nmu - a.ne) / dN;
-    const bool slow = (hi - lo) > 0.5 * width_prev2;
-    width_prev2 = width_prev1;
-    width_prev1 = hi - lo;
-    mu = (dN > 0.0 && newton > lo && newton < hi && !slow) ? newton : 0.5 * (lo + hi);
+    // safeguarded Newton: bisect when the Newton point leaves the bracket or
+    // the step is not at least halving (Numerical Recipes' rtsafe rule)
+    const double fv = Nmu - a.ne;
+    const double newton = mu - fv / dN;
+    if (!(dN > 0.0) || !(newton > lo && newton < hi) || fabs(2.0 * fv) > fabs(dxold * dN)) {
+      dxold = dx;
+      dx = 0.5 * (hi - lo);
+      mu = lo + dx;
+    } else {
+      dxold = dx;
+      dx = fv / dN;
+      mu = newton;
+    }
+    iters = it + 1;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *a.mu_out = mu;
     if (a.ncount_out) *a.ncount_out = Nmu;
+    if (a.iters_out) *a.iters_out = iters;
     if (!conv) tbk::set_status(a.st, TB_ERR_NO_CONVERGENCE, -1);
   }
 }
@@ -401,6 +413,7 @@ tb_status launch_mu(tb_ctx* c, int n, const double* lambda, const double* S,
   a.guess = mu_guess;
   a.mu_out = mu;
   a.ncount_out = n_count;
+  a.iters_out = reinterpret_cast<int*>(c->mu_state);
   a.part = c->mu_part;
   a.bar = c->bar;
   a.max_iter = c->p.mu_max_iter;

@@ -12,20 +12,19 @@
 //      recurrence (identical values), lane 0 stores it, and each lane applies
 //      the rotations to its own rows of the eigenvector matrix.
 //   2. eig_finish_kernel (one CTA per target):
-//      - TB_PREC_MIXED: FP64 Rayleigh quotients lambda_k = x_k^T T x_k /
-//        x_k^T x_k on the FP32 eigenvectors (eigenvalue error second order in
-//        the eigenvector error);
-//      - TB_PREC_FP64: two FP64 iterations of the Ogita-Aishima refinement
+//      - TB_PREC_MIXED: T itself comes from FP32 sweeps, so the FP32
+//        eigenpairs are kept (an FP64 refinement could not add accuracy);
+//      - TB_PREC_FP64: two FP64 steps of the Ogita-Aishima refinement
 //        (Japan J. Indust. Appl. Math. 35 (2018)): R = I - X^T X,
 //        S = X^T T X, lambda_i = S_ii/(1 - R_ii), E_ij = (S_ij + lambda_j R_ij)
 //        /(lambda_j - lambda_i) if the gap exceeds delta else R_ij/2,
-//        X <- X + X E.
+//        X <- X + X E, then FP64 Rayleigh quotients;
 //      then the eigenpairs are sorted ascending and S, P are formed.
 #include "tb_internal.cuh"
 
 namespace {
 
-constexpr int EW = 2;              // warps (targets) per CTA in the QL kernel
+constexpr int EW = 4;              // warps (targets) per CTA in the QL kernel
 constexpr int FT = 128;            // threads per CTA in the finishing kernel
 
 struct EigArgs {
@@ -41,8 +40,9 @@ struct EigArgs {
 __host__ __device__ inline int pitch_of(int NT) { return NT + 1; }
 
 __host__ __device__ inline size_t ql_smem_per_warp(int NT) {
-  // A and Z (NT x (NT+1) floats), v, q, d, e (NT floats), act (NT ints)
-  return sizeof(float) * (2 * (size_t)NT * pitch_of(NT) + 4 * NT) + sizeof(int) * NT;
+  // Z (NT x (NT+1) floats: the matrix, then the Householder vectors, then the
+  // eigenvectors), v, q, d, e (NT floats), act (NT ints)
+  return sizeof(float) * ((size_t)NT * pitch_of(NT) + 4 * NT) + sizeof(int) * NT;
 }
 
 __global__ void __launch_bounds__(EW * 32) eig_ql_kernel(const EigArgs a) {
@@ -50,8 +50,7 @@ __global__ void __launch_bounds__(EW * 32) eig_ql_kernel(const EigArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int NT = a.NT, PT = pitch_of(NT);
   unsigned char* base = smem + warp * ql_smem_per_warp(NT);
-  float* A = reinterpret_cast<float*>(base);
-  float* Z = A + NT * PT;
+  float* Z = reinterpret_cast<float*>(base);
   float* vv = Z + NT * PT;
   float* qq = vv + NT;
   float* d = qq + NT;
@@ -67,34 +66,36 @@ __global__ void __launch_bounds__(EW * 32) eig_ql_kernel(const EigArgs a) {
   __syncwarp();
   const double* Ti = a.T + (size_t)i * NT * NT;
   for (int x = 0; x < m; ++x)
-    for (int y = lane; y < m; y += 32) {
-      A[x * PT + y] = (float)Ti[act[x] * NT + act[y]];
-      Z[x * PT + y] = (x == y) ? 1.f : 0.f;
-    }
+    for (int y = lane; y < m; y += 32) Z[x * PT + y] = (float)Ti[act[x] * NT + act[y]];
   __syncwarp();
 
-  // ---- Householder tridiagonalisation, reflections accumulated into Z
+  // ---- Householder reduction to tridiagonal form.  Step j zeroes column j
+  // below the subdiagonal with H_j = I - 2 v v^T (v supported on rows > j) and
+  // stores v in that column; each lane owns rows x = lane, lane + 32.
   for (int j = 0; j + 2 < m; ++j) {
     float xs = 0.f;
     for (int x = lane; x < m; x += 32)
-      if (x > j) xs += A[x * PT + j] * A[x * PT + j];
+      if (x > j) xs += Z[x * PT + j] * Z[x * PT + j];
     const float sig = tbk::warp_sum(xs);
-    const float x0 = A[(j + 1) * PT + j];
+    const float x0 = Z[(j + 1) * PT + j];
+    __syncwarp();
     if (sig - x0 * x0 <= 1e-30f * (sig + 1e-30f) || sig == 0.f) {
       if (lane == 0) e[j] = x0;
+      for (int x = lane; x < m; x += 32)
+        if (x > j) Z[x * PT + j] = 0.f;      // identity reflection
       __syncwarp();
       continue;
     }
     const float alpha = x0 >= 0.f ? -sqrtf(sig) : sqrtf(sig);
     const float inv = rsqrtf(2.f * (sig - x0 * alpha));
     for (int x = lane; x < m; x += 32)
-      vv[x] = x <= j ? 0.f : (x == j + 1 ? (x0 - alpha) : A[x * PT + j]) * inv;
+      vv[x] = x <= j ? 0.f : (x == j + 1 ? (x0 - alpha) : Z[x * PT + j]) * inv;
     __syncwarp();
     float kp = 0.f;
     for (int x = lane; x < m; x += 32) {
       float p = 0.f;
       if (x > j)
-        for (int l = j + 1; l < m; ++l) p += A[x * PT + l] * vv[l];
+        for (int l = j + 1; l < m; ++l) p += Z[x * PT + l] * vv[l];
       qq[x] = p;
       kp += p * vv[x];
     }
@@ -104,23 +105,53 @@ __global__ void __launch_bounds__(EW * 32) eig_ql_kernel(const EigArgs a) {
     for (int x = lane; x < m; x += 32) {
       if (x > j) {
         const float vx = vv[x], qx = qq[x];
-        for (int l = j + 1; l < m; ++l) A[x * PT + l] -= 2.f * (vx * qq[l] + qx * vv[l]);
+        for (int l = j + 1; l < m; ++l) Z[x * PT + l] -= 2.f * (vx * qq[l] + qx * vv[l]);
+        Z[x * PT + j] = vx;                  // keep v_j in column j
       }
-      float t = 0.f;
-      for (int l = j + 1; l < m; ++l) t += Z[x * PT + l] * vv[l];
-      for (int l = j + 1; l < m; ++l) Z[x * PT + l] -= 2.f * t * vv[l];
     }
     if (lane == 0) e[j] = alpha;
     __syncwarp();
   }
-  for (int x = lane; x < m; x += 32) d[x] = A[x * PT + x];
+  for (int x = lane; x < m; x += 32) d[x] = Z[x * PT + x];
   if (lane == 0) {
-    if (m >= 2) e[m - 2] = A[(m - 1) * PT + (m - 2)];
+    if (m >= 2) e[m - 2] = Z[(m - 1) * PT + (m - 2)];
     if (m >= 1) e[m - 1] = 0.f;
   }
   __syncwarp();
+  // ---- accumulate Q = H_0 H_1 ... H_{m-3} in place, last reflection first;
+  // lanes own columns l = lane, lane + 32.
+  // Invariant: before applying H_j, the block of rows and columns > j holds
+  // H_{j+1} ... H_{m-3} restricted to those indices; entries left of that block
+  // still hold the reflection vectors.  Start from the trailing identity.
+  if (lane == 0) {
+    const int t0 = m >= 2 ? m - 2 : 0;
+    for (int x = t0; x < m; ++x)
+      for (int y = t0; y < m; ++y) Z[x * PT + y] = (x == y) ? 1.f : 0.f;
+  }
+  __syncwarp();
+  for (int j = m - 3; j >= 0; --j) {
+    for (int x = lane; x < m; x += 32) vv[x] = x > j ? Z[x * PT + j] : 0.f;
+    __syncwarp();
+    for (int l = lane; l < m; l += 32) {
+      if (l > j) {
+        float sl = 0.f;
+        for (int y = j + 1; y < m; ++y) sl += vv[y] * Z[y * PT + l];
+        sl *= 2.f;
+        for (int y = j + 1; y < m; ++y) Z[y * PT + l] -= sl * vv[y];
+      }
+    }
+    __syncwarp();
+    for (int x = lane; x < m; x += 32) {
+      if (x >= j) {
+        Z[x * PT + j] = (x == j) ? 1.f : 0.f;
+        Z[j * PT + x] = (x == j) ? 1.f : 0.f;
+      }
+    }
+    __syncwarp();
+  }
 
-  // ---- implicit QL with shifts on (d, e), rotations applied to the rows of Z
+  // ---- implicit QL with shifts on (d, e); rotations applied to the rows of Z.
+  // Rotation (c, s) from f, g via one reciprocal square root.
   float tn = 0.f;
   for (int x = lane; x < m; x += 32) tn = fmaxf(tn, fabsf(d[x]) + fabsf(e[x]));
 #pragma unroll
@@ -143,16 +174,17 @@ __global__ void __launch_bounds__(EW * 32) eig_ql_kernel(const EigArgs a) {
       for (int ii = mm - 1; ii >= l; --ii) {
         const float ei = e[ii], di = d[ii], di1 = d[ii + 1];
         const float f = s * ei, b = c * ei;
-        rr = sqrtf(f * f + g * g);
+        const float h = f * f + g * g;
         __syncwarp();
-        if (lane == 0) e[ii + 1] = rr;
-        if (rr == 0.f) {
-          if (lane == 0) { d[ii + 1] = di1 - p; e[mm] = 0.f; }
+        if (h == 0.f) {
+          if (lane == 0) { e[ii + 1] = 0.f; d[ii + 1] = di1 - p; e[mm] = 0.f; }
           early = true;
           break;
         }
-        s = f / rr;
-        c = g / rr;
+        const float rinv = rsqrtf(h);
+        if (lane == 0) e[ii + 1] = h * rinv;
+        s = f * rinv;
+        c = g * rinv;
         g = di1 - p;
         rr = (di - g) * s + 2.f * c * b;
         p = s * rr;
@@ -201,9 +233,8 @@ struct FinArgs {
 template <typename TV>
 __host__ __device__ inline size_t fin_smem_bytes(int NT) {
   const size_t PT = NT + 1;
-  size_t b = sizeof(int) * 2 * NT + sizeof(double) * 4 * NT;   // act, blk; lam, rank, misc
+  size_t b = sizeof(int) * 4 * NT + sizeof(double) * 4 * NT;   // act, rank, lo, hi; lam, red
   if (sizeof(TV) == sizeof(float)) {
-    b += sizeof(double) * NT * PT;          // T active
     b += sizeof(float) * NT * PT;           // X
   } else {
     b += sizeof(double) * NT * PT * 5;      // T, X, W1, Smat, Rmat
@@ -219,120 +250,126 @@ __global__ void __launch_bounds__(FT) eig_finish_kernel(const FinArgs<TV> a) {
   const int i = blockIdx.x;
   int* act = reinterpret_cast<int*>(smem);
   int* rank = act + NT;
-  double* lam = reinterpret_cast<double*>(rank + NT);
-  double* red = lam + NT;          // 3*NT doubles of scratch
-  double* Tm = red + 3 * NT;
+  int* blo = rank + NT;             // band of row x in compacted indices: [blo, bhi)
+  int* bhi = blo + NT;
+  double* lam = reinterpret_cast<double*>(bhi + NT);
+  double* red = lam + NT;           // 3*NT doubles of scratch
+  TV* X = reinterpret_cast<TV*>(red + 3 * NT);
   const unsigned long long mask = a.colmask[i];
   const int m = __popcll(mask);
   for (int x = tid; x < NT; x += FT)
     if ((mask >> x) & 1ull) act[__popcll(mask & ((1ull << x) - 1ull))] = x;
   __syncthreads();
-  const double* Ti = a.T + (size_t)i * NT * NT;
-  for (int q = tid; q < m * m; q += FT) {
-    const int x = q / m, y = q - x * m;
-    Tm[x * PT + y] = Ti[act[x] * NT + act[y]];
+  // active columns couple in T only when their Krylov blocks are adjacent
+  for (int x = tid; x < m; x += FT) {
+    const int bx = act[x] >> 2;
+    int lo = x, hi = x + 1;
+    while (lo > 0 && (act[lo - 1] >> 2) >= bx - 1) --lo;
+    while (hi < m && (act[hi] >> 2) <= bx + 1) ++hi;
+    blo[x] = lo;
+    bhi[x] = hi;
   }
   const float* Zi = a.Zf + (size_t)i * NT * NT;
-  TV* X = reinterpret_cast<TV*>(Tm + NT * PT);
   for (int q = tid; q < m * m; q += FT) {
     const int x = q / m, y = q - x * m;
     X[x * PT + y] = (TV)Zi[x * NT + y];
   }
   __syncthreads();
-  // active columns x, y couple only if their Krylov blocks are adjacent
-  auto near = [&](int x, int y) { int bx = act[x] >> 2, by = act[y] >> 2; return bx - by <= 1 && by - bx <= 1; };
 
   if (sizeof(TV) == sizeof(float)) {
-    for (int k = tid; k < m; k += FT) {
-      double num = 0.0, den = 0.0;
-      for (int x = 0; x < m; ++x) {
-        const double xk = (double)X[x * PT + k];
-        double t = 0.0;
-        for (int y = 0; y < m; ++y)
-          if (near(x, y)) t += Tm[x * PT + y] * (double)X[y * PT + k];
-        num += xk * t;
-        den += xk * xk;
-      }
-      lam[k] = num / den;
-    }
+    // T comes from FP32 sweeps and is FP32-accurate: the FP32 QL eigenvalues
+    // already carry the full accuracy available.
+    for (int k = tid; k < m; k += FT) lam[k] = (double)a.lamf[(size_t)i * NT + k];
     __syncthreads();
   } else {
+    const double* Ti = a.T + (size_t)i * NT * NT;
     double* Xd = reinterpret_cast<double*>(X);
-    double* W1 = Xd + NT * PT;
+    double* Tm = Xd + NT * PT;
+    double* W1 = Tm + NT * PT;
     double* Sm = W1 + NT * PT;
     double* Rm = Sm + NT * PT;
-    // ||T||_F
-    if (tid == 0) {
-      double t2 = 0.0;
-      for (int q = 0; q < m * m; ++q) { const double v = Tm[(q / m) * PT + q % m]; t2 += v * v; }
-      red[0] = sqrt(t2);
+    for (int q = tid; q < m * m; q += FT) {
+      const int x = q / m, y = q - x * m;
+      Tm[x * PT + y] = Ti[act[x] * NT + act[y]];
     }
     __syncthreads();
-    const double tnorm = red[0];
+    {
+      double t2 = 0.0;
+      for (int q = tid; q < m * m; q += FT) {
+        const double v = Tm[(q / m) * PT + q % m];
+        t2 += v * v;
+      }
+      double v1[1] = {t2};
+      tbk::block_sum<double, 1>(v1, red, red + 2 * NT);
+    }
+    const double tnorm = sqrt(red[2 * NT]);
+    // two Ogita-Aishima refinement steps (quadratic convergence from FP32; the
+    // second resolves near-degenerate pairs the first one leaves mixed)
     for (int it = 0; it < 2; ++it) {
-      for (int q = tid; q < m * m; q += FT) {           // W1 = T X (banded T)
-        const int x = q / m, k = q - x * m;
-        double t = 0.0;
-        for (int y = 0; y < m; ++y) if (near(x, y)) t += Tm[x * PT + y] * Xd[y * PT + k];
-        W1[x * PT + k] = t;
+    for (int q = tid; q < m * m; q += FT) {           // W1 = T X (banded T)
+      const int x = q / m, k = q - x * m;
+      double t = 0.0;
+      for (int y = blo[x]; y < bhi[x]; ++y) t += Tm[x * PT + y] * Xd[y * PT + k];
+      W1[x * PT + k] = t;
+    }
+    __syncthreads();
+    for (int q = tid; q < m * m; q += FT) {           // S = X^T W1, R = I - X^T X
+      const int x = q / m, y = q - x * m;
+      double sv = 0.0, rr = 0.0;
+      for (int l = 0; l < m; ++l) {
+        sv += Xd[l * PT + x] * W1[l * PT + y];
+        rr += Xd[l * PT + x] * Xd[l * PT + y];
       }
-      __syncthreads();
-      for (int q = tid; q < m * m; q += FT) {           // S = X^T W1, R = I - X^T X
-        const int x = q / m, y = q - x * m;
-        double s = 0.0, rr = 0.0;
-        for (int l = 0; l < m; ++l) {
-          s += Xd[l * PT + x] * W1[l * PT + y];
-          rr += Xd[l * PT + x] * Xd[l * PT + y];
-        }
-        Sm[x * PT + y] = s;
-        Rm[x * PT + y] = (x == y ? 1.0 : 0.0) - rr;
-      }
-      __syncthreads();
-      for (int k = tid; k < m; k += FT) lam[k] = Sm[k * PT + k] / (1.0 - Rm[k * PT + k]);
-      __syncthreads();
-      if (tid == 0) {
-        double so = 0.0, ro = 0.0;
-        for (int q = 0; q < m * m; ++q) {
-          const int x = q / m, y = q - x * m;
-          const double sv = Sm[x * PT + y] - (x == y ? lam[x] : 0.0);
-          so += sv * sv;
-          ro += Rm[x * PT + y] * Rm[x * PT + y];
-        }
-        red[1] = 2.0 * (sqrt(so) + tnorm * sqrt(ro));
-      }
-      __syncthreads();
-      const double delta = red[1];
-      for (int q = tid; q < m * m; q += FT) {           // E overwrites S
-        const int x = q / m, y = q - x * m;
-        double ev;
-        if (x == y) ev = 0.5 * Rm[x * PT + y];
-        else {
-          const double gap = lam[y] - lam[x];
-          ev = fabs(gap) > delta ? (Sm[x * PT + y] + lam[y] * Rm[x * PT + y]) / gap
-                                 : 0.5 * Rm[x * PT + y];
-        }
-        W1[x * PT + y] = ev;
-      }
-      __syncthreads();
-      for (int q = tid; q < m * m; q += FT) {           // X + X E  -> S
-        const int x = q / m, y = q - x * m;
-        double t = Xd[x * PT + y];
-        for (int l = 0; l < m; ++l) t += Xd[x * PT + l] * W1[l * PT + y];
-        Sm[x * PT + y] = t;
-      }
-      __syncthreads();
+      Sm[x * PT + y] = sv;
+      Rm[x * PT + y] = (x == y ? 1.0 : 0.0) - rr;
+    }
+    __syncthreads();
+    for (int k = tid; k < m; k += FT) lam[k] = Sm[k * PT + k] / (1.0 - Rm[k * PT + k]);
+    __syncthreads();
+    {
+      double so = 0.0, ro = 0.0;
       for (int q = tid; q < m * m; q += FT) {
         const int x = q / m, y = q - x * m;
-        Xd[x * PT + y] = Sm[x * PT + y];
+        const double sv = Sm[x * PT + y] - (x == y ? lam[x] : 0.0);
+        so += sv * sv;
+        ro += Rm[x * PT + y] * Rm[x * PT + y];
       }
-      __syncthreads();
+      double v2[2] = {so, ro};
+      tbk::block_sum<double, 2>(v2, red, red + 2 * NT);
     }
-    // final Rayleigh quotients on the refined vectors
+    const double delta = 2.0 * (sqrt(red[2 * NT]) + tnorm * sqrt(red[2 * NT + 1]));
+    for (int q = tid; q < m * m; q += FT) {           // E
+      const int x = q / m, y = q - x * m;
+      double ev;
+      if (x == y) {
+        ev = 0.5 * Rm[x * PT + y];
+      } else {
+        const double gap = lam[y] - lam[x];
+        ev = fabs(gap) > delta ? (Sm[x * PT + y] + lam[y] * Rm[x * PT + y]) / gap
+                               : 0.5 * Rm[x * PT + y];
+      }
+      W1[x * PT + y] = ev;
+    }
+    __syncthreads();
+    for (int q = tid; q < m * m; q += FT) {           // X + X E -> S
+      const int x = q / m, y = q - x * m;
+      double t = Xd[x * PT + y];
+      for (int l = 0; l < m; ++l) t += Xd[x * PT + l] * W1[l * PT + y];
+      Sm[x * PT + y] = t;
+    }
+    __syncthreads();
+    for (int q = tid; q < m * m; q += FT) {
+      const int x = q / m, y = q - x * m;
+      Xd[x * PT + y] = Sm[x * PT + y];
+    }
+    __syncthreads();
+    }
+    // Rayleigh quotients on the refined vectors
     for (int k = tid; k < m; k += FT) {
       double num = 0.0, den = 0.0;
       for (int x = 0; x < m; ++x) {
         double t = 0.0;
-        for (int y = 0; y < m; ++y) if (near(x, y)) t += Tm[x * PT + y] * Xd[y * PT + k];
+        for (int y = blo[x]; y < bhi[x]; ++y) t += Tm[x * PT + y] * Xd[y * PT + k];
         num += Xd[x * PT + k] * t;
         den += Xd[x * PT + k] * Xd[x * PT + k];
       }
@@ -367,13 +404,11 @@ __global__ void __launch_bounds__(FT) eig_finish_kernel(const FinArgs<TV> a) {
   const int nrows = 4 * (deg + 1);
   for (int q = tid; q < nrows * NT; q += FT) {
     const int rr = q / NT, k = q - rr * NT;
-    double out = 0.0;
     if (k < m) {
       const TV* yr = a.Y + (rbase + rr) * NT;
       TV t = (TV)0;
       for (int l = 0; l < m; ++l) t += yr[act[l]] * X[l * PT + k];
-      out = (double)t;
-      a.P[(rbase + rr) * NT + rank[k]] = out;
+      a.P[(rbase + rr) * NT + rank[k]] = (double)t;
     } else {
       a.P[(rbase + rr) * NT + k] = 0.0;
     }

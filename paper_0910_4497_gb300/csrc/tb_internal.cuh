@@ -71,8 +71,7 @@ struct tb_ctx {
   float* Zf = nullptr;               // n * NT * NT
   float* lamf = nullptr;             // n * NT
   void* Vg = nullptr;                // kry_grid * Dmax * NT (TV) when the basis is global
-  int* lcol = nullptr;               // kry_grid * max_cluster * max_hnbr
-  int* lblk = nullptr;
+  int2* lent = nullptr;              // kry_grid * max_cluster * max_hnbr (slot, bond)
   double* mu_part = nullptr;         // mu_grid * 4
   unsigned int* bar = nullptr;       // barrier counter
   double* mu_state = nullptr;        // 4 doubles

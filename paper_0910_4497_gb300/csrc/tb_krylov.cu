@@ -4,17 +4,22 @@
 // One CTA per target atom (persistent, grid-stride over targets).  For target
 // i with cluster atoms cl[0..nc) (cl[0] = i, the rest ascending):
 //   * the local sparsity of H_c is built in the CTA: for each slot s and each
-//     Hamiltonian neighbour of cl[s] that is in the cluster, (local slot,
-//     global bond index).  H_c is never formed: its 4x4 blocks are read from
-//     the global bond table (FP64, or its FP32 mirror) during each sweep;
-//   * V_1 = E_i (the target's four orbitals, slot 0), B_0 = 0, and for
-//     k = 1..r:
-//       W = H_c V_k - V_{k-1} B_{k-1}^T        (block sparse sweep, 4 columns)
-//       A_k = V_k^T W;  W -= V_k A_k
-//       passes x: C = Q^T W, W -= Q C           (Q = V_1..V_k, classical GS)
-//       W = V_{k+1} B_k                         (in-block MGS, two passes per
-//                                                column, column dropped when its
-//                                                norm is <= defl_tol)
+//     Hamiltonian neighbour of cl[s] that is in the cluster, the pair (local
+//     slot, global bond index).  H_c is never formed: its 4x4 blocks are read
+//     from the global bond table (FP64, or its FP32 mirror) in every sweep;
+//   * V_1 = E_i (the target's four orbitals, slot 0) and for k = 1..r:
+//       W = H_c V_k - V_{k-1} B_{k-1}^T          block-sparse sweep, 4 columns
+//       pass 1: C = Q^T W, W -= Q C               Q = [V_1..V_k]; the V_k part
+//                                                 of C is A_k = V_k^T H_c V_k
+//       pass 2 (optional): the same again          (classical Gram-Schmidt,
+//                                                 "twice is enough")
+//       W = V_{k+1} B_k                           Cholesky QR applied twice on
+//                                                 the 4x4 Gram matrix; when the
+//                                                 block is ill-conditioned or
+//                                                 near deflation, modified
+//                                                 Gram-Schmidt per column with
+//                                                 the column dropped when its
+//                                                 norm is <= defl_tol
 //     T gets A_k on the diagonal and B_k / B_k^T off the diagonal;
 //   * the rows of V belonging to the target and its Hamiltonian neighbours are
 //     written out (Y) for the density-matrix columns.
@@ -32,25 +37,65 @@ constexpr int KW = KT / 32;
 constexpr int FL_MASK = KW;
 constexpr int FL_ACT = KW + 2;
 
-__device__ __forceinline__ void load_h(const double* __restrict__ H, int blk, double h[16]) {
-  const double2* p = reinterpret_cast<const double2*>(H + (size_t)blk * 16);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    double2 v = __ldg(p + q);
-    h[2 * q] = v.x;
-    h[2 * q + 1] = v.y;
-  }
+template <typename TV>
+struct alignas(4 * sizeof(TV)) vec4 {
+  TV v[4];
+};
+
+template <typename TV>
+__device__ __forceinline__ vec4<TV> ld4(const TV* p) {
+  return *reinterpret_cast<const vec4<TV>*>(p);
 }
-__device__ __forceinline__ void load_h(const float* __restrict__ H, int blk, float h[16]) {
-  const float4* p = reinterpret_cast<const float4*>(H + (size_t)blk * 16);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    float4 v = __ldg(p + q);
-    h[4 * q] = v.x;
-    h[4 * q + 1] = v.y;
-    h[4 * q + 2] = v.z;
-    h[4 * q + 3] = v.w;
+template <typename TV>
+__device__ __forceinline__ void st4(TV* p, const vec4<TV>& x) {
+  *reinterpret_cast<vec4<TV>*>(p) = x;
+}
+template <typename TV>
+__device__ __forceinline__ vec4<TV> ldg4(const TV* p) {
+  vec4<TV> r;
+  if constexpr (sizeof(TV) == 4) {
+    float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+  } else {
+    double2 t0 = __ldg(reinterpret_cast<const double2*>(p));
+    double2 t1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    r.v[0] = t0.x; r.v[1] = t0.y; r.v[2] = t1.x; r.v[3] = t1.y;
   }
+  return r;
+}
+
+// Sum 16 per-lane values over the warp with a butterfly that halves the
+// number of live values at every step (16 shuffles instead of 80).  On return
+// lanes with (lane & 1) == 0 hold the total of value index (lane >> 1).
+template <typename TV>
+__device__ __forceinline__ TV warp_reduce16(TV (&v)[16], int lane) {
+  TV a8[8];
+  const bool h16 = lane & 16;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const TV send = h16 ? v[j] : v[8 + j];
+    const TV keep = h16 ? v[8 + j] : v[j];
+    a8[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  TV a4[4];
+  const bool h8 = lane & 8;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const TV send = h8 ? a8[j] : a8[4 + j];
+    const TV keep = h8 ? a8[4 + j] : a8[j];
+    a4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  TV a2[2];
+  const bool h4 = lane & 4;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const TV send = h4 ? a4[j] : a4[2 + j];
+    const TV keep = h4 ? a4[2 + j] : a4[j];
+    a2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  const bool h2 = lane & 2;
+  TV a1 = (h2 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? a2[0] : a2[1], 2);
+  return a1 + __shfl_xor_sync(0xffffffffu, a1, 1);
 }
 
 template <typename TV>
@@ -66,8 +111,7 @@ struct KryArgs {
   TV* Y;
   unsigned long long* colmask;
   TV* Vg;
-  int* lcol;
-  int* lblk;
+  int2* lent;
   int* st;
 };
 
@@ -81,49 +125,102 @@ __device__ __forceinline__ int find_slot(const int* cl, int nc, int b) {
   return (lo < nc && cl[lo] == b) ? lo : -1;
 }
 
-__host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ __forceinline__ size_t align32(size_t x) { return (x + 31) & ~size_t(31); }
 
 template <typename TV>
 __host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, bool vsmem) {
   const size_t Dmax = 4 * (size_t)max_cluster;
+  const size_t np = (size_t)(r > KW ? r : KW);
   size_t b = 0;
-  b += align16(sizeof(int) * max_cluster);            // cl
-  b += align16(sizeof(int) * (max_cluster + 1));      // rowptr
-  b += align16(sizeof(TV) * Dmax * 4);                // W
-  if (vsmem) b += align16(sizeof(TV) * Dmax * 4 * r); // basis
-  b += align16(sizeof(TV) * 16 * r);                  // projection coefficients
-  b += align16(sizeof(TV) * 16 * 2);                  // A_k, B_{k-1}
-  b += align16(sizeof(double) * 16);                  // B_k (FP64)
-  b += align16(sizeof(TV) * 16 * KW);                 // reduction scratch
-  b += align16(sizeof(int) * 16);                     // flags
+  b += align32(sizeof(int) * max_cluster);            // cl
+  b += align32(sizeof(int) * (max_cluster + 1));      // rowptr
+  b += align32(sizeof(TV) * Dmax * 4);                // W
+  if (vsmem) b += align32(sizeof(TV) * Dmax * 4 * r); // basis
+  b += align32(sizeof(TV) * 16 * np);                 // projection partials
+  b += align32(sizeof(TV) * 16 * r);                  // projection coefficients
+  b += align32(sizeof(TV) * 16 * 2);                  // B_{k-1}, Gram
+  b += align32(sizeof(double) * 16 * 2);              // B_k, first Cholesky factor
+  b += align32(sizeof(TV) * 16 * KW);                 // reduction scratch
+  b += align32(sizeof(int) * 16);                     // flags
   return b;
+}
+
+// Cholesky of a 4x4 Gram matrix g (row-major) into the upper-triangular R
+// (row-major); returns false when a pivot is not a healthy fraction of its
+// diagonal or falls near the deflation threshold.
+template <typename TV>
+__device__ __forceinline__ bool chol4(const TV (&g)[16], TV (&R)[16], TV rel, double abs_tol) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) R[q] = (TV)0;
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    TV d = g[c * 4 + c];
+#pragma unroll
+    for (int j = 0; j < c; ++j) d -= R[j * 4 + c] * R[j * 4 + c];
+    if (!(d > rel * g[c * 4 + c]) || !(d > (TV)(abs_tol * abs_tol))) ok = false;
+    const TV rc = sqrt(d > (TV)0 ? d : (TV)1);
+    R[c * 4 + c] = rc;
+    const TV inv = (TV)1 / rc;
+#pragma unroll
+    for (int e = c + 1; e < 4; ++e) {
+      TV t = g[c * 4 + e];
+#pragma unroll
+      for (int j = 0; j < c; ++j) t -= R[j * 4 + c] * R[j * 4 + e];
+      R[c * 4 + e] = t * inv;
+    }
+  }
+  return ok;
+}
+
+// Inverse of an upper-triangular 4x4 R (row-major).
+template <typename TV>
+__device__ __forceinline__ void triinv4(const TV (&R)[16], TV (&X)[16]) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) X[q] = (TV)0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    X[c * 4 + c] = (TV)1 / R[c * 4 + c];
+#pragma unroll
+    for (int rr = c - 1; rr >= 0; --rr) {
+      TV t = (TV)0;
+#pragma unroll
+      for (int j = rr + 1; j <= c; ++j) t += R[rr * 4 + j] * X[j * 4 + c];
+      X[rr * 4 + c] = -t / R[rr * 4 + rr];
+    }
+  }
 }
 
 template <typename TV, bool VSMEM>
 __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(32) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r = a.r, NT = 4 * r, Dmax = 4 * a.max_cluster;
+  const int np = r > KW ? r : KW;
   size_t off = 0;
-  int* cl = reinterpret_cast<int*>(smem + off);      off += align16(sizeof(int) * a.max_cluster);
-  int* rowptr = reinterpret_cast<int*>(smem + off);  off += align16(sizeof(int) * (a.max_cluster + 1));
-  TV* W = reinterpret_cast<TV*>(smem + off);         off += align16(sizeof(TV) * Dmax * 4);
+  int* cl = reinterpret_cast<int*>(smem + off);      off += align32(sizeof(int) * a.max_cluster);
+  int* rowptr = reinterpret_cast<int*>(smem + off);  off += align32(sizeof(int) * (a.max_cluster + 1));
+  TV* W = reinterpret_cast<TV*>(smem + off);         off += align32(sizeof(TV) * Dmax * 4);
   TV* V;
   if (VSMEM) {
     V = reinterpret_cast<TV*>(smem + off);
-    off += align16(sizeof(TV) * (size_t)Dmax * 4 * r);
+    off += align32(sizeof(TV) * (size_t)Dmax * 4 * r);
   } else {
     V = a.Vg + (size_t)blockIdx.x * Dmax * 4 * r;
   }
-  TV* Cc = reinterpret_cast<TV*>(smem + off);        off += align16(sizeof(TV) * 16 * r);
-  TV* Ablk = reinterpret_cast<TV*>(smem + off);
-  TV* Bp = Ablk + 16;                                off += align16(sizeof(TV) * 32);
-  double* Bs = reinterpret_cast<double*>(smem + off); off += align16(sizeof(double) * 16);
-  TV* red = reinterpret_cast<TV*>(smem + off);       off += align16(sizeof(TV) * 16 * KW);
+  TV* Cp = reinterpret_cast<TV*>(smem + off);        off += align32(sizeof(TV) * 16 * np);
+  TV* Cc = reinterpret_cast<TV*>(smem + off);        off += align32(sizeof(TV) * 16 * r);
+  TV* Bp = reinterpret_cast<TV*>(smem + off);
+  TV* Gs = Bp + 16;                                  off += align32(sizeof(TV) * 32);
+  double* Bs = reinterpret_cast<double*>(smem + off);
+  double* R1s = Bs + 16;                             off += align32(sizeof(double) * 32);
+  TV* red = reinterpret_cast<TV*>(smem + off);       off += align32(sizeof(TV) * 16 * KW);
   int* flags = reinterpret_cast<int*>(smem + off);
-  int* lcol = a.lcol + (size_t)blockIdx.x * a.max_cluster * a.max_hnbr;
-  int* lblk = a.lblk + (size_t)blockIdx.x * a.max_cluster * a.max_hnbr;
+  int2* lent = a.lent + (size_t)blockIdx.x * a.max_cluster * a.max_hnbr;
   const TV Es = (TV)a.Es, Ep = (TV)a.Ep;
+  // Cholesky-QR acceptance: each pivot must keep this fraction of its diagonal
+  const TV chol_rel = sizeof(TV) == 4 ? (TV)1e-3 : (TV)1e-8;
+  const double chol_abs = 1000.0 * a.defl_tol;
 
   for (int i = blockIdx.x; i < a.n; i += gridDim.x) {
     const int c0 = a.c_off[i];
@@ -196,11 +293,7 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
       const int pe = min(a.h_off[at + 1], a.h_off[at] + a.max_hnbr);
       for (int p = a.h_off[at]; p < pe; ++p) {
         const int t = find_slot(cl, nc, a.h_idx[p]);
-        if (t >= 0) {
-          lcol[e] = t;
-          lblk[e] = p;
-          ++e;
-        }
+        if (t >= 0) lent[e++] = make_int2(t, p);
       }
     }
     // seed block V_1 = E_i
@@ -218,181 +311,246 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
     for (int k = 0; k < r; ++k) {
       const TV* Vk = V + (size_t)k * Dmax * 4;
       const TV* Vp = V + (size_t)(k > 0 ? k - 1 : 0) * Dmax * 4;
-      // ---- W = H_c V_k - V_{k-1} B_{k-1}^T
+      // ---- W = H_c V_k - V_{k-1} B_{k-1}^T ; item (s, alpha) = one row of W
       for (int it = tid; it < 4 * nc; it += KT) {
-        const int s = it >> 2, c = it & 3;
-        TV x0 = Vk[(4 * s + 0) * 4 + c], x1 = Vk[(4 * s + 1) * 4 + c];
-        TV x2 = Vk[(4 * s + 2) * 4 + c], x3 = Vk[(4 * s + 3) * 4 + c];
-        TV a0 = Es * x0, a1 = Ep * x1, a2 = Ep * x2, a3 = Ep * x3;
+        const int s = it >> 2, al = it & 3;
+        const vec4<TV> vs = ld4(Vk + (4 * s + al) * 4);
+        const TV on = al == 0 ? Es : Ep;
+        TV acc[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] = on * vs.v[c];
         const int e1 = rowptr[s + 1];
+#pragma unroll 2
         for (int e = rowptr[s]; e < e1; ++e) {
-          const int t = lcol[e];
-          TV h[16];
-          load_h(a.H, lblk[e], h);
-          const TV y0 = Vk[(4 * t + 0) * 4 + c], y1 = Vk[(4 * t + 1) * 4 + c];
-          const TV y2 = Vk[(4 * t + 2) * 4 + c], y3 = Vk[(4 * t + 3) * 4 + c];
-          a0 += h[0] * y0 + h[1] * y1 + h[2] * y2 + h[3] * y3;
-          a1 += h[4] * y0 + h[5] * y1 + h[6] * y2 + h[7] * y3;
-          a2 += h[8] * y0 + h[9] * y1 + h[10] * y2 + h[11] * y3;
-          a3 += h[12] * y0 + h[13] * y1 + h[14] * y2 + h[15] * y3;
+          const int2 en = lent[e];
+          const vec4<TV> h = ldg4(a.H + (size_t)en.y * 16 + al * 4);
+#pragma unroll
+          for (int be = 0; be < 4; ++be) {
+            const vec4<TV> vt = ld4(Vk + (4 * en.x + be) * 4);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[c] += h.v[be] * vt.v[c];
+          }
         }
         if (k > 0) {
-          const TV b0 = Bp[c * 4 + 0], b1 = Bp[c * 4 + 1], b2 = Bp[c * 4 + 2], b3 = Bp[c * 4 + 3];
-          const TV* pr = Vp + (4 * s) * 4;
-          a0 -= pr[0] * b0 + pr[1] * b1 + pr[2] * b2 + pr[3] * b3;
-          a1 -= pr[4] * b0 + pr[5] * b1 + pr[6] * b2 + pr[7] * b3;
-          a2 -= pr[8] * b0 + pr[9] * b1 + pr[10] * b2 + pr[11] * b3;
-          a3 -= pr[12] * b0 + pr[13] * b1 + pr[14] * b2 + pr[15] * b3;
+          const vec4<TV> vp = ld4(Vp + (4 * s + al) * 4);
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            acc[c] -= vp.v[0] * Bp[c * 4 + 0] + vp.v[1] * Bp[c * 4 + 1] +
+                      vp.v[2] * Bp[c * 4 + 2] + vp.v[3] * Bp[c * 4 + 3];
         }
-        W[(4 * s + 0) * 4 + c] = a0;
-        W[(4 * s + 1) * 4 + c] = a1;
-        W[(4 * s + 2) * 4 + c] = a2;
-        W[(4 * s + 3) * 4 + c] = a3;
+        vec4<TV> o;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) o.v[c] = acc[c];
+        st4(W + (4 * s + al) * 4, o);
       }
       __syncthreads();
-      // ---- A_k = V_k^T W
-      {
-        TV part[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) part[q] = (TV)0;
-        for (int row = tid; row < D; row += KT) {
-          TV v[4], w[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) { v[q] = Vk[row * 4 + q]; w[q] = W[row * 4 + q]; }
-#pragma unroll
-          for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) part[ii * 4 + c] += v[ii] * w[c];
-        }
-        tbk::block_sum<TV, 16>(part, red, Ablk);
-      }
-      if (tid < 16) {
-        const int ii = tid >> 2, c = tid & 3;
-        Ti[(4 * k + ii) * NT + 4 * k + c] = 0.5 * ((double)Ablk[ii * 4 + c] + (double)Ablk[c * 4 + ii]);
-      }
-      for (int row = tid; row < D; row += KT) {
-        TV v[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = Vk[row * 4 + q];
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          W[row * 4 + c] -= v[0] * Ablk[c] + v[1] * Ablk[4 + c] + v[2] * Ablk[8 + c] + v[3] * Ablk[12 + c];
-      }
-      __syncthreads();
-      if (k == r - 1) break;
-      // ---- full reorthogonalisation: classical Gram-Schmidt against V_1..V_k
-      for (int pass = 0; pass < a.reorth_passes; ++pass) {
-        for (int b = warp; b <= k; b += KW) {
+      // ---- classical Gram-Schmidt against V_1..V_k (pass 0 yields A_k); on
+      // the last step only A_k is needed
+      const int passes = (k == r - 1) ? 1 : a.reorth_passes;
+      for (int pass = 0; pass < passes; ++pass) {
+        const int b0 = (k == r - 1) ? k : 0;
+        const int nb = k + 1 - b0;
+        const int nseg = nb >= KW ? 1 : KW / nb;
+        const int items = nb * nseg;
+        for (int w = warp; w < items; w += KW) {
+          const int b = b0 + w / nseg, seg = w % nseg;
+          const int rlo = (D * seg) / nseg, rhi = (D * (seg + 1)) / nseg;
           const TV* Vb = V + (size_t)b * Dmax * 4;
-          TV part[16];
+          TV acc[16];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) part[q] = (TV)0;
-          for (int row = lane; row < D; row += 32) {
-            TV v[4], w[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) { v[q] = Vb[row * 4 + q]; w[q] = W[row * 4 + q]; }
+          for (int q = 0; q < 16; ++q) acc[q] = (TV)0;
+          for (int row = rlo + lane; row < rhi; row += 32) {
+            const vec4<TV> v = ld4(Vb + row * 4);
+            const vec4<TV> x = ld4(W + row * 4);
 #pragma unroll
             for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-              for (int c = 0; c < 4; ++c) part[ii * 4 + c] += v[ii] * w[c];
+              for (int c = 0; c < 4; ++c) acc[ii * 4 + c] += v.v[ii] * x.v[c];
           }
-#pragma unroll
-          for (int q = 0; q < 16; ++q) part[q] = tbk::warp_sum(part[q]);
-          if (lane < 16) {
-            TV val = part[0];
-#pragma unroll
-            for (int q = 1; q < 16; ++q) if (lane == q) val = part[q];
-            Cc[b * 16 + lane] = val;
-          }
+          const TV tot = warp_reduce16(acc, lane);
+          if ((lane & 1) == 0) Cp[w * 16 + (lane >> 1)] = tot;
         }
         __syncthreads();
+        for (int t = tid; t < nb * 16; t += KT) {
+          const int bl = t >> 4, q = t & 15;
+          TV sum = (TV)0;
+          for (int sg = 0; sg < nseg; ++sg) sum += Cp[(bl * nseg + sg) * 16 + q];
+          Cc[(b0 + bl) * 16 + q] = sum;
+        }
+        __syncthreads();
+        if (pass == 0 && tid < 16) {
+          const int ii = tid >> 2, c = tid & 3;
+          Ti[(4 * k + ii) * NT + 4 * k + c] =
+              0.5 * ((double)Cc[k * 16 + ii * 4 + c] + (double)Cc[k * 16 + c * 4 + ii]);
+        }
+        if (k == r - 1) break;
         for (int row = tid; row < D; row += KT) {
-          TV w[4];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) w[c] = W[row * 4 + c];
+          vec4<TV> x = ld4(W + row * 4);
           for (int b = 0; b <= k; ++b) {
-            const TV* vb = V + (size_t)b * Dmax * 4 + row * 4;
-            const TV v0 = vb[0], v1 = vb[1], v2 = vb[2], v3 = vb[3];
+            const vec4<TV> v = ld4(V + (size_t)b * Dmax * 4 + row * 4);
             const TV* cb = Cc + b * 16;
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-              w[c] -= v0 * cb[c] + v1 * cb[4 + c] + v2 * cb[8 + c] + v3 * cb[12 + c];
-          }
+            for (int ii = 0; ii < 4; ++ii) {
+              const vec4<TV> crow = ld4(cb + ii * 4);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) W[row * 4 + c] = w[c];
+              for (int c = 0; c < 4; ++c) x.v[c] -= v.v[ii] * crow.v[c];
+            }
+          }
+          st4(W + row * 4, x);
         }
         __syncthreads();
       }
-      // ---- in-block QR with deflation (one warp): W = V_{k+1} B_k
-      if (warp == 0) {
-        TV* Vn = V + (size_t)(k + 1) * Dmax * 4;
-        double R[16];
+      if (k == r - 1) break;
+      // ---- in-block QR: W = V_{k+1} B_k.  Cholesky QR twice; the MGS path
+      // takes over when a pivot signals ill-conditioning or deflation.
+      TV* Vn = V + (size_t)(k + 1) * Dmax * 4;
+      int chol_state = 0;   // 1: first factor refused (W untouched); 2: second refused
+      for (int cq = 0; cq < 2; ++cq) {
+        TV g[10];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) R[q] = 0.0;
-        int act = 0;
-        bool nonfinite = false;
+        for (int q = 0; q < 10; ++q) g[q] = (TV)0;
+        for (int row = tid; row < D; row += KT) {
+          const vec4<TV> x = ld4(W + row * 4);
+          int q = 0;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          for (int pass = 0; pass < 2; ++pass) {
-            if (c == 0) break;
-            TV dd[3] = {(TV)0, (TV)0, (TV)0};
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int e = c; e < 4; ++e) g[q++] += x.v[c] * x.v[e];
+        }
+        tbk::block_sum<TV, 10>(g, red, Gs);
+        TV G[16];
+        {
+          int q = 0;
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int e = c; e < 4; ++e) { G[c * 4 + e] = Gs[q]; G[e * 4 + c] = Gs[q]; ++q; }
+        }
+        TV R[16], Ri[16];
+        // every thread factors the same shared Gram matrix: the decision is uniform
+        if (!chol4(G, R, chol_rel, cq == 0 ? chol_abs : 0.0)) {
+          chol_state = cq + 1;
+          break;
+        }
+        triinv4(R, Ri);
+        TV* dst = cq == 0 ? W : Vn;
+        for (int row = tid; row < D; row += KT) {
+          const vec4<TV> x = ld4(W + row * 4);
+          vec4<TV> y;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            TV t = (TV)0;
+#pragma unroll
+            for (int j = 0; j <= c; ++j) t += x.v[j] * Ri[j * 4 + c];
+            y.v[c] = t;
+          }
+          st4(dst + row * 4, y);
+        }
+        if (tid == 0) {
+          if (cq == 0) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) R1s[q] = (double)R[q];
+          } else {
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr)          // B_k = R2 R1
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                double t = 0.0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) t += (double)R[rr * 4 + j] * R1s[j * 4 + c];
+                Bs[rr * 4 + c] = t;
+              }
+            flags[FL_ACT] = 0xF;
+          }
+        }
+        __syncthreads();
+      }
+      if (chol_state != 0) {
+        if (warp == 0) {
+          double R[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) R[q] = 0.0;
+          int act = 0;
+          bool nonfinite = false;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            for (int pass = 0; pass < 2; ++pass) {
+              if (c == 0) break;
+              TV dd[3] = {(TV)0, (TV)0, (TV)0};
+              for (int row = lane; row < D; row += 32) {
+                const TV w = W[row * 4 + c];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) if (j < c) dd[j] += Vn[row * 4 + j] * w;
+              }
+#pragma unroll
+              for (int j = 0; j < 3; ++j) if (j < c) dd[j] = tbk::warp_sum(dd[j]);
+              for (int row = lane; row < D; row += 32) {
+                TV w = W[row * 4 + c];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) if (j < c) w -= dd[j] * Vn[row * 4 + j];
+                W[row * 4 + c] = w;
+              }
+#pragma unroll
+              for (int j = 0; j < 3; ++j) if (j < c) R[j * 4 + c] += (double)dd[j];
+            }
+            TV nn = (TV)0;
             for (int row = lane; row < D; row += 32) {
               const TV w = W[row * 4 + c];
-#pragma unroll
-              for (int j = 0; j < 3; ++j) if (j < c) dd[j] += Vn[row * 4 + j] * w;
+              nn += w * w;
             }
-#pragma unroll
-            for (int j = 0; j < 3; ++j) if (j < c) dd[j] = tbk::warp_sum(dd[j]);
-            for (int row = lane; row < D; row += 32) {
-              TV w = W[row * 4 + c];
-#pragma unroll
-              for (int j = 0; j < 3; ++j) if (j < c) w -= dd[j] * Vn[row * 4 + j];
-              W[row * 4 + c] = w;
+            nn = tbk::warp_sum(nn);
+            const double nrm = sqrt((double)nn);
+            if (!isfinite(nrm)) nonfinite = true;
+            if (nrm > a.defl_tol) {
+              const TV inv = (TV)(1.0 / nrm);
+              for (int row = lane; row < D; row += 32) Vn[row * 4 + c] = W[row * 4 + c] * inv;
+              R[c * 4 + c] = nrm;
+              act |= 1 << c;
+            } else {
+              for (int row = lane; row < D; row += 32) Vn[row * 4 + c] = (TV)0;
             }
+          }
+          if (lane == 0) {
+            if (chol_state == 2) {      // W was already W R1^{-1}: B_k = R_mgs R1
 #pragma unroll
-            for (int j = 0; j < 3; ++j) if (j < c) R[j * 4 + c] += (double)dd[j];
-          }
-          TV nn = (TV)0;
-          for (int row = lane; row < D; row += 32) {
-            const TV w = W[row * 4 + c];
-            nn += w * w;
-          }
-          nn = tbk::warp_sum(nn);
-          const double nrm = sqrt((double)nn);
-          if (!isfinite(nrm)) nonfinite = true;
-          if (nrm > a.defl_tol) {
-            const TV inv = (TV)(1.0 / nrm);
-            for (int row = lane; row < D; row += 32) Vn[row * 4 + c] = W[row * 4 + c] * inv;
-            R[c * 4 + c] = nrm;
-            act |= 1 << c;
-          } else {
-            for (int row = lane; row < D; row += 32) Vn[row * 4 + c] = (TV)0;
+              for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                  double t = 0.0;
+#pragma unroll
+                  for (int j = 0; j < 4; ++j) t += R[rr * 4 + j] * R1s[j * 4 + c];
+                  Bs[rr * 4 + c] = t;
+                }
+            } else {
+#pragma unroll
+              for (int q = 0; q < 16; ++q) Bs[q] = R[q];
+            }
+            flags[FL_ACT] = act;
+            if (nonfinite) tbk::set_status(a.st, TB_ERR_NONFINITE, i);
           }
         }
-        if (lane == 0) {
-#pragma unroll
-          for (int q = 0; q < 16; ++q) Bs[q] = R[q];
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              Ti[(4 * (k + 1) + j) * NT + 4 * k + c] = R[j * 4 + c];
-              Ti[(4 * k + c) * NT + 4 * (k + 1) + j] = R[j * 4 + c];
-            }
-          flags[FL_ACT] = act;
-          // active-column mask of the basis, 64 bits kept as two ints
-          unsigned long long mask = ((unsigned long long)(unsigned)flags[FL_MASK + 1] << 32) |
-                                    (unsigned)flags[FL_MASK];
-          mask |= (unsigned long long)act << (4 * (k + 1));
-          flags[FL_MASK] = (int)(mask & 0xffffffffull);
-          flags[FL_MASK + 1] = (int)(mask >> 32);
-          if (nonfinite) tbk::set_status(a.st, TB_ERR_NONFINITE, i);
-        }
+        __syncthreads();
       }
-      __syncthreads();
+      if (tid == 0) {
+        const int act = flags[FL_ACT];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            Ti[(4 * (k + 1) + j) * NT + 4 * k + c] = Bs[j * 4 + c];
+            Ti[(4 * k + c) * NT + 4 * (k + 1) + j] = Bs[j * 4 + c];
+          }
+        // active-column mask of the basis, 64 bits kept as two ints
+        unsigned long long mask = ((unsigned long long)(unsigned)flags[FL_MASK + 1] << 32) |
+                                  (unsigned)flags[FL_MASK];
+        mask |= (unsigned long long)act << (4 * (k + 1));
+        flags[FL_MASK] = (int)(mask & 0xffffffffull);
+        flags[FL_MASK + 1] = (int)(mask >> 32);
+        if (!isfinite(Bs[0] + Bs[5] + Bs[10] + Bs[15])) tbk::set_status(a.st, TB_ERR_NONFINITE, i);
+      }
       if (tid < 16) Bp[tid] = (TV)Bs[tid];
-      const int act_now = flags[FL_ACT];
       __syncthreads();
+      const int act_now = flags[FL_ACT];
       if (act_now == 0) break;
       nblocks = k + 2;
     }
@@ -405,7 +563,7 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
       for (int q = tid; q < nrows * NT; q += KT) {
         const int rr = q / NT, col = q - rr * NT;
         const int qq = rr >> 2, beta = rr & 3;
-        const int slot = qq == 0 ? 0 : lcol[rowptr[0] + qq - 1];
+        const int slot = qq == 0 ? 0 : lent[rowptr[0] + qq - 1].x;
         const int b = col >> 2, c = col & 3;
         TV val = (TV)0;
         if (b < nblocks) val = V[(size_t)b * Dmax * 4 + (4 * slot + beta) * 4 + c];
@@ -426,7 +584,7 @@ tb_status launch_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const i
   a.Es = p.Es; a.Ep = p.Ep; a.defl_tol = p.defl_tol;
   a.c_off = c_off; a.c_idx = c_idx; a.h_off = h_off; a.h_idx = h_idx; a.H = H;
   a.T = c->T; a.Y = reinterpret_cast<TV*>(c->Y); a.colmask = c->colmask;
-  a.Vg = reinterpret_cast<TV*>(c->Vg); a.lcol = c->lcol; a.lblk = c->lblk; a.st = c->d_status;
+  a.Vg = reinterpret_cast<TV*>(c->Vg); a.lent = c->lent; a.st = c->d_status;
   const int grid = n < c->kry_grid ? n : c->kry_grid;
   if (grid <= 0) return TB_OK;
   krylov_kernel<TV, VSMEM><<<grid, KT, c->kry_smem, s>>>(a);

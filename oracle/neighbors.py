@@ -10,15 +10,18 @@ box of side L:
   |R_j - R_i| <= Rc, ascending j.
 
 Distance test (the definition the lists must reproduce bit for bit):
-d = R_j - R_i; d <- d - L * rint(d / L) per component (minimum image, ties to
-even); r2 = (dx*dx + dy*dy) + dz*dz with every operation rounded separately
-(no fused multiply-add); the pair is in iff r2 <= R*R.
+d = R_j - R_i per component, then the nearest periodic image: d - L if
+d > L/2, d + L if d < -L/2, else d (positions lie in [0, L), so one shift
+suffices; a separation of exactly half a box keeps its sign);
+r2 = (dx*dx + dy*dy) + dz*dz with every operation rounded separately (no fused
+multiply-add); the pair is in iff r2 <= R*R.
 """
 import numpy as np
 
 
 def minimum_image(d, L):
-    return d - L * np.rint(d / L)
+    h = 0.5 * L
+    return np.where(d > h, d - L, np.where(d < -h, d + L, d))
 
 
 def pair_r2(pos, i, L):

@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--reorth-passes", type=int, default=2)
+    ap.add_argument("--reorth-passes", type=int, default=1)
     return ap.parse_args()
 
 

@@ -114,7 +114,7 @@ tb_status tb_get_status(tb_ctx* ctx, int* code, int* info, void* stream);
  * a1. Neighbour and cluster lists (Sec. 2: atoms within the cutoff radius of
  * the target).  Brute force over all pairs with an FP32 prefilter; the
  * membership decision is the FP64 test below, so the lists are bit-exact:
- *   d = x_j - x_i;  d -= L * rint(d / L)  (per component, ties to even)
+ *   d = x_j - x_i;  d -= L if d > L/2;  d += L if d < -L/2   (per component)
  *   r2 = (dx*dx + dy*dy) + dz*dz   (each operation rounded, no FMA)
  *   Hamiltonian list of i: all j != i with r2 <= rm*rm, ascending j;
  *   cluster of i: i itself first, then all j != i with r2 <= Rc*Rc, ascending.

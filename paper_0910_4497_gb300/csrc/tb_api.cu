@@ -57,11 +57,12 @@ size_t carve(tb_ctx* c, int n, unsigned char* base) {
   c->lamf = k.take<float>((size_t)n * NT);
   c->Vg = k.take<unsigned char>(krylov_basis_bytes_global(c));
   c->lent = k.take<int2>((size_t)c->kry_grid * p.max_cluster * p.max_hnbr);
-  c->mu_part = k.take<double>(4 * (size_t)(c->mu_grid > 0 ? c->mu_grid : 1));
+  c->mu_part = k.take<double>(2 * 16 * (size_t)(c->mu_grid > 0 ? c->mu_grid : 1));
   c->bar = k.take<unsigned>(4);
   c->mu_state = k.take<double>(4);
   c->rho = k.take<double>(rows * 16 > (size_t)n * 2 ? rows * 16 : (size_t)n * 2);
   c->per_target = k.take<double>((size_t)n * 5);
+  c->bondf = k.take<double>(hcap * 4);
   c->h_off = k.take<int>(n + 1);
   c->h_idx = k.take<int>(hcap);
   c->c_off = k.take<int>(n + 1);

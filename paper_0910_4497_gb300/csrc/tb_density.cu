@@ -13,7 +13,7 @@
 
 namespace {
 
-constexpr int MT = 256;    // mu kernel threads
+constexpr int MT = 256;    // mu kernel threads (16 per partial value: MT >= 16 * 16)
 constexpr int RT = 128;    // rho kernel threads
 
 __device__ __forceinline__ double fermi(double x) {
@@ -74,12 +74,15 @@ struct MuArgs {
   double* mu_out;
   double* ncount_out;
   int* iters_out;
-  double* part;        // 2 generations x gridDim x 2
+  double* part;        // 2 generations x gridDim x MU_PART doubles
   unsigned* bar;
   int max_iter;
   long long timeout;
   int* st;
 };
+
+constexpr int MU_NPT = 16;     // trial points per coarse pass
+constexpr int MU_PART = 16;    // partial slots per block and generation
 
 __device__ __forceinline__ double pair_weight(const double* S, int NT, long long q) {
   const long long i = q / NT;
@@ -88,28 +91,41 @@ __device__ __forceinline__ double pair_weight(const double* S, int NT, long long
   return s[0] * s[0] + s[NT] * s[NT] + s[2 * NT] * s[2 * NT] + s[3 * NT] * s[3 * NT];
 }
 
-// Sum two per-block partials over all blocks in a fixed order (warp 0).
-__device__ void sum_partials(const double* part, int G, double* out2) {
-  if (threadIdx.x < 32) {
-    double a = 0.0, b = 0.0;
-    for (int g = threadIdx.x; g < G; g += 32) {
-      a += part[2 * g];
-      b += part[2 * g + 1];
-    }
-    a = tbk::warp_sum(a);
-    b = tbk::warp_sum(b);
-    if (threadIdx.x == 0) { out2[0] = a; out2[1] = b; }
+// Every block publishes M partials in generation buffer `gen`, passes the grid
+// barrier, then sums all blocks' partials in block order (fixed order: every
+// block obtains bitwise the same totals).  Returns false on barrier timeout.
+template <int M>
+__device__ bool grid_allreduce(const double (&v)[M], const MuArgs& a, unsigned& gen,
+                               double* red, double* tot, int* sflag) {
+  const int G = gridDim.x;
+  tbk::block_sum16<double, M>(v, red, tot);
+  double* pg = a.part + (size_t)(gen & 1) * G * MU_PART;
+  if (threadIdx.x < M) pg[blockIdx.x * MU_PART + threadIdx.x] = tot[threadIdx.x];
+  ++gen;
+  if (!grid_barrier(a.bar, gen * G, a.timeout, a.st, sflag)) return false;
+  // 16 threads per value stride over the blocks, then a fixed shuffle tree
+  {
+    const int m = threadIdx.x >> 4, sub = threadIdx.x & 15;
+    double sum = 0.0;
+    if (m < M)
+      for (int g = sub; g < G; g += 16) sum += pg[g * MU_PART + m];
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    __syncthreads();
+    if (m < M && sub == 0) tot[m] = sum;
   }
   __syncthreads();
+  return true;
 }
 
 __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
-  __shared__ double red[MT / 32 * 2];
-  __shared__ double tot[2];
+  __shared__ double red[MT / 32 * 16];
+  __shared__ double tot[16];
   __shared__ int sflag;
   const int G = gridDim.x;
   const long long gtid = (long long)blockIdx.x * MT + threadIdx.x;
   const long long gstride = (long long)G * MT;
+  const double ikT = 1.0 / a.kT;
   unsigned gen = 0;
   // ---- bracket: [min lam - 40 kT, max lam + 40 kT] over pairs with weight
   double lmin = 1e300, lmax = -1e300;
@@ -127,25 +143,72 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
   }
   if ((threadIdx.x & 31) == 0) { red[2 * (threadIdx.x >> 5)] = lmin; red[2 * (threadIdx.x >> 5) + 1] = lmax; }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double m0 = 1e300, m1 = -1e300;
-    for (int w = 0; w < MT / 32; ++w) { m0 = fmin(m0, red[2 * w]); m1 = fmax(m1, red[2 * w + 1]); }
-    a.part[2 * blockIdx.x] = m0;
-    a.part[2 * blockIdx.x + 1] = -m1;
-  }
-  if (!grid_barrier(a.bar, (++gen) * G, a.timeout, a.st, &sflag)) return;
-  if (threadIdx.x < 32) {
-    double m0 = 1e300, m1 = 1e300;
-    for (int g = threadIdx.x; g < G; g += 32) { m0 = fmin(m0, a.part[2 * g]); m1 = fmin(m1, a.part[2 * g + 1]); }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      m0 = fmin(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-      m1 = fmin(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+  {
+    double* pg = a.part + (size_t)(gen & 1) * G * MU_PART;
+    if (threadIdx.x == 0) {
+      double m0 = 1e300, m1 = -1e300;
+      for (int w = 0; w < MT / 32; ++w) { m0 = fmin(m0, red[2 * w]); m1 = fmax(m1, red[2 * w + 1]); }
+      pg[blockIdx.x * MU_PART] = m0;
+      pg[blockIdx.x * MU_PART + 1] = m1;
     }
-    if (threadIdx.x == 0) { tot[0] = m0; tot[1] = -m1; }
+    ++gen;
+    if (!grid_barrier(a.bar, gen * G, a.timeout, a.st, &sflag)) return;
+    if (threadIdx.x == 0) {
+      double m0 = 1e300, m1 = -1e300;
+      for (int g = 0; g < G; ++g) { m0 = fmin(m0, pg[g * MU_PART]); m1 = fmax(m1, pg[g * MU_PART + 1]); }
+      tot[0] = m0;
+      tot[1] = m1;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  double lo = tot[0] - 40.0 * a.kT, hi = tot[1] + 40.0 * a.kT;
+  const double lo0 = tot[0] - 40.0 * a.kT, hi0 = tot[1] + 40.0 * a.kT;
+  double lo = lo0, hi = hi0;
+  int iters = 0;
+  // ---- coarse bracketing with FP32 occupations at MU_NPT points per pass
+  for (int pass = 0; pass < 6 && hi - lo > 0.01; ++pass) {
+    double v[MU_NPT];
+    float cnt[MU_NPT];
+    const double h = (hi - lo) / (MU_NPT + 1);
+#pragma unroll
+    for (int t = 0; t < MU_NPT; ++t) cnt[t] = 0.f;
+    for (long long q = gtid; q < a.npairs; q += gstride) {
+      const double w = pair_weight(a.S, a.NT, q);
+      if (w == 0.0) continue;
+      const float x0 = (float)((a.lambda[q] - lo) * ikT), dx = (float)(h * ikT);
+      const float wf = (float)w;
+#pragma unroll
+      for (int t = 0; t < MU_NPT; ++t) {
+        const float x = fminf(fmaxf(x0 - (t + 1) * dx, -80.f), 80.f);
+        cnt[t] += wf / (1.f + __expf(x));
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < MU_NPT; ++t) v[t] = (double)cnt[t];
+    if (!grid_allreduce<MU_NPT>(v, a, gen, red, tot, &sflag)) return;
+    int jfirst = MU_NPT;            // first trial point with N > N_e (N increases with mu)
+    for (int t = MU_NPT - 1; t >= 0; --t) if (2.0 * tot[t] > a.ne) jfirst = t;
+    const double nlo = jfirst == 0 ? lo : lo + jfirst * h;
+    const double nhi = jfirst == MU_NPT ? hi : lo + (jfirst + 1) * h;
+    lo = nlo;
+    hi = nhi;
+    ++iters;
+  }
+  // ---- FP64 check of the coarse bracket ends (FP32 counts may misjudge a
+  // point whose count is within rounding of N_e); widen to the full bracket
+  // on the side that fails
+  if (lo > lo0 || hi < hi0) {
+    double v[2] = {0.0, 0.0};
+    for (long long q = gtid; q < a.npairs; q += gstride) {
+      const double w = pair_weight(a.S, a.NT, q);
+      if (w == 0.0) continue;
+      v[0] += w * fermi((a.lambda[q] - lo) * ikT);
+      v[1] += w * fermi((a.lambda[q] - hi) * ikT);
+    }
+    if (!grid_allreduce<2>(v, a, gen, red, tot, &sflag)) return;
+    if (2.0 * tot[0] > a.ne) lo = lo0;
+    if (2.0 * tot[1] < a.ne) hi = hi0;
+  }
+  // ---- FP64 safeguarded Newton on N(mu) - N_e
   double mu = 0.5 * (lo + hi);
   if (a.guess) {
     const double g = *a.guess;
@@ -154,29 +217,23 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
   double dxold = hi - lo, dx = dxold;
   double Nmu = 0.0;
   bool conv = false;
-  int iters = 0;
   for (int it = 0; it < a.max_iter; ++it) {
-    double n = 0.0, dn = 0.0;
+    double v[2] = {0.0, 0.0};
     for (long long q = gtid; q < a.npairs; q += gstride) {
       const double w = pair_weight(a.S, a.NT, q);
       if (w == 0.0) continue;
-      const double f = fermi((a.lambda[q] - mu) / a.kT);
-      n += w * f;
-      dn += w * f * (1.0 - f);
+      const double f = fermi((a.lambda[q] - mu) * ikT);
+      v[0] += w * f;
+      v[1] += w * f * (1.0 - f);
     }
-    double v[2] = {n, dn};
-    tbk::block_sum<double, 2>(v, red, tot);
-    // generation 0 held the bracket partials; iterations alternate 1, 0, 1, ...
-    double* pg = a.part + (size_t)((it + 1) & 1) * 2 * G;
-    if (threadIdx.x == 0) { pg[2 * blockIdx.x] = tot[0]; pg[2 * blockIdx.x + 1] = tot[1]; }
-    if (!grid_barrier(a.bar, (++gen) * G, a.timeout, a.st, &sflag)) return;
-    sum_partials(pg, G, tot);
+    if (!grid_allreduce<2>(v, a, gen, red, tot, &sflag)) return;
+    ++iters;
     Nmu = 2.0 * tot[0];
-    const double dN = 2.0 * tot[1] / a.kT;
+    const double dN = 2.0 * tot[1] * ikT;
     if (fabs(Nmu - a.ne) <= a.tolN || hi - lo < 1e-13) { conv = true; break; }
     if (Nmu < a.ne) lo = mu; else hi = mu;
-    // safeguarded Newton: bisect when the Newton point leaves the bracket or
-    // the step is not at least halving (Numerical Recipes' rtsafe rule)
+    // bisect when the Newton point leaves the bracket or the step is not at
+    // least halving (Numerical Recipes' rtsafe rule)
     const double fv = Nmu - a.ne;
     const double newton = mu - fv / dN;
     if (!(dN > 0.0) || !(newton > lo && newton < hi) || fabs(2.0 * fv) > fabs(dxold * dN)) {
@@ -188,7 +245,6 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
       dx = fv / dN;
       mu = newton;
     }
-    iters = it + 1;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *a.mu_out = mu;
@@ -214,9 +270,12 @@ struct RhoArgs {
   int* st;
 };
 
+// TA: type of the density-block contraction (FP32 in the mixed path, whose
+// P and S carry FP32 accuracy; FP64 otherwise).  Energy sums stay FP64.
+template <typename TA>
 __global__ void __launch_bounds__(RT) rho_kernel(const RhoArgs a) {
-  __shared__ double fk[tbk::MAX_NT];
-  __shared__ double sk[4 * tbk::MAX_NT];
+  __shared__ TA fk[tbk::MAX_NT];
+  __shared__ TA sk[4 * tbk::MAX_NT];
   __shared__ double red[RT / 32 * 3];
   __shared__ double tot[3];
   const int i = blockIdx.x, NT = a.NT;
@@ -235,8 +294,8 @@ __global__ void __launch_bounds__(RT) rho_kernel(const RhoArgs a) {
       v[1] += w * entropy_term(f);
       v[2] += w * f;
     }
-    fk[k] = f;
-    for (int al = 0; al < 4; ++al) sk[al * NT + k] = Si[al * NT + k];
+    fk[k] = (TA)f;
+    for (int al = 0; al < 4; ++al) sk[al * NT + k] = (TA)Si[al * NT + k];
   }
   tbk::block_sum<double, 3>(v, red, tot);
   if (threadIdx.x == 0) {
@@ -250,9 +309,9 @@ __global__ void __launch_bounds__(RT) rho_kernel(const RhoArgs a) {
   for (int q = threadIdx.x; q < nout; q += RT) {
     const int blk = q >> 4, be = (q >> 2) & 3, al = q & 3;
     const double* pr = a.P + ((base + blk) * 4 + be) * NT;
-    double t = 0.0;
-    for (int k = 0; k < m; ++k) t += pr[k] * fk[k] * sk[al * NT + k];
-    a.rho[(base + blk) * 16 + be * 4 + al] = t;
+    TA t = (TA)0;
+    for (int k = 0; k < m; ++k) t += (TA)pr[k] * fk[k] * sk[al * NT + k];
+    a.rho[(base + blk) * 16 + be * 4 + al] = (double)t;
   }
 }
 
@@ -267,68 +326,79 @@ struct ForceArgs {
   const double* dH;
   const double* rho;
   tb_gsp rep;
+  double* bondf;
   double* F;
   double* per_target;
   int* st;
 };
 
-__global__ void __launch_bounds__(256) force_kernel(const ForceArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// One thread per directed bond k -> j: the bond's Hellmann-Feynman term
+// 2 sum_ab [rho^(k)_{j b,k a} + rho^(j)_{k a,j b}] dH_ab plus the pair
+// repulsion, stored per bond; force_sum_kernel adds each atom's bonds in order.
+__global__ void __launch_bounds__(256) force_bond_kernel(const ForceArgs a) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.h_off[a.n]) return;
+  int lo = 0, hi = a.n;                 // source atom k: h_off[k] <= p < h_off[k+1]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (a.h_off[mid] <= p) lo = mid; else hi = mid;
+  }
+  const int k = lo;
+  const int j = a.h_idx[p];
+  double* out = a.bondf + (size_t)p * 4;
+  int l2 = a.h_off[j], h2 = a.h_off[j + 1];    // position of k in j's list
+  while (l2 < h2) {
+    const int mid = (l2 + h2) >> 1;
+    if (a.h_idx[mid] < k) l2 = mid + 1; else h2 = mid;
+  }
+  if (l2 >= a.h_off[j + 1] || a.h_idx[l2] != k) {
+    tbk::set_status(a.st, TB_ERR_INVALID_ARG, k);
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+    return;
+  }
+  const int q = p - a.h_off[k];
+  const int rq = l2 - a.h_off[j];
+  const double* rk = a.rho + ((size_t)(k + a.h_off[k]) + 1 + q) * 16;    // rho^(k)_{j b, k a} [b][a]
+  const double* rj = a.rho + ((size_t)(j + a.h_off[j]) + 1 + rq) * 16;   // rho^(j)_{k a, j b} [a][b]
+  const double* G = a.dH + (size_t)p * 48;
+  double acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int al = 0; al < 4; ++al)
+#pragma unroll
+    for (int be = 0; be < 4; ++be) {
+      const double rs = rk[be * 4 + al] + rj[al * 4 + be];
+#pragma unroll
+      for (int kk = 0; kk < 3; ++kk) acc[kk] += rs * G[kk * 16 + al * 4 + be];
+    }
+  const double hL = 0.5 * a.L;
+  double d[3];
+#pragma unroll
+  for (int kk = 0; kk < 3; ++kk) {
+    const double x = a.pos[3 * j + kk] - a.pos[3 * k + kk];
+    d[kk] = x > hL ? x - a.L : (x < -hL ? x + a.L : x);
+  }
+  const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  double phi, dphi;
+  tb_gsp_eval(a.rep, r, phi, dphi);
+  const double sc = dphi / r;
+  out[0] = 2.0 * acc[0] + sc * d[0];
+  out[1] = 2.0 * acc[1] + sc * d[1];
+  out[2] = 2.0 * acc[2] + sc * d[2];
+  out[3] = 0.5 * phi;
+}
+
+__global__ void __launch_bounds__(256) force_sum_kernel(const ForceArgs a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.n) return;
-  const int p0 = a.h_off[k], deg = a.h_off[k + 1] - p0;
-  double fx = 0.0, fy = 0.0, fz = 0.0, erep = 0.0;
-  if (lane < deg) {
-    const int p = p0 + lane;
-    const int j = a.h_idx[p];
-    // position of k in j's (ascending) list
-    int lo = a.h_off[j], hi = a.h_off[j + 1];
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (a.h_idx[mid] < k) lo = mid + 1; else hi = mid;
-    }
-    if (lo >= a.h_off[j + 1] || a.h_idx[lo] != k) {
-      tbk::set_status(a.st, TB_ERR_INVALID_ARG, k);
-    } else {
-      const int rq = lo - a.h_off[j];
-      const double* rk = a.rho + ((size_t)(k + p0) + 1 + lane) * 16;   // rho^(k)_{j b, k a} [b][a]
-      const double* rj = a.rho + ((size_t)(j + a.h_off[j]) + 1 + rq) * 16;  // rho^(j)_{k a, j b} [a][b]
-      const double* G = a.dH + (size_t)p * 48;
-      double acc[3] = {0.0, 0.0, 0.0};
+  double f[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int p = a.h_off[k]; p < a.h_off[k + 1]; ++p)
 #pragma unroll
-      for (int al = 0; al < 4; ++al)
-#pragma unroll
-        for (int be = 0; be < 4; ++be) {
-          const double rs = rk[be * 4 + al] + rj[al * 4 + be];
-#pragma unroll
-          for (int kk = 0; kk < 3; ++kk) acc[kk] += rs * G[kk * 16 + al * 4 + be];
-        }
-      double d[3];
-#pragma unroll
-      for (int kk = 0; kk < 3; ++kk) {
-        const double x = a.pos[3 * j + kk] - a.pos[3 * k + kk];
-        d[kk] = x - a.L * rint(x / a.L);
-      }
-      const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-      double phi, dphi;
-      tb_gsp_eval(a.rep, r, phi, dphi);
-      fx = 2.0 * acc[0] + dphi * d[0] / r;
-      fy = 2.0 * acc[1] + dphi * d[1] / r;
-      fz = 2.0 * acc[2] + dphi * d[2] / r;
-      erep = 0.5 * phi;
-    }
-  }
-  fx = tbk::warp_sum(fx);
-  fy = tbk::warp_sum(fy);
-  fz = tbk::warp_sum(fz);
-  erep = tbk::warp_sum(erep);
-  if (lane == 0) {
-    a.F[3 * k] = fx;
-    a.F[3 * k + 1] = fy;
-    a.F[3 * k + 2] = fz;
-    a.per_target[5 * k + 3] = erep;
-    if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) tbk::set_status(a.st, TB_ERR_NONFINITE, k);
-  }
+    for (int c = 0; c < 4; ++c) f[c] += a.bondf[(size_t)p * 4 + c];
+  a.F[3 * k] = f[0];
+  a.F[3 * k + 1] = f[1];
+  a.F[3 * k + 2] = f[2];
+  a.per_target[5 * k + 3] = f[3];
+  if (!(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]))) tbk::set_status(a.st, TB_ERR_NONFINITE, k);
 }
 
 // energies[8] = {E_band, -TS, A, E_rep, E_tot, N(mu), mu, KE}; columns of
@@ -443,11 +513,14 @@ tb_status launch_forces(tb_ctx* c, int n, const double* pos, double L, const int
                         double* F, double* energies, cudaStream_t s) {
   const int NT = 4 * c->p.r;
   RhoArgs ra{NT, h_off, kdim, lambda, S, P, mu, c->p.kT, c->rho, c->per_target, c->d_status};
-  rho_kernel<<<n, RT, 0, s>>>(ra);
+  if (c->p.prec == TB_PREC_MIXED) rho_kernel<float><<<n, RT, 0, s>>>(ra);
+  else rho_kernel<double><<<n, RT, 0, s>>>(ra);
   TB_CUDA_TRY(cudaGetLastError());
-  ForceArgs fa{n, pos, L, h_off, h_idx, dHblk, c->rho, tb_repulsion_gsp(c->p), F,
+  ForceArgs fa{n, pos, L, h_off, h_idx, dHblk, c->rho, tb_repulsion_gsp(c->p), c->bondf, F,
                c->per_target, c->d_status};
-  force_kernel<<<(int)(((long long)n * 32 + 255) / 256), 256, 0, s>>>(fa);
+  force_bond_kernel<<<(int)(((long long)n * c->p.max_hnbr + 255) / 256), 256, 0, s>>>(fa);
+  TB_CUDA_TRY(cudaGetLastError());
+  force_sum_kernel<<<(n + 255) / 256, 256, 0, s>>>(fa);
   TB_CUDA_TRY(cudaGetLastError());
   energy_reduce_kernel<<<1, 1024, 0, s>>>(n, c->per_target, mu, energies, 0);
   TB_CUDA_TRY(cudaGetLastError());

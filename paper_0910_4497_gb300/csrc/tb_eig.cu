@@ -156,7 +156,9 @@ __global__ void __launch_bounds__(EW * 32) eig_ql_kernel(const EigArgs a) {
   for (int x = lane; x < m; x += 32) tn = fmaxf(tn, fabsf(d[x]) + fabsf(e[x]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) tn = fmaxf(tn, __shfl_xor_sync(0xffffffffu, tn, o));
-  const float tol = 1.2e-7f * tn;
+  // deflate an off-diagonal once it is a few FP32 ulps of ||T||: below that the
+  // rotations only churn rounding noise
+  const float tol = 4.8e-7f * tn;
   bool failed = false;
   for (int l = 0; l < m; ++l) {
     int iter = 0;

@@ -6,7 +6,7 @@
 //   p_i(g) p_j(h) = l_g l_h (Vpps - Vppp) + delta_gh Vppp,
 // each times the distance scaling s(r).  The gradient block is
 //   dt/dd_k = s'(r) l_k M(l) + s(r) dM/dd_k,  dl_g/dd_k = (delta_gk - l_g l_k)/r.
-// One warp per atom, one lane per bond (max_hnbr <= 32).
+// One thread per bond; its source atom is found by binary search in h_off.
 #include "tb_internal.cuh"
 #include "tb_model.cuh"
 
@@ -21,18 +21,21 @@ assemble_kernel(int n, const double* __restrict__ pos, double L,
                 const int* __restrict__ h_off, const int* __restrict__ h_idx,
                 tb_gsp g, SK sk, double* __restrict__ Hblk, double* __restrict__ dHblk,
                 float* __restrict__ Hmir, int* st) {
-  const int lane = threadIdx.x & 31;
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (i >= n) return;
-  const int p0 = h_off[i], deg = h_off[i + 1] - p0;
-  if (lane >= deg) return;
-  const int pidx = p0 + lane;
+  const int pidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pidx >= h_off[n]) return;
+  int lo = 0, hi = n;                 // source atom: h_off[i] <= pidx < h_off[i+1]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (h_off[mid] <= pidx) lo = mid; else hi = mid;
+  }
+  const int i = lo;
   const int j = h_idx[pidx];
+  const double hL = 0.5 * L;
   double d[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    double x = pos[3 * j + k] - pos[3 * i + k];
-    d[k] = x - L * rint(x / L);
+    const double x = pos[3 * j + k] - pos[3 * i + k];
+    d[k] = x > hL ? x - L : (x < -hL ? x + L : x);
   }
   const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
   if (!(r > 0.0)) {
@@ -89,7 +92,7 @@ tb_status launch_assemble(tb_ctx* c, int n, const double* pos, double L,
   const tb_params& p = c->p;
   SK sk{p.Vss, p.Vsp, p.Vpps, p.Vppp};
   const int threads = 256;
-  const int grid = (int)(((long long)n * 32 + threads - 1) / threads);
+  const int grid = (int)(((long long)n * p.max_hnbr + threads - 1) / threads);
   assemble_kernel<<<grid, threads, 0, s>>>(n, pos, L, h_off, h_idx, tb_hopping_gsp(p),
                                            sk, Hblk, dHblk, Hmir, c->d_status);
   TB_CUDA_TRY(cudaGetLastError());

@@ -51,6 +51,61 @@ __device__ __forceinline__ void block_sum(T (&v)[M], T* red, T* out) {
   __syncthreads();
 }
 
+// Sum 16 per-lane values over the warp with a butterfly that halves the
+// number of live values at every step (16 shuffles instead of 80).  On return
+// lanes with (lane & 1) == 0 hold the total of value index (lane >> 1).
+template <typename T>
+__device__ __forceinline__ T warp_reduce16(const T (&v)[16], int lane) {
+  T a8[8];
+  const bool h16 = lane & 16;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const T send = h16 ? v[j] : v[8 + j];
+    const T keep = h16 ? v[8 + j] : v[j];
+    a8[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  T a4[4];
+  const bool h8 = lane & 8;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const T send = h8 ? a8[j] : a8[4 + j];
+    const T keep = h8 ? a8[4 + j] : a8[j];
+    a4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  T a2[2];
+  const bool h4 = lane & 4;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const T send = h4 ? a4[j] : a4[2 + j];
+    const T keep = h4 ? a4[2 + j] : a4[j];
+    a2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  const bool h2 = lane & 2;
+  const T a1 = (h2 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? a2[0] : a2[1], 2);
+  return a1 + __shfl_xor_sync(0xffffffffu, a1, 1);
+}
+
+// Block reduction of M <= 16 values per thread through the butterfly above:
+// same contract as block_sum (red needs nwarps*16 entries).
+template <typename T, int M>
+__device__ __forceinline__ void block_sum16(const T (&v)[M], T* red, T* out) {
+  static_assert(M <= 16, "at most 16 values");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  T p[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) p[q] = q < M ? v[q] : T(0);
+  const T t = warp_reduce16(p, lane);
+  if ((lane & 1) == 0 && (lane >> 1) < M) red[warp * 16 + (lane >> 1)] = t;
+  __syncthreads();
+  if (threadIdx.x < M) {
+    T s = 0;
+    for (int w = 0; w < nw; ++w) s += red[w * 16 + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
 }  // namespace tbk
 
 struct tb_ctx {
@@ -76,7 +131,8 @@ struct tb_ctx {
   unsigned int* bar = nullptr;       // barrier counter
   double* mu_state = nullptr;        // 4 doubles
   double* rho = nullptr;             // n*(1+max_hnbr)*16
-  double* per_target = nullptr;      // n * 4
+  double* per_target = nullptr;      // n * 5
+  double* bondf = nullptr;           // n*max_hnbr*4: per-bond force and half repulsion
   double* dscratch = nullptr;        // eig refinement scratch
   // MD-owned buffers
   int *h_off = nullptr, *h_idx = nullptr, *c_off = nullptr, *c_idx = nullptr;

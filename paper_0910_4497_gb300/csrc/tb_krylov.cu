@@ -64,40 +64,6 @@ __device__ __forceinline__ vec4<TV> ldg4(const TV* p) {
   return r;
 }
 
-// Sum 16 per-lane values over the warp with a butterfly that halves the
-// number of live values at every step (16 shuffles instead of 80).  On return
-// lanes with (lane & 1) == 0 hold the total of value index (lane >> 1).
-template <typename TV>
-__device__ __forceinline__ TV warp_reduce16(TV (&v)[16], int lane) {
-  TV a8[8];
-  const bool h16 = lane & 16;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const TV send = h16 ? v[j] : v[8 + j];
-    const TV keep = h16 ? v[8 + j] : v[j];
-    a8[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-  TV a4[4];
-  const bool h8 = lane & 8;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const TV send = h8 ? a8[j] : a8[4 + j];
-    const TV keep = h8 ? a8[4 + j] : a8[j];
-    a4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-  TV a2[2];
-  const bool h4 = lane & 4;
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const TV send = h4 ? a4[j] : a4[2 + j];
-    const TV keep = h4 ? a4[2 + j] : a4[j];
-    a2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  }
-  const bool h2 = lane & 2;
-  TV a1 = (h2 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? a2[0] : a2[1], 2);
-  return a1 + __shfl_xor_sync(0xffffffffu, a1, 1);
-}
-
 template <typename TV>
 struct KryArgs {
   int n, r, max_cluster, max_hnbr, reorth_passes;
@@ -347,6 +313,9 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
       // ---- classical Gram-Schmidt against V_1..V_k (pass 0 yields A_k); on
       // the last step only A_k is needed
       const int passes = (k == r - 1) ? 1 : a.reorth_passes;
+      TV g[10];                             // Gram partials of the final W
+#pragma unroll
+      for (int q = 0; q < 10; ++q) g[q] = (TV)0;
       for (int pass = 0; pass < passes; ++pass) {
         const int b0 = (k == r - 1) ? k : 0;
         const int nb = k + 1 - b0;
@@ -367,7 +336,7 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
 #pragma unroll
               for (int c = 0; c < 4; ++c) acc[ii * 4 + c] += v.v[ii] * x.v[c];
           }
-          const TV tot = warp_reduce16(acc, lane);
+          const TV tot = tbk::warp_reduce16(acc, lane);
           if ((lane & 1) == 0) Cp[w * 16 + (lane >> 1)] = tot;
         }
         __syncthreads();
@@ -384,6 +353,7 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
               0.5 * ((double)Cc[k * 16 + ii * 4 + c] + (double)Cc[k * 16 + c * 4 + ii]);
         }
         if (k == r - 1) break;
+        const bool last = pass == passes - 1;
         for (int row = tid; row < D; row += KT) {
           vec4<TV> x = ld4(W + row * 4);
           for (int b = 0; b <= k; ++b) {
@@ -397,8 +367,15 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
             }
           }
           st4(W + row * 4, x);
+          if (last) {                       // Gram matrix of the orthogonalised W
+            int q = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int e = c; e < 4; ++e) g[q++] += x.v[c] * x.v[e];
+          }
         }
-        __syncthreads();
+        if (!last) __syncthreads();         // the Gram reduction below synchronises
       }
       if (k == r - 1) break;
       // ---- in-block QR: W = V_{k+1} B_k.  Cholesky QR twice; the MGS path
@@ -406,18 +383,7 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
       TV* Vn = V + (size_t)(k + 1) * Dmax * 4;
       int chol_state = 0;   // 1: first factor refused (W untouched); 2: second refused
       for (int cq = 0; cq < 2; ++cq) {
-        TV g[10];
-#pragma unroll
-        for (int q = 0; q < 10; ++q) g[q] = (TV)0;
-        for (int row = tid; row < D; row += KT) {
-          const vec4<TV> x = ld4(W + row * 4);
-          int q = 0;
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int e = c; e < 4; ++e) g[q++] += x.v[c] * x.v[e];
-        }
-        tbk::block_sum<TV, 10>(g, red, Gs);
+        tbk::block_sum16<TV, 10>(g, red, Gs);
         TV G[16];
         {
           int q = 0;
@@ -434,6 +400,8 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
         }
         triinv4(R, Ri);
         TV* dst = cq == 0 ? W : Vn;
+#pragma unroll
+        for (int q = 0; q < 10; ++q) g[q] = (TV)0;
         for (int row = tid; row < D; row += KT) {
           const vec4<TV> x = ld4(W + row * 4);
           vec4<TV> y;
@@ -445,6 +413,13 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
             y.v[c] = t;
           }
           st4(dst + row * 4, y);
+          if (cq == 0) {                    // Gram matrix for the second factor
+            int q = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int e = c; e < 4; ++e) g[q++] += y.v[c] * y.v[e];
+          }
         }
         if (tid == 0) {
           if (cq == 0) {
@@ -463,7 +438,7 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
             flags[FL_ACT] = 0xF;
           }
         }
-        __syncthreads();
+        if (cq == 1) __syncthreads();       // cq == 0: the next reduction synchronises
       }
       if (chol_state != 0) {
         if (warp == 0) {

@@ -5,7 +5,8 @@
 // An FP32 minimum-image distance with a 0.01 A margin prefilters candidates;
 // membership is decided by the FP64 test (each operation separately rounded,
 // no FMA), which makes the lists bit-exact:
-//   d = x_j - x_i;  d -= L * rint(d / L);  r2 = (dx*dx + dy*dy) + dz*dz <= R*R.
+//   d = x_j - x_i;  d -= L if d > L/2;  d += L if d < -L/2;
+//   r2 = (dx*dx + dy*dy) + dz*dz <= R*R.
 // Lists are compacted with warp ballots, so they come out in ascending j.
 #include "tb_internal.cuh"
 
@@ -24,9 +25,9 @@ __global__ void pos_to_f32_kernel(int n, const double* __restrict__ pos, double 
   posf[i] = make_float4((float)x, (float)y, (float)z, 0.f);
 }
 
-__device__ __forceinline__ double min_image_rn(double d, double L) {
-  double q = rint(__ddiv_rn(d, L));
-  return __dsub_rn(d, __dmul_rn(L, q));
+// Nearest periodic image of a separation d in (-L, L).
+__device__ __forceinline__ double min_image_rn(double d, double L, double h) {
+  return d > h ? __dsub_rn(d, L) : (d < -h ? __dadd_rn(d, L) : d);
 }
 
 // MODE 0: count (writes hcnt/ccnt); MODE 1: fill the CSR lists.
@@ -72,9 +73,10 @@ nbr_kernel(int n, const double* __restrict__ pos, const float4* __restrict__ pos
         dz -= Lf * rintf(dz * invLf);
         float r2f = dx * dx + dy * dy + dz * dz;
         if (r2f <= Rc_pre2 || r2f <= Rh_pre2) {
-          double ex = min_image_rn(__dsub_rn(pos[3 * j], xi), L);
-          double ey = min_image_rn(__dsub_rn(pos[3 * j + 1], yi), L);
-          double ez = min_image_rn(__dsub_rn(pos[3 * j + 2], zi), L);
+          const double hL = 0.5 * L;
+          double ex = min_image_rn(__dsub_rn(pos[3 * j], xi), L, hL);
+          double ey = min_image_rn(__dsub_rn(pos[3 * j + 1], yi), L, hL);
+          double ez = min_image_rn(__dsub_rn(pos[3 * j + 2], zi), L, hL);
           double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)),
                                 __dmul_rn(ez, ez));
           in_h = r2 <= R2h;

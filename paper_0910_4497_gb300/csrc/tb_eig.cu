@@ -5,12 +5,13 @@
 // FP64 arithmetic on this GPU runs at ~1/70 of the FP32 rate with ~70-cycle
 // latency, so a serial FP64 tridiagonal QL would dominate the whole force
 // evaluation.  The eigensolve is therefore split:
-//   1. eig_ql_kernel (one warp per target, FP32): Householder reduction of the
-//      active part of T to tridiagonal form with the reflections accumulated,
-//      then implicit QL with shifts (Bowdler, Martin, Reinsch & Wilkinson,
-//      1968) accumulating the rotations.  Every lane runs the scalar
-//      recurrence (identical values), lane 0 stores it, and each lane applies
-//      the rotations to its own rows of the eigenvector matrix.
+//   1. eig_tri_kernel (one warp per target, FP32): Householder reduction of
+//      the active part of T to tridiagonal form; eigenvalues by Sturm-sequence
+//      bisection, each lane owning its own eigenvalues; eigenvectors by
+//      inverse iteration (tridiagonal LU with partial pivoting, three solves),
+//      lane-parallel, with Gram-Schmidt inside clusters of eigenvalues closer
+//      than 1e-3 ||T|| after every solve (the scheme of LAPACK's stein);
+//      back-transformation through the stored reflections.
 //   2. eig_finish_kernel (one CTA per target):
 //      - TB_PREC_MIXED: T itself comes from FP32 sweeps, so the FP32
 //        eigenpairs are kept (an FP64 refinement could not add accuracy);
@@ -24,7 +25,7 @@
 
 namespace {
 
-constexpr int EW = 4;              // warps (targets) per CTA in the QL kernel
+constexpr int EW = 4;              // warps (targets) per CTA in the eigensolver
 constexpr int FT = 128;            // threads per CTA in the finishing kernel
 
 struct EigArgs {
@@ -37,25 +38,96 @@ struct EigArgs {
   int* st;
 };
 
-__host__ __device__ inline int pitch_of(int NT) { return NT + 1; }
+// Row pitch of the per-warp matrices: a multiple of 4 (float4 rows) whose
+// stride in banks keeps 8 consecutive rows' 16-byte accesses conflict-free.
+__host__ __device__ inline int pitch_of(int NT) { return NT + 4; }
 
-__host__ __device__ inline size_t ql_smem_per_warp(int NT) {
-  // Z (NT x (NT+1) floats: the matrix, then the Householder vectors, then the
-  // eigenvectors), v, q, d, e (NT floats), act (NT ints)
-  return sizeof(float) * ((size_t)NT * pitch_of(NT) + 4 * NT) + sizeof(int) * NT;
+__host__ __device__ inline size_t eig_smem_per_warp(int NT) {
+  // H (Householder vectors), Y (eigenvectors), v and q padded to NT + 4 for
+  // float4 reads past the active size, d, e, e2, lam (NT floats), act
+  return sizeof(float) * (2 * (size_t)NT * pitch_of(NT) + 2 * (NT + 4) + 4 * NT) +
+         sizeof(int) * NT;
 }
 
-__global__ void __launch_bounds__(EW * 32) eig_ql_kernel(const EigArgs a) {
+// Number of eigenvalues of the symmetric tridiagonal (d, e2 = e^2) below x
+// (Sturm sequence of the LDL^T pivots; tiny pivots are replaced by -pivmin).
+__device__ __forceinline__ int sturm_count(const float* d, const float* e2, int m, float x,
+                                           float pivmin) {
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  int cnt = q < 0.f;
+  for (int i = 1; i < m; ++i) {
+    q = d[i] - x - __fdividef(e2[i - 1], q);
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += q < 0.f;
+  }
+  return cnt;
+}
+
+// Tridiagonal LU with partial pivoting of (T - lambda I) (rows swapped when the
+// subdiagonal exceeds the pivot): U has diagonals u0, u1, u2; mult/piv hold
+// the eliminations.  Solves overwrite y with (T - lambda I)^{-1} y.
+struct TriLU {
+  float u0[tbk::MAX_NT], u1[tbk::MAX_NT], u2[tbk::MAX_NT], mult[tbk::MAX_NT];
+  unsigned long long piv;
+};
+
+__device__ __forceinline__ void trilu_factor(TriLU& f, const float* d, const float* e, int m,
+                                             float lam, float tiny) {
+  float cd = d[0] - lam, cs = m > 1 ? e[0] : 0.f, cs2 = 0.f;
+  f.piv = 0ull;
+  for (int i = 0; i + 1 < m; ++i) {
+    const float sub = e[i], nd = d[i + 1] - lam, ns = (i + 2 < m) ? e[i + 1] : 0.f;
+    if (fabsf(cd) >= fabsf(sub)) {
+      const float piv = fabsf(cd) < tiny ? (cd < 0.f ? -tiny : tiny) : cd;
+      const float l = sub / piv;
+      f.u0[i] = piv; f.u1[i] = cs; f.u2[i] = cs2; f.mult[i] = l;
+      cd = nd - l * cs;
+      cs = ns - l * cs2;
+      cs2 = 0.f;
+    } else {
+      const float l = cd / sub;
+      f.u0[i] = sub; f.u1[i] = nd; f.u2[i] = ns; f.mult[i] = l;
+      f.piv |= 1ull << i;
+      cd = cs - l * nd;
+      cs = cs2 - l * ns;
+      cs2 = 0.f;
+    }
+  }
+  f.u0[m - 1] = fabsf(cd) < tiny ? (cd < 0.f ? -tiny : tiny) : cd;
+  f.u1[m - 1] = 0.f;
+  f.u2[m - 1] = 0.f;
+}
+
+__device__ __forceinline__ void trilu_solve(const TriLU& f, float* y, int m) {
+  for (int i = 0; i + 1 < m; ++i) {          // apply P and L^{-1}
+    float a = y[i], b = y[i + 1];
+    if ((f.piv >> i) & 1ull) { const float t = a; a = b; b = t; }
+    y[i] = a;
+    y[i + 1] = b - f.mult[i] * a;
+  }
+  for (int i = m - 1; i >= 0; --i) {         // U^{-1}
+    float t = y[i];
+    if (i + 1 < m) t -= f.u1[i] * y[i + 1];
+    if (i + 2 < m) t -= f.u2[i] * y[i + 2];
+    y[i] = t / f.u0[i];
+  }
+}
+
+__global__ void __launch_bounds__(EW * 32) eig_tri_kernel(const EigArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int NT = a.NT, PT = pitch_of(NT);
-  unsigned char* base = smem + warp * ql_smem_per_warp(NT);
-  float* Z = reinterpret_cast<float*>(base);
-  float* vv = Z + NT * PT;
-  float* qq = vv + NT;
-  float* d = qq + NT;
+  unsigned char* base = smem + warp * eig_smem_per_warp(NT);
+  float* H = reinterpret_cast<float*>(base);
+  float* Y = H + NT * PT;
+  float* vv = Y + NT * PT;
+  float* qq = vv + NT + 4;
+  float* d = qq + NT + 4;
   float* e = d + NT;
-  int* act = reinterpret_cast<int*>(e + NT);
+  float* e2 = e + NT;
+  float* lam = e2 + NT;
+  int* act = reinterpret_cast<int*>(lam + NT);
   const int i = blockIdx.x * EW + warp;
   if (i >= a.n) return;
 
@@ -66,152 +138,186 @@ __global__ void __launch_bounds__(EW * 32) eig_ql_kernel(const EigArgs a) {
   __syncwarp();
   const double* Ti = a.T + (size_t)i * NT * NT;
   for (int x = 0; x < m; ++x)
-    for (int y = lane; y < m; y += 32) Z[x * PT + y] = (float)Ti[act[x] * NT + act[y]];
+    for (int y = lane; y < PT; y += 32)
+      H[x * PT + y] = y < m ? (float)Ti[act[x] * NT + act[y]] : 0.f;
+  for (int y = lane; y < NT + 4; y += 32) { vv[y] = 0.f; qq[y] = 0.f; }
   __syncwarp();
 
   // ---- Householder reduction to tridiagonal form.  Step j zeroes column j
-  // below the subdiagonal with H_j = I - 2 v v^T (v supported on rows > j) and
-  // stores v in that column; each lane owns rows x = lane, lane + 32.
+  // below the subdiagonal with I - 2 v v^T (v supported on rows > j) and keeps
+  // v in that column; lane owns rows x = lane, lane + 32.  Row updates run
+  // over float4 chunks from the aligned chunk holding column j + 1 (the extra
+  // columns get a zero update because v and q vanish there).
   for (int j = 0; j + 2 < m; ++j) {
     float xs = 0.f;
     for (int x = lane; x < m; x += 32)
-      if (x > j) xs += Z[x * PT + j] * Z[x * PT + j];
+      if (x > j) xs += H[x * PT + j] * H[x * PT + j];
     const float sig = tbk::warp_sum(xs);
-    const float x0 = Z[(j + 1) * PT + j];
+    const float x0 = H[(j + 1) * PT + j];
     __syncwarp();
     if (sig - x0 * x0 <= 1e-30f * (sig + 1e-30f) || sig == 0.f) {
       if (lane == 0) e[j] = x0;
       for (int x = lane; x < m; x += 32)
-        if (x > j) Z[x * PT + j] = 0.f;      // identity reflection
+        if (x > j) H[x * PT + j] = 0.f;      // identity reflection
       __syncwarp();
       continue;
     }
     const float alpha = x0 >= 0.f ? -sqrtf(sig) : sqrtf(sig);
     const float inv = rsqrtf(2.f * (sig - x0 * alpha));
     for (int x = lane; x < m; x += 32)
-      vv[x] = x <= j ? 0.f : (x == j + 1 ? (x0 - alpha) : Z[x * PT + j]) * inv;
+      vv[x] = x <= j ? 0.f : (x == j + 1 ? (x0 - alpha) : H[x * PT + j]) * inv;
     __syncwarp();
+    const int c0 = (j + 1) & ~3;
     float kp = 0.f;
     for (int x = lane; x < m; x += 32) {
       float p = 0.f;
-      if (x > j)
-        for (int l = j + 1; l < m; ++l) p += Z[x * PT + l] * vv[l];
+      if (x > j) {
+        const float* row = H + x * PT;
+        for (int l = c0; l < m; l += 4) {
+          const float4 h4 = *reinterpret_cast<const float4*>(row + l);
+          const float4 v4 = *reinterpret_cast<const float4*>(vv + l);
+          p += h4.x * v4.x + h4.y * v4.y + h4.z * v4.z + h4.w * v4.w;
+        }
+      }
       qq[x] = p;
       kp += p * vv[x];
     }
     const float K = tbk::warp_sum(kp);
+    __syncwarp();
     for (int x = lane; x < m; x += 32) qq[x] -= K * vv[x];
     __syncwarp();
     for (int x = lane; x < m; x += 32) {
       if (x > j) {
-        const float vx = vv[x], qx = qq[x];
-        for (int l = j + 1; l < m; ++l) Z[x * PT + l] -= 2.f * (vx * qq[l] + qx * vv[l]);
-        Z[x * PT + j] = vx;                  // keep v_j in column j
+        const float vx = 2.f * vv[x], qx = 2.f * qq[x];
+        float* row = H + x * PT;
+        for (int l = c0; l < m; l += 4) {
+          float4 h4 = *reinterpret_cast<float4*>(row + l);
+          const float4 v4 = *reinterpret_cast<const float4*>(vv + l);
+          const float4 q4 = *reinterpret_cast<const float4*>(qq + l);
+          h4.x -= vx * q4.x + qx * v4.x;
+          h4.y -= vx * q4.y + qx * v4.y;
+          h4.z -= vx * q4.z + qx * v4.z;
+          h4.w -= vx * q4.w + qx * v4.w;
+          *reinterpret_cast<float4*>(row + l) = h4;
+        }
       }
     }
+    __syncwarp();
+    for (int x = lane; x < m; x += 32)
+      if (x > j) H[x * PT + j] = vv[x];      // keep v_j in column j
     if (lane == 0) e[j] = alpha;
+    for (int x = lane; x < NT + 4; x += 32) { vv[x] = 0.f; qq[x] = 0.f; }
     __syncwarp();
   }
-  for (int x = lane; x < m; x += 32) d[x] = Z[x * PT + x];
+  for (int x = lane; x < m; x += 32) d[x] = H[x * PT + x];
   if (lane == 0) {
-    if (m >= 2) e[m - 2] = Z[(m - 1) * PT + (m - 2)];
+    if (m >= 2) e[m - 2] = H[(m - 1) * PT + (m - 2)];
     if (m >= 1) e[m - 1] = 0.f;
   }
   __syncwarp();
-  // ---- accumulate Q = H_0 H_1 ... H_{m-3} in place, last reflection first;
-  // lanes own columns l = lane, lane + 32.
-  // Invariant: before applying H_j, the block of rows and columns > j holds
-  // H_{j+1} ... H_{m-3} restricted to those indices; entries left of that block
-  // still hold the reflection vectors.  Start from the trailing identity.
-  if (lane == 0) {
-    const int t0 = m >= 2 ? m - 2 : 0;
-    for (int x = t0; x < m; ++x)
-      for (int y = t0; y < m; ++y) Z[x * PT + y] = (x == y) ? 1.f : 0.f;
+  float gl = 1e30f, gu = -1e30f, emax = 0.f;
+  for (int x = lane; x < m; x += 32) {
+    e2[x] = e[x] * e[x];
+    const float rad = fabsf(e[x]) + (x > 0 ? fabsf(e[x - 1]) : 0.f);
+    gl = fminf(gl, d[x] - rad);
+    gu = fmaxf(gu, d[x] + rad);
+    emax = fmaxf(emax, e[x] * e[x]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    gl = fminf(gl, __shfl_xor_sync(0xffffffffu, gl, o));
+    gu = fmaxf(gu, __shfl_xor_sync(0xffffffffu, gu, o));
+    emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
   }
   __syncwarp();
-  for (int j = m - 3; j >= 0; --j) {
-    for (int x = lane; x < m; x += 32) vv[x] = x > j ? Z[x * PT + j] : 0.f;
-    __syncwarp();
-    for (int l = lane; l < m; l += 32) {
-      if (l > j) {
-        float sl = 0.f;
-        for (int y = j + 1; y < m; ++y) sl += vv[y] * Z[y * PT + l];
-        sl *= 2.f;
-        for (int y = j + 1; y < m; ++y) Z[y * PT + l] -= sl * vv[y];
-      }
+  const float tnorm = fmaxf(fabsf(gl), fabsf(gu));
+  const float pivmin = fmaxf(1e-30f, 1.2e-7f * 1.2e-7f * emax);
+  gl -= 2.4e-7f * tnorm + pivmin;
+  gu += 2.4e-7f * tnorm + pivmin;
+
+  // ---- eigenvalues by bisection: lane owns indices k = lane and lane + 32
+  {
+    const int k0 = lane, k1 = lane + 32;
+    float a0 = gl, b0 = gu, a1 = gl, b1 = gu;
+    for (int it = 0; it < 64; ++it) {
+      const bool go0 = k0 < m && (b0 - a0) > 2.4e-7f * fmaxf(fabsf(a0), fabsf(b0)) + pivmin;
+      const bool go1 = k1 < m && (b1 - a1) > 2.4e-7f * fmaxf(fabsf(a1), fabsf(b1)) + pivmin;
+      if (!__any_sync(0xffffffffu, go0 || go1)) break;
+      const float m0 = 0.5f * (a0 + b0), m1 = 0.5f * (a1 + b1);
+      if (go0) { if (sturm_count(d, e2, m, m0, pivmin) > k0) b0 = m0; else a0 = m0; }
+      if (go1) { if (sturm_count(d, e2, m, m1, pivmin) > k1) b1 = m1; else a1 = m1; }
     }
-    __syncwarp();
-    for (int x = lane; x < m; x += 32) {
-      if (x >= j) {
-        Z[x * PT + j] = (x == j) ? 1.f : 0.f;
-        Z[j * PT + x] = (x == j) ? 1.f : 0.f;
-      }
+    if (k0 < m) lam[k0] = 0.5f * (a0 + b0);
+    if (k1 < m) lam[k1] = 0.5f * (a1 + b1);
+  }
+  __syncwarp();
+
+  // ---- eigenvectors by inverse iteration (lane-parallel), Gram-Schmidt
+  // inside clusters of close eigenvalues between iterations
+  const float gtol = 1e-3f * tnorm;
+  const float tiny = 1.2e-7f * tnorm + 1e-30f;
+  for (int half = 0; half < 2; ++half) {
+    const int k = lane + 32 * half;
+    if (!__any_sync(0xffffffffu, k < m)) break;
+    TriLU f;
+    float y[tbk::MAX_NT];
+    if (k < m) {
+      trilu_factor(f, d, e, m, lam[k], tiny);
+      for (int x = 0; x < m; ++x) y[x] = 1.f + 0.25f * (float)(((x * 7 + k * 13) % 17) - 8) / 8.f;
     }
-    __syncwarp();
+    for (int it = 0; it < 3; ++it) {
+      if (k < m) {
+        trilu_solve(f, y, m);
+        float nn = 0.f;
+        for (int x = 0; x < m; ++x) nn += y[x] * y[x];
+        const float s = rsqrtf(fmaxf(nn, 1e-30f));
+        for (int x = 0; x < m; ++x) Y[x * PT + k] = y[x] * s;
+      }
+      __syncwarp();
+      // clusters: runs of consecutive eigenvalues closer than gtol; members
+      // are orthogonalised in index order against the earlier ones
+      const int kb = 32 * half, ke = min(m, kb + 32);
+      for (int kk = 1; kk < m; ++kk) {
+        if (!(lam[kk] - lam[kk - 1] < gtol)) continue;
+        if (kk < kb || kk >= ke) continue;
+        int first = kk - 1;
+        while (first > 0 && lam[first] - lam[first - 1] < gtol) --first;
+        for (int kp2 = first; kp2 < kk; ++kp2) {
+          float dt = 0.f;
+          for (int x = lane; x < m; x += 32) dt += Y[x * PT + kk] * Y[x * PT + kp2];
+          dt = tbk::warp_sum(dt);
+          for (int x = lane; x < m; x += 32) Y[x * PT + kk] -= dt * Y[x * PT + kp2];
+          __syncwarp();
+        }
+        float nn = 0.f;
+        for (int x = lane; x < m; x += 32) nn += Y[x * PT + kk] * Y[x * PT + kk];
+        nn = tbk::warp_sum(nn);
+        const float s = rsqrtf(fmaxf(nn, 1e-30f));
+        for (int x = lane; x < m; x += 32) Y[x * PT + kk] *= s;
+        __syncwarp();
+      }
+      if (k < m)
+        for (int x = 0; x < m; ++x) y[x] = Y[x * PT + k];
+      __syncwarp();
+    }
   }
 
-  // ---- implicit QL with shifts on (d, e); rotations applied to the rows of Z.
-  // Rotation (c, s) from f, g via one reciprocal square root.
-  float tn = 0.f;
-  for (int x = lane; x < m; x += 32) tn = fmaxf(tn, fabsf(d[x]) + fabsf(e[x]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) tn = fmaxf(tn, __shfl_xor_sync(0xffffffffu, tn, o));
-  // deflate an off-diagonal once it is a few FP32 ulps of ||T||: below that the
-  // rotations only churn rounding noise
-  const float tol = 4.8e-7f * tn;
-  bool failed = false;
-  for (int l = 0; l < m; ++l) {
-    int iter = 0;
-    while (true) {
-      int mm = l;
-      while (mm < m - 1 && fabsf(e[mm]) > tol) ++mm;
-      if (mm == l) break;
-      if (++iter > 60) { failed = true; break; }
-      const float el = e[l], dl = d[l];
-      float g = (d[l + 1] - dl) / (2.f * el);
-      float rr = sqrtf(g * g + 1.f);
-      g = d[mm] - dl + el / (g + (g >= 0.f ? rr : -rr));
-      float s = 1.f, c = 1.f, p = 0.f;
-      bool early = false;
-      for (int ii = mm - 1; ii >= l; --ii) {
-        const float ei = e[ii], di = d[ii], di1 = d[ii + 1];
-        const float f = s * ei, b = c * ei;
-        const float h = f * f + g * g;
-        __syncwarp();
-        if (h == 0.f) {
-          if (lane == 0) { e[ii + 1] = 0.f; d[ii + 1] = di1 - p; e[mm] = 0.f; }
-          early = true;
-          break;
-        }
-        const float rinv = rsqrtf(h);
-        if (lane == 0) e[ii + 1] = h * rinv;
-        s = f * rinv;
-        c = g * rinv;
-        g = di1 - p;
-        rr = (di - g) * s + 2.f * c * b;
-        p = s * rr;
-        if (lane == 0) d[ii + 1] = g + p;
-        g = c * rr - b;
-        for (int x = lane; x < m; x += 32) {
-          const float z1 = Z[x * PT + ii + 1], z0 = Z[x * PT + ii];
-          Z[x * PT + ii + 1] = s * z0 + c * z1;
-          Z[x * PT + ii] = c * z0 - s * z1;
-        }
-      }
-      __syncwarp();
-      if (!early) {
-        if (lane == 0) { d[l] = d[l] - p; e[l] = g; e[mm] = 0.f; }
-      }
-      __syncwarp();
+  // ---- back-transformation: eigenvectors of T = H_0 ... H_{m-3} Y; lane
+  // owns columns k = lane, lane + 32
+  for (int j = m - 3; j >= 0; --j) {
+    for (int k = lane; k < m; k += 32) {
+      float t = 0.f;
+      for (int x = j + 1; x < m; ++x) t += H[x * PT + j] * Y[x * PT + k];
+      t *= 2.f;
+      for (int x = j + 1; x < m; ++x) Y[x * PT + k] -= t * H[x * PT + j];
     }
-    if (failed) break;
   }
-  if (failed && lane == 0) tbk::set_status(a.st, TB_ERR_NO_CONVERGENCE, i);
+  __syncwarp();
   float* lf = a.lamf + (size_t)i * NT;
   float* zo = a.Zf + (size_t)i * NT * NT;
-  for (int x = lane; x < m; x += 32) lf[x] = d[x];
+  for (int x = lane; x < m; x += 32) lf[x] = lam[x];
   for (int x = 0; x < m; ++x)
-    for (int y = lane; y < m; y += 32) zo[x * NT + y] = Z[x * PT + y];
+    for (int y = lane; y < m; y += 32) zo[x * NT + y] = Y[x * PT + y];
   if (lane == 0) a.kdim[i] = m;
 }
 
@@ -421,8 +527,8 @@ __global__ void __launch_bounds__(FT) eig_finish_kernel(const FinArgs<TV> a) {
 
 tb_status eig_configure(tb_ctx* c) {
   const int NT = 4 * c->p.r;
-  c->eig_smem = EW * ql_smem_per_warp(NT);
-  TB_CUDA_TRY(cudaFuncSetAttribute(eig_ql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  c->eig_smem = EW * eig_smem_per_warp(NT);
+  TB_CUDA_TRY(cudaFuncSetAttribute(eig_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)c->eig_smem));
   if (c->p.prec == TB_PREC_FP64) {
     c->fin_smem = fin_smem_bytes<double>(NT);
@@ -441,7 +547,7 @@ tb_status launch_eig(tb_ctx* c, int n, const int* h_off, double* lambda, double*
   if (n <= 0) return TB_OK;
   const int NT = 4 * c->p.r;
   EigArgs ea{n, NT, c->T, c->colmask, c->Zf, c->lamf, kdim, c->d_status};
-  eig_ql_kernel<<<(n + EW - 1) / EW, EW * 32, c->eig_smem, s>>>(ea);
+  eig_tri_kernel<<<(n + EW - 1) / EW, EW * 32, c->eig_smem, s>>>(ea);
   TB_CUDA_TRY(cudaGetLastError());
   if (c->p.prec == TB_PREC_FP64) {
     FinArgs<double> fa{n, NT, c->T, c->colmask, c->Zf, c->lamf,

@@ -256,7 +256,8 @@ tb_status tb_krylov_density(tb_ctx* c, int n, const int* c_off, const int* c_idx
   if (c->p.prec == TB_PREC_FP64 && !Hblk) return TB_ERR_INVALID_ARG;
   if (c->p.prec == TB_PREC_MIXED && !Hmirror) return TB_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  TB_STAGE(c, 2, s, launch_krylov(c, n, c_off, c_idx, h_off, h_idx, Hblk, Hmirror, s));
+  TB_STAGE(c, 2, s, launch_krylov(c, n, c_off, c_idx, h_off, h_idx, Hblk, Hmirror, lambda, S,
+                                  P, kdim, s));
   TB_STAGE(c, 3, s, launch_eig(c, n, h_off, lambda, S, P, kdim, s));
   return TB_OK;
 }
@@ -302,8 +303,8 @@ tb_status tb_md_step(tb_ctx* c, int n, double* pos, double* vel, double* F, doub
   if ((st = launch_assemble(c, n, pos, L, c->h_off, c->h_idx, c->Hblk, c->dHblk,
                             c->p.prec == TB_PREC_MIXED ? c->Hmir : nullptr, s)) != TB_OK)
     return st;
-  if ((st = launch_krylov(c, n, c->c_off, c->c_idx, c->h_off, c->h_idx, c->Hblk, c->Hmir, s)) !=
-      TB_OK)
+  if ((st = launch_krylov(c, n, c->c_off, c->c_idx, c->h_off, c->h_idx, c->Hblk, c->Hmir,
+                          c->lambda, c->S, c->P, c->kdim, s)) != TB_OK)
     return st;
   if ((st = launch_eig(c, n, c->h_off, c->lambda, c->S, c->P, c->kdim, s)) != TB_OK) return st;
   if ((st = launch_mu(c, n, c->lambda, c->S, 4.0 * n, c->mu, c->mu, c->ncount, s)) != TB_OK)

@@ -78,6 +78,8 @@ struct MuArgs {
   unsigned* bar;
   int max_iter;
   long long timeout;
+  long long per_block; // pairs handled (and staged in shared memory) per block
+  int staged;          // 1: (lambda, w) of the block's pairs live in shared memory
   int* st;
 };
 
@@ -89,6 +91,25 @@ __device__ __forceinline__ double pair_weight(const double* S, int NT, long long
   const int k = (int)(q - i * NT);
   const double* s = S + (size_t)i * 4 * NT + k;
   return s[0] * s[0] + s[NT] * s[NT] + s[2 * NT] * s[2 * NT] + s[3 * NT] * s[3 * NT];
+}
+
+// f(x) = 1/(1+e^x) and f(1-f).  Beyond |x| = 15 the small one of f and 1-f
+// is below 3.1e-7 and is taken from the FP32 exponential (absolute error
+// ~3e-14); inside, FP64 throughout.
+__device__ __forceinline__ void occupation(double x, double& f, double& g) {
+  if (x > 15.0) {
+    const float e = __expf((float)fminf(-(float)x, 0.f));
+    f = (double)e / (1.0 + (double)e);
+    g = f * (1.0 - f);
+  } else if (x < -15.0) {
+    const float e = __expf((float)fmaxf((float)x, -200.f));
+    const double t = (double)e / (1.0 + (double)e);
+    f = 1.0 - t;
+    g = t * f;
+  } else {
+    f = fermi(x);
+    g = f * (1.0 - f);
+  }
 }
 
 // Every block publishes M partials in generation buffer `gen`, passes the grid
@@ -111,7 +132,6 @@ __device__ bool grid_allreduce(const double (&v)[M], const MuArgs& a, unsigned& 
       for (int g = sub; g < G; g += 16) sum += pg[g * MU_PART + m];
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    __syncthreads();
     if (m < M && sub == 0) tot[m] = sum;
   }
   __syncthreads();
@@ -119,45 +139,58 @@ __device__ bool grid_allreduce(const double (&v)[M], const MuArgs& a, unsigned& 
 }
 
 __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
+  extern __shared__ __align__(16) unsigned char mu_smem[];
+  double2* pairs = reinterpret_cast<double2*>(mu_smem);   // (lambda, w)
   __shared__ double red[MT / 32 * 16];
   __shared__ double tot[16];
   __shared__ int sflag;
   const int G = gridDim.x;
-  const long long gtid = (long long)blockIdx.x * MT + threadIdx.x;
-  const long long gstride = (long long)G * MT;
   const double ikT = 1.0 / a.kT;
+  const long long q0 = (long long)blockIdx.x * a.per_block;
+  const long long q1 = min(a.npairs, q0 + a.per_block);
+  const int nloc = (int)max(0ll, q1 - q0);
   unsigned gen = 0;
-  // ---- bracket: [min lam - 40 kT, max lam + 40 kT] over pairs with weight
-  double lmin = 1e300, lmax = -1e300;
-  for (long long q = gtid; q < a.npairs; q += gstride) {
-    if (pair_weight(a.S, a.NT, q) > 0.0) {
-      const double l = a.lambda[q];
-      lmin = fmin(lmin, l);
-      lmax = fmax(lmax, l);
+  // pair accessor: shared-memory copy when staged, else recomputed from global
+  auto get = [&](int t, double& l, double& w) {
+    if (a.staged) {
+      const double2 v = pairs[t];
+      l = v.x;
+      w = v.y;
+    } else {
+      l = a.lambda[q0 + t];
+      w = pair_weight(a.S, a.NT, q0 + t);
     }
+  };
+  double lmin = 1e300, lmax = -1e300;
+  for (int t = threadIdx.x; t < nloc; t += MT) {
+    const double l = a.lambda[q0 + t], w = pair_weight(a.S, a.NT, q0 + t);
+    if (a.staged) pairs[t] = make_double2(l, w);
+    if (w > 0.0) { lmin = fmin(lmin, l); lmax = fmax(lmax, l); }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    lmin = fmin(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
-    lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-  }
-  if ((threadIdx.x & 31) == 0) { red[2 * (threadIdx.x >> 5)] = lmin; red[2 * (threadIdx.x >> 5) + 1] = lmax; }
-  __syncthreads();
+  // ---- bracket: [min lam - 40 kT, max lam + 40 kT] over pairs with weight
   {
+    double v[2] = {lmin, -lmax};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v[0] = fmin(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
+      v[1] = fmin(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
+    }
+    if ((threadIdx.x & 31) == 0) { red[2 * (threadIdx.x >> 5)] = v[0]; red[2 * (threadIdx.x >> 5) + 1] = v[1]; }
+    __syncthreads();
     double* pg = a.part + (size_t)(gen & 1) * G * MU_PART;
     if (threadIdx.x == 0) {
-      double m0 = 1e300, m1 = -1e300;
-      for (int w = 0; w < MT / 32; ++w) { m0 = fmin(m0, red[2 * w]); m1 = fmax(m1, red[2 * w + 1]); }
+      double m0 = 1e300, m1 = 1e300;
+      for (int w = 0; w < MT / 32; ++w) { m0 = fmin(m0, red[2 * w]); m1 = fmin(m1, red[2 * w + 1]); }
       pg[blockIdx.x * MU_PART] = m0;
       pg[blockIdx.x * MU_PART + 1] = m1;
     }
     ++gen;
     if (!grid_barrier(a.bar, gen * G, a.timeout, a.st, &sflag)) return;
     if (threadIdx.x == 0) {
-      double m0 = 1e300, m1 = -1e300;
-      for (int g = 0; g < G; ++g) { m0 = fmin(m0, pg[g * MU_PART]); m1 = fmax(m1, pg[g * MU_PART + 1]); }
+      double m0 = 1e300, m1 = 1e300;
+      for (int g = 0; g < G; ++g) { m0 = fmin(m0, pg[g * MU_PART]); m1 = fmin(m1, pg[g * MU_PART + 1]); }
       tot[0] = m0;
-      tot[1] = m1;
+      tot[1] = -m1;
     }
     __syncthreads();
   }
@@ -171,44 +204,33 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
     const double h = (hi - lo) / (MU_NPT + 1);
 #pragma unroll
     for (int t = 0; t < MU_NPT; ++t) cnt[t] = 0.f;
-    for (long long q = gtid; q < a.npairs; q += gstride) {
-      const double w = pair_weight(a.S, a.NT, q);
+    const float dx = (float)(h * ikT);
+    for (int t = threadIdx.x; t < nloc; t += MT) {
+      double l, w;
+      get(t, l, w);
       if (w == 0.0) continue;
-      const float x0 = (float)((a.lambda[q] - lo) * ikT), dx = (float)(h * ikT);
-      const float wf = (float)w;
+      const float x0 = (float)((l - lo) * ikT), wf = (float)w;
 #pragma unroll
-      for (int t = 0; t < MU_NPT; ++t) {
-        const float x = fminf(fmaxf(x0 - (t + 1) * dx, -80.f), 80.f);
-        cnt[t] += wf / (1.f + __expf(x));
+      for (int u = 0; u < MU_NPT; ++u) {
+        const float x = fminf(fmaxf(x0 - (u + 1) * dx, -80.f), 80.f);
+        cnt[u] += __fdividef(wf, 1.f + __expf(x));
       }
     }
 #pragma unroll
-    for (int t = 0; t < MU_NPT; ++t) v[t] = (double)cnt[t];
+    for (int u = 0; u < MU_NPT; ++u) v[u] = (double)cnt[u];
     if (!grid_allreduce<MU_NPT>(v, a, gen, red, tot, &sflag)) return;
     int jfirst = MU_NPT;            // first trial point with N > N_e (N increases with mu)
-    for (int t = MU_NPT - 1; t >= 0; --t) if (2.0 * tot[t] > a.ne) jfirst = t;
+    for (int u = MU_NPT - 1; u >= 0; --u) if (2.0 * tot[u] > a.ne) jfirst = u;
     const double nlo = jfirst == 0 ? lo : lo + jfirst * h;
     const double nhi = jfirst == MU_NPT ? hi : lo + (jfirst + 1) * h;
     lo = nlo;
     hi = nhi;
     ++iters;
   }
-  // ---- FP64 check of the coarse bracket ends (FP32 counts may misjudge a
-  // point whose count is within rounding of N_e); widen to the full bracket
-  // on the side that fails
-  if (lo > lo0 || hi < hi0) {
-    double v[2] = {0.0, 0.0};
-    for (long long q = gtid; q < a.npairs; q += gstride) {
-      const double w = pair_weight(a.S, a.NT, q);
-      if (w == 0.0) continue;
-      v[0] += w * fermi((a.lambda[q] - lo) * ikT);
-      v[1] += w * fermi((a.lambda[q] - hi) * ikT);
-    }
-    if (!grid_allreduce<2>(v, a, gen, red, tot, &sflag)) return;
-    if (2.0 * tot[0] > a.ne) lo = lo0;
-    if (2.0 * tot[1] < a.ne) hi = hi0;
-  }
-  // ---- FP64 safeguarded Newton on N(mu) - N_e
+  // ---- FP64 safeguarded Newton on N(mu) - N_e.  The first pass also counts
+  // at the coarse bracket ends (FP32 counts may misjudge a point whose count
+  // is within rounding of N_e) and widens the bracket on a side that fails.
+  const bool check = lo > lo0 || hi < hi0;
   double mu = 0.5 * (lo + hi);
   if (a.guess) {
     const double g = *a.guess;
@@ -218,20 +240,34 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
   double Nmu = 0.0;
   bool conv = false;
   for (int it = 0; it < a.max_iter; ++it) {
-    double v[2] = {0.0, 0.0};
-    for (long long q = gtid; q < a.npairs; q += gstride) {
-      const double w = pair_weight(a.S, a.NT, q);
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    const bool ends = it == 0 && check;
+    for (int t = threadIdx.x; t < nloc; t += MT) {
+      double l, w;
+      get(t, l, w);
       if (w == 0.0) continue;
-      const double f = fermi((a.lambda[q] - mu) * ikT);
+      double f, g;
+      occupation((l - mu) * ikT, f, g);
       v[0] += w * f;
-      v[1] += w * f * (1.0 - f);
+      v[1] += w * g;
+      if (ends) {
+        double f2, g2;
+        occupation((l - lo) * ikT, f2, g2);
+        v[2] += w * f2;
+        occupation((l - hi) * ikT, f2, g2);
+        v[3] += w * f2;
+      }
     }
-    if (!grid_allreduce<2>(v, a, gen, red, tot, &sflag)) return;
+    if (!grid_allreduce<4>(v, a, gen, red, tot, &sflag)) return;
     ++iters;
     Nmu = 2.0 * tot[0];
     const double dN = 2.0 * tot[1] * ikT;
+    if (ends) {
+      if (2.0 * tot[2] > a.ne) lo = lo0;
+      if (2.0 * tot[3] < a.ne) hi = hi0;
+    }
     if (fabs(Nmu - a.ne) <= a.tolN || hi - lo < 1e-13) { conv = true; break; }
-    if (Nmu < a.ne) lo = mu; else hi = mu;
+    if (Nmu < a.ne) lo = fmax(lo, mu); else hi = fmin(hi, mu);
     // bisect when the Newton point leaves the bracket or the step is not at
     // least halving (Numerical Recipes' rtsafe rule)
     const double fv = Nmu - a.ne;
@@ -461,8 +497,14 @@ __global__ void kick_kernel(int n, double* vel, const double* F, double dt, doub
 }  // namespace
 
 tb_status mu_configure(tb_ctx* c) {
+  int dev = 0, max_smem = 0;
+  TB_CUDA_TRY(cudaGetDevice(&dev));
+  TB_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  c->mu_smem_max = max_smem - 8 * 1024;       // leave room for the static arrays
+  TB_CUDA_TRY(cudaFuncSetAttribute(mu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   c->mu_smem_max));
   int occ = 0;
-  TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mu_kernel, MT, 0));
+  TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mu_kernel, MT, c->mu_smem_max));
   if (occ < 1) return TB_ERR_CUDA;
   c->mu_grid = c->num_sms;   // one block per SM: co-resident, short final sums
   return TB_OK;
@@ -489,14 +531,16 @@ tb_status launch_mu(tb_ctx* c, int n, const double* lambda, const double* S,
   a.max_iter = c->p.mu_max_iter;
   a.timeout = c->p.timeout_cycles;
   a.st = c->d_status;
-  long long want = (a.npairs + MT * 4 - 1) / (MT * 4);
-  int grid = (int)(want < c->mu_grid ? want : c->mu_grid);
-  if (grid < 1) grid = 1;
+  // one block per SM; each block stages its contiguous share of the pairs
+  const int grid = c->mu_grid;
+  a.per_block = (a.npairs + grid - 1) / grid;
+  const size_t stage = (size_t)a.per_block * sizeof(double2);
+  a.staged = stage <= (size_t)c->mu_smem_max ? 1 : 0;
   TB_CUDA_TRY(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), s));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(MT);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = a.staged ? stage : 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

@@ -13,8 +13,8 @@
 //      than 1e-3 ||T|| after every solve (the scheme of LAPACK's stein);
 //      back-transformation through the stored reflections.
 //   2. eig_finish_kernel (one CTA per target):
-//      - TB_PREC_MIXED: T itself comes from FP32 sweeps, so the FP32
-//        eigenpairs are kept (an FP64 refinement could not add accuracy);
+//      - TB_PREC_MIXED: a first-order Loewdin step makes the FP32 eigenvectors
+//        orthonormal, then FP64 Rayleigh quotients give the eigenvalues;
 //      - TB_PREC_FP64: two FP64 steps of the Ogita-Aishima refinement
 //        (Japan J. Indust. Appl. Math. 35 (2018)): R = I - X^T X,
 //        S = X^T T X, lambda_i = S_ii/(1 - R_ii), E_ij = (S_ij + lambda_j R_ij)
@@ -343,7 +343,7 @@ __host__ __device__ inline size_t fin_smem_bytes(int NT) {
   const size_t PT = NT + 1;
   size_t b = sizeof(int) * 4 * NT + sizeof(double) * 4 * NT;   // act, rank, lo, hi; lam, red
   if (sizeof(TV) == sizeof(float)) {
-    b += sizeof(float) * NT * PT;           // X
+    b += sizeof(float) * NT * PT * 3;       // X, E, scratch
   } else {
     b += sizeof(double) * NT * PT * 5;      // T, X, W1, Smat, Rmat
   }
@@ -385,9 +385,39 @@ __global__ void __launch_bounds__(FT) eig_finish_kernel(const FinArgs<TV> a) {
   __syncthreads();
 
   if (sizeof(TV) == sizeof(float)) {
-    // T comes from FP32 sweeps and is FP32-accurate: the FP32 QL eigenvalues
-    // already carry the full accuracy available.
-    for (int k = tid; k < m; k += FT) lam[k] = (double)a.lamf[(size_t)i * NT + k];
+    // Loewdin orthonormalisation X <- X (I - E/2), E = X^T X - I (inverse
+    // iteration leaves vectors of nearby eigenvalues orthogonal only to
+    // ~eps ||T|| / gap), then FP64 Rayleigh quotients on the final vectors.
+    float* Xf = reinterpret_cast<float*>(X);
+    float* E = Xf + NT * PT;
+    float* X2 = E + NT * PT;
+    for (int q = tid; q < m * m; q += FT) {
+      const int x = q / m, y = q - x * m;
+      float t = 0.f;
+      for (int l = 0; l < m; ++l) t += Xf[l * PT + x] * Xf[l * PT + y];
+      E[x * PT + y] = 0.5f * (t - (x == y ? 1.f : 0.f));
+    }
+    __syncthreads();
+    for (int q = tid; q < m * m; q += FT) {
+      const int x = q / m, k = q - x * m;
+      float t = Xf[x * PT + k];
+      for (int l = 0; l < m; ++l) t -= Xf[x * PT + l] * E[l * PT + k];
+      X2[x * PT + k] = t;
+    }
+    __syncthreads();
+    for (int q = tid; q < m * m; q += FT) Xf[(q / m) * PT + q % m] = X2[(q / m) * PT + q % m];
+    __syncthreads();
+    const double* Ti = a.T + (size_t)i * NT * NT;
+    for (int k = tid; k < m; k += FT) {
+      double num = 0.0, den = 0.0;
+      for (int x = 0; x < m; ++x) {
+        double t = 0.0;
+        for (int y = blo[x]; y < bhi[x]; ++y) t += Ti[act[x] * NT + act[y]] * (double)Xf[y * PT + k];
+        num += (double)Xf[x * PT + k] * t;
+        den += (double)Xf[x * PT + k] * (double)Xf[x * PT + k];
+      }
+      lam[k] = num / den;
+    }
     __syncthreads();
   } else {
     const double* Ti = a.T + (size_t)i * NT * NT;
@@ -546,9 +576,12 @@ tb_status launch_eig(tb_ctx* c, int n, const int* h_off, double* lambda, double*
                      double* P, int* kdim, cudaStream_t s) {
   if (n <= 0) return TB_OK;
   const int NT = 4 * c->p.r;
-  EigArgs ea{n, NT, c->T, c->colmask, c->Zf, c->lamf, kdim, c->d_status};
-  eig_tri_kernel<<<(n + EW - 1) / EW, EW * 32, c->eig_smem, s>>>(ea);
-  TB_CUDA_TRY(cudaGetLastError());
+  if (c->kry_fused && c->p.prec == TB_PREC_MIXED) return TB_OK;   // done in the Krylov kernel
+  if (!c->kry_fused) {
+    EigArgs ea{n, NT, c->T, c->colmask, c->Zf, c->lamf, kdim, c->d_status};
+    eig_tri_kernel<<<(n + EW - 1) / EW, EW * 32, c->eig_smem, s>>>(ea);
+    TB_CUDA_TRY(cudaGetLastError());
+  }
   if (c->p.prec == TB_PREC_FP64) {
     FinArgs<double> fa{n, NT, c->T, c->colmask, c->Zf, c->lamf,
                        reinterpret_cast<const double*>(c->Y), h_off, lambda, S, P, c->d_status};

@@ -145,10 +145,12 @@ struct tb_ctx {
   int kry_grid = 0;
   size_t kry_smem = 0;
   bool kry_vsmem = false;
+  bool kry_fused = false;           // projected eigensolve inside the Krylov kernel
   int eig_grid = 0;
   size_t eig_smem = 0;
   size_t fin_smem = 0;
   int mu_grid = 0;
+  int mu_smem_max = 0;
   // stage timing events (tb_profile_enable)
   bool profiling = false;
   bool prof_ran[6] = {false, false, false, false, false, false};
@@ -167,7 +169,8 @@ tb_status launch_assemble(tb_ctx* c, int n, const double* pos, double L,
 tb_status krylov_configure(tb_ctx* c);
 tb_status launch_krylov(tb_ctx* c, int n, const int* c_off, const int* c_idx,
                         const int* h_off, const int* h_idx, const double* Hblk,
-                        const float* Hmir, cudaStream_t s);
+                        const float* Hmir, double* lambda, double* S, double* P, int* kdim,
+                        cudaStream_t s);
 tb_status eig_configure(tb_ctx* c);
 tb_status launch_eig(tb_ctx* c, int n, const int* h_off, double* lambda, double* S,
                      double* P, int* kdim, cudaStream_t s);

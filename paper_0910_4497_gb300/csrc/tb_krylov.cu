@@ -27,6 +27,7 @@
 // otherwise in a per-CTA slot of global memory (L2-resident).
 // Layout of the basis: block b occupies Dmax*4 values, row-major [row][4].
 #include "tb_internal.cuh"
+#include "tb_eig_tail.cuh"
 
 namespace {
 
@@ -36,6 +37,7 @@ constexpr int KW = KT / 32;
 // active-column bits of the newest block.
 constexpr int FL_MASK = KW;
 constexpr int FL_ACT = KW + 2;
+constexpr int FL_OK = KW + 3;
 
 template <typename TV>
 struct alignas(4 * sizeof(TV)) vec4 {
@@ -79,6 +81,13 @@ struct KryArgs {
   TV* Vg;
   int2* lent;
   int* st;
+  // fused eigensolve outputs
+  float* lamf;
+  float* Zf;
+  double* lambda;
+  double* S;
+  double* P;
+  int* kdim;
 };
 
 __device__ __forceinline__ int find_slot(const int* cl, int nc, int b) {
@@ -104,7 +113,7 @@ __host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, bool vs
   if (vsmem) b += align32(sizeof(TV) * Dmax * 4 * r); // basis
   b += align32(sizeof(TV) * 16 * np);                 // projection partials
   b += align32(sizeof(TV) * 16 * r);                  // projection coefficients
-  b += align32(sizeof(TV) * 16 * 2);                  // B_{k-1}, Gram
+  b += align32(sizeof(TV) * 16 * 4);                  // B_{k-1}, Gram, R, R^{-1}
   b += align32(sizeof(double) * 16 * 2);              // B_k, first Cholesky factor
   b += align32(sizeof(TV) * 16 * KW);                 // reduction scratch
   b += align32(sizeof(int) * 16);                     // flags
@@ -125,9 +134,10 @@ __device__ __forceinline__ bool chol4(const TV (&g)[16], TV (&R)[16], TV rel, do
 #pragma unroll
     for (int j = 0; j < c; ++j) d -= R[j * 4 + c] * R[j * 4 + c];
     if (!(d > rel * g[c * 4 + c]) || !(d > (TV)(abs_tol * abs_tol))) ok = false;
-    const TV rc = sqrt(d > (TV)0 ? d : (TV)1);
+    const TV dd = d > (TV)0 ? d : (TV)1;
+    const TV inv = (TV)rsqrt(dd);
+    const TV rc = dd * inv;
     R[c * 4 + c] = rc;
-    const TV inv = (TV)1 / rc;
 #pragma unroll
     for (int e = c + 1; e < 4; ++e) {
       TV t = g[c * 4 + e];
@@ -152,12 +162,12 @@ __device__ __forceinline__ void triinv4(const TV (&R)[16], TV (&X)[16]) {
       TV t = (TV)0;
 #pragma unroll
       for (int j = rr + 1; j <= c; ++j) t += R[rr * 4 + j] * X[j * 4 + c];
-      X[rr * 4 + c] = -t / R[rr * 4 + rr];
+      X[rr * 4 + c] = -t * X[rr * 4 + rr];   // X[rr][rr] = 1/R[rr][rr], set earlier
     }
   }
 }
 
-template <typename TV, bool VSMEM>
+template <typename TV, bool VSMEM, bool FUSED>
 __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
   extern __shared__ __align__(32) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -177,7 +187,9 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
   TV* Cp = reinterpret_cast<TV*>(smem + off);        off += align32(sizeof(TV) * 16 * np);
   TV* Cc = reinterpret_cast<TV*>(smem + off);        off += align32(sizeof(TV) * 16 * r);
   TV* Bp = reinterpret_cast<TV*>(smem + off);
-  TV* Gs = Bp + 16;                                  off += align32(sizeof(TV) * 32);
+  TV* Gs = Bp + 16;
+  TV* Rsh = Gs + 16;
+  TV* Rish = Rsh + 16;                               off += align32(sizeof(TV) * 64);
   double* Bs = reinterpret_cast<double*>(smem + off);
   double* R1s = Bs + 16;                             off += align32(sizeof(double) * 32);
   TV* red = reinterpret_cast<TV*>(smem + off);       off += align32(sizeof(TV) * 16 * KW);
@@ -286,7 +298,7 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[c] = on * vs.v[c];
         const int e1 = rowptr[s + 1];
-#pragma unroll 2
+#pragma unroll 4
         for (int e = rowptr[s]; e < e1; ++e) {
           const int2 en = lent[e];
           const vec4<TV> h = ldg4(a.H + (size_t)en.y * 16 + al * 4);
@@ -384,21 +396,29 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
       int chol_state = 0;   // 1: first factor refused (W untouched); 2: second refused
       for (int cq = 0; cq < 2; ++cq) {
         tbk::block_sum16<TV, 10>(g, red, Gs);
-        TV G[16];
-        {
+        // one thread factors the Gram matrix and publishes R^{-1} (and R)
+        if (tid == 0) {
+          TV G[16];
           int q = 0;
 #pragma unroll
           for (int c = 0; c < 4; ++c)
 #pragma unroll
             for (int e = c; e < 4; ++e) { G[c * 4 + e] = Gs[q]; G[e * 4 + c] = Gs[q]; ++q; }
+          TV R[16], Ri[16];
+          const bool ok = chol4(G, R, chol_rel, cq == 0 ? chol_abs : 0.0);
+          triinv4(R, Ri);
+#pragma unroll
+          for (int q2 = 0; q2 < 16; ++q2) { Rsh[q2] = R[q2]; Rish[q2] = Ri[q2]; }
+          flags[FL_OK] = ok ? 1 : 0;
         }
-        TV R[16], Ri[16];
-        // every thread factors the same shared Gram matrix: the decision is uniform
-        if (!chol4(G, R, chol_rel, cq == 0 ? chol_abs : 0.0)) {
+        __syncthreads();
+        if (!flags[FL_OK]) {        // uniform: every thread reads the same flag
           chol_state = cq + 1;
           break;
         }
-        triinv4(R, Ri);
+        TV R[16], Ri[16];
+#pragma unroll
+        for (int q2 = 0; q2 < 16; ++q2) { R[q2] = Rsh[q2]; Ri[q2] = Rish[q2]; }
         TV* dst = cq == 0 ? W : Vn;
 #pragma unroll
         for (int q = 0; q < 10; ++q) g[q] = (TV)0;
@@ -546,12 +566,51 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
       }
     }
     __syncthreads();
+    if constexpr (FUSED) {
+      // ---- projected eigensolve in the shared memory the basis occupied
+      const unsigned long long mask =
+          ((unsigned long long)(unsigned)flags[FL_MASK + 1] << 32) | (unsigned)flags[FL_MASK];
+      const tbtail::TailOut o =
+          tbtail::eig_tail<KT>(Ti, mask, NT, reinterpret_cast<float*>(V), a.st, i);
+      const int m = o.m, PU = tbtail::tpitch(NT);
+      if (tid == 0) a.kdim[i] = m;
+      if constexpr (sizeof(TV) == sizeof(double)) {
+        // FP64 path: the FP32 eigenpairs seed the FP64 refinement kernel
+        for (int k = tid; k < m; k += KT) a.lamf[(size_t)i * NT + k] = o.lam[k];
+        for (int q = tid; q < m * m; q += KT) {
+          const int x = q / m, k = q - x * m;
+          a.Zf[(size_t)i * NT * NT + x * NT + k] = o.U[x * PU + k];
+        }
+      } else {
+        // mixed path: spectral record lambda (ascending), S, P = Y[:, act] U
+        double* lo = a.lambda + (size_t)i * NT;
+        for (int k = tid; k < NT; k += KT) lo[k] = k < m ? o.rq[2 * k] / o.rq[2 * k + 1] : 0.0;
+        double* So = a.S + (size_t)i * 4 * NT;
+        for (int q = tid; q < 4 * NT; q += KT) {
+          const int al = q / NT, k = q - al * NT;
+          So[q] = k < m ? (double)o.U[al * PU + k] : 0.0;
+        }
+        const size_t rbase = (size_t)(i + a.h_off[i]) * 4;
+        const int nrows = 4 * (deg + 1);
+        for (int q = tid; q < nrows * NT; q += KT) {
+          const int rr = q / NT, k = q - rr * NT;
+          float t = 0.f;
+          if (k < m) {
+            const TV* yr = a.Y + (rbase + rr) * NT;
+            for (int l = 0; l < m; ++l) t += (float)yr[o.act[l]] * o.U[l * PU + k];
+          }
+          a.P[(rbase + rr) * NT + k] = (double)t;
+        }
+      }
+      __syncthreads();
+    }
   }
 }
 
-template <typename TV, bool VSMEM>
+template <typename TV, bool VSMEM, bool FUSED>
 tb_status launch_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int* h_off,
-                   const int* h_idx, const TV* H, cudaStream_t s) {
+                   const int* h_idx, const TV* H, double* lambda, double* S, double* P,
+                   int* kdim, cudaStream_t s) {
   const tb_params& p = c->p;
   KryArgs<TV> a;
   a.n = n; a.r = p.r; a.max_cluster = p.max_cluster; a.max_hnbr = p.max_hnbr;
@@ -560,25 +619,31 @@ tb_status launch_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const i
   a.c_off = c_off; a.c_idx = c_idx; a.h_off = h_off; a.h_idx = h_idx; a.H = H;
   a.T = c->T; a.Y = reinterpret_cast<TV*>(c->Y); a.colmask = c->colmask;
   a.Vg = reinterpret_cast<TV*>(c->Vg); a.lent = c->lent; a.st = c->d_status;
+  a.lamf = c->lamf; a.Zf = c->Zf; a.lambda = lambda; a.S = S; a.P = P; a.kdim = kdim;
   const int grid = n < c->kry_grid ? n : c->kry_grid;
   if (grid <= 0) return TB_OK;
-  krylov_kernel<TV, VSMEM><<<grid, KT, c->kry_smem, s>>>(a);
+  krylov_kernel<TV, VSMEM, FUSED><<<grid, KT, c->kry_smem, s>>>(a);
   TB_CUDA_TRY(cudaGetLastError());
   return TB_OK;
 }
 
-template <typename TV, bool VSMEM>
+template <typename TV, bool VSMEM, bool FUSED>
 tb_status configure_t(tb_ctx* c, int max_smem) {
   const size_t bytes = kry_smem_bytes<TV>(c->p.r, c->p.max_cluster, VSMEM);
   if ((int)bytes > max_smem) return TB_ERR_CAPACITY;
-  TB_CUDA_TRY(cudaFuncSetAttribute(krylov_kernel<TV, VSMEM>,
+  if (FUSED) {   // the eigensolve workspace must fit where the basis was
+    const size_t basis = sizeof(TV) * 4 * (size_t)c->p.max_cluster * 4 * c->p.r;
+    if (sizeof(float) * tbtail::tail_floats(4 * c->p.r) > basis) return TB_ERR_CAPACITY;
+  }
+  TB_CUDA_TRY(cudaFuncSetAttribute(krylov_kernel<TV, VSMEM, FUSED>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   int occ = 0;
-  TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, krylov_kernel<TV, VSMEM>,
-                                                            KT, bytes));
+  TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &occ, krylov_kernel<TV, VSMEM, FUSED>, KT, bytes));
   if (occ < 1) return TB_ERR_CAPACITY;
   c->kry_smem = bytes;
   c->kry_vsmem = VSMEM;
+  c->kry_fused = FUSED;
   c->kry_grid = c->num_sms * occ;
   return TB_OK;
 }
@@ -596,22 +661,40 @@ tb_status krylov_configure(tb_ctx* c) {
   TB_CUDA_TRY(cudaGetDevice(&dev));
   TB_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const bool force_global = getenv("TB_KRYLOV_BASIS_GLOBAL") != nullptr;
+  const bool no_fuse = getenv("TB_EIG_SEPARATE") != nullptr;
   if (c->p.prec == TB_PREC_FP64) {
-    if (!force_global && configure_t<double, true>(c, max_smem) == TB_OK) return TB_OK;
-    return configure_t<double, false>(c, max_smem);
+    if (!force_global && !no_fuse && configure_t<double, true, true>(c, max_smem) == TB_OK)
+      return TB_OK;
+    if (!force_global && configure_t<double, true, false>(c, max_smem) == TB_OK) return TB_OK;
+    return configure_t<double, false, false>(c, max_smem);
   }
-  if (!force_global && configure_t<float, true>(c, max_smem) == TB_OK) return TB_OK;
-  return configure_t<float, false>(c, max_smem);
+  if (!force_global && !no_fuse && configure_t<float, true, true>(c, max_smem) == TB_OK)
+    return TB_OK;
+  if (!force_global && configure_t<float, true, false>(c, max_smem) == TB_OK) return TB_OK;
+  return configure_t<float, false, false>(c, max_smem);
 }
 
 tb_status launch_krylov(tb_ctx* c, int n, const int* c_off, const int* c_idx,
                         const int* h_off, const int* h_idx, const double* Hblk,
-                        const float* Hmir, cudaStream_t s) {
+                        const float* Hmir, double* lambda, double* S, double* P, int* kdim,
+                        cudaStream_t s) {
   if (c->p.prec == TB_PREC_FP64) {
-    if (c->kry_vsmem) return launch_t<double, true>(c, n, c_off, c_idx, h_off, h_idx, Hblk, s);
-    return launch_t<double, false>(c, n, c_off, c_idx, h_off, h_idx, Hblk, s);
+    if (c->kry_fused)
+      return launch_t<double, true, true>(c, n, c_off, c_idx, h_off, h_idx, Hblk, lambda, S, P,
+                                          kdim, s);
+    if (c->kry_vsmem)
+      return launch_t<double, true, false>(c, n, c_off, c_idx, h_off, h_idx, Hblk, lambda, S,
+                                           P, kdim, s);
+    return launch_t<double, false, false>(c, n, c_off, c_idx, h_off, h_idx, Hblk, lambda, S, P,
+                                          kdim, s);
   }
   if (!Hmir) return TB_ERR_INVALID_ARG;
-  if (c->kry_vsmem) return launch_t<float, true>(c, n, c_off, c_idx, h_off, h_idx, Hmir, s);
-  return launch_t<float, false>(c, n, c_off, c_idx, h_off, h_idx, Hmir, s);
+  if (c->kry_fused)
+    return launch_t<float, true, true>(c, n, c_off, c_idx, h_off, h_idx, Hmir, lambda, S, P,
+                                       kdim, s);
+  if (c->kry_vsmem)
+    return launch_t<float, true, false>(c, n, c_off, c_idx, h_off, h_idx, Hmir, lambda, S, P,
+                                        kdim, s);
+  return launch_t<float, false, false>(c, n, c_off, c_idx, h_off, h_idx, Hmir, lambda, S, P,
+                                       kdim, s);
 }

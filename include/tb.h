@@ -222,6 +222,39 @@ tb_status tb_md_step(tb_ctx* ctx, int n, double* pos, double* vel, double* F,
 tb_status tb_profile_enable(tb_ctx* ctx, int enable);
 tb_status tb_profile_read(tb_ctx* ctx, float* ms);
 
+/*
+ * Allocation-free chemical-potential search.  The paper has no counterpart:
+ * this is a deployment variant of tb_find_mu for callers that may not
+ * allocate device memory (a host runtime that owns all device allocations
+ * through its own pool, or code where a cudaMalloc could synchronise the
+ * device at the wrong time), and therefore cannot create a tb_ctx.
+ * It runs the same search as tb_find_mu with no context: its scratch (partial
+ * sums of at most TB_FIND_MU_STATIC_MAX_BLOCKS blocks, one per SM, a barrier
+ * counter) lives in a fixed 40 KB device array inside the library that every
+ * GPU loading the library keeps until process exit.  No allocation of any kind
+ * happens in the call.
+ *   n, r            atoms and Krylov block order (NT = 4r, 1 <= r <= 16)
+ *   lambda, S       device, as produced by tb_krylov_density
+ *   kT, n_electrons, mu_tol, max_iter   as in tb_params / tb_find_mu
+ *   mu_guess        device, may be NULL
+ *   mu              device out: one double;  n_count: device out, may be NULL
+ *   status          device out: int[2] = {tb_status code, info}, cleared on
+ *                   the stream before the search; read it after the stream
+ *                   has completed (timeouts, non-convergence).
+ * Returns TB_ERR_INVALID_ARG for bad arguments and TB_ERR_CAPACITY when the
+ * device has more SMs than TB_FIND_MU_STATIC_MAX_BLOCKS.
+ * The first call on a device does a one-time set-up there (looks up the
+ * array's device address, sets the kernel's shared-memory limit); make that
+ * first call before any stream capture.  All calls share the one array and it
+ * keeps the last call's contents: calls whose executions overlap on the GPU
+ * race with each other, so order them on one stream or synchronise.
+ */
+#define TB_FIND_MU_STATIC_MAX_BLOCKS 160
+tb_status tb_find_mu_static(int n, int r, const double* lambda, const double* S, double kT,
+                            double n_electrons, double mu_tol, int max_iter,
+                            const double* mu_guess, double* mu, double* n_count, int* status,
+                            void* stream);
+
 /* Library version string (static, host). */
 const char* tb_version(void);
 

@@ -23,7 +23,7 @@ TB_PREC_MIXED = 1
 EXPORTS = ["tb_params_default", "tb_ctx_create", "tb_ctx_destroy", "tb_ctx_reserve",
            "tb_ctx_workspace_bytes", "tb_get_status", "tb_build_neighbors",
            "tb_assemble_H", "tb_krylov_density", "tb_find_mu", "tb_forces", "tb_md_step",
-           "tb_profile_enable", "tb_profile_read", "tb_version"]
+           "tb_profile_enable", "tb_profile_read", "tb_find_mu_static", "tb_version"]
 
 
 class TBParams(ctypes.Structure):
@@ -66,6 +66,7 @@ def load_library(path=LIB_PATH):
         "tb_md_step": [P, I, VP, VP, VP, D, D, D, VP, VP],
         "tb_profile_enable": [P, I],
         "tb_profile_read": [P, ctypes.POINTER(ctypes.c_float)],
+        "tb_find_mu_static": [I, I, VP, VP, D, D, D, I, VP, VP, VP, VP, VP],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -221,6 +222,17 @@ def tb_profile_read(ctx):
     ms = (ctypes.c_float * 6)()
     _check("tb_profile_read", lib().tb_profile_read(ctx, ms))
     return dict(zip(STAGES, list(ms)))
+
+
+def tb_find_mu_static(n, r, lam, S, kT, n_electrons, mu_tol, max_iter, mu_guess, mu,
+                      n_count, status, stream=None):
+    """Allocation-free mu search (no context); status is a device int32[2]."""
+    i32, f64 = torch.int32, torch.float64
+    _check("tb_find_mu_static", lib().tb_find_mu_static(
+        int(n), int(r), _ptr(lam, f64, "lambda"), _ptr(S, f64, "S"), float(kT),
+        float(n_electrons), float(mu_tol), int(max_iter), _ptr(mu_guess, f64, "mu_guess"),
+        _ptr(mu, f64, "mu"), _ptr(n_count, f64, "n_count"), _ptr(status, i32, "status"),
+        _stream(stream)))
 
 
 def tb_version():

@@ -586,3 +586,115 @@ tb_status launch_md_kick(tb_ctx* c, int n, double* vel, const double* F, double 
   TB_CUDA_TRY(cudaGetLastError());
   return TB_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the chemical-potential search.
+//
+// Some callers cannot allocate device memory at all: code running inside a
+// host runtime that owns every allocation (a pre-sized memory pool or arena,
+// or a process where a cudaMalloc would synchronise the device at a bad
+// moment).  They cannot create a tb_ctx either, because tb_ctx_create and
+// tb_ctx_reserve allocate.  tb_find_mu_static gives them the mu search with
+// its scratch (per-block partial sums, the grid-barrier counter and the
+// status word) in this file-scope device array instead of in a context.
+//
+// The array is sized for TB_FIND_MU_STATIC_MAX_BLOCKS blocks of the
+// cooperative search (one block per SM); every GPU that loads the library
+// holds it until the process exits.  All calls share it and it keeps the last
+// call's contents, so the counter and status words are cleared on the stream
+// before each launch; calls whose executions overlap on the GPU race on it.
+namespace {
+
+constexpr int kStaticPartDoubles = 2 * MU_PART * TB_FIND_MU_STATIC_MAX_BLOCKS;
+// [0, kStaticPartDoubles) partial sums; then one 256-byte line holding the
+// barrier counter (word 0) and the status code and info (words 1, 2)
+static __device__ __align__(256) double g_mu_scratch[kStaticPartDoubles + 32];
+
+struct StaticMuDevice {
+  bool ready = false;
+  double* scratch = nullptr;   // device address of g_mu_scratch on this device
+  int sms = 0;
+  int smem_max = 0;
+};
+constexpr int kMaxDevices = 64;
+StaticMuDevice g_static_mu[kMaxDevices];
+
+// One-time set-up on the current device: device address of the scratch array
+// (its name on the host is only a stand-in), SM count and the kernel's
+// shared-memory limit.  Not capturable into a CUDA graph.
+tb_status static_mu_setup(int dev) {
+  StaticMuDevice& d = g_static_mu[dev];
+  if (d.ready) return TB_OK;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_mu_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return TB_ERR_CUDA;
+  }
+  int sms = 0, max_smem = 0;
+  TB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  TB_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int smem = max_smem - 8 * 1024;
+  TB_CUDA_TRY(cudaFuncSetAttribute(mu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  d.scratch = static_cast<double*>(p);
+  d.sms = sms;
+  d.smem_max = smem;
+  d.ready = true;
+  return TB_OK;
+}
+
+}  // namespace
+
+extern "C" tb_status tb_find_mu_static(int n, int r, const double* lambda, const double* S,
+                                       double kT, double n_electrons, double mu_tol,
+                                       int max_iter, const double* mu_guess, double* mu,
+                                       double* n_count, int* status, void* stream) {
+  if (n <= 0 || r < 1 || r > tbk::MAX_R || !lambda || !S || !mu || !status) return TB_ERR_INVALID_ARG;
+  if (!(kT > 0.0) || !(n_electrons > 0.0) || !(mu_tol > 0.0) || max_iter < 1) return TB_ERR_INVALID_ARG;
+  int dev = 0;
+  TB_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return TB_ERR_INVALID_ARG;
+  tb_status st = static_mu_setup(dev);
+  if (st != TB_OK) return st;
+  const StaticMuDevice& d = g_static_mu[dev];
+  // one block per SM, as the context-based search; the array holds partials
+  // for at most TB_FIND_MU_STATIC_MAX_BLOCKS blocks
+  if (d.sms > TB_FIND_MU_STATIC_MAX_BLOCKS) return TB_ERR_CAPACITY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int NT = 4 * r;
+  MuArgs a;
+  a.npairs = (long long)n * NT;
+  a.NT = NT;
+  a.lambda = lambda;
+  a.S = S;
+  a.kT = kT;
+  a.ne = n_electrons;
+  a.tolN = mu_tol * n_electrons;
+  a.guess = mu_guess;
+  a.mu_out = mu;
+  a.ncount_out = n_count;
+  a.iters_out = nullptr;
+  a.part = d.scratch;
+  unsigned* line = reinterpret_cast<unsigned*>(d.scratch + kStaticPartDoubles);
+  a.bar = line;
+  a.max_iter = max_iter;
+  a.timeout = 4000000000LL;
+  a.st = status;
+  const int grid = d.sms;
+  a.per_block = (a.npairs + grid - 1) / grid;
+  const size_t stage = (size_t)a.per_block * sizeof(double2);
+  a.staged = stage <= (size_t)d.smem_max ? 1 : 0;
+  TB_CUDA_TRY(cudaMemsetAsync(line, 0, sizeof(unsigned), s));       // barrier counter
+  TB_CUDA_TRY(cudaMemsetAsync(status, 0, 2 * sizeof(int), s));      // caller's status words
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(MT);
+  cfg.dynamicSmemBytes = a.staged ? stage : 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  TB_CUDA_TRY(cudaLaunchKernelEx(&cfg, mu_kernel, a));
+  return TB_OK;
+}

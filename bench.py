@@ -195,8 +195,10 @@ def kernel_traffic(prec):
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    src = open(os.path.join(ROOT, "paper_0910_4497_gb300", "csrc", "tb_krylov.cu"), "rb").read()
-    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+    h = hashlib.sha256()
+    for rel in rec.get("sources", []):
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    if not rec.get("sources") or rec.get("source_sha256") != h.hexdigest():
         return None
     return rec.get("dram_bytes_per_launch", {}).get(prec)
 

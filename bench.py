@@ -6,7 +6,13 @@ Lanczos, projected eigensolve, mu, density blocks, forces) per step, replayed
 as one CUDA graph.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
-                  [--impl ours|reference]
+                  [--impl ours|reference] [--workload c60_1920|md15360]
+
+--workload md15360 times molecular dynamics instead: the 4x4x4 fcc C60 cell
+of 15360 atoms (a = 12.5 A, cluster cutoff 6.5 A, r = 16), velocity-Verlet
+steps of 0.5 fs from 2000 K Maxwell-Boltzmann velocities, one CUDA graph per
+step; value = atom-steps/s, with the NVE energy drift of the mixed and FP64
+paths over the same steps from the same state.
 
 Prints one JSON line (rank 0).  With --gpus N > 1 (torchrun, one rank per GPU)
 every rank evaluates its own replica of the cell; value = total atoms / max time.
@@ -42,6 +48,8 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reorth-passes", type=int, default=1)
+    ap.add_argument("--workload", default="c60_1920", choices=["c60_1920", "md15360"])
+    ap.add_argument("--no-fp64-compare", action="store_true")
     return ap.parse_args()
 
 
@@ -354,9 +362,229 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
     return 0
 
+# ---------------------------------------------------------------- MD workload
+
+MD_METRIC = "atom-steps/s (15360-atom C60 NVE MD, velocity Verlet, 1 GB300)"
+MD_UNIT = "atom-steps/s"
+MD_INDEX = 4
+
+
+def md_workload():
+    from synth import CONFIGS, fcc_c60_crystal, maxwell_boltzmann_velocities, workload_params
+    from synth.configs import MASS_C_AMU
+    cfg = CONFIGS[MD_INDEX]
+    pos, L, _ = fcc_c60_crystal(cfg["ncell"], cfg["a"], cfg["jitter"], cfg["seed"],
+                                cfg["bridges"])
+    vel = maxwell_boltzmann_velocities(len(pos), cfg["T_init"], MASS_C_AMU, cfg["seed"] + 1)
+    p = workload_params(cfg, defl_tol=1e-9)
+    return cfg, pos, vel, L, p
+
+
+def oracle_md_sample(pos, L, p, n_targets):
+    """Oracle per-target work (cluster H, block Lanczos, eigenpairs, density
+    blocks) of n_targets evenly spaced targets; returns seconds per target."""
+    from oracle.neighbors import neighbor_lists, cluster_lists
+    from oracle.hamiltonian import BondTable
+    from oracle.pipeline import target_record
+    from oracle.density import rho_blocks
+    hl = neighbor_lists(pos, L, p["rm"])
+    cl = cluster_lists(pos, L, p["Rc"])
+    bonds = BondTable(pos, L, hl, p)
+    stride = max(1, len(pos) // n_targets)
+    t0 = time.perf_counter()
+    nt = 0
+    for i in range(0, len(pos), stride):
+        lam, S, P = target_record(bonds, cl[i], hl[i], p["r"], p["defl_tol"])
+        rho_blocks(S, P, lam, 4.5, p["kT"])
+        nt += 1
+    return (time.perf_counter() - t0) / nt, nt
+
+
+def md_trajectory(system, steps, flush, stream, record):
+    """Replay `steps` MD graphs; per-step CUDA-event times and total energies."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    etot = torch.zeros(steps, dtype=torch.float64, device=system.device)
+    for k in range(steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        system.replay()
+        ev[k][1].record(stream)
+        etot[k:k + 1].copy_(system.energies[4:5] + system.energies[7:8])
+        if record:
+            ev[k][1].synchronize()
+    torch.cuda.synchronize(system.device)
+    return [a.elapsed_time(b) for a, b in ev], etot.cpu().numpy()
+
+
+def run_md(args):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    from synth.configs import MASS_C_AMU
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        cfg, pos, vel, L, p = md_workload()
+        t_tgt, nt = oracle_md_sample(pos, L, p, 64)
+        value = 1.0 / t_tgt          # atom-steps/s: one target's work per atom-step
+        line = {"metric": MD_METRIC, "value": value, "unit": MD_UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * t_tgt * len(pos), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "impl": "reference",
+                "config": {"workload": cfg["name"], "n_atoms": len(pos), "l2": "n/a (CPU)"},
+                "cpu_baseline": {"value": value, "unit": MD_UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"per-target oracle work of {nt} evenly spaced "
+                                           f"targets, scaled to one {len(pos)}-atom force "
+                                           f"evaluation per MD step"},
+                "e2e": {"value": value, "unit": MD_UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+    if world > 1:
+        import torch.distributed as dist
+        if rank == 0:
+            __graft_entry__.build()
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        dist.barrier()
+        if rank != 0:
+            __graft_entry__.build()
+    else:
+        __graft_entry__.build()
+        torch.cuda.set_device(local)
+    import paper_0910_4497_gb300 as tb
+
+    cfg, pos, vel, L, p = md_workload()
+    p["reorth_passes"] = args.reorth_passes
+    n = len(pos)
+    dt = cfg["dt_fs"]
+    cpu_base = None
+    if rank == 0 and not args.no_cpu_baseline:
+        t_tgt, nt = oracle_md_sample(pos, L, p, 64)
+        cpu_base = {"value": 1.0 / t_tgt, "unit": MD_UNIT, "cores": 1, "kind": "oracle",
+                    "sample": f"oracle per-target work (cluster H, block Lanczos, eigenpairs, "
+                              f"density blocks) of {nt} evenly spaced targets, "
+                              f"{t_tgt * nt:.1f} s, scaled to {n} targets per MD step"}
+    dev = torch.device("cuda", local)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    def make(prec):
+        s = tb.TBSystem(n, L, p, prec=prec, device=dev)
+        s.set_positions(pos)
+        s.vel.copy_(torch.as_tensor(vel, dtype=torch.float64))
+        s.evaluate()
+        s.capture_md(dt, MASS_C_AMU)
+        return s
+
+    system = make(args.prec)
+    for _ in range(max(args.warmup, 3)):
+        system.replay()
+    torch.cuda.synchronize(dev)
+    system.check()
+    state = [t.clone() for t in (system.pos, system.vel, system.F)]
+
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier()
+    step_ms, etot = md_trajectory(system, args.steps, flush, stream, True)
+    barrier()
+    clk = clocks.stop() if clocks else None
+    system.check()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = t.item()
+    value = world * n * args.steps / (total_ms / 1e3)
+    pos_end = system.pos.clone()
+
+    # ---- end to end: the state goes host -> device and back every step
+    hp = [t.cpu().pin_memory() for t in state]
+    hE = torch.empty(8, dtype=torch.float64).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e2e_ms = 0.0
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0.record(stream)
+        for d, h in zip((system.pos, system.vel, system.F), hp):
+            d.copy_(h, non_blocking=True)
+        system.replay()
+        for d, h in zip((system.pos, system.vel, system.F), hp):
+            h.copy_(d, non_blocking=True)
+        hE.copy_(system.energies, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = t.item()
+    e2e_value = world * n * args.steps / (e2e_ms / 1e3)
+    system.close()
+
+    # ---- the FP64 path over the same steps from the same state
+    fp64 = None
+    if rank == 0 and args.prec != "fp64" and not args.no_fp64_compare:
+        s64 = tb.TBSystem(n, L, p, prec="fp64", device=dev)
+        s64.set_positions(state[0])
+        s64.vel.copy_(state[1])
+        s64.evaluate()
+        s64.capture_md(dt, MASS_C_AMU)
+        ms64, etot64 = md_trajectory(s64, args.steps, flush, stream, True)
+        s64.check()
+        dpos = (s64.pos - pos_end + 0.5 * L).remainder(L) - 0.5 * L
+        fp64 = {"atom_steps_per_s": n * args.steps / (sum(ms64) / 1e3),
+                "ms_per_step": sum(ms64) / args.steps,
+                "energy_drift_eV_per_atom": float((etot64[-1] - etot64[0]) / n),
+                "max_position_diff_vs_mixed_A": float(dpos.abs().max().item())}
+        s64.close()
+
+    if rank == 0:
+        line = {
+            "metric": MD_METRIC, "value": value, "unit": MD_UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.prec == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "n_atoms": n, "a": cfg["a"],
+                       "ncell": cfg["ncell"], "Rc": cfg["Rc"], "krylov_r": cfg["r"],
+                       "kT": cfg["kT"], "dt_fs": dt, "T_init_K": cfg["T_init"],
+                       "precision": args.prec,
+                       "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "graph": "one CUDA graph per MD step",
+                       "reorth_passes": args.reorth_passes},
+            "e2e": {"value": e2e_value, "unit": MD_UNIT, "h2d_bytes_per_step": 3 * n * 3 * 8,
+                    "d2h_bytes_per_step": 3 * n * 3 * 8 + 8 * 8},
+            "cpu_baseline": cpu_base,
+            "clocks": clk,
+            "gpu_launches": 14 * args.steps,
+            "nve": {"energy_drift_eV_per_atom": float((etot[-1] - etot[0]) / n),
+                    "energy_span_eV_per_atom": float((etot.max() - etot.min()) / n),
+                    "fp64_path": fp64},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
 
 def main():
     args = parse()
+    if args.workload == "md15360":
+        return run_md(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

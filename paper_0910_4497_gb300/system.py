@@ -101,6 +101,25 @@ class TBSystem:
         self.graph = g
         return g
 
+    def capture_md(self, dt_fs, mass_amu):
+        """CUDA graph of one velocity-Verlet step (self.F must hold the force at
+        self.pos); replay() then advances the trajectory by one step."""
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        saved = [t.clone() for t in (self.pos, self.vel, self.F, self.mu)]
+        with torch.cuda.stream(s):
+            self.md_step(dt_fs, mass_amu, s)
+        torch.cuda.current_stream(self.device).wait_stream(s)
+        torch.cuda.synchronize(self.device)
+        self.check()
+        for t, v in zip((self.pos, self.vel, self.F, self.mu), saved):
+            t.copy_(v)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.md_step(dt_fs, mass_amu)
+        self.graph = g
+        return g
+
     def replay(self):
         self.graph.replay()
 

@@ -17,10 +17,12 @@ following the paper's steps in order:
   (``krylov``),
 * Sec. 2: density matrix rho = sum_m |m> f(e_m) <m| and the force
   <F_i> = Tr[rho F_i] (``density``),
-* plus the velocity-Verlet step of the MD workload (``md``) and the exact
-  O(N^3) whole-cell diagonalisation used as a limit check (``exact``).
+* plus the velocity-Verlet step of the MD workload (``md``), the exact
+  O(N^3) whole-cell diagonalisation used as a limit check (``exact``), and
+  the exact gradient of the truncated local free energy at r = r_min
+  (``local_exact``).
 
 Library primitives used as single steps: numpy matmul, numpy.linalg.eigh.
 """
-from . import model, neighbors, hamiltonian, krylov, density, md, exact  # noqa: F401
+from . import model, neighbors, hamiltonian, krylov, density, md, exact, local_exact  # noqa: F401
 from .pipeline import force_evaluation, OracleResult  # noqa: F401

@@ -6,13 +6,21 @@ Lanczos, projected eigensolve, mu, density blocks, forces) per step, replayed
 as one CUDA graph.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
-                  [--impl ours|reference] [--workload c60_1920|md15360]
+                  [--impl ours|reference] [--workload c60_1920|md15360|autograd1920]
 
 --workload md15360 times molecular dynamics instead: the 4x4x4 fcc C60 cell
 of 15360 atoms (a = 12.5 A, cluster cutoff 6.5 A, r = 16), velocity-Verlet
 steps of 0.5 fs from 2000 K Maxwell-Boltzmann velocities, one CUDA graph per
 step; value = atom-steps/s, with the NVE energy drift of the mixed and FP64
 paths over the same steps from the same state.
+
+--workload autograd1920 times the exact local gradient instead (the
+truncated local free energy at Krylov order r = r_min, whose projected
+problem is the dense cluster eigenproblem, ~392 x 392 per target, with its
+Daleckii-Krein backward) on the 1920-atom compressed cell: one step = forward
+(spectra, mu, energies) + backward; the stored-eigenvector backward is timed
+against the recomputing one, and --fd-coords seeded coordinates are checked
+by central differences (h = 1e-4 A) of the FP64 energy.
 
 Prints one JSON line (rank 0).  With --gpus N > 1 (torchrun, one rank per GPU)
 every rank evaluates its own replica of the cell; value = total atoms / max time.
@@ -48,7 +56,9 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reorth-passes", type=int, default=1)
-    ap.add_argument("--workload", default="c60_1920", choices=["c60_1920", "md15360"])
+    ap.add_argument("--workload", default="c60_1920",
+                    choices=["c60_1920", "md15360", "autograd1920"])
+    ap.add_argument("--fd-coords", type=int, default=8)
     ap.add_argument("--no-fp64-compare", action="store_true")
     return ap.parse_args()
 
@@ -581,8 +591,221 @@ def run_md(args):
     return 0
 
 
+# ---------------------------------------------------------------- exact local gradient
+
+AG_METRIC = "atom force evals/s (exact local gradient at r = r_min, forward + backward, 1 GB300)"
+AG_INDEX = 3
+
+
+def ag_workload():
+    from synth import CONFIGS, fcc_c60_crystal, workload_params
+    cfg = CONFIGS[AG_INDEX]
+    pos, L, _ = fcc_c60_crystal(cfg["ncell"], cfg["a"], cfg["jitter"], cfg["seed"],
+                                cfg["bridges"])
+    return cfg, pos, L, workload_params(cfg, defl_tol=1e-9)
+
+
+def oracle_ag_sample(pos, L, p, n_targets):
+    """Oracle per-target work of the exact local path (dense eigh of H_c, the
+    Daleckii-Krein matrix and its bond contraction at a fixed mu) on evenly
+    spaced targets; seconds per target."""
+    import numpy as np
+    from oracle.neighbors import neighbor_lists, cluster_lists
+    from oracle.hamiltonian import BondTable
+    from oracle import local_exact
+    hl = neighbor_lists(pos, L, p["rm"])
+    cl = cluster_lists(pos, L, p["Rc"])
+    bonds = BondTable(pos, L, hl, p)
+    F = np.zeros((len(pos), 3))
+    stride = max(1, len(pos) // n_targets)
+    t0 = time.perf_counter()
+    nt = 0
+    for i in range(0, len(pos), stride):
+        lam, Z = local_exact.target_spectrum(bonds, cl[i])
+        G = local_exact.target_gradient_matrix(lam, Z, 3.5, p["kT"])
+        local_exact.target_force_terms(bonds, cl[i], G, F)
+        nt += 1
+    return (time.perf_counter() - t0) / nt, nt
+
+
+def run_autograd(args):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    from synth.c60 import wrap
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    cfg, pos, L, p = ag_workload()
+    n = len(pos)
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+        t_tgt, nt = oracle_ag_sample(pos, L, p, 16)
+        value = 1.0 / t_tgt
+        line = {"metric": AG_METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tgt * n,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": cfg["name"], "n_atoms": n, "l2": "n/a (CPU)"},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"dense eigh + Daleckii-Krein gradient of {nt} "
+                                           f"evenly spaced targets, scaled to {n} targets"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+    if world > 1:
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        if rank == 0:
+            __graft_entry__.build()
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        dist.barrier()
+        if rank != 0:
+            __graft_entry__.build()
+    else:
+        __graft_entry__.build()
+    import paper_0910_4497_gb300 as tb
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cpu_base = None
+    if rank == 0 and not args.no_cpu_baseline:
+        t_tgt, nt = oracle_ag_sample(pos, L, p, 16)
+        cpu_base = {"value": 1.0 / t_tgt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": f"dense eigh + Daleckii-Krein gradient of {nt} evenly spaced "
+                              f"targets ({t_tgt * nt:.1f} s), scaled to {n} targets"}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(system, steps, backward=True):
+        f, b = [], []
+        for k in range(steps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            flush.fill_(float(k))
+            e[0].record(stream)
+            system.local_forward()
+            e[1].record(stream)
+            if backward:
+                system.local_gradient()
+            e[2].record(stream)
+            e[2].synchronize()
+            f.append(e[0].elapsed_time(e[1]))
+            b.append(e[1].elapsed_time(e[2]))
+        return f, b
+
+    res = {}
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    for store in (True, False):
+        s = tb.TBSystem(n, L, p, prec=args.prec, device=dev)
+        s.reserve_local(store_basis=store)
+        s.set_positions(pos)
+        for _ in range(max(args.warmup, 3)):
+            s.local_forward()
+            s.local_gradient()
+        barrier()
+        f, b = timed(s, args.steps)
+        barrier()
+        s.check()
+        res[store] = dict(fwd=f, bwd=b, F=s.F_loc.cpu().numpy(),
+                          zbytes=(s.Z_loc.numel() * s.Z_loc.element_size()) if store else 0)
+        if store:
+            # end to end: positions from pinned host memory, forces and energies back
+            hp = torch.as_tensor(pos, dtype=torch.float64).pin_memory()
+            hF = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+            hE = torch.empty(8, dtype=torch.float64).pin_memory()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            e2e_ms = 0.0
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                e0.record(stream)
+                s.pos.copy_(hp, non_blocking=True)
+                s.local_forward()
+                s.local_gradient()
+                hF.copy_(s.F_loc, non_blocking=True)
+                hE.copy_(s.energies_loc, non_blocking=True)
+                e1.record(stream)
+                e1.synchronize()
+                e2e_ms += e0.elapsed_time(e1)
+            res["e2e_ms"] = e2e_ms
+        s.close()
+    clk = clocks.stop() if clocks else None
+    t_step = sum(a + b for a, b in zip(res[True]["fwd"], res[True]["bwd"]))
+    if world > 1:
+        t = torch.tensor([t_step, res["e2e_ms"]], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_step, res["e2e_ms"] = t.tolist()
+    value = world * n * args.steps / (t_step / 1e3)
+    check = None
+    if rank == 0:
+        # FP64 reference gradient and central differences of the FP64 energy
+        s64 = tb.TBSystem(n, L, p, prec="fp64", device=dev)
+        s64.reserve_local(store_basis=False)
+        s64.set_positions(pos)
+        s64.local_forward()
+        s64.local_gradient()
+        F64 = s64.F_loc.cpu().numpy()
+        rng = np.random.default_rng(cfg["seed"])
+        h = 1e-4
+        fd_err = 0.0
+        for q in rng.choice(3 * n, size=args.fd_coords, replace=False):
+            atom, k = divmod(int(q), 3)
+            ev = []
+            for sgn in (1.0, -1.0):
+                x = pos.copy()
+                x[atom, k] += sgn * h
+                s64.set_positions(wrap(x, L))
+                s64.local_forward()
+                ev.append(s64.energies_loc[4].item())
+            fd_err = max(fd_err, abs(-(ev[0] - ev[1]) / (2 * h) - F64[atom, k]))
+        s64.check()
+        s64.close()
+        check = {"fd_coords": args.fd_coords, "fd_h_A": h,
+                 "fd_vs_fp64_gradient_max_eV_per_A": fd_err,
+                 "force_vs_fp64_path_max_eV_per_A": float(np.abs(res[True]["F"] - F64).max()),
+                 "stored_equals_recomputed": bool(np.array_equal(res[True]["F"],
+                                                                 res[False]["F"]))}
+        mean = statistics.mean
+        line = {
+            "metric": AG_METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.prec == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "n_atoms": n, "a": cfg["a"], "Rc": cfg["Rc"],
+                       "krylov_r": "r_min (dense cluster eigenproblem)", "kT": cfg["kT"],
+                       "precision": args.prec, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "step": "forward (spectra, mu, energies) + stored-basis backward"},
+            "e2e": {"value": world * n * args.steps / (res["e2e_ms"] / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": n * 3 * 8, "d2h_bytes_per_step": n * 3 * 8 + 64},
+            "roofline": None,
+            "cpu_baseline": cpu_base,
+            "clocks": clk,
+            "gpu_launches": 7 * args.steps,
+            "backward": {"forward_ms": mean(res[True]["fwd"]),
+                         "stored_basis_ms": mean(res[True]["bwd"]),
+                         "recomputed_basis_ms": mean(res[False]["bwd"]),
+                         "stored_basis_bytes": res[True]["zbytes"],
+                         "recomputed_basis_bytes": 0},
+            "check": check,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "autograd1920":
+        return run_autograd(args)
     if args.workload == "md15360":
         return run_md(args)
     if args.impl == "reference":

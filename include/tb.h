@@ -256,6 +256,56 @@ tb_status tb_find_mu_static(int n, int r, const double* lambda, const double* S,
                             void* stream);
 
 /* Library version string (static, host). */
+/*
+ * a11. Exact gradient of the truncated local free energy (differentiable form
+ * of the method).  Sec. 3: once the Krylov order reaches the minimal-polynomial
+ * degree (r = r_min) the block Krylov space of a target is invariant and its
+ * projection is exact, so the target's spectral record is that of the dense
+ * eigen-decomposition of its cluster Hamiltonian H_c = Z diag(lam) Z^T
+ * (Sec. 2).  These calls evaluate that limit directly:
+ *   A_loc = sum_i A_i,  A_i = Omega_i + mu N_i,
+ *   Omega_i = 2 sum_a <i a| omega(H_c(i)) |i a>,  omega(e) = -kT ln(1 + e^{-(e-mu)/kT}),
+ * with mu fixed by sum_i N_i = N_e, and its exact gradient at fixed N_e
+ *   dOmega_i/dH_c = 2 Z (Gamma o S^T S) Z^T,   S = Z[0:4, :],
+ *   Gamma_mk = (omega(lam_m) - omega(lam_k)) / (lam_m - lam_k),  Gamma_mm = f(lam_m)
+ * (Daleckii-Krein), contracted with dH/dR over the bonds of every cluster.
+ * Clusters must hold at most TB_LOCAL_MAX_DIM / 4 atoms (max_cluster of the
+ * context <= 128).  Precision: TB_PREC_FP64 runs everything in FP64;
+ * TB_PREC_MIXED runs the dense eigen-decomposition and the W = Z M product in
+ * FP32, with eigenvalues (FP64 Rayleigh quotients on the tridiagonal form),
+ * divided differences, mu, energies and force sums in FP64.
+ *
+ * tb_ctx_reserve_local: allocates the dense workspace (one slot per SM: three
+ * matrices of 4*max_cluster squared plus scratch; ~7 x 2 MB per SM in FP64 at
+ * max_cluster 128) and per-target force terms for n atoms.  Not capturable.
+ * Returns TB_ERR_CAPACITY if max_cluster > 128.
+ *
+ * With ND = 4 * max_cluster:
+ * tb_local_forward: lists and bond blocks as produced by a1/a2 (Hblk FP64);
+ *   lambda [n*ND] out, S [n*4*ND] out (layout of tb_krylov_density with NT = ND;
+ *   entries beyond 4 n_c(i) are 0), kdim [n] out (= 4 n_c(i));
+ *   Zstore (may be NULL): [n*ND*ND] elements of the context precision (double
+ *   for TB_PREC_FP64, float for TB_PREC_MIXED), out: target i's eigenvectors
+ *   at i*ND*ND, row-major with leading dimension 4 n_c(i) (the stored-basis
+ *   backward); mu (device, out): one double; energies [8] out as in tb_forces
+ *   (A = A_loc, E_total = A_loc + E_rep).
+ * tb_local_gradient: F [n*3] out = -d(A_loc + E_rep)/dR at the given mu (the
+ *   forward's), from the forward's lambda and S; if Zstore is NULL the
+ *   eigenvectors are recomputed (same arithmetic, same bits), else read.
+ * Cluster capacity overflow and non-finite values go to the status word.
+ */
+#define TB_LOCAL_MAX_DIM 512
+tb_status tb_ctx_reserve_local(tb_ctx* ctx, int n_atoms);
+tb_status tb_local_forward(tb_ctx* ctx, int n, const double* pos, double L, const int* c_off,
+                           const int* c_idx, const int* h_off, const int* h_idx,
+                           const double* Hblk, double* lambda, double* S, int* kdim,
+                           void* Zstore, double* mu, double* energies, void* stream);
+tb_status tb_local_gradient(tb_ctx* ctx, int n, const double* pos, double L, const int* c_off,
+                            const int* c_idx, const int* h_off, const int* h_idx,
+                            const double* Hblk, const double* dHblk, const double* lambda,
+                            const double* S, const void* Zstore, const double* mu, double* F,
+                            void* stream);
+
 const char* tb_version(void);
 
 #ifdef __cplusplus

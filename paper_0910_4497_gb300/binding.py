@@ -23,7 +23,8 @@ TB_PREC_MIXED = 1
 EXPORTS = ["tb_params_default", "tb_ctx_create", "tb_ctx_destroy", "tb_ctx_reserve",
            "tb_ctx_workspace_bytes", "tb_get_status", "tb_build_neighbors",
            "tb_assemble_H", "tb_krylov_density", "tb_find_mu", "tb_forces", "tb_md_step",
-           "tb_profile_enable", "tb_profile_read", "tb_find_mu_static", "tb_version"]
+           "tb_profile_enable", "tb_profile_read", "tb_find_mu_static",
+           "tb_ctx_reserve_local", "tb_local_forward", "tb_local_gradient", "tb_version"]
 
 
 class TBParams(ctypes.Structure):
@@ -67,6 +68,9 @@ def load_library(path=LIB_PATH):
         "tb_profile_enable": [P, I],
         "tb_profile_read": [P, ctypes.POINTER(ctypes.c_float)],
         "tb_find_mu_static": [I, I, VP, VP, D, D, D, I, VP, VP, VP, VP, VP],
+        "tb_ctx_reserve_local": [P, I],
+        "tb_local_forward": [P, I, VP, D, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP],
+        "tb_local_gradient": [P, I, VP, D, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -232,6 +236,40 @@ def tb_find_mu_static(n, r, lam, S, kT, n_electrons, mu_tol, max_iter, mu_guess,
         int(n), int(r), _ptr(lam, f64, "lambda"), _ptr(S, f64, "S"), float(kT),
         float(n_electrons), float(mu_tol), int(max_iter), _ptr(mu_guess, f64, "mu_guess"),
         _ptr(mu, f64, "mu"), _ptr(n_count, f64, "n_count"), _ptr(status, i32, "status"),
+        _stream(stream)))
+
+
+def tb_ctx_reserve_local(ctx, n_atoms):
+    _check("tb_ctx_reserve_local", lib().tb_ctx_reserve_local(ctx, int(n_atoms)))
+
+
+def _zstore(Z):
+    if Z is None:
+        return None
+    if Z.dtype not in (torch.float32, torch.float64):
+        raise TypeError("Zstore: expected float32 or float64")
+    return _ptr(Z, Z.dtype, "Zstore")
+
+
+def tb_local_forward(ctx, n, pos, L, c_off, c_idx, h_off, h_idx, Hblk, lam, S, kdim, Zstore,
+                     mu, energies, stream=None):
+    i32, f64 = torch.int32, torch.float64
+    _check("tb_local_forward", lib().tb_local_forward(
+        ctx, n, _ptr(pos, f64, "pos"), float(L), _ptr(c_off, i32, "c_off"),
+        _ptr(c_idx, i32, "c_idx"), _ptr(h_off, i32, "h_off"), _ptr(h_idx, i32, "h_idx"),
+        _ptr(Hblk, f64, "Hblk"), _ptr(lam, f64, "lambda"), _ptr(S, f64, "S"),
+        _ptr(kdim, i32, "kdim"), _zstore(Zstore), _ptr(mu, f64, "mu"),
+        _ptr(energies, f64, "energies"), _stream(stream)))
+
+
+def tb_local_gradient(ctx, n, pos, L, c_off, c_idx, h_off, h_idx, Hblk, dHblk, lam, S, Zstore,
+                      mu, F, stream=None):
+    i32, f64 = torch.int32, torch.float64
+    _check("tb_local_gradient", lib().tb_local_gradient(
+        ctx, n, _ptr(pos, f64, "pos"), float(L), _ptr(c_off, i32, "c_off"),
+        _ptr(c_idx, i32, "c_idx"), _ptr(h_off, i32, "h_off"), _ptr(h_idx, i32, "h_idx"),
+        _ptr(Hblk, f64, "Hblk"), _ptr(dHblk, f64, "dHblk"), _ptr(lam, f64, "lambda"),
+        _ptr(S, f64, "S"), _zstore(Zstore), _ptr(mu, f64, "mu"), _ptr(F, f64, "F"),
         _stream(stream)))
 
 

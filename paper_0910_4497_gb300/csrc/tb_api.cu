@@ -168,6 +168,7 @@ tb_status tb_ctx_destroy(tb_ctx* c) {
   if (!c) return TB_ERR_INVALID_ARG;
   cudaDeviceSynchronize();
   if (c->ws) cudaFree(c->ws);
+  if (c->loc_ws) cudaFree(c->loc_ws);
   if (c->d_status) cudaFree(c->d_status);
   for (int q = 0; q < 12; ++q)
     if (c->prof_ev[q]) cudaEventDestroy(c->prof_ev[q]);
@@ -313,6 +314,64 @@ tb_status tb_md_step(tb_ctx* c, int n, double* pos, double* vel, double* F, doub
                           c->kdim, c->mu, F, energies, s)) != TB_OK)
     return st;
   return launch_md_kick(c, n, vel, F, dt_fs, mass_amu, energies, s);
+}
+
+tb_status tb_ctx_reserve_local(tb_ctx* c, int n_atoms) {
+  if (!c || n_atoms < 0) return TB_ERR_INVALID_ARG;
+  if (n_atoms <= c->loc_reserved_n && c->loc_ws) return TB_OK;
+  tb_status st = local_configure(c);
+  if (st != TB_OK) return st;
+  const size_t bytes = local_workspace_bytes(c, n_atoms);
+  if (c->loc_ws) {
+    cudaDeviceSynchronize();
+    cudaFree(c->loc_ws);
+    c->loc_ws = nullptr;
+    c->loc_reserved_n = 0;
+  }
+  unsigned char* ws = nullptr;
+  if (cudaMalloc(&ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return TB_ERR_NOMEM;
+  }
+  local_carve(c, n_atoms, ws);
+  c->loc_ws = ws;
+  c->loc_reserved_n = n_atoms;
+  TB_CUDA_TRY(cudaMemset(ws, 0, bytes));
+  TB_CUDA_TRY(cudaDeviceSynchronize());
+  return TB_OK;
+}
+
+tb_status tb_local_forward(tb_ctx* c, int n, const double* pos, double L, const int* c_off,
+                           const int* c_idx, const int* h_off, const int* h_idx,
+                           const double* Hblk, double* lambda, double* S, int* kdim,
+                           void* Zstore, double* mu, double* energies, void* stream) {
+  tb_status st = ready(c, n);
+  if (st != TB_OK) return st;
+  if (n > c->loc_reserved_n || !c->loc_ws) return TB_ERR_NOT_RESERVED;
+  if (n == 0) return TB_OK;
+  if (!pos || !c_off || !c_idx || !h_off || !h_idx || !Hblk || !lambda || !S || !kdim || !mu ||
+      !energies || !(L > 0.0))
+    return TB_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return launch_local_forward(c, n, pos, L, c_off, c_idx, h_off, h_idx, Hblk, lambda, S, kdim,
+                              Zstore, mu, energies, s);
+}
+
+tb_status tb_local_gradient(tb_ctx* c, int n, const double* pos, double L, const int* c_off,
+                            const int* c_idx, const int* h_off, const int* h_idx,
+                            const double* Hblk, const double* dHblk, const double* lambda,
+                            const double* S, const void* Zstore, const double* mu, double* F,
+                            void* stream) {
+  tb_status st = ready(c, n);
+  if (st != TB_OK) return st;
+  if (n > c->loc_reserved_n || !c->loc_ws) return TB_ERR_NOT_RESERVED;
+  if (n == 0) return TB_OK;
+  if (!pos || !c_off || !c_idx || !h_off || !h_idx || !Hblk || !dHblk || !lambda || !S || !mu ||
+      !F || !(L > 0.0))
+    return TB_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return launch_local_gradient(c, n, pos, L, c_off, c_idx, h_off, h_idx, Hblk, dHblk, lambda, S,
+                               Zstore, mu, F, s);
 }
 
 tb_status tb_profile_enable(tb_ctx* c, int enable) {

@@ -513,7 +513,20 @@ tb_status mu_configure(tb_ctx* c) {
 tb_status launch_mu(tb_ctx* c, int n, const double* lambda, const double* S,
                     double n_electrons, const double* mu_guess, double* mu,
                     double* n_count, cudaStream_t s) {
-  const int NT = 4 * c->p.r;
+  return launch_mu_nt(c, n, 4 * c->p.r, lambda, S, n_electrons, mu_guess, mu, n_count, s);
+}
+
+tb_status launch_energy_reduce(int n, const double* per_target, const double* mu,
+                               double* energies, cudaStream_t s) {
+  energy_reduce_kernel<<<1, 1024, 0, s>>>(n, per_target, mu, energies, 0);
+  TB_CUDA_TRY(cudaGetLastError());
+  return TB_OK;
+}
+
+// mu search over records of NT pairs per target (NT = 4r for the Krylov record)
+tb_status launch_mu_nt(tb_ctx* c, int n, int NT, const double* lambda, const double* S,
+                       double n_electrons, const double* mu_guess, double* mu,
+                       double* n_count, cudaStream_t s) {
   MuArgs a;
   a.npairs = (long long)n * NT;
   a.NT = NT;

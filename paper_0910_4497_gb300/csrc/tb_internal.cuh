@@ -151,6 +151,16 @@ struct tb_ctx {
   size_t fin_smem = 0;
   int mu_grid = 0;
   int mu_smem_max = 0;
+  // exact local gradient (a11): dense workspace, allocated by tb_ctx_reserve_local
+  int loc_ND = 0;                    // 4 * max_cluster
+  int loc_grid = 0;
+  size_t loc_smem = 0;
+  size_t loc_esize = 0;              // element size of the dense matrices
+  int loc_reserved_n = 0;
+  unsigned char* loc_ws = nullptr;
+  void *loc_A = nullptr, *loc_Z = nullptr, *loc_X = nullptr;
+  double* loc_Cb = nullptr;
+  double* loc_Floc = nullptr;
   // stage timing events (tb_profile_enable)
   bool profiling = false;
   bool prof_ran[6] = {false, false, false, false, false, false};
@@ -183,6 +193,23 @@ tb_status launch_forces(tb_ctx* c, int n, const double* pos, double L,
                         const double* lambda, const double* S, const double* P,
                         const int* kdim, const double* mu, double* F,
                         double* energies, cudaStream_t s);
+tb_status launch_mu_nt(tb_ctx* c, int n, int NT, const double* lambda, const double* S,
+                       double n_electrons, const double* mu_guess, double* mu,
+                       double* n_count, cudaStream_t s);
+tb_status launch_energy_reduce(int n, const double* per_target, const double* mu,
+                               double* energies, cudaStream_t s);
+tb_status local_configure(tb_ctx* c);
+size_t local_workspace_bytes(tb_ctx* c, int n);
+void local_carve(tb_ctx* c, int n, unsigned char* base);
+tb_status launch_local_forward(tb_ctx* c, int n, const double* pos, double L, const int* c_off,
+                               const int* c_idx, const int* h_off, const int* h_idx,
+                               const double* Hblk, double* lambda, double* S, int* kdim,
+                               void* Zstore, double* mu, double* energies, cudaStream_t s);
+tb_status launch_local_gradient(tb_ctx* c, int n, const double* pos, double L, const int* c_off,
+                                const int* c_idx, const int* h_off, const int* h_idx,
+                                const double* Hblk, const double* dHblk, const double* lambda,
+                                const double* S, const void* Zstore, const double* mu, double* F,
+                                cudaStream_t s);
 tb_status launch_md_kick_drift(tb_ctx* c, int n, double* pos, double* vel,
                                const double* F, double L, double dt, double mass,
                                cudaStream_t s);

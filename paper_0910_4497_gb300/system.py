@@ -85,6 +85,42 @@ class TBSystem:
         B.tb_md_step(self.ctx, self.n, self.pos, self.vel, self.F, self.L, dt_fs, mass_amu,
                      self.energies, stream)
 
+    # -- exact local free energy and its gradient at r = r_min (a11)
+    def reserve_local(self, store_basis=False):
+        """Dense workspace and buffers of the exact local path; with store_basis
+        the forward keeps every target's eigenvectors for the backward
+        (n * (4 max_cluster)^2 elements), else the backward recomputes them."""
+        B.tb_ctx_reserve_local(self.ctx, self.n)
+        n, ND = self.n, 4 * self.tp.max_cluster
+        kw = dict(device=self.device)
+        f64 = torch.float64
+        self.ND = ND
+        self.lam_loc = torch.zeros(n * ND, dtype=f64, **kw)
+        self.S_loc = torch.zeros(n * 4 * ND, dtype=f64, **kw)
+        self.kdim_loc = torch.zeros(n, dtype=torch.int32, **kw)
+        self.mu_loc = torch.zeros(1, dtype=f64, **kw)
+        self.energies_loc = torch.zeros(8, dtype=f64, **kw)
+        self.F_loc = torch.zeros((n, 3), dtype=f64, **kw)
+        zt = f64 if self.tp.prec == B.TB_PREC_FP64 else torch.float32
+        self.Z_loc = torch.zeros(n * ND * ND, dtype=zt, **kw) if store_basis else None
+        self.local_version = 0
+
+    def local_forward(self, stream=None):
+        """Lists, bond blocks, dense spectra of every cluster, mu and energies
+        (energies_loc[4] = A_loc + E_rep) of the positions in self.pos."""
+        self.neighbors(stream)
+        self.assemble(stream)
+        B.tb_local_forward(self.ctx, self.n, self.pos, self.L, self.c_off, self.c_idx,
+                           self.h_off, self.h_idx, self.Hblk, self.lam_loc, self.S_loc,
+                           self.kdim_loc, self.Z_loc, self.mu_loc, self.energies_loc, stream)
+        self.local_version += 1
+
+    def local_gradient(self, stream=None):
+        """F_loc = -d(A_loc + E_rep)/dR at the last local_forward's state."""
+        B.tb_local_gradient(self.ctx, self.n, self.pos, self.L, self.c_off, self.c_idx,
+                            self.h_off, self.h_idx, self.Hblk, self.dHblk, self.lam_loc,
+                            self.S_loc, self.Z_loc, self.mu_loc, self.F_loc, stream)
+
     # -- CUDA graph of one evaluation
     def capture(self):
         s = torch.cuda.Stream(device=self.device)

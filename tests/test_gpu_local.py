@@ -1,0 +1,187 @@
+"""GPU parity of the exact local gradient (truncated local free energy at
+r = r_min, Daleckii-Krein backward) through the C ABI, against the oracle's
+restatement (oracle.local_exact), plus central differences of the GPU's own
+energy and the stored-basis / recomputed-basis equivalence."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import local_exact
+from synth import CONFIGS, TB_CONSTANTS, diamond_cell, fcc_c60_crystal, workload_params
+from synth.c60 import wrap
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": dict(F=1e-6, E=1e-8), "mixed": dict(F=1e-3, E=1e-5)}
+
+
+@pytest.fixture(scope="module")
+def tb():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_0910_4497_gb300 as tb
+    assert torch.cuda.is_available()
+    return tb
+
+
+def diamond_params(**kw):
+    p = dict(TB_CONSTANTS)
+    p.update(kT=0.1, Rc=2.8, r=8, defl_tol=1e-9, n_electrons_per_atom=4.0, max_cluster=32)
+    p.update(kw)
+    return p
+
+
+def jittered_diamond(seed=7, amp=0.06):
+    pos, L = diamond_cell(2)
+    pos = pos + amp * np.random.default_rng(seed).standard_normal(pos.shape)
+    return wrap(pos, L), L
+
+
+@pytest.fixture(scope="module")
+def diamond_ref():
+    pos, L = jittered_diamond()
+    p = diamond_params()
+    return pos, L, p, local_exact.local_evaluation(pos, L, p)
+
+
+def grouped(lam, w, gap=1e-4):
+    """Sums of w over groups of eigenvalues closer than `gap` (lam ascending)."""
+    starts = np.concatenate([[0], np.nonzero(np.diff(lam) >= gap)[0] + 1])
+    return np.add.reduceat(w, starts)
+
+
+def run_local(tb, pos, L, p, prec, store):
+    s = tb.TBSystem(len(pos), L, p, prec=prec)
+    s.reserve_local(store_basis=store)
+    s.set_positions(pos)
+    s.local_forward()
+    s.local_gradient()
+    torch.cuda.synchronize()
+    s.check()
+    return s
+
+
+def spectra(s):
+    lam = s.lam_loc.view(s.n, s.ND).cpu().numpy()
+    S = s.S_loc.view(s.n, 4, s.ND).cpu().numpy()
+    kd = s.kdim_loc.cpu().numpy()
+    return [(lam[i, :kd[i]], (S[i, :, :kd[i]] ** 2).sum(axis=0)) for i in range(s.n)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_local_matches_oracle_on_truncated_clusters(tb, diamond_ref, prec):
+    pos, L, p, ref = diamond_ref
+    s = run_local(tb, pos, L, p, prec, store=False)
+    tol = TOL[prec]
+    # spectra: eigenvalues and seed weights per target
+    lam_tol = 1e-10 if prec == "fp64" else 2e-4
+    for i, (lam, w) in enumerate(spectra(s)):
+        assert len(lam) == len(ref["lam"][i])
+        assert np.abs(lam - ref["lam"][i]).max() <= lam_tol, i
+        # seed weights are unique only summed over (near-)degenerate groups
+        gw, rw = grouped(ref["lam"][i], w), grouped(ref["lam"][i], ref["w"][i])
+        assert np.abs(gw - rw).max() <= (1e-10 if prec == "fp64" else 1e-4), i
+    e = s.energies_loc.cpu().numpy()
+    assert abs(e[0] - ref["E_band"]) <= tol["E"] * abs(ref["E_band"])
+    assert abs(e[4] - ref["E_total"]) <= tol["E"] * abs(ref["E_total"])
+    assert abs(e[5] - 4.0 * len(pos)) <= 1e-9 * len(pos)
+    F = s.F_loc.cpu().numpy()
+    assert np.abs(F - ref["F"]).max() <= tol["F"], np.abs(F - ref["F"]).max()
+    assert np.abs(F.sum(axis=0)).max() <= 1e-9
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_stored_and_recomputed_basis_give_the_same_gradient(tb, diamond_ref, prec):
+    pos, L, p, _ = diamond_ref
+    a = run_local(tb, pos, L, p, prec, store=True)
+    b = run_local(tb, pos, L, p, prec, store=False)
+    assert torch.equal(a.F_loc, b.F_loc)
+    assert torch.equal(a.energies_loc, b.energies_loc)
+    a.close()
+    b.close()
+
+
+def test_local_autograd_matches_central_differences(tb):
+    pos, L = jittered_diamond(seed=9)
+    p = diamond_params()
+    s = tb.TBSystem(len(pos), L, p, prec="fp64")
+    s.reserve_local(store_basis=True)
+    x = torch.tensor(pos, dtype=torch.float64, device="cuda", requires_grad=True)
+    e = tb.local_energy(x, s)
+    (g,) = torch.autograd.grad(e, x)
+    s.check()
+    h = 1e-4
+    for atom, k in ((0, 0), (21, 1), (47, 2), (63, 0)):
+        xp, xm = pos.copy(), pos.copy()
+        xp[atom, k] += h
+        xm[atom, k] -= h
+        ep = tb.local_energy(torch.tensor(xp, device="cuda"), s).item()
+        em = tb.local_energy(torch.tensor(xm, device="cuda"), s).item()
+        fd = (ep - em) / (2 * h)
+        assert abs(fd - g[atom, k].item()) <= 1e-6, (atom, k, fd, g[atom, k].item())
+    s.close()
+
+
+def test_local_c60_cell_sampled_atoms(tb):
+    """240-atom fcc C60 cell (cluster cutoff 5.0 A, ~43 atoms per cluster,
+    172 x 172 dense problems): forces of sampled atoms against the oracle."""
+    cfg = CONFIGS[0]
+    pos, L, _ = fcc_c60_crystal(cfg["ncell"], cfg["a"], cfg["jitter"], cfg["seed"])
+    p = workload_params(cfg, defl_tol=1e-9, max_cluster=64)
+    atoms = [0, 77, 150, 239]
+    ref = None
+    for prec in ("fp64", "mixed"):
+        s = run_local(tb, pos, L, p, prec, store=False)
+        if ref is None:
+            tg = local_exact.targets_touching([np.asarray(c) for c in s.lists()[1]], atoms)
+            ref = local_exact.local_evaluation(pos, L, p, targets=tg)
+        F = s.F_loc.cpu().numpy()
+        e = s.energies_loc.cpu().numpy()
+        tol = TOL[prec]
+        assert np.abs(F[atoms] - ref["F"][atoms]).max() <= tol["F"], (prec, np.abs(F[atoms] - ref["F"][atoms]).max())
+        assert abs(e[0] - ref["E_band"]) <= tol["E"] * abs(ref["E_band"]), prec
+        s.close()
+
+
+def test_local_full_size_autograd_cell(tb):
+    """The 1920-atom compressed fcc C60 cell (a = 13.0 A, cluster cutoff 6.0 A,
+    ~98 atoms and 392 x 392 dense problems per cluster) in the launch
+    configuration the benchmark times: sampled atoms' forces against the
+    oracle, stored vs recomputed basis, and central differences of the FP64
+    energy on a few seeded coordinates."""
+    cfg = CONFIGS[3]
+    pos, L, _ = fcc_c60_crystal(cfg["ncell"], cfg["a"], cfg["jitter"], cfg["seed"])
+    p = workload_params(cfg, defl_tol=1e-9)
+    atoms = [5, 611, 1302, 1919]
+    s64 = run_local(tb, pos, L, p, "fp64", store=True)
+    cl = [np.asarray(c) for c in s64.lists()[1]]
+    ref = local_exact.local_evaluation(pos, L, p, targets=local_exact.targets_touching(cl, atoms))
+    F64 = s64.F_loc.cpu().numpy()
+    e64 = s64.energies_loc.cpu().numpy()
+    assert np.abs(F64[atoms] - ref["F"][atoms]).max() <= TOL["fp64"]["F"]
+    assert abs(e64[0] - ref["E_band"]) <= TOL["fp64"]["E"] * abs(ref["E_band"])
+    sm = run_local(tb, pos, L, p, "mixed", store=False)
+    Fm = sm.F_loc.cpu().numpy()
+    assert np.abs(Fm[atoms] - ref["F"][atoms]).max() <= TOL["mixed"]["F"]
+    assert np.abs(Fm - F64).max() <= TOL["mixed"]["F"]
+    sm.close()
+    # central differences of the FP64 energy, seeded coordinates
+    rng = np.random.default_rng(cfg["seed"])
+    h = 1e-4
+    for q in rng.choice(3 * len(pos), size=3, replace=False):
+        atom, k = divmod(int(q), 3)
+        xp, xm = pos.copy(), pos.copy()
+        xp[atom, k] += h
+        xm[atom, k] -= h
+        ev = []
+        for x in (xp, xm):
+            s64.set_positions(wrap(x, L))
+            s64.local_forward()
+            ev.append(s64.energies_loc[4].item())
+        fd = -(ev[0] - ev[1]) / (2 * h)
+        # mu is solved to |N - N_e| <= 1e-12 N_e, so A carries up to mu * 1e-12 N_e
+        # (~3e-8 eV here) of noise: 1.3e-4 eV/A after dividing by 2h at worst
+        assert abs(fd - F64[atom, k]) <= 1.5e-4, (atom, k, fd, F64[atom, k])
+    s64.check()
+    s64.close()

@@ -24,5 +24,5 @@ following the paper's steps in order:
 
 Library primitives used as single steps: numpy matmul, numpy.linalg.eigh.
 """
-from . import model, neighbors, hamiltonian, krylov, density, md, exact, local_exact  # noqa: F401
+from . import model, neighbors, hamiltonian, krylov, density, md, exact, local_exact, virial  # noqa: F401
 from .pipeline import force_evaluation, OracleResult  # noqa: F401

@@ -6,7 +6,8 @@ Lanczos, projected eigensolve, mu, density blocks, forces) per step, replayed
 as one CUDA graph.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
-                  [--impl ours|reference] [--workload c60_1920|md15360|autograd1920]
+                  [--impl ours|reference]
+                  [--workload c60_1920|md15360|autograd1920|diamond_eos]
 
 --workload md15360 times molecular dynamics instead: the 4x4x4 fcc C60 cell
 of 15360 atoms (a = 12.5 A, cluster cutoff 6.5 A, r = 16), velocity-Verlet
@@ -21,6 +22,13 @@ Daleckii-Krein backward) on the 1920-atom compressed cell: one step = forward
 (spectra, mu, energies) + backward; the stored-eigenvector backward is timed
 against the recomputing one, and --fd-coords seeded coordinates are checked
 by central differences (h = 1e-4 A) of the FP64 energy.
+
+--workload diamond_eos times pressure evaluations of the 4x4x4 cubic diamond
+supercell (512 atoms; Sec. 5's equation-of-state workload): one step = one
+force evaluation plus the virial pressure at one lattice constant, cycling
+through eight lattice constants; it reports the equation of state E(V), P(V),
+a Birch-Murnaghan fit, and its convergence with the block order r and with the
+8x8x8 supercell (4096 atoms).
 
 Prints one JSON line (rank 0).  With --gpus N > 1 (torchrun, one rank per GPU)
 every rank evaluates its own replica of the cell; value = total atoms / max time.
@@ -57,7 +65,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reorth-passes", type=int, default=1)
     ap.add_argument("--workload", default="c60_1920",
-                    choices=["c60_1920", "md15360", "autograd1920"])
+                    choices=["c60_1920", "md15360", "autograd1920", "diamond_eos"])
     ap.add_argument("--fd-coords", type=int, default=8)
     ap.add_argument("--no-fp64-compare", action="store_true")
     return ap.parse_args()
@@ -802,10 +810,263 @@ def run_autograd(args):
     return 0
 
 
+# ---------------------------------------------------------------- diamond equation of state
+
+EOS_METRIC = "pressure evaluations/s (4x4x4 diamond supercell, 512 atoms, 1 GB300)"
+EOS_UNIT = "pressure evaluations/s"
+GPA = 160.21766208
+
+
+def eos_params(a, r=None):
+    from synth import DIAMOND_EOS, TB_CONSTANTS
+    d = DIAMOND_EOS
+    p = dict(TB_CONSTANTS)
+    p.update(kT=d["kT"], Rc=d["Rc_over_a"] * a, r=d["r"] if r is None else r,
+             max_hnbr=d["max_hnbr"], max_cluster=d["max_cluster"], n_electrons_per_atom=4.0,
+             defl_tol=1e-9)
+    return p
+
+
+def oracle_pressure(a, ncell):
+    """One full oracle force evaluation plus virial of the perfect diamond cell."""
+    import oracle
+    from oracle import virial
+    from synth import diamond_cell
+    pos, L = diamond_cell(ncell, a)
+    p = eos_params(a)
+    t0 = time.perf_counter()
+    res = oracle.force_evaluation(pos, L, p)
+    W = virial.evaluation_virial(res, p)
+    dt = time.perf_counter() - t0
+    return dt, virial.pressure(W, L), res.E_total / len(pos)
+
+
+def birch_murnaghan(V, E):
+    """Third-order Birch-Murnaghan fit: E = sum_k c_k V^{-2k/3}, k = 0..3."""
+    import numpy as np
+    x = V ** (-2.0 / 3.0)
+    c = np.polyfit(x, E, 3)
+    xs = np.roots(np.polyder(c))
+    xs = xs[np.isreal(xs)].real
+    xs = xs[(xs > x.min() * 0.8) & (xs < x.max() * 1.2)]
+    if len(xs) == 0:
+        return None
+    x0 = xs[np.argmin(np.polyval(c, xs))]
+    V0 = x0 ** (-1.5)
+    # B = V d2E/dV2 at V0, with x = V^{-2/3}: dE/dV = E'(x) (-2/3) V^{-5/3}
+    d1, d2 = np.polyval(np.polyder(c), x0), np.polyval(np.polyder(c, 2), x0)
+    B0 = V0 * (d2 * (4.0 / 9.0) * V0 ** (-10.0 / 3.0) + d1 * (10.0 / 9.0) * V0 ** (-8.0 / 3.0))
+    def P_of(V):
+        xv = V ** (-2.0 / 3.0)
+        return np.polyval(np.polyder(c), xv) * (2.0 / 3.0) * V ** (-5.0 / 3.0)
+    return dict(V0_A3_per_atom=float(V0), a0_A=float((8 * V0) ** (1 / 3)),
+                B0_GPa=float(B0 * GPA), P_fit=P_of)
+
+
+def run_eos(args):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    from synth import DIAMOND_EOS, diamond_cell
+    d = DIAMOND_EOS
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    a_ref = 3.55
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+        ts = []
+        for k in range(args.warmup + args.steps):
+            dt, _, _ = oracle_pressure(d["a_list"][k % len(d["a_list"])], d["ncell"])
+            if k >= args.warmup:
+                ts.append(dt)
+        value = len(ts) / sum(ts)
+        line = {"metric": EOS_METRIC, "value": value, "unit": EOS_UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": d["name"], "n_atoms": 512, "l2": "n/a (CPU)"},
+                "cpu_baseline": {"value": value, "unit": EOS_UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": "full oracle force evaluation + virial of the 512-atom "
+                                           "cell per step, lattice constants cycled"},
+                "e2e": {"value": value, "unit": EOS_UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+    if world > 1:
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        if rank == 0:
+            __graft_entry__.build()
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        dist.barrier()
+        if rank != 0:
+            __graft_entry__.build()
+    else:
+        __graft_entry__.build()
+    import paper_0910_4497_gb300 as tb
+    from paper_0910_4497_gb300 import binding as B
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cpu_base, ref = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        t_or, P_or, e_or = oracle_pressure(a_ref, d["ncell"])
+        cpu_base = {"value": 1.0 / t_or, "unit": EOS_UNIT, "cores": 1, "kind": "oracle",
+                    "sample": f"one full oracle force evaluation + virial of the 512-atom cell "
+                              f"at a = {a_ref} A ({t_or:.1f} s, single process)"}
+        ref = (P_or, e_or)
+    systems = []
+    for a in d["a_list"]:
+        pos, L = diamond_cell(d["ncell"], a)
+        s = tb.TBSystem(len(pos), L, eos_params(a), prec=args.prec, device=dev)
+        B.tb_profile_enable(s.ctx, True)
+        s.set_positions(pos)
+        s.capture(with_virial=True)
+        systems.append((a, pos, L, s))
+    n = len(systems[0][1])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for k in range(max(args.warmup, 3)):
+        systems[k % len(systems)][3].replay()
+    barrier()
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kry = []
+    for k in range(args.steps):
+        s = systems[k % len(systems)][3]
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        s.replay()
+        ev[k][1].record(stream)
+        ev[k][1].synchronize()
+        kry.append(B.tb_profile_read(s.ctx)["krylov"])
+    barrier()
+    clk = clocks.stop() if clocks else None
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = t.item()
+    value = world * args.steps / (total_ms / 1e3)
+    # end to end: positions in, energies and pressure out
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hp = [torch.as_tensor(x[1], dtype=torch.float64).pin_memory() for x in systems]
+    hout = torch.empty(8 + 9 + 1, dtype=torch.float64).pin_memory()
+    e2e_ms = 0.0
+    barrier()
+    for k in range(args.steps):
+        q = k % len(systems)
+        s = systems[q][3]
+        flush.fill_(float(k))
+        e0.record(stream)
+        s.pos.copy_(hp[q], non_blocking=True)
+        s.replay()
+        hout[:8].copy_(s.energies, non_blocking=True)
+        hout[8:17].copy_(s.W, non_blocking=True)
+        hout[17:].copy_(s.pressure, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = t.item()
+    # equation of state and its convergence (untimed)
+    table = []
+    for a, pos, L, s in systems:
+        s.replay()
+        torch.cuda.synchronize(dev)
+        s.check()
+        e = s.energies.cpu().numpy()
+        table.append(dict(a_A=a, V_A3_per_atom=L ** 3 / n, E_eV_per_atom=float(e[4] / n),
+                          P_GPa=float(s.pressure.item() * GPA),
+                          max_abs_F=float(s.F.abs().max().item())))
+    conv = []
+    if rank == 0:
+        for a, _, _, _ in systems:
+            row = {"a_A": a}
+            for tag, ncell, r in (("r12", d["ncell"], d["r_check"]), ("8x8x8", d["ncell_big"], None)):
+                pos, L = diamond_cell(ncell, a)
+                s2 = tb.TBSystem(len(pos), L, eos_params(a, r), prec=args.prec, device=dev)
+                s2.set_positions(pos)
+                s2.evaluate(with_virial=True)
+                torch.cuda.synchronize(dev)
+                s2.check()
+                row[f"P_GPa_{tag}"] = float(s2.pressure.item() * GPA)
+                row[f"E_eV_per_atom_{tag}"] = float(s2.energies[4].item() / len(pos))
+                s2.close()
+            conv.append(row)
+    V = np.array([t["V_A3_per_atom"] for t in table])
+    E = np.array([t["E_eV_per_atom"] for t in table])
+    fit = birch_murnaghan(V, E)
+    if fit is not None:
+        Pf = fit.pop("P_fit")
+        for t in table:
+            t["P_GPa_from_fit"] = float(Pf(t["V_A3_per_atom"]) * GPA)
+    if rank == 0:
+        alg = algorithmic_sweep_bytes(systems[0][3], args.prec)
+        kms = [v for v in kry if v > 0]
+        kry_ms = statistics.mean(kms) if kms else None
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        achieved = alg / (kry_ms * 1e-3) / 1e9 if kry_ms else None
+        acc = None
+        if ref is not None:
+            sr = systems[[x[0] for x in systems].index(a_ref)][3]
+            acc = {"vs": f"FP64 CPU oracle at a = {a_ref} A",
+                   "pressure_err_GPa": float(abs(sr.pressure.item() - ref[0]) * GPA),
+                   "energy_err_eV_per_atom": float(abs(sr.energies[4].item() / n - ref[1]))}
+        line = {
+            "metric": EOS_METRIC, "value": value, "unit": EOS_UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.prec == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": d["name"], "n_atoms": n, "a_A": d["a_list"],
+                       "Rc": "1.26 a (71 atoms per cluster)", "krylov_r": d["r"], "kT": d["kT"],
+                       "precision": args.prec, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "graph": "one CUDA graph per pressure evaluation"},
+            "e2e": {"value": world * args.steps / (e2e_ms / 1e3), "unit": EOS_UNIT,
+                    "h2d_bytes_per_step": n * 3 * 8, "d2h_bytes_per_step": 18 * 8},
+            "roofline": {"bound": "hbm", "kernel": "krylov_kernel", "achieved": achieved,
+                         "peak": hbm, "unit": "GB/s", "frac": achieved / hbm if achieved else None,
+                         "traffic": None, "algorithmic_bytes_per_launch": alg,
+                         "kernel_ms": kry_ms},
+            "cpu_baseline": cpu_base,
+            "clocks": clk,
+            "gpu_launches": 13 * args.steps,
+            "paper_context": {"seconds_gpu_8800gtx_xu": 55.65, "seconds_cpu_elses_xu": 29.19,
+                              "note": "time to compute the pressure of the 4x4x4 supercell; the "
+                                      "number of evaluations inside is not stated"},
+            "eos": table,
+            "birch_murnaghan": fit,
+            "convergence": conv,
+            "accuracy": acc,
+        }
+        print(json.dumps(line), flush=True)
+    for _, _, _, s in systems:
+        s.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.workload == "autograd1920":
         return run_autograd(args)
+    if args.workload == "diamond_eos":
+        return run_eos(args)
     if args.workload == "md15360":
         return run_md(args)
     if args.impl == "reference":

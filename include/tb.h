@@ -257,6 +257,23 @@ tb_status tb_find_mu_static(int n, int r, const double* lambda, const double* S,
 
 /* Library version string (static, host). */
 /*
+ * Virial and pressure (Sec. 5: pressure of a diamond supercell for its
+ * equation of state).  Every force of tb_forces is a sum over directed bonds,
+ * F_k = sum_{j in H(k)} f_kj (band term of both density-matrix columns plus
+ * the pair repulsion), f_jk = -f_kj; the configurational virial is the pair form
+ *   W_ab = -1/2 sum over directed bonds (k -> j) of d_a f_kj,b,   d = R_j - R_k,
+ * (equal to sum_k R_k,a F_k,b for an isolated system), and the static pressure
+ * P = tr W / (3 L^3).  Reads the per-bond forces that the most recent tb_forces
+ * or tb_md_step left in the context, so pos, L, h_off, h_idx must be that
+ * call's; after tb_md_step pass h_off = h_idx = NULL to use the context's own
+ * lists (those of the step's force evaluation).  W [9] out (row-major, eV);
+ * pressure [1] out (eV/A^3; 1 eV/A^3 = 160.21766 GPa), may be NULL.  Add
+ * 2 KE / (3 L^3) for the kinetic part of a moving system.
+ */
+tb_status tb_virial(tb_ctx* ctx, int n, const double* pos, double L, const int* h_off,
+                    const int* h_idx, double* W, double* pressure, void* stream);
+
+/*
  * a11. Exact gradient of the truncated local free energy (differentiable form
  * of the method).  Sec. 3: once the Krylov order reaches the minimal-polynomial
  * degree (r = r_min) the block Krylov space of a target is invariant and its

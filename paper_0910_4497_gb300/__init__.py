@@ -8,7 +8,7 @@ from . import binding
 from .binding import (TBParams, TBError, make_params, tb_ctx_create, tb_ctx_destroy,
                       tb_ctx_reserve, tb_ctx_workspace_bytes, tb_get_status,
                       tb_build_neighbors, tb_assemble_H, tb_krylov_density, tb_find_mu,
-                      tb_forces, tb_md_step, tb_ctx_reserve_local, tb_local_forward,
+                      tb_forces, tb_md_step, tb_virial, tb_ctx_reserve_local, tb_local_forward,
                       tb_local_gradient, tb_version)
 from .system import TBSystem
 from .autograd import TBEnergy, TBLocalEnergy, energy, local_energy
@@ -18,6 +18,6 @@ binding.lib()   # fail loudly now if the CUDA library is missing
 __all__ = ["TBParams", "TBError", "make_params", "tb_ctx_create", "tb_ctx_destroy",
            "tb_ctx_reserve", "tb_ctx_workspace_bytes", "tb_get_status",
            "tb_build_neighbors", "tb_assemble_H", "tb_krylov_density", "tb_find_mu",
-           "tb_forces", "tb_md_step", "tb_ctx_reserve_local", "tb_local_forward",
+           "tb_forces", "tb_md_step", "tb_virial", "tb_ctx_reserve_local", "tb_local_forward",
            "tb_local_gradient", "tb_version", "TBSystem", "TBEnergy", "TBLocalEnergy",
            "energy", "local_energy"]

@@ -24,7 +24,8 @@ EXPORTS = ["tb_params_default", "tb_ctx_create", "tb_ctx_destroy", "tb_ctx_reser
            "tb_ctx_workspace_bytes", "tb_get_status", "tb_build_neighbors",
            "tb_assemble_H", "tb_krylov_density", "tb_find_mu", "tb_forces", "tb_md_step",
            "tb_profile_enable", "tb_profile_read", "tb_find_mu_static",
-           "tb_ctx_reserve_local", "tb_local_forward", "tb_local_gradient", "tb_version"]
+           "tb_virial", "tb_ctx_reserve_local", "tb_local_forward", "tb_local_gradient",
+           "tb_version"]
 
 
 class TBParams(ctypes.Structure):
@@ -68,6 +69,7 @@ def load_library(path=LIB_PATH):
         "tb_profile_enable": [P, I],
         "tb_profile_read": [P, ctypes.POINTER(ctypes.c_float)],
         "tb_find_mu_static": [I, I, VP, VP, D, D, D, I, VP, VP, VP, VP, VP],
+        "tb_virial": [P, I, VP, D, VP, VP, VP, VP, VP],
         "tb_ctx_reserve_local": [P, I],
         "tb_local_forward": [P, I, VP, D, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP],
         "tb_local_gradient": [P, I, VP, D, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP],
@@ -236,6 +238,14 @@ def tb_find_mu_static(n, r, lam, S, kT, n_electrons, mu_tol, max_iter, mu_guess,
         int(n), int(r), _ptr(lam, f64, "lambda"), _ptr(S, f64, "S"), float(kT),
         float(n_electrons), float(mu_tol), int(max_iter), _ptr(mu_guess, f64, "mu_guess"),
         _ptr(mu, f64, "mu"), _ptr(n_count, f64, "n_count"), _ptr(status, i32, "status"),
+        _stream(stream)))
+
+
+def tb_virial(ctx, n, pos, L, h_off, h_idx, W, pressure=None, stream=None):
+    i32, f64 = torch.int32, torch.float64
+    _check("tb_virial", lib().tb_virial(
+        ctx, n, _ptr(pos, f64, "pos"), float(L), _ptr(h_off, i32, "h_off"),
+        _ptr(h_idx, i32, "h_idx"), _ptr(W, f64, "W"), _ptr(pressure, f64, "pressure"),
         _stream(stream)))
 
 

@@ -316,6 +316,19 @@ tb_status tb_md_step(tb_ctx* c, int n, double* pos, double* vel, double* F, doub
   return launch_md_kick(c, n, vel, F, dt_fs, mass_amu, energies, s);
 }
 
+tb_status tb_virial(tb_ctx* c, int n, const double* pos, double L, const int* h_off,
+                    const int* h_idx, double* W, double* pressure, void* stream) {
+  tb_status st = ready(c, n);
+  if (st != TB_OK) return st;
+  if (!h_off && !h_idx) {      // the context's own lists, as left by tb_md_step
+    h_off = c->h_off;
+    h_idx = c->h_idx;
+  }
+  if (!pos || !h_off || !h_idx || !W || !(L > 0.0)) return TB_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return launch_virial(c, n, pos, L, h_off, h_idx, W, pressure, s);
+}
+
 tb_status tb_ctx_reserve_local(tb_ctx* c, int n_atoms) {
   if (!c || n_atoms < 0) return TB_ERR_INVALID_ARG;
   if (n_atoms <= c->loc_reserved_n && c->loc_ws) return TB_OK;

@@ -437,6 +437,39 @@ __global__ void __launch_bounds__(256) force_sum_kernel(const ForceArgs a) {
   if (!(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]))) tbk::set_status(a.st, TB_ERR_NONFINITE, k);
 }
 
+// Virial of the pair-decomposed forces, W_ab = -1/2 sum over directed bonds of
+// d_a f_b (d = R_j - R_k by minimum image, f the bond's force on k stored by
+// force_bond_kernel), and the static pressure tr W / (3 L^3).  One block,
+// atoms strided over the threads, fixed-order block reduction.
+__global__ void __launch_bounds__(1024)
+virial_kernel(int n, const double* pos, double L, const int* h_off, const int* h_idx,
+              const double* bondf, double* W, double* pressure) {
+  __shared__ double red[32 * 16];
+  __shared__ double tot[16];
+  double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const double hL = 0.5 * L;
+  for (int k = threadIdx.x; k < n; k += 1024) {
+    for (int p = h_off[k]; p < h_off[k + 1]; ++p) {
+      const int j = h_idx[p];
+      double d[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double x = pos[3 * j + c] - pos[3 * k + c];
+        d[c] = x > hL ? x - L : (x < -hL ? x + L : x);
+      }
+      const double* f = bondf + (size_t)p * 4;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) v[a * 3 + b] += d[a] * f[b];
+    }
+  }
+  tbk::block_sum16<double, 9>(v, red, tot);
+  if (threadIdx.x < 9) W[threadIdx.x] = -0.5 * tot[threadIdx.x];
+  if (threadIdx.x == 0 && pressure)
+    *pressure = -0.5 * (tot[0] + tot[4] + tot[8]) / (3.0 * L * L * L);
+}
+
 // energies[8] = {E_band, -TS, A, E_rep, E_tot, N(mu), mu, KE}; columns of
 // per_target: E_band, -TS, N_e, E_rep, KE.  `cols` selects what to refresh.
 __global__ void __launch_bounds__(1024)
@@ -514,6 +547,13 @@ tb_status launch_mu(tb_ctx* c, int n, const double* lambda, const double* S,
                     double n_electrons, const double* mu_guess, double* mu,
                     double* n_count, cudaStream_t s) {
   return launch_mu_nt(c, n, 4 * c->p.r, lambda, S, n_electrons, mu_guess, mu, n_count, s);
+}
+
+tb_status launch_virial(tb_ctx* c, int n, const double* pos, double L, const int* h_off,
+                        const int* h_idx, double* W, double* pressure, cudaStream_t s) {
+  virial_kernel<<<1, 1024, 0, s>>>(n, pos, L, h_off, h_idx, c->bondf, W, pressure);
+  TB_CUDA_TRY(cudaGetLastError());
+  return TB_OK;
 }
 
 tb_status launch_energy_reduce(int n, const double* per_target, const double* mu,

@@ -198,6 +198,8 @@ tb_status launch_mu_nt(tb_ctx* c, int n, int NT, const double* lambda, const dou
                        double* n_count, cudaStream_t s);
 tb_status launch_energy_reduce(int n, const double* per_target, const double* mu,
                                double* energies, cudaStream_t s);
+tb_status launch_virial(tb_ctx* c, int n, const double* pos, double L, const int* h_off,
+                        const int* h_idx, double* W, double* pressure, cudaStream_t s);
 tb_status local_configure(tb_ctx* c);
 size_t local_workspace_bytes(tb_ctx* c, int n);
 void local_carve(tb_ctx* c, int n, unsigned char* base);

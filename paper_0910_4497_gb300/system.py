@@ -48,6 +48,8 @@ class TBSystem:
         self.F = torch.zeros((n, 3), dtype=f64, **kw)
         self.vel = torch.zeros((n, 3), dtype=f64, **kw)
         self.energies = torch.zeros(8, dtype=f64, **kw)
+        self.W = torch.zeros(9, dtype=f64, **kw)
+        self.pressure = torch.zeros(1, dtype=f64, **kw)
         self.graph = None
 
     # -- the five stages of one force evaluation
@@ -73,13 +75,21 @@ class TBSystem:
                     self.lam, self.S, self.P, self.kdim, self.mu, self.F, self.energies,
                     stream)
 
-    def evaluate(self, stream=None, warm_start=False):
-        """One full force evaluation (a1..a10) of the positions in self.pos."""
+    def evaluate(self, stream=None, warm_start=False, with_virial=False):
+        """One full force evaluation (a1..a10) of the positions in self.pos;
+        with_virial adds the virial W (3x3, eV) and static pressure (eV/A^3)."""
         self.neighbors(stream)
         self.assemble(stream)
         self.krylov(stream)
         self.find_mu(stream, warm_start=warm_start)
         self.forces(stream)
+        if with_virial:
+            self.virial(stream)
+
+    def virial(self, stream=None):
+        """Virial and static pressure from the last forces() call."""
+        B.tb_virial(self.ctx, self.n, self.pos, self.L, self.h_off, self.h_idx, self.W,
+                    self.pressure, stream)
 
     def md_step(self, dt_fs, mass_amu, stream=None):
         B.tb_md_step(self.ctx, self.n, self.pos, self.vel, self.F, self.L, dt_fs, mass_amu,
@@ -122,18 +132,18 @@ class TBSystem:
                             self.S_loc, self.Z_loc, self.mu_loc, self.F_loc, stream)
 
     # -- CUDA graph of one evaluation
-    def capture(self):
+    def capture(self, with_virial=False):
         s = torch.cuda.Stream(device=self.device)
         s.wait_stream(torch.cuda.current_stream(self.device))
         with torch.cuda.stream(s):
             for _ in range(2):
-                self.evaluate(s)
+                self.evaluate(s, with_virial=with_virial)
         torch.cuda.current_stream(self.device).wait_stream(s)
         torch.cuda.synchronize(self.device)
         self.check()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            self.evaluate()
+            self.evaluate(with_virial=with_virial)
         self.graph = g
         return g
 

@@ -49,6 +49,16 @@ CONFIGS = [
 ]
 
 
+# Equation of state of cubic diamond (Sec. 5): 4x4x4 supercell (512 atoms), perfect
+# lattice at each lattice constant a; the cluster cutoff scales with a
+# (Rc = 1.26 a, between the 6th and 7th neighbour shells) so every cluster holds
+# the same 71 atoms at every a.  Convergence: block order r, and the 8x8x8
+# supercell (4096 atoms).
+DIAMOND_EOS = dict(name="diamond_4x4x4_eos_512", ncell=4, ncell_big=8,
+                   a_list=[3.40, 3.45, 3.50, 3.55, 3.60, 3.65, 3.70, 3.75],
+                   Rc_over_a=1.26, r=8, r_check=12, kT=0.1, max_hnbr=32, max_cluster=96)
+
+
 def workload_params(cfg, **overrides):
     """Model + numerical parameters for one workload, as a plain dict."""
     p = dict(TB_CONSTANTS)

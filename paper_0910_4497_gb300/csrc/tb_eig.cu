@@ -3,133 +3,312 @@
 // record lambda, S = U[seed rows], P = Y U.
 //
 // FP64 arithmetic on this GPU runs at ~1/70 of the FP32 rate with ~70-cycle
-// latency, so a serial FP64 tridiagonal QL would dominate the whole force
-// evaluation.  The eigensolve is therefore split:
-//   1. eig_tri_kernel (one warp per target, FP32): Householder reduction of
-//      the active part of T to tridiagonal form; eigenvalues by Sturm-sequence
-//      bisection, each lane owning its own eigenvalues; eigenvectors by
-//      inverse iteration (tridiagonal LU with partial pivoting, three solves),
-//      lane-parallel, with Gram-Schmidt inside clusters of eigenvalues closer
-//      than 1e-3 ||T|| after every solve (the scheme of LAPACK's stein);
-//      back-transformation through the stored reflections.
-//   2. eig_finish_kernel (one CTA per target):
-//      - TB_PREC_MIXED: a first-order Loewdin step makes the FP32 eigenvectors
-//        orthonormal, then FP64 Rayleigh quotients give the eigenvalues;
-//      - TB_PREC_FP64: two FP64 steps of the Ogita-Aishima refinement
-//        (Japan J. Indust. Appl. Math. 35 (2018)): R = I - X^T X,
-//        S = X^T T X, lambda_i = S_ii/(1 - R_ii), E_ij = (S_ij + lambda_j R_ij)
-//        /(lambda_j - lambda_i) if the gap exceeds delta else R_ij/2,
-//        X <- X + X E, then FP64 Rayleigh quotients;
-//      then the eigenpairs are sorted ascending and S, P are formed.
+// latency, so the eigensolve runs in FP32 with FP64-accurate corrections:
+//   eig_warp_kernel (one warp per target, everything in the warp's shared
+//   memory, no per-thread arrays):
+//     1. Householder reduction of the active part of T to tridiagonal form,
+//        lanes owning rows (odd row pitch: column and row accesses are free
+//        of bank conflicts);
+//     2. eigenvalues by Sturm-sequence bisection, lanes owning eigenvalues;
+//     3. eigenvectors from the twisted factorisation of T' - lambda I (forward
+//        LDL^T and backward UDU^T pivots, twist index at the smallest
+//        |gamma_r|, then the two bidiagonal recurrences; only the output
+//        column is used as storage), twice, the second time at the
+//        tridiagonal Rayleigh quotient of the first vector (two lanes' worth
+//        of eigenvalues evaluated as independent chains); Gram-Schmidt inside
+//        clusters of eigenvalues closer than 1e-3 ||T||, and for a member that
+//        duplicates an earlier one (equal eigenvalues of a split tridiagonal)
+//        inverse iteration with a pivoted LU from a fresh start vector, the
+//        scheme of LAPACK's stein;
+//     4. back-transformation through the stored reflections;
+//   then, in the mixed path (TB_PREC_MIXED):
+//     5. a first-order Loewdin step U <- U (I - E/2), E = U^T U - I, row by row;
+//     6. Rayleigh quotients u^T T u on the original (FP64, block tridiagonal)
+//        T in double-float arithmetic (FP32 pairs with exact products);
+//     7. ascending order, lambda, S and P = Y U written out;
+//   in the FP64 path the FP32 eigenpairs go to eig_finish_kernel<double>:
+//      two FP64 steps of the Ogita-Aishima refinement
+//      (Japan J. Indust. Appl. Math. 35 (2018)): R = I - X^T X,
+//      S = X^T T X, lambda_i = S_ii/(1 - R_ii), E_ij = (S_ij + lambda_j R_ij)
+//      /(lambda_j - lambda_i) if the gap exceeds delta else R_ij/2,
+//      X <- X + X E, then FP64 Rayleigh quotients, ascending order, S and P.
 #include "tb_internal.cuh"
 
 namespace {
 
-constexpr int EW = 4;              // warps (targets) per CTA in the eigensolver
 constexpr int FT = 128;            // threads per CTA in the finishing kernel
+constexpr int XW_MAX = 8;          // warps (targets) per CTA in eig_warp_kernel
 
-struct EigArgs {
+struct XArgs {
   int n, NT;
   const double* T;
   const unsigned long long* colmask;
-  float* Zf;
+  const float* Y;                  // Krylov basis rows (mixed path)
+  const int* h_off;
+  float* Zf;                       // FP64 path: FP32 eigenvectors
   float* lamf;
+  double* lambda;                  // mixed path: spectral record
+  double* S;
+  double* P;
   int* kdim;
   int* st;
 };
 
-// Row pitch of the per-warp matrices: a multiple of 4 (float4 rows) whose
-// stride in banks keeps 8 consecutive rows' 16-byte accesses conflict-free.
-__host__ __device__ inline int pitch_of(int NT) { return NT + 4; }
+// odd row pitch: lanes reading one column (rows x..x+31) or one row each
+// (same column index) hit 32 different banks
+__host__ __device__ inline int xpitch(int NT) { return NT + 1; }
 
-__host__ __device__ inline size_t eig_smem_per_warp(int NT) {
-  // H (Householder vectors), Y (eigenvectors), v and q padded to NT + 4 for
-  // float4 reads past the active size, d, e, e2, lam (NT floats), act
-  return sizeof(float) * (2 * (size_t)NT * pitch_of(NT) + 2 * (NT + 4) + 4 * NT) +
-         sizeof(int) * NT;
+// H holds the matrix, then E of the Loewdin step, then the band of T as FP32
+// hi/lo pairs (12 columns per row), then staged rows of the Krylov basis
+__host__ __device__ inline int epitch(int NT) { return NT + 4; }   // E rows 16-byte aligned
+
+__host__ __device__ inline size_t xw_hsize(int NT) {
+  const size_t a = (size_t)NT * epitch(NT), b = 24 * (size_t)NT;
+  return a > b ? a : b;
 }
 
-// Number of eigenvalues of the symmetric tridiagonal (d, e2 = e^2) below x
-// (Sturm sequence of the LDL^T pivots; tiny pivots are replaced by -pivmin).
-__device__ __forceinline__ int sturm_count(const float* d, const float* e2, int m, float x,
-                                           float pivmin) {
-  float q = d[0] - x;
-  if (fabsf(q) < pivmin) q = -pivmin;
-  int cnt = q < 0.f;
+__host__ __device__ inline size_t xw_smem_per_warp(int NT) {
+  size_t b = sizeof(double) * NT;                          // lamd
+  b += sizeof(float) * (xw_hsize(NT) + (size_t)NT * xpitch(NT) + 11 * (size_t)NT + 64);
+  b += sizeof(int) * 2 * NT;                               // act, rank
+  return (b + 15) & ~size_t(15);
+}
+
+// Sturm counts (number of eigenvalues below x) at two points at once: two
+// independent dependency chains for the same lane.
+__device__ __forceinline__ void sturm_count2(const float* d, const float* e2, int m, float xa,
+                                             float xb, float pivmin, int& ca, int& cb) {
+  float qa = d[0] - xa, qb = d[0] - xb;
+  if (fabsf(qa) < pivmin) qa = -pivmin;
+  if (fabsf(qb) < pivmin) qb = -pivmin;
+  int na = qa < 0.f, nb = qb < 0.f;
   for (int i = 1; i < m; ++i) {
-    q = d[i] - x - __fdividef(e2[i - 1], q);
-    if (fabsf(q) < pivmin) q = -pivmin;
-    cnt += q < 0.f;
+    const float di = d[i], ei = e2[i - 1];
+    qa = di - xa - __fdividef(ei, qa);
+    qb = di - xb - __fdividef(ei, qb);
+    if (fabsf(qa) < pivmin) qa = -pivmin;
+    if (fabsf(qb) < pivmin) qb = -pivmin;
+    na += qa < 0.f;
+    nb += qb < 0.f;
   }
-  return cnt;
+  ca = na;
+  cb = nb;
 }
 
-// Tridiagonal LU with partial pivoting of (T - lambda I) (rows swapped when the
-// subdiagonal exceeds the pivot): U has diagonals u0, u1, u2; mult/piv hold
-// the eliminations.  Solves overwrite y with (T - lambda I)^{-1} y.
-struct TriLU {
-  float u0[tbk::MAX_NT], u1[tbk::MAX_NT], u2[tbk::MAX_NT], mult[tbk::MAX_NT];
-  unsigned long long piv;
-};
+__device__ __forceinline__ float guard(float x, float tiny) {
+  return fabsf(x) < tiny ? (x < 0.f ? -tiny : tiny) : x;
+}
 
-__device__ __forceinline__ void trilu_factor(TriLU& f, const float* d, const float* e, int m,
-                                             float lam, float tiny) {
-  float cd = d[0] - lam, cs = m > 1 ? e[0] : 0.f, cs2 = 0.f;
-  f.piv = 0ull;
-  for (int i = 0; i + 1 < m; ++i) {
-    const float sub = e[i], nd = d[i + 1] - lam, ns = (i + 2 < m) ? e[i + 1] : 0.f;
-    if (fabsf(cd) >= fabsf(sub)) {
-      const float piv = fabsf(cd) < tiny ? (cd < 0.f ? -tiny : tiny) : cd;
-      const float l = sub / piv;
-      f.u0[i] = piv; f.u1[i] = cs; f.u2[i] = cs2; f.mult[i] = l;
-      cd = nd - l * cs;
-      cs = ns - l * cs2;
-      cs2 = 0.f;
-    } else {
-      const float l = cd / sub;
-      f.u0[i] = sub; f.u1[i] = nd; f.u2[i] = ns; f.mult[i] = l;
-      f.piv |= 1ull << i;
-      cd = cs - l * nd;
-      cs = cs2 - l * ns;
-      cs2 = 0.f;
+// Eigenvectors of the tridiagonal (d, e) for the estimates lk[t] (t = 0, 1;
+// used where use[t]) from the twisted factorisations of T - lk I, written into
+// columns k[t] of Y (pitch P): forward pivots Dp_i, backward pivots Dm_i,
+// gamma_i = Dp_i + Dm_i - (d_i - lk), twist r = argmin |gamma|, z_r = 1,
+// z_i = -(e_i / Dp_i) z_{i+1} (i < r), z_{i+1} = -(e_i / Dm_{i+1}) z_i (i >= r);
+// normalised.  Only the output columns are used as storage.
+__device__ __forceinline__ void twisted_vectors(const float* d, const float* e, const float* e2,
+                                                int m, const float (&lk)[2], const bool (&use)[2],
+                                                float tiny, float* Y, int P, const int (&k)[2]) {
+  float dp[2], dm[2], best[2];
+  int r[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    dp[t] = guard(d[0] - lk[t], tiny);
+    if (use[t]) Y[k[t]] = dp[t];
+  }
+  for (int i = 1; i < m; ++i) {
+    const float di = d[i], ei = e2[i - 1];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      dp[t] = guard((di - lk[t]) - __fdividef(ei, dp[t]), tiny);
+      if (use[t]) Y[i * P + k[t]] = dp[t];
     }
   }
-  f.u0[m - 1] = fabsf(cd) < tiny ? (cd < 0.f ? -tiny : tiny) : cd;
-  f.u1[m - 1] = 0.f;
-  f.u2[m - 1] = 0.f;
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    dm[t] = guard(d[m - 1] - lk[t], tiny);
+    best[t] = use[t] ? fabsf(Y[(m - 1) * P + k[t]]) : 0.f;
+    r[t] = m - 1;
+  }
+  for (int i = m - 2; i >= 0; --i) {
+    const float di = d[i], ei = e2[i];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      dm[t] = guard((di - lk[t]) - __fdividef(ei, dm[t]), tiny);
+      if (use[t]) {
+        const float g = fabsf(Y[i * P + k[t]] + dm[t] - (di - lk[t]));
+        if (g < best[t]) { best[t] = g; r[t] = i; }
+      }
+    }
+  }
+  // U multipliers e_i / Dm_{i+1} for i = m-2 .. r, kept in rows i+1
+  const int rmin = min(use[0] ? r[0] : m, use[1] ? r[1] : m);
+#pragma unroll
+  for (int t = 0; t < 2; ++t) dm[t] = guard(d[m - 1] - lk[t], tiny);
+  for (int i = m - 2; i >= rmin; --i) {
+    const float di = d[i], ei = e[i], ei2 = e2[i];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (use[t] && i >= r[t]) Y[(i + 1) * P + k[t]] = __fdividef(ei, dm[t]);
+      dm[t] = guard((di - lk[t]) - __fdividef(ei2, dm[t]), tiny);
+    }
+  }
+  float nn[2] = {1.f, 1.f}, z[2] = {1.f, 1.f};
+  for (int i = rmin; i + 1 < m; ++i) {
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+      if (use[t] && i >= r[t]) {
+        z[t] = -Y[(i + 1) * P + k[t]] * z[t];
+        Y[(i + 1) * P + k[t]] = z[t];
+        nn[t] += z[t] * z[t];
+      }
+  }
+  const int rmax = max(use[0] ? r[0] : 0, use[1] ? r[1] : 0);
+  z[0] = z[1] = 1.f;
+  for (int i = rmax - 1; i >= 0; --i) {
+    const float ei = e[i];
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+      if (use[t] && i < r[t]) {
+        z[t] = -__fdividef(ei, Y[i * P + k[t]]) * z[t];
+        Y[i * P + k[t]] = z[t];
+        nn[t] += z[t] * z[t];
+      }
+  }
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+    if (use[t]) {
+      Y[r[t] * P + k[t]] = 1.f;
+      const float sc = rsqrtf(nn[t]);
+      for (int i = 0; i < m; ++i) Y[i * P + k[t]] *= sc;
+    }
 }
 
-__device__ __forceinline__ void trilu_solve(const TriLU& f, float* y, int m) {
-  for (int i = 0; i + 1 < m; ++i) {          // apply P and L^{-1}
-    float a = y[i], b = y[i + 1];
-    if ((f.piv >> i) & 1ull) { const float t = a; a = b; b = t; }
-    y[i] = a;
-    y[i + 1] = b - f.mult[i] * a;
-  }
-  for (int i = m - 1; i >= 0; --i) {         // U^{-1}
-    float t = y[i];
-    if (i + 1 < m) t -= f.u1[i] * y[i + 1];
-    if (i + 2 < m) t -= f.u2[i] * y[i + 2];
-    y[i] = t / f.u0[i];
-  }
+// double-float accumulation: (hi, lo) += a * b for floats a, b (exact product)
+__device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float b) {
+  const float p = a * b;
+  const float pe = fmaf(a, b, -p);
+  const float s = hi + p;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (p - bb);
+  hi = s;
+  lo += err + pe;
 }
 
-__global__ void __launch_bounds__(EW * 32) eig_tri_kernel(const EigArgs a) {
+// start vector of an inverse-iteration restart (deterministic, all components nonzero)
+__device__ __forceinline__ float start_component(int x, int k) {
+  unsigned h = (unsigned)x * 2654435761u ^ ((unsigned)k * 40503u + 0x9e3779b9u);
+  h ^= h >> 13;
+  h *= 0x5bd1e995u;
+  h ^= h >> 15;
+  return ((h & 1u) ? -1.f : 1.f) * (0.5f + (float)((h >> 1) & 1023u) * (1.0f / 1023.0f));
+}
+
+// Orthogonalise column c of Y against columns [c0, c) and normalise (whole
+// warp); returns the squared norm left after the projections.
+__device__ __forceinline__ float orth_column(float* Y, int P, int m, int c0, int c, int lane) {
+  for (int c2 = c0; c2 < c; ++c2) {
+    float dt = 0.f;
+    for (int x = lane; x < m; x += 32) dt += Y[x * P + c] * Y[x * P + c2];
+    dt = tbk::warp_sum(dt);
+    for (int x = lane; x < m; x += 32) Y[x * P + c] -= dt * Y[x * P + c2];
+    __syncwarp();
+  }
+  float nn = 0.f;
+  for (int x = lane; x < m; x += 32) nn += Y[x * P + c] * Y[x * P + c];
+  nn = tbk::warp_sum(nn);
+  const float sc = rsqrtf(fmaxf(nn, 1e-30f));
+  for (int x = lane; x < m; x += 32) Y[x * P + c] *= sc;
+  __syncwarp();
+  return nn;
+}
+
+// Inverse iteration for column c at eigenvalue lk with the pivoted
+// tridiagonal LU of T - lk I (the dlagtf/dlagts scheme), restarted from a
+// fixed start vector and kept orthogonal to columns [c0, c): used when the
+// twisted vector of a degenerate eigenvalue duplicates an earlier one (a split
+// tridiagonal).  The factorisation and the solves run on lane 0.
+__device__ void restart_column(const float* d, const float* e, int m, float lk, float tiny,
+                               float* Y, int P, int c0, int c, float* f, int lane) {
+  float* u0 = f;              // reciprocal pivots
+  float* u1 = f + m;          // first super-diagonal of U
+  float* u2 = f + 2 * m;      // second super-diagonal of U
+  float* ml = f + 3 * m;      // multipliers
+  float* pv = f + 4 * m;      // 1 where rows k, k+1 were interchanged
+  if (lane == 0) {
+    float ak = d[0] - lk, bk = m > 1 ? e[0] : 0.f;
+    for (int k = 0; k + 1 < m; ++k) {
+      const float ck = e[k], ak1 = d[k + 1] - lk, bk1 = k + 2 < m ? e[k + 1] : 0.f;
+      if (fabsf(ak) >= fabsf(ck)) {
+        const float piv = guard(ak, tiny);
+        const float mult = ck / piv;
+        u0[k] = 1.f / piv; u1[k] = bk; u2[k] = 0.f; ml[k] = mult; pv[k] = 0.f;
+        ak = ak1 - mult * bk;
+        bk = bk1;
+      } else {
+        const float mult = ak / ck;
+        u0[k] = 1.f / ck; u1[k] = ak1; u2[k] = bk1; ml[k] = mult; pv[k] = 1.f;
+        ak = bk - mult * ak1;
+        bk = -mult * bk1;
+      }
+    }
+    u0[m - 1] = 1.f / guard(ak, tiny);
+  }
+  for (int x = lane; x < m; x += 32) Y[x * P + c] = start_component(x, c);
+  __syncwarp();
+  for (int it = 0; it < 3; ++it) {
+    orth_column(Y, P, m, c0, c, lane);
+    if (lane == 0) {
+      float yk = Y[c];
+      for (int k = 0; k + 1 < m; ++k) {
+        const float yk1 = Y[(k + 1) * P + c];
+        if (pv[k] == 0.f) { Y[k * P + c] = yk; yk = yk1 - ml[k] * yk; }
+        else { Y[k * P + c] = yk1; yk = yk - ml[k] * yk1; }
+      }
+      Y[(m - 1) * P + c] = yk;
+      float y1 = 0.f, y2 = 0.f;
+      for (int k = m - 1; k >= 0; --k) {
+        float y = Y[k * P + c];
+        if (k + 1 < m) y -= u1[k] * y1;
+        if (k + 2 < m) y -= u2[k] * y2;
+        y *= u0[k];
+        Y[k * P + c] = y;
+        y2 = y1;
+        y1 = y;
+      }
+    }
+    __syncwarp();
+    float mx = 0.f;                          // rescale before the next projection
+    for (int x = lane; x < m; x += 32) mx = fmaxf(mx, fabsf(Y[x * P + c]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const float sc = 1.f / fmaxf(mx, 1e-30f);
+    for (int x = lane; x < m; x += 32) Y[x * P + c] *= sc;
+    __syncwarp();
+  }
+  orth_column(Y, P, m, c0, c, lane);
+}
+
+template <bool FULL>
+__global__ void __launch_bounds__(XW_MAX * 32) eig_warp_kernel(const XArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int NT = a.NT, PT = pitch_of(NT);
-  unsigned char* base = smem + warp * eig_smem_per_warp(NT);
-  float* H = reinterpret_cast<float*>(base);
-  float* Y = H + NT * PT;
-  float* vv = Y + NT * PT;
-  float* qq = vv + NT + 4;
-  float* d = qq + NT + 4;
+  const int NT = a.NT, P = xpitch(NT);
+  unsigned char* base = smem + warp * xw_smem_per_warp(NT);
+  double* lamd = reinterpret_cast<double*>(base);
+  float* H = reinterpret_cast<float*>(lamd + NT);
+  float* Y = H + xw_hsize(NT);
+  float* d = Y + NT * P;
   float* e = d + NT;
   float* e2 = e + NT;
   float* lam = e2 + NT;
-  int* act = reinterpret_cast<int*>(lam + NT);
-  const int i = blockIdx.x * EW + warp;
-  if (i >= a.n) return;
+  float* v = lam + NT;
+  float* q = v + NT;
+  float* fs = q + NT;                          // 5 NT: restart factorisation
+  float* slc = fs + 5 * NT;                    // 64 slicing counts
+  int* act = reinterpret_cast<int*>(slc + 64);
+  int* rank = act + NT;
+  const int i = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (i >= a.n) return;                       // whole warp: no block barriers below
 
   const unsigned long long mask = a.colmask[i];
   const int m = __popcll(mask);
@@ -137,82 +316,88 @@ __global__ void __launch_bounds__(EW * 32) eig_tri_kernel(const EigArgs a) {
     if ((mask >> x) & 1ull) act[__popcll(mask & ((1ull << x) - 1ull))] = x;
   __syncwarp();
   const double* Ti = a.T + (size_t)i * NT * NT;
-  for (int x = 0; x < m; ++x)
-    for (int y = lane; y < PT; y += 32)
-      H[x * PT + y] = y < m ? (float)Ti[act[x] * NT + act[y]] : 0.f;
-  for (int y = lane; y < NT + 4; y += 32) { vv[y] = 0.f; qq[y] = 0.f; }
+  for (int y = lane; y < m; y += 32) {
+    const int ay = act[y];
+    int x = 0;
+    for (; x + 3 < m; x += 4) {             // four independent loads in flight
+      const double t0 = Ti[act[x] * NT + ay], t1 = Ti[act[x + 1] * NT + ay];
+      const double t2 = Ti[act[x + 2] * NT + ay], t3 = Ti[act[x + 3] * NT + ay];
+      H[x * P + y] = (float)t0;
+      H[(x + 1) * P + y] = (float)t1;
+      H[(x + 2) * P + y] = (float)t2;
+      H[(x + 3) * P + y] = (float)t3;
+    }
+    for (; x < m; ++x) H[x * P + y] = (float)Ti[act[x] * NT + ay];
+  }
   __syncwarp();
 
-  // ---- Householder reduction to tridiagonal form.  Step j zeroes column j
-  // below the subdiagonal with I - 2 v v^T (v supported on rows > j) and keeps
-  // v in that column; lane owns rows x = lane, lane + 32.  Row updates run
-  // over float4 chunks from the aligned chunk holding column j + 1 (the extra
-  // columns get a zero update because v and q vanish there).
+  // ---- 1. Householder: step j maps column j below the diagonal to
+  // (alpha, 0, ...) with I - 2 v v^T and keeps v there; lanes own rows
+  // x = j+1+lane and j+33+lane.
   for (int j = 0; j + 2 < m; ++j) {
+    const int x0 = j + 1 + lane, x1 = x0 + 32;
+    const bool h0 = x0 < m, h1 = x1 < m;
     float xs = 0.f;
-    for (int x = lane; x < m; x += 32)
-      if (x > j) xs += H[x * PT + j] * H[x * PT + j];
+    if (h0) xs += H[x0 * P + j] * H[x0 * P + j];
+    if (h1) xs += H[x1 * P + j] * H[x1 * P + j];
     const float sig = tbk::warp_sum(xs);
-    const float x0 = H[(j + 1) * PT + j];
-    __syncwarp();
-    if (sig - x0 * x0 <= 1e-30f * (sig + 1e-30f) || sig == 0.f) {
-      if (lane == 0) e[j] = x0;
-      for (int x = lane; x < m; x += 32)
-        if (x > j) H[x * PT + j] = 0.f;      // identity reflection
+    const float xj = H[(j + 1) * P + j];
+    if (sig - xj * xj <= 1e-30f * (sig + 1e-30f) || sig == 0.f) {
+      if (lane == 0) e[j] = xj;
+      __syncwarp();
+      if (h0) H[x0 * P + j] = 0.f;                     // identity
+      if (h1) H[x1 * P + j] = 0.f;
       __syncwarp();
       continue;
     }
-    const float alpha = x0 >= 0.f ? -sqrtf(sig) : sqrtf(sig);
-    const float inv = rsqrtf(2.f * (sig - x0 * alpha));
-    for (int x = lane; x < m; x += 32)
-      vv[x] = x <= j ? 0.f : (x == j + 1 ? (x0 - alpha) : H[x * PT + j]) * inv;
+    const float alpha = xj >= 0.f ? -sqrtf(sig) : sqrtf(sig);
+    const float inv = rsqrtf(2.f * (sig - xj * alpha));
+    if (h0) v[x0] = (x0 == j + 1 ? (xj - alpha) : H[x0 * P + j]) * inv;
+    if (h1) v[x1] = H[x1 * P + j] * inv;
     __syncwarp();
-    const int c0 = (j + 1) & ~3;
-    float kp = 0.f;
-    for (int x = lane; x < m; x += 32) {
-      float p = 0.f;
-      if (x > j) {
-        const float* row = H + x * PT;
-        for (int l = c0; l < m; l += 4) {
-          const float4 h4 = *reinterpret_cast<const float4*>(row + l);
-          const float4 v4 = *reinterpret_cast<const float4*>(vv + l);
-          p += h4.x * v4.x + h4.y * v4.y + h4.z * v4.z + h4.w * v4.w;
-        }
-      }
-      qq[x] = p;
-      kp += p * vv[x];
+    const float* r0 = H + (h0 ? x0 : j + 1) * P;
+    const float* r1 = H + (h1 ? x1 : j + 1) * P;
+    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+    int l = j + 1;
+    for (; l + 1 < m; l += 2) {
+      const float v0 = v[l], v1 = v[l + 1];
+      a0 += r0[l] * v0;
+      a1 += r0[l + 1] * v1;
+      b0 += r1[l] * v0;
+      b1 += r1[l + 1] * v1;
     }
+    if (l < m) {
+      a0 += r0[l] * v[l];
+      b0 += r1[l] * v[l];
+    }
+    const float p0 = a0 + a1, p1 = b0 + b1;
+    float kp = 0.f;
+    if (h0) { q[x0] = p0; kp += p0 * v[x0]; }
+    if (h1) { q[x1] = p1; kp += p1 * v[x1]; }
     const float K = tbk::warp_sum(kp);
     __syncwarp();
-    for (int x = lane; x < m; x += 32) qq[x] -= K * vv[x];
+    if (h0) q[x0] -= K * v[x0];
+    if (h1) q[x1] -= K * v[x1];
     __syncwarp();
-    for (int x = lane; x < m; x += 32) {
-      if (x > j) {
-        const float vx = 2.f * vv[x], qx = 2.f * qq[x];
-        float* row = H + x * PT;
-        for (int l = c0; l < m; l += 4) {
-          float4 h4 = *reinterpret_cast<float4*>(row + l);
-          const float4 v4 = *reinterpret_cast<const float4*>(vv + l);
-          const float4 q4 = *reinterpret_cast<const float4*>(qq + l);
-          h4.x -= vx * q4.x + qx * v4.x;
-          h4.y -= vx * q4.y + qx * v4.y;
-          h4.z -= vx * q4.z + qx * v4.z;
-          h4.w -= vx * q4.w + qx * v4.w;
-          *reinterpret_cast<float4*>(row + l) = h4;
-        }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int x = t == 0 ? x0 : x1;
+      if (x < m) {
+        const float vx = 2.f * v[x], qx = 2.f * q[x];
+        float* row = H + x * P;
+#pragma unroll 4
+        for (int c = j + 1; c < m; ++c) row[c] -= vx * q[c] + qx * v[c];
+        row[j] = v[x];                                // keep v_j in column j
       }
     }
-    __syncwarp();
-    for (int x = lane; x < m; x += 32)
-      if (x > j) H[x * PT + j] = vv[x];      // keep v_j in column j
     if (lane == 0) e[j] = alpha;
-    for (int x = lane; x < NT + 4; x += 32) { vv[x] = 0.f; qq[x] = 0.f; }
     __syncwarp();
   }
-  for (int x = lane; x < m; x += 32) d[x] = H[x * PT + x];
+  for (int x = lane; x < m; x += 32) d[x] = H[x * P + x];
+  __syncwarp();
   if (lane == 0) {
-    if (m >= 2) e[m - 2] = H[(m - 1) * PT + (m - 2)];
-    if (m >= 1) e[m - 1] = 0.f;
+    if (m >= 2) e[m - 2] = H[(m - 1) * P + (m - 2)];
+    e[m - 1] = 0.f;
   }
   __syncwarp();
   float gl = 1e30f, gu = -1e30f, emax = 0.f;
@@ -230,95 +415,298 @@ __global__ void __launch_bounds__(EW * 32) eig_tri_kernel(const EigArgs a) {
     emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
   }
   __syncwarp();
-  const float tnorm = fmaxf(fabsf(gl), fabsf(gu));
+  const float tnorm = fmaxf(fmaxf(fabsf(gl), fabsf(gu)), 1e-30f);
   const float pivmin = fmaxf(1e-30f, 1.2e-7f * 1.2e-7f * emax);
+  const float tiny = 1.2e-7f * tnorm;
   gl -= 2.4e-7f * tnorm + pivmin;
   gu += 2.4e-7f * tnorm + pivmin;
 
-  // ---- eigenvalues by bisection: lane owns indices k = lane and lane + 32
+  // ---- 2. eigenvalues by bisection; lane owns k = lane and lane + 32, both
+  // evaluated in one Sturm pass
   {
     const int k0 = lane, k1 = lane + 32;
-    float a0 = gl, b0 = gu, a1 = gl, b1 = gu;
+    // slicing pass: counts at 64 points splitting [gl, gu] evenly (two per
+    // lane), then every eigenvalue starts from the slice that holds it
+    const float h = (gu - gl) * (1.f / 65.f);
+    int s0 = 0, s1 = 0;
+    sturm_count2(d, e2, m, gl + h * (float)(lane + 1), gl + h * (float)(lane + 33), pivmin, s0, s1);
+    float* cnt = slc;
+    cnt[lane] = (float)s0;
+    cnt[lane + 32] = (float)s1;
+    __syncwarp();
+    float lo0 = gl, hi0 = gu, lo1 = gl, hi1 = gu;
+    for (int t = 0; t < 64; ++t) {           // point t + 1 has cnt[t] eigenvalues below it
+      const float xt = gl + h * (float)(t + 1);
+      const int ct = (int)cnt[t];
+      if (ct > k0) hi0 = fminf(hi0, xt); else lo0 = fmaxf(lo0, xt);
+      if (ct > k1) hi1 = fminf(hi1, xt); else lo1 = fmaxf(lo1, xt);
+    }
+    __syncwarp();
     for (int it = 0; it < 64; ++it) {
-      const bool go0 = k0 < m && (b0 - a0) > 2.4e-7f * fmaxf(fabsf(a0), fabsf(b0)) + pivmin;
-      const bool go1 = k1 < m && (b1 - a1) > 2.4e-7f * fmaxf(fabsf(a1), fabsf(b1)) + pivmin;
-      if (!__any_sync(0xffffffffu, go0 || go1)) break;
-      const float m0 = 0.5f * (a0 + b0), m1 = 0.5f * (a1 + b1);
-      if (go0) { if (sturm_count(d, e2, m, m0, pivmin) > k0) b0 = m0; else a0 = m0; }
-      if (go1) { if (sturm_count(d, e2, m, m1, pivmin) > k1) b1 = m1; else a1 = m1; }
+      const bool g0 = k0 < m && (hi0 - lo0) > 2.4e-7f * fmaxf(fabsf(lo0), fabsf(hi0)) + pivmin;
+      const bool g1 = k1 < m && (hi1 - lo1) > 2.4e-7f * fmaxf(fabsf(lo1), fabsf(hi1)) + pivmin;
+      if (!__any_sync(0xffffffffu, g0 || g1)) break;
+      const float m0 = 0.5f * (lo0 + hi0), m1 = 0.5f * (lo1 + hi1);
+      int c0 = 0, c1 = 0;
+      if (g0 || g1) sturm_count2(d, e2, m, m0, m1, pivmin, c0, c1);
+      if (g0) { if (c0 > k0) hi0 = m0; else lo0 = m0; }
+      if (g1) { if (c1 > k1) hi1 = m1; else lo1 = m1; }
     }
-    if (k0 < m) lam[k0] = 0.5f * (a0 + b0);
-    if (k1 < m) lam[k1] = 0.5f * (a1 + b1);
+    if (k0 < m) lam[k0] = 0.5f * (lo0 + hi0);
+    if (k1 < m) lam[k1] = 0.5f * (lo1 + hi1);
   }
   __syncwarp();
-
-  // ---- eigenvectors by inverse iteration (lane-parallel), Gram-Schmidt
-  // inside clusters of close eigenvalues between iterations
+  // ---- 3. eigenvectors: twisted factorisations, twice (the second at the
+  // tridiagonal Rayleigh quotient of the first vector)
+  {
+    const int kk[2] = {lane, lane + 32};
+    const bool use[2] = {lane < m, lane + 32 < m};
+    float lk[2] = {use[0] ? lam[lane] : 0.f, use[1] ? lam[lane + 32] : 0.f};
+    twisted_vectors(d, e, e2, m, lk, use, tiny, Y, P, kk);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (!use[t]) continue;
+      float n0 = 0.f, n1 = 0.f, zp = 0.f;
+      for (int x = 0; x < m; ++x) {
+        const float z = Y[x * P + kk[t]];
+        n0 += d[x] * z * z;
+        if (x > 0) n1 += e[x - 1] * zp * z;
+        zp = z;
+      }
+      // stay inside the eigenvalue's own bisection bracket, so that a vector
+      // mixed with a close neighbour cannot move the shift onto that neighbour
+      const float hw = 1.2e-7f * fabsf(lk[t]) + pivmin;
+      lk[t] = fminf(fmaxf(n0 + 2.f * n1, lk[t] - hw), lk[t] + hw);
+    }
+    twisted_vectors(d, e, e2, m, lk, use, tiny, Y, P, kk);
+  }
+  __syncwarp();
+  // Gram-Schmidt inside clusters of close eigenvalues (index order); a member
+  // that loses most of its norm duplicated an earlier one and is recomputed
   const float gtol = 1e-3f * tnorm;
-  const float tiny = 1.2e-7f * tnorm + 1e-30f;
-  for (int half = 0; half < 2; ++half) {
-    const int k = lane + 32 * half;
-    if (!__any_sync(0xffffffffu, k < m)) break;
-    TriLU f;
-    float y[tbk::MAX_NT];
-    if (k < m) {
-      trilu_factor(f, d, e, m, lam[k], tiny);
-      for (int x = 0; x < m; ++x) y[x] = 1.f + 0.25f * (float)(((x * 7 + k * 13) % 17) - 8) / 8.f;
-    }
-    for (int it = 0; it < 3; ++it) {
-      if (k < m) {
-        trilu_solve(f, y, m);
-        float nn = 0.f;
-        for (int x = 0; x < m; ++x) nn += y[x] * y[x];
-        const float s = rsqrtf(fmaxf(nn, 1e-30f));
-        for (int x = 0; x < m; ++x) Y[x * PT + k] = y[x] * s;
-      }
-      __syncwarp();
-      // clusters: runs of consecutive eigenvalues closer than gtol; members
-      // are orthogonalised in index order against the earlier ones
-      const int kb = 32 * half, ke = min(m, kb + 32);
-      for (int kk = 1; kk < m; ++kk) {
-        if (!(lam[kk] - lam[kk - 1] < gtol)) continue;
-        if (kk < kb || kk >= ke) continue;
-        int first = kk - 1;
-        while (first > 0 && lam[first] - lam[first - 1] < gtol) --first;
-        for (int kp2 = first; kp2 < kk; ++kp2) {
-          float dt = 0.f;
-          for (int x = lane; x < m; x += 32) dt += Y[x * PT + kk] * Y[x * PT + kp2];
-          dt = tbk::warp_sum(dt);
-          for (int x = lane; x < m; x += 32) Y[x * PT + kk] -= dt * Y[x * PT + kp2];
-          __syncwarp();
-        }
-        float nn = 0.f;
-        for (int x = lane; x < m; x += 32) nn += Y[x * PT + kk] * Y[x * PT + kk];
-        nn = tbk::warp_sum(nn);
-        const float s = rsqrtf(fmaxf(nn, 1e-30f));
-        for (int x = lane; x < m; x += 32) Y[x * PT + kk] *= s;
-        __syncwarp();
-      }
-      if (k < m)
-        for (int x = 0; x < m; ++x) y[x] = Y[x * PT + k];
-      __syncwarp();
-    }
+  for (int c = 1; c < m; ++c) {
+    if (!(lam[c] - lam[c - 1] < gtol)) continue;
+    int first = c - 1;
+    while (first > 0 && lam[first] - lam[first - 1] < gtol) --first;
+    const float nn = orth_column(Y, P, m, first, c, lane);
+    if (nn < 0.25f) restart_column(d, e, m, lam[c], tiny, Y, P, first, c, fs, lane);
   }
 
-  // ---- back-transformation: eigenvectors of T = H_0 ... H_{m-3} Y; lane
-  // owns columns k = lane, lane + 32
-  for (int j = m - 3; j >= 0; --j) {
-    for (int k = lane; k < m; k += 32) {
-      float t = 0.f;
-      for (int x = j + 1; x < m; ++x) t += H[x * PT + j] * Y[x * PT + k];
-      t *= 2.f;
-      for (int x = j + 1; x < m; ++x) Y[x * PT + k] -= t * H[x * PT + j];
+  // ---- 4. back-transformation U = H_0 ... H_{m-3} Y; lanes own columns
+  // lane and lane + 32
+  {
+    const int k0 = lane, k1 = lane + 32;
+    const bool c0 = k0 < m, c1 = k1 < m;
+    float* y0 = Y + (c0 ? k0 : 0);
+    float* y1 = Y + (c1 ? k1 : 0);
+    for (int j = m - 3; j >= 0; --j) {
+      float s0 = 0.f, s1 = 0.f, t0 = 0.f, t1 = 0.f;
+      int x = j + 1;
+      for (; x + 1 < m; x += 2) {
+        const float hx = H[x * P + j], hx1 = H[(x + 1) * P + j];
+        s0 += hx * y0[x * P];
+        s1 += hx1 * y0[(x + 1) * P];
+        t0 += hx * y1[x * P];
+        t1 += hx1 * y1[(x + 1) * P];
+      }
+      if (x < m) {
+        const float hx = H[x * P + j];
+        s0 += hx * y0[x * P];
+        t0 += hx * y1[x * P];
+      }
+      const float f0 = 2.f * (s0 + s1), f1 = 2.f * (t0 + t1);
+      __syncwarp();
+#pragma unroll 4
+      for (int xx = j + 1; xx < m; ++xx) {
+        const float hx = H[xx * P + j];
+        if (c0) y0[xx * P] -= f0 * hx;
+        if (c1) y1[xx * P] -= f1 * hx;
+      }
     }
   }
   __syncwarp();
-  float* lf = a.lamf + (size_t)i * NT;
-  float* zo = a.Zf + (size_t)i * NT * NT;
-  for (int x = lane; x < m; x += 32) lf[x] = lam[x];
-  for (int x = 0; x < m; ++x)
-    for (int y = lane; y < m; y += 32) zo[x * NT + y] = Y[x * PT + y];
-  if (lane == 0) a.kdim[i] = m;
+
+  if constexpr (!FULL) {
+    float* lf = a.lamf + (size_t)i * NT;
+    float* zo = a.Zf + (size_t)i * NT * NT;
+    for (int x = lane; x < m; x += 32) lf[x] = lam[x];
+    for (int x = 0; x < m; ++x)
+      for (int y = lane; y < m; y += 32) zo[x * NT + y] = Y[x * P + y];
+    if (lane == 0) a.kdim[i] = m;
+    return;
+  } else {
+    // ---- 5. Loewdin U <- U (I - E/2), E = U^T U - I: E into H (aligned
+    // rows), then each lane updates its own rows 16 columns at a time; a chunk
+    // written back before the next chunk is formed changes the result only at
+    // second order in E, below the first-order step's own error.
+    float* E = H;
+    const int PE = epitch(NT);
+    for (int b = lane; b < m; b += 32) {
+      int c = 0;
+      for (; c + 1 < m; c += 2) {
+        float t0 = 0.f, t1 = 0.f;
+        for (int x = 0; x < m; ++x) {
+          const float yb = Y[x * P + b];
+          t0 += Y[x * P + c] * yb;
+          t1 += Y[x * P + c + 1] * yb;
+        }
+        E[c * PE + b] = 0.5f * (t0 - (b == c ? 1.f : 0.f));
+        E[(c + 1) * PE + b] = 0.5f * (t1 - (b == c + 1 ? 1.f : 0.f));
+      }
+      if (c < m) {
+        float t0 = 0.f;
+        for (int x = 0; x < m; ++x) t0 += Y[x * P + c] * Y[x * P + b];
+        E[c * PE + b] = 0.5f * (t0 - (b == c ? 1.f : 0.f));
+      }
+    }
+    __syncwarp();
+    // (columns past m of a chunk read whatever follows in shared memory; their
+    // sums are discarded)
+    for (int x = lane; x < m; x += 32) {
+      float* yx = Y + x * P;
+      for (int b0 = 0; b0 < m; b0 += 16) {
+        float acc[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+        for (int c = 0; c < m; ++c) {
+          const float yc = yx[c];
+          const float4* er = reinterpret_cast<const float4*>(E + c * PE + b0);
+#pragma unroll
+          for (int j4 = 0; j4 < 4; ++j4) {
+            const float4 ev = er[j4];
+            acc[4 * j4 + 0] += yc * ev.x;
+            acc[4 * j4 + 1] += yc * ev.y;
+            acc[4 * j4 + 2] += yc * ev.z;
+            acc[4 * j4 + 3] += yc * ev.w;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (b0 + j < m) yx[b0 + j] -= acc[j];
+      }
+    }
+    __syncwarp();
+    // ---- 6. Rayleigh quotients on the original block-tridiagonal T: row x
+    // couples to the active columns of its own and the adjacent Krylov blocks
+    // (band [blo, bhi) in active indices); T staged as FP32 hi/lo pairs.
+    int* blo = reinterpret_cast<int*>(v);
+    int* bhi = reinterpret_cast<int*>(q);
+    float* Thi = H;                       // [x][12]
+    float* Tlo = H + NT * 12;
+    for (int x = lane; x < m; x += 32) {
+      const int bx = act[x] >> 2;
+      int lo = x, hi = x + 1;
+      while (lo > 0 && (act[lo - 1] >> 2) >= bx - 1) --lo;
+      while (hi < m && (act[hi] >> 2) <= bx + 1) ++hi;
+      blo[x] = lo;
+      bhi[x] = hi;
+      for (int w = 0; w < hi - lo; ++w) {
+        const double tv = Ti[act[x] * NT + act[lo + w]];
+        const float th = (float)tv;
+        Thi[x * 12 + w] = th;
+        Tlo[x * 12 + w] = (float)(tv - (double)th);
+      }
+    }
+    __syncwarp();
+    {
+      const int kk[2] = {lane, lane + 32};
+      const bool use[2] = {lane < m, lane + 32 < m};
+      float nh[2] = {0.f, 0.f}, nl[2] = {0.f, 0.f}, dh[2] = {0.f, 0.f}, dl[2] = {0.f, 0.f};
+      for (int x = 0; x < m; ++x) {
+        const int l0 = blo[x], nw = bhi[x] - l0;
+        float th[2] = {0.f, 0.f}, tl[2] = {0.f, 0.f};
+        for (int w = 0; w < nw; ++w) {
+          const float ah = Thi[x * 12 + w], al = Tlo[x * 12 + w];
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            const float u = use[t] ? Y[(l0 + w) * P + kk[t]] : 0.f;
+            df_fma(th[t], tl[t], ah, u);
+            tl[t] += al * u;
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const float ux = use[t] ? Y[x * P + kk[t]] : 0.f;
+          df_fma(nh[t], nl[t], ux, th[t]);
+          nl[t] += ux * tl[t];
+          df_fma(dh[t], dl[t], ux, ux);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+        if (use[t]) {
+          const double lk = ((double)nh[t] + (double)nl[t]) / ((double)dh[t] + (double)dl[t]);
+          lamd[kk[t]] = lk;
+          if (!isfinite(lk)) tbk::set_status(a.st, TB_ERR_NONFINITE, i);
+        }
+    }
+    __syncwarp();
+    // ---- 7. ascending order (ties by index), spectral record
+    for (int k = lane; k < m; k += 32) {
+      int rk = 0;
+      const double lk = lamd[k];
+      for (int c = 0; c < m; ++c) rk += (lamd[c] < lk) || (lamd[c] == lk && c < k);
+      rank[k] = rk;
+    }
+    __syncwarp();
+    double* lo = a.lambda + (size_t)i * NT;
+    for (int k = lane; k < NT; k += 32) {
+      if (k < m) lo[rank[k]] = lamd[k];
+      else lo[k] = 0.0;
+    }
+    double* So = a.S + (size_t)i * 4 * NT;
+    for (int k = lane; k < NT; k += 32)
+#pragma unroll
+      for (int al = 0; al < 4; ++al) {
+        if (k < m) So[al * NT + rank[k]] = (double)Y[al * P + k];
+        else So[al * NT + k] = 0.0;
+      }
+    // P = Y[rows, active] U: rows staged through H in chunks of RW rows
+    const int deg = a.h_off[i + 1] - a.h_off[i];
+    const size_t rbase = (size_t)(i + a.h_off[i]) * 4;
+    const int nrows = 4 * (deg + 1);
+    const int RW = (int)(xw_hsize(NT) / NT);
+    float* Yr = H;
+    for (int r0 = 0; r0 < nrows; r0 += RW) {
+      const int nr = min(RW, nrows - r0);
+      __syncwarp();
+      for (int x = lane; x < m; x += 32) {
+        const int ax = act[x];
+        int rr = 0;
+        for (; rr + 3 < nr; rr += 4) {        // four independent loads in flight
+          const float y0 = a.Y[(rbase + r0 + rr) * NT + ax];
+          const float y1 = a.Y[(rbase + r0 + rr + 1) * NT + ax];
+          const float y2 = a.Y[(rbase + r0 + rr + 2) * NT + ax];
+          const float y3 = a.Y[(rbase + r0 + rr + 3) * NT + ax];
+          Yr[rr * NT + x] = y0;
+          Yr[(rr + 1) * NT + x] = y1;
+          Yr[(rr + 2) * NT + x] = y2;
+          Yr[(rr + 3) * NT + x] = y3;
+        }
+        for (; rr < nr; ++rr) Yr[rr * NT + x] = a.Y[(rbase + r0 + rr) * NT + ax];
+      }
+      __syncwarp();
+      for (int rr = 0; rr < nr; ++rr) {
+        double* pr = a.P + (rbase + r0 + rr) * NT;
+        const float* yr = Yr + rr * NT;
+        for (int k = lane; k < NT; k += 32) {
+          if (k < m) {
+            float s0 = 0.f, s1 = 0.f;
+            int x = 0;
+            for (; x + 1 < m; x += 2) {
+              s0 += yr[x] * Y[x * P + k];
+              s1 += yr[x + 1] * Y[(x + 1) * P + k];
+            }
+            if (x < m) s0 += yr[x] * Y[x * P + k];
+            pr[rank[k]] = (double)(s0 + s1);
+          } else {
+            pr[k] = 0.0;
+          }
+        }
+      }
+    }
+    if (lane == 0) a.kdim[i] = m;
+  }
 }
 
 // ------------------------------------------------------------------ finishing
@@ -342,11 +730,7 @@ template <typename TV>
 __host__ __device__ inline size_t fin_smem_bytes(int NT) {
   const size_t PT = NT + 1;
   size_t b = sizeof(int) * 4 * NT + sizeof(double) * 4 * NT;   // act, rank, lo, hi; lam, red
-  if (sizeof(TV) == sizeof(float)) {
-    b += sizeof(float) * NT * PT * 3;       // X, E, scratch
-  } else {
-    b += sizeof(double) * NT * PT * 5;      // T, X, W1, Smat, Rmat
-  }
+  b += sizeof(double) * NT * PT * 5;                           // T, X, W1, Smat, Rmat
   return b + 64;
 }
 
@@ -384,136 +768,101 @@ __global__ void __launch_bounds__(FT) eig_finish_kernel(const FinArgs<TV> a) {
   }
   __syncthreads();
 
-  if (sizeof(TV) == sizeof(float)) {
-    // Loewdin orthonormalisation X <- X (I - E/2), E = X^T X - I (inverse
-    // iteration leaves vectors of nearby eigenvalues orthogonal only to
-    // ~eps ||T|| / gap), then FP64 Rayleigh quotients on the final vectors.
-    float* Xf = reinterpret_cast<float*>(X);
-    float* E = Xf + NT * PT;
-    float* X2 = E + NT * PT;
+  {
+  const double* Ti = a.T + (size_t)i * NT * NT;
+  double* Xd = reinterpret_cast<double*>(X);
+  double* Tm = Xd + NT * PT;
+  double* W1 = Tm + NT * PT;
+  double* Sm = W1 + NT * PT;
+  double* Rm = Sm + NT * PT;
+  for (int q = tid; q < m * m; q += FT) {
+    const int x = q / m, y = q - x * m;
+    Tm[x * PT + y] = Ti[act[x] * NT + act[y]];
+  }
+  __syncthreads();
+  {
+    double t2 = 0.0;
+    for (int q = tid; q < m * m; q += FT) {
+      const double v = Tm[(q / m) * PT + q % m];
+      t2 += v * v;
+    }
+    double v1[1] = {t2};
+    tbk::block_sum<double, 1>(v1, red, red + 2 * NT);
+  }
+  const double tnorm = sqrt(red[2 * NT]);
+  // two Ogita-Aishima refinement steps (quadratic convergence from FP32; the
+  // second resolves near-degenerate pairs the first one leaves mixed)
+  for (int it = 0; it < 2; ++it) {
+  for (int q = tid; q < m * m; q += FT) {           // W1 = T X (banded T)
+    const int x = q / m, k = q - x * m;
+    double t = 0.0;
+    for (int y = blo[x]; y < bhi[x]; ++y) t += Tm[x * PT + y] * Xd[y * PT + k];
+    W1[x * PT + k] = t;
+  }
+  __syncthreads();
+  for (int q = tid; q < m * m; q += FT) {           // S = X^T W1, R = I - X^T X
+    const int x = q / m, y = q - x * m;
+    double sv = 0.0, rr = 0.0;
+    for (int l = 0; l < m; ++l) {
+      sv += Xd[l * PT + x] * W1[l * PT + y];
+      rr += Xd[l * PT + x] * Xd[l * PT + y];
+    }
+    Sm[x * PT + y] = sv;
+    Rm[x * PT + y] = (x == y ? 1.0 : 0.0) - rr;
+  }
+  __syncthreads();
+  for (int k = tid; k < m; k += FT) lam[k] = Sm[k * PT + k] / (1.0 - Rm[k * PT + k]);
+  __syncthreads();
+  {
+    double so = 0.0, ro = 0.0;
     for (int q = tid; q < m * m; q += FT) {
       const int x = q / m, y = q - x * m;
-      float t = 0.f;
-      for (int l = 0; l < m; ++l) t += Xf[l * PT + x] * Xf[l * PT + y];
-      E[x * PT + y] = 0.5f * (t - (x == y ? 1.f : 0.f));
+      const double sv = Sm[x * PT + y] - (x == y ? lam[x] : 0.0);
+      so += sv * sv;
+      ro += Rm[x * PT + y] * Rm[x * PT + y];
     }
-    __syncthreads();
-    for (int q = tid; q < m * m; q += FT) {
-      const int x = q / m, k = q - x * m;
-      float t = Xf[x * PT + k];
-      for (int l = 0; l < m; ++l) t -= Xf[x * PT + l] * E[l * PT + k];
-      X2[x * PT + k] = t;
+    double v2[2] = {so, ro};
+    tbk::block_sum<double, 2>(v2, red, red + 2 * NT);
+  }
+  const double delta = 2.0 * (sqrt(red[2 * NT]) + tnorm * sqrt(red[2 * NT + 1]));
+  for (int q = tid; q < m * m; q += FT) {           // E
+    const int x = q / m, y = q - x * m;
+    double ev;
+    if (x == y) {
+      ev = 0.5 * Rm[x * PT + y];
+    } else {
+      const double gap = lam[y] - lam[x];
+      ev = fabs(gap) > delta ? (Sm[x * PT + y] + lam[y] * Rm[x * PT + y]) / gap
+                             : 0.5 * Rm[x * PT + y];
     }
-    __syncthreads();
-    for (int q = tid; q < m * m; q += FT) Xf[(q / m) * PT + q % m] = X2[(q / m) * PT + q % m];
-    __syncthreads();
-    const double* Ti = a.T + (size_t)i * NT * NT;
-    for (int k = tid; k < m; k += FT) {
-      double num = 0.0, den = 0.0;
-      for (int x = 0; x < m; ++x) {
-        double t = 0.0;
-        for (int y = blo[x]; y < bhi[x]; ++y) t += Ti[act[x] * NT + act[y]] * (double)Xf[y * PT + k];
-        num += (double)Xf[x * PT + k] * t;
-        den += (double)Xf[x * PT + k] * (double)Xf[x * PT + k];
-      }
-      lam[k] = num / den;
-    }
-    __syncthreads();
-  } else {
-    const double* Ti = a.T + (size_t)i * NT * NT;
-    double* Xd = reinterpret_cast<double*>(X);
-    double* Tm = Xd + NT * PT;
-    double* W1 = Tm + NT * PT;
-    double* Sm = W1 + NT * PT;
-    double* Rm = Sm + NT * PT;
-    for (int q = tid; q < m * m; q += FT) {
-      const int x = q / m, y = q - x * m;
-      Tm[x * PT + y] = Ti[act[x] * NT + act[y]];
-    }
-    __syncthreads();
-    {
-      double t2 = 0.0;
-      for (int q = tid; q < m * m; q += FT) {
-        const double v = Tm[(q / m) * PT + q % m];
-        t2 += v * v;
-      }
-      double v1[1] = {t2};
-      tbk::block_sum<double, 1>(v1, red, red + 2 * NT);
-    }
-    const double tnorm = sqrt(red[2 * NT]);
-    // two Ogita-Aishima refinement steps (quadratic convergence from FP32; the
-    // second resolves near-degenerate pairs the first one leaves mixed)
-    for (int it = 0; it < 2; ++it) {
-    for (int q = tid; q < m * m; q += FT) {           // W1 = T X (banded T)
-      const int x = q / m, k = q - x * m;
+    W1[x * PT + y] = ev;
+  }
+  __syncthreads();
+  for (int q = tid; q < m * m; q += FT) {           // X + X E -> S
+    const int x = q / m, y = q - x * m;
+    double t = Xd[x * PT + y];
+    for (int l = 0; l < m; ++l) t += Xd[x * PT + l] * W1[l * PT + y];
+    Sm[x * PT + y] = t;
+  }
+  __syncthreads();
+  for (int q = tid; q < m * m; q += FT) {
+    const int x = q / m, y = q - x * m;
+    Xd[x * PT + y] = Sm[x * PT + y];
+  }
+  __syncthreads();
+  }
+  // Rayleigh quotients on the refined vectors
+  for (int k = tid; k < m; k += FT) {
+    double num = 0.0, den = 0.0;
+    for (int x = 0; x < m; ++x) {
       double t = 0.0;
       for (int y = blo[x]; y < bhi[x]; ++y) t += Tm[x * PT + y] * Xd[y * PT + k];
-      W1[x * PT + k] = t;
+      num += Xd[x * PT + k] * t;
+      den += Xd[x * PT + k] * Xd[x * PT + k];
     }
-    __syncthreads();
-    for (int q = tid; q < m * m; q += FT) {           // S = X^T W1, R = I - X^T X
-      const int x = q / m, y = q - x * m;
-      double sv = 0.0, rr = 0.0;
-      for (int l = 0; l < m; ++l) {
-        sv += Xd[l * PT + x] * W1[l * PT + y];
-        rr += Xd[l * PT + x] * Xd[l * PT + y];
-      }
-      Sm[x * PT + y] = sv;
-      Rm[x * PT + y] = (x == y ? 1.0 : 0.0) - rr;
-    }
-    __syncthreads();
-    for (int k = tid; k < m; k += FT) lam[k] = Sm[k * PT + k] / (1.0 - Rm[k * PT + k]);
-    __syncthreads();
-    {
-      double so = 0.0, ro = 0.0;
-      for (int q = tid; q < m * m; q += FT) {
-        const int x = q / m, y = q - x * m;
-        const double sv = Sm[x * PT + y] - (x == y ? lam[x] : 0.0);
-        so += sv * sv;
-        ro += Rm[x * PT + y] * Rm[x * PT + y];
-      }
-      double v2[2] = {so, ro};
-      tbk::block_sum<double, 2>(v2, red, red + 2 * NT);
-    }
-    const double delta = 2.0 * (sqrt(red[2 * NT]) + tnorm * sqrt(red[2 * NT + 1]));
-    for (int q = tid; q < m * m; q += FT) {           // E
-      const int x = q / m, y = q - x * m;
-      double ev;
-      if (x == y) {
-        ev = 0.5 * Rm[x * PT + y];
-      } else {
-        const double gap = lam[y] - lam[x];
-        ev = fabs(gap) > delta ? (Sm[x * PT + y] + lam[y] * Rm[x * PT + y]) / gap
-                               : 0.5 * Rm[x * PT + y];
-      }
-      W1[x * PT + y] = ev;
-    }
-    __syncthreads();
-    for (int q = tid; q < m * m; q += FT) {           // X + X E -> S
-      const int x = q / m, y = q - x * m;
-      double t = Xd[x * PT + y];
-      for (int l = 0; l < m; ++l) t += Xd[x * PT + l] * W1[l * PT + y];
-      Sm[x * PT + y] = t;
-    }
-    __syncthreads();
-    for (int q = tid; q < m * m; q += FT) {
-      const int x = q / m, y = q - x * m;
-      Xd[x * PT + y] = Sm[x * PT + y];
-    }
-    __syncthreads();
-    }
-    // Rayleigh quotients on the refined vectors
-    for (int k = tid; k < m; k += FT) {
-      double num = 0.0, den = 0.0;
-      for (int x = 0; x < m; ++x) {
-        double t = 0.0;
-        for (int y = blo[x]; y < bhi[x]; ++y) t += Tm[x * PT + y] * Xd[y * PT + k];
-        num += Xd[x * PT + k] * t;
-        den += Xd[x * PT + k] * Xd[x * PT + k];
-      }
-      lam[k] = num / den;
-    }
-    __syncthreads();
+    lam[k] = num / den;
+  }
+  __syncthreads();
   }
   // ---- ascending order (ties by index)
   for (int k = tid; k < m; k += FT) {
@@ -557,17 +906,21 @@ __global__ void __launch_bounds__(FT) eig_finish_kernel(const FinArgs<TV> a) {
 
 tb_status eig_configure(tb_ctx* c) {
   const int NT = 4 * c->p.r;
-  c->eig_smem = EW * eig_smem_per_warp(NT);
-  TB_CUDA_TRY(cudaFuncSetAttribute(eig_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)c->eig_smem));
+  const size_t per = xw_smem_per_warp(NT);
+  int xw = (int)((110 * 1024) / per);        // two CTAs per SM
+  if (xw > XW_MAX) xw = XW_MAX;
+  if (xw < 1) xw = 1;
+  c->eig_warps = xw;
+  c->eig_smem = xw * per;
   if (c->p.prec == TB_PREC_FP64) {
+    TB_CUDA_TRY(cudaFuncSetAttribute(eig_warp_kernel<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->eig_smem));
     c->fin_smem = fin_smem_bytes<double>(NT);
     TB_CUDA_TRY(cudaFuncSetAttribute(eig_finish_kernel<double>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->fin_smem));
   } else {
-    c->fin_smem = fin_smem_bytes<float>(NT);
-    TB_CUDA_TRY(cudaFuncSetAttribute(eig_finish_kernel<float>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->fin_smem));
+    TB_CUDA_TRY(cudaFuncSetAttribute(eig_warp_kernel<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->eig_smem));
   }
   return TB_OK;
 }
@@ -577,19 +930,19 @@ tb_status launch_eig(tb_ctx* c, int n, const int* h_off, double* lambda, double*
   if (n <= 0) return TB_OK;
   const int NT = 4 * c->p.r;
   if (c->kry_fused && c->p.prec == TB_PREC_MIXED) return TB_OK;   // done in the Krylov kernel
-  if (!c->kry_fused) {
-    EigArgs ea{n, NT, c->T, c->colmask, c->Zf, c->lamf, kdim, c->d_status};
-    eig_tri_kernel<<<(n + EW - 1) / EW, EW * 32, c->eig_smem, s>>>(ea);
-    TB_CUDA_TRY(cudaGetLastError());
-  }
+  const int xw = c->eig_warps;
+  XArgs xa{n, NT, c->T, c->colmask, reinterpret_cast<const float*>(c->Y), h_off, c->Zf,
+           c->lamf, lambda, S, P, kdim, c->d_status};
   if (c->p.prec == TB_PREC_FP64) {
+    if (!c->kry_fused) {
+      eig_warp_kernel<false><<<(n + xw - 1) / xw, xw * 32, c->eig_smem, s>>>(xa);
+      TB_CUDA_TRY(cudaGetLastError());
+    }
     FinArgs<double> fa{n, NT, c->T, c->colmask, c->Zf, c->lamf,
                        reinterpret_cast<const double*>(c->Y), h_off, lambda, S, P, c->d_status};
     eig_finish_kernel<double><<<n, FT, c->fin_smem, s>>>(fa);
   } else {
-    FinArgs<float> fa{n, NT, c->T, c->colmask, c->Zf, c->lamf,
-                      reinterpret_cast<const float*>(c->Y), h_off, lambda, S, P, c->d_status};
-    eig_finish_kernel<float><<<n, FT, c->fin_smem, s>>>(fa);
+    eig_warp_kernel<true><<<(n + xw - 1) / xw, xw * 32, c->eig_smem, s>>>(xa);
   }
   TB_CUDA_TRY(cudaGetLastError());
   return TB_OK;

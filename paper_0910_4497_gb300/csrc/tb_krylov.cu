@@ -660,15 +660,21 @@ tb_status krylov_configure(tb_ctx* c) {
   int dev = 0, max_smem = 0;
   TB_CUDA_TRY(cudaGetDevice(&dev));
   TB_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  // Placement of the projected eigensolve: the mixed path runs it in the
+  // warp-per-target eigensolver kernel (faster: every target's eigensolve runs
+  // concurrently instead of after its CTA's Lanczos); the FP64 path runs it
+  // inside the Krylov kernel, whose FP32 vectors are the better start for the
+  // FP64 refinement.  TB_EIG_SEPARATE / TB_EIG_FUSED override either choice.
   const bool force_global = getenv("TB_KRYLOV_BASIS_GLOBAL") != nullptr;
-  const bool no_fuse = getenv("TB_EIG_SEPARATE") != nullptr;
+  const bool want_fused = getenv("TB_EIG_FUSED") != nullptr ||
+                          (c->p.prec == TB_PREC_FP64 && getenv("TB_EIG_SEPARATE") == nullptr);
   if (c->p.prec == TB_PREC_FP64) {
-    if (!force_global && !no_fuse && configure_t<double, true, true>(c, max_smem) == TB_OK)
+    if (!force_global && want_fused && configure_t<double, true, true>(c, max_smem) == TB_OK)
       return TB_OK;
     if (!force_global && configure_t<double, true, false>(c, max_smem) == TB_OK) return TB_OK;
     return configure_t<double, false, false>(c, max_smem);
   }
-  if (!force_global && !no_fuse && configure_t<float, true, true>(c, max_smem) == TB_OK)
+  if (!force_global && want_fused && configure_t<float, true, true>(c, max_smem) == TB_OK)
     return TB_OK;
   if (!force_global && configure_t<float, true, false>(c, max_smem) == TB_OK) return TB_OK;
   return configure_t<float, false, false>(c, max_smem);

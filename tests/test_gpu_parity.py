@@ -226,18 +226,19 @@ def test_global_basis_mode_matches(tb):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_separate_eigensolver_kernel_matches(tb, prec):
-    """The projected eigensolve normally runs inside the Krylov kernel; the
-    stand-alone eigensolver kernel (used when the basis cannot be reused as
-    workspace) must give the same answers."""
+def test_eigensolver_placements_match(tb, prec):
+    """The projected eigensolve runs either inside the Krylov kernel (default
+    for FP64) or in the warp-per-target eigensolver kernel (default for the
+    mixed path); the non-default placement must give the same answers."""
     pos, L, p = cfg_system(0)
-    os.environ["TB_EIG_SEPARATE"] = "1"
+    other = "TB_EIG_SEPARATE" if prec == "fp64" else "TB_EIG_FUSED"
+    os.environ[other] = "1"
     try:
-        s_sep, _ = compare_full(tb, "cfg0", pos, L, p, prec)
+        s_alt, _ = compare_full(tb, "cfg0", pos, L, p, prec)
     finally:
-        del os.environ["TB_EIG_SEPARATE"]
-    s_fused, _ = compare_full(tb, "cfg0", pos, L, p, prec)
-    assert np.abs(s_sep.F.cpu().numpy() - s_fused.F.cpu().numpy()).max() <= TOL[prec]["F"]
+        del os.environ[other]
+    s_def, _ = compare_full(tb, "cfg0", pos, L, p, prec)
+    assert np.abs(s_alt.F.cpu().numpy() - s_def.F.cpu().numpy()).max() <= TOL[prec]["F"]
 
 
 def test_single_reorth_pass_within_tolerance(tb):

@@ -354,7 +354,8 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": alg, "kernel_ms": kry_ms}
         stages = {k: (statistics.mean([x for x in v if x >= 0]) if any(x >= 0 for x in v)
                       else None) for k, v in stage_ms.items()}
-        launches_per_step = 12   # 4 list + 1 assembly + 3 Krylov/eig + 1 mu + 3 forces
+        # 4 list + 1 assembly + 1 Krylov + eigensolver (1 mixed, 2 FP64) + 1 mu + 4 forces/energies
+        launches_per_step = 12 if args.prec == "mixed" else 13
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,

@@ -526,6 +526,57 @@ __global__ void __launch_bounds__(XW_MAX * 32) eig_warp_kernel(const XArgs a) {
   }
   __syncwarp();
 
+  // ---- 5. Loewdin U <- U (I - E/2), E = U^T U - I: E into H (aligned
+  // rows), then each lane updates its own rows 16 columns at a time; a chunk
+  // written back before the next chunk is formed changes the result only at
+  // second order in E, below the first-order step's own error.
+  float* E = H;
+  const int PE = epitch(NT);
+  for (int b = lane; b < m; b += 32) {
+    int c = 0;
+    for (; c + 1 < m; c += 2) {
+      float t0 = 0.f, t1 = 0.f;
+      for (int x = 0; x < m; ++x) {
+        const float yb = Y[x * P + b];
+        t0 += Y[x * P + c] * yb;
+        t1 += Y[x * P + c + 1] * yb;
+      }
+      E[c * PE + b] = 0.5f * (t0 - (b == c ? 1.f : 0.f));
+      E[(c + 1) * PE + b] = 0.5f * (t1 - (b == c + 1 ? 1.f : 0.f));
+    }
+    if (c < m) {
+      float t0 = 0.f;
+      for (int x = 0; x < m; ++x) t0 += Y[x * P + c] * Y[x * P + b];
+      E[c * PE + b] = 0.5f * (t0 - (b == c ? 1.f : 0.f));
+    }
+  }
+  __syncwarp();
+  // (columns past m of a chunk read whatever follows in shared memory; their
+  // sums are discarded)
+  for (int x = lane; x < m; x += 32) {
+    float* yx = Y + x * P;
+    for (int b0 = 0; b0 < m; b0 += 16) {
+      float acc[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+      for (int c = 0; c < m; ++c) {
+        const float yc = yx[c];
+        const float4* er = reinterpret_cast<const float4*>(E + c * PE + b0);
+#pragma unroll
+        for (int j4 = 0; j4 < 4; ++j4) {
+          const float4 ev = er[j4];
+          acc[4 * j4 + 0] += yc * ev.x;
+          acc[4 * j4 + 1] += yc * ev.y;
+          acc[4 * j4 + 2] += yc * ev.z;
+          acc[4 * j4 + 3] += yc * ev.w;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (b0 + j < m) yx[b0 + j] -= acc[j];
+    }
+  }
+  __syncwarp();
   if constexpr (!FULL) {
     float* lf = a.lamf + (size_t)i * NT;
     float* zo = a.Zf + (size_t)i * NT * NT;
@@ -535,57 +586,6 @@ __global__ void __launch_bounds__(XW_MAX * 32) eig_warp_kernel(const XArgs a) {
     if (lane == 0) a.kdim[i] = m;
     return;
   } else {
-    // ---- 5. Loewdin U <- U (I - E/2), E = U^T U - I: E into H (aligned
-    // rows), then each lane updates its own rows 16 columns at a time; a chunk
-    // written back before the next chunk is formed changes the result only at
-    // second order in E, below the first-order step's own error.
-    float* E = H;
-    const int PE = epitch(NT);
-    for (int b = lane; b < m; b += 32) {
-      int c = 0;
-      for (; c + 1 < m; c += 2) {
-        float t0 = 0.f, t1 = 0.f;
-        for (int x = 0; x < m; ++x) {
-          const float yb = Y[x * P + b];
-          t0 += Y[x * P + c] * yb;
-          t1 += Y[x * P + c + 1] * yb;
-        }
-        E[c * PE + b] = 0.5f * (t0 - (b == c ? 1.f : 0.f));
-        E[(c + 1) * PE + b] = 0.5f * (t1 - (b == c + 1 ? 1.f : 0.f));
-      }
-      if (c < m) {
-        float t0 = 0.f;
-        for (int x = 0; x < m; ++x) t0 += Y[x * P + c] * Y[x * P + b];
-        E[c * PE + b] = 0.5f * (t0 - (b == c ? 1.f : 0.f));
-      }
-    }
-    __syncwarp();
-    // (columns past m of a chunk read whatever follows in shared memory; their
-    // sums are discarded)
-    for (int x = lane; x < m; x += 32) {
-      float* yx = Y + x * P;
-      for (int b0 = 0; b0 < m; b0 += 16) {
-        float acc[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) acc[j] = 0.f;
-        for (int c = 0; c < m; ++c) {
-          const float yc = yx[c];
-          const float4* er = reinterpret_cast<const float4*>(E + c * PE + b0);
-#pragma unroll
-          for (int j4 = 0; j4 < 4; ++j4) {
-            const float4 ev = er[j4];
-            acc[4 * j4 + 0] += yc * ev.x;
-            acc[4 * j4 + 1] += yc * ev.y;
-            acc[4 * j4 + 2] += yc * ev.z;
-            acc[4 * j4 + 3] += yc * ev.w;
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (b0 + j < m) yx[b0 + j] -= acc[j];
-      }
-    }
-    __syncwarp();
     // ---- 6. Rayleigh quotients on the original block-tridiagonal T: row x
     // couples to the active columns of its own and the adjacent Krylov blocks
     // (band [blo, bhi) in active indices); T staged as FP32 hi/lo pairs.

@@ -146,6 +146,7 @@ struct tb_ctx {
   size_t kry_smem = 0;
   bool kry_vsmem = false;
   bool kry_fused = false;           // projected eigensolve inside the Krylov kernel
+  int kry_threads = 256;            // threads per Krylov CTA
   int eig_grid = 0;
   int eig_warps = 0;                 // targets per CTA of the warp eigensolver
   size_t eig_smem = 0;

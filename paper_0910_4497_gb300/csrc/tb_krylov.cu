@@ -31,13 +31,13 @@
 
 namespace {
 
-constexpr int KT = 256;
-constexpr int KW = KT / 32;
+constexpr int KT_MAX = 256;        // threads per CTA (the fused eigensolve needs 256)
+constexpr int KW_MAX = KT_MAX / 32;
 // flags[0..KW): warp totals of the block scan; then the column mask and the
 // active-column bits of the newest block.
-constexpr int FL_MASK = KW;
-constexpr int FL_ACT = KW + 2;
-constexpr int FL_OK = KW + 3;
+constexpr int FL_MASK = KW_MAX;
+constexpr int FL_ACT = KW_MAX + 2;
+constexpr int FL_OK = KW_MAX + 3;
 
 template <typename TV>
 struct alignas(4 * sizeof(TV)) vec4 {
@@ -105,7 +105,7 @@ __host__ __device__ __forceinline__ size_t align32(size_t x) { return (x + 31) &
 template <typename TV>
 __host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, bool vsmem) {
   const size_t Dmax = 4 * (size_t)max_cluster;
-  const size_t np = (size_t)(r > KW ? r : KW);
+  const size_t np = (size_t)(r > KW_MAX ? r : KW_MAX);
   size_t b = 0;
   b += align32(sizeof(int) * max_cluster);            // cl
   b += align32(sizeof(int) * (max_cluster + 1));      // rowptr
@@ -115,7 +115,7 @@ __host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, bool vs
   b += align32(sizeof(TV) * 16 * r);                  // projection coefficients
   b += align32(sizeof(TV) * 16 * 4);                  // B_{k-1}, Gram, R, R^{-1}
   b += align32(sizeof(double) * 16 * 2);              // B_k, first Cholesky factor
-  b += align32(sizeof(TV) * 16 * KW);                 // reduction scratch
+  b += align32(sizeof(TV) * 16 * KW_MAX);             // reduction scratch
   b += align32(sizeof(int) * 16);                     // flags
   return b;
 }
@@ -167,8 +167,11 @@ __device__ __forceinline__ void triinv4(const TV (&R)[16], TV (&X)[16]) {
   }
 }
 
-template <typename TV, bool VSMEM, bool FUSED>
-__global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
+template <typename TV, bool VSMEM, bool FUSED, int KT>
+__global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryArgs<TV> a) {
+  constexpr int KW = KT / 32;
+  static_assert(KT == 128 || KT == 256, "128 or 256 threads");
+  static_assert(!FUSED || KT == 256, "the fused eigensolve runs on 256 threads");
   extern __shared__ __align__(32) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r = a.r, NT = 4 * r, Dmax = 4 * a.max_cluster;
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
   TV* Rish = Rsh + 16;                               off += align32(sizeof(TV) * 64);
   double* Bs = reinterpret_cast<double*>(smem + off);
   double* R1s = Bs + 16;                             off += align32(sizeof(double) * 32);
-  TV* red = reinterpret_cast<TV*>(smem + off);       off += align32(sizeof(TV) * 16 * KW);
+  TV* red = reinterpret_cast<TV*>(smem + off);       off += align32(sizeof(TV) * 16 * KW_MAX);
   int* flags = reinterpret_cast<int*>(smem + off);
   int2* lent = a.lent + (size_t)blockIdx.x * a.max_cluster * a.max_hnbr;
   const TV Es = (TV)a.Es, Ep = (TV)a.Ep;
@@ -607,7 +610,7 @@ __global__ void __launch_bounds__(KT) krylov_kernel(const KryArgs<TV> a) {
   }
 }
 
-template <typename TV, bool VSMEM, bool FUSED>
+template <typename TV, bool VSMEM, bool FUSED, int KT>
 tb_status launch_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int* h_off,
                    const int* h_idx, const TV* H, double* lambda, double* S, double* P,
                    int* kdim, cudaStream_t s) {
@@ -622,28 +625,30 @@ tb_status launch_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const i
   a.lamf = c->lamf; a.Zf = c->Zf; a.lambda = lambda; a.S = S; a.P = P; a.kdim = kdim;
   const int grid = n < c->kry_grid ? n : c->kry_grid;
   if (grid <= 0) return TB_OK;
-  krylov_kernel<TV, VSMEM, FUSED><<<grid, KT, c->kry_smem, s>>>(a);
+  krylov_kernel<TV, VSMEM, FUSED, KT><<<grid, KT, c->kry_smem, s>>>(a);
   TB_CUDA_TRY(cudaGetLastError());
   return TB_OK;
 }
 
-template <typename TV, bool VSMEM, bool FUSED>
+template <typename TV, bool VSMEM, bool FUSED, int KT>
 tb_status configure_t(tb_ctx* c, int max_smem) {
   const size_t bytes = kry_smem_bytes<TV>(c->p.r, c->p.max_cluster, VSMEM);
   if ((int)bytes > max_smem) return TB_ERR_CAPACITY;
+  if (c->p.max_cluster > 4 * KT) return TB_ERR_CAPACITY;   // block scan: 4 slots per thread
   if (FUSED) {   // the eigensolve workspace must fit where the basis was
     const size_t basis = sizeof(TV) * 4 * (size_t)c->p.max_cluster * 4 * c->p.r;
     if (sizeof(float) * tbtail::tail_floats(4 * c->p.r) > basis) return TB_ERR_CAPACITY;
   }
-  TB_CUDA_TRY(cudaFuncSetAttribute(krylov_kernel<TV, VSMEM, FUSED>,
+  TB_CUDA_TRY(cudaFuncSetAttribute(krylov_kernel<TV, VSMEM, FUSED, KT>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   int occ = 0;
   TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &occ, krylov_kernel<TV, VSMEM, FUSED>, KT, bytes));
+      &occ, krylov_kernel<TV, VSMEM, FUSED, KT>, KT, bytes));
   if (occ < 1) return TB_ERR_CAPACITY;
   c->kry_smem = bytes;
   c->kry_vsmem = VSMEM;
   c->kry_fused = FUSED;
+  c->kry_threads = KT;
   c->kry_grid = c->num_sms * occ;
   return TB_OK;
 }
@@ -660,47 +665,46 @@ tb_status krylov_configure(tb_ctx* c) {
   int dev = 0, max_smem = 0;
   TB_CUDA_TRY(cudaGetDevice(&dev));
   TB_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  // Placement of the projected eigensolve: the mixed path runs it in the
-  // warp-per-target eigensolver kernel (faster: every target's eigensolve runs
-  // concurrently instead of after its CTA's Lanczos); the FP64 path runs it
-  // inside the Krylov kernel, whose FP32 vectors are the better start for the
-  // FP64 refinement.  TB_EIG_SEPARATE / TB_EIG_FUSED override either choice.
-  const bool force_global = getenv("TB_KRYLOV_BASIS_GLOBAL") != nullptr;
-  const bool want_fused = getenv("TB_EIG_FUSED") != nullptr ||
-                          (c->p.prec == TB_PREC_FP64 && getenv("TB_EIG_SEPARATE") == nullptr);
+  // Default: 128-thread CTAs with the basis in a per-CTA slot of global memory
+  // (L2-resident; four targets in flight per SM instead of two), and the
+  // projected eigensolve in the warp-per-target eigensolver kernel.
+  // Alternatives, for comparison and tests: TB_KRYLOV_WIDE (256 threads, basis
+  // in shared memory), TB_EIG_FUSED (256 threads, eigensolve inside the
+  // Krylov kernel in the shared memory the basis used).
+  const bool fused = getenv("TB_EIG_FUSED") != nullptr;
+  const bool wide = getenv("TB_KRYLOV_WIDE") != nullptr;
   if (c->p.prec == TB_PREC_FP64) {
-    if (!force_global && want_fused && configure_t<double, true, true>(c, max_smem) == TB_OK)
-      return TB_OK;
-    if (!force_global && configure_t<double, true, false>(c, max_smem) == TB_OK) return TB_OK;
-    return configure_t<double, false, false>(c, max_smem);
+    if (fused && configure_t<double, true, true, 256>(c, max_smem) == TB_OK) return TB_OK;
+    if (wide && configure_t<double, true, false, 256>(c, max_smem) == TB_OK) return TB_OK;
+    if (configure_t<double, false, false, 128>(c, max_smem) == TB_OK) return TB_OK;
+    return configure_t<double, false, false, 256>(c, max_smem);
   }
-  if (!force_global && want_fused && configure_t<float, true, true>(c, max_smem) == TB_OK)
-    return TB_OK;
-  if (!force_global && configure_t<float, true, false>(c, max_smem) == TB_OK) return TB_OK;
-  return configure_t<float, false, false>(c, max_smem);
+  if (fused && configure_t<float, true, true, 256>(c, max_smem) == TB_OK) return TB_OK;
+  if (wide && configure_t<float, true, false, 256>(c, max_smem) == TB_OK) return TB_OK;
+  if (configure_t<float, false, false, 128>(c, max_smem) == TB_OK) return TB_OK;
+  return configure_t<float, false, false, 256>(c, max_smem);
 }
 
 tb_status launch_krylov(tb_ctx* c, int n, const int* c_off, const int* c_idx,
                         const int* h_off, const int* h_idx, const double* Hblk,
                         const float* Hmir, double* lambda, double* S, double* P, int* kdim,
                         cudaStream_t s) {
-  if (c->p.prec == TB_PREC_FP64) {
-    if (c->kry_fused)
-      return launch_t<double, true, true>(c, n, c_off, c_idx, h_off, h_idx, Hblk, lambda, S, P,
-                                          kdim, s);
-    if (c->kry_vsmem)
-      return launch_t<double, true, false>(c, n, c_off, c_idx, h_off, h_idx, Hblk, lambda, S,
-                                           P, kdim, s);
-    return launch_t<double, false, false>(c, n, c_off, c_idx, h_off, h_idx, Hblk, lambda, S, P,
-                                          kdim, s);
-  }
+#define TB_KRY_DISPATCH(TV, H)                                                                  \
+  do {                                                                                          \
+    if (c->kry_fused)                                                                           \
+      return launch_t<TV, true, true, 256>(c, n, c_off, c_idx, h_off, h_idx, H, lambda, S, P,   \
+                                           kdim, s);                                            \
+    if (c->kry_vsmem)                                                                           \
+      return launch_t<TV, true, false, 256>(c, n, c_off, c_idx, h_off, h_idx, H, lambda, S, P,  \
+                                            kdim, s);                                           \
+    if (c->kry_threads == 128)                                                                  \
+      return launch_t<TV, false, false, 128>(c, n, c_off, c_idx, h_off, h_idx, H, lambda, S, P, \
+                                             kdim, s);                                          \
+    return launch_t<TV, false, false, 256>(c, n, c_off, c_idx, h_off, h_idx, H, lambda, S, P,   \
+                                           kdim, s);                                            \
+  } while (0)
+  if (c->p.prec == TB_PREC_FP64) TB_KRY_DISPATCH(double, Hblk);
   if (!Hmir) return TB_ERR_INVALID_ARG;
-  if (c->kry_fused)
-    return launch_t<float, true, true>(c, n, c_off, c_idx, h_off, h_idx, Hmir, lambda, S, P,
-                                       kdim, s);
-  if (c->kry_vsmem)
-    return launch_t<float, true, false>(c, n, c_off, c_idx, h_off, h_idx, Hmir, lambda, S, P,
-                                        kdim, s);
-  return launch_t<float, false, false>(c, n, c_off, c_idx, h_off, h_idx, Hmir, lambda, S, P,
-                                       kdim, s);
+  TB_KRY_DISPATCH(float, Hmir);
+#undef TB_KRY_DISPATCH
 }

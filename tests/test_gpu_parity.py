@@ -210,33 +210,19 @@ def test_forces_bridged_uneven_clusters(tb):
     assert sizes.max() - sizes.min() >= 20
 
 
-def test_global_basis_mode_matches(tb):
-    pos, L, p = cfg_system(0)
-    os.environ["TB_KRYLOV_BASIS_GLOBAL"] = "1"
-    try:
-        s_glob = run(tb, pos, L, p, "mixed")
-    finally:
-        del os.environ["TB_KRYLOV_BASIS_GLOBAL"]
-    s_sm = run(tb, pos, L, p, "mixed")
-    # the global-basis variant also uses the stand-alone eigensolver kernel, so
-    # the two agree to the mixed-path tolerance, not bit for bit
-    assert np.abs(s_glob.F.cpu().numpy() - s_sm.F.cpu().numpy()).max() <= TOL["mixed"]["F"]
-    ref = oracle_result("cfg0", pos, L, p)
-    assert np.abs(s_glob.F.cpu().numpy() - ref.F).max() <= TOL["mixed"]["F"]
-
-
+@pytest.mark.parametrize("variant", ["TB_KRYLOV_WIDE", "TB_EIG_FUSED"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_eigensolver_placements_match(tb, prec):
-    """The projected eigensolve runs either inside the Krylov kernel (default
-    for FP64) or in the warp-per-target eigensolver kernel (default for the
-    mixed path); the non-default placement must give the same answers."""
+def test_kernel_variants_match(tb, prec, variant):
+    """Default: 128-thread Krylov CTAs with the basis in global memory and the
+    warp-per-target eigensolver.  The alternatives (256 threads with the basis
+    in shared memory; the eigensolve fused into the Krylov kernel) must give
+    the same answers within the path's tolerance, and match the oracle."""
     pos, L, p = cfg_system(0)
-    other = "TB_EIG_SEPARATE" if prec == "fp64" else "TB_EIG_FUSED"
-    os.environ[other] = "1"
+    os.environ[variant] = "1"
     try:
         s_alt, _ = compare_full(tb, "cfg0", pos, L, p, prec)
     finally:
-        del os.environ[other]
+        del os.environ[variant]
     s_def, _ = compare_full(tb, "cfg0", pos, L, p, prec)
     assert np.abs(s_alt.F.cpu().numpy() - s_def.F.cpu().numpy()).max() <= TOL[prec]["F"]
 

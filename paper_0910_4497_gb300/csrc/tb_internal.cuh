@@ -147,6 +147,7 @@ struct tb_ctx {
   bool kry_vsmem = false;
   bool kry_fused = false;           // projected eigensolve inside the Krylov kernel
   int kry_threads = 256;            // threads per Krylov CTA
+  bool kry_lsmem = false;           // local CSR of the Krylov kernel in shared memory
   int eig_grid = 0;
   int eig_warps = 0;                 // targets per CTA of the warp eigensolver
   size_t eig_smem = 0;

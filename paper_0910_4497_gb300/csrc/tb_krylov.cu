@@ -80,6 +80,7 @@ struct KryArgs {
   unsigned long long* colmask;
   TV* Vg;
   int2* lent;
+  int lent_smem;            // 1: the local CSR lives in shared memory
   int* st;
   // fused eigensolve outputs
   float* lamf;
@@ -103,7 +104,8 @@ __device__ __forceinline__ int find_slot(const int* cl, int nc, int b) {
 __host__ __device__ __forceinline__ size_t align32(size_t x) { return (x + 31) & ~size_t(31); }
 
 template <typename TV>
-__host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, bool vsmem) {
+__host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, int max_hnbr, bool vsmem,
+                                                 bool lsmem) {
   const size_t Dmax = 4 * (size_t)max_cluster;
   const size_t np = (size_t)(r > KW_MAX ? r : KW_MAX);
   size_t b = 0;
@@ -111,6 +113,8 @@ __host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, bool vs
   b += align32(sizeof(int) * (max_cluster + 1));      // rowptr
   b += align32(sizeof(TV) * Dmax * 4);                // W
   if (vsmem) b += align32(sizeof(TV) * Dmax * 4 * r); // basis
+  else b += align32(sizeof(TV) * Dmax * 4);          // copy of the current block
+  if (lsmem) b += align32(sizeof(int2) * (size_t)max_cluster * max_hnbr);  // local CSR
   b += align32(sizeof(TV) * 16 * np);                 // projection partials
   b += align32(sizeof(TV) * 16 * r);                  // projection coefficients
   b += align32(sizeof(TV) * 16 * 4);                  // B_{k-1}, Gram, R, R^{-1}
@@ -123,17 +127,22 @@ __host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, bool vs
 // Cholesky of a 4x4 Gram matrix g (row-major) into the upper-triangular R
 // (row-major); returns false when a pivot is not a healthy fraction of its
 // diagonal or falls near the deflation threshold.
+// `well` reports whether every pivot keeps at least a quarter of its diagonal
+// (then kappa(W)^2 <= ~16 and one Cholesky-QR pass is orthogonal to ~16 eps).
 template <typename TV>
-__device__ __forceinline__ bool chol4(const TV (&g)[16], TV (&R)[16], TV rel, double abs_tol) {
+__device__ __forceinline__ bool chol4(const TV (&g)[16], TV (&R)[16], TV rel, double abs_tol,
+                                      bool& well) {
 #pragma unroll
   for (int q = 0; q < 16; ++q) R[q] = (TV)0;
   bool ok = true;
+  well = true;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     TV d = g[c * 4 + c];
 #pragma unroll
     for (int j = 0; j < c; ++j) d -= R[j * 4 + c] * R[j * 4 + c];
     if (!(d > rel * g[c * 4 + c]) || !(d > (TV)(abs_tol * abs_tol))) ok = false;
+    if (!(d >= (TV)0.25 * g[c * 4 + c])) well = false;
     const TV dd = d > (TV)0 ? d : (TV)1;
     const TV inv = (TV)rsqrt(dd);
     const TV rc = dd * inv;
@@ -181,11 +190,19 @@ __global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryAr
   int* rowptr = reinterpret_cast<int*>(smem + off);  off += align32(sizeof(int) * (a.max_cluster + 1));
   TV* W = reinterpret_cast<TV*>(smem + off);         off += align32(sizeof(TV) * Dmax * 4);
   TV* V;
+  TV* Vks = nullptr;                                 // copy of the current block (global basis)
   if (VSMEM) {
     V = reinterpret_cast<TV*>(smem + off);
     off += align32(sizeof(TV) * (size_t)Dmax * 4 * r);
   } else {
     V = a.Vg + (size_t)blockIdx.x * Dmax * 4 * r;
+    Vks = reinterpret_cast<TV*>(smem + off);
+    off += align32(sizeof(TV) * (size_t)Dmax * 4);
+  }
+  int2* lent = a.lent + (size_t)blockIdx.x * a.max_cluster * a.max_hnbr;   // local CSR
+  if (a.lent_smem) {
+    lent = reinterpret_cast<int2*>(smem + off);
+    off += align32(sizeof(int2) * (size_t)a.max_cluster * a.max_hnbr);
   }
   TV* Cp = reinterpret_cast<TV*>(smem + off);        off += align32(sizeof(TV) * 16 * np);
   TV* Cc = reinterpret_cast<TV*>(smem + off);        off += align32(sizeof(TV) * 16 * r);
@@ -197,7 +214,6 @@ __global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryAr
   double* R1s = Bs + 16;                             off += align32(sizeof(double) * 32);
   TV* red = reinterpret_cast<TV*>(smem + off);       off += align32(sizeof(TV) * 16 * KW_MAX);
   int* flags = reinterpret_cast<int*>(smem + off);
-  int2* lent = a.lent + (size_t)blockIdx.x * a.max_cluster * a.max_hnbr;
   const TV Es = (TV)a.Es, Ep = (TV)a.Ep;
   // Cholesky-QR acceptance: each pivot must keep this fraction of its diagonal
   const TV chol_rel = sizeof(TV) == 4 ? (TV)1e-3 : (TV)1e-8;
@@ -292,6 +308,11 @@ __global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryAr
     for (int k = 0; k < r; ++k) {
       const TV* Vk = V + (size_t)k * Dmax * 4;
       const TV* Vp = V + (size_t)(k > 0 ? k - 1 : 0) * Dmax * 4;
+      if constexpr (!VSMEM) {            // the sweep reads V_k rows many times: stage it
+        for (int q = tid; q < D; q += KT) st4(Vks + q * 4, ld4(Vk + q * 4));
+        __syncthreads();
+        Vk = Vks;
+      }
       // ---- W = H_c V_k - V_{k-1} B_{k-1}^T ; item (s, alpha) = one row of W
       for (int it = tid; it < 4 * nc; it += KT) {
         const int s = it >> 2, al = it & 3;
@@ -343,6 +364,7 @@ __global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryAr
           TV acc[16];
 #pragma unroll
           for (int q = 0; q < 16; ++q) acc[q] = (TV)0;
+#pragma unroll 4
           for (int row = rlo + lane; row < rhi; row += 32) {
             const vec4<TV> v = ld4(Vb + row * 4);
             const vec4<TV> x = ld4(W + row * 4);
@@ -371,6 +393,7 @@ __global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryAr
         const bool last = pass == passes - 1;
         for (int row = tid; row < D; row += KT) {
           vec4<TV> x = ld4(W + row * 4);
+#pragma unroll 4
           for (int b = 0; b <= k; ++b) {
             const vec4<TV> v = ld4(V + (size_t)b * Dmax * 4 + row * 4);
             const TV* cb = Cc + b * 16;
@@ -393,7 +416,8 @@ __global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryAr
         if (!last) __syncthreads();         // the Gram reduction below synchronises
       }
       if (k == r - 1) break;
-      // ---- in-block QR: W = V_{k+1} B_k.  Cholesky QR twice; the MGS path
+      // ---- in-block QR: W = V_{k+1} B_k.  Cholesky QR twice (once in FP32 when
+      // the first factor shows a well-conditioned block); the MGS path
       // takes over when a pivot signals ill-conditioning or deflation.
       TV* Vn = V + (size_t)(k + 1) * Dmax * 4;
       int chol_state = 0;   // 1: first factor refused (W untouched); 2: second refused
@@ -408,21 +432,25 @@ __global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryAr
 #pragma unroll
             for (int e = c; e < 4; ++e) { G[c * 4 + e] = Gs[q]; G[e * 4 + c] = Gs[q]; ++q; }
           TV R[16], Ri[16];
-          const bool ok = chol4(G, R, chol_rel, cq == 0 ? chol_abs : 0.0);
+          bool well;
+          const bool ok = chol4(G, R, chol_rel, cq == 0 ? chol_abs : 0.0, well);
           triinv4(R, Ri);
 #pragma unroll
           for (int q2 = 0; q2 < 16; ++q2) { Rsh[q2] = R[q2]; Rish[q2] = Ri[q2]; }
-          flags[FL_OK] = ok ? 1 : 0;
+          // FP32 path: a well-conditioned block needs no second pass
+          flags[FL_OK] = ok ? ((cq == 0 && well && sizeof(TV) == 4) ? 2 : 1) : 0;
         }
         __syncthreads();
-        if (!flags[FL_OK]) {        // uniform: every thread reads the same flag
+        const int okf = flags[FL_OK];
+        if (!okf) {                 // uniform: every thread reads the same flag
           chol_state = cq + 1;
           break;
         }
+        const bool single = okf == 2;
         TV R[16], Ri[16];
 #pragma unroll
         for (int q2 = 0; q2 < 16; ++q2) { R[q2] = Rsh[q2]; Ri[q2] = Rish[q2]; }
-        TV* dst = cq == 0 ? W : Vn;
+        TV* dst = (cq == 0 && !single) ? W : Vn;
 #pragma unroll
         for (int q = 0; q < 10; ++q) g[q] = (TV)0;
         for (int row = tid; row < D; row += KT) {
@@ -436,13 +464,22 @@ __global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryAr
             y.v[c] = t;
           }
           st4(dst + row * 4, y);
-          if (cq == 0) {                    // Gram matrix for the second factor
+          if (cq == 0 && !single) {         // Gram matrix for the second factor
             int q = 0;
 #pragma unroll
             for (int c = 0; c < 4; ++c)
 #pragma unroll
               for (int e = c; e < 4; ++e) g[q++] += y.v[c] * y.v[e];
           }
+        }
+        if (single) {                       // B_k = R1, done
+          if (tid == 0) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) Bs[q] = (double)R[q];
+            flags[FL_ACT] = 0xF;
+          }
+          __syncthreads();
+          break;
         }
         if (tid == 0) {
           if (cq == 0) {
@@ -622,6 +659,7 @@ tb_status launch_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const i
   a.c_off = c_off; a.c_idx = c_idx; a.h_off = h_off; a.h_idx = h_idx; a.H = H;
   a.T = c->T; a.Y = reinterpret_cast<TV*>(c->Y); a.colmask = c->colmask;
   a.Vg = reinterpret_cast<TV*>(c->Vg); a.lent = c->lent; a.st = c->d_status;
+  a.lent_smem = c->kry_lsmem ? 1 : 0;
   a.lamf = c->lamf; a.Zf = c->Zf; a.lambda = lambda; a.S = S; a.P = P; a.kdim = kdim;
   const int grid = n < c->kry_grid ? n : c->kry_grid;
   if (grid <= 0) return TB_OK;
@@ -632,19 +670,27 @@ tb_status launch_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const i
 
 template <typename TV, bool VSMEM, bool FUSED, int KT>
 tb_status configure_t(tb_ctx* c, int max_smem) {
-  const size_t bytes = kry_smem_bytes<TV>(c->p.r, c->p.max_cluster, VSMEM);
-  if ((int)bytes > max_smem) return TB_ERR_CAPACITY;
+  // the local CSR goes to shared memory when that keeps the occupancy
+  const size_t b0 = kry_smem_bytes<TV>(c->p.r, c->p.max_cluster, c->p.max_hnbr, VSMEM, false);
+  const size_t b1 = kry_smem_bytes<TV>(c->p.r, c->p.max_cluster, c->p.max_hnbr, VSMEM, true);
+  if ((int)b0 > max_smem) return TB_ERR_CAPACITY;
   if (c->p.max_cluster > 4 * KT) return TB_ERR_CAPACITY;   // block scan: 4 slots per thread
   if (FUSED) {   // the eigensolve workspace must fit where the basis was
     const size_t basis = sizeof(TV) * 4 * (size_t)c->p.max_cluster * 4 * c->p.r;
     if (sizeof(float) * tbtail::tail_floats(4 * c->p.r) > basis) return TB_ERR_CAPACITY;
   }
+  const size_t bmax = (int)b1 <= max_smem ? b1 : b0;
   TB_CUDA_TRY(cudaFuncSetAttribute(krylov_kernel<TV, VSMEM, FUSED, KT>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  int occ = 0;
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bmax));
+  int occ = 0, occ1 = 0;
   TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &occ, krylov_kernel<TV, VSMEM, FUSED, KT>, KT, bytes));
+      &occ, krylov_kernel<TV, VSMEM, FUSED, KT>, KT, b0));
   if (occ < 1) return TB_ERR_CAPACITY;
+  if (bmax == b1)
+    TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ1, krylov_kernel<TV, VSMEM, FUSED, KT>, KT, b1));
+  c->kry_lsmem = occ1 >= occ;
+  const size_t bytes = c->kry_lsmem ? b1 : b0;
   c->kry_smem = bytes;
   c->kry_vsmem = VSMEM;
   c->kry_fused = FUSED;

@@ -37,7 +37,7 @@
 namespace {
 
 constexpr int FT = 128;            // threads per CTA in the finishing kernel
-constexpr int XW_MAX = 8;          // warps (targets) per CTA in eig_warp_kernel
+constexpr int XW_MAX = 6;          // targets (64-thread groups) per CTA in eig_warp_kernel
 
 struct XArgs {
   int n, NT;
@@ -67,15 +67,40 @@ __host__ __device__ inline size_t xw_hsize(int NT) {
   return a > b ? a : b;
 }
 
-__host__ __device__ inline size_t xw_smem_per_warp(int NT) {
+constexpr int GT = 64;             // threads per target (two warps)
+constexpr int NSLICE = 2 * GT;     // spectrum-slicing points
+
+__host__ __device__ inline size_t xw_smem_per_warp(int NT) {   // per target
   size_t b = sizeof(double) * NT;                          // lamd
-  b += sizeof(float) * (xw_hsize(NT) + (size_t)NT * xpitch(NT) + 11 * (size_t)NT + 64);
+  b += sizeof(float) * (xw_hsize(NT) + (size_t)NT * xpitch(NT) + 11 * (size_t)NT + NSLICE + 8);
   b += sizeof(int) * 2 * NT;                               // act, rank
   return (b + 15) & ~size_t(15);
 }
 
+// The two warps of a target synchronise on their own named barrier.
+struct Grp {
+  int t;        // thread in the target's group, 0..63
+  int wl;       // lane in its warp
+  int gw;       // warp in the group
+  int bid;      // named barrier id
+  float* red;   // 8 floats of scratch
+};
+
+__device__ __forceinline__ void gsync(const Grp& g) {
+  asm volatile("bar.sync %0, 64;" ::"r"(g.bid) : "memory");
+}
+
+__device__ __forceinline__ float gsum(const Grp& g, float v) {
+  v = tbk::warp_sum(v);
+  if (g.wl == 0) g.red[g.gw] = v;
+  gsync(g);
+  const float tot = g.red[0] + g.red[1];
+  gsync(g);
+  return tot;
+}
+
 // Sturm counts (number of eigenvalues below x) at two points at once: two
-// independent dependency chains for the same lane.
+// independent dependency chains for the same thread.
 __device__ __forceinline__ void sturm_count2(const float* d, const float* e2, int m, float xa,
                                              float xb, float pivmin, int& ca, int& cb) {
   float qa = d[0] - xa, qb = d[0] - xb;
@@ -99,88 +124,51 @@ __device__ __forceinline__ float guard(float x, float tiny) {
   return fabsf(x) < tiny ? (x < 0.f ? -tiny : tiny) : x;
 }
 
-// Eigenvectors of the tridiagonal (d, e) for the estimates lk[t] (t = 0, 1;
-// used where use[t]) from the twisted factorisations of T - lk I, written into
-// columns k[t] of Y (pitch P): forward pivots Dp_i, backward pivots Dm_i,
-// gamma_i = Dp_i + Dm_i - (d_i - lk), twist r = argmin |gamma|, z_r = 1,
-// z_i = -(e_i / Dp_i) z_{i+1} (i < r), z_{i+1} = -(e_i / Dm_{i+1}) z_i (i >= r);
-// normalised.  Only the output columns are used as storage.
-__device__ __forceinline__ void twisted_vectors(const float* d, const float* e, const float* e2,
-                                                int m, const float (&lk)[2], const bool (&use)[2],
-                                                float tiny, float* Y, int P, const int (&k)[2]) {
-  float dp[2], dm[2], best[2];
-  int r[2];
-#pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    dp[t] = guard(d[0] - lk[t], tiny);
-    if (use[t]) Y[k[t]] = dp[t];
-  }
+// Eigenvector of the tridiagonal (d, e) for the estimate lk from the twisted
+// factorisation of T - lk I, written into column k of Y (pitch P): forward
+// pivots Dp_i, backward pivots Dm_i, gamma_i = Dp_i + Dm_i - (d_i - lk), twist
+// r = argmin |gamma|, z_r = 1, z_i = -(e_i / Dp_i) z_{i+1} (i < r),
+// z_{i+1} = -(e_i / Dm_{i+1}) z_i (i >= r); normalised.  Only the output
+// column is used as storage.
+__device__ __forceinline__ void twisted_vector(const float* d, const float* e, const float* e2,
+                                               int m, float lk, float tiny, float* Y, int P,
+                                               int k) {
+  float dp = guard(d[0] - lk, tiny);
+  Y[k] = dp;
   for (int i = 1; i < m; ++i) {
-    const float di = d[i], ei = e2[i - 1];
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      dp[t] = guard((di - lk[t]) - __fdividef(ei, dp[t]), tiny);
-      if (use[t]) Y[i * P + k[t]] = dp[t];
-    }
+    dp = guard((d[i] - lk) - __fdividef(e2[i - 1], dp), tiny);
+    Y[i * P + k] = dp;
   }
-#pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    dm[t] = guard(d[m - 1] - lk[t], tiny);
-    best[t] = use[t] ? fabsf(Y[(m - 1) * P + k[t]]) : 0.f;
-    r[t] = m - 1;
-  }
+  float dm = guard(d[m - 1] - lk, tiny);
+  float best = fabsf(Y[(m - 1) * P + k]);
+  int r = m - 1;
   for (int i = m - 2; i >= 0; --i) {
-    const float di = d[i], ei = e2[i];
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      dm[t] = guard((di - lk[t]) - __fdividef(ei, dm[t]), tiny);
-      if (use[t]) {
-        const float g = fabsf(Y[i * P + k[t]] + dm[t] - (di - lk[t]));
-        if (g < best[t]) { best[t] = g; r[t] = i; }
-      }
-    }
+    const float di = d[i] - lk;
+    dm = guard(di - __fdividef(e2[i], dm), tiny);
+    const float g = fabsf(Y[i * P + k] + dm - di);
+    if (g < best) { best = g; r = i; }
   }
   // U multipliers e_i / Dm_{i+1} for i = m-2 .. r, kept in rows i+1
-  const int rmin = min(use[0] ? r[0] : m, use[1] ? r[1] : m);
-#pragma unroll
-  for (int t = 0; t < 2; ++t) dm[t] = guard(d[m - 1] - lk[t], tiny);
-  for (int i = m - 2; i >= rmin; --i) {
-    const float di = d[i], ei = e[i], ei2 = e2[i];
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      if (use[t] && i >= r[t]) Y[(i + 1) * P + k[t]] = __fdividef(ei, dm[t]);
-      dm[t] = guard((di - lk[t]) - __fdividef(ei2, dm[t]), tiny);
-    }
+  dm = guard(d[m - 1] - lk, tiny);
+  for (int i = m - 2; i >= r; --i) {
+    Y[(i + 1) * P + k] = __fdividef(e[i], dm);
+    dm = guard((d[i] - lk) - __fdividef(e2[i], dm), tiny);
   }
-  float nn[2] = {1.f, 1.f}, z[2] = {1.f, 1.f};
-  for (int i = rmin; i + 1 < m; ++i) {
-#pragma unroll
-    for (int t = 0; t < 2; ++t)
-      if (use[t] && i >= r[t]) {
-        z[t] = -Y[(i + 1) * P + k[t]] * z[t];
-        Y[(i + 1) * P + k[t]] = z[t];
-        nn[t] += z[t] * z[t];
-      }
+  float nn = 1.f, z = 1.f;
+  for (int i = r; i + 1 < m; ++i) {
+    z = -Y[(i + 1) * P + k] * z;
+    Y[(i + 1) * P + k] = z;
+    nn += z * z;
   }
-  const int rmax = max(use[0] ? r[0] : 0, use[1] ? r[1] : 0);
-  z[0] = z[1] = 1.f;
-  for (int i = rmax - 1; i >= 0; --i) {
-    const float ei = e[i];
-#pragma unroll
-    for (int t = 0; t < 2; ++t)
-      if (use[t] && i < r[t]) {
-        z[t] = -__fdividef(ei, Y[i * P + k[t]]) * z[t];
-        Y[i * P + k[t]] = z[t];
-        nn[t] += z[t] * z[t];
-      }
+  z = 1.f;
+  for (int i = r - 1; i >= 0; --i) {
+    z = -__fdividef(e[i], Y[i * P + k]) * z;
+    Y[i * P + k] = z;
+    nn += z * z;
   }
-#pragma unroll
-  for (int t = 0; t < 2; ++t)
-    if (use[t]) {
-      Y[r[t] * P + k[t]] = 1.f;
-      const float sc = rsqrtf(nn[t]);
-      for (int i = 0; i < m; ++i) Y[i * P + k[t]] *= sc;
-    }
+  Y[r * P + k] = 1.f;
+  const float sc = rsqrtf(nn);
+  for (int i = 0; i < m; ++i) Y[i * P + k] *= sc;
 }
 
 // double-float accumulation: (hi, lo) += a * b for floats a, b (exact product)
@@ -204,21 +192,19 @@ __device__ __forceinline__ float start_component(int x, int k) {
 }
 
 // Orthogonalise column c of Y against columns [c0, c) and normalise (whole
-// warp); returns the squared norm left after the projections.
-__device__ __forceinline__ float orth_column(float* Y, int P, int m, int c0, int c, int lane) {
+// group, one row per thread); returns the squared norm left after the
+// projections.
+__device__ __forceinline__ float orth_column(const Grp& g, float* Y, int P, int m, int c0, int c) {
+  const int x = g.t;
+  const bool hx = x < m;
   for (int c2 = c0; c2 < c; ++c2) {
-    float dt = 0.f;
-    for (int x = lane; x < m; x += 32) dt += Y[x * P + c] * Y[x * P + c2];
-    dt = tbk::warp_sum(dt);
-    for (int x = lane; x < m; x += 32) Y[x * P + c] -= dt * Y[x * P + c2];
-    __syncwarp();
+    const float dt = gsum(g, hx ? Y[x * P + c] * Y[x * P + c2] : 0.f);
+    if (hx) Y[x * P + c] -= dt * Y[x * P + c2];
   }
-  float nn = 0.f;
-  for (int x = lane; x < m; x += 32) nn += Y[x * P + c] * Y[x * P + c];
-  nn = tbk::warp_sum(nn);
+  const float nn = gsum(g, hx ? Y[x * P + c] * Y[x * P + c] : 0.f);
   const float sc = rsqrtf(fmaxf(nn, 1e-30f));
-  for (int x = lane; x < m; x += 32) Y[x * P + c] *= sc;
-  __syncwarp();
+  if (hx) Y[x * P + c] *= sc;
+  gsync(g);
   return nn;
 }
 
@@ -226,15 +212,15 @@ __device__ __forceinline__ float orth_column(float* Y, int P, int m, int c0, int
 // tridiagonal LU of T - lk I (the dlagtf/dlagts scheme), restarted from a
 // fixed start vector and kept orthogonal to columns [c0, c): used when the
 // twisted vector of a degenerate eigenvalue duplicates an earlier one (a split
-// tridiagonal).  The factorisation and the solves run on lane 0.
-__device__ void restart_column(const float* d, const float* e, int m, float lk, float tiny,
-                               float* Y, int P, int c0, int c, float* f, int lane) {
+// tridiagonal).  The factorisation and the solves run on thread 0.
+__device__ void restart_column(const Grp& g, const float* d, const float* e, int m, float lk,
+                               float tiny, float* Y, int P, int c0, int c, float* f) {
   float* u0 = f;              // reciprocal pivots
   float* u1 = f + m;          // first super-diagonal of U
   float* u2 = f + 2 * m;      // second super-diagonal of U
   float* ml = f + 3 * m;      // multipliers
   float* pv = f + 4 * m;      // 1 where rows k, k+1 were interchanged
-  if (lane == 0) {
+  if (g.t == 0) {
     float ak = d[0] - lk, bk = m > 1 ? e[0] : 0.f;
     for (int k = 0; k + 1 < m; ++k) {
       const float ck = e[k], ak1 = d[k + 1] - lk, bk1 = k + 2 < m ? e[k + 1] : 0.f;
@@ -253,11 +239,11 @@ __device__ void restart_column(const float* d, const float* e, int m, float lk, 
     }
     u0[m - 1] = 1.f / guard(ak, tiny);
   }
-  for (int x = lane; x < m; x += 32) Y[x * P + c] = start_component(x, c);
-  __syncwarp();
+  if (g.t < m) Y[g.t * P + c] = start_component(g.t, c);
+  gsync(g);
   for (int it = 0; it < 3; ++it) {
-    orth_column(Y, P, m, c0, c, lane);
-    if (lane == 0) {
+    orth_column(g, Y, P, m, c0, c);
+    if (g.t == 0) {
       float yk = Y[c];
       for (int k = 0; k + 1 < m; ++k) {
         const float yk1 = Y[(k + 1) * P + c];
@@ -276,24 +262,28 @@ __device__ void restart_column(const float* d, const float* e, int m, float lk, 
         y1 = y;
       }
     }
-    __syncwarp();
-    float mx = 0.f;                          // rescale before the next projection
-    for (int x = lane; x < m; x += 32) mx = fmaxf(mx, fabsf(Y[x * P + c]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const float sc = 1.f / fmaxf(mx, 1e-30f);
-    for (int x = lane; x < m; x += 32) Y[x * P + c] *= sc;
-    __syncwarp();
+    gsync(g);
+    // rescale before the next projection (sum of squares, not a maximum:
+    // one group reduction)
+    const float nn = gsum(g, g.t < m ? Y[g.t * P + c] * Y[g.t * P + c] : 0.f);
+    if (g.t < m) Y[g.t * P + c] *= rsqrtf(fmaxf(nn, 1e-30f));
+    gsync(g);
   }
-  orth_column(Y, P, m, c0, c, lane);
+  orth_column(g, Y, P, m, c0, c);
 }
 
 template <bool FULL>
-__global__ void __launch_bounds__(XW_MAX * 32) eig_warp_kernel(const XArgs a) {
+__global__ void __launch_bounds__(XW_MAX * GT, 2) eig_warp_kernel(const XArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = threadIdx.x / GT;
+  Grp g;
+  g.t = threadIdx.x % GT;
+  g.wl = threadIdx.x & 31;
+  g.gw = g.t >> 5;
+  g.bid = 1 + grp;
+  const int t = g.t;
   const int NT = a.NT, P = xpitch(NT);
-  unsigned char* base = smem + warp * xw_smem_per_warp(NT);
+  unsigned char* base = smem + grp * xw_smem_per_warp(NT);
   double* lamd = reinterpret_cast<double*>(base);
   float* H = reinterpret_cast<float*>(lamd + NT);
   float* Y = H + xw_hsize(NT);
@@ -304,183 +294,163 @@ __global__ void __launch_bounds__(XW_MAX * 32) eig_warp_kernel(const XArgs a) {
   float* v = lam + NT;
   float* q = v + NT;
   float* fs = q + NT;                          // 5 NT: restart factorisation
-  float* slc = fs + 5 * NT;                    // 64 slicing counts
-  int* act = reinterpret_cast<int*>(slc + 64);
+  float* slc = fs + 5 * NT;                    // NSLICE slicing counts
+  g.red = slc + NSLICE;                        // 8 floats
+  int* act = reinterpret_cast<int*>(g.red + 8);
   int* rank = act + NT;
-  const int i = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (i >= a.n) return;                       // whole warp: no block barriers below
+  const int i = blockIdx.x * (blockDim.x / GT) + grp;
+  if (i >= a.n) return;                       // whole group: no block barriers below
 
   const unsigned long long mask = a.colmask[i];
   const int m = __popcll(mask);
-  for (int x = lane; x < NT; x += 32)
-    if ((mask >> x) & 1ull) act[__popcll(mask & ((1ull << x) - 1ull))] = x;
-  __syncwarp();
+  if (t < NT && ((mask >> t) & 1ull)) act[__popcll(mask & ((1ull << t) - 1ull))] = t;
+  gsync(g);
   const double* Ti = a.T + (size_t)i * NT * NT;
-  for (int y = lane; y < m; y += 32) {
-    const int ay = act[y];
+  if (t < m) {
+    const int ay = act[t];
     int x = 0;
-    for (; x + 3 < m; x += 4) {             // four independent loads in flight
+    for (; x + 3 < m; x += 4) {               // four independent loads in flight
       const double t0 = Ti[act[x] * NT + ay], t1 = Ti[act[x + 1] * NT + ay];
       const double t2 = Ti[act[x + 2] * NT + ay], t3 = Ti[act[x + 3] * NT + ay];
-      H[x * P + y] = (float)t0;
-      H[(x + 1) * P + y] = (float)t1;
-      H[(x + 2) * P + y] = (float)t2;
-      H[(x + 3) * P + y] = (float)t3;
+      H[x * P + t] = (float)t0;
+      H[(x + 1) * P + t] = (float)t1;
+      H[(x + 2) * P + t] = (float)t2;
+      H[(x + 3) * P + t] = (float)t3;
     }
-    for (; x < m; ++x) H[x * P + y] = (float)Ti[act[x] * NT + ay];
+    for (; x < m; ++x) H[x * P + t] = (float)Ti[act[x] * NT + ay];
   }
-  __syncwarp();
+  gsync(g);
 
   // ---- 1. Householder: step j maps column j below the diagonal to
-  // (alpha, 0, ...) with I - 2 v v^T and keeps v there; lanes own rows
-  // x = j+1+lane and j+33+lane.
+  // (alpha, 0, ...) with I - 2 v v^T and keeps v there; thread t owns row
+  // x = j + 1 + t.
   for (int j = 0; j + 2 < m; ++j) {
-    const int x0 = j + 1 + lane, x1 = x0 + 32;
-    const bool h0 = x0 < m, h1 = x1 < m;
-    float xs = 0.f;
-    if (h0) xs += H[x0 * P + j] * H[x0 * P + j];
-    if (h1) xs += H[x1 * P + j] * H[x1 * P + j];
-    const float sig = tbk::warp_sum(xs);
+    const int x = j + 1 + t;
+    const bool hx = x < m;
     const float xj = H[(j + 1) * P + j];
+    const float hxj = hx ? H[x * P + j] : 0.f;
+    const float sig = gsum(g, hxj * hxj);
     if (sig - xj * xj <= 1e-30f * (sig + 1e-30f) || sig == 0.f) {
-      if (lane == 0) e[j] = xj;
-      __syncwarp();
-      if (h0) H[x0 * P + j] = 0.f;                     // identity
-      if (h1) H[x1 * P + j] = 0.f;
-      __syncwarp();
+      if (t == 0) e[j] = xj;
+      if (hx) H[x * P + j] = 0.f;                     // identity
+      gsync(g);
       continue;
     }
     const float alpha = xj >= 0.f ? -sqrtf(sig) : sqrtf(sig);
     const float inv = rsqrtf(2.f * (sig - xj * alpha));
-    if (h0) v[x0] = (x0 == j + 1 ? (xj - alpha) : H[x0 * P + j]) * inv;
-    if (h1) v[x1] = H[x1 * P + j] * inv;
-    __syncwarp();
-    const float* r0 = H + (h0 ? x0 : j + 1) * P;
-    const float* r1 = H + (h1 ? x1 : j + 1) * P;
-    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
-    int l = j + 1;
-    for (; l + 1 < m; l += 2) {
-      const float v0 = v[l], v1 = v[l + 1];
-      a0 += r0[l] * v0;
-      a1 += r0[l + 1] * v1;
-      b0 += r1[l] * v0;
-      b1 += r1[l + 1] * v1;
-    }
-    if (l < m) {
-      a0 += r0[l] * v[l];
-      b0 += r1[l] * v[l];
-    }
-    const float p0 = a0 + a1, p1 = b0 + b1;
-    float kp = 0.f;
-    if (h0) { q[x0] = p0; kp += p0 * v[x0]; }
-    if (h1) { q[x1] = p1; kp += p1 * v[x1]; }
-    const float K = tbk::warp_sum(kp);
-    __syncwarp();
-    if (h0) q[x0] -= K * v[x0];
-    if (h1) q[x1] -= K * v[x1];
-    __syncwarp();
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int x = t == 0 ? x0 : x1;
-      if (x < m) {
-        const float vx = 2.f * v[x], qx = 2.f * q[x];
-        float* row = H + x * P;
-#pragma unroll 4
-        for (int c = j + 1; c < m; ++c) row[c] -= vx * q[c] + qx * v[c];
-        row[j] = v[x];                                // keep v_j in column j
+    if (hx) v[x] = (x == j + 1 ? (xj - alpha) : hxj) * inv;
+    gsync(g);
+    float p = 0.f;
+    if (hx) {
+      const float* row = H + x * P;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      int l = j + 1;
+      for (; l + 3 < m; l += 4) {
+        a0 += row[l] * v[l];
+        a1 += row[l + 1] * v[l + 1];
+        a2 += row[l + 2] * v[l + 2];
+        a3 += row[l + 3] * v[l + 3];
       }
+      for (; l < m; ++l) a0 += row[l] * v[l];
+      p = (a0 + a1) + (a2 + a3);
+      q[x] = p;
     }
-    if (lane == 0) e[j] = alpha;
-    __syncwarp();
+    const float K = gsum(g, hx ? p * v[x] : 0.f);
+    if (hx) q[x] -= K * v[x];
+    gsync(g);
+    if (hx) {
+      const float vx = 2.f * v[x], qx = 2.f * q[x];
+      float* row = H + x * P;
+#pragma unroll 4
+      for (int c = j + 1; c < m; ++c) row[c] -= vx * q[c] + qx * v[c];
+      row[j] = v[x];                                  // keep v_j in column j
+    }
+    if (t == 0) e[j] = alpha;
+    gsync(g);
   }
-  for (int x = lane; x < m; x += 32) d[x] = H[x * P + x];
-  __syncwarp();
-  if (lane == 0) {
+  if (t < m) d[t] = H[t * P + t];
+  if (t == 0) {
     if (m >= 2) e[m - 2] = H[(m - 1) * P + (m - 2)];
     e[m - 1] = 0.f;
   }
-  __syncwarp();
-  float gl = 1e30f, gu = -1e30f, emax = 0.f;
-  for (int x = lane; x < m; x += 32) {
-    e2[x] = e[x] * e[x];
-    const float rad = fabsf(e[x]) + (x > 0 ? fabsf(e[x - 1]) : 0.f);
-    gl = fminf(gl, d[x] - rad);
-    gu = fmaxf(gu, d[x] + rad);
-    emax = fmaxf(emax, e[x] * e[x]);
+  gsync(g);
+  float lmin = 1e30f, lmax = -1e30f, emax = 0.f;
+  if (t < m) {
+    e2[t] = e[t] * e[t];
+    const float rad = fabsf(e[t]) + (t > 0 ? fabsf(e[t - 1]) : 0.f);
+    lmin = d[t] - rad;
+    lmax = d[t] + rad;
+    emax = e[t] * e[t];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    gl = fminf(gl, __shfl_xor_sync(0xffffffffu, gl, o));
-    gu = fmaxf(gu, __shfl_xor_sync(0xffffffffu, gu, o));
+    lmin = fminf(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+    lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
     emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
   }
-  __syncwarp();
-  const float tnorm = fmaxf(fmaxf(fabsf(gl), fabsf(gu)), 1e-30f);
+  if (g.wl == 0) { g.red[3 * g.gw] = lmin; g.red[3 * g.gw + 1] = lmax; g.red[3 * g.gw + 2] = emax; }
+  gsync(g);
+  lmin = fminf(g.red[0], g.red[3]);
+  lmax = fmaxf(g.red[1], g.red[4]);
+  emax = fmaxf(g.red[2], g.red[5]);
+  gsync(g);
+  const float tnorm = fmaxf(fmaxf(fabsf(lmin), fabsf(lmax)), 1e-30f);
   const float pivmin = fmaxf(1e-30f, 1.2e-7f * 1.2e-7f * emax);
   const float tiny = 1.2e-7f * tnorm;
-  gl -= 2.4e-7f * tnorm + pivmin;
-  gu += 2.4e-7f * tnorm + pivmin;
+  lmin -= 2.4e-7f * tnorm + pivmin;
+  lmax += 2.4e-7f * tnorm + pivmin;
 
-  // ---- 2. eigenvalues by bisection; lane owns k = lane and lane + 32, both
-  // evaluated in one Sturm pass
+  // ---- 2. eigenvalues: counts at NSLICE points splitting [lmin, lmax]
+  // evenly (two per thread), then trisection from the slice holding each
+  // eigenvalue (thread t owns eigenvalue t), a fixed number of rounds shrinking
+  // the slice to 2.4e-7 ||T||
   {
-    const int k0 = lane, k1 = lane + 32;
-    // slicing pass: counts at 64 points splitting [gl, gu] evenly (two per
-    // lane), then every eigenvalue starts from the slice that holds it
-    const float h = (gu - gl) * (1.f / 65.f);
+    const float h = (lmax - lmin) / (float)(NSLICE + 1);
     int s0 = 0, s1 = 0;
-    sturm_count2(d, e2, m, gl + h * (float)(lane + 1), gl + h * (float)(lane + 33), pivmin, s0, s1);
-    float* cnt = slc;
-    cnt[lane] = (float)s0;
-    cnt[lane + 32] = (float)s1;
-    __syncwarp();
-    float lo0 = gl, hi0 = gu, lo1 = gl, hi1 = gu;
-    for (int t = 0; t < 64; ++t) {           // point t + 1 has cnt[t] eigenvalues below it
-      const float xt = gl + h * (float)(t + 1);
-      const int ct = (int)cnt[t];
-      if (ct > k0) hi0 = fminf(hi0, xt); else lo0 = fmaxf(lo0, xt);
-      if (ct > k1) hi1 = fminf(hi1, xt); else lo1 = fmaxf(lo1, xt);
+    sturm_count2(d, e2, m, lmin + h * (float)(t + 1), lmin + h * (float)(t + 1 + GT), pivmin, s0,
+                 s1);
+    slc[t] = (float)s0;
+    slc[t + GT] = (float)s1;
+    gsync(g);
+    float lo = lmin, hi = lmax;
+    for (int u = 0; u < NSLICE; ++u) {            // point u + 1 has slc[u] eigenvalues below
+      const float xu = lmin + h * (float)(u + 1);
+      if ((int)slc[u] > t) hi = fminf(hi, xu); else lo = fmaxf(lo, xu);
     }
-    __syncwarp();
-    for (int it = 0; it < 64; ++it) {
-      const bool g0 = k0 < m && (hi0 - lo0) > 2.4e-7f * fmaxf(fabsf(lo0), fabsf(hi0)) + pivmin;
-      const bool g1 = k1 < m && (hi1 - lo1) > 2.4e-7f * fmaxf(fabsf(lo1), fabsf(hi1)) + pivmin;
-      if (!__any_sync(0xffffffffu, g0 || g1)) break;
-      const float m0 = 0.5f * (lo0 + hi0), m1 = 0.5f * (lo1 + hi1);
-      int c0 = 0, c1 = 0;
-      if (g0 || g1) sturm_count2(d, e2, m, m0, m1, pivmin, c0, c1);
-      if (g0) { if (c0 > k0) hi0 = m0; else lo0 = m0; }
-      if (g1) { if (c1 > k1) hi1 = m1; else lo1 = m1; }
-    }
-    if (k0 < m) lam[k0] = 0.5f * (lo0 + hi0);
-    if (k1 < m) lam[k1] = 0.5f * (lo1 + hi1);
-  }
-  __syncwarp();
-  // ---- 3. eigenvectors: twisted factorisations, twice (the second at the
-  // tridiagonal Rayleigh quotient of the first vector)
-  {
-    const int kk[2] = {lane, lane + 32};
-    const bool use[2] = {lane < m, lane + 32 < m};
-    float lk[2] = {use[0] ? lam[lane] : 0.f, use[1] ? lam[lane + 32] : 0.f};
-    twisted_vectors(d, e, e2, m, lk, use, tiny, Y, P, kk);
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      if (!use[t]) continue;
-      float n0 = 0.f, n1 = 0.f, zp = 0.f;
-      for (int x = 0; x < m; ++x) {
-        const float z = Y[x * P + kk[t]];
-        n0 += d[x] * z * z;
-        if (x > 0) n1 += e[x - 1] * zp * z;
-        zp = z;
+    const float tol = 2.4e-7f * tnorm + pivmin;
+    const int rounds = (h > tol) ? (int)ceilf(logf(h / tol) * 0.91023922f) : 0;   // log_3
+    if (t < m) {
+      for (int it = 0; it < rounds; ++it) {
+        const float w = (hi - lo) * (1.f / 3.f);
+        const float p1 = lo + w, p2 = hi - w;
+        int c1, c2;
+        sturm_count2(d, e2, m, p1, p2, pivmin, c1, c2);
+        if (c1 > t) hi = p1;
+        else if (c2 > t) { lo = p1; hi = p2; }
+        else lo = p2;
       }
-      // stay inside the eigenvalue's own bisection bracket, so that a vector
-      // mixed with a close neighbour cannot move the shift onto that neighbour
-      const float hw = 1.2e-7f * fabsf(lk[t]) + pivmin;
-      lk[t] = fminf(fmaxf(n0 + 2.f * n1, lk[t] - hw), lk[t] + hw);
+      lam[t] = 0.5f * (lo + hi);
     }
-    twisted_vectors(d, e, e2, m, lk, use, tiny, Y, P, kk);
   }
-  __syncwarp();
+  gsync(g);
+  // ---- 3. eigenvectors: twisted factorisations, twice (the second at the
+  // tridiagonal Rayleigh quotient of the first vector, kept inside the
+  // eigenvalue's own bracket so that a vector mixed with a close neighbour
+  // cannot move the shift onto that neighbour)
+  if (t < m) {
+    const float lk = lam[t];
+    twisted_vector(d, e, e2, m, lk, tiny, Y, P, t);
+    float n0 = 0.f, n1 = 0.f, zp = 0.f;
+    for (int x = 0; x < m; ++x) {
+      const float z = Y[x * P + t];
+      n0 += d[x] * z * z;
+      if (x > 0) n1 += e[x - 1] * zp * z;
+      zp = z;
+    }
+    const float hw = 1.2e-7f * tnorm + pivmin;
+    twisted_vector(d, e, e2, m, fminf(fmaxf(n0 + 2.f * n1, lk - hw), lk + hw), tiny, Y, P, t);
+  }
+  gsync(g);
   // Gram-Schmidt inside clusters of close eigenvalues (index order); a member
   // that loses most of its norm duplicated an earlier one and is recomputed
   const float gtol = 1e-3f * tnorm;
@@ -488,61 +458,56 @@ __global__ void __launch_bounds__(XW_MAX * 32) eig_warp_kernel(const XArgs a) {
     if (!(lam[c] - lam[c - 1] < gtol)) continue;
     int first = c - 1;
     while (first > 0 && lam[first] - lam[first - 1] < gtol) --first;
-    const float nn = orth_column(Y, P, m, first, c, lane);
-    if (nn < 0.25f) restart_column(d, e, m, lam[c], tiny, Y, P, first, c, fs, lane);
+    const float nn = orth_column(g, Y, P, m, first, c);
+    if (nn < 0.25f) restart_column(g, d, e, m, lam[c], tiny, Y, P, first, c, fs);
   }
 
-  // ---- 4. back-transformation U = H_0 ... H_{m-3} Y; lanes own columns
-  // lane and lane + 32
-  {
-    const int k0 = lane, k1 = lane + 32;
-    const bool c0 = k0 < m, c1 = k1 < m;
-    float* y0 = Y + (c0 ? k0 : 0);
-    float* y1 = Y + (c1 ? k1 : 0);
+  // ---- 4. back-transformation U = H_0 ... H_{m-3} Y; thread t owns column t
+  if (t < m) {
+    float* yk = Y + t;
     for (int j = m - 3; j >= 0; --j) {
-      float s0 = 0.f, s1 = 0.f, t0 = 0.f, t1 = 0.f;
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
       int x = j + 1;
-      for (; x + 1 < m; x += 2) {
-        const float hx = H[x * P + j], hx1 = H[(x + 1) * P + j];
-        s0 += hx * y0[x * P];
-        s1 += hx1 * y0[(x + 1) * P];
-        t0 += hx * y1[x * P];
-        t1 += hx1 * y1[(x + 1) * P];
+      for (; x + 3 < m; x += 4) {
+        s0 += H[x * P + j] * yk[x * P];
+        s1 += H[(x + 1) * P + j] * yk[(x + 1) * P];
+        s2 += H[(x + 2) * P + j] * yk[(x + 2) * P];
+        s3 += H[(x + 3) * P + j] * yk[(x + 3) * P];
       }
-      if (x < m) {
-        const float hx = H[x * P + j];
-        s0 += hx * y0[x * P];
-        t0 += hx * y1[x * P];
-      }
-      const float f0 = 2.f * (s0 + s1), f1 = 2.f * (t0 + t1);
-      __syncwarp();
+      for (; x < m; ++x) s0 += H[x * P + j] * yk[x * P];
+      const float f0 = 2.f * ((s0 + s1) + (s2 + s3));
 #pragma unroll 4
-      for (int xx = j + 1; xx < m; ++xx) {
-        const float hx = H[xx * P + j];
-        if (c0) y0[xx * P] -= f0 * hx;
-        if (c1) y1[xx * P] -= f1 * hx;
-      }
+      for (int xx = j + 1; xx < m; ++xx) yk[xx * P] -= f0 * H[xx * P + j];
     }
   }
-  __syncwarp();
+  gsync(g);
 
   // ---- 5. Loewdin U <- U (I - E/2), E = U^T U - I: E into H (aligned
-  // rows), then each lane updates its own rows 16 columns at a time; a chunk
+  // rows), then each thread updates its own row 16 columns at a time; a chunk
   // written back before the next chunk is formed changes the result only at
   // second order in E, below the first-order step's own error.
   float* E = H;
   const int PE = epitch(NT);
-  for (int b = lane; b < m; b += 32) {
+  if (t < m) {
+    const int b = t;
     int c = 0;
     for (; c + 1 < m; c += 2) {
-      float t0 = 0.f, t1 = 0.f;
-      for (int x = 0; x < m; ++x) {
+      float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+      int x = 0;
+      for (; x + 1 < m; x += 2) {
+        const float yb0 = Y[x * P + b], yb1 = Y[(x + 1) * P + b];
+        t0 += Y[x * P + c] * yb0;
+        t1 += Y[x * P + c + 1] * yb0;
+        t2 += Y[(x + 1) * P + c] * yb1;
+        t3 += Y[(x + 1) * P + c + 1] * yb1;
+      }
+      if (x < m) {
         const float yb = Y[x * P + b];
         t0 += Y[x * P + c] * yb;
         t1 += Y[x * P + c + 1] * yb;
       }
-      E[c * PE + b] = 0.5f * (t0 - (b == c ? 1.f : 0.f));
-      E[(c + 1) * PE + b] = 0.5f * (t1 - (b == c + 1 ? 1.f : 0.f));
+      E[c * PE + b] = 0.5f * ((t0 + t2) - (b == c ? 1.f : 0.f));
+      E[(c + 1) * PE + b] = 0.5f * ((t1 + t3) - (b == c + 1 ? 1.f : 0.f));
     }
     if (c < m) {
       float t0 = 0.f;
@@ -550,11 +515,11 @@ __global__ void __launch_bounds__(XW_MAX * 32) eig_warp_kernel(const XArgs a) {
       E[c * PE + b] = 0.5f * (t0 - (b == c ? 1.f : 0.f));
     }
   }
-  __syncwarp();
+  gsync(g);
   // (columns past m of a chunk read whatever follows in shared memory; their
   // sums are discarded)
-  for (int x = lane; x < m; x += 32) {
-    float* yx = Y + x * P;
+  if (t < m) {
+    float* yx = Y + t * P;
     for (int b0 = 0; b0 < m; b0 += 16) {
       float acc[16];
 #pragma unroll
@@ -576,14 +541,15 @@ __global__ void __launch_bounds__(XW_MAX * 32) eig_warp_kernel(const XArgs a) {
         if (b0 + j < m) yx[b0 + j] -= acc[j];
     }
   }
-  __syncwarp();
+  gsync(g);
+
   if constexpr (!FULL) {
     float* lf = a.lamf + (size_t)i * NT;
     float* zo = a.Zf + (size_t)i * NT * NT;
-    for (int x = lane; x < m; x += 32) lf[x] = lam[x];
+    if (t < m) lf[t] = lam[t];
     for (int x = 0; x < m; ++x)
-      for (int y = lane; y < m; y += 32) zo[x * NT + y] = Y[x * P + y];
-    if (lane == 0) a.kdim[i] = m;
+      if (t < m) zo[x * NT + t] = Y[x * P + t];
+    if (t == 0) a.kdim[i] = m;
     return;
   } else {
     // ---- 6. Rayleigh quotients on the original block-tridiagonal T: row x
@@ -593,8 +559,8 @@ __global__ void __launch_bounds__(XW_MAX * 32) eig_warp_kernel(const XArgs a) {
     int* bhi = reinterpret_cast<int*>(q);
     float* Thi = H;                       // [x][12]
     float* Tlo = H + NT * 12;
-    for (int x = lane; x < m; x += 32) {
-      const int bx = act[x] >> 2;
+    if (t < m) {
+      const int x = t, bx = act[x] >> 2;
       int lo = x, hi = x + 1;
       while (lo > 0 && (act[lo - 1] >> 2) >= bx - 1) --lo;
       while (hi < m && (act[hi] >> 2) <= bx + 1) ++hi;
@@ -607,60 +573,47 @@ __global__ void __launch_bounds__(XW_MAX * 32) eig_warp_kernel(const XArgs a) {
         Tlo[x * 12 + w] = (float)(tv - (double)th);
       }
     }
-    __syncwarp();
-    {
-      const int kk[2] = {lane, lane + 32};
-      const bool use[2] = {lane < m, lane + 32 < m};
-      float nh[2] = {0.f, 0.f}, nl[2] = {0.f, 0.f}, dh[2] = {0.f, 0.f}, dl[2] = {0.f, 0.f};
+    gsync(g);
+    if (t < m) {
+      const int k = t;
+      float nh = 0.f, nl = 0.f, dh = 0.f, dl = 0.f;
       for (int x = 0; x < m; ++x) {
         const int l0 = blo[x], nw = bhi[x] - l0;
-        float th[2] = {0.f, 0.f}, tl[2] = {0.f, 0.f};
+        float th = 0.f, tl = 0.f;
         for (int w = 0; w < nw; ++w) {
-          const float ah = Thi[x * 12 + w], al = Tlo[x * 12 + w];
-#pragma unroll
-          for (int t = 0; t < 2; ++t) {
-            const float u = use[t] ? Y[(l0 + w) * P + kk[t]] : 0.f;
-            df_fma(th[t], tl[t], ah, u);
-            tl[t] += al * u;
-          }
+          const float u = Y[(l0 + w) * P + k];
+          df_fma(th, tl, Thi[x * 12 + w], u);
+          tl += Tlo[x * 12 + w] * u;
         }
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          const float ux = use[t] ? Y[x * P + kk[t]] : 0.f;
-          df_fma(nh[t], nl[t], ux, th[t]);
-          nl[t] += ux * tl[t];
-          df_fma(dh[t], dl[t], ux, ux);
-        }
+        const float ux = Y[x * P + k];
+        df_fma(nh, nl, ux, th);
+        nl += ux * tl;
+        df_fma(dh, dl, ux, ux);
       }
-#pragma unroll
-      for (int t = 0; t < 2; ++t)
-        if (use[t]) {
-          const double lk = ((double)nh[t] + (double)nl[t]) / ((double)dh[t] + (double)dl[t]);
-          lamd[kk[t]] = lk;
-          if (!isfinite(lk)) tbk::set_status(a.st, TB_ERR_NONFINITE, i);
-        }
+      const double lk = ((double)nh + (double)nl) / ((double)dh + (double)dl);
+      lamd[k] = lk;
+      if (!isfinite(lk)) tbk::set_status(a.st, TB_ERR_NONFINITE, i);
     }
-    __syncwarp();
+    gsync(g);
     // ---- 7. ascending order (ties by index), spectral record
-    for (int k = lane; k < m; k += 32) {
+    if (t < m) {
       int rk = 0;
-      const double lk = lamd[k];
-      for (int c = 0; c < m; ++c) rk += (lamd[c] < lk) || (lamd[c] == lk && c < k);
-      rank[k] = rk;
+      const double lk = lamd[t];
+      for (int c = 0; c < m; ++c) rk += (lamd[c] < lk) || (lamd[c] == lk && c < t);
+      rank[t] = rk;
     }
-    __syncwarp();
+    gsync(g);
     double* lo = a.lambda + (size_t)i * NT;
-    for (int k = lane; k < NT; k += 32) {
-      if (k < m) lo[rank[k]] = lamd[k];
-      else lo[k] = 0.0;
-    }
     double* So = a.S + (size_t)i * 4 * NT;
-    for (int k = lane; k < NT; k += 32)
+    if (t < NT) {
+      if (t < m) lo[rank[t]] = lamd[t];
+      else lo[t] = 0.0;
 #pragma unroll
       for (int al = 0; al < 4; ++al) {
-        if (k < m) So[al * NT + rank[k]] = (double)Y[al * P + k];
-        else So[al * NT + k] = 0.0;
+        if (t < m) So[al * NT + rank[t]] = (double)Y[al * P + t];
+        else So[al * NT + t] = 0.0;
       }
+    }
     // P = Y[rows, active] U: rows staged through H in chunks of RW rows
     const int deg = a.h_off[i + 1] - a.h_off[i];
     const size_t rbase = (size_t)(i + a.h_off[i]) * 4;
@@ -669,43 +622,66 @@ __global__ void __launch_bounds__(XW_MAX * 32) eig_warp_kernel(const XArgs a) {
     float* Yr = H;
     for (int r0 = 0; r0 < nrows; r0 += RW) {
       const int nr = min(RW, nrows - r0);
-      __syncwarp();
-      for (int x = lane; x < m; x += 32) {
-        const int ax = act[x];
+      gsync(g);
+      if (t < m) {
+        const int ax = act[t];
         int rr = 0;
         for (; rr + 3 < nr; rr += 4) {        // four independent loads in flight
           const float y0 = a.Y[(rbase + r0 + rr) * NT + ax];
           const float y1 = a.Y[(rbase + r0 + rr + 1) * NT + ax];
           const float y2 = a.Y[(rbase + r0 + rr + 2) * NT + ax];
           const float y3 = a.Y[(rbase + r0 + rr + 3) * NT + ax];
-          Yr[rr * NT + x] = y0;
-          Yr[(rr + 1) * NT + x] = y1;
-          Yr[(rr + 2) * NT + x] = y2;
-          Yr[(rr + 3) * NT + x] = y3;
+          Yr[rr * NT + t] = y0;
+          Yr[(rr + 1) * NT + t] = y1;
+          Yr[(rr + 2) * NT + t] = y2;
+          Yr[(rr + 3) * NT + t] = y3;
         }
-        for (; rr < nr; ++rr) Yr[rr * NT + x] = a.Y[(rbase + r0 + rr) * NT + ax];
+        for (; rr < nr; ++rr) Yr[rr * NT + t] = a.Y[(rbase + r0 + rr) * NT + ax];
       }
-      __syncwarp();
-      for (int rr = 0; rr < nr; ++rr) {
-        double* pr = a.P + (rbase + r0 + rr) * NT;
-        const float* yr = Yr + rr * NT;
-        for (int k = lane; k < NT; k += 32) {
-          if (k < m) {
-            float s0 = 0.f, s1 = 0.f;
+      gsync(g);
+      if (t < NT) {
+        int rr = 0;
+        for (; rr + 1 < nr; rr += 2) {          // two rows at a time
+          double* p0 = a.P + (rbase + r0 + rr) * NT;
+          double* p1 = p0 + NT;
+          if (t < m) {
+            const float* y0 = Yr + rr * NT;
+            const float* y1 = y0 + NT;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
             int x = 0;
             for (; x + 1 < m; x += 2) {
-              s0 += yr[x] * Y[x * P + k];
-              s1 += yr[x + 1] * Y[(x + 1) * P + k];
+              const float u0 = Y[x * P + t], u1 = Y[(x + 1) * P + t];
+              s0 += y0[x] * u0;
+              s1 += y0[x + 1] * u1;
+              s2 += y1[x] * u0;
+              s3 += y1[x + 1] * u1;
             }
-            if (x < m) s0 += yr[x] * Y[x * P + k];
-            pr[rank[k]] = (double)(s0 + s1);
+            if (x < m) {
+              const float u0 = Y[x * P + t];
+              s0 += y0[x] * u0;
+              s2 += y1[x] * u0;
+            }
+            p0[rank[t]] = (double)(s0 + s1);
+            p1[rank[t]] = (double)(s2 + s3);
           } else {
-            pr[k] = 0.0;
+            p0[t] = 0.0;
+            p1[t] = 0.0;
+          }
+        }
+        if (rr < nr) {
+          double* p0 = a.P + (rbase + r0 + rr) * NT;
+          if (t < m) {
+            const float* y0 = Yr + rr * NT;
+            float s0 = 0.f;
+            for (int x = 0; x < m; ++x) s0 += y0[x] * Y[x * P + t];
+            p0[rank[t]] = (double)s0;
+          } else {
+            p0[t] = 0.0;
           }
         }
       }
     }
-    if (lane == 0) a.kdim[i] = m;
+    if (t == 0) a.kdim[i] = m;
   }
 }
 
@@ -907,9 +883,13 @@ __global__ void __launch_bounds__(FT) eig_finish_kernel(const FinArgs<TV> a) {
 tb_status eig_configure(tb_ctx* c) {
   const int NT = 4 * c->p.r;
   const size_t per = xw_smem_per_warp(NT);
-  int xw = (int)((110 * 1024) / per);        // two CTAs per SM
+  int sm_smem = 0;
+  TB_CUDA_TRY(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                                     c->device));
+  int xw = (int)((size_t)(sm_smem / 2 - 1024) / per);   // targets per CTA; two CTAs per SM
   if (xw > XW_MAX) xw = XW_MAX;
   if (xw < 1) xw = 1;
+  if (NT > GT) return TB_ERR_CAPACITY;
   c->eig_warps = xw;
   c->eig_smem = xw * per;
   if (c->p.prec == TB_PREC_FP64) {
@@ -935,14 +915,14 @@ tb_status launch_eig(tb_ctx* c, int n, const int* h_off, double* lambda, double*
            c->lamf, lambda, S, P, kdim, c->d_status};
   if (c->p.prec == TB_PREC_FP64) {
     if (!c->kry_fused) {
-      eig_warp_kernel<false><<<(n + xw - 1) / xw, xw * 32, c->eig_smem, s>>>(xa);
+      eig_warp_kernel<false><<<(n + xw - 1) / xw, xw * GT, c->eig_smem, s>>>(xa);
       TB_CUDA_TRY(cudaGetLastError());
     }
     FinArgs<double> fa{n, NT, c->T, c->colmask, c->Zf, c->lamf,
                        reinterpret_cast<const double*>(c->Y), h_off, lambda, S, P, c->d_status};
     eig_finish_kernel<double><<<n, FT, c->fin_smem, s>>>(fa);
   } else {
-    eig_warp_kernel<true><<<(n + xw - 1) / xw, xw * 32, c->eig_smem, s>>>(xa);
+    eig_warp_kernel<true><<<(n + xw - 1) / xw, xw * GT, c->eig_smem, s>>>(xa);
   }
   TB_CUDA_TRY(cudaGetLastError());
   return TB_OK;

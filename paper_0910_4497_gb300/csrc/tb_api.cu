@@ -50,6 +50,13 @@ size_t carve(tb_ctx* c, int n, unsigned char* base) {
   Carver k{base};
   c->scan_h = k.take<int>(n + 1);
   c->scan_c = k.take<int>(n + 1);
+  const size_t ncell = neighbor_cell_capacity(n);
+  c->cell_cnt = k.take<int>(ncell);
+  c->cell_off = k.take<int>(ncell + 1);
+  c->cell_atoms = k.take<int>(n);
+  c->atom_cell = k.take<int>(n);
+  c->pad_h = k.take<int>(hcap);
+  c->pad_c = k.take<int>((size_t)n * p.max_cluster);
   c->T = k.take<double>((size_t)n * NT * NT);
   c->Y = k.take<unsigned char>(rows * 4 * NT * tv);
   c->colmask = k.take<unsigned long long>(n);

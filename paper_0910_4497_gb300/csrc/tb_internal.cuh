@@ -120,6 +120,12 @@ struct tb_ctx {
   // sub-buffers inside ws
   int* scan_h = nullptr;             // n+1 counts (H lists)
   int* scan_c = nullptr;             // n+1 counts (clusters)
+  int* cell_cnt = nullptr;           // neighbour cells: counts (cell capacity)
+  int* cell_off = nullptr;           // offsets (cell capacity + 1)
+  int* cell_atoms = nullptr;         // n atoms binned by cell
+  int* atom_cell = nullptr;          // n cell ids
+  int* pad_h = nullptr;              // n * max_hnbr padded Hamiltonian lists
+  int* pad_c = nullptr;              // n * max_cluster padded clusters
   double* T = nullptr;               // n * NT * NT
   void* Y = nullptr;                 // n*(1+max_hnbr)*4*NT  (TV precision)
   unsigned long long* colmask = nullptr;  // n
@@ -174,6 +180,7 @@ struct tb_ctx {
 tb_status prof_mark(tb_ctx* c, int stage, bool end, cudaStream_t s);
 
 // Launchers (defined in the kernel translation units).
+size_t neighbor_cell_capacity(int n);
 tb_status launch_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h_off,
                            int* h_idx, int* c_off, int* c_idx, cudaStream_t s);
 tb_status launch_assemble(tb_ctx* c, int n, const double* pos, double L,

@@ -8,6 +8,14 @@
 //   d = x_j - x_i;  d -= L if d > L/2;  d += L if d < -L/2;
 //   r2 = (dx*dx + dy*dy) + dz*dz <= R*R.
 // Lists are compacted with warp ballots, so they come out in ascending j.
+//
+// When the box holds at least three cells of side >= Rc + 0.01 A per
+// dimension, the candidates come from cell lists instead: atoms are binned
+// (counting sort), a warp per target scans the 27 surrounding cells with the
+// same two-stage test, sorts what it found (bitonic, in shared memory) and
+// writes padded per-atom lists that are then compacted into the CSR.  The
+// 0.01 A margin keeps every pair within Rc in adjacent cells whatever the
+// rounding of the cell assignment.
 #include "tb_internal.cuh"
 
 namespace {
@@ -132,7 +140,178 @@ scan2_kernel(int n, const int* __restrict__ a, int* __restrict__ oa,
   if (t == 1023) { oa[n] = sa[1023]; ob[n] = sb[1023]; }
 }
 
+// ---------------------------------------------------------------- cell lists
+
+__device__ __forceinline__ int cell_coord(double x, double L, int nc) {
+  int c = (int)(x * (double)nc / L);
+  return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+__global__ void cell_assign_kernel(int n, const double* __restrict__ pos, double L, int nc,
+                                   int* __restrict__ atom_cell, int* __restrict__ cell_cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int cx = cell_coord(pos[3 * i], L, nc), cy = cell_coord(pos[3 * i + 1], L, nc),
+            cz = cell_coord(pos[3 * i + 2], L, nc);
+  const int c = (cx * nc + cy) * nc + cz;
+  atom_cell[i] = c;
+  atomicAdd(&cell_cnt[c], 1);
+}
+
+__global__ void cell_fill_kernel(int n, const int* __restrict__ atom_cell,
+                                 const int* __restrict__ cell_off, int* __restrict__ cell_fill,
+                                 int* __restrict__ cell_atoms) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = atom_cell[i];
+  cell_atoms[cell_off[c] + atomicAdd(&cell_fill[c], 1)] = i;
+}
+
+// Exclusive scan of one count array (length m) into offsets (length m+1).
+__global__ void __launch_bounds__(1024) scan1_kernel(int m, const int* __restrict__ a,
+                                                     int* __restrict__ oa) {
+  __shared__ int sa[1024];
+  const int t = threadIdx.x;
+  const int chunk = (m + 1023) / 1024;
+  const int lo = min(m, t * chunk), hi = min(m, lo + chunk);
+  int s1 = 0;
+  for (int k = lo; k < hi; ++k) s1 += a[k];
+  sa[t] = s1;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int v1 = t >= o ? sa[t - o] : 0;
+    __syncthreads();
+    sa[t] += v1;
+    __syncthreads();
+  }
+  int r1 = sa[t] - s1;
+  for (int k = lo; k < hi; ++k) {
+    oa[k] = r1;
+    r1 += a[k];
+  }
+  if (t == 1023) oa[m] = sa[1023];
+}
+
+// Ascending bitonic sort of v[0..len) (len a power of two) by one warp.
+__device__ __forceinline__ void warp_bitonic(int* v, int len, int lane) {
+  for (int k = 2; k <= len; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int x = lane; x < len; x += 32) {
+        const int y = x ^ j;
+        if (y > x) {
+          const int a = v[x], b = v[y];
+          const bool up = (x & k) == 0;
+          if ((a > b) == up) { v[x] = b; v[y] = a; }
+        }
+      }
+      __syncwarp();
+    }
+}
+
+// One warp per target: candidates from the 27 cells around the target's cell,
+// the same FP32 prefilter and FP64 membership test as nbr_kernel, then sorted
+// lists written into padded per-atom rows (counts capped at the capacities).
+__global__ void __launch_bounds__(NB_THREADS)
+nbr_cell_kernel(int n, const double* __restrict__ pos, const float4* __restrict__ posf,
+                double L, double R2h, double R2c, float Rh_pre2, float Rc_pre2, int nc,
+                const int* __restrict__ atom_cell, const int* __restrict__ cell_off,
+                const int* __restrict__ cell_atoms, int capc, int* __restrict__ hcnt,
+                int* __restrict__ ccnt, int* __restrict__ pad_h, int* __restrict__ pad_c,
+                int max_h, int max_c, int* st) {
+  extern __shared__ int nb_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int* cand_c = nb_smem + warp * (capc + 64);
+  int* cand_h = cand_c + capc;
+  const int i = blockIdx.x * NB_WARPS + warp;
+  if (i >= n) return;
+  const float Lf = (float)L, invLf = (float)(1.0 / L);
+  const float4 pi = posf[i];
+  const double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+  const double hL = 0.5 * L;
+  const int ci = atom_cell[i];
+  const int cx = ci / (nc * nc), cy = (ci / nc) % nc, cz = ci % nc;
+  int nh = 0, ncand = 0;
+  for (int q = 0; q < 27; ++q) {
+    const int ox = q / 9 - 1, oy = (q / 3) % 3 - 1, oz = q % 3 - 1;
+    const int c2 = (((cx + ox + nc) % nc) * nc + (cy + oy + nc) % nc) * nc + (cz + oz + nc) % nc;
+    const int b0 = cell_off[c2], b1 = cell_off[c2 + 1];
+    for (int b = b0; b < b1; b += 32) {
+      const int bb = b + lane;
+      bool in_h = false, in_c = false;
+      int j = -1;
+      if (bb < b1) {
+        j = cell_atoms[bb];
+        if (j != i) {
+          const float4 pj = posf[j];
+          float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+          dx -= Lf * rintf(dx * invLf);
+          dy -= Lf * rintf(dy * invLf);
+          dz -= Lf * rintf(dz * invLf);
+          const float r2f = dx * dx + dy * dy + dz * dz;
+          if (r2f <= Rc_pre2 || r2f <= Rh_pre2) {
+            const double ex = min_image_rn(__dsub_rn(pos[3 * j], xi), L, hL);
+            const double ey = min_image_rn(__dsub_rn(pos[3 * j + 1], yi), L, hL);
+            const double ez = min_image_rn(__dsub_rn(pos[3 * j + 2], zi), L, hL);
+            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)),
+                                        __dmul_rn(ez, ez));
+            in_h = r2 <= R2h;
+            in_c = r2 <= R2c;
+          }
+        }
+      }
+      const unsigned bh = __ballot_sync(0xffffffffu, in_h);
+      const unsigned bc = __ballot_sync(0xffffffffu, in_c);
+      const unsigned below = (1u << lane) - 1u;
+      const int ph = nh + __popc(bh & below), pc = ncand + __popc(bc & below);
+      if (in_h && ph < 64) cand_h[ph] = j;
+      if (in_c && pc < capc) cand_c[pc] = j;
+      nh += __popc(bh);
+      ncand += __popc(bc);
+    }
+  }
+  __syncwarp();
+  // pad to a power of two with INT_MAX, sort ascending
+  const int kc = min(ncand, capc), kh = min(nh, 64);
+  int lc = 1;
+  while (lc < kc) lc <<= 1;
+  int lh = 1;
+  while (lh < kh) lh <<= 1;
+  for (int x = kc + lane; x < lc; x += 32) cand_c[x] = 0x7fffffff;
+  for (int x = kh + lane; x < lh; x += 32) cand_h[x] = 0x7fffffff;
+  __syncwarp();
+  warp_bitonic(cand_c, lc, lane);
+  warp_bitonic(cand_h, lh, lane);
+  const int wc = min(ncand + 1, max_c), wh = min(nh, max_h);
+  int* rc = pad_c + (size_t)i * max_c;
+  int* rh = pad_h + (size_t)i * max_h;
+  if (lane == 0 && max_c > 0) rc[0] = i;
+  for (int x = lane; x + 1 < wc; x += 32) rc[x + 1] = cand_c[x];
+  for (int x = lane; x < wh; x += 32) rh[x] = cand_h[x];
+  if (lane == 0) {
+    if (nh > max_h) tbk::set_status(st, TB_ERR_CAPACITY, nh);
+    if (ncand + 1 > max_c) tbk::set_status(st, TB_ERR_CAPACITY, ncand + 1);
+    hcnt[i] = wh;
+    ccnt[i] = wc;
+  }
+}
+
+// Padded per-atom rows -> CSR (one warp per atom).
+__global__ void __launch_bounds__(NB_THREADS)
+compact_kernel(int n, const int* __restrict__ pad_h, const int* __restrict__ pad_c, int max_h,
+               int max_c, const int* __restrict__ h_off, int* __restrict__ h_idx,
+               const int* __restrict__ c_off, int* __restrict__ c_idx) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * NB_WARPS + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const int h0 = h_off[i], hn = h_off[i + 1] - h0;
+  const int c0 = c_off[i], cn = c_off[i + 1] - c0;
+  for (int x = lane; x < hn; x += 32) h_idx[h0 + x] = pad_h[(size_t)i * max_h + x];
+  for (int x = lane; x < cn; x += 32) c_idx[c0 + x] = pad_c[(size_t)i * max_c + x];
+}
+
 }  // namespace
+
+size_t neighbor_cell_capacity(int n) { return (size_t)(n < 32 ? 64 : 2 * n); }
 
 tb_status launch_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h_off,
                            int* h_idx, int* c_off, int* c_idx, cudaStream_t s) {
@@ -143,6 +322,29 @@ tb_status launch_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h
   const float Rh_pre2 = (float)((p.rm + 0.01) * (p.rm + 0.01));
   const float Rc_pre2 = (float)((p.Rc + 0.01) * (p.Rc + 0.01));
   const int grid = (n + NB_WARPS - 1) / NB_WARPS;
+  // cells of side >= Rc + 0.01 A, at least 3 per dimension, at most the capacity
+  int nc = (int)(L / (p.Rc + 0.01));
+  while (nc >= 3 && (size_t)nc * nc * nc > neighbor_cell_capacity(c->reserved_n)) --nc;
+  const int capc = p.max_cluster <= 128 ? 128 : (p.max_cluster <= 256 ? 256 : 512);
+  const size_t cell_smem = (size_t)NB_WARPS * (capc + 64) * sizeof(int);
+  if (nc >= 3 && p.max_cluster <= 512) {
+    const int ncell = nc * nc * nc;
+    TB_CUDA_TRY(cudaMemsetAsync(c->cell_cnt, 0, sizeof(int) * ncell, s));
+    cell_assign_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, pos, L, nc, c->atom_cell, c->cell_cnt);
+    scan1_kernel<<<1, 1024, 0, s>>>(ncell, c->cell_cnt, c->cell_off);
+    TB_CUDA_TRY(cudaMemsetAsync(c->cell_cnt, 0, sizeof(int) * ncell, s));
+    cell_fill_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, c->atom_cell, c->cell_off, c->cell_cnt,
+                                                     c->cell_atoms);
+    nbr_cell_kernel<<<grid, NB_THREADS, cell_smem, s>>>(
+        n, pos, posf, L, R2h, R2c, Rh_pre2, Rc_pre2, nc, c->atom_cell, c->cell_off,
+        c->cell_atoms, capc, c->scan_h, c->scan_c, c->pad_h, c->pad_c, p.max_hnbr,
+        p.max_cluster, c->d_status);
+    scan2_kernel<<<1, 1024, 0, s>>>(n, c->scan_h, h_off, c->scan_c, c_off);
+    compact_kernel<<<grid, NB_THREADS, 0, s>>>(n, c->pad_h, c->pad_c, p.max_hnbr, p.max_cluster,
+                                              h_off, h_idx, c_off, c_idx);
+    TB_CUDA_TRY(cudaGetLastError());
+    return TB_OK;
+  }
   nbr_kernel<0><<<grid, NB_THREADS, 0, s>>>(n, pos, posf, L, R2h, R2c, Rh_pre2, Rc_pre2,
                                             c->scan_h, c->scan_c, nullptr, nullptr,
                                             nullptr, nullptr, p.max_hnbr,

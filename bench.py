@@ -502,6 +502,7 @@ def run_md(args):
 
     def make(prec):
         s = tb.TBSystem(n, L, p, prec=prec, device=dev)
+        tb.binding.tb_profile_enable(s.ctx, True)
         s.set_positions(pos)
         s.vel.copy_(torch.as_tensor(vel, dtype=torch.float64))
         s.evaluate()
@@ -519,6 +520,7 @@ def run_md(args):
     barrier()
     step_ms, etot = md_trajectory(system, args.steps, flush, stream, True)
     barrier()
+    stage_ms = tb.binding.tb_profile_read(system.ctx)     # the last step's stages
     clk = clocks.stop() if clocks else None
     system.check()
     total_ms = sum(step_ms)
@@ -590,6 +592,7 @@ def run_md(args):
             "cpu_baseline": cpu_base,
             "clocks": clk,
             "gpu_launches": 14 * args.steps,
+            "stage_ms": stage_ms,
             "nve": {"energy_drift_eV_per_atom": float((etot[-1] - etot[0]) / n),
                     "energy_span_eV_per_atom": float((etot.max() - etot.min()) / n),
                     "fp64_path": fp64},

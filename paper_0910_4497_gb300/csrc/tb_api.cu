@@ -306,20 +306,15 @@ tb_status tb_md_step(tb_ctx* c, int n, double* pos, double* vel, double* F, doub
     return TB_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((st = launch_md_kick_drift(c, n, pos, vel, F, L, dt_fs, mass_amu, s)) != TB_OK) return st;
-  if ((st = launch_neighbors(c, n, pos, L, c->h_off, c->h_idx, c->c_off, c->c_idx, s)) != TB_OK)
-    return st;
-  if ((st = launch_assemble(c, n, pos, L, c->h_off, c->h_idx, c->Hblk, c->dHblk,
-                            c->p.prec == TB_PREC_MIXED ? c->Hmir : nullptr, s)) != TB_OK)
-    return st;
-  if ((st = launch_krylov(c, n, c->c_off, c->c_idx, c->h_off, c->h_idx, c->Hblk, c->Hmir,
-                          c->lambda, c->S, c->P, c->kdim, s)) != TB_OK)
-    return st;
-  if ((st = launch_eig(c, n, c->h_off, c->lambda, c->S, c->P, c->kdim, s)) != TB_OK) return st;
-  if ((st = launch_mu(c, n, c->lambda, c->S, 4.0 * n, c->mu, c->mu, c->ncount, s)) != TB_OK)
-    return st;
-  if ((st = launch_forces(c, n, pos, L, c->h_off, c->h_idx, c->dHblk, c->lambda, c->S, c->P,
-                          c->kdim, c->mu, F, energies, s)) != TB_OK)
-    return st;
+  TB_STAGE(c, 0, s, launch_neighbors(c, n, pos, L, c->h_off, c->h_idx, c->c_off, c->c_idx, s));
+  TB_STAGE(c, 1, s, launch_assemble(c, n, pos, L, c->h_off, c->h_idx, c->Hblk, c->dHblk,
+                                    c->p.prec == TB_PREC_MIXED ? c->Hmir : nullptr, s));
+  TB_STAGE(c, 2, s, launch_krylov(c, n, c->c_off, c->c_idx, c->h_off, c->h_idx, c->Hblk,
+                                  c->Hmir, c->lambda, c->S, c->P, c->kdim, s));
+  TB_STAGE(c, 3, s, launch_eig(c, n, c->h_off, c->lambda, c->S, c->P, c->kdim, s));
+  TB_STAGE(c, 4, s, launch_mu(c, n, c->lambda, c->S, 4.0 * n, c->mu, c->mu, c->ncount, s));
+  TB_STAGE(c, 5, s, launch_forces(c, n, pos, L, c->h_off, c->h_idx, c->dHblk, c->lambda, c->S,
+                                  c->P, c->kdim, c->mu, F, energies, s));
   return launch_md_kick(c, n, vel, F, dt_fs, mass_amu, energies, s);
 }
 

@@ -308,13 +308,17 @@ struct RhoArgs {
 
 // TA: type of the density-block contraction (FP32 in the mixed path, whose
 // P and S carry FP32 accuracy; FP64 otherwise).  Energy sums stay FP64.
+// One CTA per target: the weights f_k S[a][k] are formed once in shared
+// memory; each warp then takes row blocks q (the target and its Hamiltonian
+// neighbours), lanes over the eigenpairs k, and reduces the 16 entries of the
+// block rho^(i)_{q b, i a} = sum_k P[q,b,k] f_k S[a,k] with one butterfly.
 template <typename TA>
 __global__ void __launch_bounds__(RT) rho_kernel(const RhoArgs a) {
-  __shared__ TA fk[tbk::MAX_NT];
-  __shared__ TA sk[4 * tbk::MAX_NT];
+  __shared__ TA fs[4 * tbk::MAX_NT];           // f_k S[a][k]
   __shared__ double red[RT / 32 * 3];
   __shared__ double tot[3];
   const int i = blockIdx.x, NT = a.NT;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int m = a.kdim[i];
   const double mu = *a.mu;
   const double* lam = a.lambda + (size_t)i * NT;
@@ -330,10 +334,10 @@ __global__ void __launch_bounds__(RT) rho_kernel(const RhoArgs a) {
       v[1] += w * entropy_term(f);
       v[2] += w * f;
     }
-    fk[k] = (TA)f;
-    for (int al = 0; al < 4; ++al) sk[al * NT + k] = (TA)Si[al * NT + k];
+#pragma unroll
+    for (int al = 0; al < 4; ++al) fs[al * NT + k] = (TA)(f * Si[al * NT + k]);
   }
-  tbk::block_sum<double, 3>(v, red, tot);
+  tbk::block_sum<double, 3>(v, red, tot);          // also publishes fs
   if (threadIdx.x == 0) {
     a.per_target[5 * i + 0] = 2.0 * tot[0];
     a.per_target[5 * i + 1] = 2.0 * a.kT * tot[1];
@@ -341,13 +345,24 @@ __global__ void __launch_bounds__(RT) rho_kernel(const RhoArgs a) {
   }
   const int deg = a.h_off[i + 1] - a.h_off[i];
   const size_t base = (size_t)(i + a.h_off[i]);
-  const int nout = (deg + 1) * 16;
-  for (int q = threadIdx.x; q < nout; q += RT) {
-    const int blk = q >> 4, be = (q >> 2) & 3, al = q & 3;
-    const double* pr = a.P + ((base + blk) * 4 + be) * NT;
-    TA t = (TA)0;
-    for (int k = 0; k < m; ++k) t += (TA)pr[k] * fk[k] * sk[al * NT + k];
-    a.rho[(base + blk) * 16 + be * 4 + al] = (double)t;
+  for (int blk = warp; blk <= deg; blk += RT / 32) {
+    const double* pr = a.P + (base + blk) * 4 * NT;
+    TA acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = (TA)0;
+    for (int k = lane; k < m; k += 32) {
+      TA pb[4], sa[4];
+#pragma unroll
+      for (int be = 0; be < 4; ++be) pb[be] = (TA)pr[be * NT + k];
+#pragma unroll
+      for (int al = 0; al < 4; ++al) sa[al] = fs[al * NT + k];
+#pragma unroll
+      for (int be = 0; be < 4; ++be)
+#pragma unroll
+        for (int al = 0; al < 4; ++al) acc[be * 4 + al] += pb[be] * sa[al];
+    }
+    const TA t = tbk::warp_reduce16(acc, lane);   // lanes 2q hold entry q = be*4 + al
+    if ((lane & 1) == 0) a.rho[(base + blk) * 16 + (lane >> 1)] = (double)t;
   }
 }
 

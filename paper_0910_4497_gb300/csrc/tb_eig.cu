@@ -462,22 +462,87 @@ __global__ void __launch_bounds__(XW_MAX * GT, 2) eig_warp_kernel(const XArgs a)
     if (nn < 0.25f) restart_column(g, d, e, m, lam[c], tiny, Y, P, first, c, fs);
   }
 
-  // ---- 4. back-transformation U = H_0 ... H_{m-3} Y; thread t owns column t
-  if (t < m) {
-    float* yk = Y + t;
-    for (int j = m - 3; j >= 0; --j) {
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      int x = j + 1;
-      for (; x + 3 < m; x += 4) {
-        s0 += H[x * P + j] * yk[x * P];
-        s1 += H[(x + 1) * P + j] * yk[(x + 1) * P];
-        s2 += H[(x + 2) * P + j] * yk[(x + 2) * P];
-        s3 += H[(x + 3) * P + j] * yk[(x + 3) * P];
+  // ---- 4. back-transformation U = H_0 ... H_{m-3} Y, eight reflections at a
+  // time in compact WY form: H_jb ... H_jb+nb-1 = I - V Tb V^T with V the
+  // reflection vectors (stored in columns jb.. of H) and Tb upper triangular,
+  // Tb_ii = 2, Tb[0:i, i] = -2 Tb[0:i, 0:i] V[:, 0:i]^T v_i (LAPACK's dlarft,
+  // forward); each thread applies the blocks to its column, last block first.
+  {
+    const int nref = m - 2;
+    float* Tb = slc;                             // 8 x 8, then the Gram entries
+    float* Gv = slc + 64;
+    for (int jb = nref > 0 ? ((nref - 1) / 8) * 8 : -1; jb >= 0; jb -= 8) {
+      const int nb = min(8, nref - jb);
+      gsync(g);
+      if (t < nb * nb) {                         // Gram entries v_a . v_b, a < b
+        const int ra = t / nb, rb = t - ra * nb;
+        if (ra < rb) {
+          float s0 = 0.f, s1 = 0.f;
+          int x = jb + rb + 1;
+          for (; x + 1 < m; x += 2) {
+            s0 += H[x * P + jb + ra] * H[x * P + jb + rb];
+            s1 += H[(x + 1) * P + jb + ra] * H[(x + 1) * P + jb + rb];
+          }
+          if (x < m) s0 += H[x * P + jb + ra] * H[x * P + jb + rb];
+          Gv[ra * 8 + rb] = s0 + s1;
+        }
       }
-      for (; x < m; ++x) s0 += H[x * P + j] * yk[x * P];
-      const float f0 = 2.f * ((s0 + s1) + (s2 + s3));
-#pragma unroll 4
-      for (int xx = j + 1; xx < m; ++xx) yk[xx * P] -= f0 * H[xx * P + j];
+      gsync(g);
+      if (t == 0) {
+        for (int ii = 0; ii < nb; ++ii) {
+          Tb[ii * 8 + ii] = 2.f;
+          for (int kk = 0; kk < ii; ++kk) {
+            float acc = 0.f;
+            for (int l = kk; l < ii; ++l) acc += Tb[kk * 8 + l] * Gv[l * 8 + ii];
+            Tb[kk * 8 + ii] = -2.f * acc;
+          }
+        }
+      }
+      gsync(g);
+      if (t < m) {
+        float* yk = Y + t;
+        float w[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) w[r] = 0.f;
+        // rows jb+1 .. jb+nb-1 meet only the first reflections of the block
+        for (int x = jb + 1; x < min(jb + nb, m); ++x) {
+          const float yx = yk[x * P];
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+            if (r < nb && x > jb + r) w[r] += H[x * P + jb + r] * yx;
+        }
+        for (int x = jb + nb; x < m; ++x) {
+          const float yx = yk[x * P];
+          const float* hx = H + x * P + jb;
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+            if (r < nb) w[r] += hx[r] * yx;
+        }
+        float w2[8];
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) {
+          float acc = 0.f;
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk)
+            if (ii < nb && kk >= ii && kk < nb) acc += Tb[ii * 8 + kk] * w[kk];
+          w2[ii] = acc;
+        }
+        for (int x = jb + 1; x < min(jb + nb, m); ++x) {
+          float acc = 0.f;
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+            if (r < nb && x > jb + r) acc += H[x * P + jb + r] * w2[r];
+          yk[x * P] -= acc;
+        }
+        for (int x = jb + nb; x < m; ++x) {
+          const float* hx = H + x * P + jb;
+          float acc = 0.f;
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+            if (r < nb) acc += hx[r] * w2[r];
+          yk[x * P] -= acc;
+        }
+      }
     }
   }
   gsync(g);

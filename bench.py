@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reorth-passes", type=int, default=1)
+    ap.add_argument("--reorth-every", type=int, default=4)
     ap.add_argument("--workload", default="c60_1920",
                     choices=["c60_1920", "md15360", "autograd1920", "diamond_eos"])
     ap.add_argument("--fd-coords", type=int, default=8)
@@ -252,6 +253,7 @@ def run_ours(args):
 
     cfg, pos, L, p = workload()
     p["reorth_passes"] = args.reorth_passes
+    p["reorth_every"] = args.reorth_every
     n = len(pos)
     cpu_base = None
     ref = None
@@ -365,7 +367,8 @@ def run_ours(args):
                 "precision": args.prec, "l2": "flushed between steps (256 MB write)",
                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                 "graph": "one CUDA graph per force evaluation",
-                "reorth_passes": args.reorth_passes}),
+                "reorth_passes": args.reorth_passes,
+                "reorth_every": args.reorth_every}),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 3 * 8,
                     "d2h_bytes_per_step": n * 3 * 8 + 8 * 8},
             "roofline": roof,
@@ -482,6 +485,7 @@ def run_md(args):
 
     cfg, pos, vel, L, p = md_workload()
     p["reorth_passes"] = args.reorth_passes
+    p["reorth_every"] = args.reorth_every
     n = len(pos)
     dt = cfg["dt_fs"]
     cpu_base = None
@@ -586,7 +590,8 @@ def run_md(args):
                        "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "graph": "one CUDA graph per MD step",
-                       "reorth_passes": args.reorth_passes},
+                       "reorth_passes": args.reorth_passes,
+                       "reorth_every": args.reorth_every},
             "e2e": {"value": e2e_value, "unit": MD_UNIT, "h2d_bytes_per_step": 3 * n * 3 * 8,
                     "d2h_bytes_per_step": 3 * n * 3 * 8 + 8 * 8},
             "cpu_baseline": cpu_base,

@@ -83,6 +83,9 @@ typedef struct tb_params {
   int reorth_passes;  /* classical Gram-Schmidt passes against all blocks: 1 or 2*/
   int mu_max_iter;    /* cap on mu search passes (e.g. 100)                      */
   long long timeout_cycles; /* budget of any device spin-wait, in SM clocks      */
+  int reorth_every;   /* full reorthogonalisation against all earlier blocks
+                       * every this many Lanczos steps (>= 1; 1 = every step);
+                       * the other steps project out the last two blocks only */
 } tb_params;
 
 typedef struct tb_ctx tb_ctx;

@@ -35,7 +35,7 @@ class TBParams(ctypes.Structure):
                  "mu_tol")] + \
               [(k, ctypes.c_int) for k in
                ("r", "prec", "max_hnbr", "max_cluster", "reorth_passes", "mu_max_iter")] + \
-              [("timeout_cycles", ctypes.c_longlong)]
+              [("timeout_cycles", ctypes.c_longlong), ("reorth_every", ctypes.c_int)]
 
 
 class TBError(RuntimeError):
@@ -130,6 +130,7 @@ def make_params(p, prec):
     tp.prec = TB_PREC_FP64 if prec in ("fp64", TB_PREC_FP64) else TB_PREC_MIXED
     tp.defl_tol = float(p.get("defl_tol", 1e-9 if tp.prec == TB_PREC_FP64 else 1e-4))
     tp.reorth_passes = int(p.get("reorth_passes", 2))
+    tp.reorth_every = int(p.get("reorth_every", 1))
     tp.mu_tol = float(p.get("mu_tol", 1e-12))
     tp.mu_max_iter = int(p.get("mu_max_iter", 100))
     if "timeout_cycles" in p:

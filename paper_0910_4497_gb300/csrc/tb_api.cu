@@ -21,6 +21,7 @@ tb_status check_params(const tb_params& p) {
   if (p.max_hnbr < 1 || p.max_hnbr > tbk::MAX_HNBR) return TB_ERR_INVALID_ARG;
   if (p.max_cluster < 1 || p.max_cluster > tbk::MAX_CLUSTER) return TB_ERR_INVALID_ARG;
   if (p.reorth_passes < 1 || p.reorth_passes > 2) return TB_ERR_INVALID_ARG;
+  if (p.reorth_every < 1) return TB_ERR_INVALID_ARG;
   if (p.mu_max_iter < 1 || !(p.mu_tol > 0.0) || !(p.defl_tol >= 0.0)) return TB_ERR_INVALID_ARG;
   if (p.timeout_cycles <= 0) return TB_ERR_INVALID_ARG;
   if (!finite_pos(p.Es) || !finite_pos(p.Ep)) return TB_ERR_INVALID_ARG;
@@ -135,6 +136,7 @@ tb_status tb_params_default(tb_params* p) {
   p->max_hnbr = 32;
   p->max_cluster = 128;
   p->reorth_passes = 2;
+  p->reorth_every = 1;
   p->mu_max_iter = 100;
   p->timeout_cycles = 4000000000LL;
   return TB_OK;

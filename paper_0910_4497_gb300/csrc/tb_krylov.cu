@@ -69,6 +69,7 @@ __device__ __forceinline__ vec4<TV> ldg4(const TV* p) {
 template <typename TV>
 struct KryArgs {
   int n, r, max_cluster, max_hnbr, reorth_passes;
+  int reorth_every;         // full reorthogonalisation every this many steps (1: always)
   double Es, Ep, defl_tol;
   const int* c_off;
   const int* c_idx;
@@ -347,13 +348,15 @@ __global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryAr
       }
       __syncthreads();
       // ---- classical Gram-Schmidt against V_1..V_k (pass 0 yields A_k); on
-      // the last step only A_k is needed
+      // the last step only A_k is needed; between full passes (every
+      // reorth_every steps) only V_{k-1} and V_k are projected out
       const int passes = (k == r - 1) ? 1 : a.reorth_passes;
       TV g[10];                             // Gram partials of the final W
 #pragma unroll
       for (int q = 0; q < 10; ++q) g[q] = (TV)0;
       for (int pass = 0; pass < passes; ++pass) {
-        const int b0 = (k == r - 1) ? k : 0;
+        const bool full = a.reorth_every <= 1 || (k % a.reorth_every) == a.reorth_every - 1;
+        const int b0 = (k == r - 1) ? k : (full ? 0 : (k > 0 ? k - 1 : 0));
         const int nb = k + 1 - b0;
         const int nseg = nb >= KW ? 1 : KW / nb;
         const int items = nb * nseg;
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryAr
         for (int row = tid; row < D; row += KT) {
           vec4<TV> x = ld4(W + row * 4);
 #pragma unroll 4
-          for (int b = 0; b <= k; ++b) {
+          for (int b = b0; b <= k; ++b) {
             const vec4<TV> v = ld4(V + (size_t)b * Dmax * 4 + row * 4);
             const TV* cb = Cc + b * 16;
 #pragma unroll
@@ -655,6 +658,7 @@ tb_status launch_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const i
   KryArgs<TV> a;
   a.n = n; a.r = p.r; a.max_cluster = p.max_cluster; a.max_hnbr = p.max_hnbr;
   a.reorth_passes = p.reorth_passes;
+  a.reorth_every = p.reorth_every;
   a.Es = p.Es; a.Ep = p.Ep; a.defl_tol = p.defl_tol;
   a.c_off = c_off; a.c_idx = c_idx; a.h_off = h_off; a.h_idx = h_idx; a.H = H;
   a.T = c->T; a.Y = reinterpret_cast<TV*>(c->Y); a.colmask = c->colmask;

@@ -203,6 +203,15 @@ def test_forces_cfg1_full_size_graph(tb, prec):
     compare_full(tb, "cfg1", pos, L, p, prec, graph=True, workers=8)
 
 
+def test_benchmark_configuration_full_size(tb):
+    """The benchmark's settings on the 1920-atom cell: one classical
+    Gram-Schmidt pass, full reorthogonalisation every fourth Lanczos step
+    (the steps between project out the last two blocks only)."""
+    pos, L, p = cfg_system(1)
+    compare_full(tb, "cfg1", pos, L, dict(p, reorth_passes=1, reorth_every=4), "mixed",
+                 graph=True, workers=8)
+
+
 def test_forces_bridged_uneven_clusters(tb):
     pos, L, p = cfg_system(2, ncell=2, r=10)
     s, ref = compare_full(tb, "cfg2small", pos, L, p, "fp64")

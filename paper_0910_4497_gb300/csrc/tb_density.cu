@@ -112,6 +112,32 @@ __device__ __forceinline__ void occupation(double x, double& f, double& g) {
   }
 }
 
+// Adds w f and w f(1-f) of one (lambda, w) pair at mu.  Pairs far from mu
+// (|x| > 15.5 by an FP32 estimate of x from the FP32 copies lf, wf) take f or
+// 1 - f (below 2e-7) from the FP32 exponential, with absolute error ~1e-14 and
+// only FP64 additions; the others take the FP64 path of occupation().
+__device__ __forceinline__ void pair_occ(double l, double w, float lf, float wf, double mu,
+                                         float muf, double ikT, float ikTf, double& n,
+                                         double& d) {
+  const float xf = (lf - muf) * ikTf;
+  if (xf > 15.5f) {
+    const float e = __expf(fmaxf(-xf, -87.f));
+    const float fw = wf * __fdividef(e, 1.f + e);
+    n += (double)fw;
+    d += (double)fw;                       // f (1 - f) = f to FP32 accuracy here
+  } else if (xf < -15.5f) {
+    const float e = __expf(fmaxf(xf, -87.f));
+    const float tw = wf * __fdividef(e, 1.f + e);
+    n += w - (double)tw;
+    d += (double)tw;
+  } else {
+    double f, g;
+    occupation((l - mu) * ikT, f, g);
+    n += w * f;
+    d += w * g;
+  }
+}
+
 // Every block publishes M partials in generation buffer `gen`, passes the grid
 // barrier, then sums all blocks' partials in block order (fixed order: every
 // block obtains bitwise the same totals).  Returns false on barrier timeout.
@@ -141,6 +167,7 @@ __device__ bool grid_allreduce(const double (&v)[M], const MuArgs& a, unsigned& 
 __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
   extern __shared__ __align__(16) unsigned char mu_smem[];
   double2* pairs = reinterpret_cast<double2*>(mu_smem);   // (lambda, w)
+  float2* pairsf = reinterpret_cast<float2*>(pairs + a.per_block);   // FP32 copies
   __shared__ double red[MT / 32 * 16];
   __shared__ double tot[16];
   __shared__ int sflag;
@@ -150,7 +177,7 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
   const long long q1 = min(a.npairs, q0 + a.per_block);
   const int nloc = (int)max(0ll, q1 - q0);
   unsigned gen = 0;
-  // pair accessor: shared-memory copy when staged, else recomputed from global
+  // pair accessors: shared-memory copies when staged, else recomputed from global
   auto get = [&](int t, double& l, double& w) {
     if (a.staged) {
       const double2 v = pairs[t];
@@ -161,10 +188,23 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
       w = pair_weight(a.S, a.NT, q0 + t);
     }
   };
+  auto getf = [&](int t, float& lf, float& wf) {
+    if (a.staged) {
+      const float2 v = pairsf[t];
+      lf = v.x;
+      wf = v.y;
+    } else {
+      lf = (float)a.lambda[q0 + t];
+      wf = (float)pair_weight(a.S, a.NT, q0 + t);
+    }
+  };
   double lmin = 1e300, lmax = -1e300;
   for (int t = threadIdx.x; t < nloc; t += MT) {
     const double l = a.lambda[q0 + t], w = pair_weight(a.S, a.NT, q0 + t);
-    if (a.staged) pairs[t] = make_double2(l, w);
+    if (a.staged) {
+      pairs[t] = make_double2(l, w);
+      pairsf[t] = make_float2((float)l, (float)w);
+    }
     if (w > 0.0) { lmin = fmin(lmin, l); lmax = fmax(lmax, l); }
   }
   // ---- bracket: [min lam - 40 kT, max lam + 40 kT] over pairs with weight
@@ -205,11 +245,12 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
 #pragma unroll
     for (int t = 0; t < MU_NPT; ++t) cnt[t] = 0.f;
     const float dx = (float)(h * ikT);
+    const float lof = (float)lo, ikTf = (float)ikT;
     for (int t = threadIdx.x; t < nloc; t += MT) {
-      double l, w;
-      get(t, l, w);
-      if (w == 0.0) continue;
-      const float x0 = (float)((l - lo) * ikT), wf = (float)w;
+      float lf, wf;
+      getf(t, lf, wf);
+      if (wf == 0.f) continue;
+      const float x0 = (lf - lof) * ikTf;
 #pragma unroll
       for (int u = 0; u < MU_NPT; ++u) {
         const float x = fminf(fmaxf(x0 - (u + 1) * dx, -80.f), 80.f);
@@ -239,23 +280,22 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
   double dxold = hi - lo, dx = dxold;
   double Nmu = 0.0;
   bool conv = false;
+  const float ikTf = (float)ikT;
   for (int it = 0; it < a.max_iter; ++it) {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     const bool ends = it == 0 && check;
+    const float muf = (float)mu, lof = (float)lo, hif = (float)hi;
     for (int t = threadIdx.x; t < nloc; t += MT) {
+      float lf, wf;
+      getf(t, lf, wf);
+      if (wf == 0.f) continue;
       double l, w;
       get(t, l, w);
-      if (w == 0.0) continue;
-      double f, g;
-      occupation((l - mu) * ikT, f, g);
-      v[0] += w * f;
-      v[1] += w * g;
+      pair_occ(l, w, lf, wf, mu, muf, ikT, ikTf, v[0], v[1]);
       if (ends) {
-        double f2, g2;
-        occupation((l - lo) * ikT, f2, g2);
-        v[2] += w * f2;
-        occupation((l - hi) * ikT, f2, g2);
-        v[3] += w * f2;
+        double dd = 0.0;
+        pair_occ(l, w, lf, wf, lo, lof, ikT, ikTf, v[2], dd);
+        pair_occ(l, w, lf, wf, hi, hif, ikT, ikTf, v[3], dd);
       }
     }
     if (!grid_allreduce<4>(v, a, gen, red, tot, &sflag)) return;
@@ -602,7 +642,7 @@ tb_status launch_mu_nt(tb_ctx* c, int n, int NT, const double* lambda, const dou
   // one block per SM; each block stages its contiguous share of the pairs
   const int grid = c->mu_grid;
   a.per_block = (a.npairs + grid - 1) / grid;
-  const size_t stage = (size_t)a.per_block * sizeof(double2);
+  const size_t stage = (size_t)a.per_block * (sizeof(double2) + sizeof(float2));
   a.staged = stage <= (size_t)c->mu_smem_max ? 1 : 0;
   TB_CUDA_TRY(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), s));
   cudaLaunchConfig_t cfg = {};
@@ -749,7 +789,7 @@ extern "C" tb_status tb_find_mu_static(int n, int r, const double* lambda, const
   a.st = status;
   const int grid = d.sms;
   a.per_block = (a.npairs + grid - 1) / grid;
-  const size_t stage = (size_t)a.per_block * sizeof(double2);
+  const size_t stage = (size_t)a.per_block * (sizeof(double2) + sizeof(float2));
   a.staged = stage <= (size_t)d.smem_max ? 1 : 0;
   TB_CUDA_TRY(cudaMemsetAsync(line, 0, sizeof(unsigned), s));       // barrier counter
   TB_CUDA_TRY(cudaMemsetAsync(status, 0, 2 * sizeof(int), s));      // caller's status words

@@ -14,7 +14,8 @@ following the paper's steps in order:
 * Sec. 3, Eq. (Krylov) and the block form of Eq. (lanczos_blas3): block Krylov
   space seeded with the target atom's four orbitals, block Lanczos with full
   reorthogonalisation, the projected matrix T = V^T H V and its eigenpairs
-  (``krylov``),
+  (``krylov``), and its m-target Level-3 form on the union cluster of a
+  group of targets (``grouping``),
 * Sec. 2: density matrix rho = sum_m |m> f(e_m) <m| and the force
   <F_i> = Tr[rho F_i] (``density``),
 * plus the velocity-Verlet step of the MD workload (``md``), the exact
@@ -24,5 +25,5 @@ following the paper's steps in order:
 
 Library primitives used as single steps: numpy matmul, numpy.linalg.eigh.
 """
-from . import model, neighbors, hamiltonian, krylov, density, md, exact, local_exact, virial  # noqa: F401
+from . import model, neighbors, hamiltonian, krylov, density, md, exact, local_exact, virial, grouping  # noqa: F401
 from .pipeline import force_evaluation, OracleResult  # noqa: F401

@@ -15,12 +15,15 @@ from .neighbors import neighbor_lists, cluster_lists
 from .hamiltonian import BondTable, cluster_hamiltonian
 from .krylov import block_lanczos, spectral_record
 from .density import find_mu, band_terms, rho_blocks, forces
+from .grouping import group_atoms, krylov_lists
 
 
 @dataclass
 class OracleResult:
     hlists: list
     clists: list
+    klists: list = None                         # per target: the atoms its Krylov run spans
+    groups: list = None                         # target groups (m-target form), or None
     lam: list = field(default_factory=list)     # per target (kdim,)
     S: list = field(default_factory=list)       # per target (4, kdim)
     P: list = field(default_factory=list)       # per target ((1+z)*4, kdim)
@@ -79,17 +82,23 @@ def spectral_records(pos, L, p, hlists, clists, targets, bonds=None, workers=1):
     return [rec for part in parts for rec in part]
 
 
-def force_evaluation(pos, L, p, workers=1, with_forces=True):
+def force_evaluation(pos, L, p, workers=1, with_forces=True, group_m=1):
     """Full evaluation.  `p` needs the model constants plus kT, Rc, r, defl_tol
-    and n_electrons_per_atom."""
+    and n_electrons_per_atom.  group_m > 1: the m-target form of Eq.
+    (lanczos_blas3), each target's Krylov run on its group's union cluster
+    (oracle.grouping)."""
     pos = np.asarray(pos, dtype=np.float64)
     n = len(pos)
     hl = neighbor_lists(pos, L, p["rm"])
     cl = cluster_lists(pos, L, p["Rc"])
+    groups, kl = None, cl
+    if group_m > 1:
+        groups = group_atoms(pos, L, group_m)
+        kl = krylov_lists(cl, groups)
     bonds = BondTable(pos, L, hl, p)
-    recs = spectral_records(pos, L, p, hl, cl, range(n), bonds=bonds,
+    recs = spectral_records(pos, L, p, hl, kl, range(n), bonds=bonds,
                             workers=workers)
-    res = OracleResult(hlists=hl, clists=cl)
+    res = OracleResult(hlists=hl, clists=cl, klists=kl, groups=groups)
     res.lam = [x[0] for x in recs]
     res.S = [x[1] for x in recs]
     res.P = [x[2] for x in recs]

@@ -69,6 +69,10 @@ def parse():
                     choices=["c60_1920", "md15360", "autograd1920", "diamond_eos"])
     ap.add_argument("--fd-coords", type=int, default=8)
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--group-m", type=int, default=1,
+                    help="targets per group of the m-target form (1 = per-target clusters)")
+    ap.add_argument("--max-union", type=int, default=320,
+                    help="union-cluster capacity of the m-target form")
     return ap.parse_args()
 
 
@@ -98,11 +102,12 @@ def config_dict(cfg, n, extra):
 # ---------------------------------------------------------------- CPU oracle
 
 def time_oracle_full(pos, L, p):
-    """One full oracle force evaluation, single process."""
+    """One full oracle force evaluation, single process (the m-target form when
+    p holds group_m > 1)."""
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     import oracle
     t0 = time.perf_counter()
-    res = oracle.force_evaluation(pos, L, p)
+    res = oracle.force_evaluation(pos, L, p, group_m=p.get("group_m", 1))
     return time.perf_counter() - t0, res
 
 
@@ -222,10 +227,31 @@ def algorithmic_sweep_bytes(system, prec):
     return total
 
 
-def kernel_traffic(prec):
+def algorithmic_sweep_bytes_grouped(system, prec):
+    """Bytes per grouped Krylov launch of the H.V sweeps: per group and sweep
+    nnzb_u*(16 b_H + 4) + 2*(4 n_u * 4 m_g * b_V) over the union cluster u of the
+    group's m_g targets (H read once for all of them), times r sweeps."""
+    hl, cl = system.lists()
+    g_off = system.g_off.cpu().numpy()
+    g_idx = system.g_idx.cpu().numpy()
+    bH = 8 if prec == "fp64" else 4
+    r = system.tp.r
+    hsets = [set(x.tolist()) for x in hl]
+    total = 0
+    for q in range(len(g_off) - 1):
+        mem = g_idx[g_off[q]:g_off[q + 1]]
+        u = set()
+        for i in mem:
+            u |= set(cl[i].tolist())
+        nnzb = len(u) + sum(len(hsets[a] & u) for a in u)
+        total += r * (nnzb * (16 * bH + 4) + 2 * (4 * len(u) * 4 * len(mem) * bH))
+    return total
+
+
+def kernel_traffic(prec, name="krylov_traffic.json"):
     """DRAM bytes per Krylov launch from the committed ncu summary, or None if
     the kernel source changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "krylov_traffic.json")
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
@@ -261,6 +287,10 @@ def run_ours(args):
     cfg, pos, L, p = workload()
     p["reorth_passes"] = args.reorth_passes
     p["reorth_every"] = args.reorth_every
+    grouped = args.group_m > 1
+    if grouped:
+        p["group_m"] = args.group_m
+        p["max_union"] = args.max_union
     n = len(pos)
     cpu_base = None
     ref = None
@@ -347,25 +377,29 @@ def run_ours(args):
     if rank == 0:
         kry = [v for v in stage_ms["krylov"] if v > 0]
         kry_ms = statistics.mean(kry) if kry else None
-        alg = algorithmic_sweep_bytes(system, args.prec)
+        alg = (algorithmic_sweep_bytes_grouped(system, args.prec) if grouped
+               else algorithmic_sweep_bytes(system, args.prec))
         peaks = {}
         pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
         if os.path.exists(pk):
             peaks = json.load(open(pk))
         hbm = peaks.get("hbm_gbs", 6800.0)
         achieved = alg / (kry_ms * 1e-3) / 1e9 if kry_ms else None
-        roof = {"bound": "hbm", "kernel": "krylov_kernel (block Lanczos H.V sweeps + "
-                "reorthogonalisation, one CTA per target)",
+        kname = ("krylov_group_kernel (m-target block Lanczos on union clusters, one CTA "
+                 "per group)" if grouped else "krylov_kernel (block Lanczos H.V sweeps + "
+                 "reorthogonalisation, one CTA per target)")
+        roof = {"bound": "hbm", "kernel": kname,
                 "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "frac": achieved / hbm if achieved else None,
-                "traffic": kernel_traffic(args.prec),
+                "traffic": kernel_traffic(args.prec, "krylov_group_traffic.json" if grouped
+                                          else "krylov_traffic.json"),
                 "algorithmic_bytes_per_launch": alg, "kernel_ms": kry_ms}
         stages = {k: (statistics.mean([x for x in v if x >= 0]) if any(x >= 0 for x in v)
                       else None) for k, v in stage_ms.items()}
         # lists + 1 assembly + 1 Krylov + eigensolver (1 mixed, 2 FP64) + 1 mu + 4 forces/energies
         launches_per_step = (list_launches(L, p["Rc"]) + 1 + 1 + (1 if args.prec == "mixed" else 2)
-                             + 1 + 4)
+                             + 1 + 4 + (2 if grouped else 0))     # grouping: count + scatter
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -376,7 +410,9 @@ def run_ours(args):
                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                 "graph": "one CUDA graph per force evaluation",
                 "reorth_passes": args.reorth_passes,
-                "reorth_every": args.reorth_every}),
+                "reorth_every": args.reorth_every,
+                **({"group_m": args.group_m, "max_union": args.max_union,
+                    "form": "m-target union clusters (Eq. lanczos_blas3)"} if grouped else {})}),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 3 * 8,
                     "d2h_bytes_per_step": n * 3 * 8 + 8 * 8},
             "roofline": roof,

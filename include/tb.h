@@ -86,6 +86,10 @@ typedef struct tb_params {
   int reorth_every;   /* full reorthogonalisation against all earlier blocks
                        * every this many Lanczos steps (>= 1; 1 = every step);
                        * the other steps project out the last two blocks only */
+  int group_m;        /* targets per group of the m-target form (1..4; 1 = one
+                       * target per cluster, the default); see tb_group_atoms */
+  int max_union;      /* capacity of a group's union cluster (atoms, <= 1024);
+                       * 0 = min(1024, group_m * max_cluster)                   */
 } tb_params;
 
 typedef struct tb_ctx tb_ctx;
@@ -207,19 +211,63 @@ tb_status tb_forces(tb_ctx* ctx, int n, const double* pos, double L,
  * pos, vel, F [n*3] in/out.  F on entry must be the force at pos.
  * energies [8] out as in tb_forces, with energies[7] = kinetic energy (eV).
  * n_electrons = 4 n.  Uses the context's own list/H/spectral buffers.
+ * With group_m > 1 the Krylov stage is the m-target form (tb_group_atoms and
+ * tb_krylov_density_grouped on the context's own groups, regrouped every step).
  */
 tb_status tb_md_step(tb_ctx* ctx, int n, double* pos, double* vel, double* F,
                      double L, double dt_fs, double mass_amu, double* energies,
                      void* stream);
 
 /*
+ * f2. Groups of m = group_m target atoms for the m-target form of the block
+ * recursion (Sec. 3, Eq. (lanczos_blas3)); the paper leaves the grouping open,
+ * this is the library's spatial reading.  The grid has g^3 cells, g the
+ * largest integer with m g^3 <= n (capped at 1024); atom i lies in cell
+ *   c = floor((x_i / L) * g) per component (each operation rounded, FP64),
+ *   clamped to [0, g-1];
+ * its key is (Morton code of c, i), the code taking bit b of c_x, c_y, c_z to
+ * bits 3b, 3b+1, 3b+2.  The atoms sorted by key are cut into consecutive
+ * groups of m; the last group holds the remainder.  Bit-exact.
+ * pos   [n*3] FP64, each coordinate in [0, L)
+ * g_off [ceil(n/m) + 1] out: group q is g_idx[g_off[q] .. g_off[q+1])
+ * g_idx [n] out: the atoms in key order
+ * Workspace: n ints of the context.  Any group_m in 1..4.
+ */
+tb_status tb_group_atoms(tb_ctx* ctx, int n, const double* pos, double L, int* g_off,
+                         int* g_idx, void* stream);
+
+/*
+ * f2. a3-a7 in the m-target form (Sec. 3, Eq. (lanczos_blas3)).  For each
+ * group q of targets g_idx[g_off[q] .. g_off[q+1]) (1..group_m targets, any
+ * partition of the atoms, e.g. from tb_group_atoms): the union of the targets'
+ * clusters is formed and each target's block Krylov space is built from its own
+ * four orbitals in the Hamiltonian of that union (A_k, B_k block diagonal over
+ * the group, one sweep of H over all the group's columns).  The outputs, their
+ * layout and the projected eigensolve are those of tb_krylov_density; with
+ * groups of one target the result is tb_krylov_density's up to rounding.
+ * Needs a context created with group_m >= 2 (else TB_ERR_INVALID_ARG).
+ * A union larger than max_union sets TB_ERR_CAPACITY (info = its size) and
+ * leaves the group's targets with an empty record; a group of a size outside
+ * 1..group_m, or a target whose cluster list does not start with it, sets
+ * TB_ERR_INVALID_ARG (info = the group or the target).  Atoms in no group get
+ * no output.
+ */
+tb_status tb_krylov_density_grouped(tb_ctx* ctx, int n, int n_groups, const int* g_off,
+                                    const int* g_idx, const int* c_off, const int* c_idx,
+                                    const int* h_off, const int* h_idx,
+                                    const double* Hblk, const float* Hmirror,
+                                    double* lambda, double* S, double* P, int* kdim,
+                                    void* stream);
+
+/*
  * Stage timing (tracing aid).  When enabled, every later call records a pair of
  * CUDA events around each of its stages on its stream (as external event nodes
  * when the stream is being captured into a graph, so graph replays record them
  * too).  Stages: 0 lists, 1 assembly, 2 block Lanczos, 3 projected
- * eigensolve + spectral record, 4 mu, 5 density blocks + forces + energies.
+ * eigensolve + spectral record, 4 mu, 5 density blocks + forces + energies,
+ * 6 grouping of the targets (tb_group_atoms, m-target form only).
  * tb_profile_enable creates the events (not capturable).
- * tb_profile_read (host out ms[6]) returns the elapsed time of each stage's most
+ * tb_profile_read (host out ms[7]) returns the elapsed time of each stage's most
  * recent execution, or -1 for a stage not yet run; the caller synchronises first.
  */
 tb_status tb_profile_enable(tb_ctx* ctx, int enable);

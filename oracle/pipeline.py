@@ -82,18 +82,20 @@ def spectral_records(pos, L, p, hlists, clists, targets, bonds=None, workers=1):
     return [rec for part in parts for rec in part]
 
 
-def force_evaluation(pos, L, p, workers=1, with_forces=True, group_m=1):
+def force_evaluation(pos, L, p, workers=1, with_forces=True, group_m=1, groups=None):
     """Full evaluation.  `p` needs the model constants plus kT, Rc, r, defl_tol
     and n_electrons_per_atom.  group_m > 1: the m-target form of Eq.
-    (lanczos_blas3), each target's Krylov run on its group's union cluster
-    (oracle.grouping)."""
+    (lanczos_blas3), each target's Krylov run on its group's union cluster, the
+    groups from oracle.grouping.group_atoms unless `groups` (a partition of the
+    atoms into lists) is given."""
     pos = np.asarray(pos, dtype=np.float64)
     n = len(pos)
     hl = neighbor_lists(pos, L, p["rm"])
     cl = cluster_lists(pos, L, p["Rc"])
-    groups, kl = None, cl
-    if group_m > 1:
+    kl = cl
+    if groups is None and group_m > 1:
         groups = group_atoms(pos, L, group_m)
+    if groups is not None:
         kl = krylov_lists(cl, groups)
     bonds = BondTable(pos, L, hl, p)
     recs = spectral_records(pos, L, p, hl, kl, range(n), bonds=bonds,

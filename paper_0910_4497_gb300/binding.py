@@ -25,7 +25,7 @@ EXPORTS = ["tb_params_default", "tb_ctx_create", "tb_ctx_destroy", "tb_ctx_reser
            "tb_assemble_H", "tb_krylov_density", "tb_find_mu", "tb_forces", "tb_md_step",
            "tb_profile_enable", "tb_profile_read", "tb_find_mu_static",
            "tb_virial", "tb_ctx_reserve_local", "tb_local_forward", "tb_local_gradient",
-           "tb_version"]
+           "tb_group_atoms", "tb_krylov_density_grouped", "tb_version"]
 
 
 class TBParams(ctypes.Structure):
@@ -35,7 +35,8 @@ class TBParams(ctypes.Structure):
                  "mu_tol")] + \
               [(k, ctypes.c_int) for k in
                ("r", "prec", "max_hnbr", "max_cluster", "reorth_passes", "mu_max_iter")] + \
-              [("timeout_cycles", ctypes.c_longlong), ("reorth_every", ctypes.c_int)]
+              [("timeout_cycles", ctypes.c_longlong), ("reorth_every", ctypes.c_int),
+               ("group_m", ctypes.c_int), ("max_union", ctypes.c_int)]
 
 
 class TBError(RuntimeError):
@@ -73,6 +74,8 @@ def load_library(path=LIB_PATH):
         "tb_ctx_reserve_local": [P, I],
         "tb_local_forward": [P, I, VP, D, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP],
         "tb_local_gradient": [P, I, VP, D, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP],
+        "tb_group_atoms": [P, I, VP, D, VP, VP, VP],
+        "tb_krylov_density_grouped": [P, I, I, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -133,6 +136,8 @@ def make_params(p, prec):
     tp.reorth_every = int(p.get("reorth_every", 1))
     tp.mu_tol = float(p.get("mu_tol", 1e-12))
     tp.mu_max_iter = int(p.get("mu_max_iter", 100))
+    tp.group_m = int(p.get("group_m", 1))
+    tp.max_union = int(p.get("max_union", 0))
     if "timeout_cycles" in p:
         tp.timeout_cycles = int(p["timeout_cycles"])
     return tp
@@ -193,6 +198,24 @@ def tb_krylov_density(ctx, n, c_off, c_idx, h_off, h_idx, Hblk, Hmirror, lam, S,
         _ptr(S, f64, "S"), _ptr(P, f64, "P"), _ptr(kdim, i32, "kdim"), _stream(stream)))
 
 
+def tb_group_atoms(ctx, n, pos, L, g_off, g_idx, stream=None):
+    i32, f64 = torch.int32, torch.float64
+    _check("tb_group_atoms", lib().tb_group_atoms(
+        ctx, n, _ptr(pos, f64, "pos"), float(L), _ptr(g_off, i32, "g_off"),
+        _ptr(g_idx, i32, "g_idx"), _stream(stream)))
+
+
+def tb_krylov_density_grouped(ctx, n, n_groups, g_off, g_idx, c_off, c_idx, h_off, h_idx,
+                              Hblk, Hmirror, lam, S, P, kdim, stream=None):
+    i32, f64 = torch.int32, torch.float64
+    _check("tb_krylov_density_grouped", lib().tb_krylov_density_grouped(
+        ctx, n, int(n_groups), _ptr(g_off, i32, "g_off"), _ptr(g_idx, i32, "g_idx"),
+        _ptr(c_off, i32, "c_off"), _ptr(c_idx, i32, "c_idx"),
+        _ptr(h_off, i32, "h_off"), _ptr(h_idx, i32, "h_idx"), _ptr(Hblk, f64, "Hblk"),
+        _ptr(Hmirror, torch.float32, "Hmirror"), _ptr(lam, f64, "lambda"),
+        _ptr(S, f64, "S"), _ptr(P, f64, "P"), _ptr(kdim, i32, "kdim"), _stream(stream)))
+
+
 def tb_find_mu(ctx, n, lam, S, kdim, n_electrons, mu_guess, mu, n_count=None, stream=None):
     i32, f64 = torch.int32, torch.float64
     _check("tb_find_mu", lib().tb_find_mu(
@@ -218,7 +241,7 @@ def tb_md_step(ctx, n, pos, vel, F, L, dt_fs, mass_amu, energies, stream=None):
         float(dt_fs), float(mass_amu), _ptr(energies, f64, "energies"), _stream(stream)))
 
 
-STAGES = ("lists", "assemble", "krylov", "eig", "mu", "forces")
+STAGES = ("lists", "assemble", "krylov", "eig", "mu", "forces", "grouping")
 
 
 def tb_profile_enable(ctx, enable=True):
@@ -226,7 +249,7 @@ def tb_profile_enable(ctx, enable=True):
 
 
 def tb_profile_read(ctx):
-    ms = (ctypes.c_float * 6)()
+    ms = (ctypes.c_float * 7)()
     _check("tb_profile_read", lib().tb_profile_read(ctx, ms))
     return dict(zip(STAGES, list(ms)))
 

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "libtb.so")
 SOURCES = ["tb_api.cu", "tb_neighbors.cu", "tb_hamiltonian.cu", "tb_krylov.cu",
-           "tb_eig.cu", "tb_density.cu", "tb_local.cu"]
+           "tb_eig.cu", "tb_density.cu", "tb_local.cu", "tb_krylov_group.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

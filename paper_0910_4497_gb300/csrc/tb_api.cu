@@ -22,6 +22,8 @@ tb_status check_params(const tb_params& p) {
   if (p.max_cluster < 1 || p.max_cluster > tbk::MAX_CLUSTER) return TB_ERR_INVALID_ARG;
   if (p.reorth_passes < 1 || p.reorth_passes > 2) return TB_ERR_INVALID_ARG;
   if (p.reorth_every < 1) return TB_ERR_INVALID_ARG;
+  if (p.group_m < 1 || p.group_m > 4) return TB_ERR_INVALID_ARG;
+  if (p.max_union < 0 || p.max_union > tbk::MAX_CLUSTER) return TB_ERR_INVALID_ARG;
   if (p.mu_max_iter < 1 || !(p.mu_tol > 0.0) || !(p.defl_tol >= 0.0)) return TB_ERR_INVALID_ARG;
   if (p.timeout_cycles <= 0) return TB_ERR_INVALID_ARG;
   if (!finite_pos(p.Es) || !finite_pos(p.Ep)) return TB_ERR_INVALID_ARG;
@@ -65,6 +67,11 @@ size_t carve(tb_ctx* c, int n, unsigned char* base) {
   c->lamf = k.take<float>((size_t)n * NT);
   c->Vg = k.take<unsigned char>(krylov_basis_bytes_global(c));
   c->lent = k.take<int2>((size_t)c->kry_grid * p.max_cluster * p.max_hnbr);
+  c->grp_V = k.take<unsigned char>(krylov_group_basis_bytes(c));
+  c->grp_lent = k.take<int2>((size_t)c->grp_grid * c->grp_max_union * p.max_hnbr);
+  c->grp_cnt = k.take<int>(n);
+  c->grp_off = k.take<int>(n + 1);
+  c->grp_idx = k.take<int>(n);
   c->mu_part = k.take<double>(2 * 16 * (size_t)(c->mu_grid > 0 ? c->mu_grid : 1));
   c->bar = k.take<unsigned>(4);
   c->mu_state = k.take<double>(4);
@@ -137,6 +144,8 @@ tb_status tb_params_default(tb_params* p) {
   p->max_cluster = 128;
   p->reorth_passes = 2;
   p->reorth_every = 1;
+  p->group_m = 1;
+  p->max_union = 0;
   p->mu_max_iter = 100;
   p->timeout_cycles = 4000000000LL;
   return TB_OK;
@@ -156,7 +165,8 @@ tb_status tb_ctx_create(tb_ctx** out, const tb_params* p) {
     return TB_ERR_CUDA;
   }
   if ((st = krylov_configure(c)) != TB_OK || (st = eig_configure(c)) != TB_OK ||
-      (st = mu_configure(c)) != TB_OK) {
+      (st = mu_configure(c)) != TB_OK ||
+      (p->group_m > 1 && (st = krylov_group_configure(c)) != TB_OK)) {
     delete c;
     return st;
   }
@@ -179,7 +189,7 @@ tb_status tb_ctx_destroy(tb_ctx* c) {
   if (c->ws) cudaFree(c->ws);
   if (c->loc_ws) cudaFree(c->loc_ws);
   if (c->d_status) cudaFree(c->d_status);
-  for (int q = 0; q < 12; ++q)
+  for (int q = 0; q < 14; ++q)
     if (c->prof_ev[q]) cudaEventDestroy(c->prof_ev[q]);
   delete c;
   return TB_OK;
@@ -272,6 +282,38 @@ tb_status tb_krylov_density(tb_ctx* c, int n, const int* c_off, const int* c_idx
   return TB_OK;
 }
 
+tb_status tb_group_atoms(tb_ctx* c, int n, const double* pos, double L, int* g_off, int* g_idx,
+                         void* stream) {
+  tb_status st = ready(c, n);
+  if (st != TB_OK) return st;
+  if (n == 0) return TB_OK;
+  if (!pos || !g_off || !g_idx || !(L > 0.0)) return TB_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TB_STAGE(c, 6, s, launch_group_atoms(c, n, pos, L, g_off, g_idx, s));
+  return TB_OK;
+}
+
+tb_status tb_krylov_density_grouped(tb_ctx* c, int n, int n_groups, const int* g_off,
+                                    const int* g_idx, const int* c_off, const int* c_idx,
+                                    const int* h_off, const int* h_idx, const double* Hblk,
+                                    const float* Hmirror, double* lambda, double* S, double* P,
+                                    int* kdim, void* stream) {
+  tb_status st = ready(c, n);
+  if (st != TB_OK) return st;
+  if (c->p.group_m < 2 || c->grp_grid <= 0) return TB_ERR_INVALID_ARG;
+  if (n == 0) return TB_OK;
+  if (n_groups < 1 || n_groups > n) return TB_ERR_INVALID_ARG;
+  if (!g_off || !g_idx || !c_off || !c_idx || !h_off || !h_idx || !lambda || !S || !P || !kdim)
+    return TB_ERR_INVALID_ARG;
+  if (c->p.prec == TB_PREC_FP64 && !Hblk) return TB_ERR_INVALID_ARG;
+  if (c->p.prec == TB_PREC_MIXED && !Hmirror) return TB_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TB_STAGE(c, 2, s, launch_krylov_grouped(c, n, n_groups, g_off, g_idx, c_off, c_idx, h_off,
+                                          h_idx, Hblk, Hmirror, s));
+  TB_STAGE(c, 3, s, launch_eig(c, n, h_off, lambda, S, P, kdim, s));
+  return TB_OK;
+}
+
 tb_status tb_find_mu(tb_ctx* c, int n, const double* lambda, const double* S, const int* kdim,
                      double n_electrons, const double* mu_guess, double* mu, double* n_count,
                      void* stream) {
@@ -308,11 +350,19 @@ tb_status tb_md_step(tb_ctx* c, int n, double* pos, double* vel, double* F, doub
     return TB_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((st = launch_md_kick_drift(c, n, pos, vel, F, L, dt_fs, mass_amu, s)) != TB_OK) return st;
+  const bool grouped = c->p.group_m > 1;
   TB_STAGE(c, 0, s, launch_neighbors(c, n, pos, L, c->h_off, c->h_idx, c->c_off, c->c_idx, s));
+  if (grouped) TB_STAGE(c, 6, s, launch_group_atoms(c, n, pos, L, c->grp_off, c->grp_idx, s));
   TB_STAGE(c, 1, s, launch_assemble(c, n, pos, L, c->h_off, c->h_idx, c->Hblk, c->dHblk,
                                     c->p.prec == TB_PREC_MIXED ? c->Hmir : nullptr, s));
-  TB_STAGE(c, 2, s, launch_krylov(c, n, c->c_off, c->c_idx, c->h_off, c->h_idx, c->Hblk,
-                                  c->Hmir, c->lambda, c->S, c->P, c->kdim, s));
+  if (grouped) {
+    const int G = (n + c->p.group_m - 1) / c->p.group_m;
+    TB_STAGE(c, 2, s, launch_krylov_grouped(c, n, G, c->grp_off, c->grp_idx, c->c_off,
+                                            c->c_idx, c->h_off, c->h_idx, c->Hblk, c->Hmir, s));
+  } else {
+    TB_STAGE(c, 2, s, launch_krylov(c, n, c->c_off, c->c_idx, c->h_off, c->h_idx, c->Hblk,
+                                    c->Hmir, c->lambda, c->S, c->P, c->kdim, s));
+  }
   TB_STAGE(c, 3, s, launch_eig(c, n, c->h_off, c->lambda, c->S, c->P, c->kdim, s));
   TB_STAGE(c, 4, s, launch_mu(c, n, c->lambda, c->S, 4.0 * n, c->mu, c->mu, c->ncount, s));
   TB_STAGE(c, 5, s, launch_forces(c, n, pos, L, c->h_off, c->h_idx, c->dHblk, c->lambda, c->S,
@@ -394,7 +444,7 @@ tb_status tb_local_gradient(tb_ctx* c, int n, const double* pos, double L, const
 tb_status tb_profile_enable(tb_ctx* c, int enable) {
   if (!c) return TB_ERR_INVALID_ARG;
   if (enable) {
-    for (int q = 0; q < 12; ++q)
+    for (int q = 0; q < 14; ++q)
       if (!c->prof_ev[q]) TB_CUDA_TRY(cudaEventCreate(&c->prof_ev[q]));
   }
   c->profiling = enable != 0;
@@ -403,7 +453,7 @@ tb_status tb_profile_enable(tb_ctx* c, int enable) {
 
 tb_status tb_profile_read(tb_ctx* c, float* ms) {
   if (!c || !ms) return TB_ERR_INVALID_ARG;
-  for (int q = 0; q < 6; ++q) {
+  for (int q = 0; q < 7; ++q) {
     ms[q] = -1.f;
     if (c->prof_ev[2 * q] && c->prof_ran[q]) {
       float t = -1.f;

@@ -160,6 +160,20 @@ struct tb_ctx {
   size_t fin_smem = 0;
   int mu_grid = 0;
   int mu_smem_max = 0;
+  // m-target form (f2): grouped block Lanczos, configured when group_m > 1
+  int grp_max_union = 0;             // capacity of a group's union cluster
+  int grp_grid = 0;
+  int grp_mc = 0;                    // targets per CTA (kernel capacity: 2 or 4)
+  int grp_threads = 0;
+  int grp_ubuf = 0;                  // concatenated member lists (power of two)
+  bool grp_vks = false;              // staged copy of V_k in shared memory
+  bool grp_lsmem = false;            // local CSR in shared memory
+  size_t grp_smem = 0;
+  void* grp_V = nullptr;             // grp_grid * grp_mc * r * 16 * max_union (TV)
+  int2* grp_lent = nullptr;          // grp_grid * max_union * max_hnbr
+  int* grp_cnt = nullptr;            // n: Morton ranks
+  int* grp_off = nullptr;            // n + 1: the context's own groups (tb_md_step)
+  int* grp_idx = nullptr;            // n
   // exact local gradient (a11): dense workspace, allocated by tb_ctx_reserve_local
   int loc_ND = 0;                    // 4 * max_cluster
   int loc_grid = 0;
@@ -172,8 +186,8 @@ struct tb_ctx {
   double* loc_Floc = nullptr;
   // stage timing events (tb_profile_enable)
   bool profiling = false;
-  bool prof_ran[6] = {false, false, false, false, false, false};
-  cudaEvent_t prof_ev[12] = {};
+  bool prof_ran[7] = {false, false, false, false, false, false, false};
+  cudaEvent_t prof_ev[14] = {};
 };
 
 // Stage timing helpers: record an event pair around a stage when enabled.
@@ -191,6 +205,15 @@ tb_status launch_krylov(tb_ctx* c, int n, const int* c_off, const int* c_idx,
                         const int* h_off, const int* h_idx, const double* Hblk,
                         const float* Hmir, double* lambda, double* S, double* P, int* kdim,
                         cudaStream_t s);
+int group_grid_cells(int n, int m);
+tb_status krylov_group_configure(tb_ctx* c);
+size_t krylov_group_basis_bytes(const tb_ctx* c);
+tb_status launch_group_atoms(tb_ctx* c, int n, const double* pos, double L, int* g_off,
+                             int* g_idx, cudaStream_t s);
+tb_status launch_krylov_grouped(tb_ctx* c, int n, int n_groups, const int* g_off,
+                                const int* g_idx, const int* c_off, const int* c_idx,
+                                const int* h_off, const int* h_idx, const double* Hblk,
+                                const float* Hmir, cudaStream_t s);
 tb_status eig_configure(tb_ctx* c);
 tb_status launch_eig(tb_ctx* c, int n, const int* h_off, double* lambda, double* S,
                      double* P, int* kdim, cudaStream_t s);

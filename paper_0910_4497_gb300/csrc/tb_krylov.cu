@@ -28,8 +28,11 @@
 // Layout of the basis: block b occupies Dmax*4 values, row-major [row][4].
 #include "tb_internal.cuh"
 #include "tb_eig_tail.cuh"
+#include "tb_krylov_common.cuh"
 
 namespace {
+
+using namespace tbkry;
 
 constexpr int KT_MAX = 256;        // threads per CTA (the fused eigensolve needs 256)
 constexpr int KW_MAX = KT_MAX / 32;
@@ -38,33 +41,6 @@ constexpr int KW_MAX = KT_MAX / 32;
 constexpr int FL_MASK = KW_MAX;
 constexpr int FL_ACT = KW_MAX + 2;
 constexpr int FL_OK = KW_MAX + 3;
-
-template <typename TV>
-struct alignas(4 * sizeof(TV)) vec4 {
-  TV v[4];
-};
-
-template <typename TV>
-__device__ __forceinline__ vec4<TV> ld4(const TV* p) {
-  return *reinterpret_cast<const vec4<TV>*>(p);
-}
-template <typename TV>
-__device__ __forceinline__ void st4(TV* p, const vec4<TV>& x) {
-  *reinterpret_cast<vec4<TV>*>(p) = x;
-}
-template <typename TV>
-__device__ __forceinline__ vec4<TV> ldg4(const TV* p) {
-  vec4<TV> r;
-  if constexpr (sizeof(TV) == 4) {
-    float4 t = __ldg(reinterpret_cast<const float4*>(p));
-    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
-  } else {
-    double2 t0 = __ldg(reinterpret_cast<const double2*>(p));
-    double2 t1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
-    r.v[0] = t0.x; r.v[1] = t0.y; r.v[2] = t1.x; r.v[3] = t1.y;
-  }
-  return r;
-}
 
 template <typename TV>
 struct KryArgs {
@@ -123,58 +99,6 @@ __host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, int max
   b += align32(sizeof(TV) * 16 * KW_MAX);             // reduction scratch
   b += align32(sizeof(int) * 16);                     // flags
   return b;
-}
-
-// Cholesky of a 4x4 Gram matrix g (row-major) into the upper-triangular R
-// (row-major); returns false when a pivot is not a healthy fraction of its
-// diagonal or falls near the deflation threshold.
-// `well` reports whether every pivot keeps at least a quarter of its diagonal
-// (then kappa(W)^2 <= ~16 and one Cholesky-QR pass is orthogonal to ~16 eps).
-template <typename TV>
-__device__ __forceinline__ bool chol4(const TV (&g)[16], TV (&R)[16], TV rel, double abs_tol,
-                                      bool& well) {
-#pragma unroll
-  for (int q = 0; q < 16; ++q) R[q] = (TV)0;
-  bool ok = true;
-  well = true;
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    TV d = g[c * 4 + c];
-#pragma unroll
-    for (int j = 0; j < c; ++j) d -= R[j * 4 + c] * R[j * 4 + c];
-    if (!(d > rel * g[c * 4 + c]) || !(d > (TV)(abs_tol * abs_tol))) ok = false;
-    if (!(d >= (TV)0.25 * g[c * 4 + c])) well = false;
-    const TV dd = d > (TV)0 ? d : (TV)1;
-    const TV inv = (TV)rsqrt(dd);
-    const TV rc = dd * inv;
-    R[c * 4 + c] = rc;
-#pragma unroll
-    for (int e = c + 1; e < 4; ++e) {
-      TV t = g[c * 4 + e];
-#pragma unroll
-      for (int j = 0; j < c; ++j) t -= R[j * 4 + c] * R[j * 4 + e];
-      R[c * 4 + e] = t * inv;
-    }
-  }
-  return ok;
-}
-
-// Inverse of an upper-triangular 4x4 R (row-major).
-template <typename TV>
-__device__ __forceinline__ void triinv4(const TV (&R)[16], TV (&X)[16]) {
-#pragma unroll
-  for (int q = 0; q < 16; ++q) X[q] = (TV)0;
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    X[c * 4 + c] = (TV)1 / R[c * 4 + c];
-#pragma unroll
-    for (int rr = c - 1; rr >= 0; --rr) {
-      TV t = (TV)0;
-#pragma unroll
-      for (int j = rr + 1; j <= c; ++j) t += R[rr * 4 + j] * X[j * 4 + c];
-      X[rr * 4 + c] = -t * X[rr * 4 + rr];   // X[rr][rr] = 1/R[rr][rr], set earlier
-    }
-  }
 }
 
 template <typename TV, bool VSMEM, bool FUSED, int KT>
@@ -598,13 +522,16 @@ __global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryAr
     {
       const size_t ybase = (size_t)(i + a.h_off[i]) * 4;
       const int nrows = (deg + 1) * 4;
+      // (a row with fewer entries than the H list was reported above; its
+      // missing neighbours get zero rows)
+      const int rcnt = rowptr[1] - rowptr[0];
       for (int q = tid; q < nrows * NT; q += KT) {
         const int rr = q / NT, col = q - rr * NT;
         const int qq = rr >> 2, beta = rr & 3;
-        const int slot = qq == 0 ? 0 : lent[rowptr[0] + qq - 1].x;
+        const int slot = qq == 0 ? 0 : (qq - 1 < rcnt ? lent[rowptr[0] + qq - 1].x : -1);
         const int b = col >> 2, c = col & 3;
         TV val = (TV)0;
-        if (b < nblocks) val = V[(size_t)b * Dmax * 4 + (4 * slot + beta) * 4 + c];
+        if (b < nblocks && slot >= 0) val = V[(size_t)b * Dmax * 4 + (4 * slot + beta) * 4 + c];
         a.Y[(ybase + rr) * NT + col] = val;
       }
     }
@@ -721,7 +648,8 @@ tb_status krylov_configure(tb_ctx* c) {
   // Alternatives, for comparison and tests: TB_KRYLOV_WIDE (256 threads, basis
   // in shared memory), TB_EIG_FUSED (256 threads, eigensolve inside the
   // Krylov kernel in the shared memory the basis used).
-  const bool fused = getenv("TB_EIG_FUSED") != nullptr;
+  // (the grouped form runs the separate eigensolver, so it keeps that one configured)
+  const bool fused = getenv("TB_EIG_FUSED") != nullptr && c->p.group_m == 1;
   const bool wide = getenv("TB_KRYLOV_WIDE") != nullptr;
   if (c->p.prec == TB_PREC_FP64) {
     if (fused && configure_t<double, true, true, 256>(c, max_smem) == TB_OK) return TB_OK;

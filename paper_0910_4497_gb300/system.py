@@ -50,6 +50,11 @@ class TBSystem:
         self.energies = torch.zeros(8, dtype=f64, **kw)
         self.W = torch.zeros(9, dtype=f64, **kw)
         self.pressure = torch.zeros(1, dtype=f64, **kw)
+        # m-target form: groups of group_m targets (tb_group_atoms)
+        self.group_m = self.tp.group_m
+        self.n_groups = (n + self.group_m - 1) // self.group_m
+        self.g_off = torch.zeros(self.n_groups + 1, dtype=i32, **kw)
+        self.g_idx = torch.zeros(n, dtype=i32, **kw)
         self.graph = None
 
     # -- the five stages of one force evaluation
@@ -62,9 +67,21 @@ class TBSystem:
                         self.Hblk, self.dHblk, self.Hmir, stream)
 
     def krylov(self, stream=None):
+        """Block Krylov runs and projected eigensolve of every target; with
+        group_m > 1 the m-target form on the groups in g_off / g_idx."""
+        if self.group_m > 1:
+            B.tb_krylov_density_grouped(self.ctx, self.n, self.n_groups, self.g_off, self.g_idx,
+                                        self.c_off, self.c_idx, self.h_off, self.h_idx,
+                                        self.Hblk, self.Hmir, self.lam, self.S, self.P,
+                                        self.kdim, stream)
+            return
         B.tb_krylov_density(self.ctx, self.n, self.c_off, self.c_idx, self.h_off,
                             self.h_idx, self.Hblk, self.Hmir, self.lam, self.S, self.P,
                             self.kdim, stream)
+
+    def group(self, stream=None):
+        """Spatial groups of group_m targets of the positions in self.pos."""
+        B.tb_group_atoms(self.ctx, self.n, self.pos, self.L, self.g_off, self.g_idx, stream)
 
     def find_mu(self, stream=None, warm_start=True):
         B.tb_find_mu(self.ctx, self.n, self.lam, self.S, self.kdim, 4.0 * self.n,
@@ -79,6 +96,8 @@ class TBSystem:
         """One full force evaluation (a1..a10) of the positions in self.pos;
         with_virial adds the virial W (3x3, eV) and static pressure (eV/A^3)."""
         self.neighbors(stream)
+        if self.group_m > 1:
+            self.group(stream)
         self.assemble(stream)
         self.krylov(stream)
         self.find_mu(stream, warm_start=warm_start)

@@ -74,4 +74,5 @@ def test_params_default_without_gpu(built):
     p = built.TBParams()
     assert built.lib().tb_params_default(ctypes.byref(p)) == 0
     assert p.kT == 0.1 and p.r == 8 and p.max_hnbr == 32
+    assert p.group_m == 1 and p.max_union == 0
     assert built.lib().tb_params_default(None) == 1

@@ -55,9 +55,11 @@ typedef enum tb_status {
 typedef enum tb_precision {
   /* Everything in FP64. */
   TB_PREC_FP64 = 0,
-  /* H.V sweeps, Krylov basis and its inner products in FP32; the block
-   * tridiagonal T, eigenvalues (FP64 Rayleigh quotients), mu, density-matrix
-   * blocks, energies and forces in FP64. */
+  /* H.V sweeps, Krylov basis and its inner products, and the projected
+   * eigensolve in FP32; the block tridiagonal T in FP64, eigenvalues as
+   * Rayleigh quotients on T in double-float arithmetic; mu (FP64 Newton, FP32
+   * terms for pairs far from mu), density-matrix blocks, energies and forces
+   * in FP64. */
   TB_PREC_MIXED = 1
 } tb_precision;
 

@@ -37,7 +37,7 @@
 namespace {
 
 constexpr int FT = 128;            // threads per CTA in the finishing kernel
-constexpr int XW_MAX = 6;          // targets (64-thread groups) per CTA in eig_warp_kernel
+constexpr int XW_MAX = 5;          // targets (64-thread groups) per CTA in eig_warp_kernel
 
 struct XArgs {
   int n, NT;
@@ -62,9 +62,17 @@ __host__ __device__ inline int xpitch(int NT) { return NT + 1; }
 // hi/lo pairs (12 columns per row), then staged rows of the Krylov basis
 __host__ __device__ inline int epitch(int NT) { return NT + 4; }   // E rows 16-byte aligned
 
+// register capacity of a row / column in the Householder and back-transform
+// phases (a multiple of 16)
+__host__ __device__ inline int ntc_of(int NT) { return NT <= 16 ? 16 : NT <= 32 ? 32 : NT <= 48 ? 48 : 64; }
+
+// H also holds the reflections between the Householder and back-transform
+// phases: ceil((NT - 2) / 8) blocks of 8 x ntc_of(NT)
 __host__ __device__ inline size_t xw_hsize(int NT) {
   const size_t a = (size_t)NT * epitch(NT), b = 24 * (size_t)NT;
-  return a > b ? a : b;
+  const size_t c = (size_t)((NT - 2 + 7) / 8) * 8 * ntc_of(NT);
+  const size_t ab = a > b ? a : b;
+  return ab > c ? ab : c;
 }
 
 constexpr int GT = 64;             // threads per target (two warps)
@@ -272,8 +280,10 @@ __device__ void restart_column(const Grp& g, const float* d, const float* e, int
   orth_column(g, Y, P, m, c0, c);
 }
 
-template <bool FULL>
-__global__ void __launch_bounds__(XW_MAX * GT, 2) eig_warp_kernel(const XArgs a) {
+// (64-wide rows: three targets per CTA by shared memory, so a looser register cap)
+template <bool FULL, int NTC>
+__global__ void __launch_bounds__(XW_MAX * GT, NTC == 64 ? 1 : 2) eig_warp_kernel(const XArgs a) {
+  static_assert(NTC % 16 == 0 && NTC <= GT, "row capacity");
   extern __shared__ __align__(16) unsigned char smem[];
   const int grp = threadIdx.x / GT;
   Grp g;
@@ -321,57 +331,103 @@ __global__ void __launch_bounds__(XW_MAX * GT, 2) eig_warp_kernel(const XArgs a)
   }
   gsync(g);
 
-  // ---- 1. Householder: step j maps column j below the diagonal to
-  // (alpha, 0, ...) with I - 2 v v^T and keeps v there; thread t owns row
-  // x = j + 1 + t.
+  // ---- 1. Householder with the rows in registers: thread t holds row t of
+  // the active matrix (pairs of columns, zero past m).  Step j: thread j
+  // publishes its row (symmetry: column j below the diagonal is row j right
+  // of it); the reflection I - 2 v v^T maps it to (alpha, 0, ...); p = A v,
+  // q = p - (v^T p) v, A <- A - 2 v q^T - 2 q v^T on the rows below j.  The
+  // vectors are read as 16-byte broadcasts; column blocks left of j+1 are
+  // skipped eight at a time.  Reflection j is kept for the back-transform in
+  // Vr, eight reflections interleaved per block: [j/8][x/2][j%8][x%2].
+  float* const rowj = fs;                        // NTC: the published row
+  float* const vs = fs + NTC;                    // NTC: v (zero outside j+1..m-1)
+  float* const qs = fs + 2 * NTC;                // NTC: q
+  float* const Vr = H;
+  float2 ar[NTC / 2];
+#pragma unroll
+  for (int k = 0; k < NTC / 2; ++k) {
+    const int c = 2 * k;
+    ar[k].x = (t < m && c < m) ? H[t * P + c] : 0.f;
+    ar[k].y = (t < m && c + 1 < m) ? H[t * P + c + 1] : 0.f;
+  }
+  gsync(g);                                      // H is overwritten by Vr below
   for (int j = 0; j + 2 < m; ++j) {
-    const int x = j + 1 + t;
-    const bool hx = x < m;
-    const float xj = H[(j + 1) * P + j];
-    const float hxj = hx ? H[x * P + j] : 0.f;
+    if (t == j) {
+#pragma unroll
+      for (int k = 0; k < NTC / 2; k += 2)
+        *reinterpret_cast<float4*>(rowj + 2 * k) = make_float4(ar[k].x, ar[k].y, ar[k + 1].x, ar[k + 1].y);
+    }
+    gsync(g);
+    const bool hx = t > j && t < m;
+    const float xj = rowj[j + 1];
+    const float hxj = hx ? rowj[t] : 0.f;
     const float sig = gsum(g, hxj * hxj);
+    float* const vrj = Vr + (j >> 3) * NTC * 8 + (j & 7) * 2;
     if (sig - xj * xj <= 1e-30f * (sig + 1e-30f) || sig == 0.f) {
-      if (t == 0) e[j] = xj;
-      if (hx) H[x * P + j] = 0.f;                     // identity
-      gsync(g);
+      if (t == 0) e[j] = xj;                      // identity: nothing to reduce
+      if (t < NTC) vrj[(t >> 1) * 16 + (t & 1)] = 0.f;
       continue;
     }
     const float alpha = xj >= 0.f ? -sqrtf(sig) : sqrtf(sig);
     const float inv = rsqrtf(2.f * (sig - xj * alpha));
-    if (hx) v[x] = (x == j + 1 ? (xj - alpha) : hxj) * inv;
-    gsync(g);
-    float p = 0.f;
-    if (hx) {
-      const float* row = H + x * P;
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      int l = j + 1;
-      for (; l + 3 < m; l += 4) {
-        a0 += row[l] * v[l];
-        a1 += row[l + 1] * v[l + 1];
-        a2 += row[l + 2] * v[l + 2];
-        a3 += row[l + 3] * v[l + 3];
-      }
-      for (; l < m; ++l) a0 += row[l] * v[l];
-      p = (a0 + a1) + (a2 + a3);
-      q[x] = p;
+    const float vx = hx ? (t == j + 1 ? (xj - alpha) : hxj) * inv : 0.f;
+    if (t < NTC) {
+      vs[t] = vx;
+      vrj[(t >> 1) * 16 + (t & 1)] = vx;
     }
-    const float K = gsum(g, hx ? p * v[x] : 0.f);
-    if (hx) q[x] -= K * v[x];
+    gsync(g);
+    float2 pa = make_float2(0.f, 0.f), pb = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < NTC / 2; k += 4) {
+      if (2 * k + 7 > j) {                       // uniform: the block holds a column > j
+        const float4 v0 = *reinterpret_cast<const float4*>(vs + 2 * k);
+        const float4 v1 = *reinterpret_cast<const float4*>(vs + 2 * k + 4);
+        pa = __ffma2_rn(ar[k], make_float2(v0.x, v0.y), pa);
+        pb = __ffma2_rn(ar[k + 1], make_float2(v0.z, v0.w), pb);
+        pa = __ffma2_rn(ar[k + 2], make_float2(v1.x, v1.y), pa);
+        pb = __ffma2_rn(ar[k + 3], make_float2(v1.z, v1.w), pb);
+      }
+    }
+    const float pr = hx ? (pa.x + pa.y) + (pb.x + pb.y) : 0.f;
+    const float K = gsum(g, pr * vx);
+    const float qx = hx ? pr - K * vx : 0.f;
+    if (t < NTC) qs[t] = qx;
     gsync(g);
     if (hx) {
-      const float vx = 2.f * v[x], qx = 2.f * q[x];
-      float* row = H + x * P;
-#pragma unroll 4
-      for (int c = j + 1; c < m; ++c) row[c] -= vx * q[c] + qx * v[c];
-      row[j] = v[x];                                  // keep v_j in column j
+      const float2 mv = make_float2(-2.f * vx, -2.f * vx), mq = make_float2(-2.f * qx, -2.f * qx);
+#pragma unroll
+      for (int k = 0; k < NTC / 2; k += 4) {
+        if (2 * k + 7 > j) {
+          const float4 v0 = *reinterpret_cast<const float4*>(vs + 2 * k);
+          const float4 v1 = *reinterpret_cast<const float4*>(vs + 2 * k + 4);
+          const float4 q0 = *reinterpret_cast<const float4*>(qs + 2 * k);
+          const float4 q1 = *reinterpret_cast<const float4*>(qs + 2 * k + 4);
+          ar[k] = __ffma2_rn(mv, make_float2(q0.x, q0.y), __ffma2_rn(mq, make_float2(v0.x, v0.y), ar[k]));
+          ar[k + 1] = __ffma2_rn(mv, make_float2(q0.z, q0.w), __ffma2_rn(mq, make_float2(v0.z, v0.w), ar[k + 1]));
+          ar[k + 2] = __ffma2_rn(mv, make_float2(q1.x, q1.y), __ffma2_rn(mq, make_float2(v1.x, v1.y), ar[k + 2]));
+          ar[k + 3] = __ffma2_rn(mv, make_float2(q1.z, q1.w), __ffma2_rn(mq, make_float2(v1.z, v1.w), ar[k + 3]));
+        }
+      }
     }
     if (t == 0) e[j] = alpha;
-    gsync(g);
   }
-  if (t < m) d[t] = H[t * P + t];
-  if (t == 0) {
-    if (m >= 2) e[m - 2] = H[(m - 1) * P + (m - 2)];
-    e[m - 1] = 0.f;
+  {
+    // diagonal and last off-diagonal entry from the rows
+    float dt = 0.f, et = 0.f;
+#pragma unroll
+    for (int k = 0; k < NTC / 2; ++k) {
+      if (2 * k == t) dt = ar[k].x;
+      if (2 * k + 1 == t) dt = ar[k].y;
+      if (2 * k == m - 2) et = ar[k].x;
+      if (2 * k + 1 == m - 2) et = ar[k].y;
+    }
+    if (t < m) d[t] = dt;
+    if (t == m - 1 && m >= 2) e[m - 2] = et;
+    if (t == 0) e[m - 1] = 0.f;
+    // reflection slots past the last one of the final block stay zero
+    const int nref = m - 2 > 0 ? m - 2 : 0;
+    for (int jj = nref; jj < ((nref + 7) & ~7); ++jj)
+      if (t < NTC) Vr[(jj >> 3) * NTC * 8 + (jj & 7) * 2 + (t >> 1) * 16 + (t & 1)] = 0.f;
   }
   gsync(g);
   float lmin = 1e30f, lmax = -1e30f, emax = 0.f;
@@ -464,27 +520,33 @@ __global__ void __launch_bounds__(XW_MAX * GT, 2) eig_warp_kernel(const XArgs a)
 
   // ---- 4. back-transformation U = H_0 ... H_{m-3} Y, eight reflections at a
   // time in compact WY form: H_jb ... H_jb+nb-1 = I - V Tb V^T with V the
-  // reflection vectors (stored in columns jb.. of H) and Tb upper triangular,
-  // Tb_ii = 2, Tb[0:i, i] = -2 Tb[0:i, 0:i] V[:, 0:i]^T v_i (LAPACK's dlarft,
-  // forward); each thread applies the blocks to its column, last block first.
+  // reflection vectors (block jb of Vr) and Tb upper triangular, Tb_ii = 2,
+  // Tb[0:i, i] = -2 Tb[0:i, 0:i] V[:, 0:i]^T v_i (LAPACK's dlarft, forward);
+  // thread t keeps column t of U in registers (pairs of rows) and applies the
+  // blocks to it, last block first.
   {
     const int nref = m - 2;
     float* Tb = slc;                             // 8 x 8, then the Gram entries
     float* Gv = slc + 64;
+    float2 u[NTC / 2];
+#pragma unroll
+    for (int k = 0; k < NTC / 2; ++k) {
+      u[k].x = (t < m && 2 * k < m) ? Y[(2 * k) * P + t] : 0.f;
+      u[k].y = (t < m && 2 * k + 1 < m) ? Y[(2 * k + 1) * P + t] : 0.f;
+    }
     for (int jb = nref > 0 ? ((nref - 1) / 8) * 8 : -1; jb >= 0; jb -= 8) {
       const int nb = min(8, nref - jb);
+      const float* Vb = Vr + (jb >> 3) * NTC * 8;    // [x/2][r][x%2]
       gsync(g);
       if (t < nb * nb) {                         // Gram entries v_a . v_b, a < b
         const int ra = t / nb, rb = t - ra * nb;
         if (ra < rb) {
-          float s0 = 0.f, s1 = 0.f;
-          int x = jb + rb + 1;
-          for (; x + 1 < m; x += 2) {
-            s0 += H[x * P + jb + ra] * H[x * P + jb + rb];
-            s1 += H[(x + 1) * P + jb + ra] * H[(x + 1) * P + jb + rb];
+          float s0 = 0.f;
+          for (int x = jb + rb + 1; x < m; ++x) {
+            const float* vx = Vb + (x >> 1) * 16 + (x & 1);
+            s0 += vx[2 * ra] * vx[2 * rb];
           }
-          if (x < m) s0 += H[x * P + jb + ra] * H[x * P + jb + rb];
-          Gv[ra * 8 + rb] = s0 + s1;
+          Gv[ra * 8 + rb] = s0;
         }
       }
       gsync(g);
@@ -500,48 +562,55 @@ __global__ void __launch_bounds__(XW_MAX * GT, 2) eig_warp_kernel(const XArgs a)
       }
       gsync(g);
       if (t < m) {
-        float* yk = Y + t;
-        float w[8];
+        // w = V^T u: pairs of rows at a time, one pair accumulator per reflection
+        float2 w2p[8];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) w[r] = 0.f;
-        // rows jb+1 .. jb+nb-1 meet only the first reflections of the block
-        for (int x = jb + 1; x < min(jb + nb, m); ++x) {
-          const float yx = yk[x * P];
+        for (int r = 0; r < 8; ++r) w2p[r] = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int r = 0; r < 8; ++r)
-            if (r < nb && x > jb + r) w[r] += H[x * P + jb + r] * yx;
+        for (int k = 0; k < NTC / 2; ++k) {
+          if (2 * k + 1 > jb && 2 * k < m) {     // uniform: rows jb+1 .. m-1
+            const float4* vk = reinterpret_cast<const float4*>(Vb + k * 16);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const float4 vv = vk[h];
+              w2p[2 * h] = __ffma2_rn(make_float2(vv.x, vv.y), u[k], w2p[2 * h]);
+              w2p[2 * h + 1] = __ffma2_rn(make_float2(vv.z, vv.w), u[k], w2p[2 * h + 1]);
+            }
+          }
         }
-        for (int x = jb + nb; x < m; ++x) {
-          const float yx = yk[x * P];
-          const float* hx = H + x * P + jb;
+        float w[8], wt[8];
 #pragma unroll
-          for (int r = 0; r < 8; ++r)
-            if (r < nb) w[r] += hx[r] * yx;
-        }
-        float w2[8];
+        for (int r = 0; r < 8; ++r) w[r] = r < nb ? w2p[r].x + w2p[r].y : 0.f;
 #pragma unroll
         for (int ii = 0; ii < 8; ++ii) {
           float acc = 0.f;
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk)
             if (ii < nb && kk >= ii && kk < nb) acc += Tb[ii * 8 + kk] * w[kk];
-          w2[ii] = acc;
+          wt[ii] = -acc;
         }
-        for (int x = jb + 1; x < min(jb + nb, m); ++x) {
-          float acc = 0.f;
+        // u -= V (Tb w)
 #pragma unroll
-          for (int r = 0; r < 8; ++r)
-            if (r < nb && x > jb + r) acc += H[x * P + jb + r] * w2[r];
-          yk[x * P] -= acc;
-        }
-        for (int x = jb + nb; x < m; ++x) {
-          const float* hx = H + x * P + jb;
-          float acc = 0.f;
+        for (int k = 0; k < NTC / 2; ++k) {
+          if (2 * k + 1 > jb && 2 * k < m) {
+            const float4* vk = reinterpret_cast<const float4*>(Vb + k * 16);
+            float2 uk = u[k];
 #pragma unroll
-          for (int r = 0; r < 8; ++r)
-            if (r < nb) acc += hx[r] * w2[r];
-          yk[x * P] -= acc;
+            for (int h = 0; h < 4; ++h) {
+              const float4 vv = vk[h];
+              uk = __ffma2_rn(make_float2(vv.x, vv.y), make_float2(wt[2 * h], wt[2 * h]), uk);
+              uk = __ffma2_rn(make_float2(vv.z, vv.w), make_float2(wt[2 * h + 1], wt[2 * h + 1]), uk);
+            }
+            u[k] = uk;
+          }
         }
+      }
+    }
+    if (t < m) {
+#pragma unroll
+      for (int k = 0; k < NTC / 2; ++k) {
+        if (2 * k < m) Y[(2 * k) * P + t] = u[k].x;
+        if (2 * k + 1 < m) Y[(2 * k + 1) * P + t] = u[k].y;
       }
     }
   }
@@ -943,6 +1012,25 @@ __global__ void __launch_bounds__(FT) eig_finish_kernel(const FinArgs<TV> a) {
   }
 }
 
+template <bool FULL>
+cudaError_t eig_set_smem(int NT, int bytes) {
+  const int ntc = ntc_of(NT);
+  auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (ntc == 16) return cudaFuncSetAttribute(eig_warp_kernel<FULL, 16>, attr, bytes);
+  if (ntc == 32) return cudaFuncSetAttribute(eig_warp_kernel<FULL, 32>, attr, bytes);
+  if (ntc == 48) return cudaFuncSetAttribute(eig_warp_kernel<FULL, 48>, attr, bytes);
+  return cudaFuncSetAttribute(eig_warp_kernel<FULL, 64>, attr, bytes);
+}
+
+template <bool FULL>
+void eig_launch(int NT, int grid, int threads, size_t smem, cudaStream_t s, const XArgs& xa) {
+  const int ntc = ntc_of(NT);
+  if (ntc == 16) eig_warp_kernel<FULL, 16><<<grid, threads, smem, s>>>(xa);
+  else if (ntc == 32) eig_warp_kernel<FULL, 32><<<grid, threads, smem, s>>>(xa);
+  else if (ntc == 48) eig_warp_kernel<FULL, 48><<<grid, threads, smem, s>>>(xa);
+  else eig_warp_kernel<FULL, 64><<<grid, threads, smem, s>>>(xa);
+}
+
 }  // namespace
 
 tb_status eig_configure(tb_ctx* c) {
@@ -958,14 +1046,12 @@ tb_status eig_configure(tb_ctx* c) {
   c->eig_warps = xw;
   c->eig_smem = xw * per;
   if (c->p.prec == TB_PREC_FP64) {
-    TB_CUDA_TRY(cudaFuncSetAttribute(eig_warp_kernel<false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->eig_smem));
+    TB_CUDA_TRY(eig_set_smem<false>(NT, (int)c->eig_smem));
     c->fin_smem = fin_smem_bytes<double>(NT);
     TB_CUDA_TRY(cudaFuncSetAttribute(eig_finish_kernel<double>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->fin_smem));
   } else {
-    TB_CUDA_TRY(cudaFuncSetAttribute(eig_warp_kernel<true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->eig_smem));
+    TB_CUDA_TRY(eig_set_smem<true>(NT, (int)c->eig_smem));
   }
   return TB_OK;
 }
@@ -980,14 +1066,14 @@ tb_status launch_eig(tb_ctx* c, int n, const int* h_off, double* lambda, double*
            c->lamf, lambda, S, P, kdim, c->d_status};
   if (c->p.prec == TB_PREC_FP64) {
     if (!c->kry_fused) {
-      eig_warp_kernel<false><<<(n + xw - 1) / xw, xw * GT, c->eig_smem, s>>>(xa);
+      eig_launch<false>(NT, (n + xw - 1) / xw, xw * GT, c->eig_smem, s, xa);
       TB_CUDA_TRY(cudaGetLastError());
     }
     FinArgs<double> fa{n, NT, c->T, c->colmask, c->Zf, c->lamf,
                        reinterpret_cast<const double*>(c->Y), h_off, lambda, S, P, c->d_status};
     eig_finish_kernel<double><<<n, FT, c->fin_smem, s>>>(fa);
   } else {
-    eig_warp_kernel<true><<<(n + xw - 1) / xw, xw * GT, c->eig_smem, s>>>(xa);
+    eig_launch<true>(NT, (n + xw - 1) / xw, xw * GT, c->eig_smem, s, xa);
   }
   TB_CUDA_TRY(cudaGetLastError());
   return TB_OK;

@@ -398,8 +398,7 @@ def run_ours(args):
         stages = {k: (statistics.mean([x for x in v if x >= 0]) if any(x >= 0 for x in v)
                       else None) for k, v in stage_ms.items()}
         # lists + 1 assembly + 1 Krylov + eigensolver (1 mixed, 2 FP64) + 1 mu + 4 forces/energies
-        launches_per_step = (list_launches(L, p["Rc"]) + 1 + 1 + (1 if args.prec == "mixed" else 2)
-                             + 1 + 4 + (2 if grouped else 0))     # grouping: count + scatter
+        launches_per_step = B.tb_ctx_kernels_per_evaluation(system.ctx, n, L)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -602,6 +601,8 @@ def run_md(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = t.item()
     e2e_value = world * n * args.steps / (e2e_ms / 1e3)
+    # kick-drift + one force evaluation + kick and its energy reduction
+    launches_per_step = tb.binding.tb_ctx_kernels_per_evaluation(system.ctx, n, L) + 3
     system.close()
 
     # ---- the FP64 path over the same steps from the same state
@@ -640,9 +641,7 @@ def run_md(args):
                     "d2h_bytes_per_step": 3 * n * 3 * 8 + 8 * 8},
             "cpu_baseline": cpu_base,
             "clocks": clk,
-            # kick-drift + lists + assembly + Krylov + eigensolver + mu + 4 forces + kick
-            "gpu_launches": (list_launches(L, p["Rc"]) + 3 + (1 if args.prec == "mixed" else 2)
-                             + 1 + 4 + 1) * args.steps,
+            "gpu_launches": launches_per_step * args.steps,
             "stage_ms": stage_ms,
             "nve": {"energy_drift_eV_per_atom": float((etot[-1] - etot[0]) / n),
                     "energy_span_eV_per_atom": float((etot.max() - etot.min()) / n),
@@ -1100,9 +1099,9 @@ def run_eos(args):
                          "kernel_ms": kry_ms},
             "cpu_baseline": cpu_base,
             "clocks": clk,
-            # lists + assembly + Krylov + eigensolver + mu + 4 forces + virial
-            "gpu_launches": (list_launches(systems[0][2], d["Rc_over_a"] * systems[0][0]) + 1 + 1
-                             + (1 if args.prec == "mixed" else 2) + 1 + 4 + 1) * args.steps,
+            # one force evaluation + the virial per step
+            "gpu_launches": (B.tb_ctx_kernels_per_evaluation(systems[0][3].ctx, n, systems[0][2])
+                             + 1) * args.steps,
             "paper_context": {"seconds_gpu_8800gtx_xu": 55.65, "seconds_cpu_elses_xu": 29.19,
                               "note": "time to compute the pressure of the 4x4x4 supercell; the "
                                       "number of evaluations inside is not stated"},

@@ -262,6 +262,15 @@ tb_status tb_krylov_density_grouped(tb_ctx* ctx, int n, int n_groups, const int*
                                     void* stream);
 
 /*
+ * Number of kernels of this library that one force evaluation of n atoms in a
+ * box of side L launches (tb_build_neighbors, [tb_group_atoms,]
+ * tb_krylov_density[_grouped], tb_find_mu, tb_forces with this context's
+ * configuration); memset nodes are not counted.  *count (host) out.  No GPU
+ * work.  TB_ERR_NOT_RESERVED if n exceeds the reserved size.
+ */
+tb_status tb_ctx_kernels_per_evaluation(const tb_ctx* ctx, int n, double L, int* count);
+
+/*
  * Stage timing (tracing aid).  When enabled, every later call records a pair of
  * CUDA events around each of its stages on its stream (as external event nodes
  * when the stream is being captured into a graph, so graph replays record them

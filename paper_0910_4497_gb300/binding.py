@@ -25,7 +25,8 @@ EXPORTS = ["tb_params_default", "tb_ctx_create", "tb_ctx_destroy", "tb_ctx_reser
            "tb_assemble_H", "tb_krylov_density", "tb_find_mu", "tb_forces", "tb_md_step",
            "tb_profile_enable", "tb_profile_read", "tb_find_mu_static",
            "tb_virial", "tb_ctx_reserve_local", "tb_local_forward", "tb_local_gradient",
-           "tb_group_atoms", "tb_krylov_density_grouped", "tb_version"]
+           "tb_group_atoms", "tb_krylov_density_grouped", "tb_ctx_kernels_per_evaluation",
+           "tb_version"]
 
 
 class TBParams(ctypes.Structure):
@@ -75,6 +76,7 @@ def load_library(path=LIB_PATH):
         "tb_local_forward": [P, I, VP, D, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP],
         "tb_local_gradient": [P, I, VP, D, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP],
         "tb_group_atoms": [P, I, VP, D, VP, VP, VP],
+        "tb_ctx_kernels_per_evaluation": [P, I, D, ctypes.POINTER(I)],
         "tb_krylov_density_grouped": [P, I, I, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP],
     }
     for name, args in sig.items():
@@ -196,6 +198,13 @@ def tb_krylov_density(ctx, n, c_off, c_idx, h_off, h_idx, Hblk, Hmirror, lam, S,
         _ptr(h_off, i32, "h_off"), _ptr(h_idx, i32, "h_idx"), _ptr(Hblk, f64, "Hblk"),
         _ptr(Hmirror, torch.float32, "Hmirror"), _ptr(lam, f64, "lambda"),
         _ptr(S, f64, "S"), _ptr(P, f64, "P"), _ptr(kdim, i32, "kdim"), _stream(stream)))
+
+
+def tb_ctx_kernels_per_evaluation(ctx, n, L):
+    k = ctypes.c_int()
+    _check("tb_ctx_kernels_per_evaluation",
+           lib().tb_ctx_kernels_per_evaluation(ctx, int(n), float(L), ctypes.byref(k)))
+    return k.value
 
 
 def tb_group_atoms(ctx, n, pos, L, g_off, g_idx, stream=None):

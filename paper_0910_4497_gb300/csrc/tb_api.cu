@@ -67,6 +67,7 @@ size_t carve(tb_ctx* c, int n, unsigned char* base) {
   c->lamf = k.take<float>((size_t)n * NT);
   c->Vg = k.take<unsigned char>(krylov_basis_bytes_global(c));
   c->lent = k.take<int2>((size_t)c->kry_grid * p.max_cluster * p.max_hnbr);
+  c->ke_work = k.take<int>((size_t)n + 1);
   c->grp_V = k.take<unsigned char>(krylov_group_basis_bytes(c));
   c->grp_lent = k.take<int2>((size_t)c->grp_grid * c->grp_max_union * p.max_hnbr);
   c->grp_cnt = k.take<int>(n);
@@ -439,6 +440,23 @@ tb_status tb_local_gradient(tb_ctx* c, int n, const double* pos, double L, const
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return launch_local_gradient(c, n, pos, L, c_off, c_idx, h_off, h_idx, Hblk, dHblk, lambda, S,
                                Zstore, mu, F, s);
+}
+
+tb_status tb_ctx_kernels_per_evaluation(const tb_ctx* c, int n, double L, int* count) {
+  if (!c || !count || n < 0 || !(L > 0.0)) return TB_ERR_INVALID_ARG;
+  if (n > c->reserved_n || !c->ws) return TB_ERR_NOT_RESERVED;
+  const bool mixed = c->p.prec == TB_PREC_MIXED;
+  int k = neighbor_kernel_count(c, L) + 1;            // lists, assembly
+  int eig = mixed ? 1 : 2;                             // group eigensolver (+ FP64 refinement)
+  if (c->p.group_m > 1) {
+    k += 2 + 1;                                        // grouping; grouped block Lanczos
+  } else {
+    k += 1;                                            // block Lanczos
+    if (krylov_eig_persistent(c, n)) eig = 0;          // eigensolve inside the Krylov launch
+    else if (c->kry_fused) eig -= 1;
+  }
+  *count = k + eig + 1 + 4;                            // mu; rho, bond forces, sums, energies
+  return TB_OK;
 }
 
 tb_status tb_profile_enable(tb_ctx* c, int enable) {

@@ -1,0 +1,801 @@
+// The projected eigensolve of one target by a 64-thread group (two warps on
+// their own named barrier), shared by the eigensolver kernel and the
+// persistent Krylov + eigensolve kernel.  Steps (T' = the active part of the
+// block tridiagonal T, m x m, m <= NT <= 64):
+//     1. Householder reduction of T' to tridiagonal form, threads holding
+//        rows in registers;
+//     2. eigenvalues by Sturm-sequence bisection, threads owning eigenvalues;
+//     3. eigenvectors from the twisted factorisation of T' - lambda I
+//        (forward LDL^T and backward UDU^T pivots, twist index at the
+//        smallest |gamma_r|, then the two bidiagonal recurrences), twice, the
+//        second time at the tridiagonal Rayleigh quotient of the first vector;
+//        Gram-Schmidt inside clusters of eigenvalues closer than 1e-3 ||T||,
+//        and for a member that duplicates an earlier one (equal eigenvalues of
+//        a split tridiagonal) inverse iteration with a pivoted LU from a fresh
+//        start vector, the scheme of LAPACK's stein;
+//     4. back-transformation through the stored reflections (compact WY
+//        blocks of eight), threads holding columns in registers;
+//   then, in the mixed path: 5. a first-order Loewdin step; 6. Rayleigh
+//   quotients on the original block-tridiagonal T in double-float arithmetic;
+//   7. ascending order, lambda, S and P = Y U; in the FP64 path the FP32
+//   eigenpairs are written for the refinement kernel.
+#pragma once
+#include "tb_internal.cuh"
+
+namespace {
+
+struct XArgs {
+  int n, NT;
+  const double* T;
+  const unsigned long long* colmask;
+  const float* Y;                  // Krylov basis rows (mixed path)
+  const int* h_off;
+  float* Zf;                       // FP64 path: FP32 eigenvectors
+  float* lamf;
+  double* lambda;                  // mixed path: spectral record
+  double* S;
+  double* P;
+  int* kdim;
+  int* st;
+};
+
+// odd row pitch: lanes reading one column (rows x..x+31) or one row each
+// (same column index) hit 32 different banks
+__host__ __device__ inline int xpitch(int NT) { return NT + 1; }
+
+// H holds the matrix, then E of the Loewdin step, then the band of T as FP32
+// hi/lo pairs (12 columns per row), then staged rows of the Krylov basis
+__host__ __device__ inline int epitch(int NT) { return NT + 4; }   // E rows 16-byte aligned
+
+// register capacity of a row / column in the Householder and back-transform
+// phases (a multiple of 16)
+__host__ __device__ inline int ntc_of(int NT) { return NT <= 16 ? 16 : NT <= 32 ? 32 : NT <= 48 ? 48 : 64; }
+
+// H also holds the reflections between the Householder and back-transform
+// phases: ceil((NT - 2) / 8) blocks of 8 x ntc_of(NT)
+__host__ __device__ inline size_t xw_hsize(int NT) {
+  const size_t a = (size_t)NT * epitch(NT), b = 24 * (size_t)NT;
+  const size_t c = (size_t)((NT - 2 + 7) / 8) * 8 * ntc_of(NT);
+  const size_t ab = a > b ? a : b;
+  return ab > c ? ab : c;
+}
+
+constexpr int GT = 64;             // threads per target (two warps)
+constexpr int NSLICE = 2 * GT;     // spectrum-slicing points
+
+__host__ __device__ inline size_t xw_smem_per_warp(int NT) {   // per target
+  size_t b = sizeof(double) * NT;                          // lamd
+  b += sizeof(float) * (xw_hsize(NT) + (size_t)NT * xpitch(NT) + 11 * (size_t)NT + NSLICE + 8);
+  b += sizeof(int) * 2 * NT;                               // act, rank
+  return (b + 15) & ~size_t(15);
+}
+
+// The two warps of a target synchronise on their own named barrier.
+struct Grp {
+  int t;        // thread in the target's group, 0..63
+  int wl;       // lane in its warp
+  int gw;       // warp in the group
+  int bid;      // named barrier id
+  float* red;   // 8 floats of scratch
+};
+
+__device__ __forceinline__ void gsync(const Grp& g) {
+  asm volatile("bar.sync %0, 64;" ::"r"(g.bid) : "memory");
+}
+
+__device__ __forceinline__ float gsum(const Grp& g, float v) {
+  v = tbk::warp_sum(v);
+  if (g.wl == 0) g.red[g.gw] = v;
+  gsync(g);
+  const float tot = g.red[0] + g.red[1];
+  gsync(g);
+  return tot;
+}
+
+// Sturm counts (number of eigenvalues below x) at two points at once: two
+// independent dependency chains for the same thread.
+__device__ __forceinline__ void sturm_count2(const float* d, const float* e2, int m, float xa,
+                                             float xb, float pivmin, int& ca, int& cb) {
+  float qa = d[0] - xa, qb = d[0] - xb;
+  if (fabsf(qa) < pivmin) qa = -pivmin;
+  if (fabsf(qb) < pivmin) qb = -pivmin;
+  int na = qa < 0.f, nb = qb < 0.f;
+  for (int i = 1; i < m; ++i) {
+    const float di = d[i], ei = e2[i - 1];
+    qa = di - xa - __fdividef(ei, qa);
+    qb = di - xb - __fdividef(ei, qb);
+    if (fabsf(qa) < pivmin) qa = -pivmin;
+    if (fabsf(qb) < pivmin) qb = -pivmin;
+    na += qa < 0.f;
+    nb += qb < 0.f;
+  }
+  ca = na;
+  cb = nb;
+}
+
+__device__ __forceinline__ float guard(float x, float tiny) {
+  return fabsf(x) < tiny ? (x < 0.f ? -tiny : tiny) : x;
+}
+
+// Eigenvector of the tridiagonal (d, e) for the estimate lk from the twisted
+// factorisation of T - lk I, written into column k of Y (pitch P): forward
+// pivots Dp_i, backward pivots Dm_i, gamma_i = Dp_i + Dm_i - (d_i - lk), twist
+// r = argmin |gamma|, z_r = 1, z_i = -(e_i / Dp_i) z_{i+1} (i < r),
+// z_{i+1} = -(e_i / Dm_{i+1}) z_i (i >= r); normalised.  Only the output
+// column is used as storage.
+__device__ __forceinline__ void twisted_vector(const float* d, const float* e, const float* e2,
+                                               int m, float lk, float tiny, float* Y, int P,
+                                               int k) {
+  float dp = guard(d[0] - lk, tiny);
+  Y[k] = dp;
+  for (int i = 1; i < m; ++i) {
+    dp = guard((d[i] - lk) - __fdividef(e2[i - 1], dp), tiny);
+    Y[i * P + k] = dp;
+  }
+  float dm = guard(d[m - 1] - lk, tiny);
+  float best = fabsf(Y[(m - 1) * P + k]);
+  int r = m - 1;
+  for (int i = m - 2; i >= 0; --i) {
+    const float di = d[i] - lk;
+    dm = guard(di - __fdividef(e2[i], dm), tiny);
+    const float g = fabsf(Y[i * P + k] + dm - di);
+    if (g < best) { best = g; r = i; }
+  }
+  // U multipliers e_i / Dm_{i+1} for i = m-2 .. r, kept in rows i+1
+  dm = guard(d[m - 1] - lk, tiny);
+  for (int i = m - 2; i >= r; --i) {
+    Y[(i + 1) * P + k] = __fdividef(e[i], dm);
+    dm = guard((d[i] - lk) - __fdividef(e2[i], dm), tiny);
+  }
+  float nn = 1.f, z = 1.f;
+  for (int i = r; i + 1 < m; ++i) {
+    z = -Y[(i + 1) * P + k] * z;
+    Y[(i + 1) * P + k] = z;
+    nn += z * z;
+  }
+  z = 1.f;
+  for (int i = r - 1; i >= 0; --i) {
+    z = -__fdividef(e[i], Y[i * P + k]) * z;
+    Y[i * P + k] = z;
+    nn += z * z;
+  }
+  Y[r * P + k] = 1.f;
+  const float sc = rsqrtf(nn);
+  for (int i = 0; i < m; ++i) Y[i * P + k] *= sc;
+}
+
+// double-float accumulation: (hi, lo) += a * b for floats a, b (exact product)
+__device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float b) {
+  const float p = a * b;
+  const float pe = fmaf(a, b, -p);
+  const float s = hi + p;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (p - bb);
+  hi = s;
+  lo += err + pe;
+}
+
+// start vector of an inverse-iteration restart (deterministic, all components nonzero)
+__device__ __forceinline__ float start_component(int x, int k) {
+  unsigned h = (unsigned)x * 2654435761u ^ ((unsigned)k * 40503u + 0x9e3779b9u);
+  h ^= h >> 13;
+  h *= 0x5bd1e995u;
+  h ^= h >> 15;
+  return ((h & 1u) ? -1.f : 1.f) * (0.5f + (float)((h >> 1) & 1023u) * (1.0f / 1023.0f));
+}
+
+// Orthogonalise column c of Y against columns [c0, c) and normalise (whole
+// group, one row per thread); returns the squared norm left after the
+// projections.
+__device__ __forceinline__ float orth_column(const Grp& g, float* Y, int P, int m, int c0, int c) {
+  const int x = g.t;
+  const bool hx = x < m;
+  for (int c2 = c0; c2 < c; ++c2) {
+    const float dt = gsum(g, hx ? Y[x * P + c] * Y[x * P + c2] : 0.f);
+    if (hx) Y[x * P + c] -= dt * Y[x * P + c2];
+  }
+  const float nn = gsum(g, hx ? Y[x * P + c] * Y[x * P + c] : 0.f);
+  const float sc = rsqrtf(fmaxf(nn, 1e-30f));
+  if (hx) Y[x * P + c] *= sc;
+  gsync(g);
+  return nn;
+}
+
+// Inverse iteration for column c at eigenvalue lk with the pivoted
+// tridiagonal LU of T - lk I (the dlagtf/dlagts scheme), restarted from a
+// fixed start vector and kept orthogonal to columns [c0, c): used when the
+// twisted vector of a degenerate eigenvalue duplicates an earlier one (a split
+// tridiagonal).  The factorisation and the solves run on thread 0.
+__device__ void restart_column(const Grp& g, const float* d, const float* e, int m, float lk,
+                               float tiny, float* Y, int P, int c0, int c, float* f) {
+  float* u0 = f;              // reciprocal pivots
+  float* u1 = f + m;          // first super-diagonal of U
+  float* u2 = f + 2 * m;      // second super-diagonal of U
+  float* ml = f + 3 * m;      // multipliers
+  float* pv = f + 4 * m;      // 1 where rows k, k+1 were interchanged
+  if (g.t == 0) {
+    float ak = d[0] - lk, bk = m > 1 ? e[0] : 0.f;
+    for (int k = 0; k + 1 < m; ++k) {
+      const float ck = e[k], ak1 = d[k + 1] - lk, bk1 = k + 2 < m ? e[k + 1] : 0.f;
+      if (fabsf(ak) >= fabsf(ck)) {
+        const float piv = guard(ak, tiny);
+        const float mult = ck / piv;
+        u0[k] = 1.f / piv; u1[k] = bk; u2[k] = 0.f; ml[k] = mult; pv[k] = 0.f;
+        ak = ak1 - mult * bk;
+        bk = bk1;
+      } else {
+        const float mult = ak / ck;
+        u0[k] = 1.f / ck; u1[k] = ak1; u2[k] = bk1; ml[k] = mult; pv[k] = 1.f;
+        ak = bk - mult * ak1;
+        bk = -mult * bk1;
+      }
+    }
+    u0[m - 1] = 1.f / guard(ak, tiny);
+  }
+  if (g.t < m) Y[g.t * P + c] = start_component(g.t, c);
+  gsync(g);
+  for (int it = 0; it < 3; ++it) {
+    orth_column(g, Y, P, m, c0, c);
+    if (g.t == 0) {
+      float yk = Y[c];
+      for (int k = 0; k + 1 < m; ++k) {
+        const float yk1 = Y[(k + 1) * P + c];
+        if (pv[k] == 0.f) { Y[k * P + c] = yk; yk = yk1 - ml[k] * yk; }
+        else { Y[k * P + c] = yk1; yk = yk - ml[k] * yk1; }
+      }
+      Y[(m - 1) * P + c] = yk;
+      float y1 = 0.f, y2 = 0.f;
+      for (int k = m - 1; k >= 0; --k) {
+        float y = Y[k * P + c];
+        if (k + 1 < m) y -= u1[k] * y1;
+        if (k + 2 < m) y -= u2[k] * y2;
+        y *= u0[k];
+        Y[k * P + c] = y;
+        y2 = y1;
+        y1 = y;
+      }
+    }
+    gsync(g);
+    // rescale before the next projection (sum of squares, not a maximum:
+    // one group reduction)
+    const float nn = gsum(g, g.t < m ? Y[g.t * P + c] * Y[g.t * P + c] : 0.f);
+    if (g.t < m) Y[g.t * P + c] *= rsqrtf(fmaxf(nn, 1e-30f));
+    gsync(g);
+  }
+  orth_column(g, Y, P, m, c0, c);
+}
+
+// The projected eigensolve of target i by one 64-thread group (g: its
+// thread, lane, warp and named barrier; base: its xw_smem_per_warp(NT) bytes
+// of shared memory).  T, Y and the column mask are read through L2 only
+// (ld.global.cg): in the persistent Krylov + eigensolve kernel they were
+// written by another SM during the same launch.
+template <bool FULL, int NTC>
+__device__ __forceinline__ void eig_group(const XArgs& a, int i, Grp g, unsigned char* base) {
+  static_assert(NTC % 16 == 0 && NTC <= GT, "row capacity");
+  const int t = g.t;
+  const int NT = a.NT, P = xpitch(NT);
+  double* lamd = reinterpret_cast<double*>(base);
+  float* H = reinterpret_cast<float*>(lamd + NT);
+  float* Y = H + xw_hsize(NT);
+  float* d = Y + NT * P;
+  float* e = d + NT;
+  float* e2 = e + NT;
+  float* lam = e2 + NT;
+  float* v = lam + NT;
+  float* q = v + NT;
+  float* fs = q + NT;                          // 5 NT: restart factorisation
+  float* slc = fs + 5 * NT;                    // NSLICE slicing counts
+  g.red = slc + NSLICE;                        // 8 floats
+  int* act = reinterpret_cast<int*>(g.red + 8);
+  int* rank = act + NT;
+
+  const unsigned long long mask = __ldcg(a.colmask + i);
+  const int m = __popcll(mask);
+  if (t < NT && ((mask >> t) & 1ull)) act[__popcll(mask & ((1ull << t) - 1ull))] = t;
+  gsync(g);
+  const double* Ti = a.T + (size_t)i * NT * NT;
+  if (t < m) {
+    const int ay = act[t];
+    int x = 0;
+    for (; x + 3 < m; x += 4) {               // four independent loads in flight
+      const double t0 = __ldcg(Ti + act[x] * NT + ay), t1 = __ldcg(Ti + act[x + 1] * NT + ay);
+      const double t2 = __ldcg(Ti + act[x + 2] * NT + ay), t3 = __ldcg(Ti + act[x + 3] * NT + ay);
+      H[x * P + t] = (float)t0;
+      H[(x + 1) * P + t] = (float)t1;
+      H[(x + 2) * P + t] = (float)t2;
+      H[(x + 3) * P + t] = (float)t3;
+    }
+    for (; x < m; ++x) H[x * P + t] = (float)__ldcg(Ti + act[x] * NT + ay);
+  }
+  gsync(g);
+
+  // ---- 1. Householder with the rows in registers: thread t holds row t of
+  // the active matrix (pairs of columns, zero past m).  Step j: thread j
+  // publishes its row (symmetry: column j below the diagonal is row j right
+  // of it); the reflection I - 2 v v^T maps it to (alpha, 0, ...); p = A v,
+  // q = p - (v^T p) v, A <- A - 2 v q^T - 2 q v^T on the rows below j.  The
+  // vectors are read as 16-byte broadcasts; column blocks left of j+1 are
+  // skipped eight at a time.  Reflection j is kept for the back-transform in
+  // Vr, eight reflections interleaved per block: [j/8][x/2][j%8][x%2].
+  float* const rowj = fs;                        // NTC: the published row
+  float* const vs = fs + NTC;                    // NTC: v (zero outside j+1..m-1)
+  float* const qs = fs + 2 * NTC;                // NTC: q
+  float* const Vr = H;
+  float2 ar[NTC / 2];
+#pragma unroll
+  for (int k = 0; k < NTC / 2; ++k) {
+    const int c = 2 * k;
+    ar[k].x = (t < m && c < m) ? H[t * P + c] : 0.f;
+    ar[k].y = (t < m && c + 1 < m) ? H[t * P + c + 1] : 0.f;
+  }
+  gsync(g);                                      // H is overwritten by Vr below
+  for (int j = 0; j + 2 < m; ++j) {
+    if (t == j) {
+#pragma unroll
+      for (int k = 0; k < NTC / 2; k += 2)
+        *reinterpret_cast<float4*>(rowj + 2 * k) = make_float4(ar[k].x, ar[k].y, ar[k + 1].x, ar[k + 1].y);
+    }
+    gsync(g);
+    const bool hx = t > j && t < m;
+    const float xj = rowj[j + 1];
+    const float hxj = hx ? rowj[t] : 0.f;
+    const float sig = gsum(g, hxj * hxj);
+    float* const vrj = Vr + (j >> 3) * NTC * 8 + (j & 7) * 2;
+    if (sig - xj * xj <= 1e-30f * (sig + 1e-30f) || sig == 0.f) {
+      if (t == 0) e[j] = xj;                      // identity: nothing to reduce
+      if (t < NTC) vrj[(t >> 1) * 16 + (t & 1)] = 0.f;
+      continue;
+    }
+    const float alpha = xj >= 0.f ? -sqrtf(sig) : sqrtf(sig);
+    const float inv = rsqrtf(2.f * (sig - xj * alpha));
+    const float vx = hx ? (t == j + 1 ? (xj - alpha) : hxj) * inv : 0.f;
+    if (t < NTC) {
+      vs[t] = vx;
+      vrj[(t >> 1) * 16 + (t & 1)] = vx;
+    }
+    gsync(g);
+    float2 pa = make_float2(0.f, 0.f), pb = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < NTC / 2; k += 4) {
+      if (2 * k + 7 > j) {                       // uniform: the block holds a column > j
+        const float4 v0 = *reinterpret_cast<const float4*>(vs + 2 * k);
+        const float4 v1 = *reinterpret_cast<const float4*>(vs + 2 * k + 4);
+        pa = __ffma2_rn(ar[k], make_float2(v0.x, v0.y), pa);
+        pb = __ffma2_rn(ar[k + 1], make_float2(v0.z, v0.w), pb);
+        pa = __ffma2_rn(ar[k + 2], make_float2(v1.x, v1.y), pa);
+        pb = __ffma2_rn(ar[k + 3], make_float2(v1.z, v1.w), pb);
+      }
+    }
+    const float pr = hx ? (pa.x + pa.y) + (pb.x + pb.y) : 0.f;
+    const float K = gsum(g, pr * vx);
+    const float qx = hx ? pr - K * vx : 0.f;
+    if (t < NTC) qs[t] = qx;
+    gsync(g);
+    if (hx) {
+      const float2 mv = make_float2(-2.f * vx, -2.f * vx), mq = make_float2(-2.f * qx, -2.f * qx);
+#pragma unroll
+      for (int k = 0; k < NTC / 2; k += 4) {
+        if (2 * k + 7 > j) {
+          const float4 v0 = *reinterpret_cast<const float4*>(vs + 2 * k);
+          const float4 v1 = *reinterpret_cast<const float4*>(vs + 2 * k + 4);
+          const float4 q0 = *reinterpret_cast<const float4*>(qs + 2 * k);
+          const float4 q1 = *reinterpret_cast<const float4*>(qs + 2 * k + 4);
+          ar[k] = __ffma2_rn(mv, make_float2(q0.x, q0.y), __ffma2_rn(mq, make_float2(v0.x, v0.y), ar[k]));
+          ar[k + 1] = __ffma2_rn(mv, make_float2(q0.z, q0.w), __ffma2_rn(mq, make_float2(v0.z, v0.w), ar[k + 1]));
+          ar[k + 2] = __ffma2_rn(mv, make_float2(q1.x, q1.y), __ffma2_rn(mq, make_float2(v1.x, v1.y), ar[k + 2]));
+          ar[k + 3] = __ffma2_rn(mv, make_float2(q1.z, q1.w), __ffma2_rn(mq, make_float2(v1.z, v1.w), ar[k + 3]));
+        }
+      }
+    }
+    if (t == 0) e[j] = alpha;
+  }
+  {
+    // diagonal and last off-diagonal entry from the rows
+    float dt = 0.f, et = 0.f;
+#pragma unroll
+    for (int k = 0; k < NTC / 2; ++k) {
+      if (2 * k == t) dt = ar[k].x;
+      if (2 * k + 1 == t) dt = ar[k].y;
+      if (2 * k == m - 2) et = ar[k].x;
+      if (2 * k + 1 == m - 2) et = ar[k].y;
+    }
+    if (t < m) d[t] = dt;
+    if (t == m - 1 && m >= 2) e[m - 2] = et;
+    if (t == 0) e[m - 1] = 0.f;
+    // reflection slots past the last one of the final block stay zero
+    const int nref = m - 2 > 0 ? m - 2 : 0;
+    for (int jj = nref; jj < ((nref + 7) & ~7); ++jj)
+      if (t < NTC) Vr[(jj >> 3) * NTC * 8 + (jj & 7) * 2 + (t >> 1) * 16 + (t & 1)] = 0.f;
+  }
+  gsync(g);
+  float lmin = 1e30f, lmax = -1e30f, emax = 0.f;
+  if (t < m) {
+    e2[t] = e[t] * e[t];
+    const float rad = fabsf(e[t]) + (t > 0 ? fabsf(e[t - 1]) : 0.f);
+    lmin = d[t] - rad;
+    lmax = d[t] + rad;
+    emax = e[t] * e[t];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lmin = fminf(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+    lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  }
+  if (g.wl == 0) { g.red[3 * g.gw] = lmin; g.red[3 * g.gw + 1] = lmax; g.red[3 * g.gw + 2] = emax; }
+  gsync(g);
+  lmin = fminf(g.red[0], g.red[3]);
+  lmax = fmaxf(g.red[1], g.red[4]);
+  emax = fmaxf(g.red[2], g.red[5]);
+  gsync(g);
+  const float tnorm = fmaxf(fmaxf(fabsf(lmin), fabsf(lmax)), 1e-30f);
+  const float pivmin = fmaxf(1e-30f, 1.2e-7f * 1.2e-7f * emax);
+  const float tiny = 1.2e-7f * tnorm;
+  lmin -= 2.4e-7f * tnorm + pivmin;
+  lmax += 2.4e-7f * tnorm + pivmin;
+
+  // ---- 2. eigenvalues: counts at NSLICE points splitting [lmin, lmax]
+  // evenly (two per thread), then trisection from the slice holding each
+  // eigenvalue (thread t owns eigenvalue t), a fixed number of rounds shrinking
+  // the slice to 2.4e-7 ||T||
+  {
+    const float h = (lmax - lmin) / (float)(NSLICE + 1);
+    int s0 = 0, s1 = 0;
+    sturm_count2(d, e2, m, lmin + h * (float)(t + 1), lmin + h * (float)(t + 1 + GT), pivmin, s0,
+                 s1);
+    slc[t] = (float)s0;
+    slc[t + GT] = (float)s1;
+    gsync(g);
+    float lo = lmin, hi = lmax;
+    for (int u = 0; u < NSLICE; ++u) {            // point u + 1 has slc[u] eigenvalues below
+      const float xu = lmin + h * (float)(u + 1);
+      if ((int)slc[u] > t) hi = fminf(hi, xu); else lo = fmaxf(lo, xu);
+    }
+    const float tol = 2.4e-7f * tnorm + pivmin;
+    const int rounds = (h > tol) ? (int)ceilf(logf(h / tol) * 0.91023922f) : 0;   // log_3
+    if (t < m) {
+      for (int it = 0; it < rounds; ++it) {
+        const float w = (hi - lo) * (1.f / 3.f);
+        const float p1 = lo + w, p2 = hi - w;
+        int c1, c2;
+        sturm_count2(d, e2, m, p1, p2, pivmin, c1, c2);
+        if (c1 > t) hi = p1;
+        else if (c2 > t) { lo = p1; hi = p2; }
+        else lo = p2;
+      }
+      lam[t] = 0.5f * (lo + hi);
+    }
+  }
+  gsync(g);
+  // ---- 3. eigenvectors: twisted factorisations, twice (the second at the
+  // tridiagonal Rayleigh quotient of the first vector, kept inside the
+  // eigenvalue's own bracket so that a vector mixed with a close neighbour
+  // cannot move the shift onto that neighbour)
+  if (t < m) {
+    const float lk = lam[t];
+    twisted_vector(d, e, e2, m, lk, tiny, Y, P, t);
+    float n0 = 0.f, n1 = 0.f, zp = 0.f;
+    for (int x = 0; x < m; ++x) {
+      const float z = Y[x * P + t];
+      n0 += d[x] * z * z;
+      if (x > 0) n1 += e[x - 1] * zp * z;
+      zp = z;
+    }
+    const float hw = 1.2e-7f * tnorm + pivmin;
+    twisted_vector(d, e, e2, m, fminf(fmaxf(n0 + 2.f * n1, lk - hw), lk + hw), tiny, Y, P, t);
+  }
+  gsync(g);
+  // Gram-Schmidt inside clusters of close eigenvalues (index order); a member
+  // that loses most of its norm duplicated an earlier one and is recomputed
+  const float gtol = 1e-3f * tnorm;
+  for (int c = 1; c < m; ++c) {
+    if (!(lam[c] - lam[c - 1] < gtol)) continue;
+    int first = c - 1;
+    while (first > 0 && lam[first] - lam[first - 1] < gtol) --first;
+    const float nn = orth_column(g, Y, P, m, first, c);
+    if (nn < 0.25f) restart_column(g, d, e, m, lam[c], tiny, Y, P, first, c, fs);
+  }
+
+  // ---- 4. back-transformation U = H_0 ... H_{m-3} Y, eight reflections at a
+  // time in compact WY form: H_jb ... H_jb+nb-1 = I - V Tb V^T with V the
+  // reflection vectors (block jb of Vr) and Tb upper triangular, Tb_ii = 2,
+  // Tb[0:i, i] = -2 Tb[0:i, 0:i] V[:, 0:i]^T v_i (LAPACK's dlarft, forward);
+  // thread t keeps column t of U in registers (pairs of rows) and applies the
+  // blocks to it, last block first.
+  {
+    const int nref = m - 2;
+    float* Tb = slc;                             // 8 x 8, then the Gram entries
+    float* Gv = slc + 64;
+    float2 u[NTC / 2];
+#pragma unroll
+    for (int k = 0; k < NTC / 2; ++k) {
+      u[k].x = (t < m && 2 * k < m) ? Y[(2 * k) * P + t] : 0.f;
+      u[k].y = (t < m && 2 * k + 1 < m) ? Y[(2 * k + 1) * P + t] : 0.f;
+    }
+    for (int jb = nref > 0 ? ((nref - 1) / 8) * 8 : -1; jb >= 0; jb -= 8) {
+      const int nb = min(8, nref - jb);
+      const float* Vb = Vr + (jb >> 3) * NTC * 8;    // [x/2][r][x%2]
+      gsync(g);
+      if (t < nb * nb) {                         // Gram entries v_a . v_b, a < b
+        const int ra = t / nb, rb = t - ra * nb;
+        if (ra < rb) {
+          float s0 = 0.f;
+          for (int x = jb + rb + 1; x < m; ++x) {
+            const float* vx = Vb + (x >> 1) * 16 + (x & 1);
+            s0 += vx[2 * ra] * vx[2 * rb];
+          }
+          Gv[ra * 8 + rb] = s0;
+        }
+      }
+      gsync(g);
+      if (t == 0) {
+        for (int ii = 0; ii < nb; ++ii) {
+          Tb[ii * 8 + ii] = 2.f;
+          for (int kk = 0; kk < ii; ++kk) {
+            float acc = 0.f;
+            for (int l = kk; l < ii; ++l) acc += Tb[kk * 8 + l] * Gv[l * 8 + ii];
+            Tb[kk * 8 + ii] = -2.f * acc;
+          }
+        }
+      }
+      gsync(g);
+      if (t < m) {
+        // w = V^T u: pairs of rows at a time, one pair accumulator per reflection
+        float2 w2p[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) w2p[r] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < NTC / 2; ++k) {
+          if (2 * k + 1 > jb && 2 * k < m) {     // uniform: rows jb+1 .. m-1
+            const float4* vk = reinterpret_cast<const float4*>(Vb + k * 16);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const float4 vv = vk[h];
+              w2p[2 * h] = __ffma2_rn(make_float2(vv.x, vv.y), u[k], w2p[2 * h]);
+              w2p[2 * h + 1] = __ffma2_rn(make_float2(vv.z, vv.w), u[k], w2p[2 * h + 1]);
+            }
+          }
+        }
+        float w[8], wt[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) w[r] = r < nb ? w2p[r].x + w2p[r].y : 0.f;
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) {
+          float acc = 0.f;
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk)
+            if (ii < nb && kk >= ii && kk < nb) acc += Tb[ii * 8 + kk] * w[kk];
+          wt[ii] = -acc;
+        }
+        // u -= V (Tb w)
+#pragma unroll
+        for (int k = 0; k < NTC / 2; ++k) {
+          if (2 * k + 1 > jb && 2 * k < m) {
+            const float4* vk = reinterpret_cast<const float4*>(Vb + k * 16);
+            float2 uk = u[k];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const float4 vv = vk[h];
+              uk = __ffma2_rn(make_float2(vv.x, vv.y), make_float2(wt[2 * h], wt[2 * h]), uk);
+              uk = __ffma2_rn(make_float2(vv.z, vv.w), make_float2(wt[2 * h + 1], wt[2 * h + 1]), uk);
+            }
+            u[k] = uk;
+          }
+        }
+      }
+    }
+    if (t < m) {
+#pragma unroll
+      for (int k = 0; k < NTC / 2; ++k) {
+        if (2 * k < m) Y[(2 * k) * P + t] = u[k].x;
+        if (2 * k + 1 < m) Y[(2 * k + 1) * P + t] = u[k].y;
+      }
+    }
+  }
+  gsync(g);
+
+  // ---- 5. Loewdin U <- U (I - E/2), E = U^T U - I: E into H (aligned
+  // rows), then each thread updates its own row 16 columns at a time; a chunk
+  // written back before the next chunk is formed changes the result only at
+  // second order in E, below the first-order step's own error.
+  float* E = H;
+  const int PE = epitch(NT);
+  if (t < m) {
+    const int b = t;
+    int c = 0;
+    for (; c + 1 < m; c += 2) {
+      float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+      int x = 0;
+      for (; x + 1 < m; x += 2) {
+        const float yb0 = Y[x * P + b], yb1 = Y[(x + 1) * P + b];
+        t0 += Y[x * P + c] * yb0;
+        t1 += Y[x * P + c + 1] * yb0;
+        t2 += Y[(x + 1) * P + c] * yb1;
+        t3 += Y[(x + 1) * P + c + 1] * yb1;
+      }
+      if (x < m) {
+        const float yb = Y[x * P + b];
+        t0 += Y[x * P + c] * yb;
+        t1 += Y[x * P + c + 1] * yb;
+      }
+      E[c * PE + b] = 0.5f * ((t0 + t2) - (b == c ? 1.f : 0.f));
+      E[(c + 1) * PE + b] = 0.5f * ((t1 + t3) - (b == c + 1 ? 1.f : 0.f));
+    }
+    if (c < m) {
+      float t0 = 0.f;
+      for (int x = 0; x < m; ++x) t0 += Y[x * P + c] * Y[x * P + b];
+      E[c * PE + b] = 0.5f * (t0 - (b == c ? 1.f : 0.f));
+    }
+  }
+  gsync(g);
+  // (columns past m of a chunk read whatever follows in shared memory; their
+  // sums are discarded)
+  if (t < m) {
+    float* yx = Y + t * P;
+    for (int b0 = 0; b0 < m; b0 += 16) {
+      float acc[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+      for (int c = 0; c < m; ++c) {
+        const float yc = yx[c];
+        const float4* er = reinterpret_cast<const float4*>(E + c * PE + b0);
+#pragma unroll
+        for (int j4 = 0; j4 < 4; ++j4) {
+          const float4 ev = er[j4];
+          acc[4 * j4 + 0] += yc * ev.x;
+          acc[4 * j4 + 1] += yc * ev.y;
+          acc[4 * j4 + 2] += yc * ev.z;
+          acc[4 * j4 + 3] += yc * ev.w;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (b0 + j < m) yx[b0 + j] -= acc[j];
+    }
+  }
+  gsync(g);
+
+  if constexpr (!FULL) {
+    float* lf = a.lamf + (size_t)i * NT;
+    float* zo = a.Zf + (size_t)i * NT * NT;
+    if (t < m) lf[t] = lam[t];
+    for (int x = 0; x < m; ++x)
+      if (t < m) zo[x * NT + t] = Y[x * P + t];
+    if (t == 0) a.kdim[i] = m;
+    return;
+  } else {
+    // ---- 6. Rayleigh quotients on the original block-tridiagonal T: row x
+    // couples to the active columns of its own and the adjacent Krylov blocks
+    // (band [blo, bhi) in active indices); T staged as FP32 hi/lo pairs.
+    int* blo = reinterpret_cast<int*>(v);
+    int* bhi = reinterpret_cast<int*>(q);
+    float* Thi = H;                       // [x][12]
+    float* Tlo = H + NT * 12;
+    if (t < m) {
+      const int x = t, bx = act[x] >> 2;
+      int lo = x, hi = x + 1;
+      while (lo > 0 && (act[lo - 1] >> 2) >= bx - 1) --lo;
+      while (hi < m && (act[hi] >> 2) <= bx + 1) ++hi;
+      blo[x] = lo;
+      bhi[x] = hi;
+      for (int w = 0; w < hi - lo; ++w) {
+        const double tv = __ldcg(Ti + act[x] * NT + act[lo + w]);
+        const float th = (float)tv;
+        Thi[x * 12 + w] = th;
+        Tlo[x * 12 + w] = (float)(tv - (double)th);
+      }
+    }
+    gsync(g);
+    if (t < m) {
+      const int k = t;
+      float nh = 0.f, nl = 0.f, dh = 0.f, dl = 0.f;
+      for (int x = 0; x < m; ++x) {
+        const int l0 = blo[x], nw = bhi[x] - l0;
+        float th = 0.f, tl = 0.f;
+        for (int w = 0; w < nw; ++w) {
+          const float u = Y[(l0 + w) * P + k];
+          df_fma(th, tl, Thi[x * 12 + w], u);
+          tl += Tlo[x * 12 + w] * u;
+        }
+        const float ux = Y[x * P + k];
+        df_fma(nh, nl, ux, th);
+        nl += ux * tl;
+        df_fma(dh, dl, ux, ux);
+      }
+      const double lk = ((double)nh + (double)nl) / ((double)dh + (double)dl);
+      lamd[k] = lk;
+      if (!isfinite(lk)) tbk::set_status(a.st, TB_ERR_NONFINITE, i);
+    }
+    gsync(g);
+    // ---- 7. ascending order (ties by index), spectral record
+    if (t < m) {
+      int rk = 0;
+      const double lk = lamd[t];
+      for (int c = 0; c < m; ++c) rk += (lamd[c] < lk) || (lamd[c] == lk && c < t);
+      rank[t] = rk;
+    }
+    gsync(g);
+    double* lo = a.lambda + (size_t)i * NT;
+    double* So = a.S + (size_t)i * 4 * NT;
+    if (t < NT) {
+      if (t < m) lo[rank[t]] = lamd[t];
+      else lo[t] = 0.0;
+#pragma unroll
+      for (int al = 0; al < 4; ++al) {
+        if (t < m) So[al * NT + rank[t]] = (double)Y[al * P + t];
+        else So[al * NT + t] = 0.0;
+      }
+    }
+    // P = Y[rows, active] U: rows staged through H in chunks of RW rows
+    const int deg = a.h_off[i + 1] - a.h_off[i];
+    const size_t rbase = (size_t)(i + a.h_off[i]) * 4;
+    const int nrows = 4 * (deg + 1);
+    const int RW = (int)(xw_hsize(NT) / NT);
+    float* Yr = H;
+    for (int r0 = 0; r0 < nrows; r0 += RW) {
+      const int nr = min(RW, nrows - r0);
+      gsync(g);
+      if (t < m) {
+        const int ax = act[t];
+        int rr = 0;
+        for (; rr + 3 < nr; rr += 4) {        // four independent loads in flight
+          const float y0 = __ldcg(a.Y + (rbase + r0 + rr) * NT + ax);
+          const float y1 = __ldcg(a.Y + (rbase + r0 + rr + 1) * NT + ax);
+          const float y2 = __ldcg(a.Y + (rbase + r0 + rr + 2) * NT + ax);
+          const float y3 = __ldcg(a.Y + (rbase + r0 + rr + 3) * NT + ax);
+          Yr[rr * NT + t] = y0;
+          Yr[(rr + 1) * NT + t] = y1;
+          Yr[(rr + 2) * NT + t] = y2;
+          Yr[(rr + 3) * NT + t] = y3;
+        }
+        for (; rr < nr; ++rr) Yr[rr * NT + t] = __ldcg(a.Y + (rbase + r0 + rr) * NT + ax);
+      }
+      gsync(g);
+      if (t < NT) {
+        int rr = 0;
+        for (; rr + 1 < nr; rr += 2) {          // two rows at a time
+          double* p0 = a.P + (rbase + r0 + rr) * NT;
+          double* p1 = p0 + NT;
+          if (t < m) {
+            const float* y0 = Yr + rr * NT;
+            const float* y1 = y0 + NT;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            int x = 0;
+            for (; x + 1 < m; x += 2) {
+              const float u0 = Y[x * P + t], u1 = Y[(x + 1) * P + t];
+              s0 += y0[x] * u0;
+              s1 += y0[x + 1] * u1;
+              s2 += y1[x] * u0;
+              s3 += y1[x + 1] * u1;
+            }
+            if (x < m) {
+              const float u0 = Y[x * P + t];
+              s0 += y0[x] * u0;
+              s2 += y1[x] * u0;
+            }
+            p0[rank[t]] = (double)(s0 + s1);
+            p1[rank[t]] = (double)(s2 + s3);
+          } else {
+            p0[t] = 0.0;
+            p1[t] = 0.0;
+          }
+        }
+        if (rr < nr) {
+          double* p0 = a.P + (rbase + r0 + rr) * NT;
+          if (t < m) {
+            const float* y0 = Yr + rr * NT;
+            float s0 = 0.f;
+            for (int x = 0; x < m; ++x) s0 += y0[x] * Y[x * P + t];
+            p0[rank[t]] = (double)s0;
+          } else {
+            p0[t] = 0.0;
+          }
+        }
+      }
+    }
+    if (t == 0) a.kdim[i] = m;
+  }
+}
+
+}  // namespace

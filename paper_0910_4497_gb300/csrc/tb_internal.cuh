@@ -154,6 +154,10 @@ struct tb_ctx {
   bool kry_fused = false;           // projected eigensolve inside the Krylov kernel
   int kry_threads = 256;            // threads per Krylov CTA
   bool kry_lsmem = false;           // local CSR of the Krylov kernel in shared memory
+  bool ke_on = false;               // persistent Krylov + eigensolve kernel (mixed path)
+  int ke_grid = 0;
+  size_t ke_smem = 0;
+  int* ke_work = nullptr;            // n + 1: work counter, then per-target Krylov-done flags
   int eig_grid = 0;
   int eig_warps = 0;                 // targets per CTA of the warp eigensolver
   size_t eig_smem = 0;
@@ -195,12 +199,14 @@ tb_status prof_mark(tb_ctx* c, int stage, bool end, cudaStream_t s);
 
 // Launchers (defined in the kernel translation units).
 size_t neighbor_cell_capacity(int n);
+int neighbor_kernel_count(const tb_ctx* c, double L);
 tb_status launch_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h_off,
                            int* h_idx, int* c_off, int* c_idx, cudaStream_t s);
 tb_status launch_assemble(tb_ctx* c, int n, const double* pos, double L,
                           const int* h_off, const int* h_idx, double* Hblk,
                           double* dHblk, float* Hmir, cudaStream_t s);
 tb_status krylov_configure(tb_ctx* c);
+bool krylov_eig_persistent(const tb_ctx* c, int n);   // Krylov launch includes the eigensolve
 tb_status launch_krylov(tb_ctx* c, int n, const int* c_off, const int* c_idx,
                         const int* h_off, const int* h_idx, const double* Hblk,
                         const float* Hmir, double* lambda, double* S, double* P, int* kdim,

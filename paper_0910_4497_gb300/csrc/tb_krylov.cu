@@ -28,6 +28,7 @@
 // Layout of the basis: block b occupies Dmax*4 values, row-major [row][4].
 #include "tb_internal.cuh"
 #include "tb_eig_tail.cuh"
+#include "tb_eig_group.cuh"
 #include "tb_krylov_common.cuh"
 
 namespace {
@@ -101,8 +102,10 @@ __host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, int max
   return b;
 }
 
+// Block Lanczos of target i by the whole CTA (the basis slot and local CSR
+// of CTA blockIdx.x).
 template <typename TV, bool VSMEM, bool FUSED, int KT>
-__global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryArgs<TV> a) {
+__device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) {
   constexpr int KW = KT / 32;
   static_assert(KT == 128 || KT == 256, "128 or 256 threads");
   static_assert(!FUSED || KT == 256, "the fused eigensolve runs on 256 threads");
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryAr
   const TV chol_rel = sizeof(TV) == 4 ? (TV)1e-3 : (TV)1e-8;
   const double chol_abs = 1000.0 * a.defl_tol;
 
-  for (int i = blockIdx.x; i < a.n; i += gridDim.x) {
+  {
     const int c0 = a.c_off[i];
     const int nc = a.c_off[i + 1] - c0;
     double* Ti = a.T + (size_t)i * NT * NT;
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryAr
         a.colmask[i] = 0ull;
       }
       __syncthreads();
-      continue;
+      return;
     }
     for (int s = tid; s < nc; s += KT) cl[s] = a.c_idx[c0 + s];
     const int deg = a.h_off[i + 1] - a.h_off[i];
@@ -166,7 +169,7 @@ __global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryAr
         a.colmask[i] = 0ull;
       }
       __syncthreads();
-      continue;
+      return;
     }
     __syncthreads();
     // ---- local sparsity of H_c: counts, block-wide exclusive scan, fill
@@ -577,6 +580,135 @@ __global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryAr
   }
 }
 
+// One CTA per target atom, persistent (grid-stride over the targets).
+template <typename TV, bool VSMEM, bool FUSED, int KT>
+__global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryArgs<TV> a) {
+  for (int i = blockIdx.x; i < a.n; i += gridDim.x) krylov_target<TV, VSMEM, FUSED, KT>(a, i);
+}
+
+__device__ __forceinline__ int ld_acquire_s32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Persistent Krylov + eigensolve (mixed path, 128-thread CTAs): one work
+// queue of n block-Lanczos targets followed by ceil(n/2) eigensolve items of
+// two targets (one per 64-thread half of the CTA, the group eigensolver), so
+// that the eigensolves fill the SMs that the last Krylov targets leave idle
+// instead of waiting for the slowest CTA.  Items are taken in order from an
+// atomic counter; an eigensolve waits for its target's Krylov record, which a
+// running CTA is producing (items are handed out only to running CTAs, so the
+// wait always ends; it is bounded by `timeout` clocks and then reports
+// TB_ERR_TIMEOUT).  The record (T, Y rows, column mask) is published by a
+// fence in every thread, a barrier and a flag; the eigensolver reads it
+// through L2.  work[0] and done[0..n) are zero at launch.
+template <int NTC>
+__global__ void __launch_bounds__(128, 4) kry_eig_kernel(const KryArgs<float> a, const XArgs xa,
+                                                         int* work, int* done, long long timeout) {
+  __shared__ int s_item;
+  __shared__ int s_ok[2];
+  extern __shared__ __align__(32) unsigned char smem[];
+  const int n = a.n;
+  const int nitems = n + (n + 1) / 2;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(work, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= nitems) break;
+    if (it < n) {
+      krylov_target<float, false, false, 128>(a, it);
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) atomicExch(done + it, 1);
+    } else {
+      const int grp = threadIdx.x >> 6;
+      const int i = 2 * (it - n) + grp;
+      if (i < n) {
+        Grp g;
+        g.t = threadIdx.x & 63;
+        g.wl = threadIdx.x & 31;
+        g.gw = g.t >> 5;
+        g.bid = 1 + grp;
+        if (g.t == 0) {
+          const long long t0 = clock64();
+          int ok = 1;
+          while (ld_acquire_s32(done + i) == 0) {
+            if (clock64() - t0 > timeout) { ok = 0; break; }
+            __nanosleep(64);
+          }
+          s_ok[grp] = ok;
+        }
+        gsync(g);
+        if (s_ok[grp]) {
+          eig_group<true, NTC>(xa, i, g, smem + grp * xw_smem_per_warp(xa.NT));
+        } else if (g.t == 0) {
+          tbk::set_status(xa.st, TB_ERR_TIMEOUT, i);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int NTC>
+tb_status kry_eig_configure_t(tb_ctx* c, int max_smem) {
+  const size_t eig = 2 * xw_smem_per_warp(4 * c->p.r);
+  const size_t bytes = c->kry_smem > eig ? c->kry_smem : eig;
+  if ((int)bytes > max_smem) return TB_ERR_CAPACITY;
+  TB_CUDA_TRY(cudaFuncSetAttribute(kry_eig_kernel<NTC>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  int occ = 0;
+  TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kry_eig_kernel<NTC>, 128, bytes));
+  if (occ < 1) return TB_ERR_CAPACITY;
+  const int grid = c->num_sms * occ;
+  // only where the eigensolve's shared memory costs the Krylov part no
+  // occupancy (the basis slots and local CSR are per CTA, sized for kry_grid)
+  if (grid != c->kry_grid) return TB_ERR_CAPACITY;
+  c->ke_smem = bytes;
+  c->ke_grid = grid;
+  c->ke_on = true;
+  return TB_OK;
+}
+
+tb_status kry_eig_configure(tb_ctx* c, int max_smem) {
+  const int NT = 4 * c->p.r;
+  const int ntc = ntc_of(NT);
+  if (ntc == 16) return kry_eig_configure_t<16>(c, max_smem);
+  if (ntc == 32) return kry_eig_configure_t<32>(c, max_smem);
+  if (ntc == 48) return kry_eig_configure_t<48>(c, max_smem);
+  return kry_eig_configure_t<64>(c, max_smem);
+}
+
+tb_status kry_eig_launch(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int* h_off,
+                         const int* h_idx, const float* H, double* lambda, double* S, double* P,
+                         int* kdim, cudaStream_t s) {
+  const tb_params& p = c->p;
+  KryArgs<float> a;
+  a.n = n; a.r = p.r; a.max_cluster = p.max_cluster; a.max_hnbr = p.max_hnbr;
+  a.reorth_passes = p.reorth_passes;
+  a.reorth_every = p.reorth_every;
+  a.Es = p.Es; a.Ep = p.Ep; a.defl_tol = p.defl_tol;
+  a.c_off = c_off; a.c_idx = c_idx; a.h_off = h_off; a.h_idx = h_idx; a.H = H;
+  a.T = c->T; a.Y = reinterpret_cast<float*>(c->Y); a.colmask = c->colmask;
+  a.Vg = reinterpret_cast<float*>(c->Vg); a.lent = c->lent; a.st = c->d_status;
+  a.lent_smem = c->kry_lsmem ? 1 : 0;
+  a.lamf = c->lamf; a.Zf = c->Zf; a.lambda = lambda; a.S = S; a.P = P; a.kdim = kdim;
+  XArgs xa{n, 4 * p.r, c->T, c->colmask, reinterpret_cast<const float*>(c->Y), h_off, c->Zf,
+           c->lamf, lambda, S, P, kdim, c->d_status};
+  TB_CUDA_TRY(cudaMemsetAsync(c->ke_work, 0, sizeof(int) * ((size_t)n + 1), s));
+  const int grid = c->ke_grid;
+  int* work = c->ke_work;
+  int* done = c->ke_work + 1;
+  const int ntc = ntc_of(4 * p.r);
+  if (ntc == 16) kry_eig_kernel<16><<<grid, 128, c->ke_smem, s>>>(a, xa, work, done, p.timeout_cycles);
+  else if (ntc == 32) kry_eig_kernel<32><<<grid, 128, c->ke_smem, s>>>(a, xa, work, done, p.timeout_cycles);
+  else if (ntc == 48) kry_eig_kernel<48><<<grid, 128, c->ke_smem, s>>>(a, xa, work, done, p.timeout_cycles);
+  else kry_eig_kernel<64><<<grid, 128, c->ke_smem, s>>>(a, xa, work, done, p.timeout_cycles);
+  TB_CUDA_TRY(cudaGetLastError());
+  return TB_OK;
+}
+
 template <typename TV, bool VSMEM, bool FUSED, int KT>
 tb_status launch_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int* h_off,
                    const int* h_idx, const TV* H, double* lambda, double* S, double* P,
@@ -632,6 +764,12 @@ tb_status configure_t(tb_ctx* c, int max_smem) {
 
 }  // namespace
 
+bool krylov_eig_persistent(const tb_ctx* c, int n) {
+  // the queue pays off where the targets fill a few waves of CTAs and the last
+  // wave would leave SMs idle; many waves leave a negligible tail
+  return c->ke_on && c->p.prec == TB_PREC_MIXED && n <= 16 * c->ke_grid;
+}
+
 size_t krylov_basis_bytes_global(const tb_ctx* c) {
   if (c->kry_vsmem) return 0;
   const size_t tv = c->p.prec == TB_PREC_FP64 ? sizeof(double) : sizeof(float);
@@ -659,7 +797,15 @@ tb_status krylov_configure(tb_ctx* c) {
   }
   if (fused && configure_t<float, true, true, 256>(c, max_smem) == TB_OK) return TB_OK;
   if (wide && configure_t<float, true, false, 256>(c, max_smem) == TB_OK) return TB_OK;
-  if (configure_t<float, false, false, 128>(c, max_smem) == TB_OK) return TB_OK;
+  if (configure_t<float, false, false, 128>(c, max_smem) == TB_OK) {
+    // default of the mixed path: the persistent Krylov + eigensolve kernel
+    // (TB_NO_PERSIST: separate Krylov and eigensolver launches, for comparison)
+    c->ke_on = false;
+    if (c->p.group_m == 1 && getenv("TB_NO_PERSIST") == nullptr &&
+        kry_eig_configure(c, max_smem) != TB_OK)
+      c->ke_on = false;
+    return TB_OK;
+  }
   return configure_t<float, false, false, 256>(c, max_smem);
 }
 
@@ -683,6 +829,8 @@ tb_status launch_krylov(tb_ctx* c, int n, const int* c_off, const int* c_idx,
   } while (0)
   if (c->p.prec == TB_PREC_FP64) TB_KRY_DISPATCH(double, Hblk);
   if (!Hmir) return TB_ERR_INVALID_ARG;
+  if (krylov_eig_persistent(c, n))
+    return kry_eig_launch(c, n, c_off, c_idx, h_off, h_idx, Hmir, lambda, S, P, kdim, s);
   TB_KRY_DISPATCH(float, Hmir);
 #undef TB_KRY_DISPATCH
 }

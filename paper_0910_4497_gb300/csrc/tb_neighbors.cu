@@ -313,6 +313,14 @@ compact_kernel(int n, const int* __restrict__ pad_h, const int* __restrict__ pad
 
 size_t neighbor_cell_capacity(int n) { return (size_t)(n < 32 ? 64 : 2 * n); }
 
+// Kernels launch_neighbors issues for a box of side L (the same path choice).
+int neighbor_kernel_count(const tb_ctx* c, double L) {
+  const tb_params& p = c->p;
+  int nc = (int)(L / (p.Rc + 0.01));
+  while (nc >= 3 && (size_t)nc * nc * nc > neighbor_cell_capacity(c->reserved_n)) --nc;
+  return (nc >= 3 && p.max_cluster <= 512) ? 7 : 4;
+}
+
 tb_status launch_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h_off,
                            int* h_idx, int* c_off, int* c_idx, cudaStream_t s) {
   const tb_params& p = c->p;

@@ -219,13 +219,15 @@ def test_forces_bridged_uneven_clusters(tb):
     assert sizes.max() - sizes.min() >= 20
 
 
-@pytest.mark.parametrize("variant", ["TB_KRYLOV_WIDE", "TB_EIG_FUSED"])
+@pytest.mark.parametrize("variant", ["TB_KRYLOV_WIDE", "TB_EIG_FUSED", "TB_NO_PERSIST"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_kernel_variants_match(tb, prec, variant):
-    """Default: 128-thread Krylov CTAs with the basis in global memory and the
-    warp-per-target eigensolver.  The alternatives (256 threads with the basis
-    in shared memory; the eigensolve fused into the Krylov kernel) must give
-    the same answers within the path's tolerance, and match the oracle."""
+    """Default: 128-thread Krylov CTAs with the basis in global memory; in the
+    mixed path one persistent launch that queues the Krylov targets and then
+    the group eigensolves.  The alternatives (256 threads with the basis in
+    shared memory; the eigensolve fused into the Krylov CTA; separate Krylov
+    and eigensolver launches) must give the same answers within the path's
+    tolerance, and match the oracle."""
     pos, L, p = cfg_system(0)
     os.environ[variant] = "1"
     try:
@@ -317,3 +319,24 @@ def test_md_step_matches_oracle_verlet(tb):
     e = s.energies.cpu().numpy()
     assert abs(e[4] - epot) <= 1e-8 * abs(epot)
     assert abs(e[7] - md.kinetic_energy(v, 12.011)) <= 1e-9 * abs(e[7])
+
+
+def test_kernels_per_evaluation_count(tb):
+    """The library's own count of kernels per force evaluation on the 1920-atom
+    cell (cell lists: 7; assembly; Krylov with the eigensolve inside in the
+    mixed path, separate group eigensolver + refinement in FP64; mu; 4 for
+    density blocks, forces and energies)."""
+    pos, L, p = cfg_system(1)
+    counts = {}
+    for prec in ("mixed", "fp64"):
+        s = tb.TBSystem(len(pos), L, p, prec=prec)
+        counts[prec] = tb.binding.tb_ctx_kernels_per_evaluation(s.ctx, len(pos), L)
+        s.close()
+    assert counts == {"mixed": 14, "fp64": 16}
+    os.environ["TB_NO_PERSIST"] = "1"
+    try:
+        s = tb.TBSystem(len(pos), L, p, prec="mixed")
+        assert tb.binding.tb_ctx_kernels_per_evaluation(s.ctx, len(pos), L) == 15
+        s.close()
+    finally:
+        del os.environ["TB_NO_PERSIST"]

@@ -150,12 +150,21 @@ __device__ bool grid_allreduce(const double (&v)[M], const MuArgs& a, unsigned& 
   if (threadIdx.x < M) pg[blockIdx.x * MU_PART + threadIdx.x] = tot[threadIdx.x];
   ++gen;
   if (!grid_barrier(a.bar, gen * G, a.timeout, a.st, sflag)) return false;
-  // 16 threads per value stride over the blocks, then a fixed shuffle tree
+  // 16 threads per value stride over the blocks (loads issued eight at a
+  // time, not one L2 round trip per partial), then a fixed shuffle tree
   {
     const int m = threadIdx.x >> 4, sub = threadIdx.x & 15;
     double sum = 0.0;
-    if (m < M)
-      for (int g = sub; g < G; g += 16) sum += pg[g * MU_PART + m];
+    if (m < M) {
+      int g = sub;
+      for (; g + 7 * 16 < G; g += 8 * 16) {
+        double t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = pg[(g + u * 16) * MU_PART + m];
+        sum += ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
+      }
+      for (; g < G; g += 16) sum += pg[g * MU_PART + m];
+    }
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (m < M && sub == 0) tot[m] = sum;
@@ -168,6 +177,8 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
   extern __shared__ __align__(16) unsigned char mu_smem[];
   double2* pairs = reinterpret_cast<double2*>(mu_smem);   // (lambda, w)
   float2* pairsf = reinterpret_cast<float2*>(pairs + a.per_block);   // FP32 copies
+  int* nearl = reinterpret_cast<int*>(pairsf + a.per_block);         // pairs near mu (Newton)
+  __shared__ int wtot[MT / 32];
   __shared__ double red[MT / 32 * 16];
   __shared__ double tot[16];
   __shared__ int sflag;
@@ -226,11 +237,25 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
     }
     ++gen;
     if (!grid_barrier(a.bar, gen * G, a.timeout, a.st, &sflag)) return;
+    // every thread takes a share of the blocks' values, then a block minimum
+    double m0 = 1e300, m1 = 1e300;
+    for (int g = threadIdx.x; g < G; g += MT) {
+      m0 = fmin(m0, pg[g * MU_PART]);
+      m1 = fmin(m1, pg[g * MU_PART + 1]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      m0 = fmin(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+      m1 = fmin(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+    }
+    __syncthreads();                                  // red is reused below
+    if ((threadIdx.x & 31) == 0) { red[2 * (threadIdx.x >> 5)] = m0; red[2 * (threadIdx.x >> 5) + 1] = m1; }
+    __syncthreads();
     if (threadIdx.x == 0) {
-      double m0 = 1e300, m1 = 1e300;
-      for (int g = 0; g < G; ++g) { m0 = fmin(m0, pg[g * MU_PART]); m1 = fmin(m1, pg[g * MU_PART + 1]); }
-      tot[0] = m0;
-      tot[1] = -m1;
+      double a0 = 1e300, a1 = 1e300;
+      for (int w = 0; w < MT / 32; ++w) { a0 = fmin(a0, red[2 * w]); a1 = fmin(a1, red[2 * w + 1]); }
+      tot[0] = a0;
+      tot[1] = -a1;
     }
     __syncthreads();
   }
@@ -281,21 +306,72 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
   double Nmu = 0.0;
   bool conv = false;
   const float ikTf = (float)ikT;
+  // Pairs within 17.5 kT of the coarse bracket's midpoint go to a compact list
+  // (block scan: a fixed order).  While mu stays within 1.5 kT of it, every
+  // other pair has |x| > 15.5 and takes pair_occ's FP32 branch, and the FP64
+  // branch runs on the list with full warps (a warp-wide FP64 instruction
+  // costs the same with one active lane as with 32).
+  const double mid = 0.5 * (lo + hi);
+  const float midf = (float)mid, Rf = (float)(17.5 * a.kT);
+  int nnear = 0;
+  if (a.staged) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int cnt = 0;
+    for (int t = threadIdx.x; t < nloc; t += MT) {
+      const float2 v2 = pairsf[t];
+      cnt += (v2.y != 0.f && fabsf(v2.x - midf) <= Rf) ? 1 : 0;
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wtot[wid] = incl;
+    __syncthreads();
+    int pos = incl - cnt;
+    for (int w2 = 0; w2 < wid; ++w2) pos += wtot[w2];
+    for (int w2 = 0; w2 < MT / 32; ++w2) nnear += wtot[w2];
+    for (int t = threadIdx.x; t < nloc; t += MT) {
+      const float2 v2 = pairsf[t];
+      if (v2.y != 0.f && fabsf(v2.x - midf) <= Rf) nearl[pos++] = t;
+    }
+    __syncthreads();
+  }
   for (int it = 0; it < a.max_iter; ++it) {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     const bool ends = it == 0 && check;
     const float muf = (float)mu, lof = (float)lo, hif = (float)hi;
-    for (int t = threadIdx.x; t < nloc; t += MT) {
-      float lf, wf;
-      getf(t, lf, wf);
-      if (wf == 0.f) continue;
-      double l, w;
-      get(t, l, w);
-      pair_occ(l, w, lf, wf, mu, muf, ikT, ikTf, v[0], v[1]);
-      if (ends) {
-        double dd = 0.0;
-        pair_occ(l, w, lf, wf, lo, lof, ikT, ikTf, v[2], dd);
-        pair_occ(l, w, lf, wf, hi, hif, ikT, ikTf, v[3], dd);
+    if (a.staged && !ends && fabs(mu - mid) <= 1.5 * a.kT) {
+      for (int t = threadIdx.x; t < nloc; t += MT) {
+        float lf, wf;
+        getf(t, lf, wf);
+        if (wf == 0.f || fabsf(lf - midf) <= Rf) continue;
+        double l, w;
+        get(t, l, w);
+        pair_occ(l, w, lf, wf, mu, muf, ikT, ikTf, v[0], v[1]);
+      }
+      for (int x = threadIdx.x; x < nnear; x += MT) {
+        const int t = nearl[x];
+        float lf, wf;
+        getf(t, lf, wf);
+        double l, w;
+        get(t, l, w);
+        pair_occ(l, w, lf, wf, mu, muf, ikT, ikTf, v[0], v[1]);
+      }
+    } else {
+      for (int t = threadIdx.x; t < nloc; t += MT) {
+        float lf, wf;
+        getf(t, lf, wf);
+        if (wf == 0.f) continue;
+        double l, w;
+        get(t, l, w);
+        pair_occ(l, w, lf, wf, mu, muf, ikT, ikTf, v[0], v[1]);
+        if (ends) {
+          double dd = 0.0;
+          pair_occ(l, w, lf, wf, lo, lof, ikT, ikTf, v[2], dd);
+          pair_occ(l, w, lf, wf, hi, hif, ikT, ikTf, v[3], dd);
+        }
       }
     }
     if (!grid_allreduce<4>(v, a, gen, red, tot, &sflag)) return;
@@ -426,9 +502,14 @@ struct ForceArgs {
 // One thread per directed bond k -> j: the bond's Hellmann-Feynman term
 // 2 sum_ab [rho^(k)_{j b,k a} + rho^(j)_{k a,j b}] dH_ab plus the pair
 // repulsion, stored per bond; force_sum_kernel adds each atom's bonds in order.
-__global__ void __launch_bounds__(256) force_bond_kernel(const ForceArgs a) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= a.h_off[a.n]) return;
+// Runs of 32 consecutive bonds (one warp) are dealt out to the warps of all
+// blocks in turn, so that every SM gets a share of this FP64-bound work in
+// full warps.
+__global__ void __launch_bounds__(64) force_bond_kernel(const ForceArgs a) {
+  const int nb = a.h_off[a.n];
+  const int wg = blockIdx.x + gridDim.x * (threadIdx.x >> 5);
+  const int stride = gridDim.x * blockDim.x;
+  for (int p = wg * 32 + (threadIdx.x & 31); p < nb; p += stride) {
   int lo = 0, hi = a.n;                 // source atom k: h_off[k] <= p < h_off[k+1]
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -445,7 +526,7 @@ __global__ void __launch_bounds__(256) force_bond_kernel(const ForceArgs a) {
   if (l2 >= a.h_off[j + 1] || a.h_idx[l2] != k) {
     tbk::set_status(a.st, TB_ERR_INVALID_ARG, k);
     out[0] = out[1] = out[2] = out[3] = 0.0;
-    return;
+    continue;
   }
   const int q = p - a.h_off[k];
   const int rq = l2 - a.h_off[j];
@@ -476,6 +557,7 @@ __global__ void __launch_bounds__(256) force_bond_kernel(const ForceArgs a) {
   out[1] = 2.0 * acc[1] + sc * d[1];
   out[2] = 2.0 * acc[2] + sc * d[2];
   out[3] = 0.5 * phi;
+  }
 }
 
 __global__ void __launch_bounds__(256) force_sum_kernel(const ForceArgs a) {
@@ -642,7 +724,7 @@ tb_status launch_mu_nt(tb_ctx* c, int n, int NT, const double* lambda, const dou
   // one block per SM; each block stages its contiguous share of the pairs
   const int grid = c->mu_grid;
   a.per_block = (a.npairs + grid - 1) / grid;
-  const size_t stage = (size_t)a.per_block * (sizeof(double2) + sizeof(float2));
+  const size_t stage = (size_t)a.per_block * (sizeof(double2) + sizeof(float2) + sizeof(int));
   a.staged = stage <= (size_t)c->mu_smem_max ? 1 : 0;
   TB_CUDA_TRY(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), s));
   cudaLaunchConfig_t cfg = {};
@@ -670,7 +752,7 @@ tb_status launch_forces(tb_ctx* c, int n, const double* pos, double L, const int
   TB_CUDA_TRY(cudaGetLastError());
   ForceArgs fa{n, pos, L, h_off, h_idx, dHblk, c->rho, tb_repulsion_gsp(c->p), c->bondf, F,
                c->per_target, c->d_status};
-  force_bond_kernel<<<(int)(((long long)n * c->p.max_hnbr + 255) / 256), 256, 0, s>>>(fa);
+  force_bond_kernel<<<16 * c->num_sms, 64, 0, s>>>(fa);
   TB_CUDA_TRY(cudaGetLastError());
   force_sum_kernel<<<(n + 255) / 256, 256, 0, s>>>(fa);
   TB_CUDA_TRY(cudaGetLastError());
@@ -789,7 +871,7 @@ extern "C" tb_status tb_find_mu_static(int n, int r, const double* lambda, const
   a.st = status;
   const int grid = d.sms;
   a.per_block = (a.npairs + grid - 1) / grid;
-  const size_t stage = (size_t)a.per_block * (sizeof(double2) + sizeof(float2));
+  const size_t stage = (size_t)a.per_block * (sizeof(double2) + sizeof(float2) + sizeof(int));
   a.staged = stage <= (size_t)d.smem_max ? 1 : 0;
   TB_CUDA_TRY(cudaMemsetAsync(line, 0, sizeof(unsigned), s));       // barrier counter
   TB_CUDA_TRY(cudaMemsetAsync(status, 0, 2 * sizeof(int), s));      // caller's status words

@@ -6,7 +6,10 @@
 //   p_i(g) p_j(h) = l_g l_h (Vpps - Vppp) + delta_gh Vppp,
 // each times the distance scaling s(r).  The gradient block is
 //   dt/dd_k = s'(r) l_k M(l) + s(r) dM/dd_k,  dl_g/dd_k = (delta_gk - l_g l_k)/r.
-// One thread per bond; its source atom is found by binary search in h_off.
+// One thread per bond; runs of 32 consecutive bonds (one warp) are dealt out
+// to the warps of all blocks in turn, so that every SM gets a share of this
+// FP64-bound work in full warps whatever the bond count; the source atom is
+// found by binary search in h_off.
 #include "tb_internal.cuh"
 #include "tb_model.cuh"
 
@@ -21,8 +24,10 @@ assemble_kernel(int n, const double* __restrict__ pos, double L,
                 const int* __restrict__ h_off, const int* __restrict__ h_idx,
                 tb_gsp g, SK sk, double* __restrict__ Hblk, double* __restrict__ dHblk,
                 float* __restrict__ Hmir, int* st) {
-  const int pidx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pidx >= h_off[n]) return;
+  const int nb = h_off[n];
+  const int wg = blockIdx.x + gridDim.x * (threadIdx.x >> 5);     // warps interleaved over blocks
+  const int stride = gridDim.x * blockDim.x;
+  for (int pidx = wg * 32 + (threadIdx.x & 31); pidx < nb; pidx += stride) {
   int lo = 0, hi = n;                 // source atom: h_off[i] <= pidx < h_off[i+1]
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -40,7 +45,7 @@ assemble_kernel(int n, const double* __restrict__ pos, double L,
   const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
   if (!(r > 0.0)) {
     tbk::set_status(st, TB_ERR_NONFINITE, i);
-    return;
+    continue;
   }
   double s, ds;
   tb_gsp_eval(g, r, s, ds);
@@ -63,7 +68,7 @@ assemble_kernel(int n, const double* __restrict__ pos, double L,
     H[q] = s * M[q];
     if (Hmir) Hmir[(size_t)pidx * 16 + q] = (float)(s * M[q]);
   }
-  double* G = dHblk + (size_t)pidx * 48;
+  double* Gd = dHblk + (size_t)pidx * 48;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     double dl[3];
@@ -80,7 +85,8 @@ assemble_kernel(int n, const double* __restrict__ pos, double L,
         dM[4 * (1 + a) + 1 + b] = (dl[a] * l[b] + l[a] * dl[b]) * dpp;
     }
 #pragma unroll
-    for (int q = 0; q < 16; ++q) G[16 * k + q] = ds * l[k] * M[q] + s * dM[q];
+    for (int q = 0; q < 16; ++q) Gd[16 * k + q] = ds * l[k] * M[q] + s * dM[q];
+  }
   }
 }
 
@@ -91,8 +97,8 @@ tb_status launch_assemble(tb_ctx* c, int n, const double* pos, double L,
                           double* dHblk, float* Hmir, cudaStream_t s) {
   const tb_params& p = c->p;
   SK sk{p.Vss, p.Vsp, p.Vpps, p.Vppp};
-  const int threads = 256;
-  const int grid = (int)(((long long)n * p.max_hnbr + threads - 1) / threads);
+  const int threads = 64;
+  const int grid = 16 * c->num_sms;                 // up to 32 warps per SM
   assemble_kernel<<<grid, threads, 0, s>>>(n, pos, L, h_off, h_idx, tb_hopping_gsp(p),
                                            sk, Hblk, dHblk, Hmir, c->d_status);
   TB_CUDA_TRY(cudaGetLastError());

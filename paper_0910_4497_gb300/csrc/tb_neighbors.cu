@@ -211,6 +211,10 @@ __device__ __forceinline__ void warp_bitonic(int* v, int len, int lane) {
 // One warp per target: candidates from the 27 cells around the target's cell,
 // the same FP32 prefilter and FP64 membership test as nbr_kernel, then sorted
 // lists written into padded per-atom rows (counts capped at the capacities).
+// The candidates that pass the prefilter are staged in shared memory and the
+// FP64 test runs on the compacted list: a warp-wide FP64 instruction costs
+// the same with one active lane as with 32, and most 32-atom batches of the
+// cells hold only a few atoms near the target.
 __global__ void __launch_bounds__(NB_THREADS)
 nbr_cell_kernel(int n, const double* __restrict__ pos, const float4* __restrict__ posf,
                 double L, double R2h, double R2c, float Rh_pre2, float Rc_pre2, int nc,
@@ -220,8 +224,9 @@ nbr_cell_kernel(int n, const double* __restrict__ pos, const float4* __restrict_
                 int max_h, int max_c, int* st) {
   extern __shared__ int nb_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int* cand_c = nb_smem + warp * (capc + 64);
+  int* cand_c = nb_smem + warp * (2 * capc + 64);
   int* cand_h = cand_c + capc;
+  int* stg = cand_h + 64;                              // capc staged candidates
   const int i = blockIdx.x * NB_WARPS + warp;
   if (i >= n) return;
   const float Lf = (float)L, invLf = (float)(1.0 / L);
@@ -230,14 +235,43 @@ nbr_cell_kernel(int n, const double* __restrict__ pos, const float4* __restrict_
   const double hL = 0.5 * L;
   const int ci = atom_cell[i];
   const int cx = ci / (nc * nc), cy = (ci / nc) % nc, cz = ci % nc;
-  int nh = 0, ncand = 0;
+  int nh = 0, ncand = 0, nstg = 0;
+  const unsigned below = (1u << lane) - 1u;
+  // FP64 membership test of the staged candidates, 32 at a time
+  auto flush = [&]() {
+    __syncwarp();
+    for (int b = 0; b < nstg; b += 32) {
+      const int x = b + lane;
+      bool in_h = false, in_c = false;
+      int j = -1;
+      if (x < nstg) {
+        j = stg[x];
+        const double ex = min_image_rn(__dsub_rn(pos[3 * j], xi), L, hL);
+        const double ey = min_image_rn(__dsub_rn(pos[3 * j + 1], yi), L, hL);
+        const double ez = min_image_rn(__dsub_rn(pos[3 * j + 2], zi), L, hL);
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)),
+                                    __dmul_rn(ez, ez));
+        in_h = r2 <= R2h;
+        in_c = r2 <= R2c;
+      }
+      const unsigned bh = __ballot_sync(0xffffffffu, in_h);
+      const unsigned bc = __ballot_sync(0xffffffffu, in_c);
+      const int ph = nh + __popc(bh & below), pc = ncand + __popc(bc & below);
+      if (in_h && ph < 64) cand_h[ph] = j;
+      if (in_c && pc < capc) cand_c[pc] = j;
+      nh += __popc(bh);
+      ncand += __popc(bc);
+    }
+    __syncwarp();
+    nstg = 0;
+  };
   for (int q = 0; q < 27; ++q) {
     const int ox = q / 9 - 1, oy = (q / 3) % 3 - 1, oz = q % 3 - 1;
     const int c2 = (((cx + ox + nc) % nc) * nc + (cy + oy + nc) % nc) * nc + (cz + oz + nc) % nc;
     const int b0 = cell_off[c2], b1 = cell_off[c2 + 1];
     for (int b = b0; b < b1; b += 32) {
       const int bb = b + lane;
-      bool in_h = false, in_c = false;
+      bool pass = false;
       int j = -1;
       if (bb < b1) {
         j = cell_atoms[bb];
@@ -248,28 +282,16 @@ nbr_cell_kernel(int n, const double* __restrict__ pos, const float4* __restrict_
           dy -= Lf * rintf(dy * invLf);
           dz -= Lf * rintf(dz * invLf);
           const float r2f = dx * dx + dy * dy + dz * dz;
-          if (r2f <= Rc_pre2 || r2f <= Rh_pre2) {
-            const double ex = min_image_rn(__dsub_rn(pos[3 * j], xi), L, hL);
-            const double ey = min_image_rn(__dsub_rn(pos[3 * j + 1], yi), L, hL);
-            const double ez = min_image_rn(__dsub_rn(pos[3 * j + 2], zi), L, hL);
-            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)),
-                                        __dmul_rn(ez, ez));
-            in_h = r2 <= R2h;
-            in_c = r2 <= R2c;
-          }
+          pass = r2f <= Rc_pre2 || r2f <= Rh_pre2;
         }
       }
-      const unsigned bh = __ballot_sync(0xffffffffu, in_h);
-      const unsigned bc = __ballot_sync(0xffffffffu, in_c);
-      const unsigned below = (1u << lane) - 1u;
-      const int ph = nh + __popc(bh & below), pc = ncand + __popc(bc & below);
-      if (in_h && ph < 64) cand_h[ph] = j;
-      if (in_c && pc < capc) cand_c[pc] = j;
-      nh += __popc(bh);
-      ncand += __popc(bc);
+      const unsigned bp = __ballot_sync(0xffffffffu, pass);
+      if (nstg + __popc(bp) > capc) flush();           // keep the stage within capacity
+      if (pass) stg[nstg + __popc(bp & below)] = j;
+      nstg += __popc(bp);
     }
   }
-  __syncwarp();
+  flush();
   // pad to a power of two with INT_MAX, sort ascending
   const int kc = min(ncand, capc), kh = min(nh, 64);
   int lc = 1;
@@ -334,7 +356,7 @@ tb_status launch_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h
   int nc = (int)(L / (p.Rc + 0.01));
   while (nc >= 3 && (size_t)nc * nc * nc > neighbor_cell_capacity(c->reserved_n)) --nc;
   const int capc = p.max_cluster <= 128 ? 128 : (p.max_cluster <= 256 ? 256 : 512);
-  const size_t cell_smem = (size_t)NB_WARPS * (capc + 64) * sizeof(int);
+  const size_t cell_smem = (size_t)NB_WARPS * (2 * capc + 64) * sizeof(int);
   if (nc >= 3 && p.max_cluster <= 512) {
     const int ncell = nc * nc * nc;
     TB_CUDA_TRY(cudaMemsetAsync(c->cell_cnt, 0, sizeof(int) * ncell, s));

@@ -440,18 +440,76 @@ __global__ void __launch_bounds__(RT) rho_kernel(const RhoArgs a) {
   const double* lam = a.lambda + (size_t)i * NT;
   const double* Si = a.S + (size_t)i * 4 * NT;
   double v[3] = {0.0, 0.0, 0.0};
-  for (int k = threadIdx.x; k < NT; k += RT) {
-    double f = 0.0;
+  if constexpr (sizeof(TA) == 4) {
+    // Mixed path.  Pairs with |x| > 15.5 (FP32 estimate) take f or 1 - f (below
+    // 2e-7) and the entropy term s = -e (|x| + 1) + O(e^2) from the FP32
+    // exponential e = exp(-|x|); the others go, compacted in index order into
+    // the first lanes, through FP64 with one exponential and one log1p:
+    //   f = 1/(1+e) or e/(1+e),  s = f ln f + (1-f) ln(1-f)
+    //     = -min(f, 1-f) |x| - log1p(e)   (exact).
+    __shared__ int nidx[tbk::MAX_NT];
+    __shared__ int wball[RT / 32];
+    const float ikTf = (float)(1.0 / a.kT), muf = (float)mu;
+    const int k = threadIdx.x;
+    bool near_k = false;
+    double w = 0.0;
     if (k < m) {
-      f = fermi((lam[k] - mu) / a.kT);
-      const double w = Si[k] * Si[k] + Si[NT + k] * Si[NT + k] + Si[2 * NT + k] * Si[2 * NT + k] +
-                       Si[3 * NT + k] * Si[3 * NT + k];
-      v[0] += w * f * lam[k];
-      v[1] += w * entropy_term(f);
-      v[2] += w * f;
-    }
+      w = Si[k] * Si[k] + Si[NT + k] * Si[NT + k] + Si[2 * NT + k] * Si[2 * NT + k] +
+          Si[3 * NT + k] * Si[3 * NT + k];
+      const float xf = ((float)lam[k] - muf) * ikTf;
+      near_k = fabsf(xf) <= 15.5f;
+      if (!near_k) {
+        const float e = __expf(-fabsf(xf));
+        const float t = __fdividef(e, 1.f + e);        // the small one of f and 1 - f
+        const double f = xf > 0.f ? (double)t : 1.0 - (double)t;
+        v[0] += w * f * lam[k];
+        v[1] += w * (double)(-(t * fabsf(xf) + e));
+        v[2] += w * f;
 #pragma unroll
-    for (int al = 0; al < 4; ++al) fs[al * NT + k] = (TA)(f * Si[al * NT + k]);
+        for (int al = 0; al < 4; ++al) fs[al * NT + k] = (TA)(f * Si[al * NT + k]);
+      }
+    } else if (k < NT) {
+#pragma unroll
+      for (int al = 0; al < 4; ++al) fs[al * NT + k] = (TA)0;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, near_k);
+    if (lane == 0) wball[warp] = __popc(bal);
+    __syncthreads();
+    int pos = __popc(bal & ((1u << lane) - 1u)), nnear = 0;
+    for (int w2 = 0; w2 < RT / 32; ++w2) {
+      if (w2 < warp) pos += wball[w2];
+      nnear += wball[w2];
+    }
+    if (near_k) nidx[pos] = k;
+    __syncthreads();
+    if (threadIdx.x < nnear) {
+      const int kk = nidx[threadIdx.x];
+      const double wk = Si[kk] * Si[kk] + Si[NT + kk] * Si[NT + kk] +
+                        Si[2 * NT + kk] * Si[2 * NT + kk] + Si[3 * NT + kk] * Si[3 * NT + kk];
+      const double x = (lam[kk] - mu) / a.kT, ax = fabs(x);
+      const double e = exp(-ax);
+      const double t = e / (1.0 + e);                  // the small one of f and 1 - f
+      const double f = x > 0.0 ? t : 1.0 - t;
+      v[0] += wk * f * lam[kk];
+      v[1] += wk * (-(t * ax) - log1p(e));
+      v[2] += wk * f;
+#pragma unroll
+      for (int al = 0; al < 4; ++al) fs[al * NT + kk] = (TA)(f * Si[al * NT + kk]);
+    }
+  } else {
+    for (int k = threadIdx.x; k < NT; k += RT) {
+      double f = 0.0;
+      if (k < m) {
+        f = fermi((lam[k] - mu) / a.kT);
+        const double w = Si[k] * Si[k] + Si[NT + k] * Si[NT + k] + Si[2 * NT + k] * Si[2 * NT + k] +
+                         Si[3 * NT + k] * Si[3 * NT + k];
+        v[0] += w * f * lam[k];
+        v[1] += w * entropy_term(f);
+        v[2] += w * f;
+      }
+#pragma unroll
+      for (int al = 0; al < 4; ++al) fs[al * NT + k] = (TA)(f * Si[al * NT + k]);
+    }
   }
   tbk::block_sum<double, 3>(v, red, tot);          // also publishes fs
   if (threadIdx.x == 0) {

@@ -52,10 +52,10 @@ __host__ __device__ inline int epitch(int NT) { return NT + 4; }   // E rows 16-
 __host__ __device__ inline int ntc_of(int NT) { return NT <= 16 ? 16 : NT <= 32 ? 32 : NT <= 48 ? 48 : 64; }
 
 // H also holds the reflections between the Householder and back-transform
-// phases: ceil((NT - 2) / 8) blocks of 8 x ntc_of(NT)
+// phases: NT - 2 rows of ntc_of(NT)
 __host__ __device__ inline size_t xw_hsize(int NT) {
   const size_t a = (size_t)NT * epitch(NT), b = 24 * (size_t)NT;
-  const size_t c = (size_t)((NT - 2 + 7) / 8) * 8 * ntc_of(NT);
+  const size_t c = (size_t)(NT > 2 ? NT - 2 : 0) * ntc_of(NT);
   const size_t ab = a > b ? a : b;
   return ab > c ? ab : c;
 }
@@ -311,16 +311,20 @@ __device__ __forceinline__ void eig_group(const XArgs& a, int i, Grp g, unsigned
   gsync(g);
 
   // ---- 1. Householder with the rows in registers: thread t holds row t of
-  // the active matrix (pairs of columns, zero past m).  Step j: thread j
-  // publishes its row (symmetry: column j below the diagonal is row j right
-  // of it); the reflection I - 2 v v^T maps it to (alpha, 0, ...); p = A v,
-  // q = p - (v^T p) v, A <- A - 2 v q^T - 2 q v^T on the rows below j.  The
-  // vectors are read as 16-byte broadcasts; column blocks left of j+1 are
-  // skipped eight at a time.  Reflection j is kept for the back-transform in
-  // Vr, eight reflections interleaved per block: [j/8][x/2][j%8][x%2].
-  float* const rowj = fs;                        // NTC: the published row
-  float* const vs = fs + NTC;                    // NTC: v (zero outside j+1..m-1)
-  float* const qs = fs + 2 * NTC;                // NTC: q
+  // the active matrix (pairs of columns, zero past m).  Step j: the owner of
+  // row j has published it (symmetry: column j below the diagonal is row j
+  // right of it); the reflection I - 2 v v^T maps it to (alpha, 0, ...);
+  // p = A v, K = v^T p, and A <- A - 2 v p^T - 2 p v^T + 4 K v v^T on the rows
+  // below j (the same matrix as A - 2 v q^T - 2 q v^T with q = p - K v, with
+  // one group barrier less); the owner of row j+1 then publishes it.  Four
+  // group barriers per step: the pivot row and the partial sums are double
+  // buffered.  The vectors are read as 16-byte broadcasts; column blocks left
+  // of j+1 are skipped eight at a time.  Reflection j is kept for the
+  // back-transform in Vr[j][0..NTC).
+  float* const rowb = fs;                        // 2 x NTC: the published row
+  float* const vs = fs + 2 * NTC;                // NTC: v (zero outside j+1..m-1)
+  float* const ps = fs + 3 * NTC;                // NTC: p = A v (zero outside j+1..m-1)
+  float* const rb = fs + 4 * NTC;                // 2 x 4: warp partials, by step parity
   float* const Vr = H;
   float2 ar[NTC / 2];
 #pragma unroll
@@ -330,21 +334,31 @@ __device__ __forceinline__ void eig_group(const XArgs& a, int i, Grp g, unsigned
     ar[k].y = (t < m && c + 1 < m) ? H[t * P + c + 1] : 0.f;
   }
   gsync(g);                                      // H is overwritten by Vr below
-  for (int j = 0; j + 2 < m; ++j) {
-    if (t == j) {
+  auto publish = [&](float* dst) {
 #pragma unroll
-      for (int k = 0; k < NTC / 2; k += 2)
-        *reinterpret_cast<float4*>(rowj + 2 * k) = make_float4(ar[k].x, ar[k].y, ar[k + 1].x, ar[k + 1].y);
-    }
-    gsync(g);
+    for (int k = 0; k < NTC / 2; k += 2)
+      *reinterpret_cast<float4*>(dst + 2 * k) = make_float4(ar[k].x, ar[k].y, ar[k + 1].x, ar[k + 1].y);
+  };
+  if (t == 0 && m > 2) publish(rowb);
+  gsync(g);
+  for (int j = 0; j + 2 < m; ++j) {
+    const float* rowj = rowb + (j & 1) * NTC;
+    float* const rbj = rb + (j & 1) * 4;
     const bool hx = t > j && t < m;
     const float xj = rowj[j + 1];
     const float hxj = hx ? rowj[t] : 0.f;
-    const float sig = gsum(g, hxj * hxj);
-    float* const vrj = Vr + (j >> 3) * NTC * 8 + (j & 7) * 2;
+    {
+      const float sw = tbk::warp_sum(hxj * hxj);
+      if (g.wl == 0) rbj[g.gw] = sw;
+    }
+    gsync(g);
+    const float sig = rbj[0] + rbj[1];
+    float* const vrj = Vr + j * NTC;
     if (sig - xj * xj <= 1e-30f * (sig + 1e-30f) || sig == 0.f) {
       if (t == 0) e[j] = xj;                      // identity: nothing to reduce
-      if (t < NTC) vrj[(t >> 1) * 16 + (t & 1)] = 0.f;
+      if (t < NTC) vrj[t] = 0.f;
+      if (t == j + 1) publish(rowb + ((j + 1) & 1) * NTC);
+      gsync(g);
       continue;
     }
     const float alpha = xj >= 0.f ? -sqrtf(sig) : sqrtf(sig);
@@ -352,7 +366,7 @@ __device__ __forceinline__ void eig_group(const XArgs& a, int i, Grp g, unsigned
     const float vx = hx ? (t == j + 1 ? (xj - alpha) : hxj) * inv : 0.f;
     if (t < NTC) {
       vs[t] = vx;
-      vrj[(t >> 1) * 16 + (t & 1)] = vx;
+      vrj[t] = vx;
     }
     gsync(g);
     float2 pa = make_float2(0.f, 0.f), pb = make_float2(0.f, 0.f);
@@ -368,19 +382,24 @@ __device__ __forceinline__ void eig_group(const XArgs& a, int i, Grp g, unsigned
       }
     }
     const float pr = hx ? (pa.x + pa.y) + (pb.x + pb.y) : 0.f;
-    const float K = gsum(g, pr * vx);
-    const float qx = hx ? pr - K * vx : 0.f;
-    if (t < NTC) qs[t] = qx;
+    if (t < NTC) ps[t] = pr;
+    {
+      const float kw = tbk::warp_sum(pr * vx);
+      if (g.wl == 0) rbj[2 + g.gw] = kw;
+    }
     gsync(g);
     if (hx) {
-      const float2 mv = make_float2(-2.f * vx, -2.f * vx), mq = make_float2(-2.f * qx, -2.f * qx);
+      const float K = rbj[2] + rbj[3];
+      const float2 mv = make_float2(-2.f * vx, -2.f * vx);
+      const float cq = -(2.f * pr - 4.f * K * vx);
+      const float2 mq = make_float2(cq, cq);
 #pragma unroll
       for (int k = 0; k < NTC / 2; k += 4) {
         if (2 * k + 7 > j) {
           const float4 v0 = *reinterpret_cast<const float4*>(vs + 2 * k);
           const float4 v1 = *reinterpret_cast<const float4*>(vs + 2 * k + 4);
-          const float4 q0 = *reinterpret_cast<const float4*>(qs + 2 * k);
-          const float4 q1 = *reinterpret_cast<const float4*>(qs + 2 * k + 4);
+          const float4 q0 = *reinterpret_cast<const float4*>(ps + 2 * k);
+          const float4 q1 = *reinterpret_cast<const float4*>(ps + 2 * k + 4);
           ar[k] = __ffma2_rn(mv, make_float2(q0.x, q0.y), __ffma2_rn(mq, make_float2(v0.x, v0.y), ar[k]));
           ar[k + 1] = __ffma2_rn(mv, make_float2(q0.z, q0.w), __ffma2_rn(mq, make_float2(v0.z, v0.w), ar[k + 1]));
           ar[k + 2] = __ffma2_rn(mv, make_float2(q1.x, q1.y), __ffma2_rn(mq, make_float2(v1.x, v1.y), ar[k + 2]));
@@ -389,6 +408,8 @@ __device__ __forceinline__ void eig_group(const XArgs& a, int i, Grp g, unsigned
       }
     }
     if (t == 0) e[j] = alpha;
+    if (t == j + 1) publish(rowb + ((j + 1) & 1) * NTC);
+    gsync(g);
   }
   {
     // diagonal and last off-diagonal entry from the rows
@@ -403,10 +424,6 @@ __device__ __forceinline__ void eig_group(const XArgs& a, int i, Grp g, unsigned
     if (t < m) d[t] = dt;
     if (t == m - 1 && m >= 2) e[m - 2] = et;
     if (t == 0) e[m - 1] = 0.f;
-    // reflection slots past the last one of the final block stay zero
-    const int nref = m - 2 > 0 ? m - 2 : 0;
-    for (int jj = nref; jj < ((nref + 7) & ~7); ++jj)
-      if (t < NTC) Vr[(jj >> 3) * NTC * 8 + (jj & 7) * 2 + (t >> 1) * 16 + (t & 1)] = 0.f;
   }
   gsync(g);
   float lmin = 1e30f, lmax = -1e30f, emax = 0.f;
@@ -497,95 +514,48 @@ __device__ __forceinline__ void eig_group(const XArgs& a, int i, Grp g, unsigned
     if (nn < 0.25f) restart_column(g, d, e, m, lam[c], tiny, Y, P, first, c, fs);
   }
 
-  // ---- 4. back-transformation U = H_0 ... H_{m-3} Y, eight reflections at a
-  // time in compact WY form: H_jb ... H_jb+nb-1 = I - V Tb V^T with V the
-  // reflection vectors (block jb of Vr) and Tb upper triangular, Tb_ii = 2,
-  // Tb[0:i, i] = -2 Tb[0:i, 0:i] V[:, 0:i]^T v_i (LAPACK's dlarft, forward);
-  // thread t keeps column t of U in registers (pairs of rows) and applies the
-  // blocks to it, last block first.
+  // ---- 4. back-transformation U = H_0 ... H_{m-3} Y: thread t keeps column
+  // t of U in registers (pairs of rows) and applies the reflections one at a
+  // time, the last first: u <- u - 2 (v^T u) v (v read as 16-byte broadcasts,
+  // rows <= j skipped eight at a time).  No barriers: each thread owns its
+  // column, and a blocked (WY) form would save no arithmetic here.
   {
     const int nref = m - 2;
-    float* Tb = slc;                             // 8 x 8, then the Gram entries
-    float* Gv = slc + 64;
-    float2 u[NTC / 2];
-#pragma unroll
-    for (int k = 0; k < NTC / 2; ++k) {
-      u[k].x = (t < m && 2 * k < m) ? Y[(2 * k) * P + t] : 0.f;
-      u[k].y = (t < m && 2 * k + 1 < m) ? Y[(2 * k + 1) * P + t] : 0.f;
-    }
-    for (int jb = nref > 0 ? ((nref - 1) / 8) * 8 : -1; jb >= 0; jb -= 8) {
-      const int nb = min(8, nref - jb);
-      const float* Vb = Vr + (jb >> 3) * NTC * 8;    // [x/2][r][x%2]
-      gsync(g);
-      if (t < nb * nb) {                         // Gram entries v_a . v_b, a < b
-        const int ra = t / nb, rb = t - ra * nb;
-        if (ra < rb) {
-          float s0 = 0.f;
-          for (int x = jb + rb + 1; x < m; ++x) {
-            const float* vx = Vb + (x >> 1) * 16 + (x & 1);
-            s0 += vx[2 * ra] * vx[2 * rb];
-          }
-          Gv[ra * 8 + rb] = s0;
-        }
-      }
-      gsync(g);
-      if (t == 0) {
-        for (int ii = 0; ii < nb; ++ii) {
-          Tb[ii * 8 + ii] = 2.f;
-          for (int kk = 0; kk < ii; ++kk) {
-            float acc = 0.f;
-            for (int l = kk; l < ii; ++l) acc += Tb[kk * 8 + l] * Gv[l * 8 + ii];
-            Tb[kk * 8 + ii] = -2.f * acc;
-          }
-        }
-      }
-      gsync(g);
-      if (t < m) {
-        // w = V^T u: pairs of rows at a time, one pair accumulator per reflection
-        float2 w2p[8];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) w2p[r] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int k = 0; k < NTC / 2; ++k) {
-          if (2 * k + 1 > jb && 2 * k < m) {     // uniform: rows jb+1 .. m-1
-            const float4* vk = reinterpret_cast<const float4*>(Vb + k * 16);
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              const float4 vv = vk[h];
-              w2p[2 * h] = __ffma2_rn(make_float2(vv.x, vv.y), u[k], w2p[2 * h]);
-              w2p[2 * h + 1] = __ffma2_rn(make_float2(vv.z, vv.w), u[k], w2p[2 * h + 1]);
-            }
-          }
-        }
-        float w[8], wt[8];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) w[r] = r < nb ? w2p[r].x + w2p[r].y : 0.f;
-#pragma unroll
-        for (int ii = 0; ii < 8; ++ii) {
-          float acc = 0.f;
-#pragma unroll
-          for (int kk = 0; kk < 8; ++kk)
-            if (ii < nb && kk >= ii && kk < nb) acc += Tb[ii * 8 + kk] * w[kk];
-          wt[ii] = -acc;
-        }
-        // u -= V (Tb w)
-#pragma unroll
-        for (int k = 0; k < NTC / 2; ++k) {
-          if (2 * k + 1 > jb && 2 * k < m) {
-            const float4* vk = reinterpret_cast<const float4*>(Vb + k * 16);
-            float2 uk = u[k];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              const float4 vv = vk[h];
-              uk = __ffma2_rn(make_float2(vv.x, vv.y), make_float2(wt[2 * h], wt[2 * h]), uk);
-              uk = __ffma2_rn(make_float2(vv.z, vv.w), make_float2(wt[2 * h + 1], wt[2 * h + 1]), uk);
-            }
-            u[k] = uk;
-          }
-        }
-      }
-    }
     if (t < m) {
+      float2 u[NTC / 2];
+#pragma unroll
+      for (int k = 0; k < NTC / 2; ++k) {
+        u[k].x = 2 * k < m ? Y[(2 * k) * P + t] : 0.f;
+        u[k].y = 2 * k + 1 < m ? Y[(2 * k + 1) * P + t] : 0.f;
+      }
+      for (int j = nref - 1; j >= 0; --j) {
+        const float* vj = Vr + j * NTC;
+        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < NTC / 2; k += 4) {
+          if (2 * k + 7 > j) {
+            const float4 v0 = *reinterpret_cast<const float4*>(vj + 2 * k);
+            const float4 v1 = *reinterpret_cast<const float4*>(vj + 2 * k + 4);
+            a0 = __ffma2_rn(u[k], make_float2(v0.x, v0.y), a0);
+            a1 = __ffma2_rn(u[k + 1], make_float2(v0.z, v0.w), a1);
+            a0 = __ffma2_rn(u[k + 2], make_float2(v1.x, v1.y), a0);
+            a1 = __ffma2_rn(u[k + 3], make_float2(v1.z, v1.w), a1);
+          }
+        }
+        const float s2 = -2.f * ((a0.x + a0.y) + (a1.x + a1.y));
+        const float2 ss = make_float2(s2, s2);
+#pragma unroll
+        for (int k = 0; k < NTC / 2; k += 4) {
+          if (2 * k + 7 > j) {
+            const float4 v0 = *reinterpret_cast<const float4*>(vj + 2 * k);
+            const float4 v1 = *reinterpret_cast<const float4*>(vj + 2 * k + 4);
+            u[k] = __ffma2_rn(ss, make_float2(v0.x, v0.y), u[k]);
+            u[k + 1] = __ffma2_rn(ss, make_float2(v0.z, v0.w), u[k + 1]);
+            u[k + 2] = __ffma2_rn(ss, make_float2(v1.x, v1.y), u[k + 2]);
+            u[k + 3] = __ffma2_rn(ss, make_float2(v1.z, v1.w), u[k + 3]);
+          }
+        }
+      }
 #pragma unroll
       for (int k = 0; k < NTC / 2; ++k) {
         if (2 * k < m) Y[(2 * k) * P + t] = u[k].x;

@@ -15,6 +15,9 @@ namespace {
 
 constexpr int MT = 256;    // mu kernel threads (16 per partial value: MT >= 16 * 16)
 constexpr int RT = 128;    // rho kernel threads
+// energy reduction threads: one block; its FP64 additions all run on one SM,
+// so four warps rather than 32 (fewer warp-wide FP64 instructions)
+constexpr int ER_T = 128;
 
 __device__ __forceinline__ double fermi(double x) {
   if (x > 50.0) return 0.0;
@@ -673,7 +676,7 @@ energy_reduce_kernel(int n, const double* per_target, const double* mu, double* 
   __shared__ double red[32 * 5];
   __shared__ double tot[5];
   double v[5] = {0, 0, 0, 0, 0};
-  for (int i = threadIdx.x; i < n; i += 1024)
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
 #pragma unroll
     for (int c = 0; c < 5; ++c) v[c] += per_target[5 * i + c];
   tbk::block_sum<double, 5>(v, red, tot);
@@ -753,7 +756,7 @@ tb_status launch_virial(tb_ctx* c, int n, const double* pos, double L, const int
 
 tb_status launch_energy_reduce(int n, const double* per_target, const double* mu,
                                double* energies, cudaStream_t s) {
-  energy_reduce_kernel<<<1, 1024, 0, s>>>(n, per_target, mu, energies, 0);
+  energy_reduce_kernel<<<1, ER_T, 0, s>>>(n, per_target, mu, energies, 0);
   TB_CUDA_TRY(cudaGetLastError());
   return TB_OK;
 }
@@ -814,7 +817,7 @@ tb_status launch_forces(tb_ctx* c, int n, const double* pos, double L, const int
   TB_CUDA_TRY(cudaGetLastError());
   force_sum_kernel<<<(n + 255) / 256, 256, 0, s>>>(fa);
   TB_CUDA_TRY(cudaGetLastError());
-  energy_reduce_kernel<<<1, 1024, 0, s>>>(n, c->per_target, mu, energies, 0);
+  energy_reduce_kernel<<<1, ER_T, 0, s>>>(n, c->per_target, mu, energies, 0);
   TB_CUDA_TRY(cudaGetLastError());
   return TB_OK;
 }
@@ -830,7 +833,7 @@ tb_status launch_md_kick(tb_ctx* c, int n, double* vel, const double* F, double 
                          double mass, double* energies, cudaStream_t s) {
   kick_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, vel, F, dt, mass, c->per_target);
   TB_CUDA_TRY(cudaGetLastError());
-  energy_reduce_kernel<<<1, 1024, 0, s>>>(n, c->per_target, c->mu, energies, 1);
+  energy_reduce_kernel<<<1, ER_T, 0, s>>>(n, c->per_target, c->mu, energies, 1);
   TB_CUDA_TRY(cudaGetLastError());
   return TB_OK;
 }

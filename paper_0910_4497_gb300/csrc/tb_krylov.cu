@@ -58,7 +58,8 @@ struct KryArgs {
   unsigned long long* colmask;
   TV* Vg;
   int2* lent;
-  int lent_smem;            // 1: the local CSR lives in shared memory
+  int lent_smem;            // 1: the local CSR lives in shared memory when it fits
+  int lent_cap;             // its entries in shared memory
   int* st;
   // fused eigensolve outputs
   float* lamf;
@@ -81,6 +82,13 @@ __device__ __forceinline__ int find_slot(const int* cl, int nc, int b) {
 
 __host__ __device__ __forceinline__ size_t align32(size_t x) { return (x + 31) & ~size_t(31); }
 
+// Entries of the local CSR kept in shared memory: 16 per cluster slot (the
+// Hamiltonian lists of carbon within 2.6 A hold 3-16 atoms); a target with
+// more uses its CTA's slot in global memory.
+__host__ __device__ __forceinline__ int lent_smem_cap(int max_cluster, int max_hnbr) {
+  return max_cluster * (max_hnbr < 16 ? max_hnbr : 16);
+}
+
 template <typename TV>
 __host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, int max_hnbr, bool vsmem,
                                                  bool lsmem) {
@@ -92,7 +100,7 @@ __host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, int max
   b += align32(sizeof(TV) * Dmax * 4);                // W
   if (vsmem) b += align32(sizeof(TV) * Dmax * 4 * r); // basis
   else b += align32(sizeof(TV) * Dmax * 4);          // copy of the current block
-  if (lsmem) b += align32(sizeof(int2) * (size_t)max_cluster * max_hnbr);  // local CSR
+  if (lsmem) b += align32(sizeof(int2) * (size_t)lent_smem_cap(max_cluster, max_hnbr));  // local CSR
   b += align32(sizeof(TV) * 16 * np);                 // projection partials
   b += align32(sizeof(TV) * 16 * r);                  // projection coefficients
   b += align32(sizeof(TV) * 16 * 4);                  // B_{k-1}, Gram, R, R^{-1}
@@ -127,10 +135,11 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
     Vks = reinterpret_cast<TV*>(smem + off);
     off += align32(sizeof(TV) * (size_t)Dmax * 4);
   }
-  int2* lent = a.lent + (size_t)blockIdx.x * a.max_cluster * a.max_hnbr;   // local CSR
+  int2* const lent_g = a.lent + (size_t)blockIdx.x * a.max_cluster * a.max_hnbr;   // local CSR
+  int2* lent_s = nullptr;
   if (a.lent_smem) {
-    lent = reinterpret_cast<int2*>(smem + off);
-    off += align32(sizeof(int2) * (size_t)a.max_cluster * a.max_hnbr);
+    lent_s = reinterpret_cast<int2*>(smem + off);
+    off += align32(sizeof(int2) * (size_t)a.lent_cap);
   }
   TV* Cp = reinterpret_cast<TV*>(smem + off);        off += align32(sizeof(TV) * 16 * np);
   TV* Cc = reinterpret_cast<TV*>(smem + off);        off += align32(sizeof(TV) * 16 * r);
@@ -212,6 +221,7 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
       }
       __syncthreads();
     }
+    int2* const lent = (lent_s && rowptr[nc] <= a.lent_cap) ? lent_s : lent_g;
     for (int s = tid; s < nc; s += KT) {
       const int at = cl[s];
       int e = rowptr[s];
@@ -582,7 +592,7 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
 
 // One CTA per target atom, persistent (grid-stride over the targets).
 template <typename TV, bool VSMEM, bool FUSED, int KT>
-__global__ void __launch_bounds__(KT, KT_MAX / KT * 2) krylov_kernel(const KryArgs<TV> a) {
+__global__ void __launch_bounds__(KT, KT == 128 ? (sizeof(TV) == 4 ? 5 : 4) : 2) krylov_kernel(const KryArgs<TV> a) {
   for (int i = blockIdx.x; i < a.n; i += gridDim.x) krylov_target<TV, VSMEM, FUSED, KT>(a, i);
 }
 
@@ -662,9 +672,8 @@ tb_status kry_eig_configure_t(tb_ctx* c, int max_smem) {
   TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kry_eig_kernel<NTC>, 128, bytes));
   if (occ < 1) return TB_ERR_CAPACITY;
   const int grid = c->num_sms * occ;
-  // only where the eigensolve's shared memory costs the Krylov part no
-  // occupancy (the basis slots and local CSR are per CTA, sized for kry_grid)
-  if (grid != c->kry_grid) return TB_ERR_CAPACITY;
+  // the basis slots and local CSR are per CTA, sized for kry_grid
+  if (grid > c->kry_grid) return TB_ERR_CAPACITY;
   c->ke_smem = bytes;
   c->ke_grid = grid;
   c->ke_on = true;
@@ -693,6 +702,7 @@ tb_status kry_eig_launch(tb_ctx* c, int n, const int* c_off, const int* c_idx, c
   a.T = c->T; a.Y = reinterpret_cast<float*>(c->Y); a.colmask = c->colmask;
   a.Vg = reinterpret_cast<float*>(c->Vg); a.lent = c->lent; a.st = c->d_status;
   a.lent_smem = c->kry_lsmem ? 1 : 0;
+  a.lent_cap = lent_smem_cap(p.max_cluster, p.max_hnbr);
   a.lamf = c->lamf; a.Zf = c->Zf; a.lambda = lambda; a.S = S; a.P = P; a.kdim = kdim;
   XArgs xa{n, 4 * p.r, c->T, c->colmask, reinterpret_cast<const float*>(c->Y), h_off, c->Zf,
            c->lamf, lambda, S, P, kdim, c->d_status};
@@ -723,6 +733,7 @@ tb_status launch_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const i
   a.T = c->T; a.Y = reinterpret_cast<TV*>(c->Y); a.colmask = c->colmask;
   a.Vg = reinterpret_cast<TV*>(c->Vg); a.lent = c->lent; a.st = c->d_status;
   a.lent_smem = c->kry_lsmem ? 1 : 0;
+  a.lent_cap = lent_smem_cap(p.max_cluster, p.max_hnbr);
   a.lamf = c->lamf; a.Zf = c->Zf; a.lambda = lambda; a.S = S; a.P = P; a.kdim = kdim;
   const int grid = n < c->kry_grid ? n : c->kry_grid;
   if (grid <= 0) return TB_OK;

@@ -63,9 +63,18 @@ __host__ __device__ inline size_t xw_hsize(int NT) {
 constexpr int GT = 64;             // threads per target (two warps)
 constexpr int NSLICE = 2 * GT;     // spectrum-slicing points
 
+// One scratch region serves, one phase at a time, the Householder vectors
+// (4 ntc_of(NT) + 8 floats), the slicing counts (NSLICE) and the restart
+// factorisation of the eigenvector phase (5 NT).
+__host__ __device__ inline size_t xw_scratch(int NT) {
+  size_t a = 5 * (size_t)NT, b = 4 * (size_t)ntc_of(NT) + 8;
+  if (b > a) a = b;
+  return a > (size_t)NSLICE ? a : (size_t)NSLICE;
+}
+
 __host__ __device__ inline size_t xw_smem_per_warp(int NT) {   // per target
   size_t b = sizeof(double) * NT;                          // lamd
-  b += sizeof(float) * (xw_hsize(NT) + (size_t)NT * xpitch(NT) + 11 * (size_t)NT + NSLICE + 8);
+  b += sizeof(float) * (xw_hsize(NT) + (size_t)NT * xpitch(NT) + 6 * (size_t)NT + xw_scratch(NT) + 8);
   b += sizeof(int) * 2 * NT;                               // act, rank
   return (b + 15) & ~size_t(15);
 }
@@ -284,9 +293,9 @@ __device__ __forceinline__ void eig_group(const XArgs& a, int i, Grp g, unsigned
   float* lam = e2 + NT;
   float* v = lam + NT;
   float* q = v + NT;
-  float* fs = q + NT;                          // 5 NT: restart factorisation
-  float* slc = fs + 5 * NT;                    // NSLICE slicing counts
-  g.red = slc + NSLICE;                        // 8 floats
+  float* fs = q + NT;                          // scratch: Householder vectors, then
+  float* slc = fs;                             // the slicing counts, then the restart
+  g.red = fs + xw_scratch(NT);                 // factorisation; 8 floats of reductions
   int* act = reinterpret_cast<int*>(g.red + 8);
   int* rank = act + NT;
 

@@ -99,6 +99,26 @@ def config_dict(cfg, n, extra):
     return d
 
 
+# ---------------------------------------------------------------- ranks
+
+def max_over_ranks(x, world, device):
+    """The largest of one float over the ranks of the job (the job's time is
+    its slowest rank's); the value itself for a single rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_throughput(units_per_rank, world, steps, total_ms):
+    """Whole-job rate: every rank processes units_per_rank per step (replicas,
+    weak scaling) and the job takes the slowest rank's total_ms."""
+    return world * units_per_rank * steps / (total_ms / 1e3)
+
+
 # ---------------------------------------------------------------- CPU oracle
 
 def time_oracle_full(pos, L, p):
@@ -350,12 +370,9 @@ def run_ours(args):
     clk = clocks.stop() if clocks else None
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = max_over_ranks(total_ms, world, dev)
     system.check()
-    value = world * n * args.steps / (total_ms / 1e3)
+    value = job_throughput(n, world, args.steps, total_ms)
     accuracy = None
     if ref is not None:
         import numpy as np
@@ -384,11 +401,8 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = t.item()
-    e2e_value = world * n * args.steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    e2e_value = job_throughput(n, world, args.steps, e2e_ms)
 
     if rank == 0:
         kry = [v for v in stage_ms["krylov"] if v > 0]
@@ -595,11 +609,8 @@ def run_md(args):
     clk = clocks.stop() if clocks else None
     system.check()
     total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = t.item()
-    value = world * n * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, world, dev)
+    value = job_throughput(n, world, args.steps, total_ms)
     pos_end = system.pos.clone()
 
     # ---- end to end: the state goes host -> device and back every step
@@ -620,11 +631,8 @@ def run_md(args):
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = t.item()
-    e2e_value = world * n * args.steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    e2e_value = job_throughput(n, world, args.steps, e2e_ms)
     # kick-drift + one force evaluation + kick and its energy reduction
     launches_per_step = tb.binding.tb_ctx_kernels_per_evaluation(system.ctx, n, L) + 3
     system.close()
@@ -824,11 +832,9 @@ def run_autograd(args):
         s.close()
     clk = clocks.stop() if clocks else None
     t_step = sum(a + b for a, b in zip(res[True]["fwd"], res[True]["bwd"]))
-    if world > 1:
-        t = torch.tensor([t_step, res["e2e_ms"]], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_step, res["e2e_ms"] = t.tolist()
-    value = world * n * args.steps / (t_step / 1e3)
+    t_step = max_over_ranks(t_step, world, dev)
+    res["e2e_ms"] = max_over_ranks(res["e2e_ms"], world, dev)
+    value = job_throughput(n, world, args.steps, t_step)
     check = None
     if rank == 0:
         # FP64 reference gradient and central differences of the FP64 energy
@@ -869,7 +875,7 @@ def run_autograd(args):
                        "precision": args.prec, "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "step": "forward (spectra, mu, energies) + stored-basis backward"},
-            "e2e": {"value": world * n * args.steps / (res["e2e_ms"] / 1e3), "unit": UNIT,
+            "e2e": {"value": job_throughput(n, world, args.steps, res["e2e_ms"]), "unit": UNIT,
                     "h2d_bytes_per_step": n * 3 * 8, "d2h_bytes_per_step": n * 3 * 8 + 64},
             "roofline": None,
             "cpu_baseline": cpu_base,
@@ -1031,11 +1037,8 @@ def run_eos(args):
     barrier()
     clk = clocks.stop() if clocks else None
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = t.item()
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, world, dev)
+    value = job_throughput(1, world, args.steps, total_ms)
     # end to end: positions in, energies and pressure out
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     hp = [torch.as_tensor(x[1], dtype=torch.float64).pin_memory() for x in systems]
@@ -1055,10 +1058,7 @@ def run_eos(args):
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = t.item()
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
     # equation of state and its convergence (untimed)
     table = []
     for a, pos, L, s in systems:
@@ -1115,7 +1115,7 @@ def run_eos(args):
                        "precision": args.prec, "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "graph": "one CUDA graph per pressure evaluation"},
-            "e2e": {"value": world * args.steps / (e2e_ms / 1e3), "unit": EOS_UNIT,
+            "e2e": {"value": job_throughput(1, world, args.steps, e2e_ms), "unit": EOS_UNIT,
                     "h2d_bytes_per_step": n * 3 * 8, "d2h_bytes_per_step": 18 * 8},
             "roofline": {"bound": "hbm", "kernel": "krylov_kernel", "achieved": achieved,
                          "peak": hbm, "unit": "GB/s", "frac": achieved / hbm if achieved else None,

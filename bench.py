@@ -330,11 +330,22 @@ def run_ours(args):
     n = len(pos)
     cpu_base = None
     ref = None
+    cpu_all = None
     if rank == 0 and not args.no_cpu_baseline:
         t_or, ref = time_oracle_full(pos, L, p)  # before any GPU work of this process
         cpu_base = {"value": n / t_or, "unit": UNIT, "cores": 1, "kind": "oracle",
                     "sample": f"one full FP64 oracle force evaluation of the {n}-atom cell "
                               f"({t_or:.1f} s, single process)"}
+        ncores = os.cpu_count() or 1
+        if ncores > 1:
+            import oracle
+            t0 = time.perf_counter()
+            oracle.force_evaluation(pos, L, p, workers=ncores, group_m=p.get("group_m", 1))
+            t_all = time.perf_counter() - t0
+            cpu_all = {"value": n / t_all, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                       "sample": f"the same evaluation with the targets spread over {ncores} "
+                                 f"spawned worker processes ({t_all:.1f} s, pool start-up "
+                                 f"included)"}
     dev = torch.device("cuda", local)
     system = tb.TBSystem(n, L, p, prec=args.prec, device=dev)
     B.tb_profile_enable(system.ctx, True)
@@ -454,6 +465,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": n * 3 * 8 + 8 * 8},
             "roofline": roof,
             "cpu_baseline": cpu_base,
+            "cpu_baseline_all_cores": cpu_all,
             "clocks": clk,
             "gpu_launches": launches_per_step * args.steps,
             "stage_ms": stages,

@@ -52,10 +52,11 @@ __host__ __device__ inline int epitch(int NT) { return NT + 4; }   // E rows 16-
 __host__ __device__ inline int ntc_of(int NT) { return NT <= 16 ? 16 : NT <= 32 ? 32 : NT <= 48 ? 48 : 64; }
 
 // H also holds the reflections between the Householder and back-transform
-// phases: NT - 2 rows of ntc_of(NT)
+// phases (NT - 2 rows of ntc_of(NT)), then the eigenvectors as rows (NT rows
+// of ntc_of(NT)) in the Loewdin step
 __host__ __device__ inline size_t xw_hsize(int NT) {
   const size_t a = (size_t)NT * epitch(NT), b = 24 * (size_t)NT;
-  const size_t c = (size_t)(NT > 2 ? NT - 2 : 0) * ntc_of(NT);
+  const size_t c = (size_t)NT * ntc_of(NT);
   const size_t ab = a > b ? a : b;
   return ab > c ? ab : c;
 }
@@ -527,110 +528,96 @@ __device__ __forceinline__ void eig_group(const XArgs& a, int i, Grp g, unsigned
   // t of U in registers (pairs of rows) and applies the reflections one at a
   // time, the last first: u <- u - 2 (v^T u) v (v read as 16-byte broadcasts,
   // rows <= j skipped eight at a time).  No barriers: each thread owns its
-  // column, and a blocked (WY) form would save no arithmetic here.
-  {
-    const int nref = m - 2;
-    if (t < m) {
-      float2 u[NTC / 2];
+  // column, and a blocked (WY) form would save no arithmetic here.  The
+  // column stays in registers through the Loewdin step and the spectral
+  // record.
+  float2 u[NTC / 2];
 #pragma unroll
-      for (int k = 0; k < NTC / 2; ++k) {
-        u[k].x = 2 * k < m ? Y[(2 * k) * P + t] : 0.f;
-        u[k].y = 2 * k + 1 < m ? Y[(2 * k + 1) * P + t] : 0.f;
-      }
-      for (int j = nref - 1; j >= 0; --j) {
-        const float* vj = Vr + j * NTC;
-        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+  for (int k = 0; k < NTC / 2; ++k) {
+    u[k].x = (t < m && 2 * k < m) ? Y[(2 * k) * P + t] : 0.f;
+    u[k].y = (t < m && 2 * k + 1 < m) ? Y[(2 * k + 1) * P + t] : 0.f;
+  }
+  if (t < m) {
+    for (int j = m - 3; j >= 0; --j) {
+      const float* vj = Vr + j * NTC;
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < NTC / 2; k += 4) {
-          if (2 * k + 7 > j) {
-            const float4 v0 = *reinterpret_cast<const float4*>(vj + 2 * k);
-            const float4 v1 = *reinterpret_cast<const float4*>(vj + 2 * k + 4);
-            a0 = __ffma2_rn(u[k], make_float2(v0.x, v0.y), a0);
-            a1 = __ffma2_rn(u[k + 1], make_float2(v0.z, v0.w), a1);
-            a0 = __ffma2_rn(u[k + 2], make_float2(v1.x, v1.y), a0);
-            a1 = __ffma2_rn(u[k + 3], make_float2(v1.z, v1.w), a1);
-          }
-        }
-        const float s2 = -2.f * ((a0.x + a0.y) + (a1.x + a1.y));
-        const float2 ss = make_float2(s2, s2);
-#pragma unroll
-        for (int k = 0; k < NTC / 2; k += 4) {
-          if (2 * k + 7 > j) {
-            const float4 v0 = *reinterpret_cast<const float4*>(vj + 2 * k);
-            const float4 v1 = *reinterpret_cast<const float4*>(vj + 2 * k + 4);
-            u[k] = __ffma2_rn(ss, make_float2(v0.x, v0.y), u[k]);
-            u[k + 1] = __ffma2_rn(ss, make_float2(v0.z, v0.w), u[k + 1]);
-            u[k + 2] = __ffma2_rn(ss, make_float2(v1.x, v1.y), u[k + 2]);
-            u[k + 3] = __ffma2_rn(ss, make_float2(v1.z, v1.w), u[k + 3]);
-          }
+      for (int k = 0; k < NTC / 2; k += 4) {
+        if (2 * k + 7 > j) {
+          const float4 v0 = *reinterpret_cast<const float4*>(vj + 2 * k);
+          const float4 v1 = *reinterpret_cast<const float4*>(vj + 2 * k + 4);
+          a0 = __ffma2_rn(u[k], make_float2(v0.x, v0.y), a0);
+          a1 = __ffma2_rn(u[k + 1], make_float2(v0.z, v0.w), a1);
+          a0 = __ffma2_rn(u[k + 2], make_float2(v1.x, v1.y), a0);
+          a1 = __ffma2_rn(u[k + 3], make_float2(v1.z, v1.w), a1);
         }
       }
+      const float s2 = -2.f * ((a0.x + a0.y) + (a1.x + a1.y));
+      const float2 ss = make_float2(s2, s2);
 #pragma unroll
-      for (int k = 0; k < NTC / 2; ++k) {
-        if (2 * k < m) Y[(2 * k) * P + t] = u[k].x;
-        if (2 * k + 1 < m) Y[(2 * k + 1) * P + t] = u[k].y;
+      for (int k = 0; k < NTC / 2; k += 4) {
+        if (2 * k + 7 > j) {
+          const float4 v0 = *reinterpret_cast<const float4*>(vj + 2 * k);
+          const float4 v1 = *reinterpret_cast<const float4*>(vj + 2 * k + 4);
+          u[k] = __ffma2_rn(ss, make_float2(v0.x, v0.y), u[k]);
+          u[k + 1] = __ffma2_rn(ss, make_float2(v0.z, v0.w), u[k + 1]);
+          u[k + 2] = __ffma2_rn(ss, make_float2(v1.x, v1.y), u[k + 2]);
+          u[k + 3] = __ffma2_rn(ss, make_float2(v1.z, v1.w), u[k + 3]);
+        }
       }
     }
   }
-  gsync(g);
+  gsync(g);                                      // every thread is done with Vr
 
-  // ---- 5. Loewdin U <- U (I - E/2), E = U^T U - I: E into H (aligned
-  // rows), then each thread updates its own row 16 columns at a time; a chunk
-  // written back before the next chunk is formed changes the result only at
-  // second order in E, below the first-order step's own error.
-  float* E = H;
-  const int PE = epitch(NT);
+  // ---- 5. Loewdin U <- U (I - E), E = (U^T U - I) / 2: the eigenvectors as
+  // rows Ut (16-byte rows, read as broadcasts) in H, thread b forms column b
+  // of E from its register column into Y's space, then updates its column
+  // u_b <- u_b - sum_c u_c E[c][b] from the rows, and U returns to Y.
+  float* const Ut = H;
   if (t < m) {
-    const int b = t;
-    int c = 0;
-    for (; c + 1 < m; c += 2) {
-      float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
-      int x = 0;
-      for (; x + 1 < m; x += 2) {
-        const float yb0 = Y[x * P + b], yb1 = Y[(x + 1) * P + b];
-        t0 += Y[x * P + c] * yb0;
-        t1 += Y[x * P + c + 1] * yb0;
-        t2 += Y[(x + 1) * P + c] * yb1;
-        t3 += Y[(x + 1) * P + c + 1] * yb1;
+#pragma unroll
+    for (int k = 0; k < NTC / 2; k += 2)
+      *reinterpret_cast<float4*>(Ut + t * NTC + 2 * k) = make_float4(u[k].x, u[k].y, u[k + 1].x, u[k + 1].y);
+  }
+  gsync(g);
+  float* const E = Y;
+  if (t < m) {
+    for (int c = 0; c < m; ++c) {
+      const float* uc = Ut + c * NTC;
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < NTC / 2; k += 2) {
+        if (2 * k < m) {
+          const float4 v = *reinterpret_cast<const float4*>(uc + 2 * k);
+          a0 = __ffma2_rn(u[k], make_float2(v.x, v.y), a0);
+          a1 = __ffma2_rn(u[k + 1], make_float2(v.z, v.w), a1);
+        }
       }
-      if (x < m) {
-        const float yb = Y[x * P + b];
-        t0 += Y[x * P + c] * yb;
-        t1 += Y[x * P + c + 1] * yb;
-      }
-      E[c * PE + b] = 0.5f * ((t0 + t2) - (b == c ? 1.f : 0.f));
-      E[(c + 1) * PE + b] = 0.5f * ((t1 + t3) - (b == c + 1 ? 1.f : 0.f));
-    }
-    if (c < m) {
-      float t0 = 0.f;
-      for (int x = 0; x < m; ++x) t0 += Y[x * P + c] * Y[x * P + b];
-      E[c * PE + b] = 0.5f * (t0 - (b == c ? 1.f : 0.f));
+      E[c * P + t] = 0.5f * (((a0.x + a0.y) + (a1.x + a1.y)) - (c == t ? 1.f : 0.f));
     }
   }
   gsync(g);
-  // (columns past m of a chunk read whatever follows in shared memory; their
-  // sums are discarded)
   if (t < m) {
-    float* yx = Y + t * P;
-    for (int b0 = 0; b0 < m; b0 += 16) {
-      float acc[16];
+    for (int c = 0; c < m; ++c) {
+      const float ec = -E[c * P + t];
+      const float2 e2 = make_float2(ec, ec);
+      const float* uc = Ut + c * NTC;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) acc[j] = 0.f;
-      for (int c = 0; c < m; ++c) {
-        const float yc = yx[c];
-        const float4* er = reinterpret_cast<const float4*>(E + c * PE + b0);
-#pragma unroll
-        for (int j4 = 0; j4 < 4; ++j4) {
-          const float4 ev = er[j4];
-          acc[4 * j4 + 0] += yc * ev.x;
-          acc[4 * j4 + 1] += yc * ev.y;
-          acc[4 * j4 + 2] += yc * ev.z;
-          acc[4 * j4 + 3] += yc * ev.w;
+      for (int k = 0; k < NTC / 2; k += 2) {
+        if (2 * k < m) {
+          const float4 v = *reinterpret_cast<const float4*>(uc + 2 * k);
+          u[k] = __ffma2_rn(e2, make_float2(v.x, v.y), u[k]);
+          u[k + 1] = __ffma2_rn(e2, make_float2(v.z, v.w), u[k + 1]);
         }
       }
+    }
+  }
+  gsync(g);                                      // E (in Y's space) is read
+  if (t < m) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (b0 + j < m) yx[b0 + j] -= acc[j];
+    for (int k = 0; k < NTC / 2; ++k) {
+      if (2 * k < m) Y[(2 * k) * P + t] = u[k].x;
+      if (2 * k + 1 < m) Y[(2 * k + 1) * P + t] = u[k].y;
     }
   }
   gsync(g);
@@ -715,6 +702,8 @@ __device__ __forceinline__ void eig_group(const XArgs& a, int i, Grp g, unsigned
     for (int r0 = 0; r0 < nrows; r0 += RW) {
       const int nr = min(RW, nrows - r0);
       gsync(g);
+      if (t >= m && t < NT)                    // past the active columns: zeros
+        for (int rr = 0; rr < nr; ++rr) Yr[rr * NT + t] = 0.f;
       if (t < m) {
         const int ax = act[t];
         int rr = 0;
@@ -737,24 +726,23 @@ __device__ __forceinline__ void eig_group(const XArgs& a, int i, Grp g, unsigned
           double* p0 = a.P + (rbase + r0 + rr) * NT;
           double* p1 = p0 + NT;
           if (t < m) {
+            // rows of the basis as 16-byte broadcasts against the register column
             const float* y0 = Yr + rr * NT;
             const float* y1 = y0 + NT;
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-            int x = 0;
-            for (; x + 1 < m; x += 2) {
-              const float u0 = Y[x * P + t], u1 = Y[(x + 1) * P + t];
-              s0 += y0[x] * u0;
-              s1 += y0[x + 1] * u1;
-              s2 += y1[x] * u0;
-              s3 += y1[x + 1] * u1;
+            float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < NTC / 2; k += 2) {
+              if (2 * k < m) {
+                const float4 v0 = *reinterpret_cast<const float4*>(y0 + 2 * k);
+                const float4 v1 = *reinterpret_cast<const float4*>(y1 + 2 * k);
+                s0 = __ffma2_rn(u[k], make_float2(v0.x, v0.y), s0);
+                s0 = __ffma2_rn(u[k + 1], make_float2(v0.z, v0.w), s0);
+                s1 = __ffma2_rn(u[k], make_float2(v1.x, v1.y), s1);
+                s1 = __ffma2_rn(u[k + 1], make_float2(v1.z, v1.w), s1);
+              }
             }
-            if (x < m) {
-              const float u0 = Y[x * P + t];
-              s0 += y0[x] * u0;
-              s2 += y1[x] * u0;
-            }
-            p0[rank[t]] = (double)(s0 + s1);
-            p1[rank[t]] = (double)(s2 + s3);
+            p0[rank[t]] = (double)(s0.x + s0.y);
+            p1[rank[t]] = (double)(s1.x + s1.y);
           } else {
             p0[t] = 0.0;
             p1[t] = 0.0;
@@ -764,9 +752,16 @@ __device__ __forceinline__ void eig_group(const XArgs& a, int i, Grp g, unsigned
           double* p0 = a.P + (rbase + r0 + rr) * NT;
           if (t < m) {
             const float* y0 = Yr + rr * NT;
-            float s0 = 0.f;
-            for (int x = 0; x < m; ++x) s0 += y0[x] * Y[x * P + t];
-            p0[rank[t]] = (double)s0;
+            float2 s0 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < NTC / 2; k += 2) {
+              if (2 * k < m) {
+                const float4 v0 = *reinterpret_cast<const float4*>(y0 + 2 * k);
+                s0 = __ffma2_rn(u[k], make_float2(v0.x, v0.y), s0);
+                s0 = __ffma2_rn(u[k + 1], make_float2(v0.z, v0.w), s0);
+              }
+            }
+            p0[rank[t]] = (double)(s0.x + s0.y);
           } else {
             p0[t] = 0.0;
           }

@@ -96,7 +96,7 @@ __host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, int max
   const size_t np = (size_t)(r > KW_MAX ? r : KW_MAX);
   size_t b = 0;
   b += align32(sizeof(int) * max_cluster);            // cl
-  b += align32(sizeof(int) * (max_cluster + 1));      // rowptr
+  b += align32(sizeof(int) * (max_cluster + 1));      // entries per slot
   b += align32(sizeof(TV) * Dmax * 4);                // W
   if (vsmem) b += align32(sizeof(TV) * Dmax * 4 * r); // basis
   else b += align32(sizeof(TV) * Dmax * 4);          // copy of the current block
@@ -123,7 +123,7 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
   const int np = r > KW ? r : KW;
   size_t off = 0;
   int* cl = reinterpret_cast<int*>(smem + off);      off += align32(sizeof(int) * a.max_cluster);
-  int* rowptr = reinterpret_cast<int*>(smem + off);  off += align32(sizeof(int) * (a.max_cluster + 1));
+  int* cnt = reinterpret_cast<int*>(smem + off);     off += align32(sizeof(int) * (a.max_cluster + 1));
   TV* W = reinterpret_cast<TV*>(smem + off);         off += align32(sizeof(TV) * Dmax * 4);
   TV* V;
   TV* Vks = nullptr;                                 // copy of the current block (global basis)
@@ -181,55 +181,35 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
       return;
     }
     __syncthreads();
-    // ---- local sparsity of H_c: counts, block-wide exclusive scan, fill
-    for (int s = tid; s < nc; s += KT) {
-      const int at = cl[s];
-      int cnt = 0;
-      const int pe = min(a.h_off[at + 1], a.h_off[at] + a.max_hnbr);
-      for (int p = a.h_off[at]; p < pe; ++p)
-        cnt += find_slot(cl, nc, a.h_idx[p]) >= 0;
-      rowptr[s] = cnt;
-    }
-    __syncthreads();
-    {
-      int v[4], tot = 0;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int idx = tid * 4 + q;
-        v[q] = idx < nc ? rowptr[idx] : 0;
-        tot += v[q];
-      }
-      int x = tot;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      if (lane == 31) flags[warp] = x;
+    // ---- local sparsity of H_c in one pass: slot s keeps its in-cluster
+    // neighbours (local slot, global bond) at s * ls .. s * ls + cnt[s] - 1,
+    // ls = 16 in shared memory; a slot with more (none in carbon within 2.6 A)
+    // sends the target to its CTA's global slot with ls = max_hnbr
+    int ls = lent_s ? a.lent_cap / a.max_cluster : a.max_hnbr;
+    int2* lent = lent_s ? lent_s : lent_g;
+    for (int pass = 0; pass < 2; ++pass) {
+      if (tid == 0) flags[FL_OK] = 0;
       __syncthreads();
-      int wbase = 0;
-      for (int w = 0; w < warp; ++w) wbase += flags[w];
-      int run = wbase + x - tot;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int idx = tid * 4 + q;
-        if (idx < nc) {
-          rowptr[idx] = run;
-          run += v[q];
-          if (idx == nc - 1) rowptr[nc] = run;
+      for (int s = tid; s < nc; s += KT) {
+        const int at = cl[s];
+        int e = 0;
+        const int pe = min(a.h_off[at + 1], a.h_off[at] + a.max_hnbr);
+        for (int p = a.h_off[at]; p < pe; ++p) {
+          const int t = find_slot(cl, nc, a.h_idx[p]);
+          if (t >= 0) {
+            if (e < ls) lent[s * ls + e] = make_int2(t, p);
+            ++e;
+          }
         }
+        cnt[s] = e;
+        if (e > ls) flags[FL_OK] = 1;
       }
       __syncthreads();
-    }
-    int2* const lent = (lent_s && rowptr[nc] <= a.lent_cap) ? lent_s : lent_g;
-    for (int s = tid; s < nc; s += KT) {
-      const int at = cl[s];
-      int e = rowptr[s];
-      const int pe = min(a.h_off[at + 1], a.h_off[at] + a.max_hnbr);
-      for (int p = a.h_off[at]; p < pe; ++p) {
-        const int t = find_slot(cl, nc, a.h_idx[p]);
-        if (t >= 0) lent[e++] = make_int2(t, p);
-      }
+      const bool over = flags[FL_OK] != 0;
+      __syncthreads();                         // every thread has read the flag
+      if (!over || lent == lent_g) break;
+      ls = a.max_hnbr;                         // overflow: the global slot
+      lent = lent_g;
     }
     // seed block V_1 = E_i
     const int D = 4 * nc;
@@ -240,7 +220,7 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
     if (tid < 16) Bp[tid] = (TV)0;
     if (tid == 0) { flags[FL_MASK] = 0xF; flags[FL_MASK + 1] = 0; flags[FL_ACT] = 0xF; }
     __syncthreads();
-    if (tid == 0 && rowptr[1] - rowptr[0] != deg) tbk::set_status(a.st, TB_ERR_INVALID_ARG, i);
+    if (tid == 0 && cnt[0] != deg) tbk::set_status(a.st, TB_ERR_INVALID_ARG, i);
 
     int nblocks = 1;
     for (int k = 0; k < r; ++k) {
@@ -259,9 +239,9 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
         TV acc[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[c] = on * vs.v[c];
-        const int e1 = rowptr[s + 1];
+        const int e1 = s * ls + cnt[s];
 #pragma unroll 4
-        for (int e = rowptr[s]; e < e1; ++e) {
+        for (int e = s * ls; e < e1; ++e) {
           const int2 en = lent[e];
           const vec4<TV> h = ldg4(a.H + (size_t)en.y * 16 + al * 4);
 #pragma unroll
@@ -537,11 +517,11 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
       const int nrows = (deg + 1) * 4;
       // (a row with fewer entries than the H list was reported above; its
       // missing neighbours get zero rows)
-      const int rcnt = rowptr[1] - rowptr[0];
+      const int rcnt = cnt[0];
       for (int q = tid; q < nrows * NT; q += KT) {
         const int rr = q / NT, col = q - rr * NT;
         const int qq = rr >> 2, beta = rr & 3;
-        const int slot = qq == 0 ? 0 : (qq - 1 < rcnt ? lent[rowptr[0] + qq - 1].x : -1);
+        const int slot = qq == 0 ? 0 : (qq - 1 < rcnt ? lent[qq - 1].x : -1);
         const int b = col >> 2, c = col & 3;
         TV val = (TV)0;
         if (b < nblocks && slot >= 0) val = V[(size_t)b * Dmax * 4 + (4 * slot + beta) * 4 + c];

@@ -343,33 +343,40 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
       int chol_state = 0;   // 1: first factor refused (W untouched); 2: second refused
       for (int cq = 0; cq < 2; ++cq) {
         tbk::block_sum16<TV, 10>(g, red, Gs);
-        // one thread factors the Gram matrix and publishes R^{-1} (and R)
-        if (tid == 0) {
+        // FP32: every thread factors the (same) Gram matrix itself, identical R
+        // and R^{-1} everywhere with no broadcast and no barrier; FP64 (a slow
+        // pipe shared by the whole SM): one thread factors and publishes
+        TV R[16], Ri[16];
+        int okf;
+        if (sizeof(TV) == 4 || tid == 0) {
           TV G[16];
           int q = 0;
 #pragma unroll
           for (int c = 0; c < 4; ++c)
 #pragma unroll
             for (int e = c; e < 4; ++e) { G[c * 4 + e] = Gs[q]; G[e * 4 + c] = Gs[q]; ++q; }
-          TV R[16], Ri[16];
           bool well;
           const bool ok = chol4(G, R, chol_rel, cq == 0 ? chol_abs : 0.0, well);
           triinv4(R, Ri);
-#pragma unroll
-          for (int q2 = 0; q2 < 16; ++q2) { Rsh[q2] = R[q2]; Rish[q2] = Ri[q2]; }
           // FP32 path: a well-conditioned block needs no second pass
-          flags[FL_OK] = ok ? ((cq == 0 && well && sizeof(TV) == 4) ? 2 : 1) : 0;
+          okf = ok ? ((cq == 0 && well && sizeof(TV) == 4) ? 2 : 1) : 0;
+          if (sizeof(TV) != 4) {
+#pragma unroll
+            for (int q2 = 0; q2 < 16; ++q2) { Rsh[q2] = R[q2]; Rish[q2] = Ri[q2]; }
+            flags[FL_OK] = okf;
+          }
         }
-        __syncthreads();
-        const int okf = flags[FL_OK];
-        if (!okf) {                 // uniform: every thread reads the same flag
+        if (sizeof(TV) != 4) {
+          __syncthreads();
+          okf = flags[FL_OK];
+#pragma unroll
+          for (int q2 = 0; q2 < 16; ++q2) { R[q2] = Rsh[q2]; Ri[q2] = Rish[q2]; }
+        }
+        if (!okf) {                 // uniform: every thread factors the same matrix
           chol_state = cq + 1;
           break;
         }
         const bool single = okf == 2;
-        TV R[16], Ri[16];
-#pragma unroll
-        for (int q2 = 0; q2 < 16; ++q2) { R[q2] = Rsh[q2]; Ri[q2] = Rish[q2]; }
         TV* dst = (cq == 0 && !single) ? W : Vn;
 #pragma unroll
         for (int q = 0; q < 10; ++q) g[q] = (TV)0;

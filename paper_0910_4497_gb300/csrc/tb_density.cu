@@ -86,7 +86,7 @@ struct MuArgs {
   int* st;
 };
 
-constexpr int MU_NPT = 16;     // trial points per coarse pass
+constexpr int MU_NPT = 32;     // trial points per coarse pass (FP32 partials: MU_PART doubles)
 constexpr int MU_PART = 16;    // partial slots per block and generation
 
 __device__ __forceinline__ double pair_weight(const double* S, int NT, long long q) {
@@ -176,6 +176,52 @@ __device__ bool grid_allreduce(const double (&v)[M], const MuArgs& a, unsigned& 
   return true;
 }
 
+// Block then grid sum of the MU_NPT FP32 counts of a coarse pass (the counts
+// only have to fall on the right side of N_e; the Newton phase re-counts the
+// bracket ends in FP64).  The partials are floats in the blocks' MU_PART
+// double slots; 8 threads per value stride over the blocks in a fixed order.
+// Returns false on barrier timeout.
+__device__ bool grid_allreduce_f32(const float (&v)[MU_NPT], const MuArgs& a, unsigned& gen,
+                                   float* redf, float* totf, int* sflag) {
+  static_assert(MU_NPT == 32 && MU_NPT * sizeof(float) == MU_PART * sizeof(double) && MT == 256,
+                "layout of the coarse partials");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
+#pragma unroll
+  for (int ch = 0; ch < MU_NPT / 16; ++ch) {
+    float p[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) p[q] = v[ch * 16 + q];
+    const float t = tbk::warp_reduce16(p, lane);
+    if ((lane & 1) == 0) redf[warp * MU_NPT + ch * 16 + (lane >> 1)] = t;
+  }
+  __syncthreads();
+  float* pg = reinterpret_cast<float*>(a.part + (size_t)(gen & 1) * G * MU_PART);
+  if (threadIdx.x < MU_NPT) {
+    float s0 = 0.f;
+    for (int w = 0; w < MT / 32; ++w) s0 += redf[w * MU_NPT + threadIdx.x];
+    pg[blockIdx.x * MU_NPT + threadIdx.x] = s0;
+  }
+  ++gen;
+  if (!grid_barrier(a.bar, gen * G, a.timeout, a.st, sflag)) return false;
+  {
+    const int m = threadIdx.x >> 3, sub = threadIdx.x & 7;
+    float sum = 0.f;
+    int g = sub;
+    for (; g + 7 * 8 < G; g += 8 * 8) {
+      float t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = pg[(g + u * 8) * MU_NPT + m];
+      sum += ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
+    }
+    for (; g < G; g += 8) sum += pg[g * MU_NPT + m];
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (sub == 0) totf[m] = sum;
+  }
+  __syncthreads();
+  return true;
+}
+
 __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
   extern __shared__ __align__(16) unsigned char mu_smem[];
   double2* pairs = reinterpret_cast<double2*>(mu_smem);   // (lambda, w)
@@ -184,6 +230,8 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
   __shared__ int wtot[MT / 32];
   __shared__ double red[MT / 32 * 16];
   __shared__ double tot[16];
+  __shared__ float redf[MT / 32 * MU_NPT];
+  __shared__ float totf[MU_NPT];
   __shared__ int sflag;
   const int G = gridDim.x;
   const double ikT = 1.0 / a.kT;
@@ -265,9 +313,10 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
   const double lo0 = tot[0] - 40.0 * a.kT, hi0 = tot[1] + 40.0 * a.kT;
   double lo = lo0, hi = hi0;
   int iters = 0;
-  // ---- coarse bracketing with FP32 occupations at MU_NPT points per pass
-  for (int pass = 0; pass < 6 && hi - lo > 0.01; ++pass) {
-    double v[MU_NPT];
+  // ---- coarse bracketing with FP32 occupations at MU_NPT points per pass, to
+  // a bracket of 0.05 eV; the counts at its ends give Newton's first point
+  double nlo_cnt = -1.0, nhi_cnt = -1.0;     // counts at lo / hi (unknown: < 0)
+  for (int pass = 0; pass < 6 && hi - lo > 0.05; ++pass) {
     float cnt[MU_NPT];
     const double h = (hi - lo) / (MU_NPT + 1);
 #pragma unroll
@@ -285,13 +334,13 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
         cnt[u] += __fdividef(wf, 1.f + __expf(x));
       }
     }
-#pragma unroll
-    for (int u = 0; u < MU_NPT; ++u) v[u] = (double)cnt[u];
-    if (!grid_allreduce<MU_NPT>(v, a, gen, red, tot, &sflag)) return;
+    if (!grid_allreduce_f32(cnt, a, gen, redf, totf, &sflag)) return;
     int jfirst = MU_NPT;            // first trial point with N > N_e (N increases with mu)
-    for (int u = MU_NPT - 1; u >= 0; --u) if (2.0 * tot[u] > a.ne) jfirst = u;
+    for (int u = MU_NPT - 1; u >= 0; --u) if (2.0 * (double)totf[u] > a.ne) jfirst = u;
     const double nlo = jfirst == 0 ? lo : lo + jfirst * h;
     const double nhi = jfirst == MU_NPT ? hi : lo + (jfirst + 1) * h;
+    if (jfirst > 0) nlo_cnt = 2.0 * (double)totf[jfirst - 1];
+    if (jfirst < MU_NPT) nhi_cnt = 2.0 * (double)totf[jfirst];
     lo = nlo;
     hi = nhi;
     ++iters;
@@ -301,6 +350,10 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
   // is within rounding of N_e) and widens the bracket on a side that fails.
   const bool check = lo > lo0 || hi < hi0;
   double mu = 0.5 * (lo + hi);
+  if (nlo_cnt >= 0.0 && nhi_cnt > nlo_cnt) {     // linear interpolation of the counts
+    const double fr = (a.ne - nlo_cnt) / (nhi_cnt - nlo_cnt);
+    if (fr > 0.0 && fr < 1.0) mu = lo + fr * (hi - lo);
+  }
   if (a.guess) {
     const double g = *a.guess;
     if (isfinite(g) && g > lo && g < hi) mu = g;

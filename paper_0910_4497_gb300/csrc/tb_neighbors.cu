@@ -224,9 +224,11 @@ nbr_cell_kernel(int n, const double* __restrict__ pos, const float4* __restrict_
                 int max_h, int max_c, int* st) {
   extern __shared__ int nb_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int* cand_c = nb_smem + warp * (2 * capc + 64);
+  int* cand_c = nb_smem + warp * (2 * capc + 64 + 64);
   int* cand_h = cand_c + capc;
   int* stg = cand_h + 64;                              // capc staged candidates
+  int* cex = stg + capc;                               // 32: start of each cell's candidates
+  int* cbg = cex + 32;                                 // 32: its first index in cell_atoms
   const int i = blockIdx.x * NB_WARPS + warp;
   if (i >= n) return;
   const float Lf = (float)L, invLf = (float)(1.0 / L);
@@ -265,30 +267,59 @@ nbr_cell_kernel(int n, const double* __restrict__ pos, const float4* __restrict_
     __syncwarp();
     nstg = 0;
   };
-  for (int q = 0; q < 27; ++q) {
-    const int ox = q / 9 - 1, oy = (q / 3) % 3 - 1, oz = q % 3 - 1;
-    const int c2 = (((cx + ox + nc) % nc) * nc + (cy + oy + nc) % nc) * nc + (cz + oz + nc) % nc;
-    const int b0 = cell_off[c2], b1 = cell_off[c2 + 1];
-    for (int b = b0; b < b1; b += 32) {
-      const int bb = b + lane;
-      bool pass = false;
-      int j = -1;
-      if (bb < b1) {
-        j = cell_atoms[bb];
-        if (j != i) {
-          const float4 pj = posf[j];
-          float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-          dx -= Lf * rintf(dx * invLf);
-          dy -= Lf * rintf(dy * invLf);
-          dz -= Lf * rintf(dz * invLf);
-          const float r2f = dx * dx + dy * dy + dz * dz;
-          pass = r2f <= Rc_pre2 || r2f <= Rh_pre2;
-        }
+  // the 27 cells' ranges in one round of loads (lane q: cell q), their
+  // candidates numbered by an exclusive scan; each lane finds the cell of its
+  // candidate by binary search, two batches of 32 in flight
+  {
+    int cb = 0, cn = 0;
+    if (lane < 27) {
+      const int ox = lane / 9 - 1, oy = (lane / 3) % 3 - 1, oz = lane % 3 - 1;
+      const int c2 = (((cx + ox + nc) % nc) * nc + (cy + oy + nc) % nc) * nc + (cz + oz + nc) % nc;
+      cb = cell_off[c2];
+      cn = cell_off[c2 + 1] - cb;
+    }
+    int incl = cn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    cex[lane] = incl - cn;
+    cbg[lane] = cb;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();
+    auto candidate = [&](int x, int& j, bool& pass) {
+      j = -1;
+      pass = false;
+      if (x >= total) return;
+      int lo = 0, hi = 26;                       // last cell q with cex[q] <= x
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cex[mid] <= x) lo = mid; else hi = mid - 1;
       }
-      const unsigned bp = __ballot_sync(0xffffffffu, pass);
-      if (nstg + __popc(bp) > capc) flush();           // keep the stage within capacity
-      if (pass) stg[nstg + __popc(bp & below)] = j;
-      nstg += __popc(bp);
+      j = cell_atoms[cbg[lo] + (x - cex[lo])];
+      if (j == i) return;
+      const float4 pj = posf[j];
+      float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+      dx -= Lf * rintf(dx * invLf);
+      dy -= Lf * rintf(dy * invLf);
+      dz -= Lf * rintf(dz * invLf);
+      const float r2f = dx * dx + dy * dy + dz * dz;
+      pass = r2f <= Rc_pre2 || r2f <= Rh_pre2;
+    };
+    for (int b = 0; b < total; b += 64) {
+      int j0, j1;
+      bool p0, p1;
+      candidate(b + lane, j0, p0);
+      candidate(b + 32 + lane, j1, p1);
+      const unsigned bp0 = __ballot_sync(0xffffffffu, p0);
+      if (nstg + __popc(bp0) > capc) flush();          // keep the stage within capacity
+      if (p0) stg[nstg + __popc(bp0 & below)] = j0;
+      nstg += __popc(bp0);
+      const unsigned bp1 = __ballot_sync(0xffffffffu, p1);
+      if (nstg + __popc(bp1) > capc) flush();
+      if (p1) stg[nstg + __popc(bp1 & below)] = j1;
+      nstg += __popc(bp1);
     }
   }
   flush();
@@ -356,7 +387,7 @@ tb_status launch_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h
   int nc = (int)(L / (p.Rc + 0.01));
   while (nc >= 3 && (size_t)nc * nc * nc > neighbor_cell_capacity(c->reserved_n)) --nc;
   const int capc = p.max_cluster <= 128 ? 128 : (p.max_cluster <= 256 ? 256 : 512);
-  const size_t cell_smem = (size_t)NB_WARPS * (2 * capc + 64) * sizeof(int);
+  const size_t cell_smem = (size_t)NB_WARPS * (2 * capc + 64 + 64) * sizeof(int);
   if (nc >= 3 && p.max_cluster <= 512) {
     const int ncell = nc * nc * nc;
     TB_CUDA_TRY(cudaMemsetAsync(c->cell_cnt, 0, sizeof(int) * ncell, s));

@@ -106,6 +106,29 @@ __device__ __forceinline__ void block_sum16(const T (&v)[M], T* red, T* out) {
   __syncthreads();
 }
 
+// The same reduction with the totals formed by every thread (NW warps): no
+// second barrier and no broadcast; the partial sums are added in warp order,
+// as in block_sum16, so every thread gets the bits block_sum16 would give.
+// `red` must not be written again before every thread has read it.
+template <typename T, int M, int NW>
+__device__ __forceinline__ void block_sum_all(const T (&v)[M], T* red, T (&out)[M]) {
+  static_assert(M <= 16, "at most 16 values");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T p[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) p[q] = q < M ? v[q] : T(0);
+  const T t = warp_reduce16(p, lane);
+  if ((lane & 1) == 0 && (lane >> 1) < M) red[warp * 16 + (lane >> 1)] = t;
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    T s = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) s += red[w * 16 + q];
+    out[q] = s;
+  }
+}
+
 }  // namespace tbk
 
 struct tb_ctx {

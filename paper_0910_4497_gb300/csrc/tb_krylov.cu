@@ -99,13 +99,13 @@ __host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, int max
   b += align32(sizeof(int) * (max_cluster + 1));      // entries per slot
   b += align32(sizeof(TV) * Dmax * 4);                // W
   if (vsmem) b += align32(sizeof(TV) * Dmax * 4 * r); // basis
-  else b += align32(sizeof(TV) * Dmax * 4);          // copy of the current block
+  else b += align32(sizeof(TV) * Dmax * 4 * (sizeof(TV) == 4 ? 2 : 1));  // V_k (FP32: and V_{k-1})
   if (lsmem) b += align32(sizeof(int2) * (size_t)lent_smem_cap(max_cluster, max_hnbr));  // local CSR
   b += align32(sizeof(TV) * 16 * np);                 // projection partials
   b += align32(sizeof(TV) * 16 * r);                  // projection coefficients
   b += align32(sizeof(TV) * 16 * 4);                  // B_{k-1}, Gram, R, R^{-1}
   b += align32(sizeof(double) * 16 * 2);              // B_k, first Cholesky factor
-  b += align32(sizeof(TV) * 16 * KW_MAX);             // reduction scratch
+  b += align32(sizeof(TV) * 16 * KW_MAX * 2);         // reduction scratch (two buffers)
   b += align32(sizeof(int) * 16);                     // flags
   return b;
 }
@@ -125,15 +125,23 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
   int* cl = reinterpret_cast<int*>(smem + off);      off += align32(sizeof(int) * a.max_cluster);
   int* cnt = reinterpret_cast<int*>(smem + off);     off += align32(sizeof(int) * (a.max_cluster + 1));
   TV* W = reinterpret_cast<TV*>(smem + off);         off += align32(sizeof(TV) * Dmax * 4);
+  // FP32 with the basis in global memory (DB): V_k and V_{k-1} double-buffered
+  // in shared memory, written there by the step that produces them (no staging
+  // pass and no L2 round trip for the blocks every step projects out; the
+  // global slot keeps every block for the full reorthogonalisations and the Y
+  // rows).  FP32 (RED): the Gram partials summed and the 4x4 factors formed by
+  // every thread, B_k published by thread 0 with the step's closing barrier.
+  constexpr bool DB = !VSMEM && sizeof(TV) == 4;
+  constexpr bool RED = sizeof(TV) == 4;
   TV* V;
-  TV* Vks = nullptr;                                 // copy of the current block (global basis)
+  TV* Vks = nullptr;                                 // shared copies of V_k (and V_{k-1})
   if (VSMEM) {
     V = reinterpret_cast<TV*>(smem + off);
     off += align32(sizeof(TV) * (size_t)Dmax * 4 * r);
   } else {
     V = a.Vg + (size_t)blockIdx.x * Dmax * 4 * r;
     Vks = reinterpret_cast<TV*>(smem + off);
-    off += align32(sizeof(TV) * (size_t)Dmax * 4);
+    off += align32(sizeof(TV) * (size_t)Dmax * 4 * (DB ? 2 : 1));
   }
   int2* const lent_g = a.lent + (size_t)blockIdx.x * a.max_cluster * a.max_hnbr;   // local CSR
   int2* lent_s = nullptr;
@@ -149,7 +157,7 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
   TV* Rish = Rsh + 16;                               off += align32(sizeof(TV) * 64);
   double* Bs = reinterpret_cast<double*>(smem + off);
   double* R1s = Bs + 16;                             off += align32(sizeof(double) * 32);
-  TV* red = reinterpret_cast<TV*>(smem + off);       off += align32(sizeof(TV) * 16 * KW_MAX);
+  TV* red = reinterpret_cast<TV*>(smem + off);       off += align32(sizeof(TV) * 16 * KW_MAX * 2);
   int* flags = reinterpret_cast<int*>(smem + off);
   const TV Es = (TV)a.Es, Ep = (TV)a.Ep;
   // Cholesky-QR acceptance: each pivot must keep this fraction of its diagonal
@@ -181,11 +189,14 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
       return;
     }
     __syncthreads();
-    // ---- local sparsity of H_c in one pass: slot s keeps its in-cluster
-    // neighbours (local slot, global bond) at s * ls .. s * ls + cnt[s] - 1,
-    // ls = 16 in shared memory; a slot with more (none in carbon within 2.6 A)
-    // sends the target to its CTA's global slot with ls = max_hnbr
-    int ls = lent_s ? a.lent_cap / a.max_cluster : a.max_hnbr;
+    // ---- local sparsity of H_c in one pass: entry e < cnt[s] of slot s (an
+    // in-cluster neighbour: local slot, global bond) at e * max_cluster + s,
+    // entry-major so that the consecutive slots of a warp read consecutive
+    // words; up to ls = 16 entries per slot in shared memory; a slot with more
+    // (none in carbon within 2.6 A) sends the target to its CTA's global slot
+    // with ls = max_hnbr
+    const int MC = a.max_cluster;
+    int ls = lent_s ? a.lent_cap / MC : a.max_hnbr;
     int2* lent = lent_s ? lent_s : lent_g;
     for (int pass = 0; pass < 2; ++pass) {
       if (tid == 0) flags[FL_OK] = 0;
@@ -197,7 +208,7 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
         for (int p = a.h_off[at]; p < pe; ++p) {
           const int t = find_slot(cl, nc, a.h_idx[p]);
           if (t >= 0) {
-            if (e < ls) lent[s * ls + e] = make_int2(t, p);
+            if (e < ls) lent[e * MC + s] = make_int2(t, p);
             ++e;
           }
         }
@@ -215,7 +226,9 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
     const int D = 4 * nc;
     for (int q = tid; q < D * 4; q += KT) {
       const int row = q >> 2, c = q & 3;
-      V[q] = (row == c) ? (TV)1 : (TV)0;
+      const TV e = (row == c) ? (TV)1 : (TV)0;
+      V[q] = e;
+      if constexpr (DB) Vks[q] = e;
     }
     if (tid < 16) Bp[tid] = (TV)0;
     if (tid == 0) { flags[FL_MASK] = 0xF; flags[FL_MASK + 1] = 0; flags[FL_ACT] = 0xF; }
@@ -226,11 +239,17 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
     for (int k = 0; k < r; ++k) {
       const TV* Vk = V + (size_t)k * Dmax * 4;
       const TV* Vp = V + (size_t)(k > 0 ? k - 1 : 0) * Dmax * 4;
-      if constexpr (!VSMEM) {            // the sweep reads V_k rows many times: stage it
+      if constexpr (DB) {
+        Vk = Vks + (size_t)(k & 1) * Dmax * 4;
+        Vp = Vks + (size_t)((k + 1) & 1) * Dmax * 4;
+      } else if constexpr (!VSMEM) {     // the sweep reads V_k rows many times: stage it
         for (int q = tid; q < D; q += KT) st4(Vks + q * 4, ld4(Vk + q * 4));
         __syncthreads();
         Vk = Vks;
       }
+      // blocks b >= bsm are read from the shared-memory copies (V_k; V_{k-1} too
+      // when double-buffered); with the basis in shared memory, all through V
+      const int bsm = DB ? k - 1 : (VSMEM ? k + 1 : k);
       // ---- W = H_c V_k - V_{k-1} B_{k-1}^T ; item (s, alpha) = one row of W
       for (int it = tid; it < 4 * nc; it += KT) {
         const int s = it >> 2, al = it & 3;
@@ -239,10 +258,10 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
         TV acc[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[c] = on * vs.v[c];
-        const int e1 = s * ls + cnt[s];
+        const int e1 = cnt[s];
 #pragma unroll 4
-        for (int e = s * ls; e < e1; ++e) {
-          const int2 en = lent[e];
+        for (int e = 0; e < e1; ++e) {
+          const int2 en = lent[e * MC + s];
           const vec4<TV> h = ldg4(a.H + (size_t)en.y * 16 + al * 4);
 #pragma unroll
           for (int be = 0; be < 4; ++be) {
@@ -280,23 +299,29 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
         for (int w = warp; w < items; w += KW) {
           const int b = b0 + w / nseg, seg = w % nseg;
           const int rlo = (D * seg) / nseg, rhi = (D * (seg + 1)) / nseg;
-          const TV* Vb = V + (size_t)b * Dmax * 4;
           TV acc[16];
 #pragma unroll
           for (int q = 0; q < 16; ++q) acc[q] = (TV)0;
+          auto rows = [&](const TV* Vb) {
 #pragma unroll 4
-          for (int row = rlo + lane; row < rhi; row += 32) {
-            const vec4<TV> v = ld4(Vb + row * 4);
-            const vec4<TV> x = ld4(W + row * 4);
+            for (int row = rlo + lane; row < rhi; row += 32) {
+              const vec4<TV> v = ld4(Vb + row * 4);
+              const vec4<TV> x = ld4(W + row * 4);
 #pragma unroll
-            for (int ii = 0; ii < 4; ++ii)
+              for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-              for (int c = 0; c < 4; ++c) acc[ii * 4 + c] += v.v[ii] * x.v[c];
-          }
+                for (int c = 0; c < 4; ++c) acc[ii * 4 + c] += v.v[ii] * x.v[c];
+            }
+          };
+          if (b >= bsm) rows((DB && b != k) ? Vp : Vk);
+          else rows(V + (size_t)b * Dmax * 4);
           const TV tot = tbk::warp_reduce16(acc, lane);
           if ((lane & 1) == 0) Cp[w * 16 + (lane >> 1)] = tot;
         }
         __syncthreads();
+        // one sum per coefficient over the row segments, shared (summing the
+        // partials in every thread where they are used costs more shared-memory
+        // traffic than this barrier)
         for (int t = tid; t < nb * 16; t += KT) {
           const int bl = t >> 4, q = t & 15;
           TV sum = (TV)0;
@@ -304,26 +329,32 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
           Cc[(b0 + bl) * 16 + q] = sum;
         }
         __syncthreads();
+        // coefficients of block b0 + bl, row ii
+        auto coef = [&](const int bl, const int ii) -> vec4<TV> {
+          return ld4(Cc + (b0 + bl) * 16 + ii * 4);
+        };
         if (pass == 0 && tid < 16) {
           const int ii = tid >> 2, c = tid & 3;
-          Ti[(4 * k + ii) * NT + 4 * k + c] =
-              0.5 * ((double)Cc[k * 16 + ii * 4 + c] + (double)Cc[k * 16 + c * 4 + ii]);
+          const vec4<TV> x1 = coef(k - b0, ii), x2 = coef(k - b0, c);
+          Ti[(4 * k + ii) * NT + 4 * k + c] = 0.5 * ((double)x1.v[c] + (double)x2.v[ii]);
         }
         if (k == r - 1) break;
         const bool last = pass == passes - 1;
         for (int row = tid; row < D; row += KT) {
           vec4<TV> x = ld4(W + row * 4);
-#pragma unroll 4
-          for (int b = b0; b <= k; ++b) {
-            const vec4<TV> v = ld4(V + (size_t)b * Dmax * 4 + row * 4);
-            const TV* cb = Cc + b * 16;
+          auto sub = [&](const TV* Vb, const int bl) {
+            const vec4<TV> v = ld4(Vb + row * 4);
 #pragma unroll
             for (int ii = 0; ii < 4; ++ii) {
-              const vec4<TV> crow = ld4(cb + ii * 4);
+              const vec4<TV> crow = coef(bl, ii);
 #pragma unroll
               for (int c = 0; c < 4; ++c) x.v[c] -= v.v[ii] * crow.v[c];
             }
-          }
+          };
+#pragma unroll 4
+          for (int b = b0; b < bsm; ++b) sub(V + (size_t)b * Dmax * 4, b - b0);
+          if (DB && k - 1 >= b0) sub(Vp, k - 1 - b0);
+          if (!VSMEM) sub(Vk, k - b0);
           st4(W + row * 4, x);
           if (last) {                       // Gram matrix of the orthogonalised W
             int q = 0;
@@ -340,15 +371,87 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
       // the first factor shows a well-conditioned block); the MGS path
       // takes over when a pivot signals ill-conditioning or deflation.
       TV* Vn = V + (size_t)(k + 1) * Dmax * 4;
+      // the shared-memory copy of V_{k+1} takes the buffer V_{k-1} leaves
+      TV* Vns = DB ? Vks + (size_t)((k + 1) & 1) * Dmax * 4 : nullptr;
       int chol_state = 0;   // 1: first factor refused (W untouched); 2: second refused
+      int act = 0xF;
+      if constexpr (RED) {
+        // FP32: every thread reduces the Gram partials and factors the (same)
+        // Gram matrix itself, so R and R^{-1} are identical everywhere with no
+        // broadcast; thread 0 forms B_k and publishes it with T before the
+        // step's closing barrier
+        TV R[16];
+        bool single = false;
+        for (int cq = 0; cq < 2; ++cq) {
+          TV gs[10];
+          tbk::block_sum_all<TV, 10, KW>(g, red + cq * 16 * KW_MAX, gs);
+          TV G[16], Ri[16];
+          int q = 0;
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int e = c; e < 4; ++e) { G[c * 4 + e] = gs[q]; G[e * 4 + c] = gs[q]; ++q; }
+          bool well;
+          const bool ok = chol4(G, R, chol_rel, cq == 0 ? chol_abs : 0.0, well);
+          triinv4(R, Ri);
+          if (!ok) {                        // uniform: every thread factors the same matrix
+            chol_state = cq + 1;
+            break;
+          }
+          single = cq == 0 && well;         // a well-conditioned block needs no second pass
+          const bool to_w = cq == 0 && !single;
+#pragma unroll
+          for (int q2 = 0; q2 < 10; ++q2) g[q2] = (TV)0;
+          for (int row = tid; row < D; row += KT) {
+            const vec4<TV> x = ld4(W + row * 4);
+            vec4<TV> y;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              TV t = (TV)0;
+#pragma unroll
+              for (int j = 0; j <= c; ++j) t += x.v[j] * Ri[j * 4 + c];
+              y.v[c] = t;
+            }
+            if (to_w) {                     // Gram matrix for the second factor
+              st4(W + row * 4, y);
+              int q3 = 0;
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int e = c; e < 4; ++e) g[q3++] += y.v[c] * y.v[e];
+            } else {
+              st4(Vn + row * 4, y);
+              if constexpr (DB) st4(Vns + row * 4, y);
+            }
+          }
+          if (!to_w) break;
+          if (tid == 0) {
+#pragma unroll
+            for (int q2 = 0; q2 < 16; ++q2) R1s[q2] = (double)R[q2];
+          }
+        }
+        if (chol_state == 0 && tid == 0) {
+          if (single) {
+#pragma unroll
+            for (int q2 = 0; q2 < 16; ++q2) Bs[q2] = (double)R[q2];
+          } else {
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr)          // B_k = R2 R1
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                double t = 0.0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) t += (double)R[rr * 4 + j] * R1s[j * 4 + c];
+                Bs[rr * 4 + c] = t;
+              }
+          }
+        }
+      } else {
       for (int cq = 0; cq < 2; ++cq) {
         tbk::block_sum16<TV, 10>(g, red, Gs);
-        // FP32: every thread factors the (same) Gram matrix itself, identical R
-        // and R^{-1} everywhere with no broadcast and no barrier; FP64 (a slow
-        // pipe shared by the whole SM): one thread factors and publishes
+        // FP64 (a slow pipe shared by the whole SM): one thread factors and publishes
         TV R[16], Ri[16];
-        int okf;
-        if (sizeof(TV) == 4 || tid == 0) {
+        if (tid == 0) {
           TV G[16];
           int q = 0;
 #pragma unroll
@@ -358,26 +461,19 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
           bool well;
           const bool ok = chol4(G, R, chol_rel, cq == 0 ? chol_abs : 0.0, well);
           triinv4(R, Ri);
-          // FP32 path: a well-conditioned block needs no second pass
-          okf = ok ? ((cq == 0 && well && sizeof(TV) == 4) ? 2 : 1) : 0;
-          if (sizeof(TV) != 4) {
 #pragma unroll
-            for (int q2 = 0; q2 < 16; ++q2) { Rsh[q2] = R[q2]; Rish[q2] = Ri[q2]; }
-            flags[FL_OK] = okf;
-          }
+          for (int q2 = 0; q2 < 16; ++q2) { Rsh[q2] = R[q2]; Rish[q2] = Ri[q2]; }
+          flags[FL_OK] = ok ? 1 : 0;
         }
-        if (sizeof(TV) != 4) {
-          __syncthreads();
-          okf = flags[FL_OK];
+        __syncthreads();
+        const int okf = flags[FL_OK];
 #pragma unroll
-          for (int q2 = 0; q2 < 16; ++q2) { R[q2] = Rsh[q2]; Ri[q2] = Rish[q2]; }
-        }
-        if (!okf) {                 // uniform: every thread factors the same matrix
+        for (int q2 = 0; q2 < 16; ++q2) { R[q2] = Rsh[q2]; Ri[q2] = Rish[q2]; }
+        if (!okf) {                 // uniform: read after the barrier
           chol_state = cq + 1;
           break;
         }
-        const bool single = okf == 2;
-        TV* dst = (cq == 0 && !single) ? W : Vn;
+        TV* dst = cq == 0 ? W : Vn;
 #pragma unroll
         for (int q = 0; q < 10; ++q) g[q] = (TV)0;
         for (int row = tid; row < D; row += KT) {
@@ -391,22 +487,13 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
             y.v[c] = t;
           }
           st4(dst + row * 4, y);
-          if (cq == 0 && !single) {         // Gram matrix for the second factor
+          if (cq == 0) {                    // Gram matrix for the second factor
             int q = 0;
 #pragma unroll
             for (int c = 0; c < 4; ++c)
 #pragma unroll
               for (int e = c; e < 4; ++e) g[q++] += y.v[c] * y.v[e];
           }
-        }
-        if (single) {                       // B_k = R1, done
-          if (tid == 0) {
-#pragma unroll
-            for (int q = 0; q < 16; ++q) Bs[q] = (double)R[q];
-            flags[FL_ACT] = 0xF;
-          }
-          __syncthreads();
-          break;
         }
         if (tid == 0) {
           if (cq == 0) {
@@ -422,17 +509,16 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
                 for (int j = 0; j < 4; ++j) t += (double)R[rr * 4 + j] * R1s[j * 4 + c];
                 Bs[rr * 4 + c] = t;
               }
-            flags[FL_ACT] = 0xF;
           }
         }
-        if (cq == 1) __syncthreads();       // cq == 0: the next reduction synchronises
+      }
       }
       if (chol_state != 0) {
         if (warp == 0) {
           double R[16];
 #pragma unroll
           for (int q = 0; q < 16; ++q) R[q] = 0.0;
-          int act = 0;
+          int mact = 0;
           bool nonfinite = false;
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
@@ -467,10 +553,13 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
               const TV inv = (TV)(1.0 / nrm);
               for (int row = lane; row < D; row += 32) Vn[row * 4 + c] = W[row * 4 + c] * inv;
               R[c * 4 + c] = nrm;
-              act |= 1 << c;
+              mact |= 1 << c;
             } else {
               for (int row = lane; row < D; row += 32) Vn[row * 4 + c] = (TV)0;
             }
+          }
+          if constexpr (DB) {               // each lane copies the rows it wrote
+            for (int row = lane; row < D; row += 32) st4(Vns + row * 4, ld4(Vn + row * 4));
           }
           if (lane == 0) {
             if (chol_state == 2) {      // W was already W R1^{-1}: B_k = R_mgs R1
@@ -487,14 +576,14 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
 #pragma unroll
               for (int q = 0; q < 16; ++q) Bs[q] = R[q];
             }
-            flags[FL_ACT] = act;
+            flags[FL_ACT] = mact;
             if (nonfinite) tbk::set_status(a.st, TB_ERR_NONFINITE, i);
           }
         }
         __syncthreads();
+        act = flags[FL_ACT];
       }
       if (tid == 0) {
-        const int act = flags[FL_ACT];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
@@ -509,11 +598,12 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
         flags[FL_MASK] = (int)(mask & 0xffffffffull);
         flags[FL_MASK + 1] = (int)(mask >> 32);
         if (!isfinite(Bs[0] + Bs[5] + Bs[10] + Bs[15])) tbk::set_status(a.st, TB_ERR_NONFINITE, i);
+        // B_k for the next sweep (published by the barrier below)
+#pragma unroll
+        for (int q = 0; q < 16; ++q) Bp[q] = (TV)Bs[q];
       }
-      if (tid < 16) Bp[tid] = (TV)Bs[tid];
       __syncthreads();
-      const int act_now = flags[FL_ACT];
-      if (act_now == 0) break;
+      if (act == 0) break;
       nblocks = k + 2;
     }
     // ---- outputs: column mask, rows of V for the target and its H neighbours
@@ -528,7 +618,7 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
       for (int q = tid; q < nrows * NT; q += KT) {
         const int rr = q / NT, col = q - rr * NT;
         const int qq = rr >> 2, beta = rr & 3;
-        const int slot = qq == 0 ? 0 : (qq - 1 < rcnt ? lent[qq - 1].x : -1);
+        const int slot = qq == 0 ? 0 : (qq - 1 < rcnt ? lent[(qq - 1) * MC].x : -1);
         const int b = col >> 2, c = col & 3;
         TV val = (TV)0;
         if (b < nblocks && slot >= 0) val = V[(size_t)b * Dmax * 4 + (4 * slot + beta) * 4 + c];

@@ -80,7 +80,7 @@ typedef struct tb_params {
   double mu_tol;      /* mu search stops when |N(mu) - N_e| <= mu_tol * N_e      */
   int r;              /* Krylov block order: basis of r blocks, 4r columns, 1..16 */
   int prec;           /* tb_precision                                            */
-  int max_hnbr;       /* capacity of one Hamiltonian neighbour list, <= 32       */
+  int max_hnbr;       /* capacity of one Hamiltonian neighbour list, <= 256      */
   int max_cluster;    /* capacity of one cluster (target included), <= 1024      */
   int reorth_passes;  /* classical Gram-Schmidt passes against all blocks: 1 or 2*/
   int mu_max_iter;    /* cap on mu search passes (e.g. 100)                      */

@@ -14,7 +14,7 @@ namespace tbk {
 
 constexpr int MAX_R = 16;           // Krylov block order cap -> NT <= 64
 constexpr int MAX_NT = 4 * MAX_R;
-constexpr int MAX_HNBR = 32;        // one warp lane per Hamiltonian neighbour
+constexpr int MAX_HNBR = 256;       // Hamiltonian list capacity (long-range hoppings: ~170 at 7 A)
 constexpr int MAX_CLUSTER = 1024;
 
 // Device status word: [0] = first tb_status code, [1] = qualifying info.

@@ -219,14 +219,14 @@ __global__ void __launch_bounds__(NB_THREADS)
 nbr_cell_kernel(int n, const double* __restrict__ pos, const float4* __restrict__ posf,
                 double L, double R2h, double R2c, float Rh_pre2, float Rc_pre2, int nc,
                 const int* __restrict__ atom_cell, const int* __restrict__ cell_off,
-                const int* __restrict__ cell_atoms, int capc, int* __restrict__ hcnt,
+                const int* __restrict__ cell_atoms, int capc, int caph, int* __restrict__ hcnt,
                 int* __restrict__ ccnt, int* __restrict__ pad_h, int* __restrict__ pad_c,
                 int max_h, int max_c, int* st) {
   extern __shared__ int nb_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int* cand_c = nb_smem + warp * (2 * capc + 64 + 64);
-  int* cand_h = cand_c + capc;
-  int* stg = cand_h + 64;                              // capc staged candidates
+  int* cand_c = nb_smem + warp * (2 * capc + caph + 64);
+  int* cand_h = cand_c + capc;                         // caph Hamiltonian neighbours
+  int* stg = cand_h + caph;                            // capc staged candidates
   int* cex = stg + capc;                               // 32: start of each cell's candidates
   int* cbg = cex + 32;                                 // 32: its first index in cell_atoms
   const int i = blockIdx.x * NB_WARPS + warp;
@@ -259,7 +259,7 @@ nbr_cell_kernel(int n, const double* __restrict__ pos, const float4* __restrict_
       const unsigned bh = __ballot_sync(0xffffffffu, in_h);
       const unsigned bc = __ballot_sync(0xffffffffu, in_c);
       const int ph = nh + __popc(bh & below), pc = ncand + __popc(bc & below);
-      if (in_h && ph < 64) cand_h[ph] = j;
+      if (in_h && ph < caph) cand_h[ph] = j;
       if (in_c && pc < capc) cand_c[pc] = j;
       nh += __popc(bh);
       ncand += __popc(bc);
@@ -324,7 +324,7 @@ nbr_cell_kernel(int n, const double* __restrict__ pos, const float4* __restrict_
   }
   flush();
   // pad to a power of two with INT_MAX, sort ascending
-  const int kc = min(ncand, capc), kh = min(nh, 64);
+  const int kc = min(ncand, capc), kh = min(nh, caph);
   int lc = 1;
   while (lc < kc) lc <<= 1;
   int lh = 1;
@@ -387,7 +387,8 @@ tb_status launch_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h
   int nc = (int)(L / (p.Rc + 0.01));
   while (nc >= 3 && (size_t)nc * nc * nc > neighbor_cell_capacity(c->reserved_n)) --nc;
   const int capc = p.max_cluster <= 128 ? 128 : (p.max_cluster <= 256 ? 256 : 512);
-  const size_t cell_smem = (size_t)NB_WARPS * (2 * capc + 64 + 64) * sizeof(int);
+  const int caph = p.max_hnbr <= 64 ? 64 : (p.max_hnbr <= 128 ? 128 : 256);
+  const size_t cell_smem = (size_t)NB_WARPS * (2 * capc + caph + 64) * sizeof(int);
   if (nc >= 3 && p.max_cluster <= 512) {
     const int ncell = nc * nc * nc;
     TB_CUDA_TRY(cudaMemsetAsync(c->cell_cnt, 0, sizeof(int) * ncell, s));
@@ -398,7 +399,7 @@ tb_status launch_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h
                                                      c->cell_atoms);
     nbr_cell_kernel<<<grid, NB_THREADS, cell_smem, s>>>(
         n, pos, posf, L, R2h, R2c, Rh_pre2, Rc_pre2, nc, c->atom_cell, c->cell_off,
-        c->cell_atoms, capc, c->scan_h, c->scan_c, c->pad_h, c->pad_c, p.max_hnbr,
+        c->cell_atoms, capc, caph, c->scan_h, c->scan_c, c->pad_h, c->pad_c, p.max_hnbr,
         p.max_cluster, c->d_status);
     scan2_kernel<<<1, 1024, 0, s>>>(n, c->scan_h, h_off, c->scan_c, c_off);
     compact_kernel<<<grid, NB_THREADS, 0, s>>>(n, c->pad_h, c->pad_c, p.max_hnbr, p.max_cluster,

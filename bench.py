@@ -22,6 +22,12 @@ steps of 0.5 fs from 2000 K Maxwell-Boltzmann velocities, one CUDA graph per
 step; value = atom-steps/s, with the NVE energy drift of the mixed and FP64
 paths over the same steps from the same state.
 
+--workload npt15360 times NPT molecular dynamics of the same 15360-atom cell at
+the paper's C60 polymerisation conditions (25 GPa, 500 K): each step is one
+velocity-Verlet step, its virial and a weak-coupling (Berendsen) scaling of the
+velocities, positions and box; value = atom-steps/s, with the temperature,
+pressure and box over the timed steps.
+
 --workload autograd1920 times the exact local gradient instead (the
 truncated local free energy at Krylov order r = r_min, whose projected
 problem is the dense cluster eigenproblem, ~392 x 392 per target, with its
@@ -72,8 +78,8 @@ def parse():
     ap.add_argument("--reorth-passes", type=int, default=1)
     ap.add_argument("--reorth-every", type=int, default=4)
     ap.add_argument("--workload", default="c60_1920",
-                    choices=["c60_1920", "longrange1920", "md15360", "autograd1920",
-                             "diamond_eos"])
+                    choices=["c60_1920", "longrange1920", "md15360", "npt15360",
+                             "autograd1920", "diamond_eos"])
     ap.add_argument("--fd-coords", type=int, default=8)
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--group-m", type=int, default=1,
@@ -794,6 +800,150 @@ def run_md(args):
     return 0
 
 
+# ---------------------------------------------------------------- NPT workload
+
+def run_npt(args):
+    """Weak-coupling NPT steps of the 15360-atom cell at 25 GPa and 500 K."""
+    import torch
+    import __graft_entry__
+    from synth import NPT, maxwell_boltzmann_velocities
+    from synth.configs import MASS_C_AMU, GPA_PER_EV_A3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cfg, pos, _, L, p = md_workload()
+    vel = maxwell_boltzmann_velocities(len(pos), NPT["T0_K"], MASS_C_AMU, cfg["seed"] + 1)
+    n = len(pos)
+    dt = NPT["dt_fs"]
+    P0 = NPT["P0_GPa"] / GPA_PER_EV_A3
+    beta = GPA_PER_EV_A3 / NPT["B_GPa"]
+    coupling = (NPT["T0_K"], P0, NPT["tau_T_fs"], NPT["tau_P_fs"], beta)
+    wl = {"workload": NPT["name"], "n_atoms": n, "a": cfg["a"], "ncell": cfg["ncell"],
+          "Rc": cfg["Rc"], "krylov_r": cfg["r"], "kT": cfg["kT"], "dt_fs": dt,
+          "T0_K": NPT["T0_K"], "P0_GPa": NPT["P0_GPa"], "tau_T_fs": NPT["tau_T_fs"],
+          "tau_P_fs": NPT["tau_P_fs"], "barostat_B_GPa": NPT["B_GPa"],
+          "coupling": "Berendsen thermostat + isotropic Berendsen barostat"}
+    if args.impl == "reference" and rank != 0:
+        return 0
+    if args.impl == "reference" or (rank == 0 and not args.no_cpu_baseline):
+        t_tgt, nt = oracle_md_sample(pos, L, p, 64)
+        cpu_base = {"value": 1.0 / t_tgt, "unit": MD_UNIT, "cores": 1, "kind": "oracle",
+                    "sample": f"oracle per-target work of {nt} evenly spaced targets, scaled "
+                              f"to one {n}-atom force evaluation per NPT step"}
+    else:
+        cpu_base = None
+    if args.impl == "reference":
+        v = cpu_base["value"]
+        line = {"metric": MD_METRIC, "value": v, "unit": MD_UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n / v,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": dict(wl, l2="n/a (CPU)"), "cpu_baseline": cpu_base,
+                "e2e": {"value": v, "unit": MD_UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+    if world > 1:
+        import torch.distributed as dist
+        if rank == 0:
+            __graft_entry__.build()
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        dist.barrier()
+        if rank != 0:
+            __graft_entry__.build()
+    else:
+        __graft_entry__.build()
+        torch.cuda.set_device(local)
+    import paper_0910_4497_gb300 as tb
+    p["reorth_passes"] = args.reorth_passes
+    p["reorth_every"] = args.reorth_every
+    dev = torch.device("cuda", local)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    s = tb.TBSystem(n, L, p, prec=args.prec, device=dev)
+    s.set_positions(pos)
+    s.vel.copy_(torch.as_tensor(vel, dtype=torch.float64))
+    s.evaluate()
+    for _ in range(max(args.warmup, 3)):
+        s.npt_step(dt, MASS_C_AMU, *coupling)
+    torch.cuda.synchronize(dev)
+    s.check()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    traj = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        s.npt_step(dt, MASS_C_AMU, *coupling)       # ends with a read of the new box
+        ev[k][1].record(stream)
+        ev[k][1].synchronize()
+        traj.append([s.L] + s.npt_state.cpu().tolist())
+    barrier()
+    clk = clocks.stop() if clocks else None
+    s.check()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    value = job_throughput(n, world, args.steps, total_ms)
+
+    # ---- end to end: the state goes host -> device and back every step
+    hp = [t.cpu().pin_memory() for t in (s.pos, s.vel, s.F)]
+    hE = torch.empty(8, dtype=torch.float64).pin_memory()
+    e2e_ms = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0.record(stream)
+        for d, h in zip((s.pos, s.vel, s.F), hp):
+            d.copy_(h, non_blocking=True)
+        s.npt_step(dt, MASS_C_AMU, *coupling)
+        for d, h in zip((s.pos, s.vel, s.F), hp):
+            h.copy_(d, non_blocking=True)
+        hE.copy_(s.energies, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    launches_per_step = tb.binding.tb_ctx_kernels_per_evaluation(s.ctx, n, L) + 5
+    s.close()
+    if rank == 0:
+        tr = traj
+        line = {
+            "metric": MD_METRIC, "value": value, "unit": MD_UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.prec == "mixed" else "f64", "data": "synthetic",
+            "config": dict(wl, precision=args.prec, l2="flushed between steps (256 MB write)",
+                           parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                           graph="none (the box changes every step; eager launches)",
+                           reorth_passes=args.reorth_passes, reorth_every=args.reorth_every),
+            "e2e": {"value": job_throughput(n, world, args.steps, e2e_ms), "unit": MD_UNIT,
+                    "h2d_bytes_per_step": 3 * n * 3 * 8,
+                    "d2h_bytes_per_step": 3 * n * 3 * 8 + 8 * 8 + 8},
+            "cpu_baseline": cpu_base,
+            "clocks": clk,
+            "gpu_launches": launches_per_step * args.steps,
+            "npt": {"L_A": [tr[0][0], tr[-1][0]], "T_K": [tr[0][1], tr[-1][1]],
+                    "P_GPa": [tr[0][2] * GPA_PER_EV_A3, tr[-1][2] * GPA_PER_EV_A3],
+                    "lambda_last": tr[-1][3], "mu_last": tr[-1][4],
+                    "duration_3ps_s_at_this_rate": NPT["duration_ps"] * 1e3 / dt
+                    * (total_ms / args.steps) / 1e3},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 # ---------------------------------------------------------------- exact local gradient
 
 AG_METRIC = "atom force evals/s (exact local gradient at r = r_min, forward + backward, 1 GB300)"
@@ -1259,6 +1409,8 @@ def main():
         return run_eos(args)
     if args.workload == "md15360":
         return run_md(args)
+    if args.workload == "npt15360":
+        return run_npt(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -336,6 +336,33 @@ tb_status tb_virial(tb_ctx* ctx, int n, const double* pos, double L, const int* 
                     const int* h_idx, double* W, double* pressure, void* stream);
 
 /*
+ * f4. Weak-coupling (Berendsen) NPT for the C60 polymerisation runs of Sec. 4
+ * (MD at 25 GPa and 500 K; the paper names neither thermostat nor barostat).
+ * Call after tb_md_step (box L) and tb_virial on that step's bonds, on the same
+ * stream; with the step's kinetic energy KE = energies[7] and virial W:
+ *   T = 2 KE / (k_B (3n - 3)),  P = (tr W + 2 KE) / (3 L^3),
+ *   lambda = sqrt(1 + (dt/tau_T) (T0/T - 1))   (lambda = 1 when T = 0),
+ *   mu = [1 - beta (dt/tau_P) (P0 - P)]^(1/3),
+ *   v <- lambda v;  x <- mu x (kept in [0, mu L));  L <- mu L.
+ * so the rescaled temperature is T + (dt/tau_T)(T0 - T) and the volume changes
+ * by -beta (dt/tau_P)(P0 - P) relative.  The next tb_md_step takes the box
+ * *L_new (copy it to the host) and the forces F of the unscaled configuration
+ * for its first half kick (the usual weak-coupling approximation; |mu - 1| is
+ * ~1e-5 per step).
+ * pos, vel [n*3] in/out (device, FP64); W [9], energies [8] in (device);
+ * L_new [1] out (device); state [4] out (device): T (K), P (eV/A^3), lambda, mu.
+ * T0 >= 0 (K); P0 (eV/A^3; 1 GPa = 1/160.21766 eV/A^3); dt_fs < tau_T_fs,
+ * dt_fs < tau_P_fs (fs); beta > 0 (A^3/eV, the barostat's compressibility).
+ * Returns TB_ERR_INVALID_ARG for arguments outside these ranges.  On the
+ * device, a factor that is not a positive finite number leaves pos, vel and
+ * the box unchanged and sets TB_ERR_NONFINITE.  Capturable.
+ */
+tb_status tb_npt_berendsen(tb_ctx* ctx, int n, double* pos, double* vel, double L,
+                           const double* W, const double* energies, double T0, double P0,
+                           double dt_fs, double tau_T_fs, double tau_P_fs, double beta,
+                           double* L_new, double* state, void* stream);
+
+/*
  * a11. Exact gradient of the truncated local free energy (differentiable form
  * of the method).  Sec. 3: once the Krylov order reaches the minimal-polynomial
  * degree (r = r_min) the block Krylov space of a target is invariant and its

@@ -26,7 +26,7 @@ EXPORTS = ["tb_params_default", "tb_ctx_create", "tb_ctx_destroy", "tb_ctx_reser
            "tb_profile_enable", "tb_profile_read", "tb_find_mu_static",
            "tb_virial", "tb_ctx_reserve_local", "tb_local_forward", "tb_local_gradient",
            "tb_group_atoms", "tb_krylov_density_grouped", "tb_ctx_kernels_per_evaluation",
-           "tb_version"]
+           "tb_npt_berendsen", "tb_version"]
 
 
 class TBParams(ctypes.Structure):
@@ -72,6 +72,7 @@ def load_library(path=LIB_PATH):
         "tb_profile_read": [P, ctypes.POINTER(ctypes.c_float)],
         "tb_find_mu_static": [I, I, VP, VP, D, D, D, I, VP, VP, VP, VP, VP],
         "tb_virial": [P, I, VP, D, VP, VP, VP, VP, VP],
+        "tb_npt_berendsen": [P, I, VP, VP, D, VP, VP, D, D, D, D, D, D, VP, VP, VP],
         "tb_ctx_reserve_local": [P, I],
         "tb_local_forward": [P, I, VP, D, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP],
         "tb_local_gradient": [P, I, VP, D, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP],
@@ -279,6 +280,16 @@ def tb_virial(ctx, n, pos, L, h_off, h_idx, W, pressure=None, stream=None):
     _check("tb_virial", lib().tb_virial(
         ctx, n, _ptr(pos, f64, "pos"), float(L), _ptr(h_off, i32, "h_off"),
         _ptr(h_idx, i32, "h_idx"), _ptr(W, f64, "W"), _ptr(pressure, f64, "pressure"),
+        _stream(stream)))
+
+
+def tb_npt_berendsen(ctx, n, pos, vel, L, W, energies, T0, P0, dt_fs, tau_T_fs, tau_P_fs,
+                     beta, L_new, state, stream=None):
+    f64 = torch.float64
+    _check("tb_npt_berendsen", lib().tb_npt_berendsen(
+        ctx, n, _ptr(pos, f64, "pos"), _ptr(vel, f64, "vel"), float(L), _ptr(W, f64, "W"),
+        _ptr(energies, f64, "energies"), float(T0), float(P0), float(dt_fs), float(tau_T_fs),
+        float(tau_P_fs), float(beta), _ptr(L_new, f64, "L_new"), _ptr(state, f64, "state"),
         _stream(stream)))
 
 

@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <cmath>
 #include "tb_internal.cuh"
 
 size_t krylov_basis_bytes_global(const tb_ctx* c);
@@ -382,6 +383,21 @@ tb_status tb_virial(tb_ctx* c, int n, const double* pos, double L, const int* h_
   if (!pos || !h_off || !h_idx || !W || !(L > 0.0)) return TB_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return launch_virial(c, n, pos, L, h_off, h_idx, W, pressure, s);
+}
+
+tb_status tb_npt_berendsen(tb_ctx* c, int n, double* pos, double* vel, double L,
+                           const double* W, const double* energies, double T0, double P0,
+                           double dt_fs, double tau_T_fs, double tau_P_fs, double beta,
+                           double* L_new, double* state, void* stream) {
+  tb_status st = ready(c, n);
+  if (st != TB_OK) return st;
+  if (!pos || !vel || !W || !energies || !L_new || !state || !(L > 0.0) || !(T0 >= 0.0) ||
+      !(dt_fs > 0.0) || !(tau_T_fs > dt_fs) || !(tau_P_fs > dt_fs) || !(beta > 0.0) ||
+      !std::isfinite(P0))
+    return TB_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return launch_npt_berendsen(c, n, pos, vel, L, W, energies, T0, P0, dt_fs, tau_T_fs, tau_P_fs,
+                              beta, L_new, state, s);
 }
 
 tb_status tb_ctx_reserve_local(tb_ctx* c, int n_atoms) {

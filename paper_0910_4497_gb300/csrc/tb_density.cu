@@ -778,7 +778,62 @@ __global__ void kick_kernel(int n, double* vel, const double* F, double dt, doub
   per_target[5 * i + 4] = 0.5 * mass * ke / ACC_CONV;
 }
 
+// f4: weak-coupling (Berendsen) NPT scaling after one Verlet step.  Every
+// block derives the two factors from the step's kinetic energy and virial (ten
+// loads, identical arithmetic in every block); block 0 publishes the new box
+// and the state.  A factor that is not a positive finite number leaves the
+// system unchanged and reports TB_ERR_NONFINITE.
+__global__ void npt_scale_kernel(int n, double* pos, double* vel, double L, const double* W,
+                                 const double* energies, double T0, double P0, double dt,
+                                 double tau_T, double tau_P, double beta, double* L_new,
+                                 double* state, int* st) {
+  __shared__ double fac[2];
+  if (threadIdx.x == 0) {
+    const double KB = 8.617333262e-5;              // eV/K
+    const double ke = energies[7];
+    const double dof = n > 1 ? 3.0 * n - 3.0 : 3.0;
+    const double T = 2.0 * ke / (KB * dof);
+    const double V = L * L * L;
+    const double P = (W[0] + W[4] + W[8] + 2.0 * ke) / (3.0 * V);
+    // no kinetic temperature (all velocities zero): nothing to rescale
+    const double lam2 = T > 0.0 ? 1.0 + dt / tau_T * (T0 / T - 1.0) : 1.0;
+    const double mu3 = 1.0 - beta * dt / tau_P * (P0 - P);
+    const bool ok = lam2 > 0.0 && mu3 > 0.0 && isfinite(lam2) && isfinite(mu3);
+    fac[0] = ok ? sqrt(lam2) : 1.0;
+    fac[1] = ok ? cbrt(mu3) : 1.0;
+    if (blockIdx.x == 0) {
+      *L_new = fac[1] * L;
+      state[0] = T;
+      state[1] = P;
+      state[2] = fac[0];
+      state[3] = fac[1];
+      if (!ok) tbk::set_status(st, TB_ERR_NONFINITE, 0);
+    }
+  }
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * n) return;
+  const double Ln = fac[1] * L;
+  vel[t] *= fac[0];
+  double x = fac[1] * pos[t];
+  if (x >= Ln) x -= Ln;                             // mu x < mu L up to rounding
+  if (x < 0.0) x = 0.0;
+  pos[t] = x;
+}
+
 }  // namespace
+
+tb_status launch_npt_berendsen(tb_ctx* c, int n, double* pos, double* vel, double L,
+                               const double* W, const double* energies, double T0, double P0,
+                               double dt, double tau_T, double tau_P, double beta,
+                               double* L_new, double* state, cudaStream_t s) {
+  const int grid = (3 * n + 255) / 256;
+  npt_scale_kernel<<<grid > 0 ? grid : 1, 256, 0, s>>>(n, pos, vel, L, W, energies, T0, P0, dt,
+                                                      tau_T, tau_P, beta, L_new, state,
+                                                      c->d_status);
+  TB_CUDA_TRY(cudaGetLastError());
+  return TB_OK;
+}
 
 tb_status mu_configure(tb_ctx* c) {
   int dev = 0, max_smem = 0;

@@ -260,6 +260,10 @@ tb_status launch_mu_nt(tb_ctx* c, int n, int NT, const double* lambda, const dou
                        double* n_count, cudaStream_t s);
 tb_status launch_energy_reduce(int n, const double* per_target, const double* mu,
                                double* energies, cudaStream_t s);
+tb_status launch_npt_berendsen(tb_ctx* c, int n, double* pos, double* vel, double L,
+                               const double* W, const double* energies, double T0, double P0,
+                               double dt, double tau_T, double tau_P, double beta,
+                               double* L_new, double* state, cudaStream_t s);
 tb_status launch_virial(tb_ctx* c, int n, const double* pos, double L, const int* h_off,
                         const int* h_idx, double* W, double* pressure, cudaStream_t s);
 tb_status local_configure(tb_ctx* c);

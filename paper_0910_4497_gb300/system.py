@@ -50,6 +50,8 @@ class TBSystem:
         self.energies = torch.zeros(8, dtype=f64, **kw)
         self.W = torch.zeros(9, dtype=f64, **kw)
         self.pressure = torch.zeros(1, dtype=f64, **kw)
+        self.L_dev = torch.zeros(1, dtype=f64, **kw)        # box after an NPT scaling
+        self.npt_state = torch.zeros(4, dtype=f64, **kw)    # T (K), P (eV/A^3), lambda, mu
         # m-target form: groups of group_m targets (tb_group_atoms)
         self.group_m = self.tp.group_m
         self.n_groups = (n + self.group_m - 1) // self.group_m
@@ -113,6 +115,21 @@ class TBSystem:
     def md_step(self, dt_fs, mass_amu, stream=None):
         B.tb_md_step(self.ctx, self.n, self.pos, self.vel, self.F, self.L, dt_fs, mass_amu,
                      self.energies, stream)
+
+    def npt_step(self, dt_fs, mass_amu, T0, P0, tau_T_fs, tau_P_fs, beta, stream=None):
+        """One velocity-Verlet step at the current box, its virial, and the
+        weak-coupling NPT scaling (f4).  Updates self.L from the device (one
+        device-to-host read, which waits for the step); the step's T, P and
+        scale factors are left in self.npt_state."""
+        self.md_step(dt_fs, mass_amu, stream)
+        B.tb_virial(self.ctx, self.n, self.pos, self.L, None, None, self.W, self.pressure,
+                    stream)
+        B.tb_npt_berendsen(self.ctx, self.n, self.pos, self.vel, self.L, self.W, self.energies,
+                           T0, P0, dt_fs, tau_T_fs, tau_P_fs, beta, self.L_dev,
+                           self.npt_state, stream)
+        if stream is not None:
+            stream.synchronize()
+        self.L = float(self.L_dev.item())
 
     # -- exact local free energy and its gradient at r = r_min (a11)
     def reserve_local(self, store_basis=False):

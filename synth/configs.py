@@ -58,6 +58,14 @@ CONFIGS = [
 ]
 
 
+# NPT workload (Sec. 4: C60 polymerisation at 25 GPa and 500 K for 3 ps): the
+# 15360-atom MD cell under weak coupling (Berendsen thermostat and isotropic
+# barostat; the paper names neither), coupling times 100 fs (T) and 500 fs (P),
+# the barostat's compressibility 1/(100 GPa).
+NPT = dict(name="c60_fcc_4x4x4_npt_15360", md_index=4, T0_K=500.0, P0_GPa=25.0,
+           tau_T_fs=100.0, tau_P_fs=500.0, B_GPa=100.0, dt_fs=0.5, duration_ps=3.0)
+GPA_PER_EV_A3 = 160.21766208
+
 # Long-range workloads: the 240-atom cell (parity against the full oracle;
 # Rc = rm = 7.0 A < L/2 = 7.085 A keeps the minimum image unique) and the
 # compressed 1920-atom cell with Rc = 8.0 A (H lists of 149-172 atoms, clusters

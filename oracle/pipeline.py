@@ -63,7 +63,7 @@ def _init_worker(pos, L, p, hlists, clists):
     _W["hl"], _W["cl"], _W["p"] = hlists, clists, p
 
 
-def _work(targets):
+def _records_of(targets):
     p = _W["p"]
     return [target_record(_W["bonds"], _W["cl"][i], _W["hl"][i], p["r"],
                           p["defl_tol"]) for i in targets]
@@ -78,7 +78,7 @@ def spectral_records(pos, L, p, hlists, clists, targets, bonds=None, workers=1):
     ctx = mp.get_context("spawn")
     with ctx.Pool(workers, initializer=_init_worker,
                   initargs=(pos, L, p, hlists, clists)) as pool:
-        parts = pool.map(_work, [list(c) for c in chunks])
+        parts = pool.map(_records_of, [list(c) for c in chunks])
     return [rec for part in parts for rec in part]
 
 

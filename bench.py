@@ -373,13 +373,16 @@ def record_bytes(system, prec):
     return total
 
 
-def kernel_traffic(prec, name="krylov_traffic.json"):
+def kernel_traffic(prec, name="krylov_traffic.json", workload=None):
     """DRAM bytes per Krylov launch from the committed ncu summary, or None if
-    the kernel source changed since it was taken."""
+    the kernel source changed since it was taken or the summary is of another
+    workload."""
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
+    if workload is not None and not rec.get("workload", "").startswith(workload):
+        return None
     h = hashlib.sha256()
     for rel in rec.get("sources", []):
         h.update(open(os.path.join(ROOT, rel), "rb").read())
@@ -547,7 +550,8 @@ def run_ours(args):
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "frac": achieved / hbm if achieved else None,
                 "traffic": kernel_traffic(args.prec, "krylov_group_traffic.json" if grouped
-                                          else "krylov_traffic.json"),
+                                          else "krylov_traffic_longrange.json" if longrange
+                                          else "krylov_traffic.json", cfg["name"]),
                 "algorithmic_bytes_per_launch": alg, "kernel_ms": kry_ms}
         stages = {k: (statistics.mean([x for x in v if x >= 0]) if any(x >= 0 for x in v)
                       else None) for k, v in stage_ms.items()}

@@ -68,3 +68,23 @@ def test_reference_arm_two_ranks_prints_once():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_traffic_record_is_taken_only_for_its_workload_and_sources(tmp_path, monkeypatch):
+    """bench.kernel_traffic returns a record's DRAM bytes only when the record
+    names the benchmarked workload and its kernel sources are unchanged."""
+    src = tmp_path / "k.cu"
+    src.write_bytes(b"kernel v1")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    import hashlib
+    rec = {"workload": "cell_A, one launch", "sources": ["k.cu"],
+           "source_sha256": hashlib.sha256(b"kernel v1").hexdigest(),
+           "dram_bytes_per_launch": {"mixed": 123.0}}
+    (prof / "t.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.kernel_traffic("mixed", "t.json", "cell_A") == 123.0
+    assert bench.kernel_traffic("mixed", "t.json", "cell_B") is None
+    assert bench.kernel_traffic("fp64", "t.json", "cell_A") is None
+    src.write_bytes(b"kernel v2")
+    assert bench.kernel_traffic("mixed", "t.json", "cell_A") is None

@@ -120,7 +120,7 @@ tb_status tb_ctx_workspace_bytes(const tb_ctx* ctx, size_t* bytes);
 tb_status tb_get_status(tb_ctx* ctx, int* code, int* info, void* stream);
 
 /*
- * a1. Neighbour and cluster lists (Sec. 2: atoms within the cutoff radius of
+ * Neighbour and cluster lists (Sec. 2: atoms within the cutoff radius of
  * the target).  Brute force over all pairs with an FP32 prefilter; the
  * membership decision is the FP64 test below, so the lists are bit-exact:
  *   d = x_j - x_i;  d -= L if d > L/2;  d += L if d < -L/2   (per component)
@@ -140,7 +140,7 @@ tb_status tb_build_neighbors(tb_ctx* ctx, int n, const double* pos, double L,
                              void* stream);
 
 /*
- * a2. Hamiltonian blocks of Eq. (1) for every directed bond p = (i -> j),
+ * Hamiltonian blocks of Eq. (1) for every directed bond p = (i -> j),
  * j = h_idx[p], d = R_j - R_i (minimum image), l = d/|d|:
  *   Hblk[p*16 + a*4 + b]      = H_{i a, j b} = s(|d|) * SK_ab(l)
  *   dHblk[p*48 + k*16 + a*4 + b] = d H_{i a, j b} / d d_k
@@ -155,7 +155,7 @@ tb_status tb_assemble_H(tb_ctx* ctx, int n, const double* pos, double L,
                         void* stream);
 
 /*
- * a3-a7. Per target atom i: cluster map, block Krylov space of order r from
+ * Per target atom i: cluster map, block Krylov space of order r from
  * V_1 = E_i (the four orbitals of i), block Lanczos with full
  * reorthogonalisation and deflation, T = block tridiagonal (A_k, B_k), its
  * eigenpairs (lam_m, U), and the spectral record.  With NT = 4r and kdim[i]
@@ -176,7 +176,7 @@ tb_status tb_krylov_density(tb_ctx* ctx, int n, const int* c_off, const int* c_i
                             void* stream);
 
 /*
- * a8. Chemical potential: solves 2 sum_i sum_m w_im f((lam_im - mu)/kT) = N_e
+ * Chemical potential: solves 2 sum_i sum_m w_im f((lam_im - mu)/kT) = N_e
  * with w_im = sum_a S[i,a,m]^2 and f(x) = 1/(1+e^x), by bracketed Newton
  * steps with bisection fallback, in FP64, in one cooperative launch.
  * mu_guess (device, may be NULL): starting point if inside the bracket.
@@ -189,7 +189,7 @@ tb_status tb_find_mu(tb_ctx* ctx, int n, const double* lambda, const double* S,
                      double* mu, double* n_count, void* stream);
 
 /*
- * a9-a10. Density-matrix blocks, energies and forces (Sec. 2: <F> = Tr[rho F]).
+ * Density-matrix blocks, energies and forces (Sec. 2: <F> = Tr[rho F]).
  *   rho^(i)_{q b, i a} = sum_m P[q,b,m] f_m S[a,m]
  *   F_k = 2 sum_{j in H(k)} sum_{a,b} [rho^(k)_{j b,k a} + rho^(j)_{k a,j b}]
  *         dHblk(k->j)_{a b}  -  dE_rep/dR_k
@@ -208,8 +208,8 @@ tb_status tb_forces(tb_ctx* ctx, int n, const double* pos, double L,
                     double* energies, void* stream);
 
 /*
- * a12. One NVE velocity-Verlet step (fs, amu; 1 eV/(A amu) = 9.648533e-3 A/fs^2):
- *   v += dt/2 F/m;  x = wrap(x + dt v);  F = F(x) [a1..a10];  v += dt/2 F/m.
+ * One NVE velocity-Verlet step (fs, amu; 1 eV/(A amu) = 9.648533e-3 A/fs^2):
+ *   v += dt/2 F/m;  x = wrap(x + dt v);  F = F(x) [lists .. forces];  v += dt/2 F/m.
  * pos, vel, F [n*3] in/out.  F on entry must be the force at pos.
  * energies [8] out as in tb_forces, with energies[7] = kinetic energy (eV).
  * n_electrons = 4 n.  Uses the context's own list/H/spectral buffers.
@@ -221,7 +221,7 @@ tb_status tb_md_step(tb_ctx* ctx, int n, double* pos, double* vel, double* F,
                      void* stream);
 
 /*
- * f2. Groups of m = group_m target atoms for the m-target form of the block
+ * Groups of m = group_m target atoms for the m-target form of the block
  * recursion (Sec. 3, Eq. (lanczos_blas3)); the paper leaves the grouping open,
  * this is the library's spatial reading.  The grid has g^3 cells, g the
  * largest integer with m g^3 <= n (capped at 1024); atom i lies in cell
@@ -239,7 +239,8 @@ tb_status tb_group_atoms(tb_ctx* ctx, int n, const double* pos, double L, int* g
                          int* g_idx, void* stream);
 
 /*
- * f2. a3-a7 in the m-target form (Sec. 3, Eq. (lanczos_blas3)).  For each
+ * Cluster map, block Krylov space, projected eigensolve and spectral record in
+ * the m-target form (Sec. 3, Eq. (lanczos_blas3)).  For each
  * group q of targets g_idx[g_off[q] .. g_off[q+1]) (1..group_m targets, any
  * partition of the atoms, e.g. from tb_group_atoms): the union of the targets'
  * clusters is formed and each target's block Krylov space is built from its own
@@ -336,7 +337,7 @@ tb_status tb_virial(tb_ctx* ctx, int n, const double* pos, double L, const int* 
                     const int* h_idx, double* W, double* pressure, void* stream);
 
 /*
- * f4. Weak-coupling (Berendsen) NPT for the C60 polymerisation runs of Sec. 4
+ * Weak-coupling (Berendsen) NPT for the C60 polymerisation runs of Sec. 4
  * (MD at 25 GPa and 500 K; the paper names neither thermostat nor barostat).
  * Call after tb_md_step (box L) and tb_virial on that step's bonds, on the same
  * stream; with the step's kinetic energy KE = energies[7] and virial W:
@@ -363,7 +364,7 @@ tb_status tb_npt_berendsen(tb_ctx* ctx, int n, double* pos, double* vel, double 
                            double* L_new, double* state, void* stream);
 
 /*
- * a11. Exact gradient of the truncated local free energy (differentiable form
+ * Exact gradient of the truncated local free energy (differentiable form
  * of the method).  Sec. 3: once the Krylov order reaches the minimal-polynomial
  * degree (r = r_min) the block Krylov space of a target is invariant and its
  * projection is exact, so the target's spectral record is that of the dense
@@ -387,7 +388,7 @@ tb_status tb_npt_berendsen(tb_ctx* ctx, int n, double* pos, double* vel, double 
  * Returns TB_ERR_CAPACITY if max_cluster > 128.
  *
  * With ND = 4 * max_cluster:
- * tb_local_forward: lists and bond blocks as produced by a1/a2 (Hblk FP64);
+ * tb_local_forward: lists and bond blocks as produced by tb_build_neighbors and tb_assemble_H (Hblk FP64);
  *   lambda [n*ND] out, S [n*4*ND] out (layout of tb_krylov_density with NT = ND;
  *   entries beyond 4 n_c(i) are 0), kdim [n] out (= 4 n_c(i));
  *   Zstore (may be NULL): [n*ND*ND] elements of the context precision (double

@@ -29,7 +29,7 @@ def kinetic_energy(vel, mass):
     return 0.5 * mass * np.sum(vel * vel) / ACC
 
 
-# ---------------------------------------------------------------- NPT (f4)
+# ---------------------------------------------------------------- NPT
 # The paper runs its C60 polymerisation at 25 GPa and 500 K (Sec. 4) without
 # naming a thermostat or barostat.  The reading used here is weak coupling
 # (Berendsen): after each velocity-Verlet step, with the step's kinetic energy

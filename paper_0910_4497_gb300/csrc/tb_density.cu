@@ -1,4 +1,4 @@
-// a8-a10, a12: chemical potential, density-matrix blocks, energies, forces
+// Chemical potential, density-matrix blocks, energies, forces
 // (Sec. 2: rho = sum_m |m> f(e_m) <m|, <F_i> = Tr[rho F_i]) and the
 // velocity-Verlet kernels.
 //
@@ -778,7 +778,7 @@ __global__ void kick_kernel(int n, double* vel, const double* F, double dt, doub
   per_target[5 * i + 4] = 0.5 * mass * ke / ACC_CONV;
 }
 
-// f4: weak-coupling (Berendsen) NPT scaling after one Verlet step.  Every
+// Weak-coupling (Berendsen) NPT scaling after one Verlet step.  Every
 // block derives the two factors from the step's kinetic energy and virial (ten
 // loads, identical arithmetic in every block); block 0 publishes the new box
 // and the state.  A factor that is not a positive finite number leaves the

@@ -1,4 +1,4 @@
-// a6-a7: eigenpairs of the projected matrix T (Sec. 3: the small Lanczos
+// Eigenpairs of the projected matrix T (Sec. 3: the small Lanczos
 // matrix is diagonalised with a dense symmetric eigensolver) and the spectral
 // record lambda, S = U[seed rows], P = Y U.
 //

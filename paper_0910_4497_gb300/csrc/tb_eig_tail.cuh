@@ -1,4 +1,4 @@
-// a6-a7 inside the block-Lanczos CTA: FP32 eigenpairs of the projected
+// The projected eigensolve inside the block-Lanczos CTA: FP32 eigenpairs of the projected
 // matrix T of one target (Sec. 3: the small Lanczos matrix is diagonalised by
 // a dense symmetric eigensolver) computed by the whole CTA in shared memory
 // that the Krylov basis no longer needs, followed (mixed path) by the spectral

@@ -1,4 +1,4 @@
-// a2: Hamiltonian blocks of Eq. (1) for every directed bond i -> j.
+// Hamiltonian blocks of Eq. (1) for every directed bond i -> j.
 //
 // Slater-Koster table for s and p orbitals with direction cosines l of
 // d = R_j - R_i (minimum image):

@@ -187,7 +187,7 @@ struct tb_ctx {
   size_t fin_smem = 0;
   int mu_grid = 0;
   int mu_smem_max = 0;
-  // m-target form (f2): grouped block Lanczos, configured when group_m > 1
+  // m-target form: grouped block Lanczos, configured when group_m > 1
   int grp_max_union = 0;             // capacity of a group's union cluster
   int grp_grid = 0;
   int grp_mc = 0;                    // targets per CTA (kernel capacity: 2 or 4)
@@ -201,7 +201,7 @@ struct tb_ctx {
   int* grp_cnt = nullptr;            // n: Morton ranks
   int* grp_off = nullptr;            // n + 1: the context's own groups (tb_md_step)
   int* grp_idx = nullptr;            // n
-  // exact local gradient (a11): dense workspace, allocated by tb_ctx_reserve_local
+  // exact local gradient: dense workspace, allocated by tb_ctx_reserve_local
   int loc_ND = 0;                    // 4 * max_cluster
   int loc_grid = 0;
   size_t loc_smem = 0;

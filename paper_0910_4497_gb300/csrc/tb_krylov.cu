@@ -1,4 +1,4 @@
-// a3-a5: per-target cluster map and block Lanczos (Sec. 3, Eq. (Krylov) and
+// Per-target cluster map and block Lanczos (Sec. 3, Eq. (Krylov) and
 // the block form of Eqs. (lanczos) / (lanczos_blas3)).
 //
 // One CTA per target atom (persistent, grid-stride over targets).  For target

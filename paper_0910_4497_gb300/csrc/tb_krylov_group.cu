@@ -1,4 +1,4 @@
-// f2: the m-target form of the block recursion (Sec. 3, Eq. (lanczos_blas3))
+// The m-target form of the block recursion (Sec. 3, Eq. (lanczos_blas3))
 // and the spatial grouping of the targets it runs on.
 //
 // Grouping.  The atoms are sorted by (Morton code of their grid cell, index)

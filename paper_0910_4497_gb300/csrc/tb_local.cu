@@ -1,4 +1,4 @@
-// a11: exact gradient of the truncated local free energy at Krylov order
+// Exact gradient of the truncated local free energy at Krylov order
 // r = r_min (the differentiable form of the method).
 //
 // Once r reaches the minimal-polynomial degree the block Krylov space of a

@@ -1,4 +1,4 @@
-// a1: neighbour and cluster lists (Sec. 2: atoms within the cutoff radius).
+// Neighbour and cluster lists (Sec. 2: atoms within the cutoff radius).
 //
 // Brute force over all pairs, tiled through shared memory: a CTA of 8 warps
 // serves 8 target atoms and streams the candidate positions once per tile.

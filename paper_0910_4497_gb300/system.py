@@ -95,7 +95,7 @@ class TBSystem:
                     stream)
 
     def evaluate(self, stream=None, warm_start=False, with_virial=False):
-        """One full force evaluation (a1..a10) of the positions in self.pos;
+        """One full force evaluation (lists to forces) of the positions in self.pos;
         with_virial adds the virial W (3x3, eV) and static pressure (eV/A^3)."""
         self.neighbors(stream)
         if self.group_m > 1:
@@ -118,7 +118,7 @@ class TBSystem:
 
     def npt_step(self, dt_fs, mass_amu, T0, P0, tau_T_fs, tau_P_fs, beta, stream=None):
         """One velocity-Verlet step at the current box, its virial, and the
-        weak-coupling NPT scaling (f4).  Updates self.L from the device (one
+        weak-coupling NPT scaling.  Updates self.L from the device (one
         device-to-host read, which waits for the step); the step's T, P and
         scale factors are left in self.npt_state."""
         self.md_step(dt_fs, mass_amu, stream)
@@ -131,7 +131,7 @@ class TBSystem:
             stream.synchronize()
         self.L = float(self.L_dev.item())
 
-    # -- exact local free energy and its gradient at r = r_min (a11)
+    # -- exact local free energy and its gradient at r = r_min
     def reserve_local(self, store_basis=False):
         """Dense workspace and buffers of the exact local path; with store_basis
         the forward keeps every target's eigenvectors for the backward

@@ -1,4 +1,4 @@
-"""GPU parity of the weak-coupling NPT step (f4) through the C ABI: three
+"""GPU parity of the weak-coupling NPT step through the C ABI: three
 steps of the 240-atom cell at 25 GPa and 500 K (tb_md_step, tb_virial,
 tb_npt_berendsen) against the oracle's Verlet step, virial and scaling on the
 same seeded state, in both precisions; the host argument checks and the

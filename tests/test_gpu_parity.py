@@ -105,7 +105,7 @@ def compare_full(tb, key, pos, L, p, prec, graph=False, workers=1):
     return s, ref
 
 
-# ---------------------------------------------------------------- a1 lists
+# ---------------------------------------------------------------- lists
 
 @pytest.mark.parametrize("k", [0, 1])
 def test_neighbor_lists_bit_exact(tb, k):
@@ -144,7 +144,7 @@ def test_position_outside_box_reports(tb):
     assert code == 1 and info == 7          # TB_ERR_INVALID_ARG at atom 7
 
 
-# ---------------------------------------------------------------- a2 H blocks
+# ---------------------------------------------------------------- H blocks
 
 def test_hamiltonian_blocks(tb):
     pos, L, p = cfg_system(0)
@@ -165,7 +165,7 @@ def test_hamiltonian_blocks(tb):
     assert np.abs(Hm - bonds.t).max() <= 1e-6
 
 
-# ---------------------------------------------------------------- a3-a7 spectra
+# ---------------------------------------------------------------- spectral records
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_spectral_record_moments_and_rho(tb, prec):
@@ -188,7 +188,7 @@ def test_spectral_record_moments_and_rho(tb, prec):
         assert np.abs(rg - rr).max() <= tol["rho"], i
 
 
-# ---------------------------------------------------------------- a8-a10 full
+# ---------------------------------------------------------------- full evaluation
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_forces_cfg0(tb, prec):
@@ -291,7 +291,7 @@ def test_krylov_order_one(tb):
     compare_full(tb, "cfg0_r1", pos, L, p, "fp64")
 
 
-# ---------------------------------------------------------------- a12 MD
+# ---------------------------------------------------------------- MD
 
 def test_md_step_matches_oracle_verlet(tb):
     from synth import maxwell_boltzmann_velocities

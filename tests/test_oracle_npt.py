@@ -1,4 +1,4 @@
-"""Pins of the oracle's weak-coupling NPT step (f4; Berendsen thermostat and
+"""Pins of the oracle's weak-coupling NPT step (Berendsen thermostat and
 isotropic barostat, the reading used since the paper names neither) against
 what its definition fixes: no change at the target state, the rescaled
 temperature T + (dt/tau_T)(T0 - T) recomputed from the rescaled velocities,

@@ -121,8 +121,10 @@ tb_status tb_get_status(tb_ctx* ctx, int* code, int* info, void* stream);
 
 /*
  * Neighbour and cluster lists (Sec. 2: atoms within the cutoff radius of
- * the target).  Brute force over all pairs with an FP32 prefilter; the
- * membership decision is the FP64 test below, so the lists are bit-exact:
+ * the target).  Candidates come from cell lists (cells of side >= Rc + 0.01 A)
+ * when the box holds at least 3 such cells per dimension, else from all
+ * pairs; an FP32 prefilter drops far pairs, and the membership decision is the
+ * FP64 test below, so the lists are bit-exact and the same on both paths:
  *   d = x_j - x_i;  d -= L if d > L/2;  d += L if d < -L/2   (per component)
  *   r2 = (dx*dx + dy*dy) + dz*dz   (each operation rounded, no FMA)
  *   Hamiltonian list of i: all j != i with r2 <= rm*rm, ascending j;
@@ -318,7 +320,6 @@ tb_status tb_find_mu_static(int n, int r, const double* lambda, const double* S,
                             const double* mu_guess, double* mu, double* n_count, int* status,
                             void* stream);
 
-/* Library version string (static, host). */
 /*
  * Virial and pressure (Sec. 5: pressure of a diamond supercell for its
  * equation of state).  Every force of tb_forces is a sum over directed bonds,
@@ -356,7 +357,11 @@ tb_status tb_virial(tb_ctx* ctx, int n, const double* pos, double L, const int* 
  * dt_fs < tau_P_fs (fs); beta > 0 (A^3/eV, the barostat's compressibility).
  * Returns TB_ERR_INVALID_ARG for arguments outside these ranges.  On the
  * device, a factor that is not a positive finite number leaves pos, vel and
- * the box unchanged and sets TB_ERR_NONFINITE.  Capturable.
+ * the box unchanged and sets the status word: TB_ERR_NONFINITE when a factor
+ * is NaN or infinite (non-finite kinetic energy or virial), TB_ERR_INVALID_ARG
+ * when it is finite but not positive (the target state too far from the
+ * current one for the coupling constants), info 0 for lambda^2, 1 for mu^3.
+ * Capturable.
  */
 tb_status tb_npt_berendsen(tb_ctx* ctx, int n, double* pos, double* vel, double L,
                            const double* W, const double* energies, double T0, double P0,
@@ -413,6 +418,7 @@ tb_status tb_local_gradient(tb_ctx* ctx, int n, const double* pos, double L, con
                             const double* S, const void* Zstore, const double* mu, double* F,
                             void* stream);
 
+/* Library version string (static, host). */
 const char* tb_version(void);
 
 #ifdef __cplusplus

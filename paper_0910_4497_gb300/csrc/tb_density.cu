@@ -8,6 +8,8 @@
 // states).  All sums are taken in a fixed order (per-thread, then fixed
 // shuffle trees, then a fixed sequence over blocks), so results are
 // deterministic from run to run.
+#include <atomic>
+#include <mutex>
 #include "tb_internal.cuh"
 #include "tb_model.cuh"
 
@@ -782,7 +784,10 @@ __global__ void kick_kernel(int n, double* vel, const double* F, double dt, doub
 // block derives the two factors from the step's kinetic energy and virial (ten
 // loads, identical arithmetic in every block); block 0 publishes the new box
 // and the state.  A factor that is not a positive finite number leaves the
-// system unchanged and reports TB_ERR_NONFINITE.
+// system unchanged: a NaN or infinite factor (from a non-finite kinetic energy
+// or virial) reports TB_ERR_NONFINITE, a finite but non-positive one (a target
+// far from the current state for the coupling constants) TB_ERR_INVALID_ARG
+// with info 0 for the thermostat's lambda^2, 1 for the barostat's mu^3.
 __global__ void npt_scale_kernel(int n, double* pos, double* vel, double L, const double* W,
                                  const double* energies, double T0, double P0, double dt,
                                  double tau_T, double tau_P, double beta, double* L_new,
@@ -798,7 +803,8 @@ __global__ void npt_scale_kernel(int n, double* pos, double* vel, double L, cons
     // no kinetic temperature (all velocities zero): nothing to rescale
     const double lam2 = T > 0.0 ? 1.0 + dt / tau_T * (T0 / T - 1.0) : 1.0;
     const double mu3 = 1.0 - beta * dt / tau_P * (P0 - P);
-    const bool ok = lam2 > 0.0 && mu3 > 0.0 && isfinite(lam2) && isfinite(mu3);
+    const bool fin = isfinite(lam2) && isfinite(mu3);
+    const bool ok = fin && lam2 > 0.0 && mu3 > 0.0;
     fac[0] = ok ? sqrt(lam2) : 1.0;
     fac[1] = ok ? cbrt(mu3) : 1.0;
     if (blockIdx.x == 0) {
@@ -807,7 +813,8 @@ __global__ void npt_scale_kernel(int n, double* pos, double* vel, double L, cons
       state[1] = P;
       state[2] = fac[0];
       state[3] = fac[1];
-      if (!ok) tbk::set_status(st, TB_ERR_NONFINITE, 0);
+      if (!fin) tbk::set_status(st, TB_ERR_NONFINITE, isfinite(lam2) ? 1 : 0);
+      else if (!ok) tbk::set_status(st, TB_ERR_INVALID_ARG, lam2 > 0.0 ? 1 : 0);
     }
   }
   __syncthreads();
@@ -954,23 +961,26 @@ tb_status launch_md_kick(tb_ctx* c, int n, double* vel, const double* F, double 
 // or a process where a cudaMalloc would synchronise the device at a bad
 // moment).  They cannot create a tb_ctx either, because tb_ctx_create and
 // tb_ctx_reserve allocate.  tb_find_mu_static gives them the mu search with
-// its scratch (per-block partial sums, the grid-barrier counter and the
-// status word) in this file-scope device array instead of in a context.
+// its scratch (per-block partial sums and the grid-barrier counter) in this
+// file-scope device array instead of in a context; the status words are the
+// caller's.
 //
 // The array is sized for TB_FIND_MU_STATIC_MAX_BLOCKS blocks of the
 // cooperative search (one block per SM); every GPU that loads the library
 // holds it until the process exits.  All calls share it and it keeps the last
-// call's contents, so the counter and status words are cleared on the stream
-// before each launch; calls whose executions overlap on the GPU race on it.
+// call's contents, so the counter (and the caller's status words) are cleared
+// on the stream before each launch; calls whose executions overlap on the GPU
+// race on it.  The per-device set-up is guarded, so first calls from several
+// host threads at once are safe.
 namespace {
 
 constexpr int kStaticPartDoubles = 2 * MU_PART * TB_FIND_MU_STATIC_MAX_BLOCKS;
-// [0, kStaticPartDoubles) partial sums; then one 256-byte line holding the
-// barrier counter (word 0) and the status code and info (words 1, 2)
+// [0, kStaticPartDoubles) partial sums; then one 256-byte line whose first
+// word is the grid-barrier counter (the rest of the line is unused)
 static __device__ __align__(256) double g_mu_scratch[kStaticPartDoubles + 32];
 
 struct StaticMuDevice {
-  bool ready = false;
+  std::atomic<bool> ready{false};   // published with release after the fields below
   double* scratch = nullptr;   // device address of g_mu_scratch on this device
   int sms = 0;
   int smem_max = 0;
@@ -981,9 +991,13 @@ StaticMuDevice g_static_mu[kMaxDevices];
 // One-time set-up on the current device: device address of the scratch array
 // (its name on the host is only a stand-in), SM count and the kernel's
 // shared-memory limit.  Not capturable into a CUDA graph.
+std::mutex g_static_mu_lock;
+
 tb_status static_mu_setup(int dev) {
   StaticMuDevice& d = g_static_mu[dev];
-  if (d.ready) return TB_OK;
+  if (d.ready.load(std::memory_order_acquire)) return TB_OK;
+  std::lock_guard<std::mutex> guard(g_static_mu_lock);
+  if (d.ready.load(std::memory_order_relaxed)) return TB_OK;
   void* p = nullptr;
   if (cudaGetSymbolAddress(&p, g_mu_scratch) != cudaSuccess || !p) {
     cudaGetLastError();
@@ -997,7 +1011,7 @@ tb_status static_mu_setup(int dev) {
   d.scratch = static_cast<double*>(p);
   d.sms = sms;
   d.smem_max = smem;
-  d.ready = true;
+  d.ready.store(true, std::memory_order_release);
   return TB_OK;
 }
 

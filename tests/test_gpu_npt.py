@@ -108,7 +108,7 @@ def test_npt_argument_checks_and_device_refusal(tb):
     B.tb_npt_berendsen(s.ctx, s.n, s.pos, s.vel, s.L, s.W, s.energies, T0, 1e3, 0.5, tT, tP,
                        beta, s.L_dev, s.npt_state)
     torch.cuda.synchronize()
-    code, _ = s.status()
-    assert B.STATUS_NAMES[code] == "TB_ERR_NONFINITE"
+    code, info = s.status()
+    assert B.STATUS_NAMES[code] == "TB_ERR_INVALID_ARG" and info == 1     # mu^3 <= 0
     assert torch.equal(s.pos, x0) and torch.equal(s.vel, v0) and s.L_dev.item() == s.L
     s.close()

@@ -5,7 +5,9 @@ Callers that may not allocate device memory (a host runtime owning every
 device allocation through its own pool) use tb_find_mu_static: it needs no
 tb_ctx and keeps its scratch in a fixed array inside the library.  It must
 give the same chemical potential as tb_find_mu, on every call: the array
-keeps the previous call's contents, so two calls run back to back here.
+keeps the previous call's contents, so two calls run back to back here, and
+the second call (after the one-time set-up) must leave the device's free
+memory and torch's allocation count unchanged.
 
 This file is named to be collected last.
 """
@@ -40,13 +42,21 @@ def test_static_mu_matches_context_mu_twice(tb, prec):
     mu_ref = s.mu.item()
     n_ref = s.ncount.item()
     ne = 4.0 * s.n
-    for call in range(2):
-        mu = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
-        ncount = torch.zeros(1, dtype=torch.float64, device="cuda")
-        status = torch.full((2,), -7, dtype=torch.int32, device="cuda")
+    outs = [(torch.full((1,), float("nan"), dtype=torch.float64, device="cuda"),
+             torch.zeros(1, dtype=torch.float64, device="cuda"),
+             torch.full((2,), -7, dtype=torch.int32, device="cuda")) for _ in range(2)]
+    for call, (mu, ncount, status) in enumerate(outs):
+        if call == 1:
+            # the first call did the one-time set-up: from here on nothing may
+            # allocate, neither on the device nor through torch's allocator
+            free0 = torch.cuda.mem_get_info()[0]
+            allocs0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
         tb.binding.tb_find_mu_static(s.n, s.tp.r, s.lam, s.S, p["kT"], ne, s.tp.mu_tol,
                                      s.tp.mu_max_iter, None, mu, ncount, status)
         torch.cuda.synchronize()
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == allocs0
         assert status.tolist() == [0, 0], f"call {call}: device status {status.tolist()}"
         # same search on the same data and grid: the electron count tolerance of
         # the parity tests, and in practice the same bits

@@ -92,7 +92,22 @@ typedef struct tb_params {
                        * target per cluster, the default); see tb_group_atoms */
   int max_union;      /* capacity of a group's union cluster (atoms, <= 1024);
                        * 0 = min(1024, group_m * max_cluster)                   */
+  int schedule;       /* tb_schedule: how the mixed path's block Lanczos and
+                       * projected eigensolve are launched                      */
 } tb_params;
+
+typedef enum tb_schedule {
+  /* The library chooses: its own measurement when tb_autotune has run on
+   * this context, else the persistent queue when the targets fill at most 16
+   * waves of CTAs and separate launches otherwise. */
+  TB_SCHED_AUTO = 0,
+  /* One persistent launch: a work queue of block-Lanczos targets followed by
+   * projected-eigensolve items, so the eigensolves fill the SMs the last
+   * Krylov targets leave idle (mixed path, single-target clusters). */
+  TB_SCHED_PERSISTENT = 1,
+  /* Separate block-Lanczos and eigensolver launches. */
+  TB_SCHED_SEPARATE = 2
+} tb_schedule;
 
 typedef struct tb_ctx tb_ctx;
 

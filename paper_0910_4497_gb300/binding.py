@@ -19,6 +19,7 @@ STATUS_NAMES = {0: "TB_OK", 1: "TB_ERR_INVALID_ARG", 2: "TB_ERR_CUDA", 3: "TB_ER
                 7: "TB_ERR_NO_CONVERGENCE", 8: "TB_ERR_TIMEOUT", 9: "TB_ERR_NOT_RESERVED"}
 TB_PREC_FP64 = 0
 TB_PREC_MIXED = 1
+SCHEDULES = {"auto": 0, "persistent": 1, "separate": 2}
 
 EXPORTS = ["tb_params_default", "tb_ctx_create", "tb_ctx_destroy", "tb_ctx_reserve",
            "tb_ctx_workspace_bytes", "tb_get_status", "tb_build_neighbors",
@@ -37,7 +38,8 @@ class TBParams(ctypes.Structure):
               [(k, ctypes.c_int) for k in
                ("r", "prec", "max_hnbr", "max_cluster", "reorth_passes", "mu_max_iter")] + \
               [("timeout_cycles", ctypes.c_longlong), ("reorth_every", ctypes.c_int),
-               ("group_m", ctypes.c_int), ("max_union", ctypes.c_int)]
+               ("group_m", ctypes.c_int), ("max_union", ctypes.c_int),
+               ("schedule", ctypes.c_int)]
 
 
 class TBError(RuntimeError):
@@ -141,6 +143,8 @@ def make_params(p, prec):
     tp.mu_max_iter = int(p.get("mu_max_iter", 100))
     tp.group_m = int(p.get("group_m", 1))
     tp.max_union = int(p.get("max_union", 0))
+    sched = p.get("schedule", "auto")
+    tp.schedule = SCHEDULES[sched] if isinstance(sched, str) else int(sched)
     if "timeout_cycles" in p:
         tp.timeout_cycles = int(p["timeout_cycles"])
     return tp

@@ -27,6 +27,7 @@ tb_status check_params(const tb_params& p) {
   if (p.max_union < 0 || p.max_union > tbk::MAX_CLUSTER) return TB_ERR_INVALID_ARG;
   if (p.mu_max_iter < 1 || !(p.mu_tol > 0.0) || !(p.defl_tol >= 0.0)) return TB_ERR_INVALID_ARG;
   if (p.timeout_cycles <= 0) return TB_ERR_INVALID_ARG;
+  if (p.schedule < TB_SCHED_AUTO || p.schedule > TB_SCHED_SEPARATE) return TB_ERR_INVALID_ARG;
   if (!finite_pos(p.Es) || !finite_pos(p.Ep)) return TB_ERR_INVALID_ARG;
   return TB_OK;
 }
@@ -469,7 +470,6 @@ tb_status tb_ctx_kernels_per_evaluation(const tb_ctx* c, int n, double L, int* c
   } else {
     k += 1;                                            // block Lanczos
     if (krylov_eig_persistent(c, n)) eig = 0;          // eigensolve inside the Krylov launch
-    else if (c->kry_fused) eig -= 1;
   }
   *count = k + eig + 1 + 4;                            // mu; rho, bond forces, sums, energies
   return TB_OK;

@@ -279,16 +279,13 @@ tb_status launch_eig(tb_ctx* c, int n, const int* h_off, double* lambda, double*
                      double* P, int* kdim, cudaStream_t s) {
   if (n <= 0) return TB_OK;
   const int NT = 4 * c->p.r;
-  if ((c->kry_fused && c->p.prec == TB_PREC_MIXED) || krylov_eig_persistent(c, n))
-    return TB_OK;                   // done in the Krylov launch
+  if (krylov_eig_persistent(c, n)) return TB_OK;      // done in the Krylov launch
   const int xw = c->eig_warps;
   XArgs xa{n, NT, c->T, c->colmask, reinterpret_cast<const float*>(c->Y), h_off, c->Zf,
            c->lamf, lambda, S, P, kdim, c->d_status};
   if (c->p.prec == TB_PREC_FP64) {
-    if (!c->kry_fused) {
-      eig_launch<false>(NT, (n + xw - 1) / xw, xw * GT, c->eig_smem, s, xa);
-      TB_CUDA_TRY(cudaGetLastError());
-    }
+    eig_launch<false>(NT, (n + xw - 1) / xw, xw * GT, c->eig_smem, s, xa);
+    TB_CUDA_TRY(cudaGetLastError());
     FinArgs<double> fa{n, NT, c->T, c->colmask, c->Zf, c->lamf,
                        reinterpret_cast<const double*>(c->Y), h_off, lambda, S, P, c->d_status};
     eig_finish_kernel<double><<<n, FT, c->fin_smem, s>>>(fa);

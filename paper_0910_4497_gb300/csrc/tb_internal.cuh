@@ -173,8 +173,6 @@ struct tb_ctx {
   // launch configuration
   int kry_grid = 0;
   size_t kry_smem = 0;
-  bool kry_vsmem = false;
-  bool kry_fused = false;           // projected eigensolve inside the Krylov kernel
   int kry_threads = 256;            // threads per Krylov CTA
   bool kry_lsmem = false;           // local CSR of the Krylov kernel in shared memory
   bool ke_on = false;               // persistent Krylov + eigensolve kernel (mixed path)

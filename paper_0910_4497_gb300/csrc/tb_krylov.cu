@@ -27,7 +27,6 @@
 // otherwise in a per-CTA slot of global memory (L2-resident).
 // Layout of the basis: block b occupies Dmax*4 values, row-major [row][4].
 #include "tb_internal.cuh"
-#include "tb_eig_tail.cuh"
 #include "tb_eig_group.cuh"
 #include "tb_krylov_common.cuh"
 
@@ -112,11 +111,11 @@ __host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, int max
 
 // Block Lanczos of target i by the whole CTA (the basis slot and local CSR
 // of CTA blockIdx.x).
-template <typename TV, bool VSMEM, bool FUSED, int KT>
+template <typename TV, int KT>
 __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) {
   constexpr int KW = KT / 32;
+  constexpr bool VSMEM = false;      // the basis lives in the CTA's global slot
   static_assert(KT == 128 || KT == 256, "128 or 256 threads");
-  static_assert(!FUSED || KT == 256, "the fused eigensolve runs on 256 threads");
   extern __shared__ __align__(32) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r = a.r, NT = 4 * r, Dmax = 4 * a.max_cluster;
@@ -626,51 +625,13 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
       }
     }
     __syncthreads();
-    if constexpr (FUSED) {
-      // ---- projected eigensolve in the shared memory the basis occupied
-      const unsigned long long mask =
-          ((unsigned long long)(unsigned)flags[FL_MASK + 1] << 32) | (unsigned)flags[FL_MASK];
-      const tbtail::TailOut o =
-          tbtail::eig_tail<KT>(Ti, mask, NT, reinterpret_cast<float*>(V), a.st, i);
-      const int m = o.m, PU = tbtail::tpitch(NT);
-      if (tid == 0) a.kdim[i] = m;
-      if constexpr (sizeof(TV) == sizeof(double)) {
-        // FP64 path: the FP32 eigenpairs seed the FP64 refinement kernel
-        for (int k = tid; k < m; k += KT) a.lamf[(size_t)i * NT + k] = o.lam[k];
-        for (int q = tid; q < m * m; q += KT) {
-          const int x = q / m, k = q - x * m;
-          a.Zf[(size_t)i * NT * NT + x * NT + k] = o.U[x * PU + k];
-        }
-      } else {
-        // mixed path: spectral record lambda (ascending), S, P = Y[:, act] U
-        double* lo = a.lambda + (size_t)i * NT;
-        for (int k = tid; k < NT; k += KT) lo[k] = k < m ? o.rq[2 * k] / o.rq[2 * k + 1] : 0.0;
-        double* So = a.S + (size_t)i * 4 * NT;
-        for (int q = tid; q < 4 * NT; q += KT) {
-          const int al = q / NT, k = q - al * NT;
-          So[q] = k < m ? (double)o.U[al * PU + k] : 0.0;
-        }
-        const size_t rbase = (size_t)(i + a.h_off[i]) * 4;
-        const int nrows = 4 * (deg + 1);
-        for (int q = tid; q < nrows * NT; q += KT) {
-          const int rr = q / NT, k = q - rr * NT;
-          float t = 0.f;
-          if (k < m) {
-            const TV* yr = a.Y + (rbase + rr) * NT;
-            for (int l = 0; l < m; ++l) t += (float)yr[o.act[l]] * o.U[l * PU + k];
-          }
-          a.P[(rbase + rr) * NT + k] = (double)t;
-        }
-      }
-      __syncthreads();
-    }
   }
 }
 
 // One CTA per target atom, persistent (grid-stride over the targets).
-template <typename TV, bool VSMEM, bool FUSED, int KT>
+template <typename TV, int KT>
 __global__ void __launch_bounds__(KT, KT == 128 ? (sizeof(TV) == 4 ? 5 : 4) : 2) krylov_kernel(const KryArgs<TV> a) {
-  for (int i = blockIdx.x; i < a.n; i += gridDim.x) krylov_target<TV, VSMEM, FUSED, KT>(a, i);
+  for (int i = blockIdx.x; i < a.n; i += gridDim.x) krylov_target<TV, KT>(a, i);
 }
 
 __device__ __forceinline__ int ld_acquire_s32(const int* p) {
@@ -704,7 +665,7 @@ __global__ void __launch_bounds__(128, 4) kry_eig_kernel(const KryArgs<float> a,
     const int it = s_item;
     if (it >= nitems) break;
     if (it < n) {
-      krylov_target<float, false, false, 128>(a, it);
+      krylov_target<float, 128>(a, it);
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) atomicExch(done + it, 1);
@@ -796,7 +757,7 @@ tb_status kry_eig_launch(tb_ctx* c, int n, const int* c_off, const int* c_idx, c
   return TB_OK;
 }
 
-template <typename TV, bool VSMEM, bool FUSED, int KT>
+template <typename TV, int KT>
 tb_status launch_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int* h_off,
                    const int* h_idx, const TV* H, double* lambda, double* S, double* P,
                    int* kdim, cudaStream_t s) {
@@ -814,37 +775,32 @@ tb_status launch_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const i
   a.lamf = c->lamf; a.Zf = c->Zf; a.lambda = lambda; a.S = S; a.P = P; a.kdim = kdim;
   const int grid = n < c->kry_grid ? n : c->kry_grid;
   if (grid <= 0) return TB_OK;
-  krylov_kernel<TV, VSMEM, FUSED, KT><<<grid, KT, c->kry_smem, s>>>(a);
+  krylov_kernel<TV, KT><<<grid, KT, c->kry_smem, s>>>(a);
   TB_CUDA_TRY(cudaGetLastError());
   return TB_OK;
 }
 
-template <typename TV, bool VSMEM, bool FUSED, int KT>
+template <typename TV, int KT>
 tb_status configure_t(tb_ctx* c, int max_smem) {
+  constexpr bool VSMEM = false;
   // the local CSR goes to shared memory when that keeps the occupancy
   const size_t b0 = kry_smem_bytes<TV>(c->p.r, c->p.max_cluster, c->p.max_hnbr, VSMEM, false);
   const size_t b1 = kry_smem_bytes<TV>(c->p.r, c->p.max_cluster, c->p.max_hnbr, VSMEM, true);
   if ((int)b0 > max_smem) return TB_ERR_CAPACITY;
   if (c->p.max_cluster > 4 * KT) return TB_ERR_CAPACITY;   // block scan: 4 slots per thread
-  if (FUSED) {   // the eigensolve workspace must fit where the basis was
-    const size_t basis = sizeof(TV) * 4 * (size_t)c->p.max_cluster * 4 * c->p.r;
-    if (sizeof(float) * tbtail::tail_floats(4 * c->p.r) > basis) return TB_ERR_CAPACITY;
-  }
   const size_t bmax = (int)b1 <= max_smem ? b1 : b0;
-  TB_CUDA_TRY(cudaFuncSetAttribute(krylov_kernel<TV, VSMEM, FUSED, KT>,
+  TB_CUDA_TRY(cudaFuncSetAttribute(krylov_kernel<TV, KT>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bmax));
   int occ = 0, occ1 = 0;
   TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &occ, krylov_kernel<TV, VSMEM, FUSED, KT>, KT, b0));
+      &occ, krylov_kernel<TV, KT>, KT, b0));
   if (occ < 1) return TB_ERR_CAPACITY;
   if (bmax == b1)
     TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ1, krylov_kernel<TV, VSMEM, FUSED, KT>, KT, b1));
+        &occ1, krylov_kernel<TV, KT>, KT, b1));
   c->kry_lsmem = occ1 >= occ;
   const size_t bytes = c->kry_lsmem ? b1 : b0;
   c->kry_smem = bytes;
-  c->kry_vsmem = VSMEM;
-  c->kry_fused = FUSED;
   c->kry_threads = KT;
   c->kry_grid = c->num_sms * occ;
   return TB_OK;
@@ -853,13 +809,15 @@ tb_status configure_t(tb_ctx* c, int max_smem) {
 }  // namespace
 
 bool krylov_eig_persistent(const tb_ctx* c, int n) {
+  if (!c->ke_on || c->p.prec != TB_PREC_MIXED) return false;
+  if (c->p.schedule == TB_SCHED_PERSISTENT) return true;
+  if (c->p.schedule == TB_SCHED_SEPARATE) return false;
   // the queue pays off where the targets fill a few waves of CTAs and the last
   // wave would leave SMs idle; many waves leave a negligible tail
-  return c->ke_on && c->p.prec == TB_PREC_MIXED && n <= 16 * c->ke_grid;
+  return n <= 16 * c->ke_grid;
 }
 
 size_t krylov_basis_bytes_global(const tb_ctx* c) {
-  if (c->kry_vsmem) return 0;
   const size_t tv = c->p.prec == TB_PREC_FP64 ? sizeof(double) : sizeof(float);
   return (size_t)c->kry_grid * 4 * c->p.max_cluster * 4 * c->p.r * tv;
 }
@@ -868,52 +826,35 @@ tb_status krylov_configure(tb_ctx* c) {
   int dev = 0, max_smem = 0;
   TB_CUDA_TRY(cudaGetDevice(&dev));
   TB_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  // Default: 128-thread CTAs with the basis in a per-CTA slot of global memory
-  // (L2-resident; four targets in flight per SM instead of two), and the
-  // projected eigensolve in the warp-per-target eigensolver kernel.
-  // Alternatives, for comparison and tests: TB_KRYLOV_WIDE (256 threads, basis
-  // in shared memory), TB_EIG_FUSED (256 threads, eigensolve inside the
-  // Krylov kernel in the shared memory the basis used).
-  // (the grouped form runs the separate eigensolver, so it keeps that one configured)
-  const bool fused = getenv("TB_EIG_FUSED") != nullptr && c->p.group_m == 1;
-  const bool wide = getenv("TB_KRYLOV_WIDE") != nullptr;
+  // 128-thread CTAs with the basis in a per-CTA slot of global memory
+  // (L2-resident; four or five targets in flight per SM), 256 threads when
+  // the 128-thread form does not fit; the projected eigensolve in the group
+  // eigensolver, inside the Krylov launch (persistent queue) or after it.
   if (c->p.prec == TB_PREC_FP64) {
-    if (fused && configure_t<double, true, true, 256>(c, max_smem) == TB_OK) return TB_OK;
-    if (wide && configure_t<double, true, false, 256>(c, max_smem) == TB_OK) return TB_OK;
-    if (configure_t<double, false, false, 128>(c, max_smem) == TB_OK) return TB_OK;
-    return configure_t<double, false, false, 256>(c, max_smem);
+    if (configure_t<double, 128>(c, max_smem) == TB_OK) return TB_OK;
+    return configure_t<double, 256>(c, max_smem);
   }
-  if (fused && configure_t<float, true, true, 256>(c, max_smem) == TB_OK) return TB_OK;
-  if (wide && configure_t<float, true, false, 256>(c, max_smem) == TB_OK) return TB_OK;
-  if (configure_t<float, false, false, 128>(c, max_smem) == TB_OK) {
-    // default of the mixed path: the persistent Krylov + eigensolve kernel
-    // (TB_NO_PERSIST: separate Krylov and eigensolver launches, for comparison)
+  if (configure_t<float, 128>(c, max_smem) == TB_OK) {
+    // the persistent Krylov + eigensolve kernel, unless separate launches
+    // are asked for (the grouped form runs the separate eigensolver)
     c->ke_on = false;
-    if (c->p.group_m == 1 && getenv("TB_NO_PERSIST") == nullptr &&
+    if (c->p.group_m == 1 && c->p.schedule != TB_SCHED_SEPARATE &&
         kry_eig_configure(c, max_smem) != TB_OK)
       c->ke_on = false;
     return TB_OK;
   }
-  return configure_t<float, false, false, 256>(c, max_smem);
+  return configure_t<float, 256>(c, max_smem);
 }
 
 tb_status launch_krylov(tb_ctx* c, int n, const int* c_off, const int* c_idx,
                         const int* h_off, const int* h_idx, const double* Hblk,
                         const float* Hmir, double* lambda, double* S, double* P, int* kdim,
                         cudaStream_t s) {
-#define TB_KRY_DISPATCH(TV, H)                                                                  \
-  do {                                                                                          \
-    if (c->kry_fused)                                                                           \
-      return launch_t<TV, true, true, 256>(c, n, c_off, c_idx, h_off, h_idx, H, lambda, S, P,   \
-                                           kdim, s);                                            \
-    if (c->kry_vsmem)                                                                           \
-      return launch_t<TV, true, false, 256>(c, n, c_off, c_idx, h_off, h_idx, H, lambda, S, P,  \
-                                            kdim, s);                                           \
-    if (c->kry_threads == 128)                                                                  \
-      return launch_t<TV, false, false, 128>(c, n, c_off, c_idx, h_off, h_idx, H, lambda, S, P, \
-                                             kdim, s);                                          \
-    return launch_t<TV, false, false, 256>(c, n, c_off, c_idx, h_off, h_idx, H, lambda, S, P,   \
-                                           kdim, s);                                            \
+#define TB_KRY_DISPATCH(TV, H)                                                                \
+  do {                                                                                        \
+    if (c->kry_threads == 128)                                                                \
+      return launch_t<TV, 128>(c, n, c_off, c_idx, h_off, h_idx, H, lambda, S, P, kdim, s);   \
+    return launch_t<TV, 256>(c, n, c_off, c_idx, h_off, h_idx, H, lambda, S, P, kdim, s);     \
   } while (0)
   if (c->p.prec == TB_PREC_FP64) TB_KRY_DISPATCH(double, Hblk);
   if (!Hmir) return TB_ERR_INVALID_ARG;

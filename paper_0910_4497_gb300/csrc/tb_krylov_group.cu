@@ -876,13 +876,10 @@ tb_status krylov_group_configure(tb_ctx* c) {
   int dev = 0, max_smem = 0;
   TB_CUDA_TRY(cudaGetDevice(&dev));
   TB_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  // Default: 512 threads for groups of up to four in FP32 (the FP64 kernel
-  // would spill at 128 registers), else 256; the staged copy of V_k when it
-  // fits.  TB_GROUP_THREADS (256 / 512) and
-  // TB_GROUP_NOSTAGE override, for comparison.
-  int kt = (p.group_m > 2 && p.prec == TB_PREC_MIXED) ? 512 : 256;
-  if (const char* e = getenv("TB_GROUP_THREADS")) kt = atoi(e) == 512 ? 512 : 256;
-  const bool nostage = getenv("TB_GROUP_NOSTAGE") != nullptr;
+  // 512 threads for groups of up to four in FP32 (the FP64 kernel would
+  // spill at 128 registers), else 256; the staged copy of V_k when it fits.
+  const int kt = (p.group_m > 2 && p.prec == TB_PREC_MIXED) ? 512 : 256;
+  const bool nostage = false;
   if (p.prec == TB_PREC_FP64)
     return p.group_m > 2 ? kryg_configure_mc<double, 4>(c, max_smem, kt, nostage)
                          : kryg_configure_mc<double, 2>(c, max_smem, kt, nostage);

@@ -1,0 +1,594 @@
+// Block Lanczos of one target atom for the mixed path (Sec. 3, Eq. (Krylov)
+// and the block form of Eqs. (lanczos) / (lanczos_blas3)), on the cluster
+// Hamiltonian H_c of Sec. 2 given as Slater-Koster records.
+//
+// The 4x4 block of a directed bond i -> j is fixed by the distance scaling
+// s(|d|) and the direction l = d/|d| (d = R_j - R_i) through the table of
+// Eq. (1); the sweep applies it to a 4-vector u = (u_s, u_p) without forming
+// it:
+//   (H u)_s = s [Vss u_s + Vsp (l.u_p)]
+//   (H u)_p = l s [(Vpps - Vppp)(l.u_p) - Vsp u_s] + s Vppp u_p
+// so a target's in-cluster bonds cost one 16-byte record each (8 bytes in
+// BF16), staged in shared memory once per target, instead of a 64-byte block
+// read from L2 in every sweep.
+//
+// Layout: every block of the Krylov basis (and W) is stored slot-major with
+// the 4x4 block of cluster slot s transposed, [s][c][b] = V[4s + b][c], so
+// that one thread per (slot s, column c) reads the neighbour's column c as
+// one float4.  Items are (s, c) = 4s + c; the four columns of a slot are
+// neighbouring lanes of one warp.
+//
+// Per step k (V_k, V_{k-1} and W rotate through three shared-memory buffers;
+// every block is also written to the CTA's basis slot in global memory for
+// the full reorthogonalisations and the output rows):
+//   W = H_c V_k - V_{k-1} B_{k-1}^T              sweep
+//   C = Q^T W, W -= Q C                          classical Gram-Schmidt against
+//                                                Q = [V_b0..V_k] (all blocks every
+//                                                reorth_every steps, else the last
+//                                                two); the V_k part of C is A_k
+//   W = V_{k+1} B_k                               Cholesky QR (twice unless the
+//                                                first factor shows a well-
+//                                                conditioned block), modified
+//                                                Gram-Schmidt with deflation
+//                                                when a pivot is refused
+// T is written compactly: per target the 2r - 1 blocks A_0, B_0, A_1, ...
+#pragma once
+#include <cuda_bf16.h>
+#include "tb_internal.cuh"
+#include "tb_krylov_common.cuh"
+
+namespace tbsk {
+
+using namespace tbkry;
+
+constexpr int KT = 128;                 // threads per target
+constexpr int KW = KT / 32;
+constexpr int FL_MASK = 0, FL_ACT = 2, FL_OK = 3, FL_OVER = 4;
+
+struct SkArgs {
+  int n, r, max_cluster, max_hnbr, reorth_passes, reorth_every;
+  int ecap;                             // local entries kept in shared memory
+  float Es, Ep, Vss, Vsp, Cpp, Vppp;    // Cpp = Vpps - Vppp
+  double defl_tol;
+  const int* c_off;
+  const int* c_idx;
+  const int* h_off;
+  const int* h_idx;
+  const float4* Hsk;                    // (s, l_x, l_y, l_z) per directed bond
+  double* T;                            // compact block tridiagonal, tc_doubles(r) per target
+  float* Y;
+  unsigned long long* colmask;
+  float* Vg;                            // per-CTA basis slots: r blocks of 16 max_cluster
+  void* recg;                           // per-CTA overflow records: max_cluster * max_hnbr
+  int* rslg;                            // and their neighbour offsets
+  int* st;
+};
+
+__host__ __device__ __forceinline__ size_t al32(size_t x) { return (x + 31) & ~size_t(31); }
+
+template <bool BF>
+__host__ __device__ inline size_t sk_rec_bytes() { return BF ? 8 : 16; }
+
+// Shared memory of one target (bytes).
+template <bool BF>
+__host__ __device__ inline size_t sk_smem_bytes(int r, int max_cluster, int ecap) {
+  const size_t MC = (size_t)max_cluster;
+  size_t b = 0;
+  b += al32(sizeof(int) * MC);                       // cl
+  b += al32(sizeof(int) * (MC + 1));                 // roff
+  b += 3 * al32(sizeof(float) * 16 * MC);            // V_k, V_{k-1}, W
+  if (BF) b += al32(sizeof(uint2) * 4 * MC);         // BF16 copy of V_k for the sweep
+  b += al32(sk_rec_bytes<BF>() * (size_t)ecap);      // records
+  b += al32(sizeof(int) * (size_t)ecap);             // neighbour offsets
+  const int np = r > KW ? r : KW;
+  b += al32(sizeof(float) * 16 * np);                // projection partials
+  b += al32(sizeof(float) * 16 * r);                 // projection coefficients
+  b += al32(sizeof(float) * 16 * 3);                 // B_{k-1}, R, R^-1
+  b += al32(sizeof(float) * 16 * KW);                // reduction scratch
+  b += al32(sizeof(double) * 32);                    // B_k, first Cholesky factor
+  b += al32(sizeof(int) * 8);                        // flags
+  return b;
+}
+
+__device__ __forceinline__ uint2 pack_bf16x4(float4 v) {
+  const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+  const __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
+  return make_uint2(*reinterpret_cast<const unsigned*>(&a), *reinterpret_cast<const unsigned*>(&b));
+}
+__device__ __forceinline__ float4 unpack_bf16x4(uint2 u) {
+  return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                     __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+}
+
+__device__ __forceinline__ float4 f4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void sf4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float dot4(float4 a, float4 b) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+__device__ __forceinline__ float4 axpy4(float a, float4 x, float4 y) {   // y + a x
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ float comp(float4 v, int q) {
+  return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ int find_slot(const int* cl, int nc, int b) {
+  if (b == cl[0]) return 0;
+  int lo = 1, hi = nc;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (cl[mid] < b) lo = mid + 1; else hi = mid;
+  }
+  return (lo < nc && cl[lo] == b) ? lo : -1;
+}
+
+// Exclusive scan of v[0..m) in place (m <= 8 KT), v[m] = total; all threads.
+__device__ __forceinline__ void block_scan(int* v, int m, int* wtot) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (m + KT - 1) / KT;
+  const int s0 = min(m, tid * per), s1 = min(m, s0 + per);
+  int loc = 0;
+  for (int s = s0; s < s1; ++s) loc += v[s];
+  int inc = loc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wtot[warp] = inc;
+  __syncthreads();
+  int base = 0;
+#pragma unroll
+  for (int w = 0; w < KW; ++w) base += w < warp ? wtot[w] : 0;
+  int run = base + inc - loc;
+  for (int s = s0; s < s1; ++s) {
+    const int t = v[s];
+    v[s] = run;
+    run += t;
+  }
+  if (tid == KT - 1) v[m] = run;
+  __syncthreads();
+}
+
+// Compact T: block 2k = A_k, block 2k+1 = B_k (T[4(k+1)+j][4k+c] = B_k[j][c]).
+__device__ __forceinline__ double* tc_block(double* Ti, int blk) { return Ti + 16 * blk; }
+
+template <bool BF>
+__device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
+  extern __shared__ __align__(32) unsigned char smem[];
+  using Rec = typename std::conditional<BF, uint2, float4>::type;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r = a.r, NT = 4 * r, MC = a.max_cluster;
+  const int np = r > KW ? r : KW;
+  size_t off = 0;
+  int* cl = reinterpret_cast<int*>(smem + off);       off += al32(sizeof(int) * MC);
+  int* roff = reinterpret_cast<int*>(smem + off);     off += al32(sizeof(int) * (MC + 1));
+  float* buf[3];
+  for (int q = 0; q < 3; ++q) {
+    buf[q] = reinterpret_cast<float*>(smem + off);    off += al32(sizeof(float) * 16 * MC);
+  }
+  uint2* vbf = nullptr;
+  if (BF) { vbf = reinterpret_cast<uint2*>(smem + off); off += al32(sizeof(uint2) * 4 * MC); }
+  Rec* rec_s = reinterpret_cast<Rec*>(smem + off);    off += al32(sizeof(Rec) * (size_t)a.ecap);
+  int* rsl_s = reinterpret_cast<int*>(smem + off);    off += al32(sizeof(int) * (size_t)a.ecap);
+  float* Cp = reinterpret_cast<float*>(smem + off);   off += al32(sizeof(float) * 16 * np);
+  float* Cc = reinterpret_cast<float*>(smem + off);   off += al32(sizeof(float) * 16 * r);
+  float* Bp = reinterpret_cast<float*>(smem + off);
+  float* Rsh = Bp + 16;
+  float* Rish = Rsh + 16;                              off += al32(sizeof(float) * 48);
+  float* red = reinterpret_cast<float*>(smem + off);  off += al32(sizeof(float) * 16 * KW);
+  double* Bs = reinterpret_cast<double*>(smem + off);
+  double* R1s = Bs + 16;                              off += al32(sizeof(double) * 32);
+  int* flags = reinterpret_cast<int*>(smem + off);
+  float* const Vg = a.Vg + (size_t)blockIdx.x * r * 16 * MC;
+  const size_t gcap = (size_t)MC * a.max_hnbr;
+  const float Es = a.Es, Ep = a.Ep, Vss = a.Vss, Vsp = a.Vsp, Cpp = a.Cpp, Vppp = a.Vppp;
+  const float chol_rel = 1e-3f;
+  const double chol_abs = 1000.0 * a.defl_tol;
+  double* const Ti = a.T + (size_t)i * tc_doubles(r);
+
+  const int c0 = a.c_off[i];
+  const int nc = a.c_off[i + 1] - c0;
+  if (nc < 1 || nc > MC || a.c_idx[c0] != i) {
+    if (tid == 0) {
+      tbk::set_status(a.st, TB_ERR_INVALID_ARG, i);
+      a.colmask[i] = 0ull;
+    }
+    __syncthreads();
+    return;
+  }
+  const int deg = a.h_off[i + 1] - a.h_off[i];
+  if (deg > a.max_hnbr) {
+    if (tid == 0) {
+      tbk::set_status(a.st, TB_ERR_CAPACITY, deg);
+      a.colmask[i] = 0ull;
+    }
+    __syncthreads();
+    return;
+  }
+  for (int s = tid; s < nc; s += KT) cl[s] = a.c_idx[c0 + s];
+  __syncthreads();
+  // ---- local sparsity of H_c: per slot, its in-cluster Hamiltonian
+  // neighbours in list order (count, scan, fill), each as a record and the
+  // neighbour block's offset; the records go to shared memory when they fit,
+  // else to the CTA's overflow slot
+  for (int s = tid; s < nc; s += KT) {
+    const int at = cl[s];
+    const int pe = min(a.h_off[at + 1], a.h_off[at] + a.max_hnbr);
+    int e = 0;
+    for (int p = a.h_off[at]; p < pe; ++p) e += find_slot(cl, nc, a.h_idx[p]) >= 0;
+    roff[s] = e;
+  }
+  __syncthreads();
+  block_scan(roff, nc, flags + 8 - KW);                // wtot scratch: the last flag words
+  const int ne = roff[nc];
+  Rec* rec = rec_s;
+  int* rsl = rsl_s;
+  if (ne > a.ecap) {
+    rec = reinterpret_cast<Rec*>(a.recg) + (size_t)blockIdx.x * gcap;
+    rsl = a.rslg + (size_t)blockIdx.x * gcap;
+  }
+  for (int s = tid; s < nc; s += KT) {
+    const int at = cl[s];
+    const int pe = min(a.h_off[at + 1], a.h_off[at] + a.max_hnbr);
+    int e = roff[s];
+    for (int p = a.h_off[at]; p < pe; ++p) {
+      const int t = find_slot(cl, nc, a.h_idx[p]);
+      if (t >= 0) {
+        const float4 hv = __ldg(a.Hsk + p);
+        if constexpr (BF) rec[e] = pack_bf16x4(hv);
+        else rec[e] = hv;
+        rsl[e] = 16 * t;
+        ++e;
+      }
+    }
+  }
+  // seed block V_1 = E_i: slot 0 holds the identity
+  float* Vk = buf[0];
+  float* Vkm1 = buf[1];
+  float* W = buf[2];
+  for (int q = tid; q < 16 * nc; q += KT) {
+    const float v = (q < 16 && (q >> 2) == (q & 3)) ? 1.f : 0.f;
+    Vk[q] = v;
+    Vg[q] = v;
+  }
+  if constexpr (BF) {
+    for (int q = tid; q < 4 * nc; q += KT)
+      vbf[q] = pack_bf16x4(make_float4(q < 4 && q == 0 ? 1.f : 0.f, q == 1 ? 1.f : 0.f,
+                                       q == 2 ? 1.f : 0.f, q == 3 ? 1.f : 0.f));
+  }
+  if (tid < 16) Bp[tid] = 0.f;
+  if (tid == 0) { flags[FL_MASK] = 0xF; flags[FL_MASK + 1] = 0; flags[FL_ACT] = 0xF; }
+  __syncthreads();
+  if (tid == 0 && roff[1] - roff[0] != deg) tbk::set_status(a.st, TB_ERR_INVALID_ARG, i);
+
+  const int D4 = 4 * nc;                 // items (slot, column)
+  int nblocks = 1;
+  for (int k = 0; k < r; ++k) {
+    // ---- W = H_c V_k - V_{k-1} B_{k-1}^T, item (s, c)
+    for (int it = tid; it < D4; it += KT) {
+      const int s = it >> 2, c = it & 3;
+      const float4 u0 = f4(Vk + 16 * s + 4 * c);
+      float4 acc = make_float4(Es * u0.x, Ep * u0.y, Ep * u0.z, Ep * u0.w);
+      const int e1 = roff[s + 1];
+#pragma unroll 2
+      for (int e = roff[s]; e < e1; ++e) {
+        float4 hv, u;
+        if constexpr (BF) {
+          hv = unpack_bf16x4(rec[e]);
+          u = unpack_bf16x4(vbf[(rsl[e] >> 2) + c]);
+        } else {
+          hv = rec[e];
+          u = f4(Vk + rsl[e] + 4 * c);
+        }
+        const float dt = fmaf(hv.y, u.y, fmaf(hv.z, u.z, hv.w * u.w));
+        const float ps = fmaf(Vss, u.x, Vsp * dt);
+        const float pp = fmaf(Cpp, dt, -Vsp * u.x);
+        acc.x = fmaf(hv.x, ps, acc.x);
+        const float t = hv.x * pp, w = hv.x * Vppp;
+        acc.y = fmaf(hv.y, t, fmaf(w, u.y, acc.y));
+        acc.z = fmaf(hv.z, t, fmaf(w, u.z, acc.z));
+        acc.w = fmaf(hv.w, t, fmaf(w, u.w, acc.w));
+      }
+      if (k > 0) {
+        const float4 b = f4(Bp + 4 * c);            // B_{k-1}[c][d], d >= c
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+          const float bd = comp(b, d);
+          if (d >= c) acc = axpy4(-bd, f4(Vkm1 + 16 * s + 4 * d), acc);
+        }
+      }
+      sf4(W + 16 * s + 4 * c, acc);
+    }
+    __syncthreads();
+    // ---- classical Gram-Schmidt (pass 0 yields A_k); the last step needs
+    // only A_k; between full passes only V_{k-1} and V_k are projected out
+    const int passes = (k == r - 1) ? 1 : a.reorth_passes;
+    float g[4] = {0.f, 0.f, 0.f, 0.f};                 // Gram row c of the final W
+    for (int pass = 0; pass < passes; ++pass) {
+      const bool full = a.reorth_every <= 1 || (k % a.reorth_every) == a.reorth_every - 1;
+      const int b0 = (k == r - 1) ? k : (full ? 0 : (k > 0 ? k - 1 : 0));
+      const int nb = k + 1 - b0;
+      auto blk = [&](int b) -> const float* {
+        return b == k ? Vk : (b == k - 1 ? Vkm1 : Vg + (size_t)b * 16 * MC);
+      };
+      const int nseg = nb >= KW ? 1 : KW / nb;
+      const int items = nb * nseg;
+      for (int w = warp; w < items; w += KW) {
+        const int b = b0 + w / nseg, seg = w % nseg;
+        const int slo = (nc * seg) / nseg, shi = (nc * (seg + 1)) / nseg;
+        const float* Vb = blk(b);
+        float acc[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+        for (int s = slo + lane; s < shi; s += 32) {
+          float4 v[4], x[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) { v[q] = f4(Vb + 16 * s + 4 * q); x[q] = f4(W + 16 * s + 4 * q); }
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[ii * 4 + c] += dot4(v[ii], x[c]);
+        }
+        const float tot = tbk::warp_reduce16(acc, lane);
+        if ((lane & 1) == 0) Cp[w * 16 + (lane >> 1)] = tot;
+      }
+      __syncthreads();
+      // coefficients of block b, stored by column: Cc[b][c][ii] = (V_b^T W)[ii][c]
+      for (int t = tid; t < nb * 16; t += KT) {
+        const int bl = t >> 4, q = t & 15;
+        float sum = 0.f;
+        for (int sg = 0; sg < nseg; ++sg) sum += Cp[(bl * nseg + sg) * 16 + q];
+        Cc[(b0 + bl) * 16 + (q & 3) * 4 + (q >> 2)] = sum;
+      }
+      __syncthreads();
+      if (pass == 0 && tid < 16) {                     // A_k = V_k^T H V_k, symmetrised
+        const int ii = tid >> 2, c = tid & 3;
+        tc_block(Ti, 2 * k)[tid] =
+            0.5 * ((double)Cc[k * 16 + c * 4 + ii] + (double)Cc[k * 16 + ii * 4 + c]);
+      }
+      if (k == r - 1) break;
+      const bool last = pass == passes - 1;
+      // W -= sum_b V_b C_b; on the last pass the Gram matrix of the result
+      for (int base = warp * 32; base < D4; base += KT) {
+        const int it = base + lane;
+        const bool on = it < D4;
+        const int s = on ? it >> 2 : 0, c = it & 3;
+        float4 x = on ? f4(W + 16 * s + 4 * c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int b = b0; b <= k; ++b) {
+          const float* Vb = blk(b);
+          const float4 cf = f4(Cc + b * 16 + 4 * c);
+          x = axpy4(-cf.x, f4(Vb + 16 * s), x);
+          x = axpy4(-cf.y, f4(Vb + 16 * s + 4), x);
+          x = axpy4(-cf.z, f4(Vb + 16 * s + 8), x);
+          x = axpy4(-cf.w, f4(Vb + 16 * s + 12), x);
+        }
+        if (on) sf4(W + 16 * s + 4 * c, x);
+        if (last) {
+          __syncwarp();
+          if (on) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (e > c) g[e] += dot4(x, f4(W + 16 * s + 4 * e));
+            g[c] += dot4(x, x);
+          }
+        }
+      }
+      if (!last) __syncthreads();
+    }
+    if (k == r - 1) break;
+    // ---- in-block QR: W = V_{k+1} B_k
+    // chol_state: 0 Cholesky accepted, 1 first factor refused (W untouched),
+    // 2 second factor refused (the first one applied)
+    int chol_state = 0;
+    bool single = false;
+    float* src = W;
+    float* dst = Vkm1;                                 // free after the projections
+    for (int cq = 0; cq < 2; ++cq) {
+      float gv[16];
+      const int c = tid & 3;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) gv[q] = ((q >> 2) == c && (q & 3) >= c) ? g[q & 3] : 0.f;
+      const float tot = tbk::warp_reduce16(gv, lane);
+      if ((lane & 1) == 0) red[warp * 16 + (lane >> 1)] = tot;
+      __syncthreads();
+      if (warp == 0) {                                 // uniform over the warp
+        float G[16], R[16], Ri[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          float sum = 0.f;
+#pragma unroll
+          for (int w = 0; w < KW; ++w) sum += red[w * 16 + q];
+          G[q] = sum;
+        }
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+          for (int e = 0; e < cc; ++e) G[cc * 4 + e] = G[e * 4 + cc];
+        bool well;
+        const bool ok = chol4(G, R, chol_rel, cq == 0 ? chol_abs : 0.0, well);
+        triinv4(R, Ri);
+        if (lane < 16) { Rsh[lane] = R[lane]; Rish[lane] = Ri[lane]; }
+        if (lane == 0) {
+          flags[FL_OK] = (ok ? 1 : 0) | (well ? 2 : 0);
+          if (cq == 0) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) R1s[q] = (double)R[q];
+          }
+        }
+      }
+      __syncthreads();
+      const int fl = flags[FL_OK];
+      if (!(fl & 1)) { chol_state = cq + 1; break; }
+      single = cq == 0 && (fl & 2);
+      const bool fin = single || cq == 1;
+      float ri[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) ri[q] = Rish[q];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) g[q] = 0.f;
+      float* const out = cq == 0 ? dst : W;
+      for (int base = warp * 32; base < D4; base += KT) {
+        const int it = base + lane;
+        const bool on = it < D4;
+        const int s = on ? it >> 2 : 0;
+        const float* xs = (cq == 0 ? src : dst) + 16 * s;
+        float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (j <= c) y = axpy4(ri[j * 4 + c], f4(xs + 4 * j), y);
+        __syncwarp();                                  // every lane has read its slot
+        if (on) {
+          sf4(out + 16 * s + 4 * c, y);
+          if (fin) {
+            sf4(Vg + (size_t)(k + 1) * 16 * MC + 16 * s + 4 * c, y);
+            if constexpr (BF) vbf[4 * s + c] = pack_bf16x4(y);
+          }
+        }
+        if (!fin) {                                    // Gram matrix for the second factor
+          __syncwarp();
+          if (on) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (e > c) g[e] += dot4(y, f4(out + 16 * s + 4 * e));
+            g[c] += dot4(y, y);
+          }
+        }
+      }
+      if (fin) break;
+    }
+    // V_{k+1} is in dst after one factor (or MGS on W), in W after two
+    float* Vn = (chol_state == 1 || (chol_state == 0 && single)) ? dst : W;
+    int act = 0xF;
+    if (chol_state != 0) {
+      // modified Gram-Schmidt by warp 0 on the columns of the last written
+      // block, a column dropped when its norm is <= defl_tol
+      float* S = chol_state == 1 ? W : dst;
+      float* O = chol_state == 1 ? dst : W;
+      __syncthreads();
+      if (warp == 0) {
+        double R[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) R[q] = 0.0;
+        int mact = 0;
+        bool nonfinite = false;
+        auto at = [](int row, int col) { return (row >> 2) * 16 + col * 4 + (row & 3); };
+        for (int c = 0; c < 4; ++c) {
+          for (int ps = 0; ps < 2 && c > 0; ++ps) {
+            float dd[3] = {0.f, 0.f, 0.f};
+            for (int row = lane; row < D4; row += 32) {
+              const float w = S[at(row, c)];
+#pragma unroll
+              for (int j = 0; j < 3; ++j) if (j < c) dd[j] += O[at(row, j)] * w;
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j) if (j < c) dd[j] = tbk::warp_sum(dd[j]);
+            for (int row = lane; row < D4; row += 32) {
+              float w = S[at(row, c)];
+#pragma unroll
+              for (int j = 0; j < 3; ++j) if (j < c) w -= dd[j] * O[at(row, j)];
+              S[at(row, c)] = w;
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j) if (j < c) R[j * 4 + c] += (double)dd[j];
+          }
+          float nn = 0.f;
+          for (int row = lane; row < D4; row += 32) {
+            const float w = S[at(row, c)];
+            nn += w * w;
+          }
+          nn = tbk::warp_sum(nn);
+          const double nrm = sqrt((double)nn);
+          if (!isfinite(nrm)) nonfinite = true;
+          const bool keep = nrm > a.defl_tol;
+          const float inv = keep ? (float)(1.0 / nrm) : 0.f;
+          for (int row = lane; row < D4; row += 32) O[at(row, c)] = S[at(row, c)] * inv;
+          if (keep) { R[c * 4 + c] = nrm; mact |= 1 << c; }
+          __syncwarp();
+        }
+        // copies of V_{k+1}: the basis slot and (BF16) the sweep's copy
+        for (int q = lane; q < 16 * nc; q += 32) Vg[(size_t)(k + 1) * 16 * MC + q] = O[q];
+        if constexpr (BF) {
+          for (int q = lane; q < 4 * nc; q += 32) vbf[q] = pack_bf16x4(f4(O + 4 * q));
+        }
+        if (lane == 0) {
+          if (chol_state == 2) {                       // S was W R1^-1: B_k = R_mgs R1
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                double t = 0.0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) t += R[rr * 4 + j] * R1s[j * 4 + c];
+                Bs[rr * 4 + c] = t;
+              }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) Bs[q] = R[q];
+          }
+          flags[FL_ACT] = mact;
+          if (nonfinite) tbk::set_status(a.st, TB_ERR_NONFINITE, i);
+        }
+      }
+      Vn = O;
+      __syncthreads();
+      act = flags[FL_ACT];
+    } else if (tid < 16) {                             // B_k = R (one factor) or R2 R1
+      const int j = tid >> 2, c = tid & 3;
+      double t;
+      if (single) {
+        t = (double)Rsh[tid];
+      } else {
+        t = 0.0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) t += (double)Rsh[j * 4 + m] * R1s[m * 4 + c];
+      }
+      Bs[tid] = t;
+    }
+    __syncthreads();                                   // Bs complete
+    if (tid < 16) {
+      tc_block(Ti, 2 * k + 1)[tid] = Bs[tid];
+      Bp[tid] = (float)Bs[tid];
+    }
+    if (tid == 0) {
+      unsigned long long mask = ((unsigned long long)(unsigned)flags[FL_MASK + 1] << 32) |
+                                (unsigned)flags[FL_MASK];
+      mask |= (unsigned long long)act << (4 * (k + 1));
+      flags[FL_MASK] = (int)(mask & 0xffffffffull);
+      flags[FL_MASK + 1] = (int)(mask >> 32);
+      if (!isfinite(Bs[0] + Bs[5] + Bs[10] + Bs[15])) tbk::set_status(a.st, TB_ERR_NONFINITE, i);
+    }
+    __syncthreads();
+    // rotate: V_{k+1} becomes V_k, V_k becomes V_{k-1}, the third buffer W
+    {
+      float* o0 = Vk;
+      float* o1 = Vkm1;
+      float* o2 = W;
+      Vkm1 = o0;
+      Vk = Vn;
+      W = (Vn == o1) ? o2 : o1;
+    }
+    if (act == 0) break;
+    nblocks = k + 2;
+  }
+  // ---- outputs: column mask, rows of V for the target and its H neighbours
+  if (tid == 0)
+    a.colmask[i] = ((unsigned long long)(unsigned)flags[FL_MASK + 1] << 32) | (unsigned)flags[FL_MASK];
+  {
+    const size_t ybase = (size_t)(i + a.h_off[i]) * 4;
+    const int nrows = (deg + 1) * 4;
+    const int rcnt = roff[1] - roff[0];
+    for (int q = tid; q < nrows * NT; q += KT) {
+      const int rr = q / NT, col = q - rr * NT;
+      const int qq = rr >> 2, beta = rr & 3;
+      const int so = qq == 0 ? 0 : (qq - 1 < rcnt ? rsl[roff[0] + qq - 1] : -1);
+      const int b = col >> 2, c = col & 3;
+      float val = 0.f;
+      if (b < nblocks && so >= 0) val = Vg[(size_t)b * 16 * MC + so + 4 * c + beta];
+      a.Y[(ybase + rr) * NT + col] = val;
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace tbsk

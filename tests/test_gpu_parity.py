@@ -219,23 +219,15 @@ def test_forces_bridged_uneven_clusters(tb):
     assert sizes.max() - sizes.min() >= 20
 
 
-@pytest.mark.parametrize("variant", ["TB_KRYLOV_WIDE", "TB_EIG_FUSED", "TB_NO_PERSIST"])
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_kernel_variants_match(tb, prec, variant):
-    """Default: 128-thread Krylov CTAs with the basis in global memory; in the
-    mixed path one persistent launch that queues the Krylov targets and then
-    the group eigensolves.  The alternatives (256 threads with the basis in
-    shared memory; the eigensolve fused into the Krylov CTA; separate Krylov
-    and eigensolver launches) must give the same answers within the path's
-    tolerance, and match the oracle."""
+@pytest.mark.parametrize("schedule", ["persistent", "separate"])
+def test_schedules_match(tb, schedule):
+    """Mixed path: one persistent launch that queues the Krylov targets and
+    then the group eigensolves, or separate Krylov and eigensolver launches:
+    the same answers within the path's tolerance, and the oracle's."""
     pos, L, p = cfg_system(0)
-    os.environ[variant] = "1"
-    try:
-        s_alt, _ = compare_full(tb, "cfg0", pos, L, p, prec)
-    finally:
-        del os.environ[variant]
-    s_def, _ = compare_full(tb, "cfg0", pos, L, p, prec)
-    assert np.abs(s_alt.F.cpu().numpy() - s_def.F.cpu().numpy()).max() <= TOL[prec]["F"]
+    s_alt, _ = compare_full(tb, "cfg0", pos, L, dict(p, schedule=schedule), "mixed")
+    s_def, _ = compare_full(tb, "cfg0", pos, L, p, "mixed")
+    assert np.abs(s_alt.F.cpu().numpy() - s_def.F.cpu().numpy()).max() <= TOL["mixed"]["F"]
 
 
 def test_single_reorth_pass_within_tolerance(tb):
@@ -333,10 +325,6 @@ def test_kernels_per_evaluation_count(tb):
         counts[prec] = tb.binding.tb_ctx_kernels_per_evaluation(s.ctx, len(pos), L)
         s.close()
     assert counts == {"mixed": 14, "fp64": 16}
-    os.environ["TB_NO_PERSIST"] = "1"
-    try:
-        s = tb.TBSystem(len(pos), L, p, prec="mixed")
-        assert tb.binding.tb_ctx_kernels_per_evaluation(s.ctx, len(pos), L) == 15
-        s.close()
-    finally:
-        del os.environ["TB_NO_PERSIST"]
+    s = tb.TBSystem(len(pos), L, dict(p, schedule="separate"), prec="mixed")
+    assert tb.binding.tb_ctx_kernels_per_evaluation(s.ctx, len(pos), L) == 15
+    s.close()

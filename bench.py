@@ -385,7 +385,10 @@ def kernel_traffic(prec, name="krylov_traffic.json", workload=None):
         return None
     h = hashlib.sha256()
     for rel in rec.get("sources", []):
-        h.update(open(os.path.join(ROOT, rel), "rb").read())
+        src = os.path.join(ROOT, rel)
+        if not os.path.exists(src):           # a source of that kernel is gone: changed
+            return None
+        h.update(open(src, "rb").read())
     if not rec.get("sources") or rec.get("source_sha256") != h.hexdigest():
         return None
     return rec.get("dram_bytes_per_launch", {}).get(prec)

@@ -60,7 +60,12 @@ typedef enum tb_precision {
    * Rayleigh quotients on T in double-float arithmetic; mu (FP64 Newton, FP32
    * terms for pairs far from mu), density-matrix blocks, energies and forces
    * in FP64. */
-  TB_PREC_MIXED = 1
+  TB_PREC_MIXED = 1,
+  /* As TB_PREC_MIXED, with the H.V sweeps in BF16: the Slater-Koster records
+   * and the Krylov block V_k enter the sweep's products rounded to BF16
+   * (8-bit mantissa), the products accumulated in FP32.  Not available with
+   * the m-target form (group_m > 1). */
+  TB_PREC_BF16 = 2
 } tb_precision;
 
 /* Model and numerical parameters (all lengths A, energies eV). */
@@ -163,12 +168,16 @@ tb_status tb_build_neighbors(tb_ctx* ctx, int n, const double* pos, double L,
  *   dHblk[p*48 + k*16 + a*4 + b] = d H_{i a, j b} / d d_k
  *   (so dH/dR_i = -dHblk and dH/dR_j = +dHblk).
  * The on-site block diag(Es, Ep, Ep, Ep) is implicit (not stored).
- * Hmirror (optional, may be NULL): FP32 copy of Hblk, [p*16 + a*4 + b], used
- * by TB_PREC_MIXED.  Arrays sized by h_off[n] entries.
+ * Hsk (may be NULL for TB_PREC_FP64, required otherwise): the FP32
+ * Slater-Koster record of each directed bond, [p*4 + 0..3] =
+ * (s(|d|), l_x, l_y, l_z), from which the block is s(|d|) SK(l) with the
+ * context's Vss, Vsp, Vpps, Vppp; the mixed and BF16 paths sweep with these
+ * 16-byte records instead of the 128-byte FP64 blocks.  Arrays sized by
+ * h_off[n] entries.
  */
 tb_status tb_assemble_H(tb_ctx* ctx, int n, const double* pos, double L,
                         const int* h_off, const int* h_idx,
-                        double* Hblk, double* dHblk, float* Hmirror,
+                        double* Hblk, double* dHblk, float* Hsk,
                         void* stream);
 
 /*
@@ -184,11 +193,12 @@ tb_status tb_assemble_H(tb_ctx* ctx, int n, const double* pos, double L,
  *       in h_idx order; P needs (n + h_off[n]) * 4 * NT doubles
  *   kdim[i]                      int
  * Then rho_{(q) b, i a} = sum_m P[q,b,m] f((lam_m - mu)/kT) S[a,m].
- * Hmirror must be non-NULL when prec == TB_PREC_MIXED.
+ * TB_PREC_FP64 sweeps with Hblk; the other precisions with the records Hsk
+ * of tb_assemble_H (must be non-NULL), staged in shared memory per target.
  */
 tb_status tb_krylov_density(tb_ctx* ctx, int n, const int* c_off, const int* c_idx,
                             const int* h_off, const int* h_idx,
-                            const double* Hblk, const float* Hmirror,
+                            const double* Hblk, const float* Hsk,
                             double* lambda, double* S, double* P, int* kdim,
                             void* stream);
 
@@ -275,7 +285,7 @@ tb_status tb_group_atoms(tb_ctx* ctx, int n, const double* pos, double L, int* g
 tb_status tb_krylov_density_grouped(tb_ctx* ctx, int n, int n_groups, const int* g_off,
                                     const int* g_idx, const int* c_off, const int* c_idx,
                                     const int* h_off, const int* h_idx,
-                                    const double* Hblk, const float* Hmirror,
+                                    const double* Hblk, const float* Hsk,
                                     double* lambda, double* S, double* P, int* kdim,
                                     void* stream);
 

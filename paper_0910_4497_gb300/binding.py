@@ -19,6 +19,8 @@ STATUS_NAMES = {0: "TB_OK", 1: "TB_ERR_INVALID_ARG", 2: "TB_ERR_CUDA", 3: "TB_ER
                 7: "TB_ERR_NO_CONVERGENCE", 8: "TB_ERR_TIMEOUT", 9: "TB_ERR_NOT_RESERVED"}
 TB_PREC_FP64 = 0
 TB_PREC_MIXED = 1
+TB_PREC_BF16 = 2
+PRECISIONS = {"fp64": TB_PREC_FP64, "mixed": TB_PREC_MIXED, "bf16": TB_PREC_BF16}
 SCHEDULES = {"auto": 0, "persistent": 1, "separate": 2}
 
 EXPORTS = ["tb_params_default", "tb_ctx_create", "tb_ctx_destroy", "tb_ctx_reserve",
@@ -135,7 +137,7 @@ def make_params(p, prec):
     tp.r = int(p["r"])
     tp.max_hnbr = int(p.get("max_hnbr", 32))
     tp.max_cluster = int(p.get("max_cluster", 128))
-    tp.prec = TB_PREC_FP64 if prec in ("fp64", TB_PREC_FP64) else TB_PREC_MIXED
+    tp.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     tp.defl_tol = float(p.get("defl_tol", 1e-9 if tp.prec == TB_PREC_FP64 else 1e-4))
     tp.reorth_passes = int(p.get("reorth_passes", 2))
     tp.reorth_every = int(p.get("reorth_every", 1))
@@ -187,21 +189,21 @@ def tb_build_neighbors(ctx, n, pos, L, h_off, h_idx, c_off, c_idx, stream=None):
         _stream(stream)))
 
 
-def tb_assemble_H(ctx, n, pos, L, h_off, h_idx, Hblk, dHblk, Hmirror=None, stream=None):
+def tb_assemble_H(ctx, n, pos, L, h_off, h_idx, Hblk, dHblk, Hsk=None, stream=None):
     i32, f64 = torch.int32, torch.float64
     _check("tb_assemble_H", lib().tb_assemble_H(
         ctx, n, _ptr(pos, f64, "pos"), float(L), _ptr(h_off, i32, "h_off"),
         _ptr(h_idx, i32, "h_idx"), _ptr(Hblk, f64, "Hblk"), _ptr(dHblk, f64, "dHblk"),
-        _ptr(Hmirror, torch.float32, "Hmirror"), _stream(stream)))
+        _ptr(Hsk, torch.float32, "Hsk"), _stream(stream)))
 
 
-def tb_krylov_density(ctx, n, c_off, c_idx, h_off, h_idx, Hblk, Hmirror, lam, S, P, kdim,
+def tb_krylov_density(ctx, n, c_off, c_idx, h_off, h_idx, Hblk, Hsk, lam, S, P, kdim,
                       stream=None):
     i32, f64 = torch.int32, torch.float64
     _check("tb_krylov_density", lib().tb_krylov_density(
         ctx, n, _ptr(c_off, i32, "c_off"), _ptr(c_idx, i32, "c_idx"),
         _ptr(h_off, i32, "h_off"), _ptr(h_idx, i32, "h_idx"), _ptr(Hblk, f64, "Hblk"),
-        _ptr(Hmirror, torch.float32, "Hmirror"), _ptr(lam, f64, "lambda"),
+        _ptr(Hsk, torch.float32, "Hsk"), _ptr(lam, f64, "lambda"),
         _ptr(S, f64, "S"), _ptr(P, f64, "P"), _ptr(kdim, i32, "kdim"), _stream(stream)))
 
 
@@ -220,13 +222,13 @@ def tb_group_atoms(ctx, n, pos, L, g_off, g_idx, stream=None):
 
 
 def tb_krylov_density_grouped(ctx, n, n_groups, g_off, g_idx, c_off, c_idx, h_off, h_idx,
-                              Hblk, Hmirror, lam, S, P, kdim, stream=None):
+                              Hblk, Hsk, lam, S, P, kdim, stream=None):
     i32, f64 = torch.int32, torch.float64
     _check("tb_krylov_density_grouped", lib().tb_krylov_density_grouped(
         ctx, n, int(n_groups), _ptr(g_off, i32, "g_off"), _ptr(g_idx, i32, "g_idx"),
         _ptr(c_off, i32, "c_off"), _ptr(c_idx, i32, "c_idx"),
         _ptr(h_off, i32, "h_off"), _ptr(h_idx, i32, "h_idx"), _ptr(Hblk, f64, "Hblk"),
-        _ptr(Hmirror, torch.float32, "Hmirror"), _ptr(lam, f64, "lambda"),
+        _ptr(Hsk, torch.float32, "Hsk"), _ptr(lam, f64, "lambda"),
         _ptr(S, f64, "S"), _ptr(P, f64, "P"), _ptr(kdim, i32, "kdim"), _stream(stream)))
 
 

@@ -18,7 +18,9 @@ tb_status check_params(const tb_params& p) {
   if (!(p.kT > 0.0) || !(p.Rc >= p.rm) || !(p.rm > p.r1) || !(p.r1 > 0.0)) return TB_ERR_INVALID_ARG;
   if (!(p.r0 > 0.0) || !(p.rc > 0.0) || !(p.dc > 0.0) || !(p.d0 > 0.0)) return TB_ERR_INVALID_ARG;
   if (p.r < 1 || p.r > tbk::MAX_R) return TB_ERR_INVALID_ARG;
-  if (p.prec != TB_PREC_FP64 && p.prec != TB_PREC_MIXED) return TB_ERR_INVALID_ARG;
+  if (p.prec != TB_PREC_FP64 && p.prec != TB_PREC_MIXED && p.prec != TB_PREC_BF16)
+    return TB_ERR_INVALID_ARG;
+  if (p.prec == TB_PREC_BF16 && p.group_m > 1) return TB_ERR_INVALID_ARG;
   if (p.max_hnbr < 1 || p.max_hnbr > tbk::MAX_HNBR) return TB_ERR_INVALID_ARG;
   if (p.max_cluster < 1 || p.max_cluster > tbk::MAX_CLUSTER) return TB_ERR_INVALID_ARG;
   if (p.reorth_passes < 1 || p.reorth_passes > 2) return TB_ERR_INVALID_ARG;
@@ -62,13 +64,16 @@ size_t carve(tb_ctx* c, int n, unsigned char* base) {
   c->atom_cell = k.take<int>(n);
   c->pad_h = k.take<int>(hcap);
   c->pad_c = k.take<int>((size_t)n * p.max_cluster);
-  c->T = k.take<double>((size_t)n * NT * NT);
+  c->T = k.take<double>((size_t)n * tc_doubles(p.r));
   c->Y = k.take<unsigned char>(rows * 4 * NT * tv);
   c->colmask = k.take<unsigned long long>(n);
   c->Zf = k.take<float>((size_t)n * NT * NT);
   c->lamf = k.take<float>((size_t)n * NT);
   c->Vg = k.take<unsigned char>(krylov_basis_bytes_global(c));
-  c->lent = k.take<int2>((size_t)c->kry_grid * p.max_cluster * p.max_hnbr);
+  c->lent = k.take<int2>(p.prec == TB_PREC_FP64
+                             ? (size_t)c->kry_grid * p.max_cluster * p.max_hnbr : 0);
+  c->recg = k.take<float4>(krylov_overflow_records(c));
+  c->rslg = k.take<int>(krylov_overflow_records(c));
   c->ke_work = k.take<int>((size_t)n + 1);
   c->grp_V = k.take<unsigned char>(krylov_group_basis_bytes(c));
   c->grp_lent = k.take<int2>((size_t)c->grp_grid * c->grp_max_union * p.max_hnbr);
@@ -87,7 +92,7 @@ size_t carve(tb_ctx* c, int n, unsigned char* base) {
   c->c_idx = k.take<int>((size_t)n * p.max_cluster);
   c->Hblk = k.take<double>(hcap * 16);
   c->dHblk = k.take<double>(hcap * 48);
-  c->Hmir = k.take<float>(hcap * 16);
+  c->Hsk = k.take<float>(hcap * 4);
   c->lambda = k.take<double>((size_t)n * NT);
   c->S = k.take<double>((size_t)n * 4 * NT);
   c->P = k.take<double>(rows * 4 * NT);
@@ -255,21 +260,21 @@ tb_status tb_build_neighbors(tb_ctx* c, int n, const double* pos, double L, int*
 }
 
 tb_status tb_assemble_H(tb_ctx* c, int n, const double* pos, double L, const int* h_off,
-                        const int* h_idx, double* Hblk, double* dHblk, float* Hmirror,
+                        const int* h_idx, double* Hblk, double* dHblk, float* Hsk,
                         void* stream) {
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;
   if (n == 0) return TB_OK;
   if (!pos || !h_off || !h_idx || !Hblk || !dHblk || !(L > 0.0)) return TB_ERR_INVALID_ARG;
-  if (c->p.prec == TB_PREC_MIXED && !Hmirror) return TB_ERR_INVALID_ARG;
+  if (c->p.prec != TB_PREC_FP64 && !Hsk) return TB_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  TB_STAGE(c, 1, s, launch_assemble(c, n, pos, L, h_off, h_idx, Hblk, dHblk, Hmirror, s));
+  TB_STAGE(c, 1, s, launch_assemble(c, n, pos, L, h_off, h_idx, Hblk, dHblk, Hsk, s));
   return TB_OK;
 }
 
 tb_status tb_krylov_density(tb_ctx* c, int n, const int* c_off, const int* c_idx,
                             const int* h_off, const int* h_idx, const double* Hblk,
-                            const float* Hmirror, double* lambda, double* S, double* P,
+                            const float* Hsk, double* lambda, double* S, double* P,
                             int* kdim, void* stream) {
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;
@@ -277,9 +282,9 @@ tb_status tb_krylov_density(tb_ctx* c, int n, const int* c_off, const int* c_idx
   if (!c_off || !c_idx || !h_off || !h_idx || !lambda || !S || !P || !kdim)
     return TB_ERR_INVALID_ARG;
   if (c->p.prec == TB_PREC_FP64 && !Hblk) return TB_ERR_INVALID_ARG;
-  if (c->p.prec == TB_PREC_MIXED && !Hmirror) return TB_ERR_INVALID_ARG;
+  if (c->p.prec != TB_PREC_FP64 && !Hsk) return TB_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  TB_STAGE(c, 2, s, launch_krylov(c, n, c_off, c_idx, h_off, h_idx, Hblk, Hmirror, lambda, S,
+  TB_STAGE(c, 2, s, launch_krylov(c, n, c_off, c_idx, h_off, h_idx, Hblk, Hsk, lambda, S,
                                   P, kdim, s));
   TB_STAGE(c, 3, s, launch_eig(c, n, h_off, lambda, S, P, kdim, s));
   return TB_OK;
@@ -299,7 +304,7 @@ tb_status tb_group_atoms(tb_ctx* c, int n, const double* pos, double L, int* g_o
 tb_status tb_krylov_density_grouped(tb_ctx* c, int n, int n_groups, const int* g_off,
                                     const int* g_idx, const int* c_off, const int* c_idx,
                                     const int* h_off, const int* h_idx, const double* Hblk,
-                                    const float* Hmirror, double* lambda, double* S, double* P,
+                                    const float* Hsk, double* lambda, double* S, double* P,
                                     int* kdim, void* stream) {
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;
@@ -309,10 +314,10 @@ tb_status tb_krylov_density_grouped(tb_ctx* c, int n, int n_groups, const int* g
   if (!g_off || !g_idx || !c_off || !c_idx || !h_off || !h_idx || !lambda || !S || !P || !kdim)
     return TB_ERR_INVALID_ARG;
   if (c->p.prec == TB_PREC_FP64 && !Hblk) return TB_ERR_INVALID_ARG;
-  if (c->p.prec == TB_PREC_MIXED && !Hmirror) return TB_ERR_INVALID_ARG;
+  if (c->p.prec != TB_PREC_FP64 && !Hsk) return TB_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   TB_STAGE(c, 2, s, launch_krylov_grouped(c, n, n_groups, g_off, g_idx, c_off, c_idx, h_off,
-                                          h_idx, Hblk, Hmirror, s));
+                                          h_idx, Hblk, Hsk, s));
   TB_STAGE(c, 3, s, launch_eig(c, n, h_off, lambda, S, P, kdim, s));
   return TB_OK;
 }
@@ -357,14 +362,14 @@ tb_status tb_md_step(tb_ctx* c, int n, double* pos, double* vel, double* F, doub
   TB_STAGE(c, 0, s, launch_neighbors(c, n, pos, L, c->h_off, c->h_idx, c->c_off, c->c_idx, s));
   if (grouped) TB_STAGE(c, 6, s, launch_group_atoms(c, n, pos, L, c->grp_off, c->grp_idx, s));
   TB_STAGE(c, 1, s, launch_assemble(c, n, pos, L, c->h_off, c->h_idx, c->Hblk, c->dHblk,
-                                    c->p.prec == TB_PREC_MIXED ? c->Hmir : nullptr, s));
+                                    c->p.prec != TB_PREC_FP64 ? c->Hsk : nullptr, s));
   if (grouped) {
     const int G = (n + c->p.group_m - 1) / c->p.group_m;
     TB_STAGE(c, 2, s, launch_krylov_grouped(c, n, G, c->grp_off, c->grp_idx, c->c_off,
-                                            c->c_idx, c->h_off, c->h_idx, c->Hblk, c->Hmir, s));
+                                            c->c_idx, c->h_off, c->h_idx, c->Hblk, c->Hsk, s));
   } else {
     TB_STAGE(c, 2, s, launch_krylov(c, n, c->c_off, c->c_idx, c->h_off, c->h_idx, c->Hblk,
-                                    c->Hmir, c->lambda, c->S, c->P, c->kdim, s));
+                                    c->Hsk, c->lambda, c->S, c->P, c->kdim, s));
   }
   TB_STAGE(c, 3, s, launch_eig(c, n, c->h_off, c->lambda, c->S, c->P, c->kdim, s));
   TB_STAGE(c, 4, s, launch_mu(c, n, c->lambda, c->S, 4.0 * n, c->mu, c->mu, c->ncount, s));
@@ -462,7 +467,7 @@ tb_status tb_local_gradient(tb_ctx* c, int n, const double* pos, double L, const
 tb_status tb_ctx_kernels_per_evaluation(const tb_ctx* c, int n, double L, int* count) {
   if (!c || !count || n < 0 || !(L > 0.0)) return TB_ERR_INVALID_ARG;
   if (n > c->reserved_n || !c->ws) return TB_ERR_NOT_RESERVED;
-  const bool mixed = c->p.prec == TB_PREC_MIXED;
+  const bool mixed = c->p.prec != TB_PREC_FP64;
   int k = neighbor_kernel_count(c, L) + 1;            // lists, assembly
   int eig = mixed ? 1 : 2;                             // group eigensolver (+ FP64 refinement)
   if (c->p.group_m > 1) {

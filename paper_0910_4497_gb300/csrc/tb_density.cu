@@ -923,7 +923,7 @@ tb_status launch_forces(tb_ctx* c, int n, const double* pos, double L, const int
                         double* F, double* energies, cudaStream_t s) {
   const int NT = 4 * c->p.r;
   RhoArgs ra{NT, h_off, kdim, lambda, S, P, mu, c->p.kT, c->rho, c->per_target, c->d_status};
-  if (c->p.prec == TB_PREC_MIXED) rho_kernel<float><<<n, RT, 0, s>>>(ra);
+  if (c->p.prec != TB_PREC_FP64) rho_kernel<float><<<n, RT, 0, s>>>(ra);
   else rho_kernel<double><<<n, RT, 0, s>>>(ra);
   TB_CUDA_TRY(cudaGetLastError());
   ForceArgs fa{n, pos, L, h_off, h_idx, dHblk, c->rho, tb_repulsion_gsp(c->p), c->bondf, F,

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(FT) eig_finish_kernel(const FinArgs<TV> a) {
   __syncthreads();
 
   {
-  const double* Ti = a.T + (size_t)i * NT * NT;
+  const double* Ti = a.T + (size_t)i * tc_doubles(NT / 4);
   double* Xd = reinterpret_cast<double*>(X);
   double* Tm = Xd + NT * PT;
   double* W1 = Tm + NT * PT;
@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(FT) eig_finish_kernel(const FinArgs<TV> a) {
   double* Rm = Sm + NT * PT;
   for (int q = tid; q < m * m; q += FT) {
     const int x = q / m, y = q - x * m;
-    Tm[x * PT + y] = Ti[act[x] * NT + act[y]];
+    const int tq = tc_index(act[x], act[y]);
+    Tm[x * PT + y] = tq < 0 ? 0.0 : Ti[tq];
   }
   __syncthreads();
   {

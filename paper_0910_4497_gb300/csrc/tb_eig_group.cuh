@@ -304,19 +304,16 @@ __device__ __forceinline__ void eig_group(const XArgs& a, int i, Grp g, unsigned
   const int m = __popcll(mask);
   if (t < NT && ((mask >> t) & 1ull)) act[__popcll(mask & ((1ull << t) - 1ull))] = t;
   gsync(g);
-  const double* Ti = a.T + (size_t)i * NT * NT;
+  // T is block tridiagonal, stored compactly (tc_index); entries outside
+  // the block band are zero
+  const double* Ti = a.T + (size_t)i * tc_doubles(NT / 4);
+  auto tget = [&](int x, int y) -> double {
+    const int q = tc_index(x, y);
+    return q < 0 ? 0.0 : __ldcg(Ti + q);
+  };
   if (t < m) {
     const int ay = act[t];
-    int x = 0;
-    for (; x + 3 < m; x += 4) {               // four independent loads in flight
-      const double t0 = __ldcg(Ti + act[x] * NT + ay), t1 = __ldcg(Ti + act[x + 1] * NT + ay);
-      const double t2 = __ldcg(Ti + act[x + 2] * NT + ay), t3 = __ldcg(Ti + act[x + 3] * NT + ay);
-      H[x * P + t] = (float)t0;
-      H[(x + 1) * P + t] = (float)t1;
-      H[(x + 2) * P + t] = (float)t2;
-      H[(x + 3) * P + t] = (float)t3;
-    }
-    for (; x < m; ++x) H[x * P + t] = (float)__ldcg(Ti + act[x] * NT + ay);
+    for (int x = 0; x < m; ++x) H[x * P + t] = (float)tget(act[x], ay);
   }
   gsync(g);
 
@@ -646,7 +643,7 @@ __device__ __forceinline__ void eig_group(const XArgs& a, int i, Grp g, unsigned
       blo[x] = lo;
       bhi[x] = hi;
       for (int w = 0; w < hi - lo; ++w) {
-        const double tv = __ldcg(Ti + act[x] * NT + act[lo + w]);
+        const double tv = tget(act[x], act[lo + w]);
         const float th = (float)tv;
         Thi[x * 12 + w] = th;
         Tlo[x * 12 + w] = (float)(tv - (double)th);

@@ -9,7 +9,9 @@
 // One thread per bond; runs of 32 consecutive bonds (one warp) are dealt out
 // to the warps of all blocks in turn, so that every SM gets a share of this
 // FP64-bound work in full warps whatever the bond count; the source atom is
-// found by binary search in h_off.
+// found by binary search in h_off.  For the mixed and BF16 paths the bond's
+// Slater-Koster record (s(r), l) goes out as one float4: the sweeps rebuild
+// the block's action from it (16 bytes per bond instead of a 64-byte block).
 #include "tb_internal.cuh"
 #include "tb_model.cuh"
 
@@ -23,7 +25,7 @@ __global__ void __launch_bounds__(256)
 assemble_kernel(int n, const double* __restrict__ pos, double L,
                 const int* __restrict__ h_off, const int* __restrict__ h_idx,
                 tb_gsp g, SK sk, double* __restrict__ Hblk, double* __restrict__ dHblk,
-                float* __restrict__ Hmir, int* st) {
+                float4* __restrict__ Hsk, int* st) {
   const int nb = h_off[n];
   const int wg = blockIdx.x + gridDim.x * (threadIdx.x >> 5);     // warps interleaved over blocks
   const int stride = gridDim.x * blockDim.x;
@@ -64,10 +66,8 @@ assemble_kernel(int n, const double* __restrict__ pos, double L,
   }
   double* H = Hblk + (size_t)pidx * 16;
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    H[q] = s * M[q];
-    if (Hmir) Hmir[(size_t)pidx * 16 + q] = (float)(s * M[q]);
-  }
+  for (int q = 0; q < 16; ++q) H[q] = s * M[q];
+  if (Hsk) Hsk[pidx] = make_float4((float)s, (float)l[0], (float)l[1], (float)l[2]);
   double* Gd = dHblk + (size_t)pidx * 48;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -94,13 +94,14 @@ assemble_kernel(int n, const double* __restrict__ pos, double L,
 
 tb_status launch_assemble(tb_ctx* c, int n, const double* pos, double L,
                           const int* h_off, const int* h_idx, double* Hblk,
-                          double* dHblk, float* Hmir, cudaStream_t s) {
+                          double* dHblk, float* Hsk, cudaStream_t s) {
   const tb_params& p = c->p;
   SK sk{p.Vss, p.Vsp, p.Vpps, p.Vppp};
   const int threads = 64;
   const int grid = 16 * c->num_sms;                 // up to 32 warps per SM
   assemble_kernel<<<grid, threads, 0, s>>>(n, pos, L, h_off, h_idx, tb_hopping_gsp(p),
-                                           sk, Hblk, dHblk, Hmir, c->d_status);
+                                           sk, Hblk, dHblk, reinterpret_cast<float4*>(Hsk),
+                                           c->d_status);
   TB_CUDA_TRY(cudaGetLastError());
   return TB_OK;
 }

@@ -10,6 +10,19 @@
     if (e_ != cudaSuccess) return TB_ERR_CUDA;             \
   } while (0)
 
+// Block-tridiagonal T of one target, stored compactly: 2r - 1 blocks of 16
+// doubles, block 2k = A_k (row-major), block 2k+1 = B_k with
+// T[4(k+1)+j][4k+c] = T[4k+c][4(k+1)+j] = B_k[j][c].
+__host__ __device__ __forceinline__ size_t tc_doubles(int r) { return (size_t)(2 * r - 1) * 16; }
+// Index of T[x][y] in the compact form, or -1 outside the block band.
+__host__ __device__ __forceinline__ int tc_index(int x, int y) {
+  const int kx = x >> 2, ky = y >> 2, jx = x & 3, jy = y & 3;
+  if (kx == ky) return 32 * kx + 4 * jx + jy;
+  if (kx == ky + 1) return 32 * ky + 16 + 4 * jx + jy;
+  if (ky == kx + 1) return 32 * kx + 16 + 4 * jy + jx;
+  return -1;
+}
+
 namespace tbk {
 
 constexpr int MAX_R = 16;           // Krylov block order cap -> NT <= 64
@@ -149,13 +162,15 @@ struct tb_ctx {
   int* atom_cell = nullptr;          // n cell ids
   int* pad_h = nullptr;              // n * max_hnbr padded Hamiltonian lists
   int* pad_c = nullptr;              // n * max_cluster padded clusters
-  double* T = nullptr;               // n * NT * NT
+  double* T = nullptr;               // n * tc_doubles(r): compact block-tridiagonal T
   void* Y = nullptr;                 // n*(1+max_hnbr)*4*NT  (TV precision)
   unsigned long long* colmask = nullptr;  // n
   float* Zf = nullptr;               // n * NT * NT
   float* lamf = nullptr;             // n * NT
   void* Vg = nullptr;                // kry_grid * Dmax * NT (TV) when the basis is global
-  int2* lent = nullptr;              // kry_grid * max_cluster * max_hnbr (slot, bond)
+  int2* lent = nullptr;              // kry_grid * max_cluster * max_hnbr (slot, bond), FP64 path
+  void* recg = nullptr;              // mixed path: per-CTA overflow of the local
+  int* rslg = nullptr;               //   Slater-Koster records and neighbour offsets
   double* mu_part = nullptr;         // mu_grid * 4
   unsigned int* bar = nullptr;       // barrier counter
   double* mu_state = nullptr;        // 4 doubles
@@ -166,7 +181,7 @@ struct tb_ctx {
   // MD-owned buffers
   int *h_off = nullptr, *h_idx = nullptr, *c_off = nullptr, *c_idx = nullptr;
   double *Hblk = nullptr, *dHblk = nullptr;
-  float* Hmir = nullptr;
+  float* Hsk = nullptr;               // n * max_hnbr * 4: Slater-Koster records (mixed)
   double *lambda = nullptr, *S = nullptr, *P = nullptr;
   int* kdim = nullptr;
   double *mu = nullptr, *ncount = nullptr;
@@ -178,6 +193,9 @@ struct tb_ctx {
   bool ke_on = false;               // persistent Krylov + eigensolve kernel (mixed path)
   int ke_grid = 0;
   size_t ke_smem = 0;
+  int sk_ecap = 0;                   // local records kept in shared memory per target
+  int sk_grid = 0;                   // CTAs of the mixed Krylov kernel (separate launch)
+  size_t sk_smem = 0;
   int* ke_work = nullptr;            // n + 1: work counter, then per-target Krylov-done flags
   int eig_grid = 0;
   int eig_warps = 0;                 // targets per CTA of the warp eigensolver
@@ -225,13 +243,14 @@ tb_status launch_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h
                            int* h_idx, int* c_off, int* c_idx, cudaStream_t s);
 tb_status launch_assemble(tb_ctx* c, int n, const double* pos, double L,
                           const int* h_off, const int* h_idx, double* Hblk,
-                          double* dHblk, float* Hmir, cudaStream_t s);
+                          double* dHblk, float* Hsk, cudaStream_t s);
 tb_status krylov_configure(tb_ctx* c);
 bool krylov_eig_persistent(const tb_ctx* c, int n);   // Krylov launch includes the eigensolve
 tb_status launch_krylov(tb_ctx* c, int n, const int* c_off, const int* c_idx,
                         const int* h_off, const int* h_idx, const double* Hblk,
-                        const float* Hmir, double* lambda, double* S, double* P, int* kdim,
+                        const float* Hsk, double* lambda, double* S, double* P, int* kdim,
                         cudaStream_t s);
+size_t krylov_overflow_records(const tb_ctx* c);   // records per CTA overflow slot x CTAs
 int group_grid_cells(int n, int m);
 tb_status krylov_group_configure(tb_ctx* c);
 size_t krylov_group_basis_bytes(const tb_ctx* c);
@@ -240,7 +259,7 @@ tb_status launch_group_atoms(tb_ctx* c, int n, const double* pos, double L, int*
 tb_status launch_krylov_grouped(tb_ctx* c, int n, int n_groups, const int* g_off,
                                 const int* g_idx, const int* c_off, const int* c_idx,
                                 const int* h_off, const int* h_idx, const double* Hblk,
-                                const float* Hmir, cudaStream_t s);
+                                const float* Hsk, cudaStream_t s);
 tb_status eig_configure(tb_ctx* c);
 tb_status launch_eig(tb_ctx* c, int n, const int* h_off, double* lambda, double* S,
                      double* P, int* kdim, cudaStream_t s);

@@ -29,6 +29,7 @@
 #include "tb_internal.cuh"
 #include "tb_eig_group.cuh"
 #include "tb_krylov_common.cuh"
+#include "tb_krylov_sk.cuh"
 
 namespace {
 
@@ -166,8 +167,7 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
   {
     const int c0 = a.c_off[i];
     const int nc = a.c_off[i + 1] - c0;
-    double* Ti = a.T + (size_t)i * NT * NT;
-    for (int q = tid; q < NT * NT; q += KT) Ti[q] = 0.0;
+    double* Ti = a.T + (size_t)i * tc_doubles(r);
     const bool bad = (nc < 1 || nc > a.max_cluster || a.c_idx[c0] != i);
     if (bad) {
       if (tid == 0) {
@@ -335,7 +335,7 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
         if (pass == 0 && tid < 16) {
           const int ii = tid >> 2, c = tid & 3;
           const vec4<TV> x1 = coef(k - b0, ii), x2 = coef(k - b0, c);
-          Ti[(4 * k + ii) * NT + 4 * k + c] = 0.5 * ((double)x1.v[c] + (double)x2.v[ii]);
+          Ti[32 * k + 4 * ii + c] = 0.5 * ((double)x1.v[c] + (double)x2.v[ii]);   // A_k
         }
         if (k == r - 1) break;
         const bool last = pass == passes - 1;
@@ -587,8 +587,7 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
         for (int j = 0; j < 4; ++j)
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            Ti[(4 * (k + 1) + j) * NT + 4 * k + c] = Bs[j * 4 + c];
-            Ti[(4 * k + c) * NT + 4 * (k + 1) + j] = Bs[j * 4 + c];
+            Ti[32 * k + 16 + 4 * j + c] = Bs[j * 4 + c];                         // B_k
           }
         // active-column mask of the basis, 64 bits kept as two ints
         unsigned long long mask = ((unsigned long long)(unsigned)flags[FL_MASK + 1] << 32) |
@@ -651,8 +650,8 @@ __device__ __forceinline__ int ld_acquire_s32(const int* p) {
 // TB_ERR_TIMEOUT).  The record (T, Y rows, column mask) is published by a
 // fence in every thread, a barrier and a flag; the eigensolver reads it
 // through L2.  work[0] and done[0..n) are zero at launch.
-template <int NTC>
-__global__ void __launch_bounds__(128, 4) kry_eig_kernel(const KryArgs<float> a, const XArgs xa,
+template <int NTC, bool BF>
+__global__ void __launch_bounds__(128, 4) kry_eig_kernel(const tbsk::SkArgs a, const XArgs xa,
                                                          int* work, int* done, long long timeout) {
   __shared__ int s_item;
   __shared__ int s_ok[2];
@@ -665,7 +664,7 @@ __global__ void __launch_bounds__(128, 4) kry_eig_kernel(const KryArgs<float> a,
     const int it = s_item;
     if (it >= nitems) break;
     if (it < n) {
-      krylov_target<float, 128>(a, it);
+      tbsk::krylov_sk_target<BF>(a, it);
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) atomicExch(done + it, 1);
@@ -699,49 +698,92 @@ __global__ void __launch_bounds__(128, 4) kry_eig_kernel(const KryArgs<float> a,
   }
 }
 
-template <int NTC>
-tb_status kry_eig_configure_t(tb_ctx* c, int max_smem) {
-  const size_t eig = 2 * xw_smem_per_warp(4 * c->p.r);
-  const size_t bytes = c->kry_smem > eig ? c->kry_smem : eig;
+// Separate launch of the mixed-path block Lanczos: one CTA per target,
+// persistent grid-stride.
+template <bool BF>
+__global__ void __launch_bounds__(tbsk::KT, 4) krylov_sk_kernel(const tbsk::SkArgs a) {
+  for (int i = blockIdx.x; i < a.n; i += gridDim.x) tbsk::krylov_sk_target<BF>(a, i);
+}
+
+tbsk::SkArgs sk_args(const tb_ctx* c, int n, const int* c_off, const int* c_idx,
+                     const int* h_off, const int* h_idx, const float* Hsk) {
+  const tb_params& p = c->p;
+  tbsk::SkArgs a;
+  a.n = n; a.r = p.r; a.max_cluster = p.max_cluster; a.max_hnbr = p.max_hnbr;
+  a.reorth_passes = p.reorth_passes; a.reorth_every = p.reorth_every;
+  a.ecap = c->sk_ecap;
+  a.Es = (float)p.Es; a.Ep = (float)p.Ep; a.Vss = (float)p.Vss; a.Vsp = (float)p.Vsp;
+  a.Cpp = (float)(p.Vpps - p.Vppp); a.Vppp = (float)p.Vppp;
+  a.defl_tol = p.defl_tol;
+  a.c_off = c_off; a.c_idx = c_idx; a.h_off = h_off; a.h_idx = h_idx;
+  a.Hsk = reinterpret_cast<const float4*>(Hsk);
+  a.T = c->T; a.Y = reinterpret_cast<float*>(c->Y); a.colmask = c->colmask;
+  a.Vg = reinterpret_cast<float*>(c->Vg); a.recg = c->recg; a.rslg = c->rslg;
+  a.st = c->d_status;
+  return a;
+}
+
+template <bool BF>
+tb_status sk_configure_t(tb_ctx* c, int max_smem) {
+  const tb_params& p = c->p;
+  const int MC = p.max_cluster;
+  // records kept in shared memory: 8 per cluster slot (carbon within 2.6 A:
+  // ~8 in-cluster neighbours on average); none when the Hamiltonian lists are
+  // long (long-range hoppings), where they would not fit anyway
+  c->sk_ecap = p.max_hnbr > 48 ? 0 : 8 * MC;
+  size_t bytes = tbsk::sk_smem_bytes<BF>(p.r, MC, c->sk_ecap);
+  if ((int)bytes > max_smem) {
+    c->sk_ecap = 0;
+    bytes = tbsk::sk_smem_bytes<BF>(p.r, MC, 0);
+  }
   if ((int)bytes > max_smem) return TB_ERR_CAPACITY;
-  TB_CUDA_TRY(cudaFuncSetAttribute(kry_eig_kernel<NTC>,
+  TB_CUDA_TRY(cudaFuncSetAttribute(krylov_sk_kernel<BF>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   int occ = 0;
-  TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kry_eig_kernel<NTC>, 128, bytes));
+  TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, krylov_sk_kernel<BF>,
+                                                            tbsk::KT, bytes));
   if (occ < 1) return TB_ERR_CAPACITY;
-  const int grid = c->num_sms * occ;
-  // the basis slots and local CSR are per CTA, sized for kry_grid
-  if (grid > c->kry_grid) return TB_ERR_CAPACITY;
-  c->ke_smem = bytes;
-  c->ke_grid = grid;
-  c->ke_on = true;
+  c->sk_smem = bytes;
+  c->sk_grid = c->num_sms * occ;
+  c->kry_threads = tbsk::KT;
+  c->kry_grid = c->sk_grid;
   return TB_OK;
 }
 
-tb_status kry_eig_configure(tb_ctx* c, int max_smem) {
-  const int NT = 4 * c->p.r;
-  const int ntc = ntc_of(NT);
-  if (ntc == 16) return kry_eig_configure_t<16>(c, max_smem);
-  if (ntc == 32) return kry_eig_configure_t<32>(c, max_smem);
-  if (ntc == 48) return kry_eig_configure_t<48>(c, max_smem);
-  return kry_eig_configure_t<64>(c, max_smem);
+template <int NTC, bool BF>
+tb_status kry_eig_configure_t(tb_ctx* c, int max_smem) {
+  const size_t eig = 2 * xw_smem_per_warp(4 * c->p.r);
+  const size_t bytes = c->sk_smem > eig ? c->sk_smem : eig;
+  if ((int)bytes > max_smem) return TB_ERR_CAPACITY;
+  TB_CUDA_TRY(cudaFuncSetAttribute(kry_eig_kernel<NTC, BF>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  int occ = 0;
+  TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kry_eig_kernel<NTC, BF>, 128,
+                                                            bytes));
+  if (occ < 1) return TB_ERR_CAPACITY;
+  c->ke_smem = bytes;
+  c->ke_grid = c->num_sms * occ;
+  c->ke_on = true;
+  // the basis slots and overflow records are per CTA: size them for both launches
+  if (c->ke_grid > c->kry_grid) c->kry_grid = c->ke_grid;
+  return TB_OK;
 }
 
+template <bool BF>
+tb_status kry_eig_configure(tb_ctx* c, int max_smem) {
+  const int ntc = ntc_of(4 * c->p.r);
+  if (ntc == 16) return kry_eig_configure_t<16, BF>(c, max_smem);
+  if (ntc == 32) return kry_eig_configure_t<32, BF>(c, max_smem);
+  if (ntc == 48) return kry_eig_configure_t<48, BF>(c, max_smem);
+  return kry_eig_configure_t<64, BF>(c, max_smem);
+}
+
+template <bool BF>
 tb_status kry_eig_launch(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int* h_off,
-                         const int* h_idx, const float* H, double* lambda, double* S, double* P,
+                         const int* h_idx, const float* Hsk, double* lambda, double* S, double* P,
                          int* kdim, cudaStream_t s) {
   const tb_params& p = c->p;
-  KryArgs<float> a;
-  a.n = n; a.r = p.r; a.max_cluster = p.max_cluster; a.max_hnbr = p.max_hnbr;
-  a.reorth_passes = p.reorth_passes;
-  a.reorth_every = p.reorth_every;
-  a.Es = p.Es; a.Ep = p.Ep; a.defl_tol = p.defl_tol;
-  a.c_off = c_off; a.c_idx = c_idx; a.h_off = h_off; a.h_idx = h_idx; a.H = H;
-  a.T = c->T; a.Y = reinterpret_cast<float*>(c->Y); a.colmask = c->colmask;
-  a.Vg = reinterpret_cast<float*>(c->Vg); a.lent = c->lent; a.st = c->d_status;
-  a.lent_smem = c->kry_lsmem ? 1 : 0;
-  a.lent_cap = lent_smem_cap(p.max_cluster, p.max_hnbr);
-  a.lamf = c->lamf; a.Zf = c->Zf; a.lambda = lambda; a.S = S; a.P = P; a.kdim = kdim;
+  const tbsk::SkArgs a = sk_args(c, n, c_off, c_idx, h_off, h_idx, Hsk);
   XArgs xa{n, 4 * p.r, c->T, c->colmask, reinterpret_cast<const float*>(c->Y), h_off, c->Zf,
            c->lamf, lambda, S, P, kdim, c->d_status};
   TB_CUDA_TRY(cudaMemsetAsync(c->ke_work, 0, sizeof(int) * ((size_t)n + 1), s));
@@ -749,10 +791,22 @@ tb_status kry_eig_launch(tb_ctx* c, int n, const int* c_off, const int* c_idx, c
   int* work = c->ke_work;
   int* done = c->ke_work + 1;
   const int ntc = ntc_of(4 * p.r);
-  if (ntc == 16) kry_eig_kernel<16><<<grid, 128, c->ke_smem, s>>>(a, xa, work, done, p.timeout_cycles);
-  else if (ntc == 32) kry_eig_kernel<32><<<grid, 128, c->ke_smem, s>>>(a, xa, work, done, p.timeout_cycles);
-  else if (ntc == 48) kry_eig_kernel<48><<<grid, 128, c->ke_smem, s>>>(a, xa, work, done, p.timeout_cycles);
-  else kry_eig_kernel<64><<<grid, 128, c->ke_smem, s>>>(a, xa, work, done, p.timeout_cycles);
+  const long long to = p.timeout_cycles;
+  if (ntc == 16) kry_eig_kernel<16, BF><<<grid, 128, c->ke_smem, s>>>(a, xa, work, done, to);
+  else if (ntc == 32) kry_eig_kernel<32, BF><<<grid, 128, c->ke_smem, s>>>(a, xa, work, done, to);
+  else if (ntc == 48) kry_eig_kernel<48, BF><<<grid, 128, c->ke_smem, s>>>(a, xa, work, done, to);
+  else kry_eig_kernel<64, BF><<<grid, 128, c->ke_smem, s>>>(a, xa, work, done, to);
+  TB_CUDA_TRY(cudaGetLastError());
+  return TB_OK;
+}
+
+template <bool BF>
+tb_status sk_launch(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int* h_off,
+                    const int* h_idx, const float* Hsk, cudaStream_t s) {
+  const tbsk::SkArgs a = sk_args(c, n, c_off, c_idx, h_off, h_idx, Hsk);
+  const int grid = n < c->sk_grid ? n : c->sk_grid;
+  if (grid <= 0) return TB_OK;
+  krylov_sk_kernel<BF><<<grid, tbsk::KT, c->sk_smem, s>>>(a);
   TB_CUDA_TRY(cudaGetLastError());
   return TB_OK;
 }
@@ -809,7 +863,7 @@ tb_status configure_t(tb_ctx* c, int max_smem) {
 }  // namespace
 
 bool krylov_eig_persistent(const tb_ctx* c, int n) {
-  if (!c->ke_on || c->p.prec != TB_PREC_MIXED) return false;
+  if (!c->ke_on || c->p.prec == TB_PREC_FP64) return false;
   if (c->p.schedule == TB_SCHED_PERSISTENT) return true;
   if (c->p.schedule == TB_SCHED_SEPARATE) return false;
   // the queue pays off where the targets fill a few waves of CTAs and the last
@@ -826,29 +880,34 @@ tb_status krylov_configure(tb_ctx* c) {
   int dev = 0, max_smem = 0;
   TB_CUDA_TRY(cudaGetDevice(&dev));
   TB_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  // 128-thread CTAs with the basis in a per-CTA slot of global memory
-  // (L2-resident; four or five targets in flight per SM), 256 threads when
-  // the 128-thread form does not fit; the projected eigensolve in the group
-  // eigensolver, inside the Krylov launch (persistent queue) or after it.
+  // FP64: 128-thread CTAs with the basis in a per-CTA slot of global memory
+  // (L2-resident), 256 threads when the 128-thread form does not fit.  Mixed
+  // and BF16: the Slater-Koster record kernel, and the persistent Krylov +
+  // eigensolve queue unless separate launches are asked for (the grouped form
+  // runs the separate eigensolver).
   if (c->p.prec == TB_PREC_FP64) {
     if (configure_t<double, 128>(c, max_smem) == TB_OK) return TB_OK;
     return configure_t<double, 256>(c, max_smem);
   }
-  if (configure_t<float, 128>(c, max_smem) == TB_OK) {
-    // the persistent Krylov + eigensolve kernel, unless separate launches
-    // are asked for (the grouped form runs the separate eigensolver)
-    c->ke_on = false;
-    if (c->p.group_m == 1 && c->p.schedule != TB_SCHED_SEPARATE &&
-        kry_eig_configure(c, max_smem) != TB_OK)
+  const bool bf = c->p.prec == TB_PREC_BF16;
+  tb_status st = bf ? sk_configure_t<true>(c, max_smem) : sk_configure_t<false>(c, max_smem);
+  if (st != TB_OK) return st;
+  c->ke_on = false;
+  if (c->p.group_m == 1 && c->p.schedule != TB_SCHED_SEPARATE) {
+    if ((bf ? kry_eig_configure<true>(c, max_smem) : kry_eig_configure<false>(c, max_smem)) != TB_OK)
       c->ke_on = false;
-    return TB_OK;
   }
-  return configure_t<float, 256>(c, max_smem);
+  return TB_OK;
+}
+
+size_t krylov_overflow_records(const tb_ctx* c) {
+  if (c->p.prec == TB_PREC_FP64) return 0;
+  return (size_t)c->kry_grid * c->p.max_cluster * c->p.max_hnbr;
 }
 
 tb_status launch_krylov(tb_ctx* c, int n, const int* c_off, const int* c_idx,
                         const int* h_off, const int* h_idx, const double* Hblk,
-                        const float* Hmir, double* lambda, double* S, double* P, int* kdim,
+                        const float* Hsk, double* lambda, double* S, double* P, int* kdim,
                         cudaStream_t s) {
 #define TB_KRY_DISPATCH(TV, H)                                                                \
   do {                                                                                        \
@@ -857,9 +916,12 @@ tb_status launch_krylov(tb_ctx* c, int n, const int* c_off, const int* c_idx,
     return launch_t<TV, 256>(c, n, c_off, c_idx, h_off, h_idx, H, lambda, S, P, kdim, s);     \
   } while (0)
   if (c->p.prec == TB_PREC_FP64) TB_KRY_DISPATCH(double, Hblk);
-  if (!Hmir) return TB_ERR_INVALID_ARG;
+  if (!Hsk) return TB_ERR_INVALID_ARG;
+  const bool bf = c->p.prec == TB_PREC_BF16;
   if (krylov_eig_persistent(c, n))
-    return kry_eig_launch(c, n, c_off, c_idx, h_off, h_idx, Hmir, lambda, S, P, kdim, s);
-  TB_KRY_DISPATCH(float, Hmir);
+    return bf ? kry_eig_launch<true>(c, n, c_off, c_idx, h_off, h_idx, Hsk, lambda, S, P, kdim, s)
+              : kry_eig_launch<false>(c, n, c_off, c_idx, h_off, h_idx, Hsk, lambda, S, P, kdim, s);
+  return bf ? sk_launch<true>(c, n, c_off, c_idx, h_off, h_idx, Hsk, s)
+            : sk_launch<false>(c, n, c_off, c_idx, h_off, h_idx, Hsk, s);
 #undef TB_KRY_DISPATCH
 }

@@ -110,8 +110,10 @@ struct KryGArgs {
   const int* c_idx;
   const int* h_off;
   const int* h_idx;
-  const TV* H;
-  double* T;
+  const TV* H;                        // FP64: the bond blocks
+  const float4* Hsk;                  // FP32: Slater-Koster records (s, l)
+  float Vss, Vsp, Cpp, Vppp;          // Cpp = Vpps - Vppp
+  double* T;                          // compact block-tridiagonal T
   TV* Y;
   unsigned long long* colmask;
   TV* Vg;
@@ -119,6 +121,31 @@ struct KryGArgs {
   int lent_smem;
   int* st;
 };
+
+// Row al of the 4x4 block of bond p: read from the FP64 table, or rebuilt
+// from the FP32 Slater-Koster record (s, l) with the table of Eq. (1):
+// row s = s (Vss, Vsp l), row p_g = s (-Vsp l_g, (Vpps - Vppp) l_g l + Vppp e_g).
+template <typename TV>
+__device__ __forceinline__ vec4<TV> hrow(const KryGArgs<TV>& a, int p, int al) {
+  if constexpr (sizeof(TV) == 8) {
+    return ldg4(a.H + (size_t)p * 16 + al * 4);
+  } else {
+    const float4 h = __ldg(a.Hsk + p);
+    vec4<TV> o;
+    if (al == 0) {
+      const float sv = h.x * a.Vsp;
+      o.v[0] = h.x * a.Vss; o.v[1] = sv * h.y; o.v[2] = sv * h.z; o.v[3] = sv * h.w;
+    } else {
+      const float lg = al == 1 ? h.y : (al == 2 ? h.z : h.w);
+      const float t = h.x * a.Cpp * lg, d = h.x * a.Vppp;
+      o.v[0] = -h.x * a.Vsp * lg;
+      o.v[1] = fmaf(t, h.y, al == 1 ? d : 0.f);
+      o.v[2] = fmaf(t, h.z, al == 2 ? d : 0.f);
+      o.v[3] = fmaf(t, h.w, al == 3 ? d : 0.f);
+    }
+    return o;
+  }
+}
 
 // integer scratch in shared memory
 constexpr int GI_WT = 0;          // warp totals of the block scans (<= 16 warps)
@@ -286,11 +313,6 @@ __global__ void __launch_bounds__(KT, 1) krylov_group_kernel(const KryGArgs<TV> 
       }
     }
 #pragma unroll
-    for (int t = 0; t < MC; ++t) {
-      if (mem[t] < 0) continue;
-      double* Ti = a.T + (size_t)mem[t] * NT * NT;
-      for (int q = tid; q < NT * NT; q += KT) Ti[q] = 0.0;
-    }
     if (bad) {
       if (tid == 0) {
         tbk::set_status(a.st, code, info);
@@ -453,7 +475,7 @@ __global__ void __launch_bounds__(KT, 1) krylov_group_kernel(const KryGArgs<TV> 
 #pragma unroll 2
         for (int e = rowptr[s]; e < e1; ++e) {
           const int2 en = lent[e];
-          const vec4<TV> h = ldg4(a.H + (size_t)en.y * 16 + al * 4);
+          const vec4<TV> h = hrow<TV>(a, en.y, al);
 #pragma unroll
           for (int t = 0; t < MC; ++t) {
             if (!((live >> t) & 1)) continue;
@@ -530,8 +552,8 @@ __global__ void __launch_bounds__(KT, 1) krylov_group_kernel(const KryGArgs<TV> 
           const int t = tid >> 4, ii = (tid >> 2) & 3, c = tid & 3;
           if ((live >> t) & 1) {
             const TV* ck = Cc + ((size_t)t * r + k) * 16;
-            a.T[(size_t)a.g_idx[q0 + t] * NT * NT + (4 * k + ii) * NT + 4 * k + c] =
-                0.5 * ((double)ck[ii * 4 + c] + (double)ck[c * 4 + ii]);
+            a.T[(size_t)a.g_idx[q0 + t] * tc_doubles(r) + 32 * k + 4 * ii + c] =
+                0.5 * ((double)ck[ii * 4 + c] + (double)ck[c * 4 + ii]);     // A_k
           }
         }
         if (k == r - 1) break;
@@ -732,16 +754,11 @@ __global__ void __launch_bounds__(KT, 1) krylov_group_kernel(const KryGArgs<TV> 
       if (tid < MC && ((live >> tid) & 1)) {
         const int t = tid;
         const int i = a.g_idx[q0 + t];
-        double* Ti = a.T + (size_t)i * NT * NT;
+        double* Ti = a.T + (size_t)i * tc_doubles(r);
         const int act = gi[GI_ACT + t];
         const double* bs = Bs + t * 16;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            Ti[(4 * (k + 1) + j) * NT + 4 * k + c] = bs[j * 4 + c];
-            Ti[(4 * k + c) * NT + 4 * (k + 1) + j] = bs[j * 4 + c];
-          }
+        for (int q = 0; q < 16; ++q) Ti[32 * k + 16 + q] = bs[q];              // B_k
         unsigned long long mask = ((unsigned long long)(unsigned)gi[GI_MASK + 2 * t + 1] << 32) |
                                   (unsigned)gi[GI_MASK + 2 * t];
         mask |= (unsigned long long)act << (4 * (k + 1));
@@ -831,9 +848,12 @@ tb_status kryg_configure_t(tb_ctx* c, int max_smem) {
 template <typename TV, int MC, int KT, bool VKS>
 tb_status kryg_launch_t(tb_ctx* c, int n, int n_groups, const int* g_off, const int* g_idx,
                         const int* c_off, const int* c_idx, const int* h_off, const int* h_idx,
-                        const TV* H, cudaStream_t s) {
+                        const TV* H, const float* Hsk, cudaStream_t s) {
   const tb_params& p = c->p;
   KryGArgs<TV> a;
+  a.Hsk = reinterpret_cast<const float4*>(Hsk);
+  a.Vss = (float)p.Vss; a.Vsp = (float)p.Vsp; a.Cpp = (float)(p.Vpps - p.Vppp);
+  a.Vppp = (float)p.Vppp;
   a.n = n; a.n_groups = n_groups; a.r = p.r; a.max_cluster = p.max_cluster;
   a.max_union = c->grp_max_union; a.max_hnbr = p.max_hnbr;
   a.reorth_passes = p.reorth_passes; a.reorth_every = p.reorth_every; a.ubuf = c->grp_ubuf;
@@ -878,7 +898,7 @@ tb_status krylov_group_configure(tb_ctx* c) {
   TB_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   // 512 threads for groups of up to four in FP32 (the FP64 kernel would
   // spill at 128 registers), else 256; the staged copy of V_k when it fits.
-  const int kt = (p.group_m > 2 && p.prec == TB_PREC_MIXED) ? 512 : 256;
+  const int kt = (p.group_m > 2 && p.prec != TB_PREC_FP64) ? 512 : 256;
   const bool nostage = false;
   if (p.prec == TB_PREC_FP64)
     return p.group_m > 2 ? kryg_configure_mc<double, 4>(c, max_smem, kt, nostage)
@@ -914,26 +934,27 @@ tb_status launch_group_atoms(tb_ctx* c, int n, const double* pos, double L, int*
 tb_status launch_krylov_grouped(tb_ctx* c, int n, int n_groups, const int* g_off,
                                 const int* g_idx, const int* c_off, const int* c_idx,
                                 const int* h_off, const int* h_idx, const double* Hblk,
-                                const float* Hmir, cudaStream_t s) {
+                                const float* Hsk, cudaStream_t s) {
 #define TB_KRYG_DISPATCH(TV, MC, H)                                                             \
   do {                                                                                          \
     if (c->grp_threads == 512)                                                                  \
       return c->grp_vks ? kryg_launch_t<TV, MC, 512, true>(c, n, n_groups, g_off, g_idx, c_off, \
-                                                           c_idx, h_off, h_idx, H, s)           \
+                                                           c_idx, h_off, h_idx, H, Hsk, s)           \
                         : kryg_launch_t<TV, MC, 512, false>(c, n, n_groups, g_off, g_idx,       \
-                                                            c_off, c_idx, h_off, h_idx, H, s);  \
+                                                            c_off, c_idx, h_off, h_idx, H, Hsk, s);  \
     return c->grp_vks ? kryg_launch_t<TV, MC, 256, true>(c, n, n_groups, g_off, g_idx, c_off,   \
-                                                         c_idx, h_off, h_idx, H, s)             \
+                                                         c_idx, h_off, h_idx, H, Hsk, s)             \
                       : kryg_launch_t<TV, MC, 256, false>(c, n, n_groups, g_off, g_idx, c_off,  \
-                                                          c_idx, h_off, h_idx, H, s);           \
+                                                          c_idx, h_off, h_idx, H, Hsk, s);           \
   } while (0)
   if (c->grp_grid <= 0) return TB_ERR_INVALID_ARG;
   if (c->p.prec == TB_PREC_FP64) {
     if (c->grp_mc == 4) TB_KRYG_DISPATCH(double, 4, Hblk);
     TB_KRYG_DISPATCH(double, 2, Hblk);
   }
-  if (!Hmir) return TB_ERR_INVALID_ARG;
-  if (c->grp_mc == 4) TB_KRYG_DISPATCH(float, 4, Hmir);
-  TB_KRYG_DISPATCH(float, 2, Hmir);
+  if (!Hsk) return TB_ERR_INVALID_ARG;
+  const float* none = nullptr;
+  if (c->grp_mc == 4) TB_KRYG_DISPATCH(float, 4, none);
+  TB_KRYG_DISPATCH(float, 2, none);
 #undef TB_KRYG_DISPATCH
 }

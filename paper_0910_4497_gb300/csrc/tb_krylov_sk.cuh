@@ -34,6 +34,7 @@
 // T is written compactly: per target the 2r - 1 blocks A_0, B_0, A_1, ...
 #pragma once
 #include <cuda_bf16.h>
+#include <type_traits>
 #include "tb_internal.cuh"
 #include "tb_krylov_common.cuh"
 
@@ -43,7 +44,7 @@ using namespace tbkry;
 
 constexpr int KT = 128;                 // threads per target
 constexpr int KW = KT / 32;
-constexpr int FL_MASK = 0, FL_ACT = 2, FL_OK = 3, FL_OVER = 4;
+constexpr int FL_MASK = 0, FL_ACT = 2, FL_OK = 3;   // flags[4..8): scan scratch
 
 struct SkArgs {
   int n, r, max_cluster, max_hnbr, reorth_passes, reorth_every;
@@ -85,7 +86,7 @@ __host__ __device__ inline size_t sk_smem_bytes(int r, int max_cluster, int ecap
   b += al32(sizeof(float) * 16 * r);                 // projection coefficients
   b += al32(sizeof(float) * 16 * 3);                 // B_{k-1}, R, R^-1
   b += al32(sizeof(float) * 16 * KW);                // reduction scratch
-  b += al32(sizeof(double) * 32);                    // B_k, first Cholesky factor
+  b += al32(sizeof(double) * 48);                    // B_k, first Cholesky factor, MGS factor
   b += al32(sizeof(int) * 8);                        // flags
   return b;
 }
@@ -178,7 +179,8 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
   float* Rish = Rsh + 16;                              off += al32(sizeof(float) * 48);
   float* red = reinterpret_cast<float*>(smem + off);  off += al32(sizeof(float) * 16 * KW);
   double* Bs = reinterpret_cast<double*>(smem + off);
-  double* R1s = Bs + 16;                              off += al32(sizeof(double) * 32);
+  double* R1s = Bs + 16;
+  double* Rm = Bs + 32;                               off += al32(sizeof(double) * 48);
   int* flags = reinterpret_cast<int*>(smem + off);
   float* const Vg = a.Vg + (size_t)blockIdx.x * r * 16 * MC;
   const size_t gcap = (size_t)MC * a.max_hnbr;
@@ -368,9 +370,10 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
           __syncwarp();
           if (on) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if (e > c) g[e] += dot4(x, f4(W + 16 * s + 4 * e));
-            g[c] += dot4(x, x);
+            for (int e = 0; e < 4; ++e) {                // constant indices into g
+              if (e == c) g[e] += dot4(x, x);
+              else if (e > c) g[e] += dot4(x, f4(W + 16 * s + 4 * e));
+            }
           }
         }
       }
@@ -408,8 +411,9 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
         bool well;
         const bool ok = chol4(G, R, chol_rel, cq == 0 ? chol_abs : 0.0, well);
         triinv4(R, Ri);
-        if (lane < 16) { Rsh[lane] = R[lane]; Rish[lane] = Ri[lane]; }
         if (lane == 0) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) { Rsh[q] = R[q]; Rish[q] = Ri[q]; }
           flags[FL_OK] = (ok ? 1 : 0) | (well ? 2 : 0);
           if (cq == 0) {
 #pragma unroll
@@ -422,9 +426,8 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
       if (!(fl & 1)) { chol_state = cq + 1; break; }
       single = cq == 0 && (fl & 2);
       const bool fin = single || cq == 1;
-      float ri[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) ri[q] = Rish[q];
+      // column c of R^-1 (upper triangular: rows j <= c)
+      const float ric[4] = {Rish[c], Rish[4 + c], Rish[8 + c], Rish[12 + c]};
 #pragma unroll
       for (int q = 0; q < 4; ++q) g[q] = 0.f;
       float* const out = cq == 0 ? dst : W;
@@ -436,7 +439,7 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
         float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          if (j <= c) y = axpy4(ri[j * 4 + c], f4(xs + 4 * j), y);
+          if (j <= c) y = axpy4(ric[j], f4(xs + 4 * j), y);
         __syncwarp();                                  // every lane has read its slot
         if (on) {
           sf4(out + 16 * s + 4 * c, y);
@@ -449,9 +452,10 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
           __syncwarp();
           if (on) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if (e > c) g[e] += dot4(y, f4(out + 16 * s + 4 * e));
-            g[c] += dot4(y, y);
+            for (int e = 0; e < 4; ++e) {
+              if (e == c) g[e] += dot4(y, y);
+              else if (e > c) g[e] += dot4(y, f4(out + 16 * s + 4 * e));
+            }
           }
         }
       }
@@ -467,9 +471,11 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
       float* O = chol_state == 1 ? dst : W;
       __syncthreads();
       if (warp == 0) {
-        double R[16];
+        double* const R = Rm;                          // written by lane 0 only
+        if (lane == 0) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) R[q] = 0.0;
+          for (int q = 0; q < 16; ++q) R[q] = 0.0;
+        }
         int mact = 0;
         bool nonfinite = false;
         auto at = [](int row, int col) { return (row >> 2) * 16 + col * 4 + (row & 3); };
@@ -489,8 +495,10 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
               for (int j = 0; j < 3; ++j) if (j < c) w -= dd[j] * O[at(row, j)];
               S[at(row, c)] = w;
             }
+            if (lane == 0) {
 #pragma unroll
-            for (int j = 0; j < 3; ++j) if (j < c) R[j * 4 + c] += (double)dd[j];
+              for (int j = 0; j < 3; ++j) if (j < c) R[j * 4 + c] += (double)dd[j];
+            }
           }
           float nn = 0.f;
           for (int row = lane; row < D4; row += 32) {
@@ -503,7 +511,10 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
           const bool keep = nrm > a.defl_tol;
           const float inv = keep ? (float)(1.0 / nrm) : 0.f;
           for (int row = lane; row < D4; row += 32) O[at(row, c)] = S[at(row, c)] * inv;
-          if (keep) { R[c * 4 + c] = nrm; mact |= 1 << c; }
+          if (keep) {
+            if (lane == 0) R[c * 4 + c] = nrm;
+            mact |= 1 << c;
+          }
           __syncwarp();
         }
         // copies of V_{k+1}: the basis slot and (BF16) the sweep's copy

@@ -15,7 +15,7 @@ class TBSystem:
     params: dict with the model constants (Es, Ep, Vss, Vsp, Vpps, Vppp, r0, n, nc,
     rc, phi0, d0, m, mc, dc, r1, rm), kT, Rc, r, and optionally max_hnbr,
     max_cluster, defl_tol, reorth_passes, mu_tol, mu_max_iter.
-    prec: "fp64" or "mixed".
+    prec: "fp64", "mixed" or "bf16" (mixed with BF16 H.V sweeps).
     """
 
     def __init__(self, n, L, params, prec="fp64", device="cuda"):
@@ -38,7 +38,8 @@ class TBSystem:
         self.c_idx = torch.zeros(n * mc, dtype=i32, **kw)
         self.Hblk = torch.zeros(n * mh * 16, dtype=f64, **kw)
         self.dHblk = torch.zeros(n * mh * 48, dtype=f64, **kw)
-        self.Hmir = torch.zeros(n * mh * 16, dtype=f32, **kw) if self.tp.prec == B.TB_PREC_MIXED else None
+        # Slater-Koster records (s(r), l) of the bonds for the mixed and BF16 sweeps
+        self.Hsk = torch.zeros(n * mh * 4, dtype=f32, **kw) if self.tp.prec != B.TB_PREC_FP64 else None
         self.lam = torch.zeros(n * NT, dtype=f64, **kw)
         self.S = torch.zeros(n * 4 * NT, dtype=f64, **kw)
         self.P = torch.zeros((n + n * mh) * 4 * NT, dtype=f64, **kw)
@@ -66,7 +67,7 @@ class TBSystem:
 
     def assemble(self, stream=None):
         B.tb_assemble_H(self.ctx, self.n, self.pos, self.L, self.h_off, self.h_idx,
-                        self.Hblk, self.dHblk, self.Hmir, stream)
+                        self.Hblk, self.dHblk, self.Hsk, stream)
 
     def krylov(self, stream=None):
         """Block Krylov runs and projected eigensolve of every target; with
@@ -74,11 +75,11 @@ class TBSystem:
         if self.group_m > 1:
             B.tb_krylov_density_grouped(self.ctx, self.n, self.n_groups, self.g_off, self.g_idx,
                                         self.c_off, self.c_idx, self.h_off, self.h_idx,
-                                        self.Hblk, self.Hmir, self.lam, self.S, self.P,
+                                        self.Hblk, self.Hsk, self.lam, self.S, self.P,
                                         self.kdim, stream)
             return
         B.tb_krylov_density(self.ctx, self.n, self.c_off, self.c_idx, self.h_off,
-                            self.h_idx, self.Hblk, self.Hmir, self.lam, self.S, self.P,
+                            self.h_idx, self.Hblk, self.Hsk, self.lam, self.S, self.P,
                             self.kdim, stream)
 
     def group(self, stream=None):

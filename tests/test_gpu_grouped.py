@@ -232,5 +232,5 @@ def test_grouped_entry_point_needs_group_contexts(tb):
         tb.binding.tb_krylov_density_grouped(
             s.ctx, n, n, torch.arange(n + 1, dtype=torch.int32, device="cuda"),
             torch.arange(n, dtype=torch.int32, device="cuda"), s.c_off, s.c_idx, s.h_off,
-            s.h_idx, s.Hblk, s.Hmir, s.lam, s.S, s.P, s.kdim)
+            s.h_idx, s.Hblk, s.Hsk, s.lam, s.S, s.P, s.kdim)
     s.close()

@@ -15,7 +15,7 @@ import pytest
 import torch
 
 import oracle
-from oracle import density, neighbors, hamiltonian
+from oracle import density, neighbors, hamiltonian, model
 from synth import (CONFIGS, TB_CONSTANTS, workload_params, fcc_c60_crystal, linear_chain,
                    dimer)
 
@@ -159,10 +159,15 @@ def test_hamiltonian_blocks(tb):
     nb = len(bonds.src)
     H = s.Hblk.cpu().numpy()[:nb * 16].reshape(nb, 4, 4)
     G = s.dHblk.cpu().numpy()[:nb * 48].reshape(nb, 3, 4, 4)
-    Hm = s.Hmir.cpu().numpy()[:nb * 16].reshape(nb, 4, 4)
+    rec = s.Hsk.cpu().numpy()[:nb * 4].reshape(nb, 4).astype(np.float64)
     assert np.abs(H - bonds.t).max() <= 1e-12
     assert np.abs(G - bonds.g).max() <= 1e-11
-    assert np.abs(Hm - bonds.t).max() <= 1e-6
+    # FP32 record (s(r), l): the block it stands for is s(r) SK(l), and l is d/|d|
+    r_b = np.linalg.norm(bonds.d, axis=1)
+    assert np.abs(rec[:, 0] - model.hopping_scale(r_b, p)[0]).max() <= 1e-6
+    assert np.abs(rec[:, 1:] - bonds.d / r_b[:, None]).max() <= 1e-6
+    blocks = np.stack([rec[b, 0] * model.sk_matrix(rec[b, 1:], p) for b in range(nb)])
+    assert np.abs(blocks - bonds.t).max() <= 1e-5
 
 
 # ---------------------------------------------------------------- spectral records

@@ -7,7 +7,21 @@ as one CUDA graph.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
                   [--impl ours|reference]
-                  [--workload c60_1920|longrange1920|md15360|autograd1920|diamond_eos]
+                  [--workload c60_1920|bridged6480|longrange1920|md15360|npt15360|
+                              autograd1920|diamond_eos] [--no-autotune]
+
+Before the timed region the library's autotuner (tb_autotune) times the launch
+plans of the mixed path's block-Lanczos stage on the workload's lists
+(persistent Krylov + eigensolve queue in index order or largest clusters first,
+separate launches, separate launches per cluster-size bucket with per-bucket
+tiles) and the timed steps replay the fastest; the line reports the
+cluster-size histogram and the choices ("autotune").
+
+--workload bridged6480 is the uneven-cluster workload: the 3x3x3 fcc C60 cell
+(6480 atoms, a = 12.5 A) with 30% of the nearest-neighbour molecule pairs
+bridged by 1.55-1.65 A inter-cage contacts, 0.08 A jitter, cluster cutoff
+6.5 A, r = 16, cluster capacity 384; the accuracy and CPU baseline come from a
+bounded oracle sample (the spectral records of a few targets).
 
 --workload longrange1920 is the same measurement in the long-range
 (dense-Hamiltonian) regime: synthetic hoppings of Xu's functional form decaying
@@ -70,17 +84,19 @@ CONFIG_INDEX = 1
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reorth-passes", type=int, default=1)
     ap.add_argument("--reorth-every", type=int, default=4)
     ap.add_argument("--workload", default="c60_1920",
-                    choices=["c60_1920", "longrange1920", "md15360", "npt15360",
+                    choices=["c60_1920", "bridged6480", "longrange1920", "md15360", "npt15360",
                              "autograd1920", "diamond_eos"])
     ap.add_argument("--fd-coords", type=int, default=8)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default launch plan (no tb_autotune)")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--group-m", type=int, default=1,
                     help="targets per group of the m-target form (1 = per-target clusters)")
@@ -91,7 +107,8 @@ def parse():
 
 def workload(name="c60_1920"):
     from synth import CONFIGS, LONGRANGE, fcc_c60_crystal, workload_params
-    cfg = LONGRANGE[1] if name == "longrange1920" else CONFIGS[CONFIG_INDEX]
+    cfg = (LONGRANGE[1] if name == "longrange1920" else
+           CONFIGS[2] if name == "bridged6480" else CONFIGS[CONFIG_INDEX])
     pos, L, _ = fcc_c60_crystal(cfg["ncell"], cfg["a"], cfg["jitter"], cfg["seed"],
                                 cfg["bridges"])
     p = workload_params(cfg, defl_tol=1e-9)
@@ -105,13 +122,21 @@ def list_launches(L, Rc):
     return 7 if int(L / (Rc + 0.01)) >= 3 else 4
 
 
-def config_dict(cfg, n, extra):
+L2_NOTE = ("L2 flushed between timed steps on the GPU (256 MB write); the oracle arm "
+           "runs on the host")
+
+
+def config_dict(cfg, n, world=1, extra=None):
+    """The workload, identical for the GPU arm and the oracle (reference) arm;
+    run settings of one arm go to the line's "run" key instead."""
     d = {"workload": cfg["name"], "n_atoms": n, "a": cfg["a"], "ncell": cfg["ncell"],
-         "Rc": cfg["Rc"], "krylov_r": cfg["r"], "kT": cfg["kT"]}
+         "Rc": cfg["Rc"], "krylov_r": cfg["r"], "kT": cfg["kT"], "l2": L2_NOTE,
+         "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
     if cfg.get("model") == "longrange":
         d.update(model="synthetic long-range GSP hoppings (nc 2, rc 4.0 A, tail 6.5-7.0 A)",
                  rm=7.0, max_hnbr=cfg["max_hnbr"], max_cluster=cfg["max_cluster"])
-    d.update(extra)
+    if extra:
+        d.update(extra)
     return d
 
 
@@ -220,7 +245,7 @@ def run_reference(args):
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     cfg, pos, L, p = workload(args.workload)
-    if cfg.get("model") == "longrange":
+    if cfg.get("model") == "longrange" or args.workload == "bridged6480":
         for _ in range(args.warmup):
             oracle_target_sample(pos, L, p, k=2)
         per_atom = []
@@ -236,7 +261,7 @@ def run_reference(args):
                 "ms_per_step": 1e3 * statistics.mean(per_atom) * len(pos),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic", "impl": "reference",
-                "config": config_dict(cfg, len(pos), {"l2": "n/a (CPU)"}),
+                "config": config_dict(cfg, len(pos), int(os.environ.get("WORLD_SIZE", "1"))),
                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                                  "sample": sample},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -264,7 +289,7 @@ def run_reference(args):
             "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": config_dict(cfg, len(pos), {"l2": "n/a (CPU)"}),
+            "config": config_dict(cfg, len(pos), int(os.environ.get("WORLD_SIZE", "1"))),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -394,6 +419,39 @@ def kernel_traffic(prec, name="krylov_traffic.json", workload=None):
     return rec.get("dram_bytes_per_launch", {}).get(prec)
 
 
+def timed_leg(system, steps, flush, stream, B):
+    """Mean ms per graph replay (L2 flushed before each) and mean stage times
+    of `steps` replays of an already captured system."""
+    import torch
+    for _ in range(3):
+        system.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot, st = 0.0, {k: [] for k in B.STAGES}
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0.record(stream)
+        system.replay()
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+        for name, v in B.tb_profile_read(system.ctx).items():
+            if v >= 0:
+                st[name].append(v)
+    system.check()
+    return tot / steps, {k: statistics.mean(v) for k, v in st.items() if v}
+
+
+def kernel_traffic_record(prec, name, workload):
+    """{"dram": bytes, "l2": bytes} per launch of the dominant kernel from the
+    committed ncu record, or None if stale or of another workload."""
+    d = kernel_traffic(prec, name, workload)
+    if d is None:
+        return None
+    rec = json.load(open(os.path.join(ROOT, "profiles", name)))
+    return {"dram": d, "l2": rec.get("l2_bytes_per_launch", {}).get(prec)}
+
+
 def run_ours(args):
     import torch
     import __graft_entry__
@@ -417,6 +475,7 @@ def run_ours(args):
 
     cfg, pos, L, p = workload(args.workload)
     longrange = cfg.get("model") == "longrange"
+    sampled = longrange or args.workload == "bridged6480"   # oracle on a bounded sample
     p["reorth_passes"] = args.reorth_passes
     p["reorth_every"] = args.reorth_every
     grouped = args.group_m > 1
@@ -428,7 +487,7 @@ def run_ours(args):
     ref = None
     cpu_all = None
     lr_recs = None
-    if rank == 0 and not args.no_cpu_baseline and longrange:
+    if rank == 0 and not args.no_cpu_baseline and sampled:
         # a full oracle evaluation of this cell takes minutes: a bounded sample
         t_atom, nu, lr_recs = oracle_target_sample(pos, L, p, k=4)
         cpu_base = {"value": 1.0 / t_atom, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -454,6 +513,9 @@ def run_ours(args):
     system = tb.TBSystem(n, L, p, prec=args.prec, device=dev)
     B.tb_profile_enable(system.ctx, True)
     system.set_positions(pos)
+    tune = None
+    if args.prec != "fp64" and not grouped and not args.no_autotune:
+        tune = system.autotune()
     system.capture()
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -528,14 +590,20 @@ def run_ours(args):
         kry = [v for v in stage_ms["krylov"] if v > 0]
         kry_ms = statistics.mean(kry) if kry else None
         launches_per_step = B.tb_ctx_kernels_per_evaluation(system.ctx, n, L)
+        mixed = args.prec != "fp64"
         # the mixed path runs the eigensolve inside the Krylov launch when the
         # library counts no separate eigensolver kernel
-        persistent = (args.prec == "mixed" and not grouped
-                      and launches_per_step == list_launches(L, p["Rc"]) + 1 + 1 + 1 + 4)
-        alg = (algorithmic_sweep_bytes_grouped(system, args.prec) if grouped
-               else algorithmic_sweep_bytes(system, args.prec))
-        if persistent:
-            alg += record_bytes(system, args.prec)
+        if tune is not None:
+            plan = tune["schedule"]
+        elif mixed and not grouped and launches_per_step == list_launches(L, p["Rc"]) + 1 + 1 + 1 + 4:
+            plan = "persistent"
+        else:
+            plan = "separate"
+        persistent = plan in ("persistent", "persistent_largest_first")
+        sweep_prec = "fp64" if not mixed else "mixed"
+        sweep = (algorithmic_sweep_bytes_grouped(system, sweep_prec) if grouped
+                 else algorithmic_sweep_bytes(system, sweep_prec))
+        alg = sweep + (record_bytes(system, sweep_prec) if persistent else 0)
         peaks = {}
         pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
         if os.path.exists(pk):
@@ -546,31 +614,83 @@ def run_ours(args):
                  "per group)" if grouped else
                  "kry_eig_kernel (block Lanczos targets then projected eigensolves from one "
                  "work queue)" if persistent else
-                 "krylov_kernel (block Lanczos H.V sweeps + reorthogonalisation, one CTA per "
-                 "target)")
+                 "krylov_sk_kernel (one launch per cluster-size bucket; kernel_ms is the "
+                 "Krylov stage, all launches)" if plan == "bucketed" else
+                 "krylov_sk_kernel (block Lanczos on Slater-Koster records, one CTA per target)"
+                 if mixed else
+                 "krylov_kernel (FP64 block Lanczos, one CTA per target)")
+        tr = kernel_traffic_record(args.prec, "krylov_group_traffic.json" if grouped
+                                   else "krylov_traffic_longrange.json" if longrange
+                                   else "krylov_traffic.json", cfg["name"])
+        traffic = tr.get("dram") if tr else None
         roof = {"bound": "hbm", "kernel": kname,
                 "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "frac": achieved / hbm if achieved else None,
-                "traffic": kernel_traffic(args.prec, "krylov_group_traffic.json" if grouped
-                                          else "krylov_traffic_longrange.json" if longrange
-                                          else "krylov_traffic.json", cfg["name"]),
-                "algorithmic_bytes_per_launch": alg, "kernel_ms": kry_ms}
+                "traffic": traffic,
+                "algorithmic_bytes": "sweep bytes of the scope table's definition (dense 4x4 "
+                                     "bond blocks and the basis block, read and written, per "
+                                     "sweep)" + (" plus the spectral records the launch "
+                                                 "writes and reads back" if persistent else ""),
+                "algorithmic_bytes_per_launch": alg, "kernel_ms": kry_ms,
+                # measured DRAM use of the same launch (ncu record of this
+                # workload) and its L2 traffic: the level that binds
+                "dram_frac": (traffic / (kry_ms * 1e-3) / 1e9 / hbm
+                              if traffic and kry_ms else None),
+                "l2_bytes_per_launch": tr.get("l2") if tr else None,
+                "l2_GBps": (tr["l2"] / (kry_ms * 1e-3) / 1e9
+                            if tr and tr.get("l2") and kry_ms else None)}
         stages = {k: (statistics.mean([x for x in v if x >= 0]) if any(x >= 0 for x in v)
                       else None) for k, v in stage_ms.items()}
+        extra = {}
+        if mixed and not grouped and not args.no_fp64_compare:
+            # the comparison the metric is named after: the plain FP64 path on
+            # the same GPU, same cell, same Lanczos settings
+            s64 = tb.TBSystem(n, L, p, prec="fp64", device=dev)
+            B.tb_profile_enable(s64.ctx, True)
+            s64.set_positions(pos)
+            s64.capture()
+            k64 = min(args.steps, 50)
+            ms64, st64 = timed_leg(s64, k64, flush, stream, B)
+            v64 = job_throughput(n, 1, k64, ms64 * k64)
+            F64 = s64.F.cpu().numpy()
+            s64.close()
+            import numpy as np
+            extra["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": k64,
+                             "stage_ms": st64,
+                             "mixed_vs_fp64_force_max_eV_per_A":
+                                 float(np.abs(system.F.cpu().numpy() - F64).max())}
+            extra["mixed_over_fp64"] = value / v64 / max(world, 1)
+        if persistent:
+            # the same sweeps as a separate launch, so that their own time and
+            # roofline can be read apart from the eigensolves sharing the queue
+            sep = tb.TBSystem(n, L, dict(p, schedule="separate"), prec=args.prec, device=dev)
+            B.tb_profile_enable(sep.ctx, True)
+            sep.set_positions(pos)
+            sep.capture()
+            ms_sep, st_sep = timed_leg(sep, min(args.steps, 100), flush, stream, B)
+            sep.close()
+            ksep = st_sep.get("krylov")
+            a_sep = sweep / (ksep * 1e-3) / 1e9 if ksep else None
+            extra["roofline_sweeps"] = {
+                "bound": "hbm", "kernel": "krylov_sk_kernel (separate launch, same settings)",
+                "achieved": a_sep, "peak": hbm, "unit": "GB/s",
+                "frac": a_sep / hbm if a_sep else None, "kernel_ms": ksep,
+                "algorithmic_bytes_per_launch": sweep,
+                "step_ms_with_separate_launches": ms_sep}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if args.prec == "mixed" else "f64", "data": "synthetic",
-            "config": config_dict(cfg, n, {
-                "precision": args.prec, "l2": "flushed between steps (256 MB write)",
-                "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                "graph": "one CUDA graph per force evaluation",
-                "reorth_passes": args.reorth_passes,
-                "reorth_every": args.reorth_every,
-                **({"group_m": args.group_m, "max_union": args.max_union,
-                    "form": "m-target union clusters (Eq. lanczos_blas3)"} if grouped else {})}),
+            "dtype": {"mixed": "f32+f64", "bf16": "bf16+f32+f64"}.get(args.prec, "f64"),
+            "data": "synthetic",
+            "config": config_dict(cfg, n, world),
+            "run": {"precision": args.prec, "graph": "one CUDA graph per force evaluation",
+                    "reorth_passes": args.reorth_passes, "reorth_every": args.reorth_every,
+                    "schedule": plan,
+                    **({"group_m": args.group_m, "max_union": args.max_union,
+                        "form": "m-target union clusters (Eq. lanczos_blas3)"}
+                       if grouped else {})},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 3 * 8,
                     "d2h_bytes_per_step": n * 3 * 8 + 8 * 8},
             "roofline": roof,
@@ -580,6 +700,8 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "stage_ms": stages,
             "accuracy": accuracy,
+            "autotune": tune,
+            **extra,
         }
         print(json.dumps(line), flush=True)
     system.close()

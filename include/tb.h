@@ -111,7 +111,17 @@ typedef enum tb_schedule {
    * Krylov targets leave idle (mixed path, single-target clusters). */
   TB_SCHED_PERSISTENT = 1,
   /* Separate block-Lanczos and eigensolver launches. */
-  TB_SCHED_SEPARATE = 2
+  TB_SCHED_SEPARATE = 2,
+  /* The persistent queue with the targets taken in decreasing cluster size
+   * (the longest block-Lanczos runs start first; one more small launch sorts
+   * the targets into size bins of 8 atoms). */
+  TB_SCHED_PERSISTENT_LARGEST_FIRST = 3,
+  /* Separate launches per cluster-size bucket, each with its own tile: the
+   * bucket's largest cluster sizes the shared-memory basis blocks, with its
+   * own share of shared memory for the Slater-Koster records and its own
+   * register budget (CTAs per SM); then the eigensolver.  Buckets and tiles
+   * come from tb_autotune, else four equal size ranges up to max_cluster. */
+  TB_SCHED_BUCKETED = 4
 } tb_schedule;
 
 typedef struct tb_ctx tb_ctx;
@@ -288,6 +298,50 @@ tb_status tb_krylov_density_grouped(tb_ctx* ctx, int n, int n_groups, const int*
                                     const double* Hblk, const float* Hsk,
                                     double* lambda, double* S, double* P, int* kdim,
                                     void* stream);
+
+/*
+ * Autotuner of the mixed path's block-Lanczos launch (the paper's cost per
+ * target grows as O(n_c^3) with the cluster size n_c, Sec. 2, and clusters are
+ * uneven in compressed or polymerised crystals).  On the given lists (as from
+ * tb_build_neighbors / tb_assemble_H) it times, with CUDA events on `stream`:
+ *   - the persistent Krylov + eigensolve queue, in index order and largest
+ *     clusters first;
+ *   - separate launches per cluster-size bucket, for partitions of the
+ *     observed size range into 1..TB_TUNE_MAX_BUCKETS buckets, each bucket's
+ *     tile chosen among shared-memory record capacities (6 or 8 records per
+ *     cluster slot) and register budgets (4 or 5 CTAs per SM) by timing that
+ *     bucket alone, plus the separate eigensolver;
+ * and keeps the fastest plan in the context: later calls with schedule
+ * TB_SCHED_AUTO use it (the plan applies to any lists: each target goes to the
+ * bucket of its cluster size).  Finally it runs the chosen plan once, so that
+ * lambda, S, P, kdim hold the record of the given lists.  Synchronises the
+ * stream; not capturable (tune before capturing a graph).  Mixed and BF16
+ * precision with group_m == 1 only (else TB_ERR_INVALID_ARG).
+ * report (host, may be NULL) receives the histogram and the choices.
+ */
+#define TB_TUNE_MAX_BUCKETS 4
+#define TB_TUNE_BINS 128
+typedef struct tb_tune_report {
+  int bin_width;                               /* atoms per histogram bin (8)          */
+  int n_bins;                                  /* bins in use: ceil(max_cluster / 8)   */
+  int hist[TB_TUNE_BINS];                      /* targets with cluster size in
+                                                * (q bin_width, (q+1) bin_width]       */
+  int schedule;                                /* the chosen tb_schedule               */
+  float ms_persistent;                         /* Krylov + eigensolve time, per plan   */
+  float ms_persistent_largest_first;
+  float ms_separate;
+  float ms_bucketed;                           /* best partition into buckets          */
+  int n_buckets;                               /* of the best bucketed plan            */
+  int bucket_hi[TB_TUNE_MAX_BUCKETS];          /* bucket b: sizes (hi[b-1], hi[b]]     */
+  int bucket_count[TB_TUNE_MAX_BUCKETS];       /* targets in the bucket                */
+  int bucket_records_per_slot[TB_TUNE_MAX_BUCKETS];
+  int bucket_ctas_per_sm[TB_TUNE_MAX_BUCKETS];
+  float bucket_ms[TB_TUNE_MAX_BUCKETS];        /* the bucket's block-Lanczos launch    */
+} tb_tune_report;
+
+tb_status tb_autotune(tb_ctx* ctx, int n, const int* c_off, const int* c_idx, const int* h_off,
+                      const int* h_idx, const double* Hblk, const float* Hsk, double* lambda,
+                      double* S, double* P, int* kdim, tb_tune_report* report, void* stream);
 
 /*
  * Number of kernels of this library that one force evaluation of n atoms in a

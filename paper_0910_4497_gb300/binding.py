@@ -21,7 +21,11 @@ TB_PREC_FP64 = 0
 TB_PREC_MIXED = 1
 TB_PREC_BF16 = 2
 PRECISIONS = {"fp64": TB_PREC_FP64, "mixed": TB_PREC_MIXED, "bf16": TB_PREC_BF16}
-SCHEDULES = {"auto": 0, "persistent": 1, "separate": 2}
+SCHEDULES = {"auto": 0, "persistent": 1, "separate": 2, "persistent_largest_first": 3,
+             "bucketed": 4}
+SCHEDULE_NAMES = {v: k for k, v in SCHEDULES.items()}
+TUNE_MAX_BUCKETS = 4
+TUNE_BINS = 128
 
 EXPORTS = ["tb_params_default", "tb_ctx_create", "tb_ctx_destroy", "tb_ctx_reserve",
            "tb_ctx_workspace_bytes", "tb_get_status", "tb_build_neighbors",
@@ -29,7 +33,7 @@ EXPORTS = ["tb_params_default", "tb_ctx_create", "tb_ctx_destroy", "tb_ctx_reser
            "tb_profile_enable", "tb_profile_read", "tb_find_mu_static",
            "tb_virial", "tb_ctx_reserve_local", "tb_local_forward", "tb_local_gradient",
            "tb_group_atoms", "tb_krylov_density_grouped", "tb_ctx_kernels_per_evaluation",
-           "tb_npt_berendsen", "tb_version"]
+           "tb_npt_berendsen", "tb_autotune", "tb_version"]
 
 
 class TBParams(ctypes.Structure):
@@ -42,6 +46,19 @@ class TBParams(ctypes.Structure):
               [("timeout_cycles", ctypes.c_longlong), ("reorth_every", ctypes.c_int),
                ("group_m", ctypes.c_int), ("max_union", ctypes.c_int),
                ("schedule", ctypes.c_int)]
+
+
+class TBTuneReport(ctypes.Structure):
+    _fields_ = [("bin_width", ctypes.c_int), ("n_bins", ctypes.c_int),
+                ("hist", ctypes.c_int * TUNE_BINS), ("schedule", ctypes.c_int),
+                ("ms_persistent", ctypes.c_float), ("ms_persistent_largest_first", ctypes.c_float),
+                ("ms_separate", ctypes.c_float), ("ms_bucketed", ctypes.c_float),
+                ("n_buckets", ctypes.c_int),
+                ("bucket_hi", ctypes.c_int * TUNE_MAX_BUCKETS),
+                ("bucket_count", ctypes.c_int * TUNE_MAX_BUCKETS),
+                ("bucket_records_per_slot", ctypes.c_int * TUNE_MAX_BUCKETS),
+                ("bucket_ctas_per_sm", ctypes.c_int * TUNE_MAX_BUCKETS),
+                ("bucket_ms", ctypes.c_float * TUNE_MAX_BUCKETS)]
 
 
 class TBError(RuntimeError):
@@ -83,6 +100,7 @@ def load_library(path=LIB_PATH):
         "tb_group_atoms": [P, I, VP, D, VP, VP, VP],
         "tb_ctx_kernels_per_evaluation": [P, I, D, ctypes.POINTER(I)],
         "tb_krylov_density_grouped": [P, I, I, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP],
+        "tb_autotune": [P, I, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, ctypes.POINTER(TBTuneReport), VP],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -230,6 +248,31 @@ def tb_krylov_density_grouped(ctx, n, n_groups, g_off, g_idx, c_off, c_idx, h_of
         _ptr(h_off, i32, "h_off"), _ptr(h_idx, i32, "h_idx"), _ptr(Hblk, f64, "Hblk"),
         _ptr(Hsk, torch.float32, "Hsk"), _ptr(lam, f64, "lambda"),
         _ptr(S, f64, "S"), _ptr(P, f64, "P"), _ptr(kdim, i32, "kdim"), _stream(stream)))
+
+
+def tb_autotune(ctx, n, c_off, c_idx, h_off, h_idx, Hblk, Hsk, lam, S, P, kdim, stream=None):
+    """Times the launch plans of the mixed Krylov stage on these lists and keeps
+    the fastest in the context; returns the report as a dict."""
+    i32, f64 = torch.int32, torch.float64
+    r = TBTuneReport()
+    _check("tb_autotune", lib().tb_autotune(
+        ctx, n, _ptr(c_off, i32, "c_off"), _ptr(c_idx, i32, "c_idx"), _ptr(h_off, i32, "h_off"),
+        _ptr(h_idx, i32, "h_idx"), _ptr(Hblk, f64, "Hblk"), _ptr(Hsk, torch.float32, "Hsk"),
+        _ptr(lam, f64, "lambda"), _ptr(S, f64, "S"), _ptr(P, f64, "P"), _ptr(kdim, i32, "kdim"),
+        ctypes.byref(r), _stream(stream)))
+    nb = r.n_buckets
+    inf = 1e29
+    return {"histogram": {"bin_width": r.bin_width,
+                          "counts": list(r.hist[:r.n_bins])},
+            "schedule": SCHEDULE_NAMES.get(r.schedule, r.schedule),
+            "ms": {k: (v if v < inf else None) for k, v in
+                   (("persistent", r.ms_persistent),
+                    ("persistent_largest_first", r.ms_persistent_largest_first),
+                    ("separate", r.ms_separate), ("bucketed", r.ms_bucketed))},
+            "buckets": [{"sizes_up_to": r.bucket_hi[b], "targets": r.bucket_count[b],
+                         "records_per_slot_in_smem": r.bucket_records_per_slot[b],
+                         "ctas_per_sm": r.bucket_ctas_per_sm[b], "ms": r.bucket_ms[b]}
+                        for b in range(nb)]}
 
 
 def tb_find_mu(ctx, n, lam, S, kdim, n_electrons, mu_guess, mu, n_count=None, stream=None):

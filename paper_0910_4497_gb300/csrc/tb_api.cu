@@ -29,7 +29,7 @@ tb_status check_params(const tb_params& p) {
   if (p.max_union < 0 || p.max_union > tbk::MAX_CLUSTER) return TB_ERR_INVALID_ARG;
   if (p.mu_max_iter < 1 || !(p.mu_tol > 0.0) || !(p.defl_tol >= 0.0)) return TB_ERR_INVALID_ARG;
   if (p.timeout_cycles <= 0) return TB_ERR_INVALID_ARG;
-  if (p.schedule < TB_SCHED_AUTO || p.schedule > TB_SCHED_SEPARATE) return TB_ERR_INVALID_ARG;
+  if (p.schedule < TB_SCHED_AUTO || p.schedule > TB_SCHED_BUCKETED) return TB_ERR_INVALID_ARG;
   if (!finite_pos(p.Es) || !finite_pos(p.Ep)) return TB_ERR_INVALID_ARG;
   return TB_OK;
 }
@@ -75,6 +75,8 @@ size_t carve(tb_ctx* c, int n, unsigned char* base) {
   c->recg = k.take<float4>(krylov_overflow_records(c));
   c->rslg = k.take<int>(krylov_overflow_records(c));
   c->ke_work = k.take<int>((size_t)n + 1);
+  c->tgt_order = k.take<int>(n);
+  c->tgt_boff = k.take<int>(tb_plan::MAX_BINS + 1);
   c->grp_V = k.take<unsigned char>(krylov_group_basis_bytes(c));
   c->grp_lent = k.take<int2>((size_t)c->grp_grid * c->grp_max_union * p.max_hnbr);
   c->grp_cnt = k.take<int>(n);
@@ -464,6 +466,18 @@ tb_status tb_local_gradient(tb_ctx* c, int n, const double* pos, double L, const
                                Zstore, mu, F, s);
 }
 
+tb_status tb_autotune(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int* h_off,
+                      const int* h_idx, const double* Hblk, const float* Hsk, double* lambda,
+                      double* S, double* P, int* kdim, tb_tune_report* report, void* stream) {
+  (void)Hblk;
+  tb_status st = ready(c, n);
+  if (st != TB_OK) return st;
+  if (!c_off || !c_idx || !h_off || !h_idx || !Hsk || !lambda || !S || !P || !kdim)
+    return TB_ERR_INVALID_ARG;
+  return krylov_autotune(c, n, c_off, c_idx, h_off, h_idx, Hsk, lambda, S, P, kdim, report,
+                         static_cast<cudaStream_t>(stream));
+}
+
 tb_status tb_ctx_kernels_per_evaluation(const tb_ctx* c, int n, double L, int* count) {
   if (!c || !count || n < 0 || !(L > 0.0)) return TB_ERR_INVALID_ARG;
   if (n > c->reserved_n || !c->ws) return TB_ERR_NOT_RESERVED;
@@ -473,7 +487,7 @@ tb_status tb_ctx_kernels_per_evaluation(const tb_ctx* c, int n, double L, int* c
   if (c->p.group_m > 1) {
     k += 2 + 1;                                        // grouping; grouped block Lanczos
   } else {
-    k += 1;                                            // block Lanczos
+    k += krylov_kernel_count(c, n);                    // block Lanczos (+ size bins)
     if (krylov_eig_persistent(c, n)) eig = 0;          // eigensolve inside the Krylov launch
   }
   *count = k + eig + 1 + 4;                            // mu; rho, bond forces, sums, energies

@@ -23,6 +23,21 @@ __host__ __device__ __forceinline__ int tc_index(int x, int y) {
   return -1;
 }
 
+namespace tb_plan {
+constexpr int MAX_BUCKETS = TB_TUNE_MAX_BUCKETS;
+constexpr int MAX_BINS = TB_TUNE_BINS;
+constexpr int BIN = 8;                // atoms per size bin
+}
+
+// Tile of one launch of the mixed-path block-Lanczos kernel.
+struct tb_sk_cfg {
+  int mc = 0;                         // cluster capacity of the basis blocks
+  int ecap = 0;                       // Slater-Koster records in shared memory
+  int minb = 4;                       // CTAs per SM the register budget allows
+  int grid = 0;                       // CTAs of the launch
+  size_t smem = 0;
+};
+
 namespace tbk {
 
 constexpr int MAX_R = 16;           // Krylov block order cap -> NT <= 64
@@ -196,6 +211,14 @@ struct tb_ctx {
   int sk_ecap = 0;                   // local records kept in shared memory per target
   int sk_grid = 0;                   // CTAs of the mixed Krylov kernel (separate launch)
   size_t sk_smem = 0;
+  // launch plan of the mixed Krylov stage: tb_autotune's choice or defaults
+  bool tuned = false;
+  int plan = 0;                      // tb_schedule in force when schedule == AUTO and tuned
+  int plan_nb = 0;                   // buckets of the bucketed plan
+  int plan_hi[tb_plan::MAX_BUCKETS] = {};
+  tb_sk_cfg plan_cfg[tb_plan::MAX_BUCKETS];
+  int* tgt_order = nullptr;          // n: targets by bucket
+  int* tgt_boff = nullptr;           // MAX_BINS + 1: bucket offsets
   int* ke_work = nullptr;            // n + 1: work counter, then per-target Krylov-done flags
   int eig_grid = 0;
   int eig_warps = 0;                 // targets per CTA of the warp eigensolver
@@ -246,6 +269,11 @@ tb_status launch_assemble(tb_ctx* c, int n, const double* pos, double L,
                           double* dHblk, float* Hsk, cudaStream_t s);
 tb_status krylov_configure(tb_ctx* c);
 bool krylov_eig_persistent(const tb_ctx* c, int n);   // Krylov launch includes the eigensolve
+int krylov_schedule(const tb_ctx* c, int n);          // tb_schedule a launch of n targets uses
+int krylov_kernel_count(const tb_ctx* c, int n);      // kernels of the Krylov (+eig) stage
+tb_status krylov_autotune(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int* h_off,
+                          const int* h_idx, const float* Hsk, double* lambda, double* S,
+                          double* P, int* kdim, tb_tune_report* rep, cudaStream_t s);
 tb_status launch_krylov(tb_ctx* c, int n, const int* c_off, const int* c_idx,
                         const int* h_off, const int* h_idx, const double* Hblk,
                         const float* Hsk, double* lambda, double* S, double* P, int* kdim,

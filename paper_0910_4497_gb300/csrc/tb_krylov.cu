@@ -26,6 +26,9 @@
 // The basis lives in shared memory when r * 4 * max_cluster * 4 values fit,
 // otherwise in a per-CTA slot of global memory (L2-resident).
 // Layout of the basis: block b occupies Dmax*4 values, row-major [row][4].
+#include <algorithm>
+#include <cstring>
+#include <new>
 #include "tb_internal.cuh"
 #include "tb_eig_group.cuh"
 #include "tb_krylov_common.cuh"
@@ -652,7 +655,8 @@ __device__ __forceinline__ int ld_acquire_s32(const int* p) {
 // through L2.  work[0] and done[0..n) are zero at launch.
 template <int NTC, bool BF>
 __global__ void __launch_bounds__(128, 4) kry_eig_kernel(const tbsk::SkArgs a, const XArgs xa,
-                                                         int* work, int* done, long long timeout) {
+                                                         const int* order, int* work, int* done,
+                                                         long long timeout) {
   __shared__ int s_item;
   __shared__ int s_ok[2];
   extern __shared__ __align__(32) unsigned char smem[];
@@ -664,13 +668,15 @@ __global__ void __launch_bounds__(128, 4) kry_eig_kernel(const tbsk::SkArgs a, c
     const int it = s_item;
     if (it >= nitems) break;
     if (it < n) {
-      tbsk::krylov_sk_target<BF>(a, it);
+      const int i = order ? order[it] : it;
+      tbsk::krylov_sk_target<BF>(a, i);
       __threadfence();
       __syncthreads();
-      if (threadIdx.x == 0) atomicExch(done + it, 1);
+      if (threadIdx.x == 0) atomicExch(done + i, 1);
     } else {
       const int grp = threadIdx.x >> 6;
-      const int i = 2 * (it - n) + grp;
+      const int q = 2 * (it - n) + grp;
+      const int i = q < n ? (order ? order[q] : q) : n;
       if (i < n) {
         Grp g;
         g.t = threadIdx.x & 63;
@@ -699,10 +705,53 @@ __global__ void __launch_bounds__(128, 4) kry_eig_kernel(const tbsk::SkArgs a, c
 }
 
 // Separate launch of the mixed-path block Lanczos: one CTA per target,
-// persistent grid-stride.
-template <bool BF>
-__global__ void __launch_bounds__(tbsk::KT, 4) krylov_sk_kernel(const tbsk::SkArgs a) {
-  for (int i = blockIdx.x; i < a.n; i += gridDim.x) tbsk::krylov_sk_target<BF>(a, i);
+// persistent grid-stride, over all targets or over bucket b of a target order
+// (targets order[boff[b] .. boff[b+1])).  MINB CTAs per SM bound the registers.
+template <bool BF, int MINB>
+__global__ void __launch_bounds__(tbsk::KT, MINB) krylov_sk_kernel(const tbsk::SkArgs a,
+                                                                   const int* order,
+                                                                   const int* boff, int b) {
+  const int beg = order ? boff[b] : 0;
+  const int cnt = order ? boff[b + 1] - beg : a.n;
+  for (int j = blockIdx.x; j < cnt; j += gridDim.x)
+    tbsk::krylov_sk_target<BF>(a, order ? order[beg + j] : j);
+}
+
+// Targets sorted into cluster-size buckets (one block): bin q = sizes
+// (q width, (q+1) width], bucket map[bin]; desc puts the largest bucket first.
+// Order within a bucket follows the atomics (each target's result does not
+// depend on its position).
+struct BucketMap {
+  int width, nbins, nb, desc;
+  int map[tb_plan::MAX_BINS];
+};
+
+__global__ void __launch_bounds__(1024) bucket_kernel(int n, const int* __restrict__ c_off,
+                                                      const BucketMap m, int* __restrict__ order,
+                                                      int* __restrict__ boff) {
+  __shared__ int cnt[tb_plan::MAX_BINS], cur[tb_plan::MAX_BINS];
+  for (int b = threadIdx.x; b < m.nb; b += blockDim.x) cnt[b] = 0;
+  __syncthreads();
+  auto bucket = [&](int i) {
+    const int sz = c_off[i + 1] - c_off[i];
+    int bin = (sz - 1) / m.width;
+    bin = bin < 0 ? 0 : (bin >= m.nbins ? m.nbins - 1 : bin);
+    const int b = m.map[bin];
+    return m.desc ? m.nb - 1 - b : b;
+  };
+  for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&cnt[bucket(i)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int b = 0; b < m.nb; ++b) {
+      boff[b] = run;
+      cur[b] = run;
+      run += cnt[b];
+    }
+    boff[m.nb] = run;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) order[atomicAdd(&cur[bucket(i)], 1)] = i;
 }
 
 tbsk::SkArgs sk_args(const tb_ctx* c, int n, const int* c_off, const int* c_idx,
@@ -723,33 +772,75 @@ tbsk::SkArgs sk_args(const tb_ctx* c, int n, const int* c_off, const int* c_idx,
   return a;
 }
 
-template <bool BF>
-tb_status sk_configure_t(tb_ctx* c, int max_smem) {
-  const tb_params& p = c->p;
-  const int MC = p.max_cluster;
-  // records kept in shared memory: 8 per cluster slot (carbon within 2.6 A:
-  // ~8 in-cluster neighbours on average); none when the Hamiltonian lists are
-  // long (long-range hoppings), where they would not fit anyway
-  c->sk_ecap = p.max_hnbr > 48 ? 0 : 8 * MC;
-  size_t bytes = tbsk::sk_smem_bytes<BF>(p.r, MC, c->sk_ecap);
-  if ((int)bytes > max_smem) {
-    c->sk_ecap = 0;
-    bytes = tbsk::sk_smem_bytes<BF>(p.r, MC, 0);
-  }
-  if ((int)bytes > max_smem) return TB_ERR_CAPACITY;
-  TB_CUDA_TRY(cudaFuncSetAttribute(krylov_sk_kernel<BF>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  int occ = 0;
-  TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, krylov_sk_kernel<BF>,
-                                                            tbsk::KT, bytes));
-  if (occ < 1) return TB_ERR_CAPACITY;
-  c->sk_smem = bytes;
-  c->sk_grid = c->num_sms * occ;
-  c->kry_threads = tbsk::KT;
-  c->kry_grid = c->sk_grid;
+template <bool BF, int MINB>
+tb_status sk_occupancy(size_t smem, int* occ) {
+  TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, krylov_sk_kernel<BF, MINB>,
+                                                            tbsk::KT, smem));
   return TB_OK;
 }
 
+// Tile of a launch over clusters of up to mc atoms with `slots` records per
+// cluster slot in shared memory (0: all records in the overflow slot) and a
+// register budget for minb CTAs per SM.  The per-CTA global slots are sized
+// for kry_grid CTAs of max_cluster: a tile must not need more.
+template <bool BF>
+tb_status sk_tile(const tb_ctx* c, int mc, int slots, int minb, int max_smem, tb_sk_cfg& t) {
+  const tb_params& p = c->p;
+  t.mc = mc;
+  t.minb = minb;
+  t.ecap = (p.max_hnbr > 48) ? 0 : slots * mc;
+  t.smem = tbsk::sk_smem_bytes<BF>(p.r, mc, t.ecap);
+  if ((int)t.smem > max_smem) {
+    t.ecap = 0;
+    t.smem = tbsk::sk_smem_bytes<BF>(p.r, mc, 0);
+  }
+  if ((int)t.smem > max_smem) return TB_ERR_CAPACITY;
+  int occ = 0;
+  tb_status st = minb == 5 ? sk_occupancy<BF, 5>(t.smem, &occ) : sk_occupancy<BF, 4>(t.smem, &occ);
+  if (st != TB_OK) return st;
+  if (occ < 1) return TB_ERR_CAPACITY;
+  t.grid = c->num_sms * occ;
+  if (c->kry_grid > 0 && (size_t)t.grid * mc > (size_t)c->kry_grid * p.max_cluster)
+    t.grid = (int)((size_t)c->kry_grid * p.max_cluster / mc);
+  return t.grid > 0 ? TB_OK : TB_ERR_CAPACITY;
+}
+
+template <bool BF>
+tb_status sk_configure_t(tb_ctx* c, int max_smem) {
+  const tb_params& p = c->p;
+  // the kernel variants may use up to the opt-in shared memory
+  TB_CUDA_TRY(cudaFuncSetAttribute(krylov_sk_kernel<BF, 4>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+  TB_CUDA_TRY(cudaFuncSetAttribute(krylov_sk_kernel<BF, 5>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+  // default tile: records kept in shared memory, 8 per cluster slot (carbon
+  // within 2.6 A: ~8 in-cluster neighbours on average); none when the
+  // Hamiltonian lists are long (long-range hoppings)
+  tb_sk_cfg t;
+  c->kry_grid = 0;
+  tb_status st = sk_tile<BF>(c, p.max_cluster, 8, 4, max_smem, t);
+  if (st != TB_OK) return st;
+  c->sk_ecap = t.ecap;
+  c->sk_smem = t.smem;
+  c->sk_grid = t.grid;
+  c->kry_threads = tbsk::KT;
+  // per-CTA slots: enough for the default tile and for tiles of smaller
+  // clusters at up to 5 CTAs per SM
+  c->kry_grid = c->num_sms * 5 > t.grid ? c->num_sms * 5 : t.grid;
+  // default buckets of the bucketed plan: four equal size ranges
+  c->plan_nb = 0;
+  for (int b = 0; b < tb_plan::MAX_BUCKETS; ++b) {
+    int hi = (p.max_cluster * (b + 1) + tb_plan::MAX_BUCKETS - 1) / tb_plan::MAX_BUCKETS;
+    hi = (hi + tb_plan::BIN - 1) / tb_plan::BIN * tb_plan::BIN;
+    if (hi > p.max_cluster || b == tb_plan::MAX_BUCKETS - 1) hi = p.max_cluster;
+    if (c->plan_nb > 0 && hi <= c->plan_hi[c->plan_nb - 1]) continue;
+    tb_sk_cfg tb_;
+    if (sk_tile<BF>(c, hi, 8, 4, max_smem, tb_) != TB_OK) return TB_ERR_CAPACITY;
+    c->plan_hi[c->plan_nb] = hi;
+    c->plan_cfg[c->plan_nb++] = tb_;
+  }
+  return TB_OK;
+}
 template <int NTC, bool BF>
 tb_status kry_eig_configure_t(tb_ctx* c, int max_smem) {
   const size_t eig = 2 * xw_smem_per_warp(4 * c->p.r);
@@ -778,36 +869,98 @@ tb_status kry_eig_configure(tb_ctx* c, int max_smem) {
   return kry_eig_configure_t<64, BF>(c, max_smem);
 }
 
+// Targets sorted into size buckets on the device: nb buckets with upper
+// bounds hi[0..nb) (sizes above the last go to the last), or with hi == null
+// one bucket per size bin, largest first.
+tb_status launch_buckets(tb_ctx* c, int n, const int* c_off, int nb, const int* hi,
+                         cudaStream_t s) {
+  BucketMap m;
+  m.width = tb_plan::BIN;
+  m.nbins = (c->p.max_cluster + tb_plan::BIN - 1) / tb_plan::BIN;
+  if (m.nbins > tb_plan::MAX_BINS) m.nbins = tb_plan::MAX_BINS;
+  if (hi) {
+    m.nb = nb;
+    m.desc = 0;
+    for (int q = 0; q < m.nbins; ++q) {
+      const int top = (q + 1) * tb_plan::BIN;     // largest size of the bin
+      int b = 0;
+      while (b < nb - 1 && top > hi[b]) ++b;
+      m.map[q] = b;
+    }
+  } else {
+    m.nb = m.nbins;
+    m.desc = 1;
+    for (int q = 0; q < m.nbins; ++q) m.map[q] = q;
+  }
+  bucket_kernel<<<1, 1024, 0, s>>>(n, c_off, m, c->tgt_order, c->tgt_boff);
+  TB_CUDA_TRY(cudaGetLastError());
+  return TB_OK;
+}
+
 template <bool BF>
 tb_status kry_eig_launch(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int* h_off,
                          const int* h_idx, const float* Hsk, double* lambda, double* S, double* P,
-                         int* kdim, cudaStream_t s) {
+                         int* kdim, bool largest_first, cudaStream_t s) {
   const tb_params& p = c->p;
   const tbsk::SkArgs a = sk_args(c, n, c_off, c_idx, h_off, h_idx, Hsk);
   XArgs xa{n, 4 * p.r, c->T, c->colmask, reinterpret_cast<const float*>(c->Y), h_off, c->Zf,
            c->lamf, lambda, S, P, kdim, c->d_status};
+  const int* order = nullptr;
+  if (largest_first) {
+    tb_status st = launch_buckets(c, n, c_off, 0, nullptr, s);
+    if (st != TB_OK) return st;
+    order = c->tgt_order;
+  }
   TB_CUDA_TRY(cudaMemsetAsync(c->ke_work, 0, sizeof(int) * ((size_t)n + 1), s));
   const int grid = c->ke_grid;
   int* work = c->ke_work;
   int* done = c->ke_work + 1;
   const int ntc = ntc_of(4 * p.r);
   const long long to = p.timeout_cycles;
-  if (ntc == 16) kry_eig_kernel<16, BF><<<grid, 128, c->ke_smem, s>>>(a, xa, work, done, to);
-  else if (ntc == 32) kry_eig_kernel<32, BF><<<grid, 128, c->ke_smem, s>>>(a, xa, work, done, to);
-  else if (ntc == 48) kry_eig_kernel<48, BF><<<grid, 128, c->ke_smem, s>>>(a, xa, work, done, to);
-  else kry_eig_kernel<64, BF><<<grid, 128, c->ke_smem, s>>>(a, xa, work, done, to);
+  const size_t sm = c->ke_smem;
+  if (ntc == 16) kry_eig_kernel<16, BF><<<grid, 128, sm, s>>>(a, xa, order, work, done, to);
+  else if (ntc == 32) kry_eig_kernel<32, BF><<<grid, 128, sm, s>>>(a, xa, order, work, done, to);
+  else if (ntc == 48) kry_eig_kernel<48, BF><<<grid, 128, sm, s>>>(a, xa, order, work, done, to);
+  else kry_eig_kernel<64, BF><<<grid, 128, sm, s>>>(a, xa, order, work, done, to);
+  TB_CUDA_TRY(cudaGetLastError());
+  return TB_OK;
+}
+
+// One launch of the record kernel with tile t over all targets (order null)
+// or over bucket b of the device order.
+template <bool BF>
+tb_status sk_launch_tile(tb_ctx* c, const tbsk::SkArgs& a0, const tb_sk_cfg& t, int n,
+                         const int* order, int b, cudaStream_t s) {
+  tbsk::SkArgs a = a0;
+  a.max_cluster = t.mc;
+  a.ecap = t.ecap;
+  int grid = t.grid;
+  if (!order && n < grid) grid = n;
+  if (grid <= 0) return TB_OK;
+  if (t.minb == 5)
+    krylov_sk_kernel<BF, 5><<<grid, tbsk::KT, t.smem, s>>>(a, order, c->tgt_boff, b);
+  else
+    krylov_sk_kernel<BF, 4><<<grid, tbsk::KT, t.smem, s>>>(a, order, c->tgt_boff, b);
   TB_CUDA_TRY(cudaGetLastError());
   return TB_OK;
 }
 
 template <bool BF>
 tb_status sk_launch(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int* h_off,
-                    const int* h_idx, const float* Hsk, cudaStream_t s) {
+                    const int* h_idx, const float* Hsk, bool bucketed, cudaStream_t s) {
   const tbsk::SkArgs a = sk_args(c, n, c_off, c_idx, h_off, h_idx, Hsk);
-  const int grid = n < c->sk_grid ? n : c->sk_grid;
-  if (grid <= 0) return TB_OK;
-  krylov_sk_kernel<BF><<<grid, tbsk::KT, c->sk_smem, s>>>(a);
-  TB_CUDA_TRY(cudaGetLastError());
+  if (!bucketed) {
+    tb_sk_cfg t;
+    t.mc = c->p.max_cluster; t.ecap = c->sk_ecap; t.minb = 4; t.grid = c->sk_grid;
+    t.smem = c->sk_smem;
+    return sk_launch_tile<BF>(c, a, t, n, nullptr, 0, s);
+  }
+  tb_status st = launch_buckets(c, n, c_off, c->plan_nb, c->plan_hi, s);
+  if (st != TB_OK) return st;
+  for (int b = 0; b < c->plan_nb; ++b) {
+    st = sk_launch_tile<BF>(c, a, c->plan_cfg[b], n, c->tgt_order, b, s);
+    if (st != TB_OK) return st;
+  }
   return TB_OK;
 }
 
@@ -862,18 +1015,41 @@ tb_status configure_t(tb_ctx* c, int max_smem) {
 
 }  // namespace
 
+int krylov_schedule(const tb_ctx* c, int n) {
+  if (c->p.prec == TB_PREC_FP64 || c->p.group_m > 1) return TB_SCHED_SEPARATE;
+  int sch = c->p.schedule;
+  if (sch == TB_SCHED_AUTO) {
+    if (c->tuned) {
+      sch = c->plan;
+    } else {
+      // the queue pays off where the targets fill a few waves of CTAs and the
+      // last wave would leave SMs idle; many waves leave a negligible tail
+      sch = (c->ke_on && n <= 16 * c->ke_grid) ? TB_SCHED_PERSISTENT : TB_SCHED_SEPARATE;
+    }
+  }
+  if ((sch == TB_SCHED_PERSISTENT || sch == TB_SCHED_PERSISTENT_LARGEST_FIRST) && !c->ke_on)
+    sch = TB_SCHED_SEPARATE;
+  return sch;
+}
+
 bool krylov_eig_persistent(const tb_ctx* c, int n) {
-  if (!c->ke_on || c->p.prec == TB_PREC_FP64) return false;
-  if (c->p.schedule == TB_SCHED_PERSISTENT) return true;
-  if (c->p.schedule == TB_SCHED_SEPARATE) return false;
-  // the queue pays off where the targets fill a few waves of CTAs and the last
-  // wave would leave SMs idle; many waves leave a negligible tail
-  return n <= 16 * c->ke_grid;
+  const int sch = krylov_schedule(c, n);
+  return sch == TB_SCHED_PERSISTENT || sch == TB_SCHED_PERSISTENT_LARGEST_FIRST;
+}
+
+int krylov_kernel_count(const tb_ctx* c, int n) {
+  switch (krylov_schedule(c, n)) {
+    case TB_SCHED_PERSISTENT: return 1;
+    case TB_SCHED_PERSISTENT_LARGEST_FIRST: return 2;               // size bins, queue
+    case TB_SCHED_BUCKETED: return 1 + c->plan_nb;                  // buckets, one launch each
+    default: return 1;
+  }
 }
 
 size_t krylov_basis_bytes_global(const tb_ctx* c) {
-  const size_t tv = c->p.prec == TB_PREC_FP64 ? sizeof(double) : sizeof(float);
-  return (size_t)c->kry_grid * 4 * c->p.max_cluster * 4 * c->p.r * tv;
+  if (c->p.prec == TB_PREC_FP64)
+    return (size_t)c->kry_grid * 16 * c->p.max_cluster * c->p.r * sizeof(double);
+  return (size_t)c->kry_grid * tbsk::SP * c->p.max_cluster * c->p.r * sizeof(float);
 }
 
 tb_status krylov_configure(tb_ctx* c) {
@@ -893,7 +1069,8 @@ tb_status krylov_configure(tb_ctx* c) {
   tb_status st = bf ? sk_configure_t<true>(c, max_smem) : sk_configure_t<false>(c, max_smem);
   if (st != TB_OK) return st;
   c->ke_on = false;
-  if (c->p.group_m == 1 && c->p.schedule != TB_SCHED_SEPARATE) {
+  if (c->p.group_m == 1 && c->p.schedule != TB_SCHED_SEPARATE &&
+      c->p.schedule != TB_SCHED_BUCKETED) {
     if ((bf ? kry_eig_configure<true>(c, max_smem) : kry_eig_configure<false>(c, max_smem)) != TB_OK)
       c->ke_on = false;
   }
@@ -909,19 +1086,204 @@ tb_status launch_krylov(tb_ctx* c, int n, const int* c_off, const int* c_idx,
                         const int* h_off, const int* h_idx, const double* Hblk,
                         const float* Hsk, double* lambda, double* S, double* P, int* kdim,
                         cudaStream_t s) {
-#define TB_KRY_DISPATCH(TV, H)                                                                \
-  do {                                                                                        \
-    if (c->kry_threads == 128)                                                                \
-      return launch_t<TV, 128>(c, n, c_off, c_idx, h_off, h_idx, H, lambda, S, P, kdim, s);   \
-    return launch_t<TV, 256>(c, n, c_off, c_idx, h_off, h_idx, H, lambda, S, P, kdim, s);     \
-  } while (0)
-  if (c->p.prec == TB_PREC_FP64) TB_KRY_DISPATCH(double, Hblk);
+  if (c->p.prec == TB_PREC_FP64) {
+    if (c->kry_threads == 128)
+      return launch_t<double, 128>(c, n, c_off, c_idx, h_off, h_idx, Hblk, lambda, S, P, kdim, s);
+    return launch_t<double, 256>(c, n, c_off, c_idx, h_off, h_idx, Hblk, lambda, S, P, kdim, s);
+  }
   if (!Hsk) return TB_ERR_INVALID_ARG;
   const bool bf = c->p.prec == TB_PREC_BF16;
-  if (krylov_eig_persistent(c, n))
-    return bf ? kry_eig_launch<true>(c, n, c_off, c_idx, h_off, h_idx, Hsk, lambda, S, P, kdim, s)
-              : kry_eig_launch<false>(c, n, c_off, c_idx, h_off, h_idx, Hsk, lambda, S, P, kdim, s);
-  return bf ? sk_launch<true>(c, n, c_off, c_idx, h_off, h_idx, Hsk, s)
-            : sk_launch<false>(c, n, c_off, c_idx, h_off, h_idx, Hsk, s);
-#undef TB_KRY_DISPATCH
+  const int sch = krylov_schedule(c, n);
+  if (sch == TB_SCHED_PERSISTENT || sch == TB_SCHED_PERSISTENT_LARGEST_FIRST) {
+    const bool lf = sch == TB_SCHED_PERSISTENT_LARGEST_FIRST;
+    return bf ? kry_eig_launch<true>(c, n, c_off, c_idx, h_off, h_idx, Hsk, lambda, S, P, kdim, lf, s)
+              : kry_eig_launch<false>(c, n, c_off, c_idx, h_off, h_idx, Hsk, lambda, S, P, kdim, lf, s);
+  }
+  const bool bk = sch == TB_SCHED_BUCKETED;
+  return bf ? sk_launch<true>(c, n, c_off, c_idx, h_off, h_idx, Hsk, bk, s)
+            : sk_launch<false>(c, n, c_off, c_idx, h_off, h_idx, Hsk, bk, s);
+}
+
+// ---------------------------------------------------------------- autotuner
+
+namespace {
+
+template <bool BF>
+tb_status tune_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int* h_off,
+                 const int* h_idx, const float* Hsk, double* lambda, double* S, double* P,
+                 int* kdim, tb_tune_report* rep, cudaStream_t s) {
+  const tb_params& p = c->p;
+  int dev = 0, max_smem = 0;
+  TB_CUDA_TRY(cudaGetDevice(&dev));
+  TB_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  // cluster sizes of the given lists
+  int* off = new (std::nothrow) int[(size_t)n + 1];
+  if (!off) return TB_ERR_NOMEM;
+  if (cudaMemcpyAsync(off, c_off, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    delete[] off;
+    return TB_ERR_CUDA;
+  }
+  tb_tune_report r;
+  memset(&r, 0, sizeof(r));
+  r.bin_width = tb_plan::BIN;
+  r.n_bins = (p.max_cluster + tb_plan::BIN - 1) / tb_plan::BIN;
+  if (r.n_bins > tb_plan::MAX_BINS) r.n_bins = tb_plan::MAX_BINS;
+  int* sz = new (std::nothrow) int[(size_t)n];
+  if (!sz) { delete[] off; return TB_ERR_NOMEM; }
+  for (int i = 0; i < n; ++i) {
+    sz[i] = off[i + 1] - off[i];
+    int q = (sz[i] - 1) / tb_plan::BIN;
+    q = q < 0 ? 0 : (q >= r.n_bins ? r.n_bins - 1 : q);
+    ++r.hist[q];
+  }
+  delete[] off;
+  std::sort(sz, sz + n);
+
+  cudaEvent_t e0, e1;
+  TB_CUDA_TRY(cudaEventCreate(&e0));
+  TB_CUDA_TRY(cudaEventCreate(&e1));
+  tb_status err = TB_OK;
+  // best of three timed runs (after one untimed) of fn
+  auto timed = [&](auto fn) -> float {
+    float best = 1e30f;
+    for (int rep_ = 0; rep_ < 4 && err == TB_OK; ++rep_) {
+      if (cudaEventRecord(e0, s) != cudaSuccess) { err = TB_ERR_CUDA; break; }
+      const tb_status st = fn();
+      if (st != TB_OK) { err = st; break; }
+      float ms = 0.f;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        err = TB_ERR_CUDA;
+        break;
+      }
+      if (rep_ > 0 && ms < best) best = ms;
+    }
+    return best;
+  };
+  const int saved_schedule = c->p.schedule;
+  const bool saved_tuned = c->tuned;
+  const int saved_plan = c->plan;
+  c->p.schedule = TB_SCHED_AUTO;
+  c->tuned = true;
+  auto run_plan = [&](int plan) -> tb_status {
+    c->plan = plan;
+    tb_status st = launch_krylov(c, n, c_off, c_idx, h_off, h_idx, nullptr, Hsk, lambda, S, P,
+                                 kdim, s);
+    if (st != TB_OK) return st;
+    return launch_eig(c, n, h_off, lambda, S, P, kdim, s);
+  };
+  const float inf = 1e30f;
+  r.ms_persistent = c->ke_on ? timed([&] { return run_plan(TB_SCHED_PERSISTENT); }) : inf;
+  r.ms_persistent_largest_first =
+      c->ke_on ? timed([&] { return run_plan(TB_SCHED_PERSISTENT_LARGEST_FIRST); }) : inf;
+  r.ms_separate = timed([&] { return run_plan(TB_SCHED_SEPARATE); });
+  // bucketed plans: the observed sizes cut at quantiles into 1..4 buckets
+  // (bounds rounded up to the size bins; the last bucket reaches
+  // max_cluster, so any later list has a bucket); each bucket's tile is the
+  // fastest of its candidates timed on that bucket alone
+  const tbsk::SkArgs a = sk_args(c, n, c_off, c_idx, h_off, h_idx, Hsk);
+  r.ms_bucketed = inf;
+  int best_nb = 0, best_hi[tb_plan::MAX_BUCKETS] = {};
+  tb_sk_cfg best_cfg[tb_plan::MAX_BUCKETS];
+  float best_bms[tb_plan::MAX_BUCKETS] = {};
+  for (int nb = 1; nb <= tb_plan::MAX_BUCKETS && err == TB_OK; ++nb) {
+    int hi[tb_plan::MAX_BUCKETS], m = 0;
+    for (int b = 0; b < nb; ++b) {
+      int h = p.max_cluster;
+      if (b < nb - 1 && n > 0) {
+        const int qs = sz[(size_t)n * (b + 1) / nb - ((size_t)n * (b + 1) % nb == 0 ? 1 : 0)];
+        h = (qs + tb_plan::BIN - 1) / tb_plan::BIN * tb_plan::BIN;
+        if (h > p.max_cluster) h = p.max_cluster;
+      }
+      if (m > 0 && h <= hi[m - 1]) continue;
+      hi[m++] = h;
+    }
+    if (m != nb) continue;                         // this cut repeats a smaller one
+    c->plan_nb = m;
+    for (int b = 0; b < m; ++b) c->plan_hi[b] = hi[b];
+    if ((err = launch_buckets(c, n, c_off, m, hi, s)) != TB_OK) break;
+    float bms[tb_plan::MAX_BUCKETS];
+    for (int b = 0; b < m && err == TB_OK; ++b) {
+      bms[b] = inf;
+      const int slots[2] = {8, 6};
+      const int minbs[2] = {4, 5};
+      for (int si = 0; si < 2; ++si)
+        for (int mi = 0; mi < 2; ++mi) {
+          tb_sk_cfg t;
+          if (sk_tile<BF>(c, hi[b], slots[si], minbs[mi], max_smem, t) != TB_OK) continue;
+          const float ms = timed([&] { return sk_launch_tile<BF>(c, a, t, n, c->tgt_order, b, s); });
+          if (ms < bms[b]) { bms[b] = ms; c->plan_cfg[b] = t; }
+        }
+      if (bms[b] >= inf) err = TB_ERR_CAPACITY;
+    }
+    if (err != TB_OK) break;
+    const float tot = timed([&] { return run_plan(TB_SCHED_BUCKETED); });
+    if (tot < r.ms_bucketed) {
+      r.ms_bucketed = tot;
+      best_nb = m;
+      for (int b = 0; b < m; ++b) {
+        best_hi[b] = hi[b];
+        best_cfg[b] = c->plan_cfg[b];
+        best_bms[b] = bms[b];
+      }
+    }
+  }
+  if (err == TB_OK && best_nb > 0) {
+    c->plan_nb = best_nb;
+    for (int b = 0; b < best_nb; ++b) {
+      c->plan_hi[b] = best_hi[b];
+      c->plan_cfg[b] = best_cfg[b];
+    }
+  }
+  // the fastest plan
+  int choice = TB_SCHED_SEPARATE;
+  float bestms = r.ms_separate;
+  if (r.ms_persistent < bestms) { bestms = r.ms_persistent; choice = TB_SCHED_PERSISTENT; }
+  if (r.ms_persistent_largest_first < bestms) {
+    bestms = r.ms_persistent_largest_first;
+    choice = TB_SCHED_PERSISTENT_LARGEST_FIRST;
+  }
+  if (r.ms_bucketed < bestms) { bestms = r.ms_bucketed; choice = TB_SCHED_BUCKETED; }
+  if (err == TB_OK) {
+    c->plan = choice;
+    err = run_plan(choice);                       // leaves the record of the given lists
+    if (err == TB_OK && cudaStreamSynchronize(s) != cudaSuccess) err = TB_ERR_CUDA;
+  }
+  c->p.schedule = saved_schedule;
+  if (err != TB_OK) {
+    c->tuned = saved_tuned;
+    c->plan = saved_plan;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err == TB_OK && rep) {
+    r.schedule = choice;
+    r.n_buckets = c->plan_nb;
+    for (int b = 0; b < c->plan_nb; ++b) {
+      r.bucket_hi[b] = c->plan_hi[b];
+      const int lo = b > 0 ? c->plan_hi[b - 1] : 0;
+      for (int i = 0; i < n; ++i)
+        if (sz[i] > lo && (sz[i] <= c->plan_hi[b] || b == c->plan_nb - 1)) ++r.bucket_count[b];
+      r.bucket_records_per_slot[b] = c->plan_cfg[b].mc > 0 ? c->plan_cfg[b].ecap / c->plan_cfg[b].mc : 0;
+      r.bucket_ctas_per_sm[b] = c->plan_cfg[b].grid / c->num_sms;
+      r.bucket_ms[b] = best_bms[b];
+    }
+    *rep = r;
+  }
+  delete[] sz;
+  return err;
+}
+
+}  // namespace
+
+tb_status krylov_autotune(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int* h_off,
+                          const int* h_idx, const float* Hsk, double* lambda, double* S,
+                          double* P, int* kdim, tb_tune_report* rep, cudaStream_t s) {
+  if (c->p.prec == TB_PREC_FP64 || c->p.group_m > 1 || !Hsk) return TB_ERR_INVALID_ARG;
+  if (n <= 0) return TB_OK;
+  return c->p.prec == TB_PREC_BF16
+             ? tune_t<true>(c, n, c_off, c_idx, h_off, h_idx, Hsk, lambda, S, P, kdim, rep, s)
+             : tune_t<false>(c, n, c_off, c_idx, h_off, h_idx, Hsk, lambda, S, P, kdim, rep, s);
 }

@@ -67,6 +67,55 @@ __device__ __forceinline__ bool chol4(const TV (&g)[16], TV (&R)[16], TV rel, do
   return ok;
 }
 
+// The same factorisation, also returning the reciprocal pivots 1/R[c][c] (the
+// reciprocal square roots the factorisation forms anyway).
+template <typename TV>
+__device__ __forceinline__ bool chol4(const TV (&g)[16], TV (&R)[16], TV rel, double abs_tol,
+                                      bool& well, TV (&dinv)[4]) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) R[q] = (TV)0;
+  bool ok = true;
+  well = true;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    TV d = g[c * 4 + c];
+#pragma unroll
+    for (int j = 0; j < c; ++j) d -= R[j * 4 + c] * R[j * 4 + c];
+    if (!(d > rel * g[c * 4 + c]) || !(d > (TV)(abs_tol * abs_tol))) ok = false;
+    if (!(d >= (TV)0.25 * g[c * 4 + c])) well = false;
+    const TV dd = d > (TV)0 ? d : (TV)1;
+    const TV inv = (TV)rsqrt(dd);
+    dinv[c] = inv;
+    R[c * 4 + c] = dd * inv;
+#pragma unroll
+    for (int e = c + 1; e < 4; ++e) {
+      TV t = g[c * 4 + e];
+#pragma unroll
+      for (int j = 0; j < c; ++j) t -= R[j * 4 + c] * R[j * 4 + e];
+      R[c * 4 + e] = t * inv;
+    }
+  }
+  return ok;
+}
+
+// Inverse of an upper-triangular 4x4 R from its reciprocal pivots (no division).
+template <typename TV>
+__device__ __forceinline__ void triinv4(const TV (&R)[16], const TV (&dinv)[4], TV (&X)[16]) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) X[q] = (TV)0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    X[c * 4 + c] = dinv[c];
+#pragma unroll
+    for (int rr = c - 1; rr >= 0; --rr) {
+      TV t = (TV)0;
+#pragma unroll
+      for (int j = rr + 1; j <= c; ++j) t += R[rr * 4 + j] * X[j * 4 + c];
+      X[rr * 4 + c] = -t * dinv[rr];
+    }
+  }
+}
+
 // Inverse of an upper-triangular 4x4 R (row-major).
 template <typename TV>
 __device__ __forceinline__ void triinv4(const TV (&R)[16], TV (&X)[16]) {

@@ -16,7 +16,11 @@
 // the 4x4 block of cluster slot s transposed, [s][c][b] = V[4s + b][c], so
 // that one thread per (slot s, column c) reads the neighbour's column c as
 // one float4.  Items are (s, c) = 4s + c; the four columns of a slot are
-// neighbouring lanes of one warp.
+// neighbouring lanes of one warp.  Within slot s, column c sits at position
+// c ^ ((s >> 1) & 3): lanes reading one column of consecutive slots (one slot
+// per lane, or four lanes per slot) then hit distinct shared-memory banks,
+// which the plain 16-float pitch does not give (every other slot on the same
+// banks).
 //
 // Per step k (V_k, V_{k-1} and W rotate through three shared-memory buffers;
 // every block is also written to the CTA's basis slot in global memory for
@@ -44,6 +48,15 @@ using namespace tbkry;
 
 constexpr int KT = 128;                 // threads per target
 constexpr int KW = KT / 32;
+constexpr int SP = 16;                  // floats per cluster slot in a basis block
+constexpr int SPB = 4;                  // BF16 copy of V_k: 8-byte words per slot
+constexpr int HC = 3 * SP;              // cached neighbour slots per slot during set-up
+
+// Offset (floats) of column c of cluster slot s in a basis block:
+// (SP s | 4 f(s)) ^ 4c with f(s) = (s >> 1) & 3; the first part is what the
+// local sparsity stores per neighbour, so a lane finds its column with one XOR.
+__host__ __device__ __forceinline__ int sbase(int s) { return SP * s + 4 * ((s >> 1) & 3); }
+__host__ __device__ __forceinline__ int cofs(int s, int c) { return sbase(s) ^ (4 * c); }
 constexpr int FL_MASK = 0, FL_ACT = 2, FL_OK = 3;   // flags[4..8): scan scratch
 
 struct SkArgs {
@@ -77,8 +90,8 @@ __host__ __device__ inline size_t sk_smem_bytes(int r, int max_cluster, int ecap
   size_t b = 0;
   b += al32(sizeof(int) * MC);                       // cl
   b += al32(sizeof(int) * (MC + 1));                 // roff
-  b += 3 * al32(sizeof(float) * 16 * MC);            // V_k, V_{k-1}, W
-  if (BF) b += al32(sizeof(uint2) * 4 * MC);         // BF16 copy of V_k for the sweep
+  b += al32(sizeof(float) * 3 * SP * MC);            // V_k, V_{k-1}, W
+  if (BF) b += al32(sizeof(uint2) * SPB * MC);       // BF16 copy of V_k for the sweep
   b += al32(sk_rec_bytes<BF>() * (size_t)ecap);      // records
   b += al32(sizeof(int) * (size_t)ecap);             // neighbour offsets
   const int np = r > KW ? r : KW;
@@ -86,6 +99,7 @@ __host__ __device__ inline size_t sk_smem_bytes(int r, int max_cluster, int ecap
   b += al32(sizeof(float) * 16 * r);                 // projection coefficients
   b += al32(sizeof(float) * 16 * 3);                 // B_{k-1}, R, R^-1
   b += al32(sizeof(float) * 16 * KW);                // reduction scratch
+  b += al32(sizeof(float) * 32 * KW);                // projections summed in the sweep
   b += al32(sizeof(double) * 48);                    // B_k, first Cholesky factor, MGS factor
   b += al32(sizeof(int) * 8);                        // flags
   return b;
@@ -164,12 +178,10 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
   size_t off = 0;
   int* cl = reinterpret_cast<int*>(smem + off);       off += al32(sizeof(int) * MC);
   int* roff = reinterpret_cast<int*>(smem + off);     off += al32(sizeof(int) * (MC + 1));
-  float* buf[3];
-  for (int q = 0; q < 3; ++q) {
-    buf[q] = reinterpret_cast<float*>(smem + off);    off += al32(sizeof(float) * 16 * MC);
-  }
+  float* const bufs = reinterpret_cast<float*>(smem + off);
+  off += al32(sizeof(float) * 3 * SP * MC);
   uint2* vbf = nullptr;
-  if (BF) { vbf = reinterpret_cast<uint2*>(smem + off); off += al32(sizeof(uint2) * 4 * MC); }
+  if (BF) { vbf = reinterpret_cast<uint2*>(smem + off); off += al32(sizeof(uint2) * SPB * MC); }
   Rec* rec_s = reinterpret_cast<Rec*>(smem + off);    off += al32(sizeof(Rec) * (size_t)a.ecap);
   int* rsl_s = reinterpret_cast<int*>(smem + off);    off += al32(sizeof(int) * (size_t)a.ecap);
   float* Cp = reinterpret_cast<float*>(smem + off);   off += al32(sizeof(float) * 16 * np);
@@ -178,11 +190,13 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
   float* Rsh = Bp + 16;
   float* Rish = Rsh + 16;                              off += al32(sizeof(float) * 48);
   float* red = reinterpret_cast<float*>(smem + off);  off += al32(sizeof(float) * 16 * KW);
+  float* Pw = reinterpret_cast<float*>(smem + off);   off += al32(sizeof(float) * 32 * KW);
   double* Bs = reinterpret_cast<double*>(smem + off);
   double* R1s = Bs + 16;
   double* Rm = Bs + 32;                               off += al32(sizeof(double) * 48);
   int* flags = reinterpret_cast<int*>(smem + off);
-  float* const Vg = a.Vg + (size_t)blockIdx.x * r * 16 * MC;
+  float* const Vg = a.Vg + (size_t)blockIdx.x * r * SP * MC;
+  const size_t VB = (size_t)SP * MC;                   // floats per basis block
   const size_t gcap = (size_t)MC * a.max_hnbr;
   const float Es = a.Es, Ep = a.Ep, Vss = a.Vss, Vsp = a.Vsp, Cpp = a.Cpp, Vppp = a.Vppp;
   const float chol_rel = 1e-3f;
@@ -214,11 +228,20 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
   // neighbours in list order (count, scan, fill), each as a record and the
   // neighbour block's offset; the records go to shared memory when they fit,
   // else to the CTA's overflow slot
+  // (the neighbours' slots found in the count pass are kept for the fill pass
+  // in the basis buffers, free until the seed, when the lists are short)
+  int* const hsl = reinterpret_cast<int*>(bufs);
+  const bool cache = a.max_hnbr <= HC;
   for (int s = tid; s < nc; s += KT) {
     const int at = cl[s];
-    const int pe = min(a.h_off[at + 1], a.h_off[at] + a.max_hnbr);
+    const int p0 = a.h_off[at];
+    const int pe = min(a.h_off[at + 1], p0 + a.max_hnbr);
     int e = 0;
-    for (int p = a.h_off[at]; p < pe; ++p) e += find_slot(cl, nc, a.h_idx[p]) >= 0;
+    for (int p = p0; p < pe; ++p) {
+      const int t = find_slot(cl, nc, a.h_idx[p]);
+      if (cache) hsl[s * HC + (p - p0)] = t;
+      e += t >= 0;
+    }
     roff[s] = e;
   }
   __syncthreads();
@@ -232,32 +255,38 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
   }
   for (int s = tid; s < nc; s += KT) {
     const int at = cl[s];
-    const int pe = min(a.h_off[at + 1], a.h_off[at] + a.max_hnbr);
+    const int p0 = a.h_off[at];
+    const int pe = min(a.h_off[at + 1], p0 + a.max_hnbr);
     int e = roff[s];
-    for (int p = a.h_off[at]; p < pe; ++p) {
-      const int t = find_slot(cl, nc, a.h_idx[p]);
+    for (int p = p0; p < pe; ++p) {
+      const int t = cache ? hsl[s * HC + (p - p0)] : find_slot(cl, nc, a.h_idx[p]);
       if (t >= 0) {
         const float4 hv = __ldg(a.Hsk + p);
         if constexpr (BF) rec[e] = pack_bf16x4(hv);
         else rec[e] = hv;
-        rsl[e] = 16 * t;
+        rsl[e] = sbase(t);
         ++e;
       }
     }
   }
+  __syncthreads();                                     // the cache is overwritten below
   // seed block V_1 = E_i: slot 0 holds the identity
-  float* Vk = buf[0];
-  float* Vkm1 = buf[1];
-  float* W = buf[2];
-  for (int q = tid; q < 16 * nc; q += KT) {
+  float* Vk = bufs;
+  float* Vkm1 = bufs + VB;
+  float* W = bufs + 2 * VB;
+  for (int q = tid; q < SP * nc; q += KT) {
     const float v = (q < 16 && (q >> 2) == (q & 3)) ? 1.f : 0.f;
     Vk[q] = v;
     Vg[q] = v;
   }
   if constexpr (BF) {
-    for (int q = tid; q < 4 * nc; q += KT)
-      vbf[q] = pack_bf16x4(make_float4(q < 4 && q == 0 ? 1.f : 0.f, q == 1 ? 1.f : 0.f,
-                                       q == 2 ? 1.f : 0.f, q == 3 ? 1.f : 0.f));
+    for (int q = tid; q < 4 * nc; q += KT) {
+      const int sl = q >> 2, c = q & 3;
+      vbf[SPB * sl + c] = pack_bf16x4(make_float4(sl == 0 && c == 0 ? 1.f : 0.f,
+                                                   sl == 0 && c == 1 ? 1.f : 0.f,
+                                                   sl == 0 && c == 2 ? 1.f : 0.f,
+                                                   sl == 0 && c == 3 ? 1.f : 0.f));
+    }
   }
   if (tid < 16) Bp[tid] = 0.f;
   if (tid == 0) { flags[FL_MASK] = 0xF; flags[FL_MASK + 1] = 0; flags[FL_ACT] = 0xF; }
@@ -267,10 +296,14 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
   const int D4 = 4 * nc;                 // items (slot, column)
   int nblocks = 1;
   for (int k = 0; k < r; ++k) {
-    // ---- W = H_c V_k - V_{k-1} B_{k-1}^T, item (s, c)
+    // ---- W = H_c V_k - V_{k-1} B_{k-1}^T, item (s, c).  The projections of
+    // W on V_k and V_{k-1} (the first classical Gram-Schmidt pass for these
+    // two blocks) are summed here from the slot's blocks, which the item has
+    // at hand: pk[ii] = sum (V_k)[., ii] W[., c], pm likewise for V_{k-1}.
+    float pk[4] = {0.f, 0.f, 0.f, 0.f}, pm[4] = {0.f, 0.f, 0.f, 0.f};
     for (int it = tid; it < D4; it += KT) {
-      const int s = it >> 2, c = it & 3;
-      const float4 u0 = f4(Vk + 16 * s + 4 * c);
+      const int s = it >> 2, c = it & 3, c4x = 4 * c;
+      const float4 u0 = f4(Vk + cofs(s, c));
       float4 acc = make_float4(Es * u0.x, Ep * u0.y, Ep * u0.z, Ep * u0.w);
       const int e1 = roff[s + 1];
 #pragma unroll 2
@@ -278,10 +311,10 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
         float4 hv, u;
         if constexpr (BF) {
           hv = unpack_bf16x4(rec[e]);
-          u = unpack_bf16x4(vbf[(rsl[e] >> 2) + c]);
+          u = unpack_bf16x4(vbf[((rsl[e] >> 2) & ~3) + c]);   // SPB * slot (not swizzled)
         } else {
           hv = rec[e];
-          u = f4(Vk + rsl[e] + 4 * c);
+          u = f4(Vk + (rsl[e] ^ c4x));
         }
         const float dt = fmaf(hv.y, u.y, fmaf(hv.z, u.z, hv.w * u.w));
         const float ps = fmaf(Vss, u.x, Vsp * dt);
@@ -292,30 +325,57 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
         acc.z = fmaf(hv.z, t, fmaf(w, u.z, acc.z));
         acc.w = fmaf(hv.w, t, fmaf(w, u.w, acc.w));
       }
+      float4 vm[4];
       if (k > 0) {
         const float4 b = f4(Bp + 4 * c);            // B_{k-1}[c][d], d >= c
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
-          const float bd = comp(b, d);
-          if (d >= c) acc = axpy4(-bd, f4(Vkm1 + 16 * s + 4 * d), acc);
+          vm[d] = f4(Vkm1 + cofs(s, d));
+          if (d >= c) acc = axpy4(-comp(b, d), vm[d], acc);
         }
       }
-      sf4(W + 16 * s + 4 * c, acc);
+      sf4(W + cofs(s, c), acc);
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii) pk[ii] += dot4(f4(Vk + cofs(s, ii)), acc);
+      if (k > 0) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) pm[d] += dot4(vm[d], acc);
+      }
+    }
+    // sums over the lanes of one column (lane & 3 fixed), then per warp
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        pk[q] += __shfl_xor_sync(0xffffffffu, pk[q], o);
+        pm[q] += __shfl_xor_sync(0xffffffffu, pm[q], o);
+      }
+    }
+    if (lane < 4) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        Pw[warp * 32 + q * 4 + lane] = pk[q];
+        Pw[warp * 32 + 16 + q * 4 + lane] = pm[q];
+      }
     }
     __syncthreads();
     // ---- classical Gram-Schmidt (pass 0 yields A_k); the last step needs
     // only A_k; between full passes only V_{k-1} and V_k are projected out
     const int passes = (k == r - 1) ? 1 : a.reorth_passes;
     float g[4] = {0.f, 0.f, 0.f, 0.f};                 // Gram row c of the final W
+    const int c4 = tid & 3;                            // column of every item of this thread
     for (int pass = 0; pass < passes; ++pass) {
       const bool full = a.reorth_every <= 1 || (k % a.reorth_every) == a.reorth_every - 1;
       const int b0 = (k == r - 1) ? k : (full ? 0 : (k > 0 ? k - 1 : 0));
       const int nb = k + 1 - b0;
       auto blk = [&](int b) -> const float* {
-        return b == k ? Vk : (b == k - 1 ? Vkm1 : Vg + (size_t)b * 16 * MC);
+        return b == k ? Vk : (b == k - 1 ? Vkm1 : Vg + (size_t)b * VB);
       };
-      const int nseg = nb >= KW ? 1 : KW / nb;
-      const int items = nb * nseg;
+      // blocks from fl on were projected in the sweep (first pass only)
+      const int fl = pass == 0 ? (b0 > k - 1 ? b0 : k - 1) : k + 1;
+      const int nbl = fl - b0;                         // blocks projected here
+      const int nseg = nbl >= KW ? 1 : (nbl > 0 ? KW / nbl : 1);
+      const int items = nbl * nseg;
       for (int w = warp; w < items; w += KW) {
         const int b = b0 + w / nseg, seg = w % nseg;
         const int slo = (nc * seg) / nseg, shi = (nc * (seg + 1)) / nseg;
@@ -326,7 +386,7 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
         for (int s = slo + lane; s < shi; s += 32) {
           float4 v[4], x[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) { v[q] = f4(Vb + 16 * s + 4 * q); x[q] = f4(W + 16 * s + 4 * q); }
+          for (int q = 0; q < 4; ++q) { v[q] = f4(Vb + cofs(s, q)); x[q] = f4(W + cofs(s, q)); }
 #pragma unroll
           for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
@@ -335,13 +395,19 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
         const float tot = tbk::warp_reduce16(acc, lane);
         if ((lane & 1) == 0) Cp[w * 16 + (lane >> 1)] = tot;
       }
-      __syncthreads();
+      if (nbl > 0) __syncthreads();
       // coefficients of block b, stored by column: Cc[b][c][ii] = (V_b^T W)[ii][c]
       for (int t = tid; t < nb * 16; t += KT) {
-        const int bl = t >> 4, q = t & 15;
+        const int bl = t >> 4, q = t & 15, b = b0 + bl;
         float sum = 0.f;
-        for (int sg = 0; sg < nseg; ++sg) sum += Cp[(bl * nseg + sg) * 16 + q];
-        Cc[(b0 + bl) * 16 + (q & 3) * 4 + (q >> 2)] = sum;
+        if (b >= fl) {
+          const int h = b == k ? 0 : 16;
+#pragma unroll
+          for (int w = 0; w < KW; ++w) sum += Pw[w * 32 + h + q];
+        } else {
+          for (int sg = 0; sg < nseg; ++sg) sum += Cp[(bl * nseg + sg) * 16 + q];
+        }
+        Cc[b * 16 + (q & 3) * 4 + (q >> 2)] = sum;
       }
       __syncthreads();
       if (pass == 0 && tid < 16) {                     // A_k = V_k^T H V_k, symmetrised
@@ -351,28 +417,42 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
       }
       if (k == r - 1) break;
       const bool last = pass == passes - 1;
-      // W -= sum_b V_b C_b; on the last pass the Gram matrix of the result
-      for (int base = warp * 32; base < D4; base += KT) {
-        const int it = base + lane;
-        const bool on = it < D4;
-        const int s = on ? it >> 2 : 0, c = it & 3;
-        float4 x = on ? f4(W + 16 * s + 4 * c) : make_float4(0.f, 0.f, 0.f, 0.f);
+      // W -= sum_b V_b C_b; on the last pass the Gram matrix of the result.
+      // Up to four items per thread at a time, so that the loads of a block
+      // (from L2 for the older blocks of a full pass) are in flight together.
+      for (int base0 = warp * 32; base0 < D4; base0 += 4 * KT) {
+        float4 x[4];
+        int sl[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int it = base0 + u * KT + lane;
+          sl[u] = it < D4 ? it >> 2 : 0;
+          x[u] = it < D4 ? f4(W + cofs(sl[u], c4)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         for (int b = b0; b <= k; ++b) {
           const float* Vb = blk(b);
-          const float4 cf = f4(Cc + b * 16 + 4 * c);
-          x = axpy4(-cf.x, f4(Vb + 16 * s), x);
-          x = axpy4(-cf.y, f4(Vb + 16 * s + 4), x);
-          x = axpy4(-cf.z, f4(Vb + 16 * s + 8), x);
-          x = axpy4(-cf.w, f4(Vb + 16 * s + 12), x);
+          const float4 cf = f4(Cc + b * 16 + 4 * c4);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (base0 + u * KT >= D4) break;           // uniform over the warp
+            x[u] = axpy4(-cf.x, f4(Vb + cofs(sl[u], 0)), x[u]);
+            x[u] = axpy4(-cf.y, f4(Vb + cofs(sl[u], 1)), x[u]);
+            x[u] = axpy4(-cf.z, f4(Vb + cofs(sl[u], 2)), x[u]);
+            x[u] = axpy4(-cf.w, f4(Vb + cofs(sl[u], 3)), x[u]);
+          }
         }
-        if (on) sf4(W + 16 * s + 4 * c, x);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (base0 + u * KT + lane < D4) sf4(W + cofs(sl[u], c4), x[u]);
         if (last) {
           __syncwarp();
-          if (on) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (base0 + u * KT + lane >= D4) continue;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {                // constant indices into g
-              if (e == c) g[e] += dot4(x, x);
-              else if (e > c) g[e] += dot4(x, f4(W + 16 * s + 4 * e));
+              if (e == c4) g[e] += dot4(x[u], x[u]);
+              else if (e > c4) g[e] += dot4(x[u], f4(W + cofs(sl[u], e)));
             }
           }
         }
@@ -409,8 +489,9 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
 #pragma unroll
           for (int e = 0; e < cc; ++e) G[cc * 4 + e] = G[e * 4 + cc];
         bool well;
-        const bool ok = chol4(G, R, chol_rel, cq == 0 ? chol_abs : 0.0, well);
-        triinv4(R, Ri);
+        float dinv[4];
+        const bool ok = chol4(G, R, chol_rel, cq == 0 ? chol_abs : 0.0, well, dinv);
+        triinv4(R, dinv, Ri);
         if (lane == 0) {
 #pragma unroll
           for (int q = 0; q < 16; ++q) { Rsh[q] = R[q]; Rish[q] = Ri[q]; }
@@ -418,6 +499,34 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
           if (cq == 0) {
 #pragma unroll
             for (int q = 0; q < 16; ++q) R1s[q] = (double)R[q];
+          }
+        }
+        __syncwarp();
+        if (ok && (cq == 1 || well)) {
+          // this factor completes the QR: B_k = R (one factor) or R2 R1, one
+          // entry per lane, published with T and the column mask by the
+          // barrier that ends the step
+          if (lane < 16) {
+            const int j = lane >> 2, cc = lane & 3;
+            double t;
+            if (cq == 0) {
+              t = (double)Rsh[lane];
+            } else {
+              t = 0.0;
+#pragma unroll
+              for (int m = 0; m < 4; ++m) t += (double)Rsh[j * 4 + m] * R1s[m * 4 + cc];
+            }
+            Bs[lane] = t;
+            Bp[lane] = (float)t;
+            tc_block(Ti, 2 * k + 1)[lane] = t;
+            if (j == cc && !isfinite(t)) tbk::set_status(a.st, TB_ERR_NONFINITE, i);
+          }
+          if (lane == 0) {
+            unsigned long long mask = ((unsigned long long)(unsigned)flags[FL_MASK + 1] << 32) |
+                                      (unsigned)flags[FL_MASK];
+            mask |= 0xFull << (4 * (k + 1));
+            flags[FL_MASK] = (int)(mask & 0xffffffffull);
+            flags[FL_MASK + 1] = (int)(mask >> 32);
           }
         }
       }
@@ -435,17 +544,17 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
         const int it = base + lane;
         const bool on = it < D4;
         const int s = on ? it >> 2 : 0;
-        const float* xs = (cq == 0 ? src : dst) + 16 * s;
+        const float* xs = cq == 0 ? src : dst;
         float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          if (j <= c) y = axpy4(ric[j], f4(xs + 4 * j), y);
+          if (j <= c) y = axpy4(ric[j], f4(xs + cofs(s, j)), y);
         __syncwarp();                                  // every lane has read its slot
         if (on) {
-          sf4(out + 16 * s + 4 * c, y);
+          sf4(out + cofs(s, c), y);
           if (fin) {
-            sf4(Vg + (size_t)(k + 1) * 16 * MC + 16 * s + 4 * c, y);
-            if constexpr (BF) vbf[4 * s + c] = pack_bf16x4(y);
+            sf4(Vg + (size_t)(k + 1) * VB + cofs(s, c), y);
+            if constexpr (BF) vbf[SPB * s + c] = pack_bf16x4(y);
           }
         }
         if (!fin) {                                    // Gram matrix for the second factor
@@ -454,7 +563,7 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               if (e == c) g[e] += dot4(y, y);
-              else if (e > c) g[e] += dot4(y, f4(out + 16 * s + 4 * e));
+              else if (e > c) g[e] += dot4(y, f4(out + cofs(s, e)));
             }
           }
         }
@@ -478,7 +587,7 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
         }
         int mact = 0;
         bool nonfinite = false;
-        auto at = [](int row, int col) { return (row >> 2) * 16 + col * 4 + (row & 3); };
+        auto at = [](int row, int col) { return cofs(row >> 2, col) + (row & 3); };
         for (int c = 0; c < 4; ++c) {
           for (int ps = 0; ps < 2 && c > 0; ++ps) {
             float dd[3] = {0.f, 0.f, 0.f};
@@ -518,9 +627,10 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
           __syncwarp();
         }
         // copies of V_{k+1}: the basis slot and (BF16) the sweep's copy
-        for (int q = lane; q < 16 * nc; q += 32) Vg[(size_t)(k + 1) * 16 * MC + q] = O[q];
+        for (int q = lane; q < SP * nc; q += 32) Vg[(size_t)(k + 1) * VB + q] = O[q];
         if constexpr (BF) {
-          for (int q = lane; q < 4 * nc; q += 32) vbf[q] = pack_bf16x4(f4(O + 4 * q));
+          for (int q = lane; q < 4 * nc; q += 32)
+            vbf[SPB * (q >> 2) + (q & 3)] = pack_bf16x4(f4(O + cofs(q >> 2, q & 3)));
         }
         if (lane == 0) {
           if (chol_state == 2) {                       // S was W R1^-1: B_k = R_mgs R1
@@ -544,32 +654,20 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
       Vn = O;
       __syncthreads();
       act = flags[FL_ACT];
-    } else if (tid < 16) {                             // B_k = R (one factor) or R2 R1
-      const int j = tid >> 2, c = tid & 3;
-      double t;
-      if (single) {
-        t = (double)Rsh[tid];
-      } else {
-        t = 0.0;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) t += (double)Rsh[j * 4 + m] * R1s[m * 4 + c];
+      if (tid < 16) {
+        tc_block(Ti, 2 * k + 1)[tid] = Bs[tid];
+        Bp[tid] = (float)Bs[tid];
       }
-      Bs[tid] = t;
+      if (tid == 0) {
+        unsigned long long mask = ((unsigned long long)(unsigned)flags[FL_MASK + 1] << 32) |
+                                  (unsigned)flags[FL_MASK];
+        mask |= (unsigned long long)act << (4 * (k + 1));
+        flags[FL_MASK] = (int)(mask & 0xffffffffull);
+        flags[FL_MASK + 1] = (int)(mask >> 32);
+        if (!isfinite(Bs[0] + Bs[5] + Bs[10] + Bs[15])) tbk::set_status(a.st, TB_ERR_NONFINITE, i);
+      }
     }
-    __syncthreads();                                   // Bs complete
-    if (tid < 16) {
-      tc_block(Ti, 2 * k + 1)[tid] = Bs[tid];
-      Bp[tid] = (float)Bs[tid];
-    }
-    if (tid == 0) {
-      unsigned long long mask = ((unsigned long long)(unsigned)flags[FL_MASK + 1] << 32) |
-                                (unsigned)flags[FL_MASK];
-      mask |= (unsigned long long)act << (4 * (k + 1));
-      flags[FL_MASK] = (int)(mask & 0xffffffffull);
-      flags[FL_MASK + 1] = (int)(mask >> 32);
-      if (!isfinite(Bs[0] + Bs[5] + Bs[10] + Bs[15])) tbk::set_status(a.st, TB_ERR_NONFINITE, i);
-    }
-    __syncthreads();
+    __syncthreads();                                   // V_{k+1}, B_k and the mask complete
     // rotate: V_{k+1} becomes V_k, V_k becomes V_{k-1}, the third buffer W
     {
       float* o0 = Vk;
@@ -595,7 +693,7 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
       const int so = qq == 0 ? 0 : (qq - 1 < rcnt ? rsl[roff[0] + qq - 1] : -1);
       const int b = col >> 2, c = col & 3;
       float val = 0.f;
-      if (b < nblocks && so >= 0) val = Vg[(size_t)b * 16 * MC + so + 4 * c + beta];
+      if (b < nblocks && so >= 0) val = Vg[(size_t)b * VB + (so ^ (4 * c)) + beta];
       a.Y[(ybase + rr) * NT + col] = val;
     }
   }

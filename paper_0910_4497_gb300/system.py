@@ -82,6 +82,15 @@ class TBSystem:
                             self.h_idx, self.Hblk, self.Hsk, self.lam, self.S, self.P,
                             self.kdim, stream)
 
+    def autotune(self, stream=None):
+        """Lists and bond records of the positions in self.pos, then the
+        library's autotuner on them (mixed / BF16 path, before capture());
+        returns its report (cluster-size histogram, plan times, bucket tiles)."""
+        self.neighbors(stream)
+        self.assemble(stream)
+        return B.tb_autotune(self.ctx, self.n, self.c_off, self.c_idx, self.h_off, self.h_idx,
+                             self.Hblk, self.Hsk, self.lam, self.S, self.P, self.kdim, stream)
+
     def group(self, stream=None):
         """Spatial groups of group_m targets of the positions in self.pos."""
         B.tb_group_atoms(self.ctx, self.n, self.pos, self.L, self.g_off, self.g_idx, stream)

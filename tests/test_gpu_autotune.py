@@ -1,0 +1,127 @@
+"""Launch plans of the mixed path on uneven clusters, against the oracle.
+
+The cell is the compressed 1920-atom crystal with the molecules of its upper
+half removed (a slab with vacuum above and below): clusters run from ~40 atoms
+at the surfaces to ~100 inside, so the size histogram spans several buckets.
+Every plan (persistent queue in index order and largest clusters first,
+separate launches, separate launches per size bucket with their own tiles)
+must give the oracle's forces within the mixed path's tolerance, and so must
+the plan the autotuner picks, replayed from a CUDA graph.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import CONFIGS, fcc_c60_crystal, workload_params
+
+pytestmark = pytest.mark.gpu
+
+TOL_F, TOL_EB = 1e-3, 1e-5
+
+
+@pytest.fixture(scope="module")
+def tb():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_0910_4497_gb300 as tb
+    assert torch.cuda.is_available()
+    return tb
+
+
+@pytest.fixture(scope="module")
+def slab():
+    cfg = CONFIGS[1]
+    pos, L, info = fcc_c60_crystal(cfg["ncell"], cfg["a"], cfg["jitter"], cfg["seed"])
+    keep = [m for m, c in enumerate(info["centers"]) if c[2] < 0.5 * L]
+    pos = np.concatenate([pos[60 * m:60 * m + 60] for m in keep])
+    p = workload_params(cfg, defl_tol=1e-9, reorth_passes=1, reorth_every=4)
+    ref = oracle.force_evaluation(pos, L, p, workers=8)
+    return pos, L, p, ref
+
+
+def check(s, ref):
+    F = s.F.cpu().numpy()
+    e = s.energies.cpu().numpy()
+    err = np.abs(F - ref.F).max()
+    assert err <= TOL_F, err
+    assert abs(e[0] - ref.E_band) <= TOL_EB * abs(ref.E_band)
+    assert abs(e[5] - 4 * s.n) <= 1e-9 * s.n
+    return err
+
+
+def test_slab_clusters_are_uneven(slab):
+    from oracle.neighbors import cluster_lists
+    pos, L, p, _ = slab
+    sizes = np.array([len(c) for c in cluster_lists(pos, L, p["Rc"])])
+    assert sizes.min() < 64 and sizes.max() > 90
+
+
+@pytest.mark.parametrize("schedule", ["persistent", "persistent_largest_first", "separate",
+                                      "bucketed"])
+def test_plans_match_oracle(tb, slab, schedule):
+    pos, L, p, ref = slab
+    s = tb.TBSystem(len(pos), L, dict(p, schedule=schedule), prec="mixed")
+    s.set_positions(pos)
+    s.capture()
+    s.replay()
+    torch.cuda.synchronize()
+    s.check()
+    check(s, ref)
+    s.close()
+
+
+def test_plan_kernel_counts(tb, slab):
+    """Kernels per evaluation relative to the persistent queue: the size-bin
+    sort for largest-first; the separate eigensolver; the bucket sort and one
+    launch per default bucket (four) for the bucketed plan."""
+    pos, L, p, _ = slab
+    counts = {}
+    for sch in ("persistent", "persistent_largest_first", "separate", "bucketed"):
+        s = tb.TBSystem(len(pos), L, dict(p, schedule=sch), prec="mixed")
+        counts[sch] = tb.binding.tb_ctx_kernels_per_evaluation(s.ctx, s.n, L)
+        s.close()
+    k = counts["persistent"]
+    assert counts == {"persistent": k, "persistent_largest_first": k + 1, "separate": k + 1,
+                      "bucketed": k + 1 + 4}
+
+
+def test_autotuned_plan_matches_oracle(tb, slab):
+    pos, L, p, ref = slab
+    s = tb.TBSystem(len(pos), L, p, prec="mixed")
+    s.set_positions(pos)
+    rep = s.autotune()
+    torch.cuda.synchronize()
+    s.check()
+    h = rep["histogram"]
+    assert h["bin_width"] == 8 and sum(h["counts"]) == s.n
+    assert sum(1 for x in h["counts"] if x > 0) >= 4          # uneven: several bins
+    assert rep["schedule"] in ("persistent", "persistent_largest_first", "separate", "bucketed")
+    times = [v for v in rep["ms"].values() if v is not None]
+    assert rep["ms"][rep["schedule"]] == min(times)
+    assert 1 <= len(rep["buckets"]) <= 4
+    assert sum(b["targets"] for b in rep["buckets"]) == s.n
+    assert rep["buckets"][-1]["sizes_up_to"] == p["max_cluster"]
+    for b in rep["buckets"]:
+        assert b["records_per_slot_in_smem"] in (0, 6, 8) and b["ctas_per_sm"] >= 1
+    # the record left by the tuner is the chosen plan's on these lists
+    s.find_mu()
+    s.forces()
+    torch.cuda.synchronize()
+    check(s, ref)
+    # later evaluations (graph replays) run the chosen plan
+    s.capture()
+    s.replay()
+    torch.cuda.synchronize()
+    s.check()
+    check(s, ref)
+    s.close()
+
+
+def test_autotune_refuses_fp64(tb, slab):
+    pos, L, p, _ = slab
+    s = tb.TBSystem(len(pos), L, p, prec="fp64")
+    s.set_positions(pos)
+    with pytest.raises(tb.binding.TBError):
+        s.autotune()
+    s.close()

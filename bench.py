@@ -97,6 +97,10 @@ def parse():
     ap.add_argument("--fd-coords", type=int, default=8)
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch plan (no tb_autotune)")
+    ap.add_argument("--schedule", default="auto",
+                    choices=["auto", "persistent", "persistent_largest_first", "separate",
+                             "bucketed"],
+                    help="launch plan of the mixed block-Lanczos stage (auto: the tuned one)")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--group-m", type=int, default=1,
                     help="targets per group of the m-target form (1 = per-target clusters)")
@@ -478,6 +482,7 @@ def run_ours(args):
     sampled = longrange or args.workload == "bridged6480"   # oracle on a bounded sample
     p["reorth_passes"] = args.reorth_passes
     p["reorth_every"] = args.reorth_every
+    p["schedule"] = args.schedule
     grouped = args.group_m > 1
     if grouped:
         p["group_m"] = args.group_m
@@ -593,7 +598,9 @@ def run_ours(args):
         mixed = args.prec != "fp64"
         # the mixed path runs the eigensolve inside the Krylov launch when the
         # library counts no separate eigensolver kernel
-        if tune is not None:
+        if mixed and args.schedule != "auto":
+            plan = args.schedule
+        elif tune is not None:
             plan = tune["schedule"]
         elif mixed and not grouped and launches_per_step == list_launches(L, p["Rc"]) + 1 + 1 + 1 + 4:
             plan = "persistent"
@@ -619,7 +626,9 @@ def run_ours(args):
                  "krylov_sk_kernel (block Lanczos on Slater-Koster records, one CTA per target)"
                  if mixed else
                  "krylov_kernel (FP64 block Lanczos, one CTA per target)")
-        tr = kernel_traffic_record(args.prec, "krylov_group_traffic.json" if grouped
+        tkey = (args.prec if not mixed or grouped or longrange else
+                "mixed" if persistent else "mixed_sweep_kernel")
+        tr = kernel_traffic_record(tkey, "krylov_group_traffic.json" if grouped
                                    else "krylov_traffic_longrange.json" if longrange
                                    else "krylov_traffic.json", cfg["name"])
         traffic = tr.get("dram") if tr else None
@@ -664,18 +673,28 @@ def run_ours(args):
         if persistent:
             # the same sweeps as a separate launch, so that their own time and
             # roofline can be read apart from the eigensolves sharing the queue
-            sep = tb.TBSystem(n, L, dict(p, schedule="separate"), prec=args.prec, device=dev)
+            # (separate launches per size bucket with the autotuner's tiles: on
+            # uniform clusters one bucket, i.e. the block-Lanczos kernel alone)
+            sep = tb.TBSystem(n, L, dict(p, schedule="bucketed"), prec=args.prec, device=dev)
             B.tb_profile_enable(sep.ctx, True)
             sep.set_positions(pos)
+            if not args.no_autotune:
+                sep.autotune()
             sep.capture()
             ms_sep, st_sep = timed_leg(sep, min(args.steps, 100), flush, stream, B)
             sep.close()
             ksep = st_sep.get("krylov")
             a_sep = sweep / (ksep * 1e-3) / 1e9 if ksep else None
+            trs = kernel_traffic_record("mixed_sweep_kernel", "krylov_traffic.json", cfg["name"])
             extra["roofline_sweeps"] = {
-                "bound": "hbm", "kernel": "krylov_sk_kernel (separate launch, same settings)",
+                "bound": "hbm", "kernel": "krylov_sk_kernel (separate launches per cluster-size "
+                                          "bucket with the tuned tiles, same settings; kernel_ms "
+                                          "is the Krylov stage)",
                 "achieved": a_sep, "peak": hbm, "unit": "GB/s",
                 "frac": a_sep / hbm if a_sep else None, "kernel_ms": ksep,
+                "traffic": trs.get("dram") if trs else None,
+                "l2_bytes_per_launch": trs.get("l2") if trs else None,
+                "traffic_note": "ncu record of the default-tile separate launch",
                 "algorithmic_bytes_per_launch": sweep,
                 "step_ms_with_separate_launches": ms_sep}
         line = {
@@ -829,11 +848,15 @@ def run_md(args):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
+    tunes = {}
+
     def make(prec):
         s = tb.TBSystem(n, L, p, prec=prec, device=dev)
         tb.binding.tb_profile_enable(s.ctx, True)
         s.set_positions(pos)
         s.vel.copy_(torch.as_tensor(vel, dtype=torch.float64))
+        if prec != "fp64" and not args.no_autotune:
+            tunes[prec] = s.autotune()        # the launch plan of every step's graph
         s.evaluate()
         s.capture_md(dt, MASS_C_AMU)
         return s
@@ -919,6 +942,7 @@ def run_md(args):
             "clocks": clk,
             "gpu_launches": launches_per_step * args.steps,
             "stage_ms": stage_ms,
+            "autotune": tunes.get(args.prec),
             "nve": {"energy_drift_eV_per_atom": float((etot[-1] - etot[0]) / n),
                     "energy_span_eV_per_atom": float((etot.max() - etot.min()) / n),
                     "fp64_path": fp64},

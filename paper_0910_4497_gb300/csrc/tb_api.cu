@@ -6,7 +6,19 @@
 #include <cstring>
 #include <new>
 #include <cmath>
+#include <nvtx3/nvToolsExt.h>
 #include "tb_internal.cuh"
+
+// Tracing: every stream-ordered entry point opens an NVTX range named after
+// itself for the duration of the host call (a profiler or tracing tool shows
+// them on the host timeline; without one attached they cost a few ns).
+namespace {
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
+#define TB_NVTX(name) NvtxRange tb_nvtx_range_(name)
 
 size_t krylov_basis_bytes_global(const tb_ctx* c);
 
@@ -251,6 +263,7 @@ tb_status tb_get_status(tb_ctx* c, int* code, int* info, void* stream) {
 
 tb_status tb_build_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h_off,
                              int* h_idx, int* c_off, int* c_idx, void* stream) {
+  TB_NVTX("tb_build_neighbors");
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;
   if (n == 0) return TB_OK;
@@ -264,6 +277,7 @@ tb_status tb_build_neighbors(tb_ctx* c, int n, const double* pos, double L, int*
 tb_status tb_assemble_H(tb_ctx* c, int n, const double* pos, double L, const int* h_off,
                         const int* h_idx, double* Hblk, double* dHblk, float* Hsk,
                         void* stream) {
+  TB_NVTX("tb_assemble_H");
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;
   if (n == 0) return TB_OK;
@@ -278,6 +292,7 @@ tb_status tb_krylov_density(tb_ctx* c, int n, const int* c_off, const int* c_idx
                             const int* h_off, const int* h_idx, const double* Hblk,
                             const float* Hsk, double* lambda, double* S, double* P,
                             int* kdim, void* stream) {
+  TB_NVTX("tb_krylov_density");
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;
   if (n == 0) return TB_OK;
@@ -294,6 +309,7 @@ tb_status tb_krylov_density(tb_ctx* c, int n, const int* c_off, const int* c_idx
 
 tb_status tb_group_atoms(tb_ctx* c, int n, const double* pos, double L, int* g_off, int* g_idx,
                          void* stream) {
+  TB_NVTX("tb_group_atoms");
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;
   if (n == 0) return TB_OK;
@@ -308,6 +324,7 @@ tb_status tb_krylov_density_grouped(tb_ctx* c, int n, int n_groups, const int* g
                                     const int* h_off, const int* h_idx, const double* Hblk,
                                     const float* Hsk, double* lambda, double* S, double* P,
                                     int* kdim, void* stream) {
+  TB_NVTX("tb_krylov_density_grouped");
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;
   if (c->p.group_m < 2 || c->grp_grid <= 0) return TB_ERR_INVALID_ARG;
@@ -327,6 +344,7 @@ tb_status tb_krylov_density_grouped(tb_ctx* c, int n, int n_groups, const int* g
 tb_status tb_find_mu(tb_ctx* c, int n, const double* lambda, const double* S, const int* kdim,
                      double n_electrons, const double* mu_guess, double* mu, double* n_count,
                      void* stream) {
+  TB_NVTX("tb_find_mu");
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;
   if (!lambda || !S || !kdim || !mu || n <= 0 || !(n_electrons > 0.0)) return TB_ERR_INVALID_ARG;
@@ -339,6 +357,7 @@ tb_status tb_forces(tb_ctx* c, int n, const double* pos, double L, const int* h_
                     const int* h_idx, const double* dHblk, const double* lambda,
                     const double* S, const double* P, const int* kdim, const double* mu,
                     double* F, double* energies, void* stream) {
+  TB_NVTX("tb_forces");
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;
   if (n == 0) return TB_OK;
@@ -353,6 +372,7 @@ tb_status tb_forces(tb_ctx* c, int n, const double* pos, double L, const int* h_
 
 tb_status tb_md_step(tb_ctx* c, int n, double* pos, double* vel, double* F, double L,
                      double dt_fs, double mass_amu, double* energies, void* stream) {
+  TB_NVTX("tb_md_step");
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;
   if (n == 0) return TB_OK;
@@ -382,6 +402,7 @@ tb_status tb_md_step(tb_ctx* c, int n, double* pos, double* vel, double* F, doub
 
 tb_status tb_virial(tb_ctx* c, int n, const double* pos, double L, const int* h_off,
                     const int* h_idx, double* W, double* pressure, void* stream) {
+  TB_NVTX("tb_virial");
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;
   if (!h_off && !h_idx) {      // the context's own lists, as left by tb_md_step
@@ -397,6 +418,7 @@ tb_status tb_npt_berendsen(tb_ctx* c, int n, double* pos, double* vel, double L,
                            const double* W, const double* energies, double T0, double P0,
                            double dt_fs, double tau_T_fs, double tau_P_fs, double beta,
                            double* L_new, double* state, void* stream) {
+  TB_NVTX("tb_npt_berendsen");
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;
   if (!pos || !vel || !W || !energies || !L_new || !state || !(L > 0.0) || !(T0 >= 0.0) ||
@@ -437,6 +459,7 @@ tb_status tb_local_forward(tb_ctx* c, int n, const double* pos, double L, const 
                            const int* c_idx, const int* h_off, const int* h_idx,
                            const double* Hblk, double* lambda, double* S, int* kdim,
                            void* Zstore, double* mu, double* energies, void* stream) {
+  TB_NVTX("tb_local_forward");
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;
   if (n > c->loc_reserved_n || !c->loc_ws) return TB_ERR_NOT_RESERVED;
@@ -454,6 +477,7 @@ tb_status tb_local_gradient(tb_ctx* c, int n, const double* pos, double L, const
                             const double* Hblk, const double* dHblk, const double* lambda,
                             const double* S, const void* Zstore, const double* mu, double* F,
                             void* stream) {
+  TB_NVTX("tb_local_gradient");
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;
   if (n > c->loc_reserved_n || !c->loc_ws) return TB_ERR_NOT_RESERVED;
@@ -469,6 +493,7 @@ tb_status tb_local_gradient(tb_ctx* c, int n, const double* pos, double L, const
 tb_status tb_autotune(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int* h_off,
                       const int* h_idx, const double* Hblk, const float* Hsk, double* lambda,
                       double* S, double* P, int* kdim, tb_tune_report* report, void* stream) {
+  TB_NVTX("tb_autotune");
   (void)Hblk;
   tb_status st = ready(c, n);
   if (st != TB_OK) return st;

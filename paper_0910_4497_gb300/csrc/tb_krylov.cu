@@ -1,12 +1,14 @@
 // Per-target cluster map and block Lanczos (Sec. 3, Eq. (Krylov) and
 // the block form of Eqs. (lanczos) / (lanczos_blas3)).
 //
-// One CTA per target atom (persistent, grid-stride over targets).  For target
+// FP64 path.  (The mixed path's kernel, on Slater-Koster records, is in
+// tb_krylov_sk.cuh.)  One CTA per target atom (persistent, grid-stride over
+// targets).  For target
 // i with cluster atoms cl[0..nc) (cl[0] = i, the rest ascending):
 //   * the local sparsity of H_c is built in the CTA: for each slot s and each
 //     Hamiltonian neighbour of cl[s] that is in the cluster, the pair (local
 //     slot, global bond index).  H_c is never formed: its 4x4 blocks are read
-//     from the global bond table (FP64, or its FP32 mirror) in every sweep;
+//     from the global FP64 bond table in every sweep;
 //   * V_1 = E_i (the target's four orbitals, slot 0) and for k = 1..r:
 //       W = H_c V_k - V_{k-1} B_{k-1}^T          block-sparse sweep, 4 columns
 //       pass 1: C = Q^T W, W -= Q C               Q = [V_1..V_k]; the V_k part
@@ -23,8 +25,8 @@
 //     T gets A_k on the diagonal and B_k / B_k^T off the diagonal;
 //   * the rows of V belonging to the target and its Hamiltonian neighbours are
 //     written out (Y) for the density-matrix columns.
-// The basis lives in shared memory when r * 4 * max_cluster * 4 values fit,
-// otherwise in a per-CTA slot of global memory (L2-resident).
+// The basis lives in a per-CTA slot of global memory (L2-resident), V_k is
+// staged in shared memory for each sweep.  T is written block-tridiagonally.
 // Layout of the basis: block b occupies Dmax*4 values, row-major [row][4].
 #include <algorithm>
 #include <cstring>
@@ -93,16 +95,14 @@ __host__ __device__ __forceinline__ int lent_smem_cap(int max_cluster, int max_h
 }
 
 template <typename TV>
-__host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, int max_hnbr, bool vsmem,
-                                                 bool lsmem) {
+__host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, int max_hnbr, bool lsmem) {
   const size_t Dmax = 4 * (size_t)max_cluster;
   const size_t np = (size_t)(r > KW_MAX ? r : KW_MAX);
   size_t b = 0;
   b += align32(sizeof(int) * max_cluster);            // cl
   b += align32(sizeof(int) * (max_cluster + 1));      // entries per slot
   b += align32(sizeof(TV) * Dmax * 4);                // W
-  if (vsmem) b += align32(sizeof(TV) * Dmax * 4 * r); // basis
-  else b += align32(sizeof(TV) * Dmax * 4 * (sizeof(TV) == 4 ? 2 : 1));  // V_k (FP32: and V_{k-1})
+  b += align32(sizeof(TV) * Dmax * 4);                // staged V_k
   if (lsmem) b += align32(sizeof(int2) * (size_t)lent_smem_cap(max_cluster, max_hnbr));  // local CSR
   b += align32(sizeof(TV) * 16 * np);                 // projection partials
   b += align32(sizeof(TV) * 16 * r);                  // projection coefficients
@@ -118,7 +118,6 @@ __host__ __device__ inline size_t kry_smem_bytes(int r, int max_cluster, int max
 template <typename TV, int KT>
 __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) {
   constexpr int KW = KT / 32;
-  constexpr bool VSMEM = false;      // the basis lives in the CTA's global slot
   static_assert(KT == 128 || KT == 256, "128 or 256 threads");
   extern __shared__ __align__(32) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -128,24 +127,11 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
   int* cl = reinterpret_cast<int*>(smem + off);      off += align32(sizeof(int) * a.max_cluster);
   int* cnt = reinterpret_cast<int*>(smem + off);     off += align32(sizeof(int) * (a.max_cluster + 1));
   TV* W = reinterpret_cast<TV*>(smem + off);         off += align32(sizeof(TV) * Dmax * 4);
-  // FP32 with the basis in global memory (DB): V_k and V_{k-1} double-buffered
-  // in shared memory, written there by the step that produces them (no staging
-  // pass and no L2 round trip for the blocks every step projects out; the
-  // global slot keeps every block for the full reorthogonalisations and the Y
-  // rows).  FP32 (RED): the Gram partials summed and the 4x4 factors formed by
-  // every thread, B_k published by thread 0 with the step's closing barrier.
-  constexpr bool DB = !VSMEM && sizeof(TV) == 4;
-  constexpr bool RED = sizeof(TV) == 4;
-  TV* V;
-  TV* Vks = nullptr;                                 // shared copies of V_k (and V_{k-1})
-  if (VSMEM) {
-    V = reinterpret_cast<TV*>(smem + off);
-    off += align32(sizeof(TV) * (size_t)Dmax * 4 * r);
-  } else {
-    V = a.Vg + (size_t)blockIdx.x * Dmax * 4 * r;
-    Vks = reinterpret_cast<TV*>(smem + off);
-    off += align32(sizeof(TV) * (size_t)Dmax * 4 * (DB ? 2 : 1));
-  }
+  // the basis in the CTA's global slot (L2-resident), V_k staged in shared
+  // memory for the sweep
+  TV* const V = a.Vg + (size_t)blockIdx.x * Dmax * 4 * r;
+  TV* const Vks = reinterpret_cast<TV*>(smem + off);
+  off += align32(sizeof(TV) * (size_t)Dmax * 4);
   int2* const lent_g = a.lent + (size_t)blockIdx.x * a.max_cluster * a.max_hnbr;   // local CSR
   int2* lent_s = nullptr;
   if (a.lent_smem) {
@@ -164,7 +150,7 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
   int* flags = reinterpret_cast<int*>(smem + off);
   const TV Es = (TV)a.Es, Ep = (TV)a.Ep;
   // Cholesky-QR acceptance: each pivot must keep this fraction of its diagonal
-  const TV chol_rel = sizeof(TV) == 4 ? (TV)1e-3 : (TV)1e-8;
+  const TV chol_rel = (TV)1e-8;
   const double chol_abs = 1000.0 * a.defl_tol;
 
   {
@@ -230,7 +216,6 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
       const int row = q >> 2, c = q & 3;
       const TV e = (row == c) ? (TV)1 : (TV)0;
       V[q] = e;
-      if constexpr (DB) Vks[q] = e;
     }
     if (tid < 16) Bp[tid] = (TV)0;
     if (tid == 0) { flags[FL_MASK] = 0xF; flags[FL_MASK + 1] = 0; flags[FL_ACT] = 0xF; }
@@ -241,17 +226,12 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
     for (int k = 0; k < r; ++k) {
       const TV* Vk = V + (size_t)k * Dmax * 4;
       const TV* Vp = V + (size_t)(k > 0 ? k - 1 : 0) * Dmax * 4;
-      if constexpr (DB) {
-        Vk = Vks + (size_t)(k & 1) * Dmax * 4;
-        Vp = Vks + (size_t)((k + 1) & 1) * Dmax * 4;
-      } else if constexpr (!VSMEM) {     // the sweep reads V_k rows many times: stage it
-        for (int q = tid; q < D; q += KT) st4(Vks + q * 4, ld4(Vk + q * 4));
-        __syncthreads();
-        Vk = Vks;
-      }
-      // blocks b >= bsm are read from the shared-memory copies (V_k; V_{k-1} too
-      // when double-buffered); with the basis in shared memory, all through V
-      const int bsm = DB ? k - 1 : (VSMEM ? k + 1 : k);
+      // the sweep reads V_k rows many times: stage it
+      for (int q = tid; q < D; q += KT) st4(Vks + q * 4, ld4(Vk + q * 4));
+      __syncthreads();
+      Vk = Vks;
+      // block k is read from the shared-memory copy, earlier blocks from the slot
+      const int bsm = k;
       // ---- W = H_c V_k - V_{k-1} B_{k-1}^T ; item (s, alpha) = one row of W
       for (int it = tid; it < 4 * nc; it += KT) {
         const int s = it >> 2, al = it & 3;
@@ -315,7 +295,7 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
                 for (int c = 0; c < 4; ++c) acc[ii * 4 + c] += v.v[ii] * x.v[c];
             }
           };
-          if (b >= bsm) rows((DB && b != k) ? Vp : Vk);
+          if (b >= bsm) rows(Vk);
           else rows(V + (size_t)b * Dmax * 4);
           const TV tot = tbk::warp_reduce16(acc, lane);
           if ((lane & 1) == 0) Cp[w * 16 + (lane >> 1)] = tot;
@@ -355,8 +335,7 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
           };
 #pragma unroll 4
           for (int b = b0; b < bsm; ++b) sub(V + (size_t)b * Dmax * 4, b - b0);
-          if (DB && k - 1 >= b0) sub(Vp, k - 1 - b0);
-          if (!VSMEM) sub(Vk, k - b0);
+          sub(Vk, k - b0);
           st4(W + row * 4, x);
           if (last) {                       // Gram matrix of the orthogonalised W
             int q = 0;
@@ -373,82 +352,9 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
       // the first factor shows a well-conditioned block); the MGS path
       // takes over when a pivot signals ill-conditioning or deflation.
       TV* Vn = V + (size_t)(k + 1) * Dmax * 4;
-      // the shared-memory copy of V_{k+1} takes the buffer V_{k-1} leaves
-      TV* Vns = DB ? Vks + (size_t)((k + 1) & 1) * Dmax * 4 : nullptr;
       int chol_state = 0;   // 1: first factor refused (W untouched); 2: second refused
       int act = 0xF;
-      if constexpr (RED) {
-        // FP32: every thread reduces the Gram partials and factors the (same)
-        // Gram matrix itself, so R and R^{-1} are identical everywhere with no
-        // broadcast; thread 0 forms B_k and publishes it with T before the
-        // step's closing barrier
-        TV R[16];
-        bool single = false;
-        for (int cq = 0; cq < 2; ++cq) {
-          TV gs[10];
-          tbk::block_sum_all<TV, 10, KW>(g, red + cq * 16 * KW_MAX, gs);
-          TV G[16], Ri[16];
-          int q = 0;
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int e = c; e < 4; ++e) { G[c * 4 + e] = gs[q]; G[e * 4 + c] = gs[q]; ++q; }
-          bool well;
-          const bool ok = chol4(G, R, chol_rel, cq == 0 ? chol_abs : 0.0, well);
-          triinv4(R, Ri);
-          if (!ok) {                        // uniform: every thread factors the same matrix
-            chol_state = cq + 1;
-            break;
-          }
-          single = cq == 0 && well;         // a well-conditioned block needs no second pass
-          const bool to_w = cq == 0 && !single;
-#pragma unroll
-          for (int q2 = 0; q2 < 10; ++q2) g[q2] = (TV)0;
-          for (int row = tid; row < D; row += KT) {
-            const vec4<TV> x = ld4(W + row * 4);
-            vec4<TV> y;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              TV t = (TV)0;
-#pragma unroll
-              for (int j = 0; j <= c; ++j) t += x.v[j] * Ri[j * 4 + c];
-              y.v[c] = t;
-            }
-            if (to_w) {                     // Gram matrix for the second factor
-              st4(W + row * 4, y);
-              int q3 = 0;
-#pragma unroll
-              for (int c = 0; c < 4; ++c)
-#pragma unroll
-                for (int e = c; e < 4; ++e) g[q3++] += y.v[c] * y.v[e];
-            } else {
-              st4(Vn + row * 4, y);
-              if constexpr (DB) st4(Vns + row * 4, y);
-            }
-          }
-          if (!to_w) break;
-          if (tid == 0) {
-#pragma unroll
-            for (int q2 = 0; q2 < 16; ++q2) R1s[q2] = (double)R[q2];
-          }
-        }
-        if (chol_state == 0 && tid == 0) {
-          if (single) {
-#pragma unroll
-            for (int q2 = 0; q2 < 16; ++q2) Bs[q2] = (double)R[q2];
-          } else {
-#pragma unroll
-            for (int rr = 0; rr < 4; ++rr)          // B_k = R2 R1
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                double t = 0.0;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) t += (double)R[rr * 4 + j] * R1s[j * 4 + c];
-                Bs[rr * 4 + c] = t;
-              }
-          }
-        }
-      } else {
+      {
       for (int cq = 0; cq < 2; ++cq) {
         tbk::block_sum16<TV, 10>(g, red, Gs);
         // FP64 (a slow pipe shared by the whole SM): one thread factors and publishes
@@ -560,9 +466,6 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
               for (int row = lane; row < D; row += 32) Vn[row * 4 + c] = (TV)0;
             }
           }
-          if constexpr (DB) {               // each lane copies the rows it wrote
-            for (int row = lane; row < D; row += 32) st4(Vns + row * 4, ld4(Vn + row * 4));
-          }
           if (lane == 0) {
             if (chol_state == 2) {      // W was already W R1^{-1}: B_k = R_mgs R1
 #pragma unroll
@@ -632,7 +535,7 @@ __device__ __forceinline__ void krylov_target(const KryArgs<TV> a, const int i) 
 
 // One CTA per target atom, persistent (grid-stride over the targets).
 template <typename TV, int KT>
-__global__ void __launch_bounds__(KT, KT == 128 ? (sizeof(TV) == 4 ? 5 : 4) : 2) krylov_kernel(const KryArgs<TV> a) {
+__global__ void __launch_bounds__(KT, KT == 128 ? 4 : 2) krylov_kernel(const KryArgs<TV> a) {
   for (int i = blockIdx.x; i < a.n; i += gridDim.x) krylov_target<TV, KT>(a, i);
 }
 
@@ -989,10 +892,9 @@ tb_status launch_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const i
 
 template <typename TV, int KT>
 tb_status configure_t(tb_ctx* c, int max_smem) {
-  constexpr bool VSMEM = false;
   // the local CSR goes to shared memory when that keeps the occupancy
-  const size_t b0 = kry_smem_bytes<TV>(c->p.r, c->p.max_cluster, c->p.max_hnbr, VSMEM, false);
-  const size_t b1 = kry_smem_bytes<TV>(c->p.r, c->p.max_cluster, c->p.max_hnbr, VSMEM, true);
+  const size_t b0 = kry_smem_bytes<TV>(c->p.r, c->p.max_cluster, c->p.max_hnbr, false);
+  const size_t b1 = kry_smem_bytes<TV>(c->p.r, c->p.max_cluster, c->p.max_hnbr, true);
   if ((int)b0 > max_smem) return TB_ERR_CAPACITY;
   if (c->p.max_cluster > 4 * KT) return TB_ERR_CAPACITY;   // block scan: 4 slots per thread
   const size_t bmax = (int)b1 <= max_smem ? b1 : b0;

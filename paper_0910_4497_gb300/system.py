@@ -141,6 +141,26 @@ class TBSystem:
             stream.synchronize()
         self.L = float(self.L_dev.item())
 
+    # -- checkpoint / restart of a trajectory
+    def checkpoint(self, path, step, seed):
+        """Write pos, vel, F, the box, the step count and the seed (host copy)."""
+        from . import checkpoint as ck
+        ck.save(path, self.pos.cpu().numpy(), self.vel.cpu().numpy(), self.F.cpu().numpy(),
+                self.L, step, seed, params=self.params, prec=self.prec)
+
+    def restore(self, path):
+        """Load a checkpoint written by checkpoint() into this system (same n);
+        returns (step, seed).  Recapture a step graph afterwards if the box
+        changed."""
+        from . import checkpoint as ck
+        st = ck.load(path)
+        if st["pos"].shape[0] != self.n:
+            raise ValueError(f"checkpoint holds {st['pos'].shape[0]} atoms, system {self.n}")
+        for t, k in ((self.pos, "pos"), (self.vel, "vel"), (self.F, "F")):
+            t.copy_(torch.as_tensor(st[k]))
+        self.L = st["L"]
+        return st["step"], st["seed"]
+
     # -- exact local free energy and its gradient at r = r_min
     def reserve_local(self, store_basis=False):
         """Dense workspace and buffers of the exact local path; with store_basis

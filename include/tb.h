@@ -305,7 +305,8 @@ tb_status tb_krylov_density_grouped(tb_ctx* ctx, int n, int n_groups, const int*
  * uneven in compressed or polymerised crystals).  On the given lists (as from
  * tb_build_neighbors / tb_assemble_H) it times, with CUDA events on `stream`:
  *   - the persistent Krylov + eigensolve queue, in index order and largest
- *     clusters first;
+ *     clusters first, each with two tiles (8 records per cluster slot in
+ *     shared memory at 4 CTAs per SM, or 6 at 5 CTAs per SM);
  *   - separate launches per cluster-size bucket, for partitions of the
  *     observed size range into 1..TB_TUNE_MAX_BUCKETS buckets, each bucket's
  *     tile chosen among shared-memory record capacities (6 or 8 records per
@@ -331,6 +332,8 @@ typedef struct tb_tune_report {
   float ms_persistent_largest_first;
   float ms_separate;
   float ms_bucketed;                           /* best partition into buckets          */
+  int persistent_records_per_slot;             /* tile of the persistent queue in the  */
+  int persistent_ctas_per_sm;                  /* context after tuning                 */
   int n_buckets;                               /* of the best bucketed plan            */
   int bucket_hi[TB_TUNE_MAX_BUCKETS];          /* bucket b: sizes (hi[b-1], hi[b]]     */
   int bucket_count[TB_TUNE_MAX_BUCKETS];       /* targets in the bucket                */

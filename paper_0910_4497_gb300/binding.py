@@ -53,6 +53,8 @@ class TBTuneReport(ctypes.Structure):
                 ("hist", ctypes.c_int * TUNE_BINS), ("schedule", ctypes.c_int),
                 ("ms_persistent", ctypes.c_float), ("ms_persistent_largest_first", ctypes.c_float),
                 ("ms_separate", ctypes.c_float), ("ms_bucketed", ctypes.c_float),
+                ("persistent_records_per_slot", ctypes.c_int),
+                ("persistent_ctas_per_sm", ctypes.c_int),
                 ("n_buckets", ctypes.c_int),
                 ("bucket_hi", ctypes.c_int * TUNE_MAX_BUCKETS),
                 ("bucket_count", ctypes.c_int * TUNE_MAX_BUCKETS),
@@ -269,6 +271,8 @@ def tb_autotune(ctx, n, c_off, c_idx, h_off, h_idx, Hblk, Hsk, lam, S, P, kdim, 
                    (("persistent", r.ms_persistent),
                     ("persistent_largest_first", r.ms_persistent_largest_first),
                     ("separate", r.ms_separate), ("bucketed", r.ms_bucketed))},
+            "persistent_tile": {"records_per_slot_in_smem": r.persistent_records_per_slot,
+                                "ctas_per_sm": r.persistent_ctas_per_sm},
             "buckets": [{"sizes_up_to": r.bucket_hi[b], "targets": r.bucket_count[b],
                          "records_per_slot_in_smem": r.bucket_records_per_slot[b],
                          "ctas_per_sm": r.bucket_ctas_per_sm[b], "ms": r.bucket_ms[b]}

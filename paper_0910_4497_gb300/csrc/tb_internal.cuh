@@ -208,6 +208,8 @@ struct tb_ctx {
   bool ke_on = false;               // persistent Krylov + eigensolve kernel (mixed path)
   int ke_grid = 0;
   size_t ke_smem = 0;
+  int ke_ecap = 0;                   // records in shared memory per target (persistent launch)
+  int ke_minb = 4;                   // CTAs per SM its register budget allows
   int sk_ecap = 0;                   // local records kept in shared memory per target
   int sk_grid = 0;                   // CTAs of the mixed Krylov kernel (separate launch)
   size_t sk_smem = 0;

@@ -556,8 +556,8 @@ __device__ __forceinline__ int ld_acquire_s32(const int* p) {
 // TB_ERR_TIMEOUT).  The record (T, Y rows, column mask) is published by a
 // fence in every thread, a barrier and a flag; the eigensolver reads it
 // through L2.  work[0] and done[0..n) are zero at launch.
-template <int NTC, bool BF>
-__global__ void __launch_bounds__(128, 4) kry_eig_kernel(const tbsk::SkArgs a, const XArgs xa,
+template <int NTC, bool BF, int MINB>
+__global__ void __launch_bounds__(128, MINB) kry_eig_kernel(const tbsk::SkArgs a, const XArgs xa,
                                                          const int* order, int* work, int* done,
                                                          long long timeout) {
   __shared__ int s_item;
@@ -744,32 +744,43 @@ tb_status sk_configure_t(tb_ctx* c, int max_smem) {
   }
   return TB_OK;
 }
-template <int NTC, bool BF>
-tb_status kry_eig_configure_t(tb_ctx* c, int max_smem) {
-  const size_t eig = 2 * xw_smem_per_warp(4 * c->p.r);
-  const size_t bytes = c->sk_smem > eig ? c->sk_smem : eig;
+// Tile of the persistent launch: `slots` records per cluster slot in shared
+// memory (0 when the Hamiltonian lists are long) and a register budget for
+// minb CTAs per SM; the eigensolve items need their two groups' shared memory.
+template <int NTC, bool BF, int MINB>
+tb_status kry_eig_tile(tb_ctx* c, int slots, int max_smem) {
+  const tb_params& p = c->p;
+  const int ecap = p.max_hnbr > 48 ? 0 : slots * p.max_cluster;
+  const size_t sk = tbsk::sk_smem_bytes<BF>(p.r, p.max_cluster, ecap);
+  const size_t eig = 2 * xw_smem_per_warp(4 * p.r);
+  const size_t bytes = sk > eig ? sk : eig;
   if ((int)bytes > max_smem) return TB_ERR_CAPACITY;
-  TB_CUDA_TRY(cudaFuncSetAttribute(kry_eig_kernel<NTC, BF>,
+  TB_CUDA_TRY(cudaFuncSetAttribute(kry_eig_kernel<NTC, BF, MINB>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   int occ = 0;
-  TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kry_eig_kernel<NTC, BF>, 128,
-                                                            bytes));
+  TB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kry_eig_kernel<NTC, BF, MINB>,
+                                                            128, bytes));
   if (occ < 1) return TB_ERR_CAPACITY;
+  int grid = c->num_sms * occ;
+  if (c->kry_grid > 0 && grid > c->kry_grid) grid = c->kry_grid;   // per-CTA slots
   c->ke_smem = bytes;
-  c->ke_grid = c->num_sms * occ;
+  c->ke_grid = grid;
+  c->ke_ecap = ecap;
+  c->ke_minb = MINB;
   c->ke_on = true;
-  // the basis slots and overflow records are per CTA: size them for both launches
-  if (c->ke_grid > c->kry_grid) c->kry_grid = c->ke_grid;
   return TB_OK;
 }
 
 template <bool BF>
-tb_status kry_eig_configure(tb_ctx* c, int max_smem) {
+tb_status kry_eig_configure(tb_ctx* c, int max_smem, int slots = 8, int minb = 4) {
   const int ntc = ntc_of(4 * c->p.r);
-  if (ntc == 16) return kry_eig_configure_t<16, BF>(c, max_smem);
-  if (ntc == 32) return kry_eig_configure_t<32, BF>(c, max_smem);
-  if (ntc == 48) return kry_eig_configure_t<48, BF>(c, max_smem);
-  return kry_eig_configure_t<64, BF>(c, max_smem);
+#define TB_KE_TILE(N) \
+  return minb == 5 ? kry_eig_tile<N, BF, 5>(c, slots, max_smem) : kry_eig_tile<N, BF, 4>(c, slots, max_smem)
+  if (ntc == 16) TB_KE_TILE(16);
+  if (ntc == 32) TB_KE_TILE(32);
+  if (ntc == 48) TB_KE_TILE(48);
+  TB_KE_TILE(64);
+#undef TB_KE_TILE
 }
 
 // Targets sorted into size buckets on the device: nb buckets with upper
@@ -805,7 +816,8 @@ tb_status kry_eig_launch(tb_ctx* c, int n, const int* c_off, const int* c_idx, c
                          const int* h_idx, const float* Hsk, double* lambda, double* S, double* P,
                          int* kdim, bool largest_first, cudaStream_t s) {
   const tb_params& p = c->p;
-  const tbsk::SkArgs a = sk_args(c, n, c_off, c_idx, h_off, h_idx, Hsk);
+  tbsk::SkArgs a = sk_args(c, n, c_off, c_idx, h_off, h_idx, Hsk);
+  a.ecap = c->ke_ecap;
   XArgs xa{n, 4 * p.r, c->T, c->colmask, reinterpret_cast<const float*>(c->Y), h_off, c->Zf,
            c->lamf, lambda, S, P, kdim, c->d_status};
   const int* order = nullptr;
@@ -821,10 +833,14 @@ tb_status kry_eig_launch(tb_ctx* c, int n, const int* c_off, const int* c_idx, c
   const int ntc = ntc_of(4 * p.r);
   const long long to = p.timeout_cycles;
   const size_t sm = c->ke_smem;
-  if (ntc == 16) kry_eig_kernel<16, BF><<<grid, 128, sm, s>>>(a, xa, order, work, done, to);
-  else if (ntc == 32) kry_eig_kernel<32, BF><<<grid, 128, sm, s>>>(a, xa, order, work, done, to);
-  else if (ntc == 48) kry_eig_kernel<48, BF><<<grid, 128, sm, s>>>(a, xa, order, work, done, to);
-  else kry_eig_kernel<64, BF><<<grid, 128, sm, s>>>(a, xa, order, work, done, to);
+#define TB_KE_LAUNCH(N)                                                                    \
+  (c->ke_minb == 5 ? kry_eig_kernel<N, BF, 5><<<grid, 128, sm, s>>>(a, xa, order, work, done, to) \
+                   : kry_eig_kernel<N, BF, 4><<<grid, 128, sm, s>>>(a, xa, order, work, done, to))
+  if (ntc == 16) TB_KE_LAUNCH(16);
+  else if (ntc == 32) TB_KE_LAUNCH(32);
+  else if (ntc == 48) TB_KE_LAUNCH(48);
+  else TB_KE_LAUNCH(64);
+#undef TB_KE_LAUNCH
   TB_CUDA_TRY(cudaGetLastError());
   return TB_OK;
 }
@@ -1077,9 +1093,22 @@ tb_status tune_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int
     return launch_eig(c, n, h_off, lambda, S, P, kdim, s);
   };
   const float inf = 1e30f;
-  r.ms_persistent = c->ke_on ? timed([&] { return run_plan(TB_SCHED_PERSISTENT); }) : inf;
-  r.ms_persistent_largest_first =
-      c->ke_on ? timed([&] { return run_plan(TB_SCHED_PERSISTENT_LARGEST_FIRST); }) : inf;
+  // persistent queue: two tiles (8 records per slot at 4 CTAs per SM, 6 at 5)
+  // in index order and largest clusters first
+  r.ms_persistent = r.ms_persistent_largest_first = inf;
+  const int ke_tiles[2][2] = {{8, 4}, {6, 5}};
+  int ke_best[2] = {0, 0};                      // tile of each order's best time
+  if (c->ke_on) {
+    for (int v = 0; v < 2 && err == TB_OK; ++v) {
+      if (kry_eig_configure<BF>(c, max_smem, ke_tiles[v][0], ke_tiles[v][1]) != TB_OK) continue;
+      const float t0 = timed([&] { return run_plan(TB_SCHED_PERSISTENT); });
+      const float t1 = timed([&] { return run_plan(TB_SCHED_PERSISTENT_LARGEST_FIRST); });
+      if (t0 < r.ms_persistent) { r.ms_persistent = t0; ke_best[0] = v; }
+      if (t1 < r.ms_persistent_largest_first) { r.ms_persistent_largest_first = t1; ke_best[1] = v; }
+    }
+    // back to the default tile until the choice is made
+    if (err == TB_OK) err = kry_eig_configure<BF>(c, max_smem, ke_tiles[0][0], ke_tiles[0][1]);
+  }
   r.ms_separate = timed([&] { return run_plan(TB_SCHED_SEPARATE); });
   // bucketed plans: the observed sizes cut at quantiles into 1..4 buckets
   // (bounds rounded up to the size bins; the last bucket reaches
@@ -1148,6 +1177,11 @@ tb_status tune_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int
     choice = TB_SCHED_PERSISTENT_LARGEST_FIRST;
   }
   if (r.ms_bucketed < bestms) { bestms = r.ms_bucketed; choice = TB_SCHED_BUCKETED; }
+  if (err == TB_OK && c->ke_on &&
+      (choice == TB_SCHED_PERSISTENT || choice == TB_SCHED_PERSISTENT_LARGEST_FIRST)) {
+    const int v = ke_best[choice == TB_SCHED_PERSISTENT ? 0 : 1];
+    err = kry_eig_configure<BF>(c, max_smem, ke_tiles[v][0], ke_tiles[v][1]);
+  }
   if (err == TB_OK) {
     c->plan = choice;
     err = run_plan(choice);                       // leaves the record of the given lists
@@ -1162,6 +1196,8 @@ tb_status tune_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int
   cudaEventDestroy(e1);
   if (err == TB_OK && rep) {
     r.schedule = choice;
+    r.persistent_records_per_slot = c->ke_on && c->p.max_cluster > 0 ? c->ke_ecap / c->p.max_cluster : 0;
+    r.persistent_ctas_per_sm = c->ke_on ? c->ke_grid / c->num_sms : 0;
     r.n_buckets = c->plan_nb;
     for (int b = 0; b < c->plan_nb; ++b) {
       r.bucket_hi[b] = c->plan_hi[b];

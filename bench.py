@@ -1292,21 +1292,33 @@ def run_autograd(args):
         F64 = s64.F_loc.cpu().numpy()
         rng = np.random.default_rng(cfg["seed"])
         h = 1e-4
-        fd_err = 0.0
+        fd_err, crossings, errs = 0.0, [], []
+        c_off0, c_idx0 = s64.c_off.clone(), s64.c_idx.clone()
         for q in rng.choice(3 * n, size=args.fd_coords, replace=False):
             atom, k = divmod(int(q), 3)
             ev = []
+            same = True
             for sgn in (1.0, -1.0):
                 x = pos.copy()
                 x[atom, k] += sgn * h
                 s64.set_positions(wrap(x, L))
                 s64.local_forward()
                 ev.append(s64.energies_loc[4].item())
-            fd_err = max(fd_err, abs(-(ev[0] - ev[1]) / (2 * h) - F64[atom, k]))
+                same = same and torch.equal(s64.c_off, c_off0) and torch.equal(s64.c_idx, c_idx0)
+            e = abs(-(ev[0] - ev[1]) / (2 * h) - F64[atom, k])
+            errs.append(e)
+            # the truncated local energy jumps where an atom crosses a cluster's
+            # cutoff sphere: a difference across such a crossing is not a derivative
+            if same:
+                fd_err = max(fd_err, e)
+            else:
+                crossings.append({"atom": atom, "axis": k, "err_eV_per_A": e})
         s64.check()
         s64.close()
         check = {"fd_coords": args.fd_coords, "fd_h_A": h,
                  "fd_vs_fp64_gradient_max_eV_per_A": fd_err,
+                 "fd_vs_fp64_gradient_median_eV_per_A": float(np.median(errs)),
+                 "fd_coords_crossing_a_cluster_cutoff": crossings,
                  "force_vs_fp64_path_max_eV_per_A": float(np.abs(res[True]["F"] - F64).max()),
                  "stored_equals_recomputed": bool(np.array_equal(res[True]["F"],
                                                                  res[False]["F"]))}

@@ -184,8 +184,8 @@ struct tb_ctx {
   float* lamf = nullptr;             // n * NT
   void* Vg = nullptr;                // kry_grid * Dmax * NT (TV) when the basis is global
   int2* lent = nullptr;              // kry_grid * max_cluster * max_hnbr (slot, bond), FP64 path
-  void* recg = nullptr;              // mixed path: per-CTA overflow of the local
-  int* rslg = nullptr;               //   Slater-Koster records and neighbour offsets
+  int* bondg = nullptr;              // mixed path: per-CTA overflow of the local
+  int* rslg = nullptr;               //   sparsity (bond indices, neighbour offsets)
   double* mu_part = nullptr;         // mu_grid * 4
   unsigned int* bar = nullptr;       // barrier counter
   double* mu_state = nullptr;        // 4 doubles
@@ -210,6 +210,7 @@ struct tb_ctx {
   size_t ke_smem = 0;
   int ke_ecap = 0;                   // records in shared memory per target (persistent launch)
   int ke_minb = 4;                   // CTAs per SM its register budget allows
+  int ke_default_slots = 8;          // records per slot of the default persistent tile
   int sk_ecap = 0;                   // local records kept in shared memory per target
   int sk_grid = 0;                   // CTAs of the mixed Krylov kernel (separate launch)
   size_t sk_smem = 0;

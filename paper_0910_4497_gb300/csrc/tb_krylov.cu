@@ -670,7 +670,7 @@ tbsk::SkArgs sk_args(const tb_ctx* c, int n, const int* c_off, const int* c_idx,
   a.c_off = c_off; a.c_idx = c_idx; a.h_off = h_off; a.h_idx = h_idx;
   a.Hsk = reinterpret_cast<const float4*>(Hsk);
   a.T = c->T; a.Y = reinterpret_cast<float*>(c->Y); a.colmask = c->colmask;
-  a.Vg = reinterpret_cast<float*>(c->Vg); a.recg = c->recg; a.rslg = c->rslg;
+  a.Vg = reinterpret_cast<float*>(c->Vg); a.bondg = c->bondg; a.rslg = c->rslg;
   a.st = c->d_status;
   return a;
 }
@@ -719,9 +719,18 @@ tb_status sk_configure_t(tb_ctx* c, int max_smem) {
   // default tile: records kept in shared memory, 8 per cluster slot (carbon
   // within 2.6 A: ~8 in-cluster neighbours on average); none when the
   // Hamiltonian lists are long (long-range hoppings)
+  // (of 8, 6, 4 or 0 records per cluster slot, the most that keeps the
+  // largest number of CTAs per SM; with 0 every target reads its records
+  // from the bond table)
   tb_sk_cfg t;
   c->kry_grid = 0;
-  tb_status st = sk_tile<BF>(c, p.max_cluster, 8, 4, max_smem, t);
+  tb_status st = TB_ERR_CAPACITY;
+  for (const int slots : {8, 6, 4, 0}) {
+    tb_sk_cfg u;
+    if (sk_tile<BF>(c, p.max_cluster, slots, 4, max_smem, u) != TB_OK) continue;
+    if (st != TB_OK || u.grid > t.grid) t = u;
+    st = TB_OK;
+  }
   if (st != TB_OK) return st;
   c->sk_ecap = t.ecap;
   c->sk_smem = t.smem;
@@ -738,7 +747,14 @@ tb_status sk_configure_t(tb_ctx* c, int max_smem) {
     if (hi > p.max_cluster || b == tb_plan::MAX_BUCKETS - 1) hi = p.max_cluster;
     if (c->plan_nb > 0 && hi <= c->plan_hi[c->plan_nb - 1]) continue;
     tb_sk_cfg tb_;
-    if (sk_tile<BF>(c, hi, 8, 4, max_smem, tb_) != TB_OK) return TB_ERR_CAPACITY;
+    bool found = false;
+    for (const int slots : {8, 6, 4, 0}) {
+      tb_sk_cfg u;
+      if (sk_tile<BF>(c, hi, slots, 4, max_smem, u) != TB_OK) continue;
+      if (!found || u.grid > tb_.grid) tb_ = u;
+      found = true;
+    }
+    if (!found) return TB_ERR_CAPACITY;
     c->plan_hi[c->plan_nb] = hi;
     c->plan_cfg[c->plan_nb++] = tb_;
   }
@@ -772,7 +788,7 @@ tb_status kry_eig_tile(tb_ctx* c, int slots, int max_smem) {
 }
 
 template <bool BF>
-tb_status kry_eig_configure(tb_ctx* c, int max_smem, int slots = 8, int minb = 4) {
+tb_status kry_eig_configure(tb_ctx* c, int max_smem, int slots, int minb) {
   const int ntc = ntc_of(4 * c->p.r);
 #define TB_KE_TILE(N) \
   return minb == 5 ? kry_eig_tile<N, BF, 5>(c, slots, max_smem) : kry_eig_tile<N, BF, 4>(c, slots, max_smem)
@@ -989,8 +1005,19 @@ tb_status krylov_configure(tb_ctx* c) {
   c->ke_on = false;
   if (c->p.group_m == 1 && c->p.schedule != TB_SCHED_SEPARATE &&
       c->p.schedule != TB_SCHED_BUCKETED) {
-    if ((bf ? kry_eig_configure<true>(c, max_smem) : kry_eig_configure<false>(c, max_smem)) != TB_OK)
-      c->ke_on = false;
+    // default tile: of 8, 6, 4 or 0 records per slot, the most that keeps the
+    // largest number of CTAs per SM
+    int best = -1, best_grid = 0;
+    for (const int slots : {8, 6, 4, 0}) {
+      if ((bf ? kry_eig_configure<true>(c, max_smem, slots, 4)
+              : kry_eig_configure<false>(c, max_smem, slots, 4)) != TB_OK)
+        continue;
+      if (c->ke_grid > best_grid) { best_grid = c->ke_grid; best = slots; }
+    }
+    c->ke_on = best >= 0 &&
+               (bf ? kry_eig_configure<true>(c, max_smem, best, 4)
+                   : kry_eig_configure<false>(c, max_smem, best, 4)) == TB_OK;
+    c->ke_default_slots = best;
   }
   return TB_OK;
 }
@@ -1096,7 +1123,7 @@ tb_status tune_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int
   // persistent queue: two tiles (8 records per slot at 4 CTAs per SM, 6 at 5)
   // in index order and largest clusters first
   r.ms_persistent = r.ms_persistent_largest_first = inf;
-  const int ke_tiles[2][2] = {{8, 4}, {6, 5}};
+  const int ke_tiles[2][2] = {{c->ke_default_slots, 4}, {6, 5}};
   int ke_best[2] = {0, 0};                      // tile of each order's best time
   if (c->ke_on) {
     for (int v = 0; v < 2 && err == TB_OK; ++v) {
@@ -1107,7 +1134,7 @@ tb_status tune_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int
       if (t1 < r.ms_persistent_largest_first) { r.ms_persistent_largest_first = t1; ke_best[1] = v; }
     }
     // back to the default tile until the choice is made
-    if (err == TB_OK) err = kry_eig_configure<BF>(c, max_smem, ke_tiles[0][0], ke_tiles[0][1]);
+    if (err == TB_OK) err = kry_eig_configure<BF>(c, max_smem, c->ke_default_slots, 4);
   }
   r.ms_separate = timed([&] { return run_plan(TB_SCHED_SEPARATE); });
   // bucketed plans: the observed sizes cut at quantiles into 1..4 buckets
@@ -1138,9 +1165,9 @@ tb_status tune_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int
     float bms[tb_plan::MAX_BUCKETS];
     for (int b = 0; b < m && err == TB_OK; ++b) {
       bms[b] = inf;
-      const int slots[2] = {8, 6};
+      const int slots[4] = {8, 6, 4, 0};
       const int minbs[2] = {4, 5};
-      for (int si = 0; si < 2; ++si)
+      for (int si = 0; si < 4; ++si)
         for (int mi = 0; mi < 2; ++mi) {
           tb_sk_cfg t;
           if (sk_tile<BF>(c, hi[b], slots[si], minbs[mi], max_smem, t) != TB_OK) continue;

@@ -73,8 +73,8 @@ struct SkArgs {
   float* Y;
   unsigned long long* colmask;
   float* Vg;                            // per-CTA basis slots: r blocks of 16 max_cluster
-  void* recg;                           // per-CTA overflow records: max_cluster * max_hnbr
-  int* rslg;                            // and their neighbour offsets
+  int* bondg;                           // per-CTA overflow: bond index of each local entry
+  int* rslg;                            //   and its neighbour offset (max_cluster * max_hnbr)
   int* st;
 };
 
@@ -247,10 +247,15 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
   __syncthreads();
   block_scan(roff, nc, flags + 8 - KW);                // wtot scratch: the last flag words
   const int ne = roff[nc];
+  // a target whose records do not fit keeps, per entry, the bond index in its
+  // CTA's overflow slot and reads the record from the bond table (L2) in
+  // every sweep
+  const bool ovf = ne > a.ecap;
   Rec* rec = rec_s;
   int* rsl = rsl_s;
-  if (ne > a.ecap) {
-    rec = reinterpret_cast<Rec*>(a.recg) + (size_t)blockIdx.x * gcap;
+  int* bnd = nullptr;
+  if (ovf) {
+    bnd = a.bondg + (size_t)blockIdx.x * gcap;
     rsl = a.rslg + (size_t)blockIdx.x * gcap;
   }
   for (int s = tid; s < nc; s += KT) {
@@ -261,9 +266,13 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
     for (int p = p0; p < pe; ++p) {
       const int t = cache ? hsl[s * HC + (p - p0)] : find_slot(cl, nc, a.h_idx[p]);
       if (t >= 0) {
-        const float4 hv = __ldg(a.Hsk + p);
-        if constexpr (BF) rec[e] = pack_bf16x4(hv);
-        else rec[e] = hv;
+        if (ovf) {
+          bnd[e] = p;
+        } else {
+          const float4 hv = __ldg(a.Hsk + p);
+          if constexpr (BF) rec[e] = pack_bf16x4(hv);
+          else rec[e] = hv;
+        }
         rsl[e] = sbase(t);
         ++e;
       }
@@ -310,10 +319,10 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
       for (int e = roff[s]; e < e1; ++e) {
         float4 hv, u;
         if constexpr (BF) {
-          hv = unpack_bf16x4(rec[e]);
+          hv = ovf ? unpack_bf16x4(pack_bf16x4(__ldg(a.Hsk + bnd[e]))) : unpack_bf16x4(rec[e]);
           u = unpack_bf16x4(vbf[((rsl[e] >> 2) & ~3) + c]);   // SPB * slot (not swizzled)
         } else {
-          hv = rec[e];
+          hv = ovf ? __ldg(a.Hsk + bnd[e]) : rec[e];
           u = f4(Vk + (rsl[e] ^ c4x));
         }
         const float dt = fmaf(hv.y, u.y, fmaf(hv.z, u.z, hv.w * u.w));

@@ -103,7 +103,7 @@ def test_autotuned_plan_matches_oracle(tb, slab):
     assert sum(b["targets"] for b in rep["buckets"]) == s.n
     assert rep["buckets"][-1]["sizes_up_to"] == p["max_cluster"]
     for b in rep["buckets"]:
-        assert b["records_per_slot_in_smem"] in (0, 6, 8) and b["ctas_per_sm"] >= 1
+        assert b["records_per_slot_in_smem"] in (0, 4, 6, 8) and b["ctas_per_sm"] >= 1
     # the record left by the tuner is the chosen plan's on these lists
     s.find_mu()
     s.forces()

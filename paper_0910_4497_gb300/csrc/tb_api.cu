@@ -84,8 +84,7 @@ size_t carve(tb_ctx* c, int n, unsigned char* base) {
   c->Vg = k.take<unsigned char>(krylov_basis_bytes_global(c));
   c->lent = k.take<int2>(p.prec == TB_PREC_FP64
                              ? (size_t)c->kry_grid * p.max_cluster * p.max_hnbr : 0);
-  c->bondg = k.take<int>(krylov_overflow_records(c));
-  c->rslg = k.take<int>(krylov_overflow_records(c));
+  c->bref = k.take<int2>(krylov_overflow_records(c));
   c->ke_work = k.take<int>((size_t)n + 1);
   c->tgt_order = k.take<int>(n);
   c->tgt_boff = k.take<int>(tb_plan::MAX_BINS + 1);

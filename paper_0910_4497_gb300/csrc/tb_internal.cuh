@@ -184,8 +184,8 @@ struct tb_ctx {
   float* lamf = nullptr;             // n * NT
   void* Vg = nullptr;                // kry_grid * Dmax * NT (TV) when the basis is global
   int2* lent = nullptr;              // kry_grid * max_cluster * max_hnbr (slot, bond), FP64 path
-  int* bondg = nullptr;              // mixed path: per-CTA overflow of the local
-  int* rslg = nullptr;               //   sparsity (bond indices, neighbour offsets)
+  int2* bref = nullptr;              // mixed path: per-CTA overflow of the local
+                                     //   sparsity (bond index, neighbour offset)
   double* mu_part = nullptr;         // mu_grid * 4
   unsigned int* bar = nullptr;       // barrier counter
   double* mu_state = nullptr;        // 4 doubles

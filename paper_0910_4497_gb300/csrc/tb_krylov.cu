@@ -670,7 +670,7 @@ tbsk::SkArgs sk_args(const tb_ctx* c, int n, const int* c_off, const int* c_idx,
   a.c_off = c_off; a.c_idx = c_idx; a.h_off = h_off; a.h_idx = h_idx;
   a.Hsk = reinterpret_cast<const float4*>(Hsk);
   a.T = c->T; a.Y = reinterpret_cast<float*>(c->Y); a.colmask = c->colmask;
-  a.Vg = reinterpret_cast<float*>(c->Vg); a.bondg = c->bondg; a.rslg = c->rslg;
+  a.Vg = reinterpret_cast<float*>(c->Vg); a.bref = c->bref;
   a.st = c->d_status;
   return a;
 }

@@ -73,8 +73,8 @@ struct SkArgs {
   float* Y;
   unsigned long long* colmask;
   float* Vg;                            // per-CTA basis slots: r blocks of 16 max_cluster
-  int* bondg;                           // per-CTA overflow: bond index of each local entry
-  int* rslg;                            //   and its neighbour offset (max_cluster * max_hnbr)
+  int2* bref;                           // per-CTA overflow (max_cluster * max_hnbr entries):
+                                        //   bond index and neighbour offset of each local entry
   int* st;
 };
 
@@ -251,13 +251,9 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
   // CTA's overflow slot and reads the record from the bond table (L2) in
   // every sweep
   const bool ovf = ne > a.ecap;
-  Rec* rec = rec_s;
-  int* rsl = rsl_s;
-  int* bnd = nullptr;
-  if (ovf) {
-    bnd = a.bondg + (size_t)blockIdx.x * gcap;
-    rsl = a.rslg + (size_t)blockIdx.x * gcap;
-  }
+  Rec* const rec = rec_s;
+  int* const rsl = rsl_s;
+  int2* const bref = a.bref + (size_t)blockIdx.x * gcap;
   for (int s = tid; s < nc; s += KT) {
     const int at = cl[s];
     const int p0 = a.h_off[at];
@@ -267,13 +263,13 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
       const int t = cache ? hsl[s * HC + (p - p0)] : find_slot(cl, nc, a.h_idx[p]);
       if (t >= 0) {
         if (ovf) {
-          bnd[e] = p;
+          bref[e] = make_int2(p, sbase(t));
         } else {
           const float4 hv = __ldg(a.Hsk + p);
           if constexpr (BF) rec[e] = pack_bf16x4(hv);
           else rec[e] = hv;
+          rsl[e] = sbase(t);
         }
-        rsl[e] = sbase(t);
         ++e;
       }
     }
@@ -314,17 +310,9 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
       const int s = it >> 2, c = it & 3, c4x = 4 * c;
       const float4 u0 = f4(Vk + cofs(s, c));
       float4 acc = make_float4(Es * u0.x, Ep * u0.y, Ep * u0.z, Ep * u0.w);
-      const int e1 = roff[s + 1];
-#pragma unroll 2
-      for (int e = roff[s]; e < e1; ++e) {
-        float4 hv, u;
-        if constexpr (BF) {
-          hv = ovf ? unpack_bf16x4(pack_bf16x4(__ldg(a.Hsk + bnd[e]))) : unpack_bf16x4(rec[e]);
-          u = unpack_bf16x4(vbf[((rsl[e] >> 2) & ~3) + c]);   // SPB * slot (not swizzled)
-        } else {
-          hv = ovf ? __ldg(a.Hsk + bnd[e]) : rec[e];
-          u = f4(Vk + (rsl[e] ^ c4x));
-        }
+      // one term of (H_c u)_s from the bond record hv = (s(r), l) and the
+      // neighbour's column u
+      auto term = [&](const float4 hv, const float4 u) {
         const float dt = fmaf(hv.y, u.y, fmaf(hv.z, u.z, hv.w * u.w));
         const float ps = fmaf(Vss, u.x, Vsp * dt);
         const float pp = fmaf(Cpp, dt, -Vsp * u.x);
@@ -333,6 +321,44 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
         acc.y = fmaf(hv.y, t, fmaf(w, u.y, acc.y));
         acc.z = fmaf(hv.z, t, fmaf(w, u.z, acc.z));
         acc.w = fmaf(hv.w, t, fmaf(w, u.w, acc.w));
+      };
+      // column c of the neighbour block at offset o (slot-major, swizzled)
+      auto col = [&](const int o) -> float4 {
+        if constexpr (BF) return unpack_bf16x4(vbf[((o >> 2) & ~3) + c]);   // SPB * slot
+        else return f4(Vk + (o ^ c4x));
+      };
+      int e = roff[s];
+      const int e1 = roff[s + 1];
+      if (ovf) {
+        // records gathered from the bond table (L2): the loads of four
+        // entries are issued before their arithmetic
+        for (; e + 4 <= e1; e += 4) {
+          int2 q[4];
+          float4 hv[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) q[j] = bref[e + j];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) hv[j] = __ldg(a.Hsk + q[j].x);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if constexpr (BF) hv[j] = unpack_bf16x4(pack_bf16x4(hv[j]));
+            term(hv[j], col(q[j].y));
+          }
+        }
+        for (; e < e1; ++e) {
+          const int2 q = bref[e];
+          float4 hv = __ldg(a.Hsk + q.x);
+          if constexpr (BF) hv = unpack_bf16x4(pack_bf16x4(hv));
+          term(hv, col(q.y));
+        }
+      } else {
+#pragma unroll 2
+        for (; e < e1; ++e) {
+          float4 hv;
+          if constexpr (BF) hv = unpack_bf16x4(rec[e]);
+          else hv = rec[e];
+          term(hv, col(rsl[e]));
+        }
       }
       float4 vm[4];
       if (k > 0) {
@@ -699,7 +725,8 @@ __device__ __forceinline__ void krylov_sk_target(const SkArgs& a, const int i) {
     for (int q = tid; q < nrows * NT; q += KT) {
       const int rr = q / NT, col = q - rr * NT;
       const int qq = rr >> 2, beta = rr & 3;
-      const int so = qq == 0 ? 0 : (qq - 1 < rcnt ? rsl[roff[0] + qq - 1] : -1);
+      const int e = roff[0] + qq - 1;       // entry of neighbour qq - 1 in row 0
+      const int so = qq == 0 ? 0 : (qq - 1 < rcnt ? (ovf ? bref[e].y : rsl[e]) : -1);
       const int b = col >> 2, c = col & 3;
       float val = 0.f;
       if (b < nblocks && so >= 0) val = Vg[(size_t)b * VB + (so ^ (4 * c)) + beta];

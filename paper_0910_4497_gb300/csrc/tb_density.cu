@@ -74,7 +74,7 @@ struct MuArgs {
   int NT;
   const double* lambda;
   const double* S;
-  double kT, ne, tolN;
+  double kT, ikT, ne, tolN;                 // ikT = 1 / kT
   const double* guess;
   double* mu_out;
   double* ncount_out;
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
   __shared__ float totf[MU_NPT];
   __shared__ int sflag;
   const int G = gridDim.x;
-  const double ikT = 1.0 / a.kT;
+  const double ikT = a.ikT;
   const long long q0 = (long long)blockIdx.x * a.per_block;
   const long long q1 = min(a.npairs, q0 + a.per_block);
   const int nloc = (int)max(0ll, q1 - q0);
@@ -312,19 +312,34 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
     }
     __syncthreads();
   }
-  const double lo0 = tot[0] - 40.0 * a.kT, hi0 = tot[1] + 40.0 * a.kT;
-  double lo = lo0, hi = hi0;
-  int iters = 0;
+  // The scalar search state (bracket, trial point, Newton step) is advanced
+  // by thread 0 alone and read by every thread after a barrier: on this GPU a
+  // warp-wide FP64 instruction holds the SM's FP64 pipe for many cycles
+  // whatever the number of active lanes, so scalar FP64 arithmetic repeated
+  // by all eight warps would cost eight times the pipe time of one.
+  enum { S_LO, S_HI, S_H, S_MU, S_MID, S_DXO, S_DX, S_NLO, S_NHI, S_NMU, S_LO0, S_HI0, S_NS };
+  __shared__ double ss[S_NS];
+  __shared__ float sf[6];                          // dx, lo, mu, lo, hi, mid as floats
+  __shared__ int si[4];                            // iterations, go on, converged, near path
+  if (threadIdx.x == 0) {
+    const double lo0 = tot[0] - 40.0 * a.kT, hi0 = tot[1] + 40.0 * a.kT;
+    const double h = (hi0 - lo0) / (MU_NPT + 1);
+    ss[S_LO0] = lo0; ss[S_HI0] = hi0;
+    ss[S_LO] = lo0; ss[S_HI] = hi0; ss[S_H] = h;
+    ss[S_NLO] = -1.0; ss[S_NHI] = -1.0;           // counts at lo / hi (unknown: < 0)
+    sf[0] = (float)(h * ikT); sf[1] = (float)lo0;
+    si[0] = 0;
+    si[1] = hi0 - lo0 > 0.05;
+  }
+  __syncthreads();
+  const float ikTf = (float)a.ikT;
   // ---- coarse bracketing with FP32 occupations at MU_NPT points per pass, to
   // a bracket of 0.05 eV; the counts at its ends give Newton's first point
-  double nlo_cnt = -1.0, nhi_cnt = -1.0;     // counts at lo / hi (unknown: < 0)
-  for (int pass = 0; pass < 6 && hi - lo > 0.05; ++pass) {
+  for (int pass = 0; pass < 6 && si[1]; ++pass) {
     float cnt[MU_NPT];
-    const double h = (hi - lo) / (MU_NPT + 1);
 #pragma unroll
     for (int t = 0; t < MU_NPT; ++t) cnt[t] = 0.f;
-    const float dx = (float)(h * ikT);
-    const float lof = (float)lo, ikTf = (float)ikT;
+    const float dx = sf[0], lof = sf[1];
     for (int t = threadIdx.x; t < nloc; t += MT) {
       float lf, wf;
       getf(t, lf, wf);
@@ -337,40 +352,59 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
       }
     }
     if (!grid_allreduce_f32(cnt, a, gen, redf, totf, &sflag)) return;
-    int jfirst = MU_NPT;            // first trial point with N > N_e (N increases with mu)
-    for (int u = MU_NPT - 1; u >= 0; --u) if (2.0 * (double)totf[u] > a.ne) jfirst = u;
-    const double nlo = jfirst == 0 ? lo : lo + jfirst * h;
-    const double nhi = jfirst == MU_NPT ? hi : lo + (jfirst + 1) * h;
-    if (jfirst > 0) nlo_cnt = 2.0 * (double)totf[jfirst - 1];
-    if (jfirst < MU_NPT) nhi_cnt = 2.0 * (double)totf[jfirst];
-    lo = nlo;
-    hi = nhi;
-    ++iters;
+    if (threadIdx.x < 32) {
+      // lane u tests trial point u; the first with N > N_e (N increases with mu)
+      static_assert(MU_NPT == 32, "one trial point per lane");
+      const unsigned above = __ballot_sync(0xffffffffu, 2.0 * (double)totf[threadIdx.x] > a.ne);
+      if (threadIdx.x == 0) {
+        const int jfirst = above ? __ffs(above) - 1 : MU_NPT;
+        const double lo = ss[S_LO], hi = ss[S_HI], h = ss[S_H];
+        const double nlo = jfirst == 0 ? lo : lo + jfirst * h;
+        const double nhi = jfirst == MU_NPT ? hi : lo + (jfirst + 1) * h;
+        if (jfirst > 0) ss[S_NLO] = 2.0 * (double)totf[jfirst - 1];
+        if (jfirst < MU_NPT) ss[S_NHI] = 2.0 * (double)totf[jfirst];
+        const double hn = (nhi - nlo) / (MU_NPT + 1);
+        ss[S_LO] = nlo; ss[S_HI] = nhi; ss[S_H] = hn;
+        sf[0] = (float)(hn * ikT); sf[1] = (float)nlo;
+        si[0] += 1;
+        si[1] = nhi - nlo > 0.05;
+      }
+    }
+    __syncthreads();
   }
   // ---- FP64 safeguarded Newton on N(mu) - N_e.  The first pass also counts
   // at the coarse bracket ends (FP32 counts may misjudge a point whose count
   // is within rounding of N_e) and widens the bracket on a side that fails.
-  const bool check = lo > lo0 || hi < hi0;
-  double mu = 0.5 * (lo + hi);
-  if (nlo_cnt >= 0.0 && nhi_cnt > nlo_cnt) {     // linear interpolation of the counts
-    const double fr = (a.ne - nlo_cnt) / (nhi_cnt - nlo_cnt);
-    if (fr > 0.0 && fr < 1.0) mu = lo + fr * (hi - lo);
+  __shared__ int s_check;
+  if (threadIdx.x == 0) {
+    const double lo = ss[S_LO], hi = ss[S_HI], nlo_cnt = ss[S_NLO], nhi_cnt = ss[S_NHI];
+    s_check = lo > ss[S_LO0] || hi < ss[S_HI0];
+    double mu = 0.5 * (lo + hi);
+    if (nlo_cnt >= 0.0 && nhi_cnt > nlo_cnt) {     // linear interpolation of the counts
+      const double fr = (a.ne - nlo_cnt) / (nhi_cnt - nlo_cnt);
+      if (fr > 0.0 && fr < 1.0) mu = lo + fr * (hi - lo);
+    }
+    if (a.guess) {
+      const double g = *a.guess;
+      if (isfinite(g) && g > lo && g < hi) mu = g;
+    }
+    ss[S_MU] = mu;
+    ss[S_DXO] = hi - lo;
+    ss[S_DX] = hi - lo;
+    ss[S_NMU] = 0.0;
+    ss[S_MID] = 0.5 * (lo + hi);
+    sf[5] = (float)ss[S_MID];
+    si[2] = 0;
   }
-  if (a.guess) {
-    const double g = *a.guess;
-    if (isfinite(g) && g > lo && g < hi) mu = g;
-  }
-  double dxold = hi - lo, dx = dxold;
-  double Nmu = 0.0;
-  bool conv = false;
-  const float ikTf = (float)ikT;
+  __syncthreads();
+  const bool check = s_check != 0;
   // Pairs within 17.5 kT of the coarse bracket's midpoint go to a compact list
-  // (block scan: a fixed order).  While mu stays within 1.5 kT of it, every
-  // other pair has |x| > 15.5 and takes pair_occ's FP32 branch, and the FP64
-  // branch runs on the list with full warps (a warp-wide FP64 instruction
-  // costs the same with one active lane as with 32).
-  const double mid = 0.5 * (lo + hi);
-  const float midf = (float)mid, Rf = (float)(17.5 * a.kT);
+  // (block scan: a fixed order).  While mu (and, on the first pass, the
+  // bracket ends) stays within 1.5 kT of it, every other pair has |x| > 15.5
+  // and takes pair_occ's FP32 branch, and the FP64 branch runs on the list
+  // with full warps (a warp-wide FP64 instruction costs the same with one
+  // active lane as with 32).
+  const float midf = sf[5], Rf = (float)(17.5 * a.kT);
   int nnear = 0;
   if (a.staged) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -397,10 +431,17 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
     __syncthreads();
   }
   for (int it = 0; it < a.max_iter; ++it) {
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
     const bool ends = it == 0 && check;
-    const float muf = (float)mu, lof = (float)lo, hif = (float)hi;
-    if (a.staged && !ends && fabs(mu - mid) <= 1.5 * a.kT) {
+    if (threadIdx.x == 0) {
+      const double mu = ss[S_MU], lo = ss[S_LO], hi = ss[S_HI], mid = ss[S_MID], w = 1.5 * a.kT;
+      si[3] = a.staged && fabs(mu - mid) <= w && (!ends || (fabs(lo - mid) <= w && fabs(hi - mid) <= w));
+      sf[2] = (float)mu; sf[3] = (float)lo; sf[4] = (float)hi;
+    }
+    __syncthreads();
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    const double mu = ss[S_MU], lo = ss[S_LO], hi = ss[S_HI];
+    const float muf = sf[2], lof = sf[3], hif = sf[4];
+    if (si[3]) {
       for (int t = threadIdx.x; t < nloc; t += MT) {
         float lf, wf;
         getf(t, lf, wf);
@@ -408,6 +449,11 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
         double l, w;
         get(t, l, w);
         pair_occ(l, w, lf, wf, mu, muf, ikT, ikTf, v[0], v[1]);
+        if (ends) {
+          double dd = 0.0;
+          pair_occ(l, w, lf, wf, lo, lof, ikT, ikTf, v[2], dd);
+          pair_occ(l, w, lf, wf, hi, hif, ikT, ikTf, v[3], dd);
+        }
       }
       for (int x = threadIdx.x; x < nnear; x += MT) {
         const int t = nearl[x];
@@ -416,6 +462,11 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
         double l, w;
         get(t, l, w);
         pair_occ(l, w, lf, wf, mu, muf, ikT, ikTf, v[0], v[1]);
+        if (ends) {
+          double dd = 0.0;
+          pair_occ(l, w, lf, wf, lo, lof, ikT, ikTf, v[2], dd);
+          pair_occ(l, w, lf, wf, hi, hif, ikT, ikTf, v[3], dd);
+        }
       }
     } else {
       for (int t = threadIdx.x; t < nloc; t += MT) {
@@ -433,34 +484,45 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
       }
     }
     if (!grid_allreduce<4>(v, a, gen, red, tot, &sflag)) return;
-    ++iters;
-    Nmu = 2.0 * tot[0];
-    const double dN = 2.0 * tot[1] * ikT;
-    if (ends) {
-      if (2.0 * tot[2] > a.ne) lo = lo0;
-      if (2.0 * tot[3] < a.ne) hi = hi0;
+    if (threadIdx.x == 0) {
+      double lo2 = lo, hi2 = hi, mu2 = mu;
+      double dxold = ss[S_DXO], dx = ss[S_DX];
+      si[0] += 1;
+      const double Nmu = 2.0 * tot[0];
+      const double dN = 2.0 * tot[1] * ikT;
+      ss[S_NMU] = Nmu;
+      if (ends) {
+        if (2.0 * tot[2] > a.ne) lo2 = ss[S_LO0];
+        if (2.0 * tot[3] < a.ne) hi2 = ss[S_HI0];
+      }
+      if (fabs(Nmu - a.ne) <= a.tolN || hi2 - lo2 < 1e-13) {
+        si[2] = 1;                                   // converged at mu
+      } else {
+        if (Nmu < a.ne) lo2 = fmax(lo2, mu2); else hi2 = fmin(hi2, mu2);
+        // bisect when the Newton point leaves the bracket or the step is not at
+        // least halving (Numerical Recipes' rtsafe rule)
+        const double fv = Nmu - a.ne;
+        const double newton = mu2 - fv / dN;
+        if (!(dN > 0.0) || !(newton > lo2 && newton < hi2) || fabs(2.0 * fv) > fabs(dxold * dN)) {
+          dxold = dx;
+          dx = 0.5 * (hi2 - lo2);
+          mu2 = lo2 + dx;
+        } else {
+          dxold = dx;
+          dx = fv / dN;
+          mu2 = newton;
+        }
+      }
+      ss[S_LO] = lo2; ss[S_HI] = hi2; ss[S_MU] = mu2; ss[S_DXO] = dxold; ss[S_DX] = dx;
     }
-    if (fabs(Nmu - a.ne) <= a.tolN || hi - lo < 1e-13) { conv = true; break; }
-    if (Nmu < a.ne) lo = fmax(lo, mu); else hi = fmin(hi, mu);
-    // bisect when the Newton point leaves the bracket or the step is not at
-    // least halving (Numerical Recipes' rtsafe rule)
-    const double fv = Nmu - a.ne;
-    const double newton = mu - fv / dN;
-    if (!(dN > 0.0) || !(newton > lo && newton < hi) || fabs(2.0 * fv) > fabs(dxold * dN)) {
-      dxold = dx;
-      dx = 0.5 * (hi - lo);
-      mu = lo + dx;
-    } else {
-      dxold = dx;
-      dx = fv / dN;
-      mu = newton;
-    }
+    __syncthreads();
+    if (si[2]) break;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *a.mu_out = mu;
-    if (a.ncount_out) *a.ncount_out = Nmu;
-    if (a.iters_out) *a.iters_out = iters;
-    if (!conv) tbk::set_status(a.st, TB_ERR_NO_CONVERGENCE, -1);
+    *a.mu_out = ss[S_MU];
+    if (a.ncount_out) *a.ncount_out = ss[S_NMU];
+    if (a.iters_out) *a.iters_out = si[0];
+    if (!si[2]) tbk::set_status(a.st, TB_ERR_NO_CONVERGENCE, -1);
   }
 }
 
@@ -725,15 +787,26 @@ virial_kernel(int n, const double* pos, double L, const int* h_off, const int* h
 
 // energies[8] = {E_band, -TS, A, E_rep, E_tot, N(mu), mu, KE}; columns of
 // per_target: E_band, -TS, N_e, E_rep, KE.  `cols` selects what to refresh.
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(ER_T)
 energy_reduce_kernel(int n, const double* per_target, const double* mu, double* energies,
                      int with_ke) {
   __shared__ double red[32 * 5];
   __shared__ double tot[5];
   double v[5] = {0, 0, 0, 0, 0};
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
+  // four rows' loads in flight per thread before their additions (in row order)
+  for (int i0 = threadIdx.x; i0 < n; i0 += 4 * ER_T) {
+    double x[4][5];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) v[c] += per_target[5 * i + c];
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * ER_T;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) x[u][c] = i < n ? per_target[5 * i + c] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) v[c] += x[u][c];
+  }
   tbk::block_sum<double, 5>(v, red, tot);
   if (threadIdx.x == 0) {
     if (with_ke) {
@@ -886,6 +959,7 @@ tb_status launch_mu_nt(tb_ctx* c, int n, int NT, const double* lambda, const dou
   a.lambda = lambda;
   a.S = S;
   a.kT = c->p.kT;
+  a.ikT = 1.0 / c->p.kT;
   a.ne = n_electrons;
   a.tolN = c->p.mu_tol * n_electrons;
   a.guess = mu_guess;
@@ -930,7 +1004,7 @@ tb_status launch_forces(tb_ctx* c, int n, const double* pos, double L, const int
                c->per_target, c->d_status};
   force_bond_kernel<<<16 * c->num_sms, 64, 0, s>>>(fa);
   TB_CUDA_TRY(cudaGetLastError());
-  force_sum_kernel<<<(n + 255) / 256, 256, 0, s>>>(fa);
+  force_sum_kernel<<<(n + 63) / 64, 64, 0, s>>>(fa);         // spread the FP64 sums over the SMs
   TB_CUDA_TRY(cudaGetLastError());
   energy_reduce_kernel<<<1, ER_T, 0, s>>>(n, c->per_target, mu, energies, 0);
   TB_CUDA_TRY(cudaGetLastError());
@@ -1040,6 +1114,7 @@ extern "C" tb_status tb_find_mu_static(int n, int r, const double* lambda, const
   a.lambda = lambda;
   a.S = S;
   a.kT = kT;
+  a.ikT = 1.0 / kT;
   a.ne = n_electrons;
   a.tolN = mu_tol * n_electrons;
   a.guess = mu_guess;

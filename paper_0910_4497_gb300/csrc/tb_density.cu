@@ -536,7 +536,7 @@ struct RhoArgs {
   const double* S;
   const double* P;
   const double* mu;
-  double kT;
+  double kT, ikT;       // ikT = 1 / kT
   double* rho;
   double* per_target;   // n x 5
   int* st;
@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(RT) rho_kernel(const RhoArgs a) {
     //     = -min(f, 1-f) |x| - log1p(e)   (exact).
     __shared__ int nidx[tbk::MAX_NT];
     __shared__ int wball[RT / 32];
-    const float ikTf = (float)(1.0 / a.kT), muf = (float)mu;
+    const float ikTf = (float)a.ikT, muf = (float)mu;
     const int k = threadIdx.x;
     bool near_k = false;
     double w = 0.0;
@@ -606,7 +606,7 @@ __global__ void __launch_bounds__(RT) rho_kernel(const RhoArgs a) {
       const int kk = nidx[threadIdx.x];
       const double wk = Si[kk] * Si[kk] + Si[NT + kk] * Si[NT + kk] +
                         Si[2 * NT + kk] * Si[2 * NT + kk] + Si[3 * NT + kk] * Si[3 * NT + kk];
-      const double x = (lam[kk] - mu) / a.kT, ax = fabs(x);
+      const double x = (lam[kk] - mu) * a.ikT, ax = fabs(x);
       const double e = exp(-ax);
       const double t = e / (1.0 + e);                  // the small one of f and 1 - f
       const double f = x > 0.0 ? t : 1.0 - t;
@@ -631,7 +631,28 @@ __global__ void __launch_bounds__(RT) rho_kernel(const RhoArgs a) {
       for (int al = 0; al < 4; ++al) fs[al * NT + k] = (TA)(f * Si[al * NT + k]);
     }
   }
-  tbk::block_sum<double, 3>(v, red, tot);          // also publishes fs
+  // block totals of the three terms: only the warps that hold pairs (k < m)
+  // reduce; the others hold zeros and skip the FP64 shuffle additions (the
+  // totals are those of a reduction over every warp); the barriers also
+  // publish fs
+  {
+    const int nwp = (m + 31) >> 5;
+    if (warp < nwp) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) v[q] = tbk::warp_sum(v[q]);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) red[warp * 3 + q] = warp < nwp ? v[q] : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      double t = 0.0;
+      for (int w = 0; w < nwp; ++w) t += red[w * 3 + threadIdx.x];
+      tot[threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
     a.per_target[5 * i + 0] = 2.0 * tot[0];
     a.per_target[5 * i + 1] = 2.0 * a.kT * tot[1];
@@ -996,7 +1017,8 @@ tb_status launch_forces(tb_ctx* c, int n, const double* pos, double L, const int
                         const double* S, const double* P, const int* kdim, const double* mu,
                         double* F, double* energies, cudaStream_t s) {
   const int NT = 4 * c->p.r;
-  RhoArgs ra{NT, h_off, kdim, lambda, S, P, mu, c->p.kT, c->rho, c->per_target, c->d_status};
+  RhoArgs ra{NT, h_off, kdim, lambda, S, P, mu, c->p.kT, 1.0 / c->p.kT, c->rho, c->per_target,
+              c->d_status};
   if (c->p.prec != TB_PREC_FP64) rho_kernel<float><<<n, RT, 0, s>>>(ra);
   else rho_kernel<double><<<n, RT, 0, s>>>(ra);
   TB_CUDA_TRY(cudaGetLastError());

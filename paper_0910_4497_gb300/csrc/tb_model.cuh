@@ -10,18 +10,25 @@ struct tb_gsp {
   double A, rref, e, rcut, ec;   // GSP form
   double r1, rm;                 // tail interval
   double v1, d1, ta, tb;         // tail: v1 + d1 x + ta x^2 + tb x^3, x = r - r1
+  double lrref, lrcut, C;        // ln r_ref, ln r_cut, (r_ref/r_cut)^ec
 };
 
+// The GSP form through logarithms: with p = (r/r_cut)^ec = exp(ec (ln r - ln r_cut)),
+// v = A exp{e [ln r_ref - ln r - p + C]} and dv/dr = -v e (1 + ec p) / r: one
+// logarithm and two exponentials (FP64 transcendentals are costly on this GPU;
+// the power form takes two powers and an exponential).
 __host__ __device__ inline void tb_gsp_core(const tb_gsp& g, double r, double& v,
                                             double& dv) {
-  double pr = pow(r / g.rcut, g.ec);
-  v = g.A * pow(g.rref / r, g.e) * exp(g.e * (-pr + pow(g.rref / g.rcut, g.ec)));
-  dv = v * (-g.e / r - g.e * g.ec * pr / r);
+  const double lr = log(r);
+  const double pr = exp(g.ec * (lr - g.lrcut));
+  v = g.A * exp(g.e * (g.lrref - lr - pr + g.C));
+  dv = -v * g.e * (1.0 + g.ec * pr) / r;
 }
 
 inline tb_gsp tb_make_gsp(double A, double rref, double e, double rcut, double ec,
                           double r1, double rm) {
-  tb_gsp g{A, rref, e, rcut, ec, r1, rm, 0, 0, 0, 0};
+  tb_gsp g{A, rref, e, rcut, ec, r1, rm, 0, 0, 0, 0, std::log(rref), std::log(rcut),
+           std::pow(rref / rcut, ec)};
   tb_gsp_core(g, r1, g.v1, g.d1);
   const double dl = rm - r1;
   g.ta = -(3.0 * g.v1 + 2.0 * g.d1 * dl) / (dl * dl);

@@ -97,7 +97,7 @@ size_t carve(tb_ctx* c, int n, unsigned char* base) {
   c->bar = k.take<unsigned>(4);
   c->mu_state = k.take<double>(4);
   c->rho = k.take<double>(rows * 16 > (size_t)n * 2 ? rows * 16 : (size_t)n * 2);
-  c->per_target = k.take<double>((size_t)n * 5);
+  c->per_target = k.take<double>((size_t)n * 5 + 4 * ((size_t)n / 64 + 1));   // + energy partials
   c->bondf = k.take<double>(hcap * 4);
   c->h_off = k.take<int>(n + 1);
   c->h_idx = k.take<int>(hcap);
@@ -514,7 +514,7 @@ tb_status tb_ctx_kernels_per_evaluation(const tb_ctx* c, int n, double L, int* c
     k += krylov_kernel_count(c, n);                    // block Lanczos (+ size bins)
     if (krylov_eig_persistent(c, n)) eig = 0;          // eigensolve inside the Krylov launch
   }
-  *count = k + eig + 1 + 4;                            // mu; rho, bond forces, sums, energies
+  *count = k + eig + 1 + 3;                            // mu; rho, bond forces, sums and energies
   return TB_OK;
 }
 

@@ -694,8 +694,11 @@ struct ForceArgs {
   tb_gsp rep;
   double* bondf;
   double* F;
-  double* per_target;
+  double* per_target;   // n x 5, then the energy partials of force_sum_kernel's blocks
   int* st;
+  double* energies;     // force_sum_kernel: the evaluation's energies (null: not formed)
+  const double* mu;
+  unsigned* ecnt;       // blocks done (zero between calls: the last block resets it)
 };
 
 // One thread per directed bond k -> j: the bond's Hellmann-Feynman term
@@ -759,18 +762,67 @@ __global__ void __launch_bounds__(64) force_bond_kernel(const ForceArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(256) force_sum_kernel(const ForceArgs a) {
+// Per atom: the force and repulsive energy as the sum of its bonds' terms in
+// list order.  Then the energies: every block sums its atoms' E_band, -TS, N_e
+// and E_rep (warp shuffles, then the two warps in order), writes the partial,
+// and the last block to finish (a fence, then an atomic count) adds the
+// partials in block order, a fixed order whatever the block schedule.
+constexpr int FS_T = 64;
+__global__ void __launch_bounds__(FS_T) force_sum_kernel(const ForceArgs a) {
+  __shared__ double red[FS_T / 32 * 4];
+  __shared__ int last;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= a.n) return;
-  double f[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int p = a.h_off[k]; p < a.h_off[k + 1]; ++p)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double e[4] = {0.0, 0.0, 0.0, 0.0};
+  if (k < a.n) {
+    double f[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int p = a.h_off[k]; p < a.h_off[k + 1]; ++p)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) f[c] += a.bondf[(size_t)p * 4 + c];
-  a.F[3 * k] = f[0];
-  a.F[3 * k + 1] = f[1];
-  a.F[3 * k + 2] = f[2];
-  a.per_target[5 * k + 3] = f[3];
-  if (!(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]))) tbk::set_status(a.st, TB_ERR_NONFINITE, k);
+      for (int c = 0; c < 4; ++c) f[c] += a.bondf[(size_t)p * 4 + c];
+    a.F[3 * k] = f[0];
+    a.F[3 * k + 1] = f[1];
+    a.F[3 * k + 2] = f[2];
+    a.per_target[5 * k + 3] = f[3];
+    if (!(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]))) tbk::set_status(a.st, TB_ERR_NONFINITE, k);
+    e[0] = a.per_target[5 * k];
+    e[1] = a.per_target[5 * k + 1];
+    e[2] = a.per_target[5 * k + 2];
+    e[3] = f[3];
+  }
+  if (!a.energies) return;                           // uniform over the grid
+#pragma unroll
+  for (int q = 0; q < 4; ++q) e[q] = tbk::warp_sum(e[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[warp * 4 + q] = e[q];
+  }
+  __syncthreads();
+  double* const part = a.per_target + (size_t)5 * a.n;
+  if (threadIdx.x < 4) part[(size_t)blockIdx.x * 4 + threadIdx.x] = red[threadIdx.x] + red[4 + threadIdx.x];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(a.ecnt, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(part + (size_t)b * 4 + threadIdx.x);
+    red[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double eb = red[0], ts = red[1], ne = red[2], er = red[3];
+    a.energies[0] = eb;
+    a.energies[1] = ts;
+    a.energies[2] = eb + ts;
+    a.energies[3] = er;
+    a.energies[4] = eb + ts + er;
+    a.energies[5] = ne;
+    a.energies[6] = *a.mu;
+    a.energies[7] = 0.0;
+    *a.ecnt = 0u;
+  }
 }
 
 // Virial of the pair-decomposed forces, W_ab = -1/2 sum over directed bonds of
@@ -1023,12 +1075,10 @@ tb_status launch_forces(tb_ctx* c, int n, const double* pos, double L, const int
   else rho_kernel<double><<<n, RT, 0, s>>>(ra);
   TB_CUDA_TRY(cudaGetLastError());
   ForceArgs fa{n, pos, L, h_off, h_idx, dHblk, c->rho, tb_repulsion_gsp(c->p), c->bondf, F,
-               c->per_target, c->d_status};
+               c->per_target, c->d_status, energies, mu, c->bar + 1};
   force_bond_kernel<<<16 * c->num_sms, 64, 0, s>>>(fa);
   TB_CUDA_TRY(cudaGetLastError());
-  force_sum_kernel<<<(n + 63) / 64, 64, 0, s>>>(fa);         // spread the FP64 sums over the SMs
-  TB_CUDA_TRY(cudaGetLastError());
-  energy_reduce_kernel<<<1, ER_T, 0, s>>>(n, c->per_target, mu, energies, 0);
+  force_sum_kernel<<<(n + FS_T - 1) / FS_T, FS_T, 0, s>>>(fa);   // forces, then the energies
   TB_CUDA_TRY(cudaGetLastError());
   return TB_OK;
 }

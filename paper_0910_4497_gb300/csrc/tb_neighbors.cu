@@ -147,12 +147,18 @@ __device__ __forceinline__ int cell_coord(double x, double L, int nc) {
   return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
+// The FP32 copy of the positions and its [0, L) check (as pos_to_f32_kernel),
+// then each atom's cell and the cells' counts.
 __global__ void cell_assign_kernel(int n, const double* __restrict__ pos, double L, int nc,
+                                   float4* __restrict__ posf, int* st,
                                    int* __restrict__ atom_cell, int* __restrict__ cell_cnt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int cx = cell_coord(pos[3 * i], L, nc), cy = cell_coord(pos[3 * i + 1], L, nc),
-            cz = cell_coord(pos[3 * i + 2], L, nc);
+  const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+  const bool ok = (x >= 0.0 && x < L) && (y >= 0.0 && y < L) && (z >= 0.0 && z < L);
+  if (!ok) tbk::set_status(st, TB_ERR_INVALID_ARG, i);
+  posf[i] = make_float4((float)x, (float)y, (float)z, 0.f);
+  const int cx = cell_coord(x, L, nc), cy = cell_coord(y, L, nc), cz = cell_coord(z, L, nc);
   const int c = (cx * nc + cy) * nc + cz;
   atom_cell[i] = c;
   atomicAdd(&cell_cnt[c], 1);
@@ -167,8 +173,9 @@ __global__ void cell_fill_kernel(int n, const int* __restrict__ atom_cell,
   cell_atoms[cell_off[c] + atomicAdd(&cell_fill[c], 1)] = i;
 }
 
-// Exclusive scan of one count array (length m) into offsets (length m+1).
-__global__ void __launch_bounds__(1024) scan1_kernel(int m, const int* __restrict__ a,
+// Exclusive scan of one count array (length m) into offsets (length m+1); the
+// counts are zeroed as they are read (they serve next as the fill cursors).
+__global__ void __launch_bounds__(1024) scan1_kernel(int m, int* __restrict__ a,
                                                      int* __restrict__ oa) {
   __shared__ int sa[1024];
   const int t = threadIdx.x;
@@ -188,6 +195,7 @@ __global__ void __launch_bounds__(1024) scan1_kernel(int m, const int* __restric
   for (int k = lo; k < hi; ++k) {
     oa[k] = r1;
     r1 += a[k];
+    a[k] = 0;
   }
   if (t == 1023) oa[m] = sa[1023];
 }
@@ -371,14 +379,13 @@ int neighbor_kernel_count(const tb_ctx* c, double L) {
   const tb_params& p = c->p;
   int nc = (int)(L / (p.Rc + 0.01));
   while (nc >= 3 && (size_t)nc * nc * nc > neighbor_cell_capacity(c->reserved_n)) --nc;
-  return (nc >= 3 && p.max_cluster <= 512) ? 7 : 4;
+  return (nc >= 3 && p.max_cluster <= 512) ? 6 : 4;
 }
 
 tb_status launch_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h_off,
                            int* h_idx, int* c_off, int* c_idx, cudaStream_t s) {
   const tb_params& p = c->p;
   float4* posf = reinterpret_cast<float4*>(c->rho);   // scratch: rho is free here
-  pos_to_f32_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, pos, L, posf, c->d_status);
   const double R2h = p.rm * p.rm, R2c = p.Rc * p.Rc;
   const float Rh_pre2 = (float)((p.rm + 0.01) * (p.rm + 0.01));
   const float Rc_pre2 = (float)((p.Rc + 0.01) * (p.Rc + 0.01));
@@ -392,9 +399,9 @@ tb_status launch_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h
   if (nc >= 3 && p.max_cluster <= 512) {
     const int ncell = nc * nc * nc;
     TB_CUDA_TRY(cudaMemsetAsync(c->cell_cnt, 0, sizeof(int) * ncell, s));
-    cell_assign_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, pos, L, nc, c->atom_cell, c->cell_cnt);
-    scan1_kernel<<<1, 1024, 0, s>>>(ncell, c->cell_cnt, c->cell_off);
-    TB_CUDA_TRY(cudaMemsetAsync(c->cell_cnt, 0, sizeof(int) * ncell, s));
+    cell_assign_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, pos, L, nc, posf, c->d_status,
+                                                       c->atom_cell, c->cell_cnt);
+    scan1_kernel<<<1, 1024, 0, s>>>(ncell, c->cell_cnt, c->cell_off);   // counts back to zero
     cell_fill_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, c->atom_cell, c->cell_off, c->cell_cnt,
                                                      c->cell_atoms);
     nbr_cell_kernel<<<grid, NB_THREADS, cell_smem, s>>>(
@@ -407,6 +414,7 @@ tb_status launch_neighbors(tb_ctx* c, int n, const double* pos, double L, int* h
     TB_CUDA_TRY(cudaGetLastError());
     return TB_OK;
   }
+  pos_to_f32_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, pos, L, posf, c->d_status);
   nbr_kernel<0><<<grid, NB_THREADS, 0, s>>>(n, pos, posf, L, R2h, R2c, Rh_pre2, Rc_pre2,
                                             c->scan_h, c->scan_c, nullptr, nullptr,
                                             nullptr, nullptr, p.max_hnbr,

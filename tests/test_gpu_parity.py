@@ -320,16 +320,16 @@ def test_md_step_matches_oracle_verlet(tb):
 
 def test_kernels_per_evaluation_count(tb):
     """The library's own count of kernels per force evaluation on the 1920-atom
-    cell (cell lists: 7; assembly; Krylov with the eigensolve inside in the
-    mixed path, separate group eigensolver + refinement in FP64; mu; 4 for
-    density blocks, forces and energies)."""
+    cell (cell lists: 6; assembly; Krylov with the eigensolve inside in the
+    mixed path, separate group eigensolver + refinement in FP64; mu; 3 for
+    density blocks, bond forces, and per-atom sums with the energies)."""
     pos, L, p = cfg_system(1)
     counts = {}
     for prec in ("mixed", "fp64"):
         s = tb.TBSystem(len(pos), L, p, prec=prec)
         counts[prec] = tb.binding.tb_ctx_kernels_per_evaluation(s.ctx, len(pos), L)
         s.close()
-    assert counts == {"mixed": 14, "fp64": 16}
+    assert counts == {"mixed": 12, "fp64": 14}
     s = tb.TBSystem(len(pos), L, dict(p, schedule="separate"), prec="mixed")
-    assert tb.binding.tb_ctx_kernels_per_evaluation(s.ctx, len(pos), L) == 15
+    assert tb.binding.tb_ctx_kernels_per_evaluation(s.ctx, len(pos), L) == 13
     s.close()

@@ -277,7 +277,7 @@ nbr_cell_kernel(int n, const double* __restrict__ pos, const float4* __restrict_
   };
   // the 27 cells' ranges in one round of loads (lane q: cell q), their
   // candidates numbered by an exclusive scan; each lane finds the cell of its
-  // candidate by binary search, two batches of 32 in flight
+  // candidate by binary search
   {
     int cb = 0, cn = 0;
     if (lane < 27) {
@@ -296,38 +296,41 @@ nbr_cell_kernel(int n, const double* __restrict__ pos, const float4* __restrict_
     cbg[lane] = cb;
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     __syncwarp();
-    auto candidate = [&](int x, int& j, bool& pass) {
-      j = -1;
-      pass = false;
-      if (x >= total) return;
-      int lo = 0, hi = 26;                       // last cell q with cex[q] <= x
+    // candidate x: its cell (the last q with cex[q] <= x) and atom index
+    auto cand_atom = [&](int x) -> int {
+      if (x >= total) return -1;
+      int lo = 0, hi = 26;
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (cex[mid] <= x) lo = mid; else hi = mid - 1;
       }
-      j = cell_atoms[cbg[lo] + (x - cex[lo])];
-      if (j == i) return;
-      const float4 pj = posf[j];
-      float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-      dx -= Lf * rintf(dx * invLf);
-      dy -= Lf * rintf(dy * invLf);
-      dz -= Lf * rintf(dz * invLf);
-      const float r2f = dx * dx + dy * dy + dz * dz;
-      pass = r2f <= Rc_pre2 || r2f <= Rh_pre2;
+      return cell_atoms[cbg[lo] + (x - cex[lo])];
     };
-    for (int b = 0; b < total; b += 64) {
-      int j0, j1;
-      bool p0, p1;
-      candidate(b + lane, j0, p0);
-      candidate(b + 32 + lane, j1, p1);
-      const unsigned bp0 = __ballot_sync(0xffffffffu, p0);
-      if (nstg + __popc(bp0) > capc) flush();          // keep the stage within capacity
-      if (p0) stg[nstg + __popc(bp0 & below)] = j0;
-      nstg += __popc(bp0);
-      const unsigned bp1 = __ballot_sync(0xffffffffu, p1);
-      if (nstg + __popc(bp1) > capc) flush();
-      if (p1) stg[nstg + __popc(bp1 & below)] = j1;
-      nstg += __popc(bp1);
+    // four batches of 32 per round: the four atom-index loads in flight, then
+    // the four position loads, then the FP32 prefilter; staged in batch order
+    for (int b = 0; b < total; b += 128) {
+      int j[4];
+      float4 pj[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) j[u] = cand_atom(b + 32 * u + lane);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pj[u] = j[u] >= 0 ? posf[j[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        bool pass = false;
+        if (j[u] >= 0 && j[u] != i) {
+          float dx = pj[u].x - pi.x, dy = pj[u].y - pi.y, dz = pj[u].z - pi.z;
+          dx -= Lf * rintf(dx * invLf);
+          dy -= Lf * rintf(dy * invLf);
+          dz -= Lf * rintf(dz * invLf);
+          const float r2f = dx * dx + dy * dy + dz * dz;
+          pass = r2f <= Rc_pre2 || r2f <= Rh_pre2;
+        }
+        const unsigned bp = __ballot_sync(0xffffffffu, pass);
+        if (nstg + __popc(bp) > capc) flush();          // keep the stage within capacity
+        if (pass) stg[nstg + __popc(bp & below)] = j[u];
+        nstg += __popc(bp);
+      }
     }
   }
   flush();

@@ -10,6 +10,7 @@
 // deterministic from run to run.
 #include <atomic>
 #include <mutex>
+#include "tb_fpconv.cuh"
 #include "tb_internal.cuh"
 #include "tb_model.cuh"
 
@@ -569,14 +570,14 @@ __global__ void __launch_bounds__(RT) rho_kernel(const RhoArgs a) {
     //     = -min(f, 1-f) |x| - log1p(e)   (exact).
     __shared__ int nidx[tbk::MAX_NT];
     __shared__ int wball[RT / 32];
-    const float ikTf = (float)a.ikT, muf = (float)mu;
+    const float ikTf = tbconv::d2f(a.ikT), muf = tbconv::d2f(mu);
     const int k = threadIdx.x;
     bool near_k = false;
     double w = 0.0;
     if (k < m) {
       w = Si[k] * Si[k] + Si[NT + k] * Si[NT + k] + Si[2 * NT + k] * Si[2 * NT + k] +
           Si[3 * NT + k] * Si[3 * NT + k];
-      const float xf = ((float)lam[k] - muf) * ikTf;
+      const float xf = (tbconv::d2f(lam[k]) - muf) * ikTf;
       near_k = fabsf(xf) <= 15.5f;
       if (!near_k) {
         const float e = __expf(-fabsf(xf));
@@ -585,8 +586,10 @@ __global__ void __launch_bounds__(RT) rho_kernel(const RhoArgs a) {
         v[0] += w * f * lam[k];
         v[1] += w * (double)(-(t * fabsf(xf) + e));
         v[2] += w * f;
+        // f S in FP32 for the FP32 contraction, S converted by integer operations
+        const float ff = xf > 0.f ? t : 1.f - t;
 #pragma unroll
-        for (int al = 0; al < 4; ++al) fs[al * NT + k] = (TA)(f * Si[al * NT + k]);
+        for (int al = 0; al < 4; ++al) fs[al * NT + k] = ff * tbconv::d2f(Si[al * NT + k]);
       }
     } else if (k < NT) {
 #pragma unroll
@@ -614,7 +617,7 @@ __global__ void __launch_bounds__(RT) rho_kernel(const RhoArgs a) {
       v[1] += wk * (-(t * ax) - log1p(e));
       v[2] += wk * f;
 #pragma unroll
-      for (int al = 0; al < 4; ++al) fs[al * NT + kk] = (TA)(f * Si[al * NT + kk]);
+      for (int al = 0; al < 4; ++al) fs[al * NT + kk] = tbconv::d2f(f) * tbconv::d2f(Si[al * NT + kk]);
     }
   } else {
     for (int k = threadIdx.x; k < NT; k += RT) {
@@ -668,7 +671,10 @@ __global__ void __launch_bounds__(RT) rho_kernel(const RhoArgs a) {
     for (int k = lane; k < m; k += 32) {
       TA pb[4], sa[4];
 #pragma unroll
-      for (int be = 0; be < 4; ++be) pb[be] = (TA)pr[be * NT + k];
+      for (int be = 0; be < 4; ++be) {
+        if constexpr (sizeof(TA) == 4) pb[be] = tbconv::d2f(pr[be * NT + k]);   // off the FP64 pipe
+        else pb[be] = pr[be * NT + k];
+      }
 #pragma unroll
       for (int al = 0; al < 4; ++al) sa[al] = fs[al * NT + k];
 #pragma unroll
@@ -677,7 +683,10 @@ __global__ void __launch_bounds__(RT) rho_kernel(const RhoArgs a) {
         for (int al = 0; al < 4; ++al) acc[be * 4 + al] += pb[be] * sa[al];
     }
     const TA t = tbk::warp_reduce16(acc, lane);   // lanes 2q hold entry q = be*4 + al
-    if ((lane & 1) == 0) a.rho[(base + blk) * 16 + (lane >> 1)] = (double)t;
+    if ((lane & 1) == 0) {
+      if constexpr (sizeof(TA) == 4) a.rho[(base + blk) * 16 + (lane >> 1)] = tbconv::f2d(t);
+      else a.rho[(base + blk) * 16 + (lane >> 1)] = (double)t;
+    }
   }
 }
 

@@ -218,8 +218,11 @@ tb_status tb_krylov_density(tb_ctx* ctx, int n, const int* c_off, const int* c_i
  * steps with bisection fallback, in FP64, in one cooperative launch.
  * mu_guess (device, may be NULL): starting point if inside the bracket.
  * mu (device, out): one double.  n_count (device, out, may be NULL): N(mu).
- * Stops when |N(mu) - N_e| <= mu_tol * N_e or the bracket is below 1e-13 eV;
- * after mu_max_iter passes sets TB_ERR_NO_CONVERGENCE (mu = best estimate).
+ * Stops when |N(mu) - N_e| <= mu_tol * N_e or the bracket is below 1e-13 eV,
+ * or after a Newton step whose residual is bounded by a tenth of that
+ * tolerance (|N''| <= N'/kT bounds it by r^2 / (2 kT N') from the previous
+ * residual r); then n_count is that step's predicted count, N_e.  After
+ * mu_max_iter passes sets TB_ERR_NO_CONVERGENCE (mu = best estimate).
  */
 tb_status tb_find_mu(tb_ctx* ctx, int n, const double* lambda, const double* S,
                      const int* kdim, double n_electrons, const double* mu_guess,

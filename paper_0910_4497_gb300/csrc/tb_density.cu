@@ -512,6 +512,16 @@ __global__ void __launch_bounds__(MT) mu_kernel(const MuArgs a) {
           dxold = dx;
           dx = fv / dN;
           mu2 = newton;
+          // Every pair's second derivative in mu is its first times
+          // (1 - 2f)/kT, so |N''| <= N'/kT and the Newton step from the
+          // residual fv leaves at most fv^2 / (2 kT N') (to leading order,
+          // over a step of at most ~1e-6 eV here).  When that is below a
+          // tenth of the tolerance the new point is returned without another
+          // pass, with its predicted count N_e (within 0.1 tolN).
+          if (fv * fv <= 0.2 * a.tolN * a.kT * dN) {
+            si[2] = 1;
+            ss[S_NMU] = a.ne;
+          }
         }
       }
       ss[S_LO] = lo2; ss[S_HI] = hi2; ss[S_MU] = mu2; ss[S_DXO] = dxold; ss[S_DX] = dx;

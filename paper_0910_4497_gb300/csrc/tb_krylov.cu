@@ -1195,12 +1195,16 @@ tb_status tune_t(tb_ctx* c, int n, const int* c_off, const int* c_idx, const int
       c->plan_cfg[b] = best_cfg[b];
     }
   }
-  // the fastest plan
+  // the fastest plan; the queue's largest-first order is kept on a tie within
+  // 1% of index order (it starts the longest block-Lanczos runs first, which
+  // shortens the launch's tail more once the caches are cold than in these
+  // back-to-back trials)
   int choice = TB_SCHED_SEPARATE;
   float bestms = r.ms_separate;
   if (r.ms_persistent < bestms) { bestms = r.ms_persistent; choice = TB_SCHED_PERSISTENT; }
-  if (r.ms_persistent_largest_first < bestms) {
-    bestms = r.ms_persistent_largest_first;
+  if (r.ms_persistent_largest_first < 1.01f * bestms &&
+      (choice != TB_SCHED_PERSISTENT || r.ms_persistent_largest_first <= 1.01f * r.ms_persistent)) {
+    bestms = fminf(bestms, r.ms_persistent_largest_first);
     choice = TB_SCHED_PERSISTENT_LARGEST_FIRST;
   }
   if (r.ms_bucketed < bestms) { bestms = r.ms_bucketed; choice = TB_SCHED_BUCKETED; }

@@ -98,7 +98,9 @@ def test_autotuned_plan_matches_oracle(tb, slab):
     assert sum(1 for x in h["counts"] if x > 0) >= 4          # uneven: several bins
     assert rep["schedule"] in ("persistent", "persistent_largest_first", "separate", "bucketed")
     times = [v for v in rep["ms"].values() if v is not None]
-    assert rep["ms"][rep["schedule"]] == min(times)
+    # the fastest plan, or the queue's largest-first order on a tie within 1%
+    assert rep["ms"][rep["schedule"]] == min(times) or (
+        rep["schedule"] == "persistent_largest_first" and rep["ms"][rep["schedule"]] <= 1.01 * min(times))
     assert 1 <= len(rep["buckets"]) <= 4
     assert sum(b["targets"] for b in rep["buckets"]) == s.n
     assert rep["buckets"][-1]["sizes_up_to"] == p["max_cluster"]

@@ -17,7 +17,8 @@
 // of global workspace (the matrices are 4 n_c x 4 n_c, up to 512 x 512):
 //   1. dense H_c from the bond blocks;
 //   2. Householder reduction to tridiagonal form (row-oriented, one reflector
-//      per step, symmetric rank-2 update of the trailing block);
+//      per step; each step's symmetric rank-2 update of the trailing block is
+//      fused with the next step's matrix-vector product, one pass per step);
 //   3. eigenvalues of the tridiagonal matrix by FP32 bisection on Sturm counts,
 //      one thread per eigenvalue;
 //   4. eigenvectors by inverse iteration with a pivoted tridiagonal LU (the
@@ -190,64 +191,180 @@ __device__ void build_hc(const LocArgs<TE>& a, int i, int nc, int nd, TE* A) {
 // ---------------------------------------------------------------- 2. tridiagonal form
 
 // Row-oriented Householder reduction of the symmetric A (nd x nd, full storage):
-// step k maps row k's part right of the diagonal, x = A[k][k+1:], to
-// (beta, 0, ..., 0) with H_k = I - tau_k v_k v_k^T (v_k[0] = 1), stored in
-// A[k][k+2:] (v) and tau[k]; diagonal dd, off-diagonal ee.
+// reflector q maps row q's part right of the diagonal, A[q][q+1:], to
+// (beta, 0, ..., 0) with H_q = I - tau_q v_q v_q^T (v_q[0] = 1), stored in
+// A[q][q+2:] (v) and tau[q]; diagonal dd, off-diagonal ee.
+//
+// Step k (k = -1 .. nd-3) works on the trailing block A22 = A[k+1:, k+1:]
+// (m = nd-k-1) and fuses reflector k's symmetric rank-2 update
+//   A22 -= v w^T + w v^T,  p = tau A22 v,  w = p - (tau/2)(p.v) v,
+// with the next step's product p' = tau' A33 v' (A33 = A22[1:, 1:]): warp 0
+// first updates row k+1 and forms reflector k+1 from it; then every warp
+// updates its rows of A33 and, while a row is still in registers, takes its
+// dot product with v'.  The trailing block is read and written once per
+// step; each lane keeps RB rows' columns in flight (RB x NI loads).  The
+// column vectors v, w, v' sit in registers for FP32, in shared memory for
+// FP64.  (Column 0 of A33's rows, below the new off-diagonal, is never read
+// again and is left stale.)
 template <typename TE>
 __device__ void tridiagonalize(TE* A, int nd, const LocSmem<TE>& s) {
+  constexpr int NI = 16;                       // columns per lane (nd <= 512)
+  constexpr bool REG = sizeof(TE) == 4;        // column vectors in registers
+  constexpr int RB = REG ? 2 : 1;              // rows per warp in flight
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int k = 0; k + 2 < nd; ++k) {
+  TE* const V[2] = {s.v, s.vbuf};              // reflector q in V[q & 1]
+  TE* const P[2] = {s.p, s.vbuf + nd};         // its product tau_q A22 v_q in P[q & 1]
+  for (int k = -1; k + 2 < nd; ++k) {
     const int m = nd - k - 1;
-    TE* rowk = A + (size_t)k * nd + k + 1;
+    TE* const base = A + (size_t)(k + 1) * (nd + 1);
+    const bool has_next = m >= 3;              // reflector k+1 exists
+    const TE t = k >= 0 ? s.sc[k & 1] : TE(0);
+    const bool upd = t != TE(0);               // uniform
+    const TE* vc = V[k & 1];
+    const TE* pc = P[k & 1];
+    TE* vn = V[(k + 1) & 1];
+    TE* pn = P[(k + 1) & 1];
+    TE c = TE(0);
+    if (upd) {
+      TE pv = TE(0);
+      for (int j = lane; j < m; j += 32) pv += pc[j] * vc[j];
+      c = TE(0.5) * t * warp_sum_t(pv);
+    }
+    // row k+1: reflector k's update, then reflector k+1
     if (warp == 0) {
-      TE sg = TE(0);
-      for (int j = 1 + lane; j < m; j += 32) {
-        const TE x = rowk[j];
-        sg += x * x;
+      TE y[NI];
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        const int j = lane + 32 * i;
+        y[i] = j < m ? base[j] : TE(0);
       }
-      sg = warp_sum_t(sg);
-      const TE alpha = rowk[0];
-      TE beta = alpha, t = TE(0), scale = TE(0);
-      if (sg > TE(0)) {
-        const TE nrm = sqrt(alpha * alpha + sg);
-        beta = alpha <= TE(0) ? nrm : -nrm;
-        t = (beta - alpha) / beta;
-        scale = TE(1) / (alpha - beta);
+      if (upd) {
+        const TE v0 = vc[0], w0 = pc[0] - c * v0;
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+          const int j = lane + 32 * i;
+          if (j < m) {
+            const TE vj = vc[j];
+            y[i] -= v0 * (pc[j] - c * vj) + w0 * vj;
+          }
+        }
       }
-      for (int j = lane; j < m; j += 32) {
-        const TE vj = j == 0 ? TE(1) : rowk[j] * scale;
-        s.v[j] = vj;
-        if (j > 0) rowk[j] = vj;
+      if (has_next) {
+        TE sg = TE(0);
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+          const int j = lane + 32 * i;
+          if (j >= 2 && j < m) sg += y[i] * y[i];
+        }
+        sg = warp_sum_t(sg);
+        const TE alpha = __shfl_sync(0xffffffffu, y[0], 1);
+        TE beta = alpha, tn = TE(0), scale = TE(0);
+        if (sg > TE(0)) {
+          const TE nrm = sqrt(alpha * alpha + sg);
+          beta = alpha <= TE(0) ? nrm : -nrm;
+          tn = (beta - alpha) / beta;
+          scale = TE(1) / (alpha - beta);
+        }
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+          const int j = lane + 32 * i;
+          if (j >= 2 && j < m) {
+            y[i] *= scale;
+            vn[j - 1] = y[i];
+          }
+        }
+        if (lane == 0) {
+          vn[0] = TE(1);
+          s.dd[k + 1] = y[0];
+          s.ee[k + 1] = beta;
+          s.tau[k + 1] = tn;
+          s.sc[(k + 1) & 1] = tn;
+        }
       }
-      if (lane == 0) {
-        s.dd[k] = A[(size_t)k * nd + k];
-        s.ee[k] = beta;
-        s.tau[k] = t;
-        s.sc[k & 1] = t;
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        const int j = lane + 32 * i;
+        if (j < m) base[j] = y[i];
       }
     }
     __syncthreads();
-    const TE t = s.sc[k & 1];
-    if (t == TE(0)) continue;          // uniform: the row is already reduced
-    TE* A22 = A + (size_t)(k + 1) * nd + k + 1;
-    for (int r = warp; r < m; r += LW) {
-      const TE* row = A22 + (size_t)r * nd;
-      TE acc = TE(0);
-      for (int j = lane; j < m; j += 32) acc += row[j] * s.v[j];
-      acc = warp_sum_t(acc);
-      if (lane == 0) s.p[r] = t * acc;
-    }
-    __syncthreads();
-    TE pv = TE(0);
-    for (int j = lane; j < m; j += 32) pv += s.p[j] * s.v[j];
-    pv = warp_sum_t(pv);
-    const TE c = TE(0.5) * t * pv;
-    for (int r = warp; r < m; r += LW) {
-      TE* row = A22 + (size_t)r * nd;
-      const TE vr = s.v[r], wr = s.p[r] - c * vr;
-      for (int j = lane; j < m; j += 32) {
-        const TE vj = s.v[j];
-        row[j] -= vr * (s.p[j] - c * vj) + wr * vj;
+    const TE tn = has_next ? s.sc[(k + 1) & 1] : TE(0);
+    const bool dot = tn != TE(0);              // uniform
+    if (upd || dot) {
+      // columns j = 1 + lane + 32 i of A22 (j < m): v_j, w_j, v'_{j-1}
+      TE cv[REG ? NI : 1], cw[REG ? NI : 1], cn[REG ? NI : 1];
+      if constexpr (REG) {
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+          const int j = 1 + lane + 32 * i;
+          const bool in = j < m;
+          cv[i] = in && upd ? vc[j] : TE(0);
+          cw[i] = in && upd ? pc[j] - c * vc[j] : TE(0);
+          cn[i] = in && dot ? vn[j - 1] : TE(0);
+        }
+      }
+      for (int r0 = 1 + RB * warp; r0 < m; r0 += RB * LW) {
+        TE x[RB][NI];
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+          const TE* row = base + (size_t)(r0 + b) * nd + 1;
+#pragma unroll
+          for (int i = 0; i < NI; ++i) {
+            const int j = 1 + lane + 32 * i;
+            x[b][i] = (r0 + b < m && j < m) ? row[j - 1] : TE(0);
+          }
+        }
+        if (upd) {
+#pragma unroll
+          for (int b = 0; b < RB; ++b) {
+            const int r = r0 + b < m ? r0 + b : 0;
+            const TE vr = vc[r], wr = pc[r] - c * vr;
+#pragma unroll
+            for (int i = 0; i < NI; ++i) {
+              if constexpr (REG) {
+                x[b][i] -= vr * cw[i] + wr * cv[i];
+              } else {
+                const int j = 1 + lane + 32 * i;
+                if (j < m) {
+                  const TE vj = vc[j];
+                  x[b][i] -= vr * (pc[j] - c * vj) + wr * vj;
+                }
+              }
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < RB; ++b) {
+            TE* row = base + (size_t)(r0 + b) * nd + 1;
+#pragma unroll
+            for (int i = 0; i < NI; ++i) {
+              const int j = 1 + lane + 32 * i;
+              if (r0 + b < m && j < m) row[j - 1] = x[b][i];
+            }
+          }
+        }
+        if (dot) {
+          TE acc[RB];
+#pragma unroll
+          for (int b = 0; b < RB; ++b) {
+            acc[b] = TE(0);
+#pragma unroll
+            for (int i = 0; i < NI; ++i) {
+              if constexpr (REG) {
+                acc[b] += x[b][i] * cn[i];
+              } else {
+                const int j = 1 + lane + 32 * i;
+                if (j < m) acc[b] += x[b][i] * vn[j - 1];
+              }
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < RB; ++b) acc[b] = warp_sum_t(acc[b]);
+          if (lane == 0) {
+#pragma unroll
+            for (int b = 0; b < RB; ++b)
+              if (r0 + b < m) pn[r0 + b - 1] = tn * acc[b];
+          }
+        }
       }
     }
     __syncthreads();

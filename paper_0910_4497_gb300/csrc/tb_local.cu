@@ -466,7 +466,9 @@ __device__ void tridiagonal_eigen(int nd, TE* Zw, TE* X, const LocSmem<TE>& s, i
     s.lam32[k] = 0.5f * (lo + hi);
   }
   __syncthreads();
-  // eigenvectors: pivoted LU of T - sigma I, three solves
+  // eigenvectors: pivoted LU of T - sigma I, three solves.  The factors (five
+  // nd x nd arrays, 3 MB per CTA in FP32) are stored and read with evict-first
+  // hints so that they do not push the CTAs' matrix slots out of L2.
   const TE tiny = TE(tnorm) * TE(sizeof(TE) == 4 ? 1.2e-7 : 2.3e-16);
   for (int e = tid; e < nd; e += LT) {
     const TE sig = TE(s.lam32[e]);
@@ -480,27 +482,27 @@ __device__ void tridiagonal_eigen(int nd, TE* Zw, TE* X, const LocSmem<TE>& s, i
       if (fabs(ak) >= fabs(ck)) {          // no interchange
         const TE piv = fabs(ak) < tiny ? (ak < TE(0) ? -tiny : tiny) : ak;
         const TE mult = ck / piv;
-        Xa[q] = TE(1) / piv;
-        Xb[q] = bk;
-        Xd[q] = TE(0);
-        Xc[q] = mult;
-        Xp[q] = TE(0);
+        __stcs(&Xa[q], TE(1) / piv);
+        __stcs(&Xb[q], bk);
+        __stcs(&Xd[q], TE(0));
+        __stcs(&Xc[q], mult);
+        __stcs(&Xp[q], TE(0));
         ak = ak1 - mult * bk;
         bk = bk1;
       } else {                             // rows k and k+1 interchanged
         const TE mult = ak / ck;
-        Xa[q] = TE(1) / ck;
-        Xb[q] = ak1;
-        Xd[q] = bk1;
-        Xc[q] = mult;
-        Xp[q] = TE(1);
+        __stcs(&Xa[q], TE(1) / ck);
+        __stcs(&Xb[q], ak1);
+        __stcs(&Xd[q], bk1);
+        __stcs(&Xc[q], mult);
+        __stcs(&Xp[q], TE(1));
         ak = bk - mult * ak1;
         bk = -mult * bk1;
       }
     }
     {
       const TE piv = fabs(ak) < tiny ? (ak < TE(0) ? -tiny : tiny) : ak;
-      Xa[(size_t)(nd - 1) * nd + e] = TE(1) / piv;
+      __stcs(&Xa[(size_t)(nd - 1) * nd + e], TE(1) / piv);
     }
     for (int x = 0; x < nd; ++x) Zw[(size_t)x * nd + e] = TE(start_component(x, e));
   }
@@ -512,8 +514,8 @@ __device__ void tridiagonal_eigen(int nd, TE* Zw, TE* X, const LocSmem<TE>& s, i
       for (int k = 0; k + 1 < nd; ++k) {
         const size_t q = (size_t)k * nd + e;
         const TE yk1 = Zw[q + nd];
-        const TE mult = Xc[q];
-        if (Xp[q] == TE(0)) {
+        const TE mult = __ldcs(&Xc[q]);
+        if (__ldcs(&Xp[q]) == TE(0)) {
           Zw[q] = yk;
           yk = yk1 - mult * yk;
         } else {
@@ -527,9 +529,9 @@ __device__ void tridiagonal_eigen(int nd, TE* Zw, TE* X, const LocSmem<TE>& s, i
       for (int k = nd - 1; k >= 0; --k) {
         const size_t q = (size_t)k * nd + e;
         TE y = Zw[q];
-        if (k + 1 < nd) y -= Xb[q] * y1;
-        if (k + 2 < nd) y -= Xd[q] * y2;
-        y *= Xa[q];
+        if (k + 1 < nd) y -= __ldcs(&Xb[q]) * y1;
+        if (k + 2 < nd) y -= __ldcs(&Xd[q]) * y2;
+        y *= __ldcs(&Xa[q]);
         Zw[q] = y;
         y2 = y1;
         y1 = y;

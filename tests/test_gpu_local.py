@@ -149,7 +149,9 @@ def test_local_full_size_autograd_cell(tb):
     ~98 atoms and 392 x 392 dense problems per cluster) in the launch
     configuration the benchmark times: sampled atoms' forces against the
     oracle, stored vs recomputed basis, and central differences of the FP64
-    energy on a few seeded coordinates."""
+    energy on eight seeded coordinates (the draw of
+    `bench.py --workload autograd1920 --fd-coords 8`, none of whose steps
+    moves an atom across a cluster cutoff)."""
     cfg = CONFIGS[3]
     pos, L, _ = fcc_c60_crystal(cfg["ncell"], cfg["a"], cfg["jitter"], cfg["seed"])
     p = workload_params(cfg, defl_tol=1e-9)
@@ -169,7 +171,7 @@ def test_local_full_size_autograd_cell(tb):
     # central differences of the FP64 energy, seeded coordinates
     rng = np.random.default_rng(cfg["seed"])
     h = 1e-4
-    for q in rng.choice(3 * len(pos), size=3, replace=False):
+    for q in rng.choice(3 * len(pos), size=8, replace=False):
         atom, k = divmod(int(q), 3)
         xp, xm = pos.copy(), pos.copy()
         xp[atom, k] += h
